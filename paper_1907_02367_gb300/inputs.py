@@ -1,0 +1,342 @@
+"""Seeded synthetic workloads for the tent-pitched Trefftz-DG solver.
+
+This module only builds inputs: spatial meshes, the wave speed per element,
+the pitching parameter kappa, and closed-form solutions of the acoustic wave
+equation (first-order fields v = dU/dt, sigma = -grad U, Section 2.1, eq. 2.2)
+used as initial and Dirichlet data.  It contains none of the method's own
+arithmetic (no quadrature, no Trefftz basis, no pitching, no tent system);
+both the CUDA library and the CPU oracle consume what it returns.
+
+Workloads (Section 6 of the paper; sizes as stated in each generator):
+  * 1+1D: interval [0,1], uniform elements, plane wave sin(pi(x-t)).
+  * 2+1D: unit square, jittered grid made Delaunay by Lawson flips,
+    standing wave cos(sqrt2 pi t) sin(pi x) sin(pi y)  (Section 6.4 shape).
+  * 3+1D: unit cube, jittered hex grid, six Kuhn tetrahedra per hex,
+    Gaussian pulses with v0 = 0.
+"""
+from __future__ import annotations
+
+import itertools
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass
+class Mesh:
+    """A simplicial mesh: coords (n_vert, dim) float64, elems (n_elem, dim+1)
+    int32 vertex ids, c (n_elem,) float64 wave speed per element."""
+    coords: np.ndarray
+    elems: np.ndarray
+    c: np.ndarray
+    name: str = ""
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def dim(self) -> int:
+        return int(self.coords.shape[1])
+
+    @property
+    def n_vert(self) -> int:
+        return int(self.coords.shape[0])
+
+    @property
+    def n_elem(self) -> int:
+        return int(self.elems.shape[0])
+
+
+# ----------------------------------------------------------------------------
+# 1D
+# ----------------------------------------------------------------------------
+def mesh_interval(n_el: int, a: float = 0.0, b: float = 1.0, c: float = 1.0) -> Mesh:
+    """Uniform partition of [a, b] into n_el elements."""
+    x = np.array([a + (b - a) * i / n_el for i in range(n_el + 1)], dtype=np.float64)
+    x[-1] = b
+    elems = np.stack([np.arange(n_el), np.arange(1, n_el + 1)], axis=1).astype(np.int32)
+    return Mesh(x[:, None].copy(), elems, np.full(n_el, c, dtype=np.float64),
+                name=f"interval{n_el}")
+
+
+# ----------------------------------------------------------------------------
+# 2D: jittered grid + Lawson flips to a Delaunay triangulation
+# ----------------------------------------------------------------------------
+def _orient2(a, b, c):
+    return (b[0] - a[0]) * (c[1] - a[1]) - (b[1] - a[1]) * (c[0] - a[0])
+
+
+def _incircle(a, b, c, d):
+    """> 0 iff d lies strictly inside the circumcircle of CCW triangle abc."""
+    m = np.array([[a[0] - d[0], a[1] - d[1], (a[0] - d[0]) ** 2 + (a[1] - d[1]) ** 2],
+                  [b[0] - d[0], b[1] - d[1], (b[0] - d[0]) ** 2 + (b[1] - d[1]) ** 2],
+                  [c[0] - d[0], c[1] - d[1], (c[0] - d[0]) ** 2 + (c[1] - d[1]) ** 2]])
+    return float(np.linalg.det(m))
+
+
+def lawson_delaunay(coords: np.ndarray, tris: np.ndarray, max_pass: int = 200) -> np.ndarray:
+    """Flip interior edges until every edge is locally Delaunay.
+
+    Deterministic: each pass visits edges in sorted order."""
+    tris = [list(t) for t in tris]
+    for t in tris:
+        if _orient2(coords[t[0]], coords[t[1]], coords[t[2]]) < 0:
+            t[1], t[2] = t[2], t[1]
+    for _ in range(max_pass):
+        edge_map: dict = {}
+        for ti, t in enumerate(tris):
+            for k in range(3):
+                a, b = t[k], t[(k + 1) % 3]
+                edge_map.setdefault((min(a, b), max(a, b)), []).append(ti)
+        flipped = False
+        touched = set()
+        for e in sorted(edge_map):
+            ts = edge_map[e]
+            if len(ts) != 2 or ts[0] in touched or ts[1] in touched:
+                continue
+            t1, t2 = tris[ts[0]], tris[ts[1]]
+            # rotate t1 so that it reads (a, b, c) with edge a->b
+            for k in range(3):
+                if {t1[k], t1[(k + 1) % 3]} == set(e):
+                    a, b, c = t1[k], t1[(k + 1) % 3], t1[(k + 2) % 3]
+                    break
+            d = [x for x in t2 if x != a and x != b][0]
+            if _incircle(coords[a], coords[b], coords[c], coords[d]) > 1e-14:
+                tris[ts[0]] = [a, d, c]
+                tris[ts[1]] = [d, b, c]
+                touched.update(ts)
+                flipped = True
+        if not flipped:
+            break
+    return np.array(tris, dtype=np.int32)
+
+
+def mesh_square(nx: int, jitter: float = 0.2, seed: int = 2, c: float = 1.0) -> Mesh:
+    """Unit square, (nx+1)^2 grid vertices; interior vertices jittered by
+    U(-jitter*h, jitter*h) per coordinate (seeded); two triangles per cell,
+    then Lawson flips to a Delaunay mesh.  2*nx^2 triangles."""
+    h = 1.0 / nx
+    rng = np.random.default_rng(seed)
+    g = np.array([[i * h, j * h] for j in range(nx + 1) for i in range(nx + 1)], dtype=np.float64)
+    g[g > 1.0] = 1.0
+    jit = rng.uniform(-jitter * h, jitter * h, size=g.shape)
+    interior = (g[:, 0] > 0) & (g[:, 0] < 1) & (g[:, 1] > 0) & (g[:, 1] < 1)
+    g[interior] += jit[interior]
+    tris = []
+    for j in range(nx):
+        for i in range(nx):
+            v00 = j * (nx + 1) + i
+            v10, v01, v11 = v00 + 1, v00 + nx + 1, v00 + nx + 2
+            tris.append([v00, v10, v11])
+            tris.append([v00, v11, v01])
+    tris = lawson_delaunay(g, np.array(tris))
+    return Mesh(g, tris, np.full(len(tris), c, dtype=np.float64), name=f"square{nx}",
+                meta={"h": h, "seed": seed, "jitter": jitter})
+
+
+# ----------------------------------------------------------------------------
+# 3D: jittered hex grid, 6 Kuhn tetrahedra per hex
+# ----------------------------------------------------------------------------
+def mesh_cube(nx: int, jitter: float = 0.1, seed: int = 4, c: float = 1.0) -> Mesh:
+    """Unit cube, (nx+1)^3 vertices, interior jittered by U(-jitter*h, jitter*h)
+    per coordinate (seeded), 6 tetrahedra per hex about the main diagonal.
+    6*nx^3 tetrahedra."""
+    h = 1.0 / nx
+    rng = np.random.default_rng(seed)
+    n1 = nx + 1
+    g = np.array([[i * h, j * h, k * h] for k in range(n1) for j in range(n1) for i in range(n1)],
+                 dtype=np.float64)
+    g[g > 1.0] = 1.0
+    jit = rng.uniform(-jitter * h, jitter * h, size=g.shape)
+    interior = np.all((g > 0) & (g < 1), axis=1)
+    g[interior] += jit[interior]
+
+    def vid(i, j, k):
+        return (k * n1 + j) * n1 + i
+
+    tets = []
+    for k in range(nx):
+        for j in range(nx):
+            for i in range(nx):
+                for perm in itertools.permutations(range(3)):
+                    cur = [0, 0, 0]
+                    tet = [vid(i, j, k)]
+                    for ax in perm:
+                        cur[ax] += 1
+                        tet.append(vid(i + cur[0], j + cur[1], k + cur[2]))
+                    tets.append(tet)
+    return Mesh(g, np.array(tets, dtype=np.int32), np.full(len(tets), c, dtype=np.float64),
+                name=f"cube{nx}", meta={"h": h, "seed": seed, "jitter": jitter})
+
+
+# ----------------------------------------------------------------------------
+# Choice of the pitching parameter kappa
+# ----------------------------------------------------------------------------
+def element_slope_factor(mesh: Mesh) -> np.ndarray:
+    """C_K = max |g| over linear functions on K with |g.(x_i-x_j)| <= |x_i-x_j|
+    on every edge of K (vertex enumeration of that polytope).
+
+    If every edge obeys |tau_i - tau_j| <= kappa |x_i - x_j| / c_K, then
+    c_K |grad tau| <= kappa C_K, so kappa < 1/C_K keeps the face space-like
+    (the causality condition of Section 2.2)."""
+    n = mesh.dim
+    if n == 1:
+        return np.ones(mesh.n_elem)
+    X = mesh.coords[mesh.elems]                              # (E, n+1, n)
+    pairs = list(itertools.combinations(range(n + 1), 2))
+    U = np.stack([X[:, j] - X[:, i] for i, j in pairs], axis=1)   # (E, m, n)
+    U = U / np.linalg.norm(U, axis=2, keepdims=True)
+    best = np.zeros(mesh.n_elem)
+    for rows in itertools.combinations(range(len(pairs)), n):
+        M = U[:, list(rows)]                                 # (E, n, n)
+        det = np.linalg.det(M)
+        ok = np.abs(det) > 1e-12
+        if not np.any(ok):
+            continue
+        for signs in itertools.product([-1.0, 1.0], repeat=n):
+            rhs = np.broadcast_to(np.array(signs), (int(ok.sum()), n))
+            gg = np.linalg.solve(M[ok], rhs[..., None])[..., 0]   # (E', n)
+            feas = np.all(np.abs(np.einsum("emn,en->em", U[ok], gg)) <= 1 + 1e-9, axis=1)
+            val = np.where(feas, np.linalg.norm(gg, axis=1), 0.0)
+            idx = np.nonzero(ok)[0]
+            best[idx] = np.maximum(best[idx], val)
+    return best
+
+
+def pitch_kappa(mesh: Mesh, safety: float = 0.9) -> float:
+    """kappa = safety / max_K C_K (1D: C_K = 1, so kappa = safety)."""
+    return float(safety / element_slope_factor(mesh).max())
+
+
+# ----------------------------------------------------------------------------
+# Closed-form solutions.  Every function returns an array (N, n+2) holding
+# (U, v, sigma_1..sigma_n) with v = dU/dt and sigma = -grad U.
+# ----------------------------------------------------------------------------
+def plane_wave_1d(x: np.ndarray, t) -> np.ndarray:
+    """U = sin(pi (x - t)), c = 1."""
+    x = np.asarray(x, dtype=np.float64).reshape(-1)
+    t = np.broadcast_to(np.asarray(t, dtype=np.float64), x.shape)
+    ph = math.pi * (x - t)
+    return np.stack([np.sin(ph), -math.pi * np.cos(ph), -math.pi * np.cos(ph)], axis=1)
+
+
+def standing_wave_2d(x: np.ndarray, t) -> np.ndarray:
+    """U = cos(sqrt2 pi t) sin(pi x) sin(pi y), c = 1 (v = 0 on the boundary)."""
+    x = np.asarray(x, dtype=np.float64).reshape(-1, 2)
+    t = np.broadcast_to(np.asarray(t, dtype=np.float64), x.shape[:1])
+    w = math.sqrt(2.0) * math.pi
+    sx, sy = np.sin(math.pi * x[:, 0]), np.sin(math.pi * x[:, 1])
+    cx, cy = np.cos(math.pi * x[:, 0]), np.cos(math.pi * x[:, 1])
+    ct, st = np.cos(w * t), np.sin(w * t)
+    return np.stack([ct * sx * sy, -w * st * sx * sy,
+                     -math.pi * ct * cx * sy, -math.pi * ct * sx * cy], axis=1)
+
+
+def standing_wave_3d(x: np.ndarray, t) -> np.ndarray:
+    """U = cos(sqrt3 pi t) sin(pi x) sin(pi y) sin(pi z), c = 1."""
+    x = np.asarray(x, dtype=np.float64).reshape(-1, 3)
+    t = np.broadcast_to(np.asarray(t, dtype=np.float64), x.shape[:1])
+    w = math.sqrt(3.0) * math.pi
+    s = np.sin(math.pi * x)
+    co = np.cos(math.pi * x)
+    ct, st = np.cos(w * t), np.sin(w * t)
+    prod = s[:, 0] * s[:, 1] * s[:, 2]
+    return np.stack([ct * prod, -w * st * prod,
+                     -math.pi * ct * co[:, 0] * s[:, 1] * s[:, 2],
+                     -math.pi * ct * s[:, 0] * co[:, 1] * s[:, 2],
+                     -math.pi * ct * s[:, 0] * s[:, 1] * co[:, 2]], axis=1)
+
+
+def gaussian_pulse(center, delta: float):
+    """U0 = exp(-|x-x0|^2/delta^2), v0 = 0, sigma0 = -grad U0 (a t = 0 state)."""
+    x0 = np.asarray(center, dtype=np.float64)
+
+    def f(x: np.ndarray, t=0.0) -> np.ndarray:
+        x = np.asarray(x, dtype=np.float64).reshape(-1, x0.size)
+        d = x - x0
+        u = np.exp(-np.sum(d * d, axis=1) / delta ** 2)
+        sig = (2.0 / delta ** 2) * d * u[:, None]
+        return np.concatenate([u[:, None], np.zeros((len(u), 1)), sig], axis=1)
+    return f
+
+
+def polynomial_solution(dim: int, which: int = 0):
+    """Polynomial solutions of -Lap U + U_tt = 0 (c = 1), used for the
+    reproduction property: U in the discrete Trefftz space is recovered
+    exactly by a consistent method.
+
+    dim 1: which 0 -> x^2 + t^2,  which 1 -> x^3 + 3 x t^2
+    dim 2: which 0 -> x^2 + y^2 + 2 t^2, which 1 -> x y t + x^3 + 3 x t^2
+    dim 3: which 0 -> x^2 + y^2 + z^2 + 3 t^2, which 1 -> x y z + y^3 + 3 y t^2 + x^2 - z^2
+    """
+    def f(x: np.ndarray, t) -> np.ndarray:
+        x = np.asarray(x, dtype=np.float64).reshape(-1, dim)
+        t = np.broadcast_to(np.asarray(t, dtype=np.float64), x.shape[:1])
+        X = x[:, 0]
+        if dim == 1:
+            if which == 0:
+                return np.stack([X**2 + t**2, 2 * t, -2 * X], axis=1)
+            return np.stack([X**3 + 3 * X * t**2, 6 * X * t, -(3 * X**2 + 3 * t**2)], axis=1)
+        Y = x[:, 1]
+        if dim == 2:
+            if which == 0:
+                return np.stack([X**2 + Y**2 + 2 * t**2, 4 * t, -2 * X, -2 * Y], axis=1)
+            U = X * Y * t + X**3 + 3 * X * t**2
+            return np.stack([U, X * Y + 6 * X * t, -(Y * t + 3 * X**2 + 3 * t**2),
+                             -(X * t)], axis=1)
+        Z = x[:, 2]
+        if which == 0:
+            return np.stack([X**2 + Y**2 + Z**2 + 3 * t**2, 6 * t, -2 * X, -2 * Y, -2 * Z], axis=1)
+        U = X * Y * Z + Y**3 + 3 * Y * t**2 + X**2 - Z**2
+        return np.stack([U, 6 * Y * t,
+                         -(Y * Z + 2 * X), -(X * Z + 3 * Y**2 + 3 * t**2),
+                         -(X * Y - 2 * Z)], axis=1)
+    return f
+
+
+# ----------------------------------------------------------------------------
+# Named workloads (sizes of the paper-shaped runs)
+# ----------------------------------------------------------------------------
+@dataclass
+class Workload:
+    name: str
+    mesh: Mesh
+    p: int
+    T: float
+    kappa: float
+    solution: object          # callable(x, t) -> (N, n+2); None if only initial data
+    init: object              # callable(x) -> (N, n+2) at t = 0
+    dirichlet: object         # callable(x, t) -> (N,) values of v on the boundary, or None (= 0)
+    alpha: float = 0.5
+    beta: float = 0.5
+
+
+def _vfield(sol):
+    return lambda x, t: sol(x, t)[:, 1]
+
+
+def workload(name: str) -> Workload:
+    """Named workloads.
+
+    plane1d      : [0,1], 16 elements, p=3, T=1, plane wave, Dirichlet both ends.
+    standing2d   : unit square, 22x22 jittered Delaunay grid (968 triangles),
+                   p=4, T=1, standing wave (v = 0 on the boundary).
+    small2d      : unit square, 6x6 jittered grid (72 triangles), p=4, T=0.25.
+    standing3d_small : unit cube 3^3 hexes (162 tets), p=3, T=0.2.
+    """
+    if name == "plane1d":
+        m = mesh_interval(16)
+        return Workload(name, m, 3, 1.0, 0.9, plane_wave_1d,
+                        lambda x: plane_wave_1d(x, 0.0), _vfield(plane_wave_1d))
+    if name == "standing2d":
+        m = mesh_square(22, 0.2, seed=2)
+        return Workload(name, m, 4, 1.0, pitch_kappa(m), standing_wave_2d,
+                        lambda x: standing_wave_2d(x, 0.0), None)
+    if name == "small2d":
+        m = mesh_square(6, 0.2, seed=7)
+        return Workload(name, m, 4, 0.25, pitch_kappa(m), standing_wave_2d,
+                        lambda x: standing_wave_2d(x, 0.0), None)
+    if name == "standing3d_small":
+        m = mesh_cube(3, 0.1, seed=4)
+        return Workload(name, m, 3, 0.2, pitch_kappa(m), standing_wave_3d,
+                        lambda x: standing_wave_3d(x, 0.0), None)
+    raise KeyError(name)

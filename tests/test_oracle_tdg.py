@@ -1,0 +1,209 @@
+"""Pins for oracle/tdg.py (the tent sweep, eq. (4.1) + Section 5).
+
+* polynomial reproduction: the method is consistent (Section 2.4; Section 5
+  notes the recovery terms preserve consistency) and any U in U^p lies in the
+  discrete space, so exact initial/Dirichlet data give U_h = U up to rounding
+  at every front point, for n = 1, 2, 3 and several p;
+* energy identity: testing a tent system with V = U_h and using
+  d/dt e + div(v sigma) = 0 inside the tent gives, with g_D = 0,
+      1/2 int_top Q_g(u) = 1/2 int_bot Q_gb(u_b) - 1/2 int_bot Q_gb(u - u_b)
+                           - int_bot (U - U_b) U dx - alpha int_D v^2 dS,
+  Q_g(u) = c^-2 v^2 + |sigma|^2 - 2 v sigma.g; so the sweep is dissipative
+  (Section 6.5: the numerical energy decreases);
+* h-convergence of e(v, sigma) at the rate p (fields in W^(p-1), Section 6.4
+  observes O(h^(q+1)) for W^q) and p-convergence faster than geometric.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import energy, pitching, tdg
+from paper_1907_02367_gb300 import inputs
+
+
+def _run(mesh, p, T, sol, kappa, dirichlet=True, record=None):
+    r = pitching.pitch(mesh.coords, mesh.elems, mesh.c, kappa, T)
+    dfun = (lambda x, t: sol(x, t)[:, 1]) if dirichlet else None
+    F, tau = tdg.sweep(mesh.coords, mesh.elems, mesh.c, p, r, lambda x: sol(x, 0.0), dfun,
+                       record=record)
+    lay = tdg.front_layout(mesh.coords, mesh.elems, p)
+    ex = sol(lay.xq.reshape(-1, mesh.dim), T).reshape(F.shape)
+    return F, tau, ex, lay, r
+
+
+REPRO = [(1, 2, 0), (1, 3, 1), (1, 5, 1), (2, 2, 0), (2, 3, 1), (2, 4, 1), (2, 5, 0),
+         (3, 2, 0), (3, 3, 1)]
+
+
+@pytest.mark.parametrize("dim,p,which", REPRO)
+def test_polynomial_reproduction(dim, p, which):
+    mesh = {1: inputs.mesh_interval(6), 2: inputs.mesh_square(3, 0.2, seed=5),
+            3: inputs.mesh_cube(1, 0.0, seed=3)}[dim]
+    sol = inputs.polynomial_solution(dim, which)
+    T = 0.3 if dim < 3 else 0.15
+    F, tau, ex, _, _ = _run(mesh, p, T, sol, inputs.pitch_kappa(mesh))
+    assert np.all(tau == T)
+    scale = np.abs(ex).max()
+    assert np.abs(F - ex).max() <= 1e-12 * max(1.0, scale) * (10 if dim == 3 else 1)
+
+
+def test_reproduction_fails_for_degree_above_p():
+    """Sanity: a solution outside U^p (degree 3 with p = 2) is not reproduced."""
+    mesh = inputs.mesh_interval(6)
+    sol = inputs.polynomial_solution(1, 1)
+    F, _, ex, _, _ = _run(mesh, 2, 0.3, sol, 0.9)
+    assert np.abs(F - ex).max() > 1e-6
+
+
+def _energy_identity_check(mesh, p, T, sol, alpha=0.5):
+    lay = tdg.front_layout(mesh.coords, mesh.elems, p)
+    n = mesh.dim
+    nodes, wts = np.polynomial.legendre.leggauss(12)
+    bverts = {0, mesh.n_vert - 1} if n == 1 else set()
+    worst = [0.0]
+    checked = [0]
+
+    def rec(it, d):
+        v, patch, B = d["v"], d["patch"], d["basis"]
+        tau = d["tau_before"]
+        ids = mesh.elems[patch]
+        tb = tau[ids]
+        tt = np.where(ids == v, d["t_top"], tb)
+        X = mesh.coords[ids]
+        J = X[:, 1:, :] - X[:, :1, :]
+        gb = np.linalg.solve(J, (tb[:, 1:] - tb[:, :1])[..., None])[..., 0]
+        gt = np.linalg.solve(J, (tt[:, 1:] - tt[:, :1])[..., None])[..., 0]
+        Q = lay.wq.shape[1]
+        x = lay.xq[patch].reshape(-1, n)
+        w = lay.wq[patch].reshape(-1)
+        cK = np.repeat(mesh.c[patch], Q)
+
+        def fields(t):
+            U, V, S = B.eval_phys(x, t, d["xc"], d["tc"], d["h"], d["c"])
+            return U @ d["x"], V @ d["x"], np.einsum("qdj,j->qd", S, d["x"])
+
+        def Qg(vv, ss, g):
+            return vv * vv / cK ** 2 + np.sum(ss * ss, axis=1) - 2 * vv * np.sum(ss * g, axis=1)
+
+        Ut, Vt, St = fields((tt @ lay.bary.T).reshape(-1))
+        Ub, Vb, Sb = fields((tb @ lay.bary.T).reshape(-1))
+        fb = np.concatenate([d["front_before"][k] for k in patch])
+        g_t = np.repeat(gt, Q, axis=0)
+        g_b = np.repeat(gb, Q, axis=0)
+        top = 0.5 * np.sum(w * Qg(Vt, St, g_t))
+        rhs = 0.5 * np.sum(w * Qg(fb[:, 1], fb[:, 2:], g_b))
+        rhs -= 0.5 * np.sum(w * Qg(Vb - fb[:, 1], Sb - fb[:, 2:], g_b))
+        rhs -= np.sum(w * (Ub - fb[:, 0]) * Ub)
+        if v in bverts:
+            tq = d["t_bot"] + (d["t_top"] - d["t_bot"]) * 0.5 * (nodes + 1)
+            xv = np.full((len(tq), 1), mesh.coords[v, 0])
+            _, Vd, _ = B.eval_phys(xv, tq, d["xc"], d["tc"], d["h"], d["c"])
+            vd = Vd @ d["x"]
+            rhs -= alpha * np.sum(0.5 * (d["t_top"] - d["t_bot"]) * wts * vd * vd)
+        elif n > 1 and _on_boundary(mesh, v):
+            return
+        scale = abs(top) + abs(0.5 * np.sum(w * Qg(fb[:, 1], fb[:, 2:], g_b))) + 1e-30
+        worst[0] = max(worst[0], abs(top - rhs) / scale)
+        checked[0] += 1
+
+    r = pitching.pitch(mesh.coords, mesh.elems, mesh.c, inputs.pitch_kappa(mesh), T)
+    F, tau = tdg.sweep(mesh.coords, mesh.elems, mesh.c, p, r, lambda x: sol(x, 0.0), None,
+                       alpha=alpha, record=rec)
+    return worst[0], checked[0], F, lay
+
+
+def _on_boundary(mesh, v):
+    x = mesh.coords[v]
+    return bool(np.any(np.isclose(x, 0.0) | np.isclose(x, 1.0)))
+
+
+def _sinsin_1d(x, t):
+    """Section 6.5 model problem U = sin(pi x) sin(pi t) (v = 0 at x = 0, 1)."""
+    x = np.asarray(x).reshape(-1)
+    t = np.broadcast_to(t, x.shape)
+    pi = math.pi
+    return np.stack([np.sin(pi * x) * np.sin(pi * t), pi * np.sin(pi * x) * np.cos(pi * t),
+                     -pi * np.cos(pi * x) * np.sin(pi * t)], axis=1)
+
+
+@pytest.mark.parametrize("p", [2, 4, 6])
+def test_energy_identity_1d_with_dirichlet(p):
+    mesh = inputs.mesh_interval(5)           # Section 6.5: 5 elements
+    worst, checked, F, lay = _energy_identity_check(mesh, p, 0.7, _sinsin_1d)
+    assert checked > 10
+    assert worst < 1e-12
+
+
+def test_energy_identity_2d_interior():
+    mesh = inputs.mesh_square(4, 0.2, seed=9)
+    worst, checked, F, lay = _energy_identity_check(mesh, 3, 0.3, inputs.standing_wave_2d)
+    assert checked > 10
+    assert worst < 1e-12
+
+
+def test_energy_decreases_1d():
+    """Section 6.5: with exact (constant-energy) data the numerical energy at
+    the flat final front is below the initial one."""
+    mesh = inputs.mesh_interval(5)
+    p = 3
+    lay = tdg.front_layout(mesh.coords, mesh.elems, p)
+    E0 = energy.front_energy(_sinsin_1d(lay.xq.reshape(-1, 1), 0.0).reshape(5, -1, 3),
+                             lay.wq, mesh.c)
+    Es = []
+    for T in (0.5, 1.0, 2.0):
+        F, tau, ex, _, _ = _run(mesh, p, T, _sinsin_1d, 0.9, dirichlet=False)
+        Es.append(energy.front_energy(F, lay.wq, mesh.c))
+    assert E0 > Es[0] > Es[1] > Es[2]
+
+
+@pytest.mark.parametrize("p", [2, 3, 4])
+def test_h_convergence_1d(p):
+    es = []
+    for ne in (8, 16, 32):
+        F, _, ex, lay, _ = _run(inputs.mesh_interval(ne), p, 1.0, inputs.plane_wave_1d, 0.9)
+        es.append(energy.error_e(F, ex, lay.wq, np.ones(ne)))
+    slopes = np.log2(np.array(es[:-1]) / np.array(es[1:]))
+    assert np.all(slopes > p - 0.3) and np.all(slopes < p + 0.6), slopes
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_h_convergence_2d(p):
+    es = []
+    for nx in (4, 8, 16):
+        m = inputs.mesh_square(nx, 0.2, seed=11)
+        F, _, ex, lay, _ = _run(m, p, 0.5, inputs.standing_wave_2d, inputs.pitch_kappa(m),
+                                dirichlet=False)
+        es.append(energy.error_e(F, ex, lay.wq, m.c))
+    slopes = np.log2(np.array(es[:-1]) / np.array(es[1:]))
+    assert np.all(slopes > p - 0.3) and np.all(slopes < p + 0.6), slopes
+
+
+def test_p_convergence_1d():
+    es = []
+    for p in range(1, 8):
+        F, _, ex, lay, _ = _run(inputs.mesh_interval(4), p, 1.0, inputs.plane_wave_1d, 0.9)
+        es.append(energy.error_e(F, ex, lay.wq, np.ones(4)))
+    ratios = np.array(es[:-1]) / np.array(es[1:])
+    assert np.all(ratios > 4.0), ratios
+
+
+@pytest.mark.parametrize("dim,p,which,cval", [(1, 3, 1, 2.5), (2, 3, 1, 0.4), (2, 4, 0, 3.0),
+                                              (3, 2, 0, 1.7)])
+def test_polynomial_reproduction_wave_speed(dim, p, which, cval):
+    """U_c(x, t) = U_1(x, c t) solves -Lap U + c^-2 U_tt = 0 when U_1 solves the
+    c = 1 equation; v = c dU_1/dt(x, ct), sigma = sigma_1(x, ct)."""
+    mesh = {1: inputs.mesh_interval(6), 2: inputs.mesh_square(3, 0.2, seed=5),
+            3: inputs.mesh_cube(1, 0.0, seed=3)}[dim]
+    mesh.c[:] = cval
+    base = inputs.polynomial_solution(dim, which)
+
+    def sol(x, t):
+        out = base(x, cval * np.asarray(t, dtype=np.float64))
+        out[:, 1] *= cval
+        return out
+
+    T = 0.3 / cval
+    F, tau, ex, _, _ = _run(mesh, p, T, sol, inputs.pitch_kappa(mesh))
+    assert np.all(tau == T)
+    assert np.abs(F - ex).max() <= 1e-11 * max(1.0, np.abs(ex).max())
