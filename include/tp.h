@@ -1,0 +1,155 @@
+/*
+ * tp.h - C ABI of libtp, a GB300 (sm_103a) solver for the tent-pitched
+ * space-time Trefftz-DG method for the acoustic wave equation
+ * (Perugia, Schoberl, Stocker, Wintersteiger, "Tent pitching and Trefftz-DG
+ * method for the acoustic wave equation").
+ *
+ * Conventions
+ *   - Every call returns an int status (TP_OK = 0).  On failure a message is
+ *     available from tp_last_error() (thread-local, valid until the next call
+ *     on the same thread).
+ *   - Host pointers are read during the call only; the library keeps copies.
+ *   - Device pointers ("d_" prefix) are caller-owned CUDA global memory on the
+ *     current device; the library never frees them.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy stream).
+ *     Device work is enqueued on it and is asynchronous; device-side errors
+ *     (singular local system) are recorded in a status word read by
+ *     tp_sync_status().
+ *   - Handles are opaque and owned by the library (tp_destroy_*).
+ *   - Field layout: a "front" array holds, for every right-hand side r,
+ *     element K and front point q, the n+2 values (U, v, sigma_1..sigma_n)
+ *     with v = dU/dt and sigma = -grad U (Section 2.1, eq. 2.2):
+ *       front[((r * n_elem + K) * Q + q) * (n + 2) + comp],  Q = (p+1)^n.
+ */
+#ifndef TP_H
+#define TP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  TP_OK = 0,
+  TP_ERR_ARG = 1,          /* invalid argument (sizes, pointers, unsupported p/dim) */
+  TP_ERR_CAUSALITY = 2,    /* a front or tent violates c|grad tau| < 1 (Section 2.2) */
+  TP_ERR_SINGULAR = 3,     /* zero or non-finite pivot in a local system */
+  TP_ERR_NOCONV = 4,       /* iterative refinement did not converge */
+  TP_ERR_TIMEOUT = 5,      /* a bounded device wait gave up */
+  TP_ERR_CUDA = 6,         /* a CUDA runtime call failed */
+  TP_ERR_OOM = 7,          /* allocation failed */
+  TP_ERR_UNSUPPORTED = 8   /* valid input outside what this build implements */
+};
+
+enum { TP_FP64 = 0, TP_MIXED = 1 };
+
+/* Spatial mesh (Section 2.1): simplices aligned with the jumps of the
+ * piecewise-constant wave speed c.  dim in {1,2,3}; coords n_vert x dim;
+ * elems n_elem x (dim+1) vertex ids; c n_elem values > 0.  Every boundary
+ * facet is a Dirichlet facet (v = g_D on Gamma_D, eq. 2.1). */
+typedef struct tp_mesh_desc {
+  int32_t dim;
+  int64_t n_vert;
+  const double* coords;
+  int64_t n_elem;
+  const int32_t* elems;
+  const double* c;
+} tp_mesh_desc;
+
+/* p: degree of the second-order Trefftz space U^p (Section 3; unknowns per
+ * single-material tent dim U^p = C(p+n,n) + C(p-1+n,n)); alpha: Dirichlet
+ * penalty of eq. (2.5) (the paper uses 0.5); beta: time-like penalty (unused
+ * until interface faces are built); kappa: pitching slope factor (edge-slope
+ * limit delta_e = kappa l_e / c_e); T: final time; precision: TP_FP64;
+ * nrhs: right-hand sides advanced together (same tents, same matrices). */
+typedef struct tp_params {
+  int32_t p;
+  double alpha;
+  double beta;
+  double kappa;
+  double T;
+  int32_t precision;
+  int32_t nrhs;
+} tp_params;
+
+typedef struct tp_tents tp_tents;
+typedef struct tp_basis tp_basis;
+typedef struct tp_ctx tp_ctx;
+
+const char* tp_last_error(void);
+
+/* Tent pitching (Section 2.2; the edge-slope limited variant named in the
+ * Section 6 setup).  Host only, deterministic, IEEE binary64 without fused
+ * multiply-add:
+ *   delta_e = (kappa * l_e) / c_e, l_e = sqrt(((dx0*dx0) + dx1*dx1) + dx2*dx2),
+ *   c_e = max c over the elements of edge e;
+ *   each round takes the local minima of tau (tau_v < T and tau_v <= tau_w for
+ *   all neighbours w), keeps a greedy independent subset scanning v upward,
+ *   and pitches v to t_top = min(T, min_w tau_w + delta_vw) at
+ *   level = 1 + max(level of the last tents at v and at its neighbours).
+ * Tents are stored sorted by (level, round, v); tents of one level are
+ * independent.  Errors: TP_ERR_ARG for bad sizes/ids or non-positive
+ * kappa, T or c. */
+int tp_pitch_mesh(const tp_mesh_desc* mesh, const tp_params* prm, tp_tents** out);
+int tp_tents_info(const tp_tents* tents, int64_t* n_tents, int32_t* n_levels);
+/* Copies the sorted tent list into caller arrays of n_tents entries. */
+int tp_tents_export(const tp_tents* tents, int32_t* vert, double* t_bot, double* t_top,
+                    int32_t* level);
+void tp_destroy_tents(tp_tents* tents);
+
+/* Trefftz basis of U^p for c = 1 (Section 3, eq. 3.1, monomial initial data,
+ * Remark 3.1 for the mapping to a tent).  Host tables, exact rationals
+ * rounded once to binary64.  exps: nmono x (dim+1) exponents (t, x_1..x_n);
+ * coef: nb x nmono coefficients of U.  dim in {1,2,3}, 1 <= p <= 8. */
+int tp_build_basis(int32_t dim, int32_t p, tp_basis** out);
+int tp_basis_info(const tp_basis* basis, int32_t* nb, int32_t* nmono);
+int tp_basis_export(const tp_basis* basis, int32_t* exps, double* coef);
+void tp_destroy_basis(tp_basis* basis);
+
+/* Uploads mesh, tents, basis and quadrature tables to the current device and
+ * allocates the front state (n_elem * Q * (dim+2) * nrhs doubles).
+ * Errors: TP_ERR_ARG on mismatched dim/p, TP_ERR_UNSUPPORTED when a tent's
+ * patch mixes wave speeds or exceeds the kernel's patch limit, TP_ERR_OOM. */
+int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const tp_basis* basis,
+              const tp_params* prm, tp_ctx** out);
+/* n_front = n_elem * Q points, n_comp = dim + 2, n_bnd = number of Dirichlet
+ * quadrature points over all tents, n_levels. */
+int tp_ctx_info(const tp_ctx* ctx, int64_t* n_front, int32_t* n_comp, int64_t* n_bnd,
+                int32_t* n_levels);
+/* Front points (Section 4.1: one spatial rule mapped onto the faces):
+ * host arrays xq (n_front x dim) and wq (n_front) physical weights. */
+int tp_front_points(const tp_ctx* ctx, double* xq, double* wq);
+/* Dirichlet quadrature points (x, t) on the vertical boundary faces of every
+ * tent, in sweep order: host array xt (n_bnd x (dim+1)).  The caller
+ * evaluates g_D there (eq. 2.1: v = g_D on Gamma_D). */
+int tp_boundary_points(const tp_ctx* ctx, double* xt);
+/* Sets the state at t = 0: d_front (device, front layout above, nrhs sets),
+ * d_gD (device, nrhs x n_bnd values of g_D, or NULL for g_D = 0).  Both are
+ * copied; the front times are reset to 0.  Asynchronous on `stream`. */
+int tp_set_state(tp_ctx* ctx, const double* d_front, const double* d_gD, void* stream);
+/* Solves every tent of one level (1-based) of the sorted tent list:
+ * assembly of eq. (4.1) with the Section 5 recovery terms, LU solve,
+ * outflow written at the top points (Section 4.1). */
+int tp_solve_layer(tp_ctx* ctx, int32_t level, void* stream);
+/* Levels [level_begin, level_end) (1-based, end exclusive) as one CUDA graph
+ * (captured on first use for that range, then replayed). */
+int tp_advance(tp_ctx* ctx, int32_t level_begin, int32_t level_end, void* stream);
+/* Energy flux through the current front (Section 6.5 energy generalised to
+ * a front t = tau(x)):  E_r = 1/2 sum_K sum_q w_q (c_K^-2 v^2 + |sigma|^2
+ * - 2 v sigma.grad tau_K) for every rhs r; equals the paper's E on a flat
+ * front.  d_out: device array of nrhs doubles. */
+int tp_energy(tp_ctx* ctx, double* d_out, void* stream);
+/* Copies the front (device, front layout) and/or the vertex front times
+ * (device, n_vert doubles); either may be NULL. */
+int tp_get_state(const tp_ctx* ctx, double* d_front, double* d_tau, void* stream);
+/* Synchronises the context's last stream and reports the device status:
+ * *status = TP_OK or TP_ERR_SINGULAR, *info = first failing tent index. */
+int tp_sync_status(tp_ctx* ctx, int32_t* status, int64_t* info);
+void tp_destroy_ctx(tp_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TP_H */

@@ -1,0 +1,1097 @@
+// libtp device side: context, the per-level tent kernel (FP64), the energy
+// reduction and the CUDA-graph sweep.
+//
+// One CTA solves one tent (Section 4.1, eq. 4.1 with the Section 5 recovery
+// terms).  For a tent at vertex v with patch star(v), basis U_h = sum_j x_j b_j
+// of U^p (Section 3, Remark 3.1 scaling) and front points q of every patch
+// element K (one spatial rule mapped onto the faces, Fig. 2):
+//
+//   top face (t = tau_top(x), n_t dS = dx, n_x dS = -g dx):
+//     c^-2 v w + s.t - v (t.g) - (s.g) w = (s - v g).(t - w g) + (c^-2 - |g|^2) v w
+//   so the top contribution is a Gram matrix  A += Z^T Z  of the rows
+//     z_0 = sqrt(w_q) sqrt(c^-2 - |g|^2) v_j,  z_m = sqrt(w_q) (s_mj - v_j g_m)
+//   (c|g| < 1 on a space-like face, Section 2.2), plus the recovery row
+//     sqrt(w_q) U_j at the bottom point;
+//   bottom data (RHS):  b_i += w_q [ (c^-2 v_b - s_b.g_b) v_i + (s_b - v_b g_b).s_i + U_b U_i ];
+//   Dirichlet vertical faces (eq. 4.1):
+//     A_ij += w (s_j.n + alpha v_j) v_i,  b_i += w g_D (alpha v_i - s_i.n).
+// Then LU with partial pivoting, and (U, v, sigma) at the top points overwrite
+// the front (Section 4.1: only the latest values are stored).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "tp_internal.h"
+
+#define TP_CUDA_OK(call)                                                              \
+  do {                                                                                \
+    cudaError_t e__ = (call);                                                         \
+    if (e__ != cudaSuccess) {                                                         \
+      tp::set_error(std::string("tp: CUDA error ") + cudaGetErrorString(e__) + " at " + \
+                    #call);                                                           \
+      return TP_ERR_CUDA;                                                             \
+    }                                                                                 \
+  } while (0)
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kMaxPair = 8;      // accumulator slots per thread in the Gram phase
+constexpr int kRhsReg = 4;       // right-hand sides per outflow pass
+
+struct KArgs {
+  int nb, nmono, Q, nrhs, CH, mono_stride;
+  int64_t ne, n_bnd;
+  double alpha;
+  const double* X;
+  const int* elems;
+  const double* cK;
+  const int* star_ptr;
+  const int* star_el;
+  const int* vfac_ptr;
+  const int* vfac;
+  const int* facet_vert;
+  const double* facet_nrm;
+  const double* bary;     // Q * (dim+1)
+  const double* wref;     // Q
+  const double* sqw;      // Q, sqrt(wref)
+  const int* tent_v;
+  const double* tent_ttop;
+  const double* tent_h;
+  const long long* tent_gdoff;
+  const int* sp_ptr;
+  const int* sp_mono;
+  const double* sp_coef;
+  const int* mono_parent;
+  const int* mono_var;
+  double* tau;
+  double* front;
+  const double* gD;
+  int* status;
+  long long* status_info;
+  // shared-memory carve (offsets in doubles)
+  int off_b, off_rows, off_bvs, off_cb, off_mono;
+};
+
+__device__ __forceinline__ void flag_error(const KArgs& a, int code, long long info) {
+  if (atomicCAS(a.status, 0, code) == 0) *a.status_info = info;
+}
+
+// monomials t^k x^alpha at (that, xhat) into m[0..nm): m[g] = m[parent[g]] * var
+template <int DIM>
+__device__ __forceinline__ void eval_monomials(const KArgs& a, double th, const double* xh, double* m) {
+  m[0] = 1.0;
+  for (int g = 1; g < a.nmono; ++g) {
+    const int vr = __ldg(a.mono_var + g);
+    const double s = (vr == 0) ? th : xh[vr - 1];
+    m[g] = m[__ldg(a.mono_parent + g)] * s;
+  }
+}
+
+// sum over the sparse entries of (basis j, component comp)
+template <int DIM>
+__device__ __forceinline__ double sp_eval(const KArgs& a, int j, int comp, const double* m) {
+  constexpr int C = DIM + 2;
+  const int e0 = __ldg(a.sp_ptr + j * C + comp), e1 = __ldg(a.sp_ptr + j * C + comp + 1);
+  double s = 0.0;
+  for (int e = e0; e < e1; ++e) s = fma(__ldg(a.sp_coef + e), m[__ldg(a.sp_mono + e)], s);
+  return s;
+}
+
+// gradient g of the linear function with increments dv[i] along the edges
+// e[i] = X_{i+1} - X_0 (solves e g = dv); returns det(e)
+template <int DIM>
+__device__ __forceinline__ double lin_grad(const double (&e)[DIM][DIM], const double* dv, double* g) {
+  if constexpr (DIM == 1) {
+    g[0] = dv[0] / e[0][0];
+    return e[0][0];
+  } else if constexpr (DIM == 2) {
+    const double det = e[0][0] * e[1][1] - e[0][1] * e[1][0];
+    const double id = 1.0 / det;
+    g[0] = (e[1][1] * dv[0] - e[0][1] * dv[1]) * id;
+    g[1] = (-e[1][0] * dv[0] + e[0][0] * dv[1]) * id;
+    return det;
+  } else {
+    // rows of e^-1^T: (e1 x e2, e2 x e0, e0 x e1) / det
+    double c0[3], c1[3], c2[3];
+    c0[0] = e[1][1] * e[2][2] - e[1][2] * e[2][1];
+    c0[1] = e[1][2] * e[2][0] - e[1][0] * e[2][2];
+    c0[2] = e[1][0] * e[2][1] - e[1][1] * e[2][0];
+    c1[0] = e[2][1] * e[0][2] - e[2][2] * e[0][1];
+    c1[1] = e[2][2] * e[0][0] - e[2][0] * e[0][2];
+    c1[2] = e[2][0] * e[0][1] - e[2][1] * e[0][0];
+    c2[0] = e[0][1] * e[1][2] - e[0][2] * e[1][1];
+    c2[1] = e[0][2] * e[1][0] - e[0][0] * e[1][2];
+    c2[2] = e[0][0] * e[1][1] - e[0][1] * e[1][0];
+    const double det = e[0][0] * c0[0] + e[0][1] * c0[1] + e[0][2] * c0[2];
+    const double id = 1.0 / det;
+    for (int d = 0; d < 3; ++d) g[d] = (dv[0] * c0[d] + dv[1] * c1[d] + dv[2] * c2[d]) * id;
+    return det;
+  }
+}
+
+// determinant of a small symmetric Gram matrix
+template <int DIM>
+__device__ __forceinline__ double small_det(const double (&G)[DIM][DIM]) {
+  if constexpr (DIM == 1) {
+    return G[0][0];
+  } else if constexpr (DIM == 2) {
+    return G[0][0] * G[1][1] - G[0][1] * G[1][0];
+  } else {
+    return G[0][0] * (G[1][1] * G[2][2] - G[1][2] * G[2][1]) -
+           G[0][1] * (G[1][0] * G[2][2] - G[1][2] * G[2][0]) +
+           G[0][2] * (G[1][0] * G[2][1] - G[1][1] * G[2][0]);
+  }
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kThreads, 1) k_layer_fp64(const KArgs a, const int tent0) {
+  constexpr int NV = DIM + 1;   // vertices per element
+  constexpr int C = DIM + 2;    // U, v, sigma
+  constexpr int RT = DIM + 2;   // Gram rows per point: DIM+1 top rows + recovery row
+  extern __shared__ __align__(16) double sm[];
+  __shared__ int s_P, s_v, s_nfac;
+  __shared__ double s_ttop, s_tbot, s_tc, s_ih, s_c, s_ic2;
+  __shared__ double s_xv[DIM];
+  __shared__ int s_el[tp::kMaxPatch];
+  __shared__ double s_X[tp::kMaxPatch][NV][DIM];
+  __shared__ double s_tb[tp::kMaxPatch][NV], s_tt[tp::kMaxPatch][NV];
+  __shared__ double s_gb[tp::kMaxPatch][DIM], s_gt[tp::kMaxPatch][DIM];
+  __shared__ double s_sdet[tp::kMaxPatch], s_st[tp::kMaxPatch];
+  __shared__ int s_piv;
+  __shared__ double s_fP[NV][DIM + 1];   // Dirichlet face simplex vertices (x, t)
+  __shared__ double s_fscale, s_fn[DIM];
+
+  const int tid = threadIdx.x;
+  const int tent = tent0 + blockIdx.x;
+  const int nb = a.nb, Q = a.Q, nrhs = a.nrhs, CH = a.CH;
+  double* sA = sm;
+  double* sb = sm + a.off_b;        // nrhs * nb (b, then x)
+  double* sR = sm + a.off_rows;     // CH * RT * nb
+  double* sV = sm + a.off_bvs;      // CH * (DIM+1) * nb : bottom (v, sigma) scaled by sqrt(w)
+  double* sCB = sm + a.off_cb;      // CH * nrhs * C    : bottom data coefficients
+  double* sM = sm + a.off_mono;     // 2*CH * mono_stride
+
+  // ---------------- phase 0: tent and patch geometry ----------------
+  if (tid == 0) {
+    const int v = a.tent_v[tent];
+    s_v = v;
+    const int p0 = a.star_ptr[v], p1 = a.star_ptr[v + 1];
+    s_P = p1 - p0;
+    s_ttop = a.tent_ttop[tent];
+    s_tbot = a.tau[v];
+    s_tc = 0.5 * (s_tbot + s_ttop);
+    s_ih = 1.0 / a.tent_h[tent];
+    const double c = a.cK[a.star_el[p0]];
+    s_c = c;
+    s_ic2 = 1.0 / (c * c);
+    for (int d = 0; d < DIM; ++d) s_xv[d] = a.X[(int64_t)v * DIM + d];
+    s_nfac = a.vfac_ptr[v + 1] - a.vfac_ptr[v];
+  }
+  __syncthreads();
+  const int P = s_P, v = s_v;
+  for (int k = tid; k < P; k += blockDim.x) {
+    const int el = a.star_el[a.star_ptr[v] + k];
+    s_el[k] = el;
+    for (int i = 0; i < NV; ++i) {
+      const int vi = a.elems[(int64_t)el * NV + i];
+      for (int d = 0; d < DIM; ++d) s_X[k][i][d] = a.X[(int64_t)vi * DIM + d];
+      const double tb = a.tau[vi];
+      s_tb[k][i] = tb;
+      s_tt[k][i] = (vi == v) ? s_ttop : tb;
+    }
+    double e[DIM][DIM], db[DIM], dt[DIM];
+    for (int i = 0; i < DIM; ++i) {
+      for (int d = 0; d < DIM; ++d) e[i][d] = s_X[k][i + 1][d] - s_X[k][0][d];
+      db[i] = s_tb[k][i + 1] - s_tb[k][0];
+      dt[i] = s_tt[k][i + 1] - s_tt[k][0];
+    }
+    double gb[DIM], gt[DIM];
+    const double det = lin_grad<DIM>(e, db, gb);
+    lin_grad<DIM>(e, dt, gt);
+    double g2 = 0.0;
+    for (int d = 0; d < DIM; ++d) {
+      s_gb[k][d] = gb[d];
+      s_gt[k][d] = gt[d];
+      g2 += gt[d] * gt[d];
+    }
+    s_sdet[k] = sqrt(fabs(det));
+    const double q = s_ic2 - g2;   // > 0 on a space-like top face
+    if (!(q > 0.0)) flag_error(a, TP_ERR_CAUSALITY, tent);
+    s_st[k] = sqrt(fmax(q, 0.0));
+  }
+  // Gram pairs owned by this thread (upper triangle, i <= j)
+  const int npair = nb * (nb + 1) / 2;
+  int pi[kMaxPair], pj[kMaxPair];
+  double acc[kMaxPair];
+#pragma unroll
+  for (int s = 0; s < kMaxPair; ++s) {
+    const int id = tid + s * kThreads;
+    int i = 0, j = 0;
+    if (id < npair) {   // row-major upper triangle enumeration
+      int rem = id;
+      i = 0;
+      while (rem >= nb - i) {
+        rem -= nb - i;
+        ++i;
+      }
+      j = i + rem;
+    }
+    pi[s] = i;
+    pj[s] = j;
+    acc[s] = 0.0;
+  }
+  const int nbpair = nrhs * nb;
+  double accb[kMaxPair];
+#pragma unroll
+  for (int s = 0; s < kMaxPair; ++s) accb[s] = 0.0;
+  __syncthreads();
+
+  // ---------------- phase 1: faces over the patch (chunks of CH points) ----------------
+  const int NP = P * Q;
+  const double c = s_c, ih = s_ih, ic2 = s_ic2, tc = s_tc;
+  for (int base = 0; base < NP; base += CH) {
+    const int nq = min(CH, NP - base);
+    if (tid < 2 * CH) {
+      const int side = tid / CH, ql = tid % CH, qg = base + ql;
+      if (ql < nq) {
+        const int k = qg / Q, q = qg % Q;
+        double x[DIM], tt = 0.0;
+        for (int d = 0; d < DIM; ++d) x[d] = 0.0;
+        for (int i = 0; i < NV; ++i) {
+          const double l = __ldg(a.bary + q * NV + i);
+          for (int d = 0; d < DIM; ++d) x[d] = fma(l, s_X[k][i][d], x[d]);
+          tt = fma(l, side == 0 ? s_tt[k][i] : s_tb[k][i], tt);
+        }
+        double xh[DIM];
+        for (int d = 0; d < DIM; ++d) xh[d] = (x[d] - s_xv[d]) * ih;
+        const double th = c * (tt - tc) * ih;
+        double* m = sM + tid * a.mono_stride;
+        eval_monomials<DIM>(a, th, xh, m);
+        const double sw = __ldg(a.sqw + q) * s_sdet[k];
+        if (side == 0) {
+          const double zs = sw * s_st[k];
+          double* R = sR + (size_t)ql * RT * nb;
+          for (int j = 0; j < nb; ++j) {
+            const double vj = c * ih * sp_eval<DIM>(a, j, 1, m);
+            R[j] = zs * vj;
+            for (int d = 0; d < DIM; ++d) {
+              const double sj = -ih * sp_eval<DIM>(a, j, 2 + d, m);
+              R[(1 + d) * nb + j] = sw * (sj - vj * s_gt[k][d]);
+            }
+          }
+        } else {
+          double* R = sR + (size_t)ql * RT * nb + (RT - 1) * nb;
+          double* V = sV + (size_t)ql * (DIM + 1) * nb;
+          for (int j = 0; j < nb; ++j) {
+            R[j] = sw * sp_eval<DIM>(a, j, 0, m);
+            V[j] = sw * c * ih * sp_eval<DIM>(a, j, 1, m);
+            for (int d = 0; d < DIM; ++d) V[(1 + d) * nb + j] = -sw * ih * sp_eval<DIM>(a, j, 2 + d, m);
+          }
+          const int el = s_el[k];
+          for (int r = 0; r < nrhs; ++r) {
+            const double* f = a.front + (((int64_t)r * a.ne + el) * Q + q) * C;
+            const double Ub = f[0], vb = f[1];
+            double sg = 0.0;
+            for (int d = 0; d < DIM; ++d) sg = fma(f[2 + d], s_gb[k][d], sg);
+            double* cb = sCB + ((size_t)ql * nrhs + r) * C;
+            cb[0] = sw * Ub;
+            cb[1] = sw * (ic2 * vb - sg);
+            for (int d = 0; d < DIM; ++d) cb[2 + d] = sw * (f[2 + d] - vb * s_gb[k][d]);
+          }
+        }
+      }
+    }
+    __syncthreads();
+    // Gram accumulation over the chunk
+#pragma unroll
+    for (int s = 0; s < kMaxPair; ++s) {
+      if (tid + s * kThreads < npair) {
+        const int i = pi[s], j = pj[s];
+        double t = acc[s];
+        for (int ql = 0; ql < nq; ++ql) {
+          const double* R = sR + (size_t)ql * RT * nb;
+#pragma unroll
+          for (int r = 0; r < RT; ++r) t = fma(R[r * nb + i], R[r * nb + j], t);
+        }
+        acc[s] = t;
+      }
+    }
+    // right-hand sides over the chunk
+#pragma unroll
+    for (int s = 0; s < kMaxPair; ++s) {
+      const int id = tid + s * kThreads;
+      if (id < nbpair) {
+        const int r = id / nb, i = id % nb;
+        double t = accb[s];
+        for (int ql = 0; ql < nq; ++ql) {
+          const double* cb = sCB + ((size_t)ql * nrhs + r) * C;
+          const double* V = sV + (size_t)ql * (DIM + 1) * nb;
+          t = fma(cb[0], sR[(size_t)ql * RT * nb + (RT - 1) * nb + i], t);
+#pragma unroll
+          for (int d = 0; d < DIM + 1; ++d) t = fma(cb[1 + d], V[d * nb + i], t);
+        }
+        accb[s] = t;
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int s = 0; s < kMaxPair; ++s) {
+    if (tid + s * kThreads < npair) {
+      sA[pi[s] * nb + pj[s]] = acc[s];
+      sA[pj[s] * nb + pi[s]] = acc[s];
+    }
+    const int id = tid + s * kThreads;
+    if (id < nbpair) sb[id] = accb[s];
+  }
+  __syncthreads();
+
+  // ---------------- phase 2: Dirichlet vertical faces through v ----------------
+  const int nfac = s_nfac;
+  for (int f = 0; f < nfac; ++f) {
+    const int fid = a.vfac[a.vfac_ptr[v] + f];
+    if (tid == 0) {
+      // simplex (x_v, t_bot), (x_v, t_top), (x_w, tau_w) for the other facet vertices
+      for (int d = 0; d < DIM; ++d) {
+        s_fP[0][d] = s_xv[d];
+        s_fP[1][d] = s_xv[d];
+        s_fn[d] = a.facet_nrm[(int64_t)fid * DIM + d];
+      }
+      s_fP[0][DIM] = s_tbot;
+      s_fP[1][DIM] = s_ttop;
+      int c2 = 2;
+      for (int i = 0; i < DIM; ++i) {
+        const int w = a.facet_vert[(int64_t)fid * DIM + i];
+        if (w == v) continue;
+        for (int d = 0; d < DIM; ++d) s_fP[c2][d] = a.X[(int64_t)w * DIM + d];
+        s_fP[c2][DIM] = a.tau[w];
+        ++c2;
+      }
+      // n! * n-volume = sqrt(det(E^T E)), E = [P_i - P_0] ((n+1) x n)
+      double E[DIM + 1][DIM];
+      for (int i = 0; i < DIM; ++i)
+        for (int d = 0; d <= DIM; ++d) E[d][i] = s_fP[i + 1][d] - s_fP[0][d];
+      double G[DIM][DIM];
+      for (int i = 0; i < DIM; ++i)
+        for (int j = 0; j < DIM; ++j) {
+          double s = 0.0;
+          for (int d = 0; d <= DIM; ++d) s += E[d][i] * E[d][j];
+          G[i][j] = s;
+        }
+      const double det = small_det<DIM>(G);
+      s_fscale = sqrt(fabs(det));
+    }
+    __syncthreads();
+    const long long goff = a.tent_gdoff[tent] + (long long)f * Q;
+    for (int base = 0; base < Q; base += CH) {
+      const int nq = min(CH, Q - base);
+      double* Pd = sR;                       // CH * nb : s_j.n + alpha v_j
+      double* Vd = sR + (size_t)CH * nb;     // CH * nb : w v_i
+      double* Sd = sV;                       // CH * nb : alpha v_i - s_i.n
+      double* Gd = sV + (size_t)CH * nb;     // CH * nrhs : w g_D
+      if (tid < nq) {
+        const int q = base + tid;
+        double xt[DIM + 1];
+        for (int d = 0; d <= DIM; ++d) xt[d] = 0.0;
+        for (int i = 0; i < NV; ++i) {
+          const double l = __ldg(a.bary + q * NV + i);
+          for (int d = 0; d <= DIM; ++d) xt[d] = fma(l, s_fP[i][d], xt[d]);
+        }
+        double xh[DIM];
+        for (int d = 0; d < DIM; ++d) xh[d] = (xt[d] - s_xv[d]) * ih;
+        const double th = c * (xt[DIM] - tc) * ih;
+        double* m = sM + tid * a.mono_stride;
+        eval_monomials<DIM>(a, th, xh, m);
+        const double w = __ldg(a.wref + q) * s_fscale;
+        for (int j = 0; j < nb; ++j) {
+          const double vj = c * ih * sp_eval<DIM>(a, j, 1, m);
+          double sn = 0.0;
+          for (int d = 0; d < DIM; ++d) sn = fma(-ih * sp_eval<DIM>(a, j, 2 + d, m), s_fn[d], sn);
+          Pd[tid * nb + j] = sn + a.alpha * vj;
+          Vd[tid * nb + j] = w * vj;
+          Sd[tid * nb + j] = a.alpha * vj - sn;
+        }
+        for (int r = 0; r < nrhs; ++r)
+          Gd[tid * nrhs + r] = (a.gD != nullptr) ? w * a.gD[(long long)r * a.n_bnd + goff + q] : 0.0;
+      }
+      __syncthreads();
+      for (int id = tid; id < nb * nb; id += blockDim.x) {
+        const int i = id / nb, j = id % nb;
+        double t = sA[id];
+        for (int ql = 0; ql < nq; ++ql) t = fma(Vd[ql * nb + i], Pd[ql * nb + j], t);
+        sA[id] = t;
+      }
+      for (int id = tid; id < nbpair; id += blockDim.x) {
+        const int r = id / nb, i = id % nb;
+        double t = sb[id];
+        for (int ql = 0; ql < nq; ++ql) t = fma(Gd[ql * nrhs + r], Sd[ql * nb + i], t);
+        sb[id] = t;
+      }
+      __syncthreads();
+    }
+  }
+
+  // ---------------- phase 3: LU with partial pivoting, then solve ----------------
+  const int lane = tid & 31, warp = tid >> 5;
+  for (int k = 0; k < nb; ++k) {
+    if (warp == 0) {
+      double best = -1.0;
+      int bi = k;
+      for (int i = k + lane; i < nb; i += 32) {
+        const double val = fabs(sA[i * nb + k]);
+        if (val > best) {
+          best = val;
+          bi = i;
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_down_sync(0xffffffffu, best, o);
+        const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) {
+          best = ob;
+          bi = oi;
+        }
+      }
+      if (lane == 0) s_piv = bi;
+    }
+    __syncthreads();
+    const int pr = s_piv;
+    if (pr != k) {
+      for (int j = tid; j < nb; j += blockDim.x) {
+        const double t = sA[k * nb + j];
+        sA[k * nb + j] = sA[pr * nb + j];
+        sA[pr * nb + j] = t;
+      }
+      for (int r = tid; r < nrhs; r += blockDim.x) {
+        const double t = sb[r * nb + k];
+        sb[r * nb + k] = sb[r * nb + pr];
+        sb[r * nb + pr] = t;
+      }
+    }
+    __syncthreads();
+    double piv = sA[k * nb + k];
+    if (!(fabs(piv) > 0.0) || !isfinite(piv)) {
+      if (tid == 0) flag_error(a, TP_ERR_SINGULAR, tent);
+      piv = 1.0;
+    }
+    const double ipiv = 1.0 / piv;
+    for (int i = k + 1 + tid; i < nb; i += blockDim.x) sA[i * nb + k] *= ipiv;
+    __syncthreads();
+    const int rem = nb - k - 1;
+    for (int id = tid; id < rem * rem; id += blockDim.x) {
+      const int i = k + 1 + id / rem, j = k + 1 + id % rem;
+      sA[i * nb + j] = fma(-sA[i * nb + k], sA[k * nb + j], sA[i * nb + j]);
+    }
+    for (int id = tid; id < rem * nrhs; id += blockDim.x) {
+      const int r = id / rem, i = k + 1 + id % rem;
+      sb[r * nb + i] = fma(-sA[i * nb + k], sb[r * nb + k], sb[r * nb + i]);
+    }
+    __syncthreads();
+  }
+  for (int k = nb - 1; k >= 0; --k) {
+    double d = sA[k * nb + k];
+    if (!(fabs(d) > 0.0) || !isfinite(d)) d = 1.0;
+    for (int r = tid; r < nrhs; r += blockDim.x) sb[r * nb + k] /= d;
+    __syncthreads();
+    for (int id = tid; id < k * nrhs; id += blockDim.x) {
+      const int r = id / k, i = id % k;
+      sb[r * nb + i] = fma(-sA[i * nb + k], sb[r * nb + k], sb[r * nb + i]);
+    }
+    __syncthreads();
+  }
+
+  // ---------------- phase 4: outflow at the top points ----------------
+  for (int base = 0; base < NP; base += 2 * CH) {
+    const int ql = tid, qg = base + ql;
+    if (ql < 2 * CH && qg < NP) {
+      const int k = qg / Q, q = qg % Q;
+      double x[DIM], tt = 0.0;
+      for (int d = 0; d < DIM; ++d) x[d] = 0.0;
+      for (int i = 0; i < NV; ++i) {
+        const double l = __ldg(a.bary + q * NV + i);
+        for (int d = 0; d < DIM; ++d) x[d] = fma(l, s_X[k][i][d], x[d]);
+        tt = fma(l, s_tt[k][i], tt);
+      }
+      double xh[DIM];
+      for (int d = 0; d < DIM; ++d) xh[d] = (x[d] - s_xv[d]) * ih;
+      const double th = c * (tt - tc) * ih;
+      double* m = sM + tid * a.mono_stride;
+      eval_monomials<DIM>(a, th, xh, m);
+      const int el = s_el[k];
+      for (int r0 = 0; r0 < nrhs; r0 += kRhsReg) {
+        double o[kRhsReg][C];
+#pragma unroll
+        for (int r = 0; r < kRhsReg; ++r)
+#pragma unroll
+          for (int cc = 0; cc < C; ++cc) o[r][cc] = 0.0;
+        for (int j = 0; j < nb; ++j) {
+          double bv[C];
+#pragma unroll
+          for (int cc = 0; cc < C; ++cc) bv[cc] = sp_eval<DIM>(a, j, cc, m);
+#pragma unroll
+          for (int r = 0; r < kRhsReg; ++r) {
+            if (r0 + r < nrhs) {
+              const double xj = sb[(r0 + r) * nb + j];
+#pragma unroll
+              for (int cc = 0; cc < C; ++cc) o[r][cc] = fma(xj, bv[cc], o[r][cc]);
+            }
+          }
+        }
+#pragma unroll
+        for (int r = 0; r < kRhsReg; ++r) {
+          if (r0 + r < nrhs) {
+            double* f = a.front + (((int64_t)(r0 + r) * a.ne + el) * Q + q) * C;
+            f[0] = o[r][0];
+            f[1] = c * ih * o[r][1];
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) f[2 + d] = -ih * o[r][2 + d];
+          }
+        }
+      }
+    }
+  }
+  if (tid == 0) a.tau[v] = s_ttop;
+}
+
+// energy flux through the front, per (rhs, element) partial sums
+template <int DIM>
+__global__ void k_energy_partial(const KArgs a, double* partial, int nblk_per_rhs) {
+  constexpr int NV = DIM + 1, C = DIM + 2;
+  __shared__ double red[kThreads];
+  const int r = blockIdx.y;
+  double acc = 0.0;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < a.ne;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    double e[DIM][DIM], dt[DIM], X0[DIM];
+    const int v0 = a.elems[k * NV];
+    for (int d = 0; d < DIM; ++d) X0[d] = a.X[(int64_t)v0 * DIM + d];
+    const double t0 = a.tau[v0];
+    for (int i = 0; i < DIM; ++i) {
+      const int vi = a.elems[k * NV + i + 1];
+      for (int d = 0; d < DIM; ++d) e[i][d] = a.X[(int64_t)vi * DIM + d] - X0[d];
+      dt[i] = a.tau[vi] - t0;
+    }
+    double g[DIM];
+    const double det = lin_grad<DIM>(e, dt, g);
+    const double ic2 = 1.0 / (a.cK[k] * a.cK[k]);
+    const double ad = fabs(det);
+    const double* f = a.front + ((int64_t)r * a.ne + k) * a.Q * C;
+    for (int q = 0; q < a.Q; ++q) {
+      const double vv = f[q * C + 1];
+      double s2 = 0.0, sg = 0.0;
+      for (int d = 0; d < DIM; ++d) {
+        s2 = fma(f[q * C + 2 + d], f[q * C + 2 + d], s2);
+        sg = fma(f[q * C + 2 + d], g[d], sg);
+      }
+      acc = fma(0.5 * __ldg(a.wref + q) * ad, ic2 * vv * vv + s2 - 2.0 * vv * sg, acc);
+    }
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[(int64_t)r * nblk_per_rhs + blockIdx.x] = red[0];
+}
+
+__global__ void k_energy_final(const double* partial, int nblk, int nrhs, double* out) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrhs) return;
+  double s = 0.0;
+  for (int b = 0; b < nblk; ++b) s += partial[(int64_t)r * nblk + b];
+  out[r] = s;
+}
+
+template <typename T>
+int upload(T** dptr, const std::vector<T>& h) {
+  *dptr = nullptr;
+  if (h.empty()) return TP_OK;
+  TP_CUDA_OK(cudaMalloc(dptr, h.size() * sizeof(T)));
+  TP_CUDA_OK(cudaMemcpy(*dptr, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return TP_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// context
+// ===========================================================================
+struct tp_ctx {
+  int dim = 0, p = 0, nb = 0, nmono = 0, Q = 0, C = 0, nrhs = 1;
+  double alpha = 0.5;
+  int64_t nv = 0, ne = 0, ntents = 0, n_bnd = 0;
+  int32_t n_levels = 0;
+  std::vector<int64_t> level_ptr;
+  tp::Topology topo;
+  tp::SimplexRule rule;
+  std::vector<double> bnd_xt;
+  KArgs args{};
+  size_t smem_bytes = 0;
+  int energy_blocks = 0;
+  std::vector<void*> allocs;
+  double* d_front = nullptr;
+  double* d_tau = nullptr;
+  double* d_gD = nullptr;
+  double* d_partial = nullptr;
+  int* d_status = nullptr;
+  long long* d_info = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  cudaStream_t last_stream = nullptr;
+  std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
+  int device = 0;
+};
+
+namespace {
+
+template <typename T>
+int ctx_upload(tp_ctx* ctx, T** d, const std::vector<T>& h) {
+  int rc = upload(d, h);
+  if (rc == TP_OK && *d) ctx->allocs.push_back((void*)*d);
+  return rc;
+}
+
+constexpr size_t kMaxDynSmem = 200 * 1024;   // cap of the shared-memory plan
+
+// the attribute is set to the plan's cap, so contexts of any size can share the kernel
+template <int DIM>
+int set_smem_attr() {
+  TP_CUDA_OK(cudaFuncSetAttribute(k_layer_fp64<DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)kMaxDynSmem));
+  return TP_OK;
+}
+
+int launch_level(tp_ctx* ctx, int32_t L, cudaStream_t st) {
+  const int64_t t0 = ctx->level_ptr[L - 1], t1 = ctx->level_ptr[L];
+  if (t1 <= t0) return TP_OK;
+  const dim3 grid((unsigned)(t1 - t0)), block(kThreads);
+  switch (ctx->dim) {
+    case 1: k_layer_fp64<1><<<grid, block, ctx->smem_bytes, st>>>(ctx->args, (int)t0); break;
+    case 2: k_layer_fp64<2><<<grid, block, ctx->smem_bytes, st>>>(ctx->args, (int)t0); break;
+    default: k_layer_fp64<3><<<grid, block, ctx->smem_bytes, st>>>(ctx->args, (int)t0); break;
+  }
+  TP_CUDA_OK(cudaGetLastError());
+  return TP_OK;
+}
+
+}  // namespace
+
+extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const tp_basis* basis,
+                         const tp_params* prm, tp_ctx** out) {
+  if (!mesh || !tents || !basis || !prm || !out) {
+    tp::set_error("tp_create: null argument");
+    return TP_ERR_ARG;
+  }
+  if (mesh->dim != basis->dim || mesh->dim != tents->dim || prm->p != basis->p ||
+      mesh->n_vert != tents->nv || prm->nrhs < 1) {
+    tp::set_error("tp_create: dim/p/n_vert mismatch between mesh, tents, basis and params");
+    return TP_ERR_ARG;
+  }
+  if (prm->precision != TP_FP64) {
+    tp::set_error("tp_create: only TP_FP64 is available in this build");
+    return TP_ERR_UNSUPPORTED;
+  }
+  auto* ctx = new tp_ctx();
+  auto fail = [&](int rc) {
+    tp_destroy_ctx(ctx);
+    return rc;
+  };
+  if (!tp::build_topology(mesh, &ctx->topo)) return fail(TP_ERR_ARG);
+  tp::Topology& T = ctx->topo;
+  const int n = T.dim;
+  ctx->dim = n;
+  ctx->p = basis->p;
+  ctx->nb = basis->nb;
+  ctx->nmono = basis->nmono;
+  ctx->C = n + 2;
+  ctx->nrhs = prm->nrhs;
+  ctx->alpha = prm->alpha;
+  ctx->nv = T.nv;
+  ctx->ne = T.ne;
+  ctx->rule = tp::simplex_rule(n, basis->p + 1);
+  ctx->Q = ctx->rule.Q;
+  ctx->ntents = (int64_t)tents->vert.size();
+  ctx->n_levels = tents->n_levels;
+  ctx->level_ptr = tents->level_ptr;
+  // patch checks: size limit and single material per tent
+  for (int64_t v = 0; v < T.nv; ++v) {
+    const int p0 = T.star_ptr[v], p1 = T.star_ptr[v + 1];
+    if (p1 - p0 > tp::kMaxPatch) {
+      tp::set_error("tp_create: vertex " + std::to_string(v) + " has more than 64 elements");
+      return fail(TP_ERR_UNSUPPORTED);
+    }
+    for (int e = p0; e < p1; ++e)
+      if (T.c[T.star_el[e]] != T.c[T.star_el[p0]]) {
+        tp::set_error("tp_create: tent at vertex " + std::to_string(v) +
+                      " mixes wave speeds (interface tents are not in this build)");
+        return fail(TP_ERR_UNSUPPORTED);
+      }
+  }
+  // replay the tents on the host: anisotropic diameter (eq. 3.3) and the
+  // Dirichlet quadrature points of every tent
+  std::vector<double> tau(T.nv, 0.0), tent_h(ctx->ntents);
+  std::vector<long long> gdoff(ctx->ntents + 1, 0);
+  const int Q = ctx->Q;
+  for (int64_t it = 0; it < ctx->ntents; ++it) {
+    const int v = tents->vert[it];
+    const double tb = tau[v], tt = tents->t_top[it], c = T.c[T.star_el[T.star_ptr[v]]];
+    std::vector<std::vector<double>> pts;
+    auto push = [&](int w, double t) {
+      std::vector<double> pnt(n + 1);
+      for (int d = 0; d < n; ++d) pnt[d] = T.X[(int64_t)w * n + d];
+      pnt[n] = t;
+      pts.push_back(pnt);
+    };
+    push(v, tb);
+    push(v, tt);
+    for (int e = T.nbr_ptr[v]; e < T.nbr_ptr[v + 1]; ++e) push(T.nbr[e], tau[T.nbr[e]]);
+    double best = 0.0;
+    for (size_t i = 0; i < pts.size(); ++i)
+      for (size_t j = i + 1; j < pts.size(); ++j) {
+        double s = 0.0;
+        for (int d = 0; d < n; ++d) s += (pts[i][d] - pts[j][d]) * (pts[i][d] - pts[j][d]);
+        const double dt = pts[i][n] - pts[j][n];
+        s += c * c * dt * dt;
+        best = std::max(best, std::sqrt(s));
+      }
+    tent_h[it] = best;
+    const int nf = T.vfac_ptr[v + 1] - T.vfac_ptr[v];
+    gdoff[it + 1] = gdoff[it] + (long long)nf * Q;
+    for (int f = 0; f < nf; ++f) {
+      const int fid = T.vfac[T.vfac_ptr[v] + f];
+      double P[4][4];
+      for (int d = 0; d < n; ++d) P[0][d] = P[1][d] = T.X[(int64_t)v * n + d];
+      P[0][n] = tb;
+      P[1][n] = tt;
+      int c2 = 2;
+      for (int i = 0; i < n; ++i) {
+        const int w = T.facet_vert[(int64_t)fid * n + i];
+        if (w == v) continue;
+        for (int d = 0; d < n; ++d) P[c2][d] = T.X[(int64_t)w * n + d];
+        P[c2][n] = tau[w];
+        ++c2;
+      }
+      for (int q = 0; q < Q; ++q)
+        for (int d = 0; d <= n; ++d) {
+          double s = 0.0;
+          for (int i = 0; i <= n; ++i) s += ctx->rule.bary[q * (n + 1) + i] * P[i][d];
+          ctx->bnd_xt.push_back(s);
+        }
+    }
+    tau[v] = tt;
+  }
+  ctx->n_bnd = gdoff[ctx->ntents];
+  gdoff.pop_back();
+
+  // device uploads
+  int rc = TP_OK;
+  KArgs& a = ctx->args;
+  double *dX, *dc, *dnrm, *dbary, *dw, *dsqw, *dttop, *dh, *dspc;
+  int *del, *dsp, *dse, *dvp, *dvf, *dfv, *dtv, *dspp, *dspm, *dpar, *dvar;
+  long long* dgo;
+  std::vector<double> sqw(Q);
+  for (int q = 0; q < Q; ++q) sqw[q] = std::sqrt(ctx->rule.w[q]);
+  std::vector<double> ttop(tents->t_top.begin(), tents->t_top.end());
+  std::vector<int> tv(tents->vert.begin(), tents->vert.end());
+  if ((rc = ctx_upload(ctx, &dX, T.X)) || (rc = ctx_upload(ctx, &dc, T.c)) ||
+      (rc = ctx_upload(ctx, &del, T.elems)) || (rc = ctx_upload(ctx, &dsp, T.star_ptr)) ||
+      (rc = ctx_upload(ctx, &dse, T.star_el)) || (rc = ctx_upload(ctx, &dvp, T.vfac_ptr)) ||
+      (rc = ctx_upload(ctx, &dvf, T.vfac)) || (rc = ctx_upload(ctx, &dfv, T.facet_vert)) ||
+      (rc = ctx_upload(ctx, &dnrm, T.facet_nrm)) || (rc = ctx_upload(ctx, &dbary, ctx->rule.bary)) ||
+      (rc = ctx_upload(ctx, &dw, ctx->rule.w)) || (rc = ctx_upload(ctx, &dsqw, sqw)) ||
+      (rc = ctx_upload(ctx, &dtv, tv)) || (rc = ctx_upload(ctx, &dttop, ttop)) ||
+      (rc = ctx_upload(ctx, &dh, tent_h)) || (rc = ctx_upload(ctx, &dgo, gdoff)) ||
+      (rc = ctx_upload(ctx, &dspp, basis->sp_ptr)) || (rc = ctx_upload(ctx, &dspm, basis->sp_mono)) ||
+      (rc = ctx_upload(ctx, &dspc, basis->sp_coef)) || (rc = ctx_upload(ctx, &dpar, basis->parent)) ||
+      (rc = ctx_upload(ctx, &dvar, basis->var)))
+    return fail(rc == TP_ERR_CUDA ? TP_ERR_OOM : rc);
+  const size_t nfront = (size_t)ctx->nrhs * T.ne * Q * ctx->C;
+  if (cudaMalloc(&ctx->d_front, nfront * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&ctx->d_tau, T.nv * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&ctx->d_status, sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&ctx->d_info, sizeof(long long)) != cudaSuccess ||
+      (ctx->n_bnd > 0 &&
+       cudaMalloc(&ctx->d_gD, (size_t)ctx->nrhs * ctx->n_bnd * sizeof(double)) != cudaSuccess)) {
+    tp::set_error("tp_create: device allocation of the front state failed");
+    return fail(TP_ERR_OOM);
+  }
+  ctx->energy_blocks = (int)std::min<int64_t>(1024, (T.ne + kThreads - 1) / kThreads);
+  if (cudaMalloc(&ctx->d_partial, (size_t)ctx->nrhs * ctx->energy_blocks * sizeof(double)) != cudaSuccess) {
+    tp::set_error("tp_create: device allocation failed");
+    return fail(TP_ERR_OOM);
+  }
+  cudaMemset(ctx->d_front, 0, nfront * sizeof(double));
+  cudaMemset(ctx->d_tau, 0, T.nv * sizeof(double));
+  cudaMemset(ctx->d_status, 0, sizeof(int));
+  cudaMemset(ctx->d_info, 0, sizeof(long long));
+  cudaGetDevice(&ctx->device);
+
+  a.nb = ctx->nb;
+  a.nmono = ctx->nmono;
+  a.Q = Q;
+  a.nrhs = ctx->nrhs;
+  a.ne = T.ne;
+  a.n_bnd = ctx->n_bnd;
+  a.alpha = ctx->alpha;
+  a.X = dX;
+  a.elems = del;
+  a.cK = dc;
+  a.star_ptr = dsp;
+  a.star_el = dse;
+  a.vfac_ptr = dvp;
+  a.vfac = dvf;
+  a.facet_vert = dfv;
+  a.facet_nrm = dnrm;
+  a.bary = dbary;
+  a.wref = dw;
+  a.sqw = dsqw;
+  a.tent_v = dtv;
+  a.tent_ttop = dttop;
+  a.tent_h = dh;
+  a.tent_gdoff = dgo;
+  a.sp_ptr = dspp;
+  a.sp_mono = dspm;
+  a.sp_coef = dspc;
+  a.mono_parent = dpar;
+  a.mono_var = dvar;
+  a.tau = ctx->d_tau;
+  a.front = ctx->d_front;
+  a.gD = nullptr;
+  a.status = ctx->d_status;
+  a.status_info = ctx->d_info;
+  // shared-memory plan: the largest chunk of points that fits
+  const int nb = ctx->nb, C = ctx->C, RT = n + 2;
+  const int npair = nb * (nb + 1) / 2;
+  if (npair > kMaxPair * kThreads || ctx->nrhs * nb > kMaxPair * kThreads) {
+    tp::set_error("tp_create: nb or nrhs too large for this kernel");
+    return fail(TP_ERR_UNSUPPORTED);
+  }
+  a.mono_stride = ctx->nmono | 1;
+  int CH = 64;
+  size_t bytes = 0;
+  for (; CH >= 8; CH /= 2) {
+    size_t off = (size_t)nb * nb;
+    a.off_b = (int)off;
+    off += (size_t)ctx->nrhs * nb;
+    a.off_rows = (int)off;
+    off += (size_t)CH * RT * nb;
+    a.off_bvs = (int)off;
+    off += (size_t)CH * (n + 1) * nb;
+    a.off_cb = (int)off;
+    off += (size_t)CH * ctx->nrhs * C;
+    a.off_mono = (int)off;
+    off += (size_t)2 * CH * a.mono_stride;
+    bytes = off * sizeof(double);
+    // the Dirichlet phase reuses the rows/bvs regions
+    const size_t need_d = (size_t)CH * (3 * nb + ctx->nrhs);
+    const size_t have_d = (size_t)CH * (RT + n + 1) * nb;
+    if (bytes <= kMaxDynSmem && need_d <= have_d) break;
+  }
+  if (CH < 8) {
+    tp::set_error("tp_create: shared-memory plan does not fit (nb/nrhs too large)");
+    return fail(TP_ERR_UNSUPPORTED);
+  }
+  a.CH = CH;
+  ctx->smem_bytes = bytes;
+  switch (n) {
+    case 1: rc = set_smem_attr<1>(); break;
+    case 2: rc = set_smem_attr<2>(); break;
+    default: rc = set_smem_attr<3>(); break;
+  }
+  if (rc) return fail(rc);
+  if (cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    tp::set_error("tp_create: stream creation failed");
+    return fail(TP_ERR_CUDA);
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    tp::set_error("tp_create: device error during set-up");
+    return fail(TP_ERR_CUDA);
+  }
+  *out = ctx;
+  return TP_OK;
+}
+
+extern "C" int tp_ctx_info(const tp_ctx* ctx, int64_t* n_front, int32_t* n_comp, int64_t* n_bnd,
+                           int32_t* n_levels) {
+  if (!ctx) {
+    tp::set_error("tp_ctx_info: null context");
+    return TP_ERR_ARG;
+  }
+  if (n_front) *n_front = ctx->ne * ctx->Q;
+  if (n_comp) *n_comp = ctx->C;
+  if (n_bnd) *n_bnd = ctx->n_bnd;
+  if (n_levels) *n_levels = ctx->n_levels;
+  return TP_OK;
+}
+
+extern "C" int tp_front_points(const tp_ctx* ctx, double* xq, double* wq) {
+  if (!ctx) {
+    tp::set_error("tp_front_points: null context");
+    return TP_ERR_ARG;
+  }
+  const tp::Topology& T = ctx->topo;
+  const int n = ctx->dim, Q = ctx->Q;
+  for (int64_t k = 0; k < T.ne; ++k) {
+    const int32_t* el = &T.elems[k * (n + 1)];
+    double e[3][3];
+    for (int i = 0; i < n; ++i)
+      for (int d = 0; d < n; ++d) e[i][d] = T.X[(int64_t)el[i + 1] * n + d] - T.X[(int64_t)el[0] * n + d];
+    double det = (n == 1) ? e[0][0]
+               : (n == 2) ? e[0][0] * e[1][1] - e[0][1] * e[1][0]
+                          : e[0][0] * (e[1][1] * e[2][2] - e[1][2] * e[2][1]) -
+                                e[0][1] * (e[1][0] * e[2][2] - e[1][2] * e[2][0]) +
+                                e[0][2] * (e[1][0] * e[2][1] - e[1][1] * e[2][0]);
+    for (int q = 0; q < Q; ++q) {
+      if (xq)
+        for (int d = 0; d < n; ++d) {
+          double s = 0.0;
+          for (int i = 0; i <= n; ++i) s += ctx->rule.bary[q * (n + 1) + i] * T.X[(int64_t)el[i] * n + d];
+          xq[(k * Q + q) * n + d] = s;
+        }
+      if (wq) wq[k * Q + q] = ctx->rule.w[q] * std::fabs(det);
+    }
+  }
+  return TP_OK;
+}
+
+extern "C" int tp_boundary_points(const tp_ctx* ctx, double* xt) {
+  if (!ctx || (!xt && ctx->n_bnd > 0)) {
+    tp::set_error("tp_boundary_points: null argument");
+    return TP_ERR_ARG;
+  }
+  std::copy(ctx->bnd_xt.begin(), ctx->bnd_xt.end(), xt);
+  return TP_OK;
+}
+
+extern "C" int tp_set_state(tp_ctx* ctx, const double* d_front, const double* d_gD, void* stream) {
+  if (!ctx || !d_front) {
+    tp::set_error("tp_set_state: null argument");
+    return TP_ERR_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t nfront = (size_t)ctx->nrhs * ctx->ne * ctx->Q * ctx->C;
+  TP_CUDA_OK(cudaMemcpyAsync(ctx->d_front, d_front, nfront * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  TP_CUDA_OK(cudaMemsetAsync(ctx->d_tau, 0, ctx->nv * sizeof(double), st));
+  TP_CUDA_OK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), st));
+  TP_CUDA_OK(cudaMemsetAsync(ctx->d_info, 0, sizeof(long long), st));
+  if (ctx->n_bnd > 0) {
+    if (d_gD) {
+      TP_CUDA_OK(cudaMemcpyAsync(ctx->d_gD, d_gD, (size_t)ctx->nrhs * ctx->n_bnd * sizeof(double),
+                                 cudaMemcpyDeviceToDevice, st));
+      ctx->args.gD = ctx->d_gD;
+    } else {
+      TP_CUDA_OK(cudaMemsetAsync(ctx->d_gD, 0, (size_t)ctx->nrhs * ctx->n_bnd * sizeof(double), st));
+      ctx->args.gD = ctx->d_gD;
+    }
+  }
+  ctx->last_stream = st;
+  return TP_OK;
+}
+
+extern "C" int tp_solve_layer(tp_ctx* ctx, int32_t level, void* stream) {
+  if (!ctx || level < 1 || level > ctx->n_levels) {
+    tp::set_error("tp_solve_layer: level out of range");
+    return TP_ERR_ARG;
+  }
+  ctx->last_stream = (cudaStream_t)stream;
+  return launch_level(ctx, level, (cudaStream_t)stream);
+}
+
+extern "C" int tp_advance(tp_ctx* ctx, int32_t level_begin, int32_t level_end, void* stream) {
+  if (!ctx || level_begin < 1 || level_end > ctx->n_levels + 1 || level_end < level_begin) {
+    tp::set_error("tp_advance: level range out of bounds");
+    return TP_ERR_ARG;
+  }
+  if (level_end == level_begin) return TP_OK;
+  auto key = std::make_pair((int)level_begin, (int)level_end);
+  auto it = ctx->graphs.find(key);
+  if (it == ctx->graphs.end()) {
+    cudaGraph_t g = nullptr;
+    TP_CUDA_OK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+    int rc = TP_OK;
+    for (int32_t L = level_begin; L < level_end && rc == TP_OK; ++L) rc = launch_level(ctx, L, ctx->cap_stream);
+    cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &g);
+    if (rc != TP_OK) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    TP_CUDA_OK(e);
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    TP_CUDA_OK(e);
+    it = ctx->graphs.emplace(key, ex).first;
+  }
+  ctx->last_stream = (cudaStream_t)stream;
+  TP_CUDA_OK(cudaGraphLaunch(it->second, (cudaStream_t)stream));
+  return TP_OK;
+}
+
+extern "C" int tp_energy(tp_ctx* ctx, double* d_out, void* stream) {
+  if (!ctx || !d_out) {
+    tp::set_error("tp_energy: null argument");
+    return TP_ERR_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const dim3 grid(ctx->energy_blocks, ctx->nrhs);
+  switch (ctx->dim) {
+    case 1: k_energy_partial<1><<<grid, kThreads, 0, st>>>(ctx->args, ctx->d_partial, ctx->energy_blocks); break;
+    case 2: k_energy_partial<2><<<grid, kThreads, 0, st>>>(ctx->args, ctx->d_partial, ctx->energy_blocks); break;
+    default: k_energy_partial<3><<<grid, kThreads, 0, st>>>(ctx->args, ctx->d_partial, ctx->energy_blocks); break;
+  }
+  TP_CUDA_OK(cudaGetLastError());
+  k_energy_final<<<(ctx->nrhs + 127) / 128, 128, 0, st>>>(ctx->d_partial, ctx->energy_blocks, ctx->nrhs, d_out);
+  TP_CUDA_OK(cudaGetLastError());
+  ctx->last_stream = st;
+  return TP_OK;
+}
+
+extern "C" int tp_get_state(const tp_ctx* ctx, double* d_front, double* d_tau, void* stream) {
+  if (!ctx) {
+    tp::set_error("tp_get_state: null context");
+    return TP_ERR_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  if (d_front)
+    TP_CUDA_OK(cudaMemcpyAsync(d_front, ctx->d_front,
+                               (size_t)ctx->nrhs * ctx->ne * ctx->Q * ctx->C * sizeof(double),
+                               cudaMemcpyDeviceToDevice, st));
+  if (d_tau) TP_CUDA_OK(cudaMemcpyAsync(d_tau, ctx->d_tau, ctx->nv * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  return TP_OK;
+}
+
+extern "C" int tp_sync_status(tp_ctx* ctx, int32_t* status, int64_t* info) {
+  if (!ctx) {
+    tp::set_error("tp_sync_status: null context");
+    return TP_ERR_ARG;
+  }
+  TP_CUDA_OK(cudaStreamSynchronize(ctx->last_stream));
+  int s = 0;
+  long long i = 0;
+  TP_CUDA_OK(cudaMemcpy(&s, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  TP_CUDA_OK(cudaMemcpy(&i, ctx->d_info, sizeof(long long), cudaMemcpyDeviceToHost));
+  if (status) *status = s;
+  if (info) *info = i;
+  return TP_OK;
+}
+
+extern "C" void tp_destroy_ctx(tp_ctx* ctx) {
+  if (!ctx) return;
+  for (auto& kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
+  for (void* p : ctx->allocs) cudaFree(p);
+  cudaFree(ctx->d_front);
+  cudaFree(ctx->d_tau);
+  cudaFree(ctx->d_gD);
+  cudaFree(ctx->d_partial);
+  cudaFree(ctx->d_status);
+  cudaFree(ctx->d_info);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  delete ctx;
+}

@@ -1,0 +1,72 @@
+// Internal structures of libtp shared by the host code (tp_host.cpp) and the
+// CUDA code (tp_cuda.cu).  Not part of the public ABI (include/tp.h).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/tp.h"
+
+namespace tp {
+
+void set_error(const std::string& msg);
+
+constexpr int kMaxDim = 3;
+constexpr int kMaxP = 8;
+constexpr int kMaxPatch = 64;     // elements in one vertex star handled by one CTA
+
+// ---------------------------------------------------------------------------
+// mesh topology built on the host
+// ---------------------------------------------------------------------------
+struct Topology {
+  int dim = 0;
+  int64_t nv = 0, ne = 0;
+  std::vector<double> X;          // nv * dim
+  std::vector<int32_t> elems;     // ne * (dim+1)
+  std::vector<double> c;          // ne
+  std::vector<int32_t> star_ptr, star_el;     // elements around a vertex (ascending)
+  std::vector<int32_t> nbr_ptr, nbr;          // neighbouring vertices (ascending)
+  std::vector<int32_t> facet_vert;            // boundary facets: dim sorted vertex ids each
+  std::vector<double> facet_nrm;              // boundary facets: outward unit normal (dim)
+  std::vector<int32_t> vfac_ptr, vfac;        // boundary facets through a vertex (facet order)
+};
+
+bool build_topology(const tp_mesh_desc* m, Topology* t);
+
+// ---------------------------------------------------------------------------
+// reference rule on the n-simplex (collapsed Gauss-Jacobi, m points per axis)
+// ---------------------------------------------------------------------------
+struct SimplexRule {
+  int n = 0, m = 0, Q = 0;
+  std::vector<double> bary;   // Q * (n+1)
+  std::vector<double> w;      // Q, sums to 1/n!
+};
+SimplexRule simplex_rule(int n, int m);
+
+}  // namespace tp
+
+// ---------------------------------------------------------------------------
+// opaque handles
+// ---------------------------------------------------------------------------
+struct tp_tents {
+  int dim = 0;
+  int64_t nv = 0;
+  double T = 0.0, kappa = 0.0;
+  std::vector<int32_t> vert, level, round;
+  std::vector<double> t_bot, t_top;
+  std::vector<int64_t> level_ptr;   // tents of level L (1-based) are [level_ptr[L-1], level_ptr[L])
+  int32_t n_levels = 0;
+};
+
+struct tp_basis {
+  int dim = 0, p = 0, nb = 0, nmono = 0;
+  std::vector<int32_t> exps;        // nmono * (dim+1): exponents of (that, xhat_1..n)
+  std::vector<int32_t> parent;      // monomial g = monomial parent[g] * variable var[g] (g >= 1)
+  std::vector<int32_t> var;
+  std::vector<double> coef;         // nb * nmono, U
+  // sparse evaluation table: for basis j and component comp in
+  // {U, d/dthat, d/dxhat_1..n}: entries [ptr[j*C+comp], ptr[j*C+comp+1])
+  std::vector<int32_t> sp_ptr, sp_mono;
+  std::vector<double> sp_coef;
+};

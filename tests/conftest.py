@@ -11,3 +11,22 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300) and the built libtp.so")
     config.addinivalue_line("markers", "slow: long-running CPU test")
+
+
+@pytest.fixture(scope="session")
+def libtp():
+    """libtp.so, built in-tree on first use (nvcc cross-compiles without a GPU)."""
+    from paper_1907_02367_gb300 import _binding
+    if not os.path.exists(_binding.LIB_PATH):
+        import __graft_entry__
+        __graft_entry__.build()
+    return _binding.load()
+
+
+@pytest.fixture(scope="session")
+def cuda_device(libtp):
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+    return torch.device("cuda:0")
