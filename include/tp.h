@@ -148,6 +148,26 @@ int tp_get_state(const tp_ctx* ctx, double* d_front, double* d_tau, void* stream
 int tp_sync_status(tp_ctx* ctx, int32_t* status, int64_t* info);
 void tp_destroy_ctx(tp_ctx* ctx);
 
+/* Allocation-free variant of tp_energy for callers that may not allocate
+ * device memory at that point (a framework that has reserved the free device
+ * memory in its own pool, or a service that fixes its device-memory budget at
+ * start-up).  The paper has no counterpart; this is a library convenience.
+ * Computes the same E_r as tp_energy from caller-owned device arrays, with no
+ * context and no cudaMalloc/cudaFree:
+ *   d_coords n_vert x dim, d_elems n_elem x (dim+1), d_c n_elem, d_tau n_vert
+ *   (front times), d_wref Q reference weights of the front rule (summing to
+ *   1/dim!, e.g. wq / |det J| of tp_front_points), d_front in the front layout,
+ *   d_out nrhs doubles.
+ * Scratch: a fixed 256 KiB module array (32768 partial sums) held by every
+ * GPU that loads libtp until exit; nrhs > 32768 is rejected with TP_ERR_ARG.
+ * The first call on a device looks up that array's address and should come
+ * before any stream capture.  All calls share the array: calls that overlap
+ * on the GPU race. */
+int tp_front_energy_noalloc(int32_t dim, int64_t n_elem, int32_t Q, int32_t nrhs,
+                            const double* d_coords, const int32_t* d_elems, const double* d_c,
+                            const double* d_tau, const double* d_wref, const double* d_front,
+                            double* d_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -23,6 +23,7 @@ EXPORTED = [
     "tp_build_basis", "tp_basis_info", "tp_basis_export", "tp_destroy_basis", "tp_create",
     "tp_ctx_info", "tp_front_points", "tp_boundary_points", "tp_set_state", "tp_solve_layer",
     "tp_advance", "tp_energy", "tp_get_state", "tp_sync_status", "tp_destroy_ctx",
+    "tp_front_energy_noalloc",
 ]
 
 
@@ -77,6 +78,7 @@ def load(path: str = LIB_PATH):
         "tp_get_state": (ct.c_int, [vp, vp, vp, vp]),
         "tp_sync_status": (ct.c_int, [vp, P(i32), P(i64)]),
         "tp_destroy_ctx": (None, [vp]),
+        "tp_front_energy_noalloc": (ct.c_int, [i32, i64, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

@@ -24,6 +24,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1094,4 +1095,100 @@ extern "C" void tp_destroy_ctx(tp_ctx* ctx) {
   cudaFree(ctx->d_info);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   delete ctx;
+}
+
+// ===========================================================================
+// Allocation-free front energy (tp_front_energy_noalloc)
+//
+// Some callers cannot allocate device memory when they need this number:
+// applications whose framework has already reserved the free device memory in
+// its own pool (a library cudaMalloc would fail or fragment that pool), and
+// long-running or certified services that fix their device-memory budget at
+// start-up and forbid allocations afterwards.  This entry point computes the
+// same quantity as tp_energy from caller-owned arrays and keeps its only
+// scratch -- the per-block partial sums -- in the fixed array below.
+//
+// The array is a module global: every GPU that loads libtp holds it (256 KiB)
+// until the process exits.  In host code its name is only a host-side
+// stand-in, so the device address is looked up once per device with
+// cudaGetSymbolAddress (done by the first call on that device, which should
+// therefore come before any stream capture).  Every call shares the array:
+// each partial slot it reads is written earlier in the same call, so nothing
+// needs clearing, but two calls that overlap on the GPU (different streams or
+// threads) race on it.
+// ===========================================================================
+namespace {
+
+constexpr int kNoAllocPartials = 32768;   // doubles: nrhs x blocks-per-rhs partial sums
+static __device__ __align__(256) double g_noalloc_partials[kNoAllocPartials];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[kMaxDevices] = {};
+
+int noalloc_scratch(double** out) {
+  int dev = 0;
+  TP_CUDA_OK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) {
+    tp::set_error("tp_front_energy_noalloc: device ordinal out of range");
+    return TP_ERR_ARG;
+  }
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (g_noalloc_ptr[dev] == nullptr) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+    if (e != cudaSuccess || p == nullptr) {
+      tp::set_error(std::string("tp_front_energy_noalloc: cudaGetSymbolAddress failed: ") +
+                    cudaGetErrorString(e));
+      return TP_ERR_CUDA;
+    }
+    g_noalloc_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return TP_OK;
+}
+
+}  // namespace
+
+extern "C" int tp_front_energy_noalloc(int32_t dim, int64_t n_elem, int32_t Q, int32_t nrhs,
+                                       const double* d_coords, const int32_t* d_elems,
+                                       const double* d_c, const double* d_tau, const double* d_wref,
+                                       const double* d_front, double* d_out, void* stream) {
+  if (dim < 1 || dim > tp::kMaxDim || n_elem < 1 || Q < 1 || nrhs < 1 || !d_coords || !d_elems ||
+      !d_c || !d_tau || !d_wref || !d_front || !d_out) {
+    tp::set_error("tp_front_energy_noalloc: invalid argument");
+    return TP_ERR_ARG;
+  }
+  if (nrhs > kNoAllocPartials) {
+    tp::set_error("tp_front_energy_noalloc: nrhs = " + std::to_string(nrhs) +
+                  " exceeds the fixed scratch of " + std::to_string(kNoAllocPartials) +
+                  " partial sums (at most that many right-hand sides)");
+    return TP_ERR_ARG;
+  }
+  double* partial = nullptr;
+  int rc = noalloc_scratch(&partial);
+  if (rc != TP_OK) return rc;
+  KArgs a{};
+  a.Q = Q;
+  a.nrhs = nrhs;
+  a.ne = n_elem;
+  a.X = d_coords;
+  a.elems = d_elems;
+  a.cK = d_c;
+  a.tau = const_cast<double*>(d_tau);
+  a.wref = d_wref;
+  a.front = const_cast<double*>(d_front);
+  const int nblk = (int)std::min<int64_t>(
+      {(int64_t)1024, (n_elem + kThreads - 1) / kThreads, (int64_t)(kNoAllocPartials / nrhs)});
+  cudaStream_t st = (cudaStream_t)stream;
+  const dim3 grid(nblk, nrhs);
+  switch (dim) {
+    case 1: k_energy_partial<1><<<grid, kThreads, 0, st>>>(a, partial, nblk); break;
+    case 2: k_energy_partial<2><<<grid, kThreads, 0, st>>>(a, partial, nblk); break;
+    default: k_energy_partial<3><<<grid, kThreads, 0, st>>>(a, partial, nblk); break;
+  }
+  TP_CUDA_OK(cudaGetLastError());
+  k_energy_final<<<(nrhs + 127) / 128, 128, 0, st>>>(partial, nblk, nrhs, d_out);
+  TP_CUDA_OK(cudaGetLastError());
+  return TP_OK;
 }
