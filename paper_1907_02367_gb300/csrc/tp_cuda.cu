@@ -17,6 +17,7 @@
 //     A_ij += w (s_j.n + alpha v_j) v_i,  b_i += w g_D (alpha v_i - s_i.n).
 // Then LU with partial pivoting, and (U, v, sigma) at the top points overwrite
 // the front (Section 4.1: only the latest values are stored).
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -39,6 +40,8 @@
       return TP_ERR_CUDA;                                                             \
     }                                                                                 \
   } while (0)
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -77,7 +80,7 @@ struct KArgs {
   int* status;
   long long* status_info;
   // shared-memory carve (offsets in doubles)
-  int off_b, off_rows, off_bvs, off_cb, off_mono;
+  int off_b, off_pg, off_pb, off_pd, off_rows, off_bvs, off_cb, off_mono;
 };
 
 __device__ __forceinline__ void flag_error(const KArgs& a, int code, long long info) {
@@ -151,8 +154,14 @@ __device__ __forceinline__ double small_det(const double (&G)[DIM][DIM]) {
   }
 }
 
+// One tent per thread-block cluster of CS CTAs (CS = gridDim.x / tents in the
+// launch, 1..8).  Every CTA rebuilds the patch geometry, assembles the Gram,
+// right-hand sides and Dirichlet terms of its slice of the patch's points, and
+// publishes them in its shared memory; after a cluster barrier every CTA sums
+// all slices through distributed shared memory in rank order (so all CTAs hold
+// the same A and b), factorises redundantly and writes the outflow of its slice.
 template <int DIM>
-__global__ void __launch_bounds__(kThreads, 1) k_layer_fp64(const KArgs a, const int tent0) {
+__global__ void __launch_bounds__(kThreads, 2) k_layer_fp64(const KArgs a, const int tent0) {
   constexpr int NV = DIM + 1;   // vertices per element
   constexpr int C = DIM + 2;    // U, v, sigma
   constexpr int RT = DIM + 2;   // Gram rows per point: DIM+1 top rows + recovery row
@@ -166,18 +175,26 @@ __global__ void __launch_bounds__(kThreads, 1) k_layer_fp64(const KArgs a, const
   __shared__ double s_gb[tp::kMaxPatch][DIM], s_gt[tp::kMaxPatch][DIM];
   __shared__ double s_sdet[tp::kMaxPatch], s_st[tp::kMaxPatch];
   __shared__ int s_piv;
-  __shared__ double s_fP[NV][DIM + 1];   // Dirichlet face simplex vertices (x, t)
-  __shared__ double s_fscale, s_fn[DIM];
+  __shared__ double s_fP[tp::kMaxFacets][NV][DIM + 1];   // Dirichlet face simplices (x, t)
+  __shared__ double s_fscale[tp::kMaxFacets], s_fn[tp::kMaxFacets][DIM];
 
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int CS = (int)cluster.num_blocks();
   const int tid = threadIdx.x;
-  const int tent = tent0 + blockIdx.x;
+  const int tent = tent0 + blockIdx.x / CS;
   const int nb = a.nb, Q = a.Q, nrhs = a.nrhs, CH = a.CH;
-  double* sA = sm;
-  double* sb = sm + a.off_b;        // nrhs * nb (b, then x)
-  double* sR = sm + a.off_rows;     // CH * RT * nb
-  double* sV = sm + a.off_bvs;      // CH * (DIM+1) * nb : bottom (v, sigma) scaled by sqrt(w)
-  double* sCB = sm + a.off_cb;      // CH * nrhs * C    : bottom data coefficients
-  double* sM = sm + a.off_mono;     // 2*CH * mono_stride
+  const int npair = nb * (nb + 1) / 2;
+  const int nbpair = nrhs * nb;
+  double* sA = sm;                    // nb * nb   : assembled matrix, then LU
+  double* sb = sm + a.off_b;          // nrhs * nb : assembled rhs, then x
+  double* sPG = sm + a.off_pg;        // npair     : this CTA's Gram slice (upper triangle)
+  double* sPB = sm + a.off_pb;        // nrhs * nb : this CTA's rhs slice
+  double* sPD = sm + a.off_pd;        // nb * nb   : this CTA's Dirichlet slice
+  double* sR = sm + a.off_rows;       // CH * RT * nb
+  double* sV = sm + a.off_bvs;        // CH * (DIM+1) * nb : bottom (v, sigma) scaled by sqrt(w)
+  double* sCB = sm + a.off_cb;        // CH * nrhs * C    : bottom data coefficients
+  double* sM = sm + a.off_mono;       // 2*CH * mono_stride
 
   // ---------------- phase 0: tent and patch geometry ----------------
   if (tid == 0) {
@@ -196,7 +213,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_layer_fp64(const KArgs a, const
     s_nfac = a.vfac_ptr[v + 1] - a.vfac_ptr[v];
   }
   __syncthreads();
-  const int P = s_P, v = s_v;
+  const int P = s_P, v = s_v, nfac = s_nfac;
   for (int k = tid; k < P; k += blockDim.x) {
     const int el = a.star_el[a.star_ptr[v] + k];
     s_el[k] = el;
@@ -227,17 +244,43 @@ __global__ void __launch_bounds__(kThreads, 1) k_layer_fp64(const KArgs a, const
     if (!(q > 0.0)) flag_error(a, TP_ERR_CAUSALITY, tent);
     s_st[k] = sqrt(fmax(q, 0.0));
   }
-  // Gram pairs owned by this thread (upper triangle, i <= j)
-  const int npair = nb * (nb + 1) / 2;
+  // Dirichlet face simplices (x_v, t_bot), (x_v, t_top), (x_w, tau_w)
+  for (int f = tid; f < nfac; f += blockDim.x) {
+    const int fid = a.vfac[a.vfac_ptr[v] + f];
+    for (int d = 0; d < DIM; ++d) {
+      s_fP[f][0][d] = a.X[(int64_t)v * DIM + d];
+      s_fP[f][1][d] = a.X[(int64_t)v * DIM + d];
+      s_fn[f][d] = a.facet_nrm[(int64_t)fid * DIM + d];
+    }
+    s_fP[f][0][DIM] = a.tau[v];
+    s_fP[f][1][DIM] = a.tent_ttop[tent];
+    int c2 = 2;
+    for (int i = 0; i < DIM; ++i) {
+      const int w = a.facet_vert[(int64_t)fid * DIM + i];
+      if (w == v) continue;
+      for (int d = 0; d < DIM; ++d) s_fP[f][c2][d] = a.X[(int64_t)w * DIM + d];
+      s_fP[f][c2][DIM] = a.tau[w];
+      ++c2;
+    }
+    // n! * n-volume = sqrt(det(E^T E)), E = [P_i - P_0] ((n+1) x n)
+    double G[DIM][DIM];
+    for (int i = 0; i < DIM; ++i)
+      for (int j = 0; j < DIM; ++j) {
+        double s = 0.0;
+        for (int d = 0; d <= DIM; ++d) s += (s_fP[f][i + 1][d] - s_fP[f][0][d]) * (s_fP[f][j + 1][d] - s_fP[f][0][d]);
+        G[i][j] = s;
+      }
+    s_fscale[f] = sqrt(fabs(small_det<DIM>(G)));
+  }
+  // Gram pairs owned by this thread (upper triangle, i <= j, row-major order)
   int pi[kMaxPair], pj[kMaxPair];
-  double acc[kMaxPair];
+  double acc[kMaxPair], accb[kMaxPair];
 #pragma unroll
   for (int s = 0; s < kMaxPair; ++s) {
     const int id = tid + s * kThreads;
     int i = 0, j = 0;
-    if (id < npair) {   // row-major upper triangle enumeration
+    if (id < npair) {
       int rem = id;
-      i = 0;
       while (rem >= nb - i) {
         rem -= nb - i;
         ++i;
@@ -247,18 +290,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_layer_fp64(const KArgs a, const
     pi[s] = i;
     pj[s] = j;
     acc[s] = 0.0;
+    accb[s] = 0.0;
   }
-  const int nbpair = nrhs * nb;
-  double accb[kMaxPair];
-#pragma unroll
-  for (int s = 0; s < kMaxPair; ++s) accb[s] = 0.0;
   __syncthreads();
 
-  // ---------------- phase 1: faces over the patch (chunks of CH points) ----------------
+  // ---------------- phase 1: this CTA's slice of the patch points ----------------
   const int NP = P * Q;
+  const int slice = (NP + CS - 1) / CS;
+  const int q0 = min(NP, rank * slice), q1 = min(NP, q0 + slice);
   const double c = s_c, ih = s_ih, ic2 = s_ic2, tc = s_tc;
-  for (int base = 0; base < NP; base += CH) {
-    const int nq = min(CH, NP - base);
+  for (int base = q0; base < q1; base += CH) {
+    const int nq = min(CH, q1 - base);
     if (tid < 2 * CH) {
       const int side = tid / CH, ql = tid % CH, qg = base + ql;
       if (ql < nq) {
@@ -310,7 +352,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_layer_fp64(const KArgs a, const
       }
     }
     __syncthreads();
-    // Gram accumulation over the chunk
 #pragma unroll
     for (int s = 0; s < kMaxPair; ++s) {
       if (tid + s * kThreads < npair) {
@@ -324,7 +365,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_layer_fp64(const KArgs a, const
         acc[s] = t;
       }
     }
-    // right-hand sides over the chunk
 #pragma unroll
     for (int s = 0; s < kMaxPair; ++s) {
       const int id = tid + s * kThreads;
@@ -343,103 +383,92 @@ __global__ void __launch_bounds__(kThreads, 1) k_layer_fp64(const KArgs a, const
     }
     __syncthreads();
   }
+  // publish this CTA's slice
 #pragma unroll
   for (int s = 0; s < kMaxPair; ++s) {
-    if (tid + s * kThreads < npair) {
-      sA[pi[s] * nb + pj[s]] = acc[s];
-      sA[pj[s] * nb + pi[s]] = acc[s];
-    }
     const int id = tid + s * kThreads;
-    if (id < nbpair) sb[id] = accb[s];
+    if (id < npair) sPG[id] = acc[s];
+    if (id < nbpair) sPB[id] = accb[s];
   }
-  __syncthreads();
 
-  // ---------------- phase 2: Dirichlet vertical faces through v ----------------
-  const int nfac = s_nfac;
-  for (int f = 0; f < nfac; ++f) {
-    const int fid = a.vfac[a.vfac_ptr[v] + f];
-    if (tid == 0) {
-      // simplex (x_v, t_bot), (x_v, t_top), (x_w, tau_w) for the other facet vertices
-      for (int d = 0; d < DIM; ++d) {
-        s_fP[0][d] = s_xv[d];
-        s_fP[1][d] = s_xv[d];
-        s_fn[d] = a.facet_nrm[(int64_t)fid * DIM + d];
-      }
-      s_fP[0][DIM] = s_tbot;
-      s_fP[1][DIM] = s_ttop;
-      int c2 = 2;
-      for (int i = 0; i < DIM; ++i) {
-        const int w = a.facet_vert[(int64_t)fid * DIM + i];
-        if (w == v) continue;
-        for (int d = 0; d < DIM; ++d) s_fP[c2][d] = a.X[(int64_t)w * DIM + d];
-        s_fP[c2][DIM] = a.tau[w];
-        ++c2;
-      }
-      // n! * n-volume = sqrt(det(E^T E)), E = [P_i - P_0] ((n+1) x n)
-      double E[DIM + 1][DIM];
-      for (int i = 0; i < DIM; ++i)
-        for (int d = 0; d <= DIM; ++d) E[d][i] = s_fP[i + 1][d] - s_fP[0][d];
-      double G[DIM][DIM];
-      for (int i = 0; i < DIM; ++i)
-        for (int j = 0; j < DIM; ++j) {
-          double s = 0.0;
-          for (int d = 0; d <= DIM; ++d) s += E[d][i] * E[d][j];
-          G[i][j] = s;
-        }
-      const double det = small_det<DIM>(G);
-      s_fscale = sqrt(fabs(det));
-    }
+  // ---------------- phase 2: Dirichlet faces, this CTA's slice of their points ----------------
+  if (nfac > 0) {
+    for (int id = tid; id < nb * nb; id += blockDim.x) sPD[id] = 0.0;
+    const int NF = nfac * Q;
+    const int fsl = (NF + CS - 1) / CS;
+    const int f0 = min(NF, rank * fsl), f1 = min(NF, f0 + fsl);
     __syncthreads();
-    const long long goff = a.tent_gdoff[tent] + (long long)f * Q;
-    for (int base = 0; base < Q; base += CH) {
-      const int nq = min(CH, Q - base);
+    for (int base = f0; base < f1; base += CH) {
+      const int nq = min(CH, f1 - base);
       double* Pd = sR;                       // CH * nb : s_j.n + alpha v_j
       double* Vd = sR + (size_t)CH * nb;     // CH * nb : w v_i
       double* Sd = sV;                       // CH * nb : alpha v_i - s_i.n
       double* Gd = sV + (size_t)CH * nb;     // CH * nrhs : w g_D
       if (tid < nq) {
-        const int q = base + tid;
+        const int fq = base + tid, f = fq / Q, q = fq % Q;
         double xt[DIM + 1];
         for (int d = 0; d <= DIM; ++d) xt[d] = 0.0;
         for (int i = 0; i < NV; ++i) {
           const double l = __ldg(a.bary + q * NV + i);
-          for (int d = 0; d <= DIM; ++d) xt[d] = fma(l, s_fP[i][d], xt[d]);
+          for (int d = 0; d <= DIM; ++d) xt[d] = fma(l, s_fP[f][i][d], xt[d]);
         }
         double xh[DIM];
         for (int d = 0; d < DIM; ++d) xh[d] = (xt[d] - s_xv[d]) * ih;
         const double th = c * (xt[DIM] - tc) * ih;
         double* m = sM + tid * a.mono_stride;
         eval_monomials<DIM>(a, th, xh, m);
-        const double w = __ldg(a.wref + q) * s_fscale;
+        const double w = __ldg(a.wref + q) * s_fscale[f];
         for (int j = 0; j < nb; ++j) {
           const double vj = c * ih * sp_eval<DIM>(a, j, 1, m);
           double sn = 0.0;
-          for (int d = 0; d < DIM; ++d) sn = fma(-ih * sp_eval<DIM>(a, j, 2 + d, m), s_fn[d], sn);
+          for (int d = 0; d < DIM; ++d) sn = fma(-ih * sp_eval<DIM>(a, j, 2 + d, m), s_fn[f][d], sn);
           Pd[tid * nb + j] = sn + a.alpha * vj;
           Vd[tid * nb + j] = w * vj;
           Sd[tid * nb + j] = a.alpha * vj - sn;
         }
+        const long long goff = a.tent_gdoff[tent] + fq;
         for (int r = 0; r < nrhs; ++r)
-          Gd[tid * nrhs + r] = (a.gD != nullptr) ? w * a.gD[(long long)r * a.n_bnd + goff + q] : 0.0;
+          Gd[tid * nrhs + r] = (a.gD != nullptr) ? w * a.gD[(long long)r * a.n_bnd + goff] : 0.0;
       }
       __syncthreads();
       for (int id = tid; id < nb * nb; id += blockDim.x) {
         const int i = id / nb, j = id % nb;
-        double t = sA[id];
+        double t = sPD[id];
         for (int ql = 0; ql < nq; ++ql) t = fma(Vd[ql * nb + i], Pd[ql * nb + j], t);
-        sA[id] = t;
+        sPD[id] = t;
       }
       for (int id = tid; id < nbpair; id += blockDim.x) {
         const int r = id / nb, i = id % nb;
-        double t = sb[id];
+        double t = sPB[id];
         for (int ql = 0; ql < nq; ++ql) t = fma(Gd[ql * nrhs + r], Sd[ql * nb + i], t);
-        sb[id] = t;
+        sPB[id] = t;
       }
       __syncthreads();
     }
   }
 
-  // ---------------- phase 3: LU with partial pivoting, then solve ----------------
+  // ---------------- cluster reduction of the slices (rank order) ----------------
+  cluster.sync();
+  for (int id = tid; id < nb * nb; id += blockDim.x) {
+    const int i = id / nb, j = id % nb;
+    const int lo = min(i, j), hi = max(i, j);
+    const int pidx = lo * nb - lo * (lo - 1) / 2 + (hi - lo);
+    double t = 0.0;
+    for (int r = 0; r < CS; ++r) {
+      const double* pg = cluster.map_shared_rank(sPG, r);
+      t += pg[pidx];
+      if (nfac > 0) t += cluster.map_shared_rank(sPD, r)[id];
+    }
+    sA[id] = t;
+  }
+  for (int id = tid; id < nbpair; id += blockDim.x) {
+    double t = 0.0;
+    for (int r = 0; r < CS; ++r) t += cluster.map_shared_rank(sPB, r)[id];
+    sb[id] = t;
+  }
+  cluster.sync();   // no CTA leaves or reuses its slice while another still reads it
+
+  // ---------------- phase 3: LU with partial pivoting, then solve (every CTA) ----------------
   const int lane = tid & 31, warp = tid >> 5;
   for (int k = 0; k < nb; ++k) {
     if (warp == 0) {
@@ -479,7 +508,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_layer_fp64(const KArgs a, const
     __syncthreads();
     double piv = sA[k * nb + k];
     if (!(fabs(piv) > 0.0) || !isfinite(piv)) {
-      if (tid == 0) flag_error(a, TP_ERR_SINGULAR, tent);
+      if (tid == 0 && rank == 0) flag_error(a, TP_ERR_SINGULAR, tent);
       piv = 1.0;
     }
     const double ipiv = 1.0 / piv;
@@ -508,10 +537,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_layer_fp64(const KArgs a, const
     __syncthreads();
   }
 
-  // ---------------- phase 4: outflow at the top points ----------------
-  for (int base = 0; base < NP; base += 2 * CH) {
+  // ---------------- phase 4: outflow at this CTA's top points ----------------
+  for (int base = q0; base < q1; base += 2 * CH) {
     const int ql = tid, qg = base + ql;
-    if (ql < 2 * CH && qg < NP) {
+    if (ql < 2 * CH && qg < q1) {
       const int k = qg / Q, q = qg % Q;
       double x[DIM], tt = 0.0;
       for (int d = 0; d < DIM; ++d) x[d] = 0.0;
@@ -558,7 +587,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_layer_fp64(const KArgs a, const
       }
     }
   }
-  if (tid == 0) a.tau[v] = s_ttop;
+  if (tid == 0 && rank == 0) a.tau[v] = s_ttop;
 }
 
 // energy flux through the front, per (rhs, element) partial sums
@@ -646,6 +675,7 @@ struct tp_ctx {
   long long* d_info = nullptr;
   cudaStream_t cap_stream = nullptr;
   cudaStream_t last_stream = nullptr;
+  int n_sm = 152, max_cs = 1;
   std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
   int device = 0;
 };
@@ -660,6 +690,7 @@ int ctx_upload(tp_ctx* ctx, T** d, const std::vector<T>& h) {
 }
 
 constexpr size_t kMaxDynSmem = 200 * 1024;   // cap of the shared-memory plan
+constexpr size_t kTwoPerSmSmem = 95 * 1024;  // plan that leaves room for two CTAs per SM
 
 // the attribute is set to the plan's cap, so contexts of any size can share the kernel
 template <int DIM>
@@ -669,15 +700,43 @@ int set_smem_attr() {
   return TP_OK;
 }
 
+template <int DIM>
+cudaError_t launch_cluster(tp_ctx* ctx, int nt, int cs, int t0, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(nt * cs));
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = ctx->smem_bytes;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_layer_fp64<DIM>, ctx->args, t0);
+}
+
+// cluster size for a level of nt tents: a power of two <= max_cs with
+// nt * cs <= 2 CTAs per SM
+int level_cluster_size(const tp_ctx* ctx, int64_t nt) {
+  int cs = 1;
+  while (cs * 2 <= ctx->max_cs && nt * cs * 2 <= 2LL * ctx->n_sm) cs *= 2;
+  return cs;
+}
+
 int launch_level(tp_ctx* ctx, int32_t L, cudaStream_t st) {
   const int64_t t0 = ctx->level_ptr[L - 1], t1 = ctx->level_ptr[L];
   if (t1 <= t0) return TP_OK;
-  const dim3 grid((unsigned)(t1 - t0)), block(kThreads);
+  const int nt = (int)(t1 - t0);
+  const int cs = level_cluster_size(ctx, nt);
+  cudaError_t e;
   switch (ctx->dim) {
-    case 1: k_layer_fp64<1><<<grid, block, ctx->smem_bytes, st>>>(ctx->args, (int)t0); break;
-    case 2: k_layer_fp64<2><<<grid, block, ctx->smem_bytes, st>>>(ctx->args, (int)t0); break;
-    default: k_layer_fp64<3><<<grid, block, ctx->smem_bytes, st>>>(ctx->args, (int)t0); break;
+    case 1: e = launch_cluster<1>(ctx, nt, cs, (int)t0, st); break;
+    case 2: e = launch_cluster<2>(ctx, nt, cs, (int)t0, st); break;
+    default: e = launch_cluster<3>(ctx, nt, cs, (int)t0, st); break;
   }
+  TP_CUDA_OK(e);
   TP_CUDA_OK(cudaGetLastError());
   return TP_OK;
 }
@@ -724,6 +783,10 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
   // patch checks: size limit and single material per tent
   for (int64_t v = 0; v < T.nv; ++v) {
     const int p0 = T.star_ptr[v], p1 = T.star_ptr[v + 1];
+    if (T.vfac_ptr[v + 1] - T.vfac_ptr[v] > tp::kMaxFacets) {
+      tp::set_error("tp_create: vertex " + std::to_string(v) + " lies on more than 16 boundary facets");
+      return fail(TP_ERR_UNSUPPORTED);
+    }
     if (p1 - p0 > tp::kMaxPatch) {
       tp::set_error("tp_create: vertex " + std::to_string(v) + " has more than 64 elements");
       return fail(TP_ERR_UNSUPPORTED);
@@ -875,12 +938,18 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
     return fail(TP_ERR_UNSUPPORTED);
   }
   a.mono_stride = ctx->nmono | 1;
-  int CH = 64;
-  size_t bytes = 0;
-  for (; CH >= 8; CH /= 2) {
+  // shared-memory plan: the largest chunk of points that keeps two CTAs per SM,
+  // else the largest that fits one
+  auto plan = [&](int CH) {
     size_t off = (size_t)nb * nb;
     a.off_b = (int)off;
     off += (size_t)ctx->nrhs * nb;
+    a.off_pg = (int)off;
+    off += (size_t)npair;
+    a.off_pb = (int)off;
+    off += (size_t)ctx->nrhs * nb;
+    a.off_pd = (int)off;
+    off += (size_t)nb * nb;
     a.off_rows = (int)off;
     off += (size_t)CH * RT * nb;
     a.off_bvs = (int)off;
@@ -889,16 +958,23 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
     off += (size_t)CH * ctx->nrhs * C;
     a.off_mono = (int)off;
     off += (size_t)2 * CH * a.mono_stride;
-    bytes = off * sizeof(double);
-    // the Dirichlet phase reuses the rows/bvs regions
-    const size_t need_d = (size_t)CH * (3 * nb + ctx->nrhs);
-    const size_t have_d = (size_t)CH * (RT + n + 1) * nb;
-    if (bytes <= kMaxDynSmem && need_d <= have_d) break;
+    return off * sizeof(double);
+  };
+  int CH = 0;
+  size_t bytes = 0;
+  for (size_t cap : {kTwoPerSmSmem, kMaxDynSmem}) {
+    for (int ch = 64; ch >= 8 && CH == 0; ch /= 2) {
+      const size_t need_d = (size_t)ch * (3 * nb + ctx->nrhs);
+      const size_t have_d = (size_t)ch * (RT + n + 1) * nb;
+      if (plan(ch) <= cap && need_d <= have_d) CH = ch;
+    }
+    if (CH) break;
   }
-  if (CH < 8) {
+  if (CH == 0) {
     tp::set_error("tp_create: shared-memory plan does not fit (nb/nrhs too large)");
     return fail(TP_ERR_UNSUPPORTED);
   }
+  bytes = plan(CH);
   a.CH = CH;
   ctx->smem_bytes = bytes;
   switch (n) {
@@ -907,6 +983,15 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
     default: rc = set_smem_attr<3>(); break;
   }
   if (rc) return fail(rc);
+  {
+    int nsm = 0;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device) == cudaSuccess && nsm > 0)
+      ctx->n_sm = nsm;
+    const double avg_pts = (double)T.star_el.size() / (double)T.nv * Q;
+    int cs = 1;
+    while (cs < 8 && avg_pts / (2.0 * cs) >= CH) cs *= 2;
+    ctx->max_cs = cs;
+  }
   if (cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
     tp::set_error("tp_create: stream creation failed");
     return fail(TP_ERR_CUDA);

@@ -15,6 +15,7 @@ void set_error(const std::string& msg);
 constexpr int kMaxDim = 3;
 constexpr int kMaxP = 8;
 constexpr int kMaxPatch = 64;     // elements in one vertex star handled by one CTA
+constexpr int kMaxFacets = 16;    // boundary facets through one vertex
 
 // ---------------------------------------------------------------------------
 // mesh topology built on the host
