@@ -46,30 +46,30 @@ def _dist():
 
 def algorithmic_flops(solver, tents_export, mesh) -> float:
     """FP64 flops (2 per FMA) of one sweep, counted from the method's operations
-    per tent:  basis evaluation at the 2 x P x Q top/bottom points and again at
-    the top points for the outflow (nnz of the sparse coefficient tables +
-    monomials); symmetric Gram over (n+2) rows per point; RHS (n+2) x nb per
-    point; LU nb^3/3 and the two triangular solves; outflow (n+2) x nb per
-    point; Dirichlet faces Q x (nb^2 + 3 nb) per boundary facet."""
-    import paper_1907_02367_gb300 as pkg
+    per tent (patch of P elements, Q front points each, nb = dim U^p):
+      * basis at the P*Q bottom and P*Q top points, and again at the top points
+        for the outflow: monomial chain (nmono - 1) + U-values (nnz of the U
+        coefficient table); first derivatives from U-values ((n+1) nb products);
+      * symmetric Gram of (n+2) rows per point: (n+2) nb (nb+1)/2;
+      * right-hand sides (n+2) nb nrhs per point; outflow (n+2) nb nrhs per point;
+      * LU nb^3/3 and the triangular solves nb^2 nrhs;
+      * Dirichlet faces: basis + nb^2 + 3 nb per face point."""
     n, nb, Q, nrhs = solver.dim, solver.basis.nb, solver.Q, solver.nrhs
     C = n + 2
     exps, coef = solver.basis.export()
     nnz_U = int(np.count_nonzero(coef))
-    # derivative tables have at most nnz_U entries each
-    nnz_all = nnz_U * C
     nmono = solver.basis.nmono
+    basis = (nmono - 1) + nnz_U
+    deriv = (n + 1) * nb
     star = np.bincount(mesh.elems.reshape(-1), minlength=mesh.n_vert)
     P = star[tents_export["vert"]].astype(np.float64)
     pts = P * Q
-    per_point = (2 * (nmono - 1) + (nnz_all - nnz_U) + nnz_all      # assembly basis (top w/o U, bottom)
-                 + C * nb * (nb + 1) / 2                              # Gram, symmetric
-                 + C * nb * nrhs                                      # RHS
-                 + (nmono - 1) + nnz_all + C * nb * nrhs)             # outflow
+    per_point = (2 * (basis + deriv)                       # assembly: bottom + top
+                 + C * nb * (nb + 1) / 2                    # Gram, symmetric
+                 + C * nb * nrhs                            # RHS
+                 + basis + C * nb * nrhs)                   # outflow
     fma = pts * per_point + nb ** 3 / 3.0 + nb * nb * nrhs
-    # Dirichlet faces
-    bnd = solver.n_bnd
-    fma_sum = float(fma.sum()) + bnd * (nb * nb + 3 * nb + nnz_all)
+    fma_sum = float(fma.sum()) + solver.n_bnd * (basis + deriv + nb * nb + 3 * nb)
     return 2.0 * fma_sum
 
 

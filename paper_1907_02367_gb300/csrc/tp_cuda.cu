@@ -47,7 +47,7 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kMaxPair = 8;      // accumulator slots per thread in the Gram phase
-constexpr int kRhsReg = 4;       // right-hand sides per outflow pass
+constexpr int kMaxCH = 64;       // points per chunk (upper bound of the plan)
 
 struct KArgs {
   int nb, nmono, Q, nrhs, CH, mono_stride;
@@ -80,7 +80,13 @@ struct KArgs {
   int* status;
   long long* status_info;
   // shared-memory carve (offsets in doubles)
-  int off_b, off_pg, off_pb, off_pd, off_rows, off_bvs, off_cb, off_mono;
+  const int* rel_ptr;
+  const int* rel_src;
+  const double* rel_fac;
+  const int* relT_ptr;
+  const int* relT_dst;
+  const double* relT_fac;
+  int off_b, off_pg, off_pb, off_pd, off_rows, off_bvs, off_cb, off_mono, off_u, off_y, off_rd;
 };
 
 __device__ __forceinline__ void flag_error(const KArgs& a, int code, long long info) {
@@ -154,12 +160,32 @@ __device__ __forceinline__ double small_det(const double (&G)[DIM][DIM]) {
   }
 }
 
+// U-values u_k = b_k(xhat, that) of every basis function at one point
+template <int DIM>
+__device__ __forceinline__ void eval_uvalues(const KArgs& a, double th, const double* xh, double* m,
+                                             double* u) {
+  eval_monomials<DIM>(a, th, xh, m);
+  for (int k = 0; k < a.nb; ++k) u[k] = sp_eval<DIM>(a, k, 0, m);
+}
+
+// d/d(var) b_j from the U-values of the same point (exact relations inside U^p)
+template <int DIM>
+__device__ __forceinline__ double rel_eval(const KArgs& a, int j, int var, const double* u) {
+  const int e0 = __ldg(a.rel_ptr + j * (DIM + 1) + var), e1 = __ldg(a.rel_ptr + j * (DIM + 1) + var + 1);
+  double s = 0.0;
+  for (int e = e0; e < e1; ++e) s = fma(__ldg(a.rel_fac + e), u[__ldg(a.rel_src + e)], s);
+  return s;
+}
+
 // One tent per thread-block cluster of CS CTAs (CS = gridDim.x / tents in the
 // launch, 1..8).  Every CTA rebuilds the patch geometry, assembles the Gram,
 // right-hand sides and Dirichlet terms of its slice of the patch's points, and
 // publishes them in its shared memory; after a cluster barrier every CTA sums
 // all slices through distributed shared memory in rank order (so all CTAs hold
 // the same A and b), factorises redundantly and writes the outflow of its slice.
+// Basis values: only U is evaluated from the monomial tables; the derivatives
+// are exact combinations of U-values (d/dx_m b_{beta,type} = beta_m b_{beta-e_m,type},
+// d/dt b_{beta,1} = b_{beta,0}, d/dt b_{beta,0} = sum_m beta_m(beta_m-1) b_{beta-2e_m,1}).
 template <int DIM>
 __global__ void __launch_bounds__(kThreads, 2) k_layer_fp64(const KArgs a, const int tent0) {
   constexpr int NV = DIM + 1;   // vertices per element
@@ -174,19 +200,21 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer_fp64(const KArgs a, const
   __shared__ double s_tb[tp::kMaxPatch][NV], s_tt[tp::kMaxPatch][NV];
   __shared__ double s_gb[tp::kMaxPatch][DIM], s_gt[tp::kMaxPatch][DIM];
   __shared__ double s_sdet[tp::kMaxPatch], s_st[tp::kMaxPatch];
-  __shared__ int s_piv;
   __shared__ double s_fP[tp::kMaxFacets][NV][DIM + 1];   // Dirichlet face simplices (x, t)
   __shared__ double s_fscale[tp::kMaxFacets], s_fn[tp::kMaxFacets][DIM];
+  __shared__ double s_psw[2 * kMaxCH], s_pzs[2 * kMaxCH];   // per (side, point): sqrt(w), top scale
+  __shared__ int s_pk[2 * kMaxCH];                          // per (side, point): patch element
+  __shared__ int s_piv;
 
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
   const int CS = (int)cluster.num_blocks();
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int tent = tent0 + blockIdx.x / CS;
   const int nb = a.nb, Q = a.Q, nrhs = a.nrhs, CH = a.CH;
   const int npair = nb * (nb + 1) / 2;
   const int nbpair = nrhs * nb;
-  double* sA = sm;                    // nb * nb   : assembled matrix, then LU
+  double* sA = sm;                    // nb * nb   : assembled matrix, then LU factors
   double* sb = sm + a.off_b;          // nrhs * nb : assembled rhs, then x
   double* sPG = sm + a.off_pg;        // npair     : this CTA's Gram slice (upper triangle)
   double* sPB = sm + a.off_pb;        // nrhs * nb : this CTA's rhs slice
@@ -195,6 +223,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer_fp64(const KArgs a, const
   double* sV = sm + a.off_bvs;        // CH * (DIM+1) * nb : bottom (v, sigma) scaled by sqrt(w)
   double* sCB = sm + a.off_cb;        // CH * nrhs * C    : bottom data coefficients
   double* sM = sm + a.off_mono;       // 2*CH * mono_stride
+  double* sU = sm + a.off_u;          // 2*CH * nb        : U-values per (side, point)
+  double* sY = sm + a.off_y;          // nrhs * C * nb    : outflow coefficient vectors
+  double* sRD = sm + a.off_rd;        // nb               : reciprocal pivots
 
   // ---------------- phase 0: tent and patch geometry ----------------
   if (tid == 0) {
@@ -301,6 +332,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer_fp64(const KArgs a, const
   const double c = s_c, ih = s_ih, ic2 = s_ic2, tc = s_tc;
   for (int base = q0; base < q1; base += CH) {
     const int nq = min(CH, q1 - base);
+    // (a) one thread per (side, point): U-values, per-point scalars, bottom data
     if (tid < 2 * CH) {
       const int side = tid / CH, ql = tid % CH, qg = base + ql;
       if (ql < nq) {
@@ -315,28 +347,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer_fp64(const KArgs a, const
         double xh[DIM];
         for (int d = 0; d < DIM; ++d) xh[d] = (x[d] - s_xv[d]) * ih;
         const double th = c * (tt - tc) * ih;
-        double* m = sM + tid * a.mono_stride;
-        eval_monomials<DIM>(a, th, xh, m);
+        eval_uvalues<DIM>(a, th, xh, sM + tid * a.mono_stride, sU + (size_t)tid * nb);
         const double sw = __ldg(a.sqw + q) * s_sdet[k];
-        if (side == 0) {
-          const double zs = sw * s_st[k];
-          double* R = sR + (size_t)ql * RT * nb;
-          for (int j = 0; j < nb; ++j) {
-            const double vj = c * ih * sp_eval<DIM>(a, j, 1, m);
-            R[j] = zs * vj;
-            for (int d = 0; d < DIM; ++d) {
-              const double sj = -ih * sp_eval<DIM>(a, j, 2 + d, m);
-              R[(1 + d) * nb + j] = sw * (sj - vj * s_gt[k][d]);
-            }
-          }
-        } else {
-          double* R = sR + (size_t)ql * RT * nb + (RT - 1) * nb;
-          double* V = sV + (size_t)ql * (DIM + 1) * nb;
-          for (int j = 0; j < nb; ++j) {
-            R[j] = sw * sp_eval<DIM>(a, j, 0, m);
-            V[j] = sw * c * ih * sp_eval<DIM>(a, j, 1, m);
-            for (int d = 0; d < DIM; ++d) V[(1 + d) * nb + j] = -sw * ih * sp_eval<DIM>(a, j, 2 + d, m);
-          }
+        s_psw[tid] = sw;
+        s_pzs[tid] = sw * s_st[k];
+        s_pk[tid] = k;
+        if (side == 1) {
           const int el = s_el[k];
           for (int r = 0; r < nrhs; ++r) {
             const double* f = a.front + (((int64_t)r * a.ne + el) * Q + q) * C;
@@ -352,6 +368,30 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer_fp64(const KArgs a, const
       }
     }
     __syncthreads();
+    // (b) all threads: derivatives and Gram rows per (side, point, basis function)
+    for (int id = tid; id < 2 * CH * nb; id += blockDim.x) {
+      const int sp = id / nb, j = id % nb, side = sp / CH, ql = sp % CH;
+      if (ql >= nq) continue;
+      const double* u = sU + (size_t)sp * nb;
+      const double sw = s_psw[sp];
+      const int k = s_pk[sp];
+      const double vj = c * ih * rel_eval<DIM>(a, j, 0, u);
+      if (side == 0) {
+        double* R = sR + (size_t)ql * RT * nb;
+        R[j] = s_pzs[sp] * vj;
+        for (int d = 0; d < DIM; ++d) {
+          const double sj = -ih * rel_eval<DIM>(a, j, 1 + d, u);
+          R[(1 + d) * nb + j] = sw * (sj - vj * s_gt[k][d]);
+        }
+      } else {
+        sR[(size_t)ql * RT * nb + (RT - 1) * nb + j] = sw * u[j];
+        double* V = sV + (size_t)ql * (DIM + 1) * nb;
+        V[j] = sw * vj;
+        for (int d = 0; d < DIM; ++d) V[(1 + d) * nb + j] = -sw * ih * rel_eval<DIM>(a, j, 1 + d, u);
+      }
+    }
+    __syncthreads();
+    // (c) Gram and right-hand sides over the chunk
 #pragma unroll
     for (int s = 0; s < kMaxPair; ++s) {
       if (tid + s * kThreads < npair) {
@@ -415,13 +455,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer_fp64(const KArgs a, const
         double xh[DIM];
         for (int d = 0; d < DIM; ++d) xh[d] = (xt[d] - s_xv[d]) * ih;
         const double th = c * (xt[DIM] - tc) * ih;
-        double* m = sM + tid * a.mono_stride;
-        eval_monomials<DIM>(a, th, xh, m);
+        double* u = sU + (size_t)tid * nb;
+        eval_uvalues<DIM>(a, th, xh, sM + tid * a.mono_stride, u);
         const double w = __ldg(a.wref + q) * s_fscale[f];
         for (int j = 0; j < nb; ++j) {
-          const double vj = c * ih * sp_eval<DIM>(a, j, 1, m);
+          const double vj = c * ih * rel_eval<DIM>(a, j, 0, u);
           double sn = 0.0;
-          for (int d = 0; d < DIM; ++d) sn = fma(-ih * sp_eval<DIM>(a, j, 2 + d, m), s_fn[f][d], sn);
+          for (int d = 0; d < DIM; ++d) sn = fma(-ih * rel_eval<DIM>(a, j, 1 + d, u), s_fn[f][d], sn);
           Pd[tid * nb + j] = sn + a.alpha * vj;
           Vd[tid * nb + j] = w * vj;
           Sd[tid * nb + j] = a.alpha * vj - sn;
@@ -455,8 +495,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer_fp64(const KArgs a, const
     const int pidx = lo * nb - lo * (lo - 1) / 2 + (hi - lo);
     double t = 0.0;
     for (int r = 0; r < CS; ++r) {
-      const double* pg = cluster.map_shared_rank(sPG, r);
-      t += pg[pidx];
+      t += cluster.map_shared_rank(sPG, r)[pidx];
       if (nfac > 0) t += cluster.map_shared_rank(sPD, r)[id];
     }
     sA[id] = t;
@@ -468,76 +507,92 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer_fp64(const KArgs a, const
   }
   cluster.sync();   // no CTA leaves or reuses its slice while another still reads it
 
-  // ---------------- phase 3: LU with partial pivoting, then solve (every CTA) ----------------
-  const int lane = tid & 31, warp = tid >> 5;
-  for (int k = 0; k < nb; ++k) {
-    if (warp == 0) {
-      double best = -1.0;
-      int bi = k;
-      for (int i = k + lane; i < nb; i += 32) {
-        const double val = fabs(sA[i * nb + k]);
-        if (val > best) {
-          best = val;
-          bi = i;
+  // ---------------- phase 3: factorisation and solve (warp 0 of every CTA) ----------------
+  // Interior tents (no Dirichlet face) have a symmetric positive definite A
+  // (space-like faces), so they are eliminated without pivoting; tents with
+  // Dirichlet faces use partial pivoting.  Right-hand sides are eliminated
+  // alongside; reciprocal pivots are kept for the back substitution.
+  if (warp == 0) {
+    const bool pivoting = (nfac > 0);
+    for (int k = 0; k < nb; ++k) {
+      if (pivoting) {
+        // |a_ik| compared through the bit patterns (non-negative doubles order as integers)
+        unsigned long long best = 0ull;
+        int bi = k;
+        for (int i = k + lane; i < nb; i += 32) {
+          const unsigned long long bits = (unsigned long long)__double_as_longlong(fabs(sA[i * nb + k]));
+          if (bits > best || (bits == best && i < bi)) {
+            best = bits;
+            bi = i;
+          }
         }
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        const double ob = __shfl_down_sync(0xffffffffu, best, o);
-        const int oi = __shfl_down_sync(0xffffffffu, bi, o);
-        if (ob > best || (ob == best && oi < bi)) {
-          best = ob;
-          bi = oi;
+        for (int o = 16; o > 0; o >>= 1) {
+          const unsigned long long ob = __shfl_down_sync(0xffffffffu, best, o);
+          const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+          if (ob > best || (ob == best && oi < bi)) {
+            best = ob;
+            bi = oi;
+          }
         }
+        const int pr = __shfl_sync(0xffffffffu, bi, 0);
+        if (pr != k) {
+          for (int j = lane; j < nb; j += 32) {
+            const double t = sA[k * nb + j];
+            sA[k * nb + j] = sA[pr * nb + j];
+            sA[pr * nb + j] = t;
+          }
+          for (int r = lane; r < nrhs; r += 32) {
+            const double t = sb[r * nb + k];
+            sb[r * nb + k] = sb[r * nb + pr];
+            sb[r * nb + pr] = t;
+          }
+        }
+        __syncwarp();
       }
-      if (lane == 0) s_piv = bi;
-    }
-    __syncthreads();
-    const int pr = s_piv;
-    if (pr != k) {
-      for (int j = tid; j < nb; j += blockDim.x) {
-        const double t = sA[k * nb + j];
-        sA[k * nb + j] = sA[pr * nb + j];
-        sA[pr * nb + j] = t;
+      double piv = sA[k * nb + k];
+      if (!(fabs(piv) > 0.0) || !isfinite(piv)) {
+        if (lane == 0 && rank == 0) flag_error(a, TP_ERR_SINGULAR, tent);
+        piv = 1.0;
       }
-      for (int r = tid; r < nrhs; r += blockDim.x) {
-        const double t = sb[r * nb + k];
-        sb[r * nb + k] = sb[r * nb + pr];
-        sb[r * nb + pr] = t;
+      const double rp = 1.0 / piv;
+      if (lane == 0) sRD[k] = rp;
+      for (int i = k + 1 + lane; i < nb; i += 32) {
+        const double l = sA[i * nb + k] * rp;
+        sA[i * nb + k] = l;
+        for (int j = k + 1; j < nb; ++j) sA[i * nb + j] = fma(-l, sA[k * nb + j], sA[i * nb + j]);
+        for (int r = 0; r < nrhs; ++r) sb[r * nb + i] = fma(-l, sb[r * nb + k], sb[r * nb + i]);
       }
+      __syncwarp();
     }
-    __syncthreads();
-    double piv = sA[k * nb + k];
-    if (!(fabs(piv) > 0.0) || !isfinite(piv)) {
-      if (tid == 0 && rank == 0) flag_error(a, TP_ERR_SINGULAR, tent);
-      piv = 1.0;
+    for (int k = nb - 1; k >= 0; --k) {
+      for (int r = lane; r < nrhs; r += 32) sb[r * nb + k] *= sRD[k];
+      __syncwarp();
+      for (int id = lane; id < k * nrhs; id += 32) {
+        const int r = id / k, i = id % k;
+        sb[r * nb + i] = fma(-sA[i * nb + k], sb[r * nb + k], sb[r * nb + i]);
+      }
+      __syncwarp();
     }
-    const double ipiv = 1.0 / piv;
-    for (int i = k + 1 + tid; i < nb; i += blockDim.x) sA[i * nb + k] *= ipiv;
-    __syncthreads();
-    const int rem = nb - k - 1;
-    for (int id = tid; id < rem * rem; id += blockDim.x) {
-      const int i = k + 1 + id / rem, j = k + 1 + id % rem;
-      sA[i * nb + j] = fma(-sA[i * nb + k], sA[k * nb + j], sA[i * nb + j]);
-    }
-    for (int id = tid; id < rem * nrhs; id += blockDim.x) {
-      const int r = id / rem, i = k + 1 + id % rem;
-      sb[r * nb + i] = fma(-sA[i * nb + k], sb[r * nb + k], sb[r * nb + i]);
-    }
-    __syncthreads();
   }
-  for (int k = nb - 1; k >= 0; --k) {
-    double d = sA[k * nb + k];
-    if (!(fabs(d) > 0.0) || !isfinite(d)) d = 1.0;
-    for (int r = tid; r < nrhs; r += blockDim.x) sb[r * nb + k] /= d;
-    __syncthreads();
-    for (int id = tid; id < k * nrhs; id += blockDim.x) {
-      const int r = id / k, i = id % k;
-      sb[r * nb + i] = fma(-sA[i * nb + k], sb[r * nb + k], sb[r * nb + i]);
-    }
-    __syncthreads();
-  }
+  __syncthreads();
 
   // ---------------- phase 4: outflow at this CTA's top points ----------------
+  // coefficient vectors of U_h, dU_h/dthat, dU_h/dxhat_m in the basis: y = D^T x
+  for (int id = tid; id < nrhs * C * nb; id += blockDim.x) {
+    const int r = id / (C * nb), rem = id % (C * nb), cc = rem / nb, kk = rem % nb;
+    double t;
+    if (cc == 0) {
+      t = sb[r * nb + kk];
+    } else {
+      const int e0 = __ldg(a.relT_ptr + kk * (DIM + 1) + cc - 1);
+      const int e1 = __ldg(a.relT_ptr + kk * (DIM + 1) + cc);
+      t = 0.0;
+      for (int e = e0; e < e1; ++e) t = fma(__ldg(a.relT_fac + e), sb[r * nb + __ldg(a.relT_dst + e)], t);
+      t *= (cc == 1) ? c * ih : -ih;
+    }
+    sY[id] = t;
+  }
+  __syncthreads();
   for (int base = q0; base < q1; base += 2 * CH) {
     const int ql = tid, qg = base + ql;
     if (ql < 2 * CH && qg < q1) {
@@ -552,38 +607,22 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer_fp64(const KArgs a, const
       double xh[DIM];
       for (int d = 0; d < DIM; ++d) xh[d] = (x[d] - s_xv[d]) * ih;
       const double th = c * (tt - tc) * ih;
-      double* m = sM + tid * a.mono_stride;
-      eval_monomials<DIM>(a, th, xh, m);
+      double* u = sU + (size_t)tid * nb;
+      eval_uvalues<DIM>(a, th, xh, sM + tid * a.mono_stride, u);
       const int el = s_el[k];
-      for (int r0 = 0; r0 < nrhs; r0 += kRhsReg) {
-        double o[kRhsReg][C];
+      for (int r = 0; r < nrhs; ++r) {
+        double o[C];
 #pragma unroll
-        for (int r = 0; r < kRhsReg; ++r)
-#pragma unroll
-          for (int cc = 0; cc < C; ++cc) o[r][cc] = 0.0;
+        for (int cc = 0; cc < C; ++cc) o[cc] = 0.0;
+        const double* y = sY + (size_t)r * C * nb;
         for (int j = 0; j < nb; ++j) {
-          double bv[C];
+          const double uj = u[j];
 #pragma unroll
-          for (int cc = 0; cc < C; ++cc) bv[cc] = sp_eval<DIM>(a, j, cc, m);
-#pragma unroll
-          for (int r = 0; r < kRhsReg; ++r) {
-            if (r0 + r < nrhs) {
-              const double xj = sb[(r0 + r) * nb + j];
-#pragma unroll
-              for (int cc = 0; cc < C; ++cc) o[r][cc] = fma(xj, bv[cc], o[r][cc]);
-            }
-          }
+          for (int cc = 0; cc < C; ++cc) o[cc] = fma(y[cc * nb + j], uj, o[cc]);
         }
+        double* f = a.front + (((int64_t)r * a.ne + el) * Q + q) * C;
 #pragma unroll
-        for (int r = 0; r < kRhsReg; ++r) {
-          if (r0 + r < nrhs) {
-            double* f = a.front + (((int64_t)(r0 + r) * a.ne + el) * Q + q) * C;
-            f[0] = o[r][0];
-            f[1] = c * ih * o[r][1];
-#pragma unroll
-            for (int d = 0; d < DIM; ++d) f[2 + d] = -ih * o[r][2 + d];
-          }
-        }
+        for (int cc = 0; cc < C; ++cc) f[cc] = o[cc];
       }
     }
   }
@@ -858,7 +897,8 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
   int rc = TP_OK;
   KArgs& a = ctx->args;
   double *dX, *dc, *dnrm, *dbary, *dw, *dsqw, *dttop, *dh, *dspc;
-  int *del, *dsp, *dse, *dvp, *dvf, *dfv, *dtv, *dspp, *dspm, *dpar, *dvar;
+  int *del, *dsp, *dse, *dvp, *dvf, *dfv, *dtv, *dspp, *dspm, *dpar, *dvar, *drp, *drs, *dtp, *dtd;
+  double *drf, *dtf;
   long long* dgo;
   std::vector<double> sqw(Q);
   for (int q = 0; q < Q; ++q) sqw[q] = std::sqrt(ctx->rule.w[q]);
@@ -874,7 +914,10 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
       (rc = ctx_upload(ctx, &dh, tent_h)) || (rc = ctx_upload(ctx, &dgo, gdoff)) ||
       (rc = ctx_upload(ctx, &dspp, basis->sp_ptr)) || (rc = ctx_upload(ctx, &dspm, basis->sp_mono)) ||
       (rc = ctx_upload(ctx, &dspc, basis->sp_coef)) || (rc = ctx_upload(ctx, &dpar, basis->parent)) ||
-      (rc = ctx_upload(ctx, &dvar, basis->var)))
+      (rc = ctx_upload(ctx, &dvar, basis->var)) || (rc = ctx_upload(ctx, &drp, basis->rel_ptr)) ||
+      (rc = ctx_upload(ctx, &drs, basis->rel_src)) || (rc = ctx_upload(ctx, &drf, basis->rel_fac)) ||
+      (rc = ctx_upload(ctx, &dtp, basis->relT_ptr)) || (rc = ctx_upload(ctx, &dtd, basis->relT_dst)) ||
+      (rc = ctx_upload(ctx, &dtf, basis->relT_fac)))
     return fail(rc == TP_ERR_CUDA ? TP_ERR_OOM : rc);
   const size_t nfront = (size_t)ctx->nrhs * T.ne * Q * ctx->C;
   if (cudaMalloc(&ctx->d_front, nfront * sizeof(double)) != cudaSuccess ||
@@ -925,6 +968,12 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
   a.sp_coef = dspc;
   a.mono_parent = dpar;
   a.mono_var = dvar;
+  a.rel_ptr = drp;
+  a.rel_src = drs;
+  a.rel_fac = drf;
+  a.relT_ptr = dtp;
+  a.relT_dst = dtd;
+  a.relT_fac = dtf;
   a.tau = ctx->d_tau;
   a.front = ctx->d_front;
   a.gD = nullptr;
@@ -958,6 +1007,12 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
     off += (size_t)CH * ctx->nrhs * C;
     a.off_mono = (int)off;
     off += (size_t)2 * CH * a.mono_stride;
+    a.off_u = (int)off;
+    off += (size_t)2 * CH * nb;
+    a.off_y = (int)off;
+    off += (size_t)ctx->nrhs * C * nb;
+    a.off_rd = (int)off;
+    off += (size_t)nb;
     return off * sizeof(double);
   };
   int CH = 0;

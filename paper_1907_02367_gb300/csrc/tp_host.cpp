@@ -340,6 +340,8 @@ extern "C" int tp_build_basis(int32_t dim, int32_t p, tp_basis** out) {
     long long num, den;
   };
   std::vector<std::vector<Term>> funcs;
+  std::vector<int> ftype;
+  std::vector<Exps> fbeta;
   for (int type = 0; type <= 1; ++type) {
     for (int deg = 0; deg <= p - type; ++deg) {
       std::vector<Exps> betas;
@@ -369,10 +371,59 @@ extern "C" int tp_build_basis(int32_t dim, int32_t p, tp_basis** out) {
           term.swap(lap);
         }
         funcs.push_back(f);
+        ftype.push_back(type);
+        fbeta.push_back(beta);
       }
     }
   }
   B->nb = (int)funcs.size();
+  // derivative relations (exact identities of the closed form, no rounding):
+  //   d/dx_m b_{beta,type} = beta_m b_{beta-e_m,type}
+  //   d/dt   b_{beta,1}    = b_{beta,0}
+  //   d/dt   b_{beta,0}    = sum_m beta_m (beta_m - 1) b_{beta-2e_m,1}
+  {
+    std::map<std::pair<int, Exps>, int> fidx;
+    for (int j = 0; j < B->nb; ++j) fidx[{ftype[j], fbeta[j]}] = j;
+    const int NVAR = n + 1;
+    std::vector<std::vector<std::pair<int, double>>> rel((size_t)B->nb * NVAR);
+    for (int j = 0; j < B->nb; ++j) {
+      const Exps& be = fbeta[j];
+      if (ftype[j] == 1) {
+        rel[(size_t)j * NVAR].push_back({fidx.at({0, be}), 1.0});
+      } else {
+        for (int mm = 1; mm <= n; ++mm)
+          if (be[mm] >= 2) {
+            Exps e = be;
+            e[mm] -= 2;
+            rel[(size_t)j * NVAR].push_back({fidx.at({1, e}), (double)(be[mm] * (be[mm] - 1))});
+          }
+      }
+      for (int mm = 1; mm <= n; ++mm)
+        if (be[mm] >= 1) {
+          Exps e = be;
+          e[mm] -= 1;
+          rel[(size_t)j * NVAR + mm].push_back({fidx.at({ftype[j], e}), (double)be[mm]});
+        }
+    }
+    B->rel_ptr.assign((size_t)B->nb * NVAR + 1, 0);
+    std::vector<std::vector<std::pair<int, double>>> relT((size_t)B->nb * NVAR);
+    for (size_t r = 0; r < rel.size(); ++r) {
+      for (auto& e : rel[r]) {
+        B->rel_src.push_back(e.first);
+        B->rel_fac.push_back(e.second);
+        relT[(size_t)e.first * NVAR + r % NVAR].push_back({(int)(r / NVAR), e.second});
+      }
+      B->rel_ptr[r + 1] = (int32_t)B->rel_src.size();
+    }
+    B->relT_ptr.assign((size_t)B->nb * NVAR + 1, 0);
+    for (size_t r = 0; r < relT.size(); ++r) {
+      for (auto& e : relT[r]) {
+        B->relT_dst.push_back(e.first);
+        B->relT_fac.push_back(e.second);
+      }
+      B->relT_ptr[r + 1] = (int32_t)B->relT_dst.size();
+    }
+  }
   B->coef.assign((size_t)B->nb * B->nmono, 0.0);
   B->sp_ptr.assign(B->nb * C + 1, 0);
   for (int j = 0; j < B->nb; ++j) {

@@ -70,4 +70,11 @@ struct tp_basis {
   // {U, d/dthat, d/dxhat_1..n}: entries [ptr[j*C+comp], ptr[j*C+comp+1])
   std::vector<int32_t> sp_ptr, sp_mono;
   std::vector<double> sp_coef;
+  // derivative relations inside U^p: d/d(var) b_j = sum fac * b_src with
+  // var in {that, xhat_1..n}; for (j, var): entries [rel_ptr[j*(n+1)+var], ...)
+  std::vector<int32_t> rel_ptr, rel_src;
+  std::vector<double> rel_fac;
+  // transposed: for (k, var): entries (j, fac) with b_k appearing in d b_j
+  std::vector<int32_t> relT_ptr, relT_dst;
+  std::vector<double> relT_fac;
 };
