@@ -46,8 +46,7 @@ namespace cg = cooperative_groups;
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kMaxPair = 8;      // accumulator slots per thread in the Gram phase
-constexpr int kMaxCH = 64;       // points per chunk (upper bound of the plan)
+constexpr int kMaxPair = 4;      // Gram pairs per thread (nb (nb+1)/2 <= 4 * 256)
 
 struct KArgs {
   int nb, nmono, Q, nrhs, CH, mono_stride;
@@ -86,7 +85,8 @@ struct KArgs {
   const int* relT_ptr;
   const int* relT_dst;
   const double* relT_fac;
-  int off_b, off_pg, off_pb, off_pd, off_rows, off_bvs, off_cb, off_mono, off_u, off_y, off_rd;
+  int off_b, off_pg, off_ph, off_pgb, off_pm, off_pd, off_pbd, off_sg, off_sm, off_f, off_del, off_u,
+      off_mono, off_cb, off_gd, off_y, off_rd;
 };
 
 __device__ __forceinline__ void flag_error(const KArgs& a, int code, long long info) {
@@ -160,37 +160,82 @@ __device__ __forceinline__ double small_det(const double (&G)[DIM][DIM]) {
   }
 }
 
-// U-values u_k = b_k(xhat, that) of every basis function at one point
-template <int DIM>
+// U-values u_k = b_k(xhat, that) of every basis function at one point (times s if SCALE)
+template <int DIM, bool SCALE = true>
 __device__ __forceinline__ void eval_uvalues(const KArgs& a, double th, const double* xh, double* m,
-                                             double* u) {
+                                             double s, double* u) {
   eval_monomials<DIM>(a, th, xh, m);
-  for (int k = 0; k < a.nb; ++k) u[k] = sp_eval<DIM>(a, k, 0, m);
+  for (int k = 0; k < a.nb; ++k) u[k] = SCALE ? s * sp_eval<DIM>(a, k, 0, m) : sp_eval<DIM>(a, k, 0, m);
 }
 
-// d/d(var) b_j from the U-values of the same point (exact relations inside U^p)
+// packed upper-triangle index of (i, j), i, j < nb
+__device__ __forceinline__ int pair_index(int i, int j, int nb) {
+  const int lo = min(i, j), hi = max(i, j);
+  return lo * nb - lo * (lo - 1) / 2 + (hi - lo);
+}
+
+// (D_va X D_vb^T)_ij for a packed symmetric X, D_var given by the relation
+// table: (D_var u)_j = sum over entries e of (j, var) of fac_e u[src_e]
 template <int DIM>
-__device__ __forceinline__ double rel_eval(const KArgs& a, int j, int var, const double* u) {
-  const int e0 = __ldg(a.rel_ptr + j * (DIM + 1) + var), e1 = __ldg(a.rel_ptr + j * (DIM + 1) + var + 1);
+__device__ __forceinline__ double congruence(const KArgs& a, int i, int va, int j, int vb, const double* X,
+                                             int nb) {
+  constexpr int NVAR = DIM + 1;
+  const int a0 = __ldg(a.rel_ptr + i * NVAR + va), a1 = __ldg(a.rel_ptr + i * NVAR + va + 1);
+  const int b0 = __ldg(a.rel_ptr + j * NVAR + vb), b1 = __ldg(a.rel_ptr + j * NVAR + vb + 1);
   double s = 0.0;
-  for (int e = e0; e < e1; ++e) s = fma(__ldg(a.rel_fac + e), u[__ldg(a.rel_src + e)], s);
+  for (int e = a0; e < a1; ++e) {
+    const int si = __ldg(a.rel_src + e);
+    double t = 0.0;
+    for (int f = b0; f < b1; ++f) t = fma(__ldg(a.rel_fac + f), X[pair_index(si, __ldg(a.rel_src + f), nb)], t);
+    s = fma(__ldg(a.rel_fac + e), t, s);
+  }
   return s;
 }
 
+// (D_var y)_i for a vector y
+template <int DIM>
+__device__ __forceinline__ double rel_apply(const KArgs& a, int i, int var, const double* y) {
+  const int e0 = __ldg(a.rel_ptr + i * (DIM + 1) + var), e1 = __ldg(a.rel_ptr + i * (DIM + 1) + var + 1);
+  double s = 0.0;
+  for (int e = e0; e < e1; ++e) s = fma(__ldg(a.rel_fac + e), y[__ldg(a.rel_src + e)], s);
+  return s;
+}
+
+// 1/x by two Newton-Raphson steps r <- r + r (1 - x r) from the binary32
+// reciprocal (quadratic convergence: 24 -> 48 -> 96 bits); falls back to the
+// division outside the binary32 range.
+__device__ __forceinline__ double recip(double x) {
+  const double ax = fabs(x);
+  if (!(ax > 1e-30 && ax < 1e30)) return 1.0 / x;
+  double r = (double)__frcp_rn((float)x);
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
+}
+
 // One tent per thread-block cluster of CS CTAs (CS = gridDim.x / tents in the
-// launch, 1..8).  Every CTA rebuilds the patch geometry, assembles the Gram,
-// right-hand sides and Dirichlet terms of its slice of the patch's points, and
-// publishes them in its shared memory; after a cluster barrier every CTA sums
-// all slices through distributed shared memory in rank order (so all CTAs hold
-// the same A and b), factorises redundantly and writes the outflow of its slice.
-// Basis values: only U is evaluated from the monomial tables; the derivatives
-// are exact combinations of U-values (d/dx_m b_{beta,type} = beta_m b_{beta-e_m,type},
-// d/dt b_{beta,1} = b_{beta,0}, d/dt b_{beta,0} = sum_m beta_m(beta_m-1) b_{beta-2e_m,1}).
+// launch, 1..8).  Each CTA takes a slice of the patch's points.
+//
+// Assembly through Grams of U-values.  With u the vector of the nb U-values
+// at a point and the exact derivative maps of U^p, v = (c/h) D_t u,
+// sigma_m = -(1/h) D_m u, the top-face form summed over the points of the
+// patch is
+//   A_top = h^-2 [ D_t G D_t^T + sum_m D_m G D_m^T + c sum_m (D_m H_m D_t^T + D_t H_m D_m^T) ],
+//   G = sum_q w u u^T,  H_m = sum_K g_{K,m} G_K  (g = top front gradient on K),
+// the recovery term is A_bot = sum_q w u_b u_b^T, the bottom data give
+//   b = gamma + (c/h) D_t alpha - (1/h) sum_m D_m beta_m
+// with moments gamma = sum w U_b u_b, alpha = sum w (c^-2 v_b - s_b.g_b) u_b,
+// beta_m = sum w (s_b,m - v_b g_b,m) u_b, and a Dirichlet facet with normal n
+// adds A_D = (c/h) D_t F E^T, b_D = E' delta, F = sum w u u^T,
+// delta = sum w g_D u, E = alpha_D (c/h) D_t - (1/h) sum_m n_m D_m,
+// E' = alpha_D (c/h) D_t + (1/h) sum_m n_m D_m.  Every CTA publishes its
+// partial Grams and moments; after a cluster barrier every CTA sums them in
+// rank order, forms A and b, factorises, and writes the outflow of its slice.
 template <int DIM>
 __global__ void __launch_bounds__(kThreads, 2) k_layer_fp64(const KArgs a, const int tent0) {
   constexpr int NV = DIM + 1;   // vertices per element
-  constexpr int C = DIM + 2;    // U, v, sigma
-  constexpr int RT = DIM + 2;   // Gram rows per point: DIM+1 top rows + recovery row
+  constexpr int C = DIM + 2;    // U, v, sigma  (and gamma, alpha, beta_m moments)
   extern __shared__ __align__(16) double sm[];
   __shared__ int s_P, s_v, s_nfac;
   __shared__ double s_ttop, s_tbot, s_tc, s_ih, s_c, s_ic2;
@@ -199,33 +244,37 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer_fp64(const KArgs a, const
   __shared__ double s_X[tp::kMaxPatch][NV][DIM];
   __shared__ double s_tb[tp::kMaxPatch][NV], s_tt[tp::kMaxPatch][NV];
   __shared__ double s_gb[tp::kMaxPatch][DIM], s_gt[tp::kMaxPatch][DIM];
-  __shared__ double s_sdet[tp::kMaxPatch], s_st[tp::kMaxPatch];
+  __shared__ double s_sdet[tp::kMaxPatch];
   __shared__ double s_fP[tp::kMaxFacets][NV][DIM + 1];   // Dirichlet face simplices (x, t)
   __shared__ double s_fscale[tp::kMaxFacets], s_fn[tp::kMaxFacets][DIM];
-  __shared__ double s_psw[2 * kMaxCH], s_pzs[2 * kMaxCH];   // per (side, point): sqrt(w), top scale
-  __shared__ int s_pk[2 * kMaxCH];                          // per (side, point): patch element
   __shared__ int s_piv;
 
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
   const int CS = (int)cluster.num_blocks();
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x;
   const int tent = tent0 + blockIdx.x / CS;
   const int nb = a.nb, Q = a.Q, nrhs = a.nrhs, CH = a.CH;
   const int npair = nb * (nb + 1) / 2;
-  const int nbpair = nrhs * nb;
-  double* sA = sm;                    // nb * nb   : assembled matrix, then LU factors
-  double* sb = sm + a.off_b;          // nrhs * nb : assembled rhs, then x
-  double* sPG = sm + a.off_pg;        // npair     : this CTA's Gram slice (upper triangle)
-  double* sPB = sm + a.off_pb;        // nrhs * nb : this CTA's rhs slice
-  double* sPD = sm + a.off_pd;        // nb * nb   : this CTA's Dirichlet slice
-  double* sR = sm + a.off_rows;       // CH * RT * nb
-  double* sV = sm + a.off_bvs;        // CH * (DIM+1) * nb : bottom (v, sigma) scaled by sqrt(w)
-  double* sCB = sm + a.off_cb;        // CH * nrhs * C    : bottom data coefficients
-  double* sM = sm + a.off_mono;       // 2*CH * mono_stride
-  double* sU = sm + a.off_u;          // 2*CH * nb        : U-values per (side, point)
-  double* sY = sm + a.off_y;          // nrhs * C * nb    : outflow coefficient vectors
-  double* sRD = sm + a.off_rd;        // nb               : reciprocal pivots
+  const int nmom = nrhs * C * nb;
+  double* sA = sm;                     // nb*nb      assembled A, then LU factors
+  double* sb = sm + a.off_b;           // nrhs*nb    assembled b, then x
+  double* sPG = sm + a.off_pg;         // npair      this CTA: G (top)
+  double* sPH = sm + a.off_ph;         // DIM*npair  this CTA: H_m
+  double* sPGb = sm + a.off_pgb;       // npair      this CTA: G (bottom, recovery)
+  double* sPM = sm + a.off_pm;         // nmom       this CTA: moments (gamma, alpha, beta_m) per rhs
+  double* sPD = sm + a.off_pd;         // nb*nb      this CTA: Dirichlet A part
+  double* sPBD = sm + a.off_pbd;       // nrhs*nb    this CTA: Dirichlet b part
+  double* sSG = sm + a.off_sg;         // (DIM+2)*npair  summed G, H_m, Gbot
+  double* sSM = sm + a.off_sm;         // nmom       summed moments
+  double* sF = sm + a.off_f;           // npair      facet Gram
+  double* sDel = sm + a.off_del;       // nrhs*nb    facet moments delta
+  double* sU = sm + a.off_u;           // 2*CH*nb    U-values (scaled) per (side, point)
+  double* sM = sm + a.off_mono;        // 2*CH*mono_stride
+  double* sCB = sm + a.off_cb;         // CH*nrhs*C  bottom data coefficients
+  double* sGd = sm + a.off_gd;         // CH*nrhs    Dirichlet data coefficients
+  double* sY = sm + a.off_y;           // nrhs*C*nb  outflow coefficient vectors
+  double* sRD = sm + a.off_rd;         // nb         reciprocal pivots
 
   // ---------------- phase 0: tent and patch geometry ----------------
   if (tid == 0) {
@@ -243,6 +292,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer_fp64(const KArgs a, const
     for (int d = 0; d < DIM; ++d) s_xv[d] = a.X[(int64_t)v * DIM + d];
     s_nfac = a.vfac_ptr[v + 1] - a.vfac_ptr[v];
   }
+  for (int id = tid; id < nmom; id += blockDim.x) sPM[id] = 0.0;
   __syncthreads();
   const int P = s_P, v = s_v, nfac = s_nfac;
   for (int k = tid; k < P; k += blockDim.x) {
@@ -271,9 +321,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer_fp64(const KArgs a, const
       g2 += gt[d] * gt[d];
     }
     s_sdet[k] = sqrt(fabs(det));
-    const double q = s_ic2 - g2;   // > 0 on a space-like top face
-    if (!(q > 0.0)) flag_error(a, TP_ERR_CAUSALITY, tent);
-    s_st[k] = sqrt(fmax(q, 0.0));
+    if (!(s_ic2 - g2 > 0.0)) flag_error(a, TP_ERR_CAUSALITY, tent);   // space-like top face
   }
   // Dirichlet face simplices (x_v, t_bot), (x_v, t_top), (x_w, tau_w)
   for (int f = tid; f < nfac; f += blockDim.x) {
@@ -305,7 +353,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer_fp64(const KArgs a, const
   }
   // Gram pairs owned by this thread (upper triangle, i <= j, row-major order)
   int pi[kMaxPair], pj[kMaxPair];
-  double acc[kMaxPair], accb[kMaxPair];
+  double aK[kMaxPair], aG[kMaxPair], aH[kMaxPair][DIM], aB[kMaxPair];
 #pragma unroll
   for (int s = 0; s < kMaxPair; ++s) {
     const int id = tid + s * kThreads;
@@ -320,8 +368,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer_fp64(const KArgs a, const
     }
     pi[s] = i;
     pj[s] = j;
-    acc[s] = 0.0;
-    accb[s] = 0.0;
+    aK[s] = aG[s] = aB[s] = 0.0;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) aH[s][d] = 0.0;
   }
   __syncthreads();
 
@@ -330,9 +379,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer_fp64(const KArgs a, const
   const int slice = (NP + CS - 1) / CS;
   const int q0 = min(NP, rank * slice), q1 = min(NP, q0 + slice);
   const double c = s_c, ih = s_ih, ic2 = s_ic2, tc = s_tc;
+  int curk = q0 / Q;
   for (int base = q0; base < q1; base += CH) {
     const int nq = min(CH, q1 - base);
-    // (a) one thread per (side, point): U-values, per-point scalars, bottom data
+    // (a) one thread per (side, point): sqrt(w)-scaled U-values, bottom data coefficients
     if (tid < 2 * CH) {
       const int side = tid / CH, ql = tid % CH, qg = base + ql;
       if (ql < nq) {
@@ -347,11 +397,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer_fp64(const KArgs a, const
         double xh[DIM];
         for (int d = 0; d < DIM; ++d) xh[d] = (x[d] - s_xv[d]) * ih;
         const double th = c * (tt - tc) * ih;
-        eval_uvalues<DIM>(a, th, xh, sM + tid * a.mono_stride, sU + (size_t)tid * nb);
         const double sw = __ldg(a.sqw + q) * s_sdet[k];
-        s_psw[tid] = sw;
-        s_pzs[tid] = sw * s_st[k];
-        s_pk[tid] = k;
+        eval_uvalues<DIM>(a, th, xh, sM + tid * a.mono_stride, sw, sU + (size_t)tid * nb);
         if (side == 1) {
           const int el = s_el[k];
           for (int r = 0; r < nrhs; ++r) {
@@ -360,162 +407,188 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer_fp64(const KArgs a, const
             double sg = 0.0;
             for (int d = 0; d < DIM; ++d) sg = fma(f[2 + d], s_gb[k][d], sg);
             double* cb = sCB + ((size_t)ql * nrhs + r) * C;
-            cb[0] = sw * Ub;
-            cb[1] = sw * (ic2 * vb - sg);
-            for (int d = 0; d < DIM; ++d) cb[2 + d] = sw * (f[2 + d] - vb * s_gb[k][d]);
+            cb[0] = sw * Ub;                       // gamma
+            cb[1] = sw * (ic2 * vb - sg);          // alpha
+            for (int d = 0; d < DIM; ++d) cb[2 + d] = sw * (f[2 + d] - vb * s_gb[k][d]);   // beta_m
           }
         }
       }
     }
     __syncthreads();
-    // (b) all threads: derivatives and Gram rows per (side, point, basis function)
-    for (int id = tid; id < 2 * CH * nb; id += blockDim.x) {
-      const int sp = id / nb, j = id % nb, side = sp / CH, ql = sp % CH;
-      if (ql >= nq) continue;
-      const double* u = sU + (size_t)sp * nb;
-      const double sw = s_psw[sp];
-      const int k = s_pk[sp];
-      const double vj = c * ih * rel_eval<DIM>(a, j, 0, u);
-      if (side == 0) {
-        double* R = sR + (size_t)ql * RT * nb;
-        R[j] = s_pzs[sp] * vj;
-        for (int d = 0; d < DIM; ++d) {
-          const double sj = -ih * rel_eval<DIM>(a, j, 1 + d, u);
-          R[(1 + d) * nb + j] = sw * (sj - vj * s_gt[k][d]);
+    // (b) Grams of U-values: top per element (flushed into G and H_m), bottom
+    for (int ql = 0; ql < nq; ++ql) {
+      const int k = (base + ql) / Q;
+      if (k != curk) {
+#pragma unroll
+        for (int s = 0; s < kMaxPair; ++s) {
+          aG[s] += aK[s];
+#pragma unroll
+          for (int d = 0; d < DIM; ++d) aH[s][d] = fma(s_gt[curk][d], aK[s], aH[s][d]);
+          aK[s] = 0.0;
         }
-      } else {
-        sR[(size_t)ql * RT * nb + (RT - 1) * nb + j] = sw * u[j];
-        double* V = sV + (size_t)ql * (DIM + 1) * nb;
-        V[j] = sw * vj;
-        for (int d = 0; d < DIM; ++d) V[(1 + d) * nb + j] = -sw * ih * rel_eval<DIM>(a, j, 1 + d, u);
+        curk = k;
+      }
+      const double* ut = sU + (size_t)ql * nb;
+      const double* ub = sU + (size_t)(CH + ql) * nb;
+#pragma unroll
+      for (int s = 0; s < kMaxPair; ++s) {
+        if (tid + s * kThreads < npair) {
+          aK[s] = fma(ut[pi[s]], ut[pj[s]], aK[s]);
+          aB[s] = fma(ub[pi[s]], ub[pj[s]], aB[s]);
+        }
       }
     }
-    __syncthreads();
-    // (c) Gram and right-hand sides over the chunk
-#pragma unroll
-    for (int s = 0; s < kMaxPair; ++s) {
-      if (tid + s * kThreads < npair) {
-        const int i = pi[s], j = pj[s];
-        double t = acc[s];
-        for (int ql = 0; ql < nq; ++ql) {
-          const double* R = sR + (size_t)ql * RT * nb;
-#pragma unroll
-          for (int r = 0; r < RT; ++r) t = fma(R[r * nb + i], R[r * nb + j], t);
-        }
-        acc[s] = t;
-      }
-    }
-#pragma unroll
-    for (int s = 0; s < kMaxPair; ++s) {
-      const int id = tid + s * kThreads;
-      if (id < nbpair) {
-        const int r = id / nb, i = id % nb;
-        double t = accb[s];
-        for (int ql = 0; ql < nq; ++ql) {
-          const double* cb = sCB + ((size_t)ql * nrhs + r) * C;
-          const double* V = sV + (size_t)ql * (DIM + 1) * nb;
-          t = fma(cb[0], sR[(size_t)ql * RT * nb + (RT - 1) * nb + i], t);
-#pragma unroll
-          for (int d = 0; d < DIM + 1; ++d) t = fma(cb[1 + d], V[d * nb + i], t);
-        }
-        accb[s] = t;
-      }
+    // (c) moments of the bottom data
+    for (int id = tid; id < nmom; id += blockDim.x) {
+      const int r = id / (C * nb), rem = id % (C * nb), cc = rem / nb, i = rem % nb;
+      double t = sPM[id];
+      for (int ql = 0; ql < nq; ++ql)
+        t = fma(sCB[((size_t)ql * nrhs + r) * C + cc], sU[(size_t)(CH + ql) * nb + i], t);
+      sPM[id] = t;
     }
     __syncthreads();
   }
-  // publish this CTA's slice
+  // publish this CTA's Grams
 #pragma unroll
   for (int s = 0; s < kMaxPair; ++s) {
     const int id = tid + s * kThreads;
-    if (id < npair) sPG[id] = acc[s];
-    if (id < nbpair) sPB[id] = accb[s];
+    if (id < npair) {
+      sPG[id] = aG[s] + aK[s];
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) sPH[d * npair + id] = (q1 > q0) ? fma(s_gt[curk][d], aK[s], aH[s][d]) : aH[s][d];
+      sPGb[id] = aB[s];
+    }
   }
 
-  // ---------------- phase 2: Dirichlet faces, this CTA's slice of their points ----------------
+  // ---------------- phase 2: Dirichlet faces (this CTA's slice of each facet's points) ----------------
   if (nfac > 0) {
     for (int id = tid; id < nb * nb; id += blockDim.x) sPD[id] = 0.0;
-    const int NF = nfac * Q;
-    const int fsl = (NF + CS - 1) / CS;
-    const int f0 = min(NF, rank * fsl), f1 = min(NF, f0 + fsl);
+    for (int id = tid; id < nrhs * nb; id += blockDim.x) {
+      sPBD[id] = 0.0;
+      sDel[id] = 0.0;
+    }
+    const int fsl = (Q + CS - 1) / CS;
+    const int f0 = min(Q, rank * fsl), f1 = min(Q, f0 + fsl);
     __syncthreads();
-    for (int base = f0; base < f1; base += CH) {
-      const int nq = min(CH, f1 - base);
-      double* Pd = sR;                       // CH * nb : s_j.n + alpha v_j
-      double* Vd = sR + (size_t)CH * nb;     // CH * nb : w v_i
-      double* Sd = sV;                       // CH * nb : alpha v_i - s_i.n
-      double* Gd = sV + (size_t)CH * nb;     // CH * nrhs : w g_D
-      if (tid < nq) {
-        const int fq = base + tid, f = fq / Q, q = fq % Q;
-        double xt[DIM + 1];
-        for (int d = 0; d <= DIM; ++d) xt[d] = 0.0;
-        for (int i = 0; i < NV; ++i) {
-          const double l = __ldg(a.bary + q * NV + i);
-          for (int d = 0; d <= DIM; ++d) xt[d] = fma(l, s_fP[f][i][d], xt[d]);
+    for (int f = 0; f < nfac; ++f) {
+      double aF[kMaxPair];
+#pragma unroll
+      for (int s = 0; s < kMaxPair; ++s) aF[s] = 0.0;
+      for (int base = f0; base < f1; base += CH) {
+        const int nq = min(CH, f1 - base);
+        if (tid < nq) {
+          const int q = base + tid;
+          double xt[DIM + 1];
+          for (int d = 0; d <= DIM; ++d) xt[d] = 0.0;
+          for (int i = 0; i < NV; ++i) {
+            const double l = __ldg(a.bary + q * NV + i);
+            for (int d = 0; d <= DIM; ++d) xt[d] = fma(l, s_fP[f][i][d], xt[d]);
+          }
+          double xh[DIM];
+          for (int d = 0; d < DIM; ++d) xh[d] = (xt[d] - s_xv[d]) * ih;
+          const double th = c * (xt[DIM] - tc) * ih;
+          const double sw = sqrt(__ldg(a.wref + q) * s_fscale[f]);
+          eval_uvalues<DIM>(a, th, xh, sM + tid * a.mono_stride, sw, sU + (size_t)tid * nb);
+          const long long goff = a.tent_gdoff[tent] + (long long)f * Q + q;
+          for (int r = 0; r < nrhs; ++r)
+            sGd[tid * nrhs + r] = (a.gD != nullptr) ? sw * a.gD[(long long)r * a.n_bnd + goff] : 0.0;
         }
-        double xh[DIM];
-        for (int d = 0; d < DIM; ++d) xh[d] = (xt[d] - s_xv[d]) * ih;
-        const double th = c * (xt[DIM] - tc) * ih;
-        double* u = sU + (size_t)tid * nb;
-        eval_uvalues<DIM>(a, th, xh, sM + tid * a.mono_stride, u);
-        const double w = __ldg(a.wref + q) * s_fscale[f];
-        for (int j = 0; j < nb; ++j) {
-          const double vj = c * ih * rel_eval<DIM>(a, j, 0, u);
-          double sn = 0.0;
-          for (int d = 0; d < DIM; ++d) sn = fma(-ih * rel_eval<DIM>(a, j, 1 + d, u), s_fn[f][d], sn);
-          Pd[tid * nb + j] = sn + a.alpha * vj;
-          Vd[tid * nb + j] = w * vj;
-          Sd[tid * nb + j] = a.alpha * vj - sn;
+        __syncthreads();
+        for (int ql = 0; ql < nq; ++ql) {
+          const double* u = sU + (size_t)ql * nb;
+#pragma unroll
+          for (int s = 0; s < kMaxPair; ++s)
+            if (tid + s * kThreads < npair) aF[s] = fma(u[pi[s]], u[pj[s]], aF[s]);
         }
-        const long long goff = a.tent_gdoff[tent] + fq;
-        for (int r = 0; r < nrhs; ++r)
-          Gd[tid * nrhs + r] = (a.gD != nullptr) ? w * a.gD[(long long)r * a.n_bnd + goff] : 0.0;
+        for (int id = tid; id < nrhs * nb; id += blockDim.x) {
+          const int r = id / nb, i = id % nb;
+          double t = sDel[id];
+          for (int ql = 0; ql < nq; ++ql) t = fma(sGd[ql * nrhs + r], sU[(size_t)ql * nb + i], t);
+          sDel[id] = t;
+        }
+        __syncthreads();
       }
+#pragma unroll
+      for (int s = 0; s < kMaxPair; ++s)
+        if (tid + s * kThreads < npair) sF[tid + s * kThreads] = aF[s];
       __syncthreads();
+      const double ac = a.alpha * c * ih;
       for (int id = tid; id < nb * nb; id += blockDim.x) {
         const int i = id / nb, j = id % nb;
-        double t = sPD[id];
-        for (int ql = 0; ql < nq; ++ql) t = fma(Vd[ql * nb + i], Pd[ql * nb + j], t);
-        sPD[id] = t;
+        double t = ac * congruence<DIM>(a, i, 0, j, 0, sF, nb);
+        for (int d = 0; d < DIM; ++d) t = fma(-ih * s_fn[f][d], congruence<DIM>(a, i, 0, j, 1 + d, sF, nb), t);
+        sPD[id] = fma(c * ih, t, sPD[id]);
       }
-      for (int id = tid; id < nbpair; id += blockDim.x) {
+      for (int id = tid; id < nrhs * nb; id += blockDim.x) {
         const int r = id / nb, i = id % nb;
-        double t = sPB[id];
-        for (int ql = 0; ql < nq; ++ql) t = fma(Gd[ql * nrhs + r], Sd[ql * nb + i], t);
-        sPB[id] = t;
+        const double* del = sDel + (size_t)r * nb;
+        double t = ac * rel_apply<DIM>(a, i, 0, del);
+        for (int d = 0; d < DIM; ++d) t = fma(ih * s_fn[f][d], rel_apply<DIM>(a, i, 1 + d, del), t);
+        sPBD[id] += t;
       }
+      __syncthreads();
+      for (int id = tid; id < nrhs * nb; id += blockDim.x) sDel[id] = 0.0;
       __syncthreads();
     }
   }
 
-  // ---------------- cluster reduction of the slices (rank order) ----------------
+  // ---------------- cluster reduction (rank order) ----------------
   cluster.sync();
-  for (int id = tid; id < nb * nb; id += blockDim.x) {
-    const int i = id / nb, j = id % nb;
-    const int lo = min(i, j), hi = max(i, j);
-    const int pidx = lo * nb - lo * (lo - 1) / 2 + (hi - lo);
+  for (int id = tid; id < (DIM + 2) * npair; id += blockDim.x) {
+    const int blk = id / npair, pid = id % npair;   // 0: G, 1..DIM: H_m, DIM+1: Gbot
+    const double* src = (blk == 0) ? sPG : (blk <= DIM ? sPH + (blk - 1) * npair : sPGb);
     double t = 0.0;
-    for (int r = 0; r < CS; ++r) {
-      t += cluster.map_shared_rank(sPG, r)[pidx];
-      if (nfac > 0) t += cluster.map_shared_rank(sPD, r)[id];
-    }
+    for (int r = 0; r < CS; ++r) t += cluster.map_shared_rank(src, r)[pid];
+    sSG[id] = t;
+  }
+  for (int id = tid; id < nmom; id += blockDim.x) {
+    double t = 0.0;
+    for (int r = 0; r < CS; ++r) t += cluster.map_shared_rank(sPM, r)[id];
+    sSM[id] = t;
+  }
+  for (int id = tid; id < nb * nb; id += blockDim.x) {
+    double t = 0.0;
+    if (nfac > 0)
+      for (int r = 0; r < CS; ++r) t += cluster.map_shared_rank(sPD, r)[id];
     sA[id] = t;
   }
-  for (int id = tid; id < nbpair; id += blockDim.x) {
+  for (int id = tid; id < nrhs * nb; id += blockDim.x) {
     double t = 0.0;
-    for (int r = 0; r < CS; ++r) t += cluster.map_shared_rank(sPB, r)[id];
+    if (nfac > 0)
+      for (int r = 0; r < CS; ++r) t += cluster.map_shared_rank(sPBD, r)[id];
     sb[id] = t;
   }
-  cluster.sync();   // no CTA leaves or reuses its slice while another still reads it
+  cluster.sync();   // no CTA leaves or reuses its partials while another still reads them
+  {
+    const double* SG = sSG;
+    const double* SGb = sSG + (DIM + 1) * npair;
+    const double ih2 = ih * ih;
+    for (int id = tid; id < nb * nb; id += blockDim.x) {
+      const int i = id / nb, j = id % nb;
+      double t = congruence<DIM>(a, i, 0, j, 0, SG, nb);
+      for (int d = 0; d < DIM; ++d) {
+        const double* H = sSG + (1 + d) * npair;
+        t += congruence<DIM>(a, i, 1 + d, j, 1 + d, SG, nb);
+        t = fma(c, congruence<DIM>(a, i, 1 + d, j, 0, H, nb) + congruence<DIM>(a, i, 0, j, 1 + d, H, nb), t);
+      }
+      sA[id] += fma(ih2, t, SGb[pair_index(i, j, nb)]);
+    }
+    for (int id = tid; id < nrhs * nb; id += blockDim.x) {
+      const int r = id / nb, i = id % nb;
+      const double* M = sSM + (size_t)r * C * nb;   // gamma, alpha, beta_1..beta_n
+      double t = M[i] + c * ih * rel_apply<DIM>(a, i, 0, M + nb);
+      for (int d = 0; d < DIM; ++d) t = fma(-ih, rel_apply<DIM>(a, i, 1 + d, M + (2 + d) * nb), t);
+      sb[id] += t;
+    }
+  }
+  __syncthreads();
 
-  // ---------------- phase 3: factorisation and solve (warp 0 of every CTA) ----------------
-  // Interior tents (no Dirichlet face) have a symmetric positive definite A
-  // (space-like faces), so they are eliminated without pivoting; tents with
-  // Dirichlet faces use partial pivoting.  Right-hand sides are eliminated
-  // alongside; reciprocal pivots are kept for the back substitution.
-  if (warp == 0) {
-    const bool pivoting = (nfac > 0);
-    for (int k = 0; k < nb; ++k) {
-      if (pivoting) {
+  // ---------------- phase 3: LU (no pivoting for interior tents: A is SPD), solve ----------------
+  const int lane = tid & 31, warp = tid >> 5;
+  const bool pivoting = (nfac > 0);
+  for (int k = 0; k < nb; ++k) {
+    if (pivoting) {
+      if (warp == 0) {
         // |a_ik| compared through the bit patterns (non-negative doubles order as integers)
         unsigned long long best = 0ull;
         int bi = k;
@@ -534,51 +607,63 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer_fp64(const KArgs a, const
             bi = oi;
           }
         }
-        const int pr = __shfl_sync(0xffffffffu, bi, 0);
-        if (pr != k) {
-          for (int j = lane; j < nb; j += 32) {
-            const double t = sA[k * nb + j];
-            sA[k * nb + j] = sA[pr * nb + j];
-            sA[pr * nb + j] = t;
-          }
-          for (int r = lane; r < nrhs; r += 32) {
-            const double t = sb[r * nb + k];
-            sb[r * nb + k] = sb[r * nb + pr];
-            sb[r * nb + pr] = t;
-          }
-        }
-        __syncwarp();
+        if (lane == 0) s_piv = bi;
       }
+      __syncthreads();
+      const int pr = s_piv;
+      if (pr != k) {
+        for (int j = tid; j < nb; j += blockDim.x) {
+          const double t = sA[k * nb + j];
+          sA[k * nb + j] = sA[pr * nb + j];
+          sA[pr * nb + j] = t;
+        }
+        for (int r = tid; r < nrhs; r += blockDim.x) {
+          const double t = sb[r * nb + k];
+          sb[r * nb + k] = sb[r * nb + pr];
+          sb[r * nb + pr] = t;
+        }
+      }
+      __syncthreads();
+    }
+    if (tid == 0) {
       double piv = sA[k * nb + k];
       if (!(fabs(piv) > 0.0) || !isfinite(piv)) {
-        if (lane == 0 && rank == 0) flag_error(a, TP_ERR_SINGULAR, tent);
+        if (rank == 0) flag_error(a, TP_ERR_SINGULAR, tent);
         piv = 1.0;
       }
-      const double rp = 1.0 / piv;
-      if (lane == 0) sRD[k] = rp;
-      for (int i = k + 1 + lane; i < nb; i += 32) {
-        const double l = sA[i * nb + k] * rp;
-        sA[i * nb + k] = l;
-        for (int j = k + 1; j < nb; ++j) sA[i * nb + j] = fma(-l, sA[k * nb + j], sA[i * nb + j]);
-        for (int r = 0; r < nrhs; ++r) sb[r * nb + i] = fma(-l, sb[r * nb + k], sb[r * nb + i]);
-      }
-      __syncwarp();
+      sRD[k] = recip(piv);
     }
-    for (int k = nb - 1; k >= 0; --k) {
-      for (int r = lane; r < nrhs; r += 32) sb[r * nb + k] *= sRD[k];
-      __syncwarp();
-      for (int id = lane; id < k * nrhs; id += 32) {
-        const int r = id / k, i = id % k;
-        sb[r * nb + i] = fma(-sA[i * nb + k], sb[r * nb + k], sb[r * nb + i]);
+    __syncthreads();
+    const double rp = sRD[k];
+    const int rem = nb - k - 1;
+    for (int i = k + 1 + tid; i < nb; i += blockDim.x) sA[i * nb + k] *= rp;   // multipliers
+    __syncthreads();
+    for (int id = tid; id < rem * (rem + nrhs); id += blockDim.x) {
+      const int i = k + 1 + id / (rem + nrhs), jj = id % (rem + nrhs);
+      const double l = sA[i * nb + k];
+      if (jj < rem) {
+        const int j = k + 1 + jj;
+        sA[i * nb + j] = fma(-l, sA[k * nb + j], sA[i * nb + j]);
+      } else {
+        const int r = jj - rem;
+        sb[r * nb + i] = fma(-l, sb[r * nb + k], sb[r * nb + i]);
       }
-      __syncwarp();
     }
+    __syncthreads();
   }
-  __syncthreads();
+  for (int k = nb - 1; k >= 0; --k) {
+    for (int r = tid; r < nrhs; r += blockDim.x) sb[r * nb + k] *= sRD[k];
+    __syncthreads();
+    for (int id = tid; id < k * nrhs; id += blockDim.x) {
+      const int r = id / k, i = id % k;
+      sb[r * nb + i] = fma(-sA[i * nb + k], sb[r * nb + k], sb[r * nb + i]);
+    }
+    __syncthreads();
+  }
 
   // ---------------- phase 4: outflow at this CTA's top points ----------------
-  // coefficient vectors of U_h, dU_h/dthat, dU_h/dxhat_m in the basis: y = D^T x
-  for (int id = tid; id < nrhs * C * nb; id += blockDim.x) {
+  // coefficient vectors of U_h, v_h, sigma_h in terms of U-values: y = D^T x
+  for (int id = tid; id < nmom; id += blockDim.x) {
     const int r = id / (C * nb), rem = id % (C * nb), cc = rem / nb, kk = rem % nb;
     double t;
     if (cc == 0) {
@@ -592,11 +677,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer_fp64(const KArgs a, const
     }
     sY[id] = t;
   }
-  __syncthreads();
   for (int base = q0; base < q1; base += 2 * CH) {
-    const int ql = tid, qg = base + ql;
-    if (ql < 2 * CH && qg < q1) {
-      const int k = qg / Q, q = qg % Q;
+    const int nq = min(2 * CH, q1 - base);
+    if (tid < nq) {
+      const int qg = base + tid, k = qg / Q, q = qg % Q;
       double x[DIM], tt = 0.0;
       for (int d = 0; d < DIM; ++d) x[d] = 0.0;
       for (int i = 0; i < NV; ++i) {
@@ -607,24 +691,19 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer_fp64(const KArgs a, const
       double xh[DIM];
       for (int d = 0; d < DIM; ++d) xh[d] = (x[d] - s_xv[d]) * ih;
       const double th = c * (tt - tc) * ih;
-      double* u = sU + (size_t)tid * nb;
-      eval_uvalues<DIM>(a, th, xh, sM + tid * a.mono_stride, u);
-      const int el = s_el[k];
-      for (int r = 0; r < nrhs; ++r) {
-        double o[C];
-#pragma unroll
-        for (int cc = 0; cc < C; ++cc) o[cc] = 0.0;
-        const double* y = sY + (size_t)r * C * nb;
-        for (int j = 0; j < nb; ++j) {
-          const double uj = u[j];
-#pragma unroll
-          for (int cc = 0; cc < C; ++cc) o[cc] = fma(y[cc * nb + j], uj, o[cc]);
-        }
-        double* f = a.front + (((int64_t)r * a.ne + el) * Q + q) * C;
-#pragma unroll
-        for (int cc = 0; cc < C; ++cc) f[cc] = o[cc];
-      }
+      eval_uvalues<DIM, false>(a, th, xh, sM + tid * a.mono_stride, 1.0, sU + (size_t)tid * nb);
     }
+    __syncthreads();
+    for (int id = tid; id < nq * nrhs * C; id += blockDim.x) {
+      const int ql = id / (nrhs * C), rc = id % (nrhs * C), r = rc / C, cc = rc % C;
+      const int qg = base + ql, k = qg / Q, q = qg % Q;
+      const double* u = sU + (size_t)ql * nb;
+      const double* y = sY + ((size_t)r * C + cc) * nb;
+      double t = 0.0;
+      for (int j = 0; j < nb; ++j) t = fma(y[j], u[j], t);
+      a.front[(((int64_t)r * a.ne + s_el[k]) * Q + q) * C + cc] = t;
+    }
+    __syncthreads();
   }
   if (tid == 0 && rank == 0) a.tau[v] = s_ttop;
 }
@@ -980,49 +1059,47 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
   a.status = ctx->d_status;
   a.status_info = ctx->d_info;
   // shared-memory plan: the largest chunk of points that fits
-  const int nb = ctx->nb, C = ctx->C, RT = n + 2;
+  const int nb = ctx->nb, C = ctx->C;
   const int npair = nb * (nb + 1) / 2;
-  if (npair > kMaxPair * kThreads || ctx->nrhs * nb > kMaxPair * kThreads) {
-    tp::set_error("tp_create: nb or nrhs too large for this kernel");
+  if (npair > kMaxPair * kThreads) {
+    tp::set_error("tp_create: dim U^p too large for this kernel (nb (nb+1)/2 > 1024)");
     return fail(TP_ERR_UNSUPPORTED);
   }
   a.mono_stride = ctx->nmono | 1;
   // shared-memory plan: the largest chunk of points that keeps two CTAs per SM,
   // else the largest that fits one
   auto plan = [&](int CH) {
-    size_t off = (size_t)nb * nb;
-    a.off_b = (int)off;
-    off += (size_t)ctx->nrhs * nb;
-    a.off_pg = (int)off;
-    off += (size_t)npair;
-    a.off_pb = (int)off;
-    off += (size_t)ctx->nrhs * nb;
-    a.off_pd = (int)off;
-    off += (size_t)nb * nb;
-    a.off_rows = (int)off;
-    off += (size_t)CH * RT * nb;
-    a.off_bvs = (int)off;
-    off += (size_t)CH * (n + 1) * nb;
-    a.off_cb = (int)off;
-    off += (size_t)CH * ctx->nrhs * C;
-    a.off_mono = (int)off;
-    off += (size_t)2 * CH * a.mono_stride;
-    a.off_u = (int)off;
-    off += (size_t)2 * CH * nb;
-    a.off_y = (int)off;
-    off += (size_t)ctx->nrhs * C * nb;
-    a.off_rd = (int)off;
-    off += (size_t)nb;
+    size_t off = 0;
+    auto take = [&](int* field, size_t count) {
+      if (field) *field = (int)off;
+      off += count;
+    };
+    const size_t nmom = (size_t)ctx->nrhs * C * nb;
+    take(nullptr, (size_t)nb * nb);                  // A at offset 0
+    take(&a.off_b, (size_t)ctx->nrhs * nb);
+    take(&a.off_pg, npair);
+    take(&a.off_ph, (size_t)n * npair);
+    take(&a.off_pgb, npair);
+    take(&a.off_pm, nmom);
+    take(&a.off_pd, (size_t)nb * nb);
+    take(&a.off_pbd, (size_t)ctx->nrhs * nb);
+    take(&a.off_sg, (size_t)(n + 2) * npair);
+    take(&a.off_sm, nmom);
+    take(&a.off_f, npair);
+    take(&a.off_del, (size_t)ctx->nrhs * nb);
+    take(&a.off_u, (size_t)2 * CH * nb);
+    take(&a.off_mono, (size_t)2 * CH * a.mono_stride);
+    take(&a.off_cb, (size_t)CH * ctx->nrhs * C);
+    take(&a.off_gd, (size_t)CH * ctx->nrhs);
+    take(&a.off_y, nmom);
+    take(&a.off_rd, nb);
     return off * sizeof(double);
   };
   int CH = 0;
   size_t bytes = 0;
   for (size_t cap : {kTwoPerSmSmem, kMaxDynSmem}) {
-    for (int ch = 64; ch >= 8 && CH == 0; ch /= 2) {
-      const size_t need_d = (size_t)ch * (3 * nb + ctx->nrhs);
-      const size_t have_d = (size_t)ch * (RT + n + 1) * nb;
-      if (plan(ch) <= cap && need_d <= have_d) CH = ch;
-    }
+    for (int ch = 32; ch >= 8 && CH == 0; ch /= 2)
+      if (plan(ch) <= cap) CH = ch;
     if (CH) break;
   }
   if (CH == 0) {
