@@ -90,11 +90,14 @@ def build_basis(dim, p) -> Basis:
 class Solver:
     """A tp_ctx: device-resident mesh, tents, tables and front state.
 
-    All device memory handed to libtp is torch CUDA float64 memory; the
-    current torch stream is passed to every call."""
+    precision "fp64": every step in binary64.  "mixed": assembly, residual
+    and outflow in float-float on the binary32 pipes, binary32 factorisation
+    of the equilibrated local matrix, iterative refinement.  All device
+    memory handed to libtp is torch CUDA float64 memory; the current torch
+    stream is passed to every call."""
 
     def __init__(self, coords, elems, c, p: int, T: float, kappa: float, alpha: float = 0.5,
-                 nrhs: int = 1, tents: Tents | None = None):
+                 nrhs: int = 1, tents: Tents | None = None, precision: str = "fp64"):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("libtp Solver needs a CUDA device")
@@ -102,7 +105,11 @@ class Solver:
         self._mesh = B._MeshArrays(coords, elems, c)
         self.tents = tents if tents is not None else Tents(coords, elems, c, kappa, T)
         self.basis = Basis(self._mesh.coords.shape[1], p)
-        self.params = B.make_params(p, T, kappa, alpha=alpha, nrhs=nrhs)
+        if precision not in ("fp64", "mixed"):
+            raise ValueError("precision must be 'fp64' or 'mixed'")
+        self.precision = precision
+        self.params = B.make_params(p, T, kappa, alpha=alpha, nrhs=nrhs,
+                                    precision=B.TP_FP64 if precision == "fp64" else B.TP_MIXED)
         h = ct.c_void_p()
         B.check(lib.tp_create(ct.byref(self._mesh.desc), self.tents.handle, self.basis.handle,
                               ct.byref(self.params), ct.byref(h)))

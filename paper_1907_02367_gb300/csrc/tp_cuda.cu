@@ -20,6 +20,8 @@
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -47,6 +49,7 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kMaxPair = 4;      // Gram pairs per thread (nb (nb+1)/2 <= 4 * 256)
+constexpr int kMaxRefine = 8;    // refinement steps of the mixed path
 
 struct KArgs {
   int nb, nmono, Q, nrhs, CH, mono_stride;
@@ -71,6 +74,7 @@ struct KArgs {
   const int* sp_ptr;
   const int* sp_mono;
   const double* sp_coef;
+  const float2* sp_coef_dd;   // (hi, lo) binary32 pair of every sp_coef entry
   const int* mono_parent;
   const int* mono_var;
   double* tau;
@@ -85,33 +89,15 @@ struct KArgs {
   const int* relT_ptr;
   const int* relT_dst;
   const double* relT_fac;
+  const float* rel_facf;      // relation factors (small integers) in binary32
+  const float* relT_facf;
+  int off_al, off_eq, off_perm, off_z, off_x;   // mixed path: binary32 LU and refinement
   int off_b, off_pg, off_ph, off_pgb, off_pm, off_pd, off_pbd, off_sg, off_sm, off_f, off_del, off_u,
       off_mono, off_cb, off_gd, off_y, off_rd;
 };
 
 __device__ __forceinline__ void flag_error(const KArgs& a, int code, long long info) {
   if (atomicCAS(a.status, 0, code) == 0) *a.status_info = info;
-}
-
-// monomials t^k x^alpha at (that, xhat) into m[0..nm): m[g] = m[parent[g]] * var
-template <int DIM>
-__device__ __forceinline__ void eval_monomials(const KArgs& a, double th, const double* xh, double* m) {
-  m[0] = 1.0;
-  for (int g = 1; g < a.nmono; ++g) {
-    const int vr = __ldg(a.mono_var + g);
-    const double s = (vr == 0) ? th : xh[vr - 1];
-    m[g] = m[__ldg(a.mono_parent + g)] * s;
-  }
-}
-
-// sum over the sparse entries of (basis j, component comp)
-template <int DIM>
-__device__ __forceinline__ double sp_eval(const KArgs& a, int j, int comp, const double* m) {
-  constexpr int C = DIM + 2;
-  const int e0 = __ldg(a.sp_ptr + j * C + comp), e1 = __ldg(a.sp_ptr + j * C + comp + 1);
-  double s = 0.0;
-  for (int e = e0; e < e1; ++e) s = fma(__ldg(a.sp_coef + e), m[__ldg(a.sp_mono + e)], s);
-  return s;
 }
 
 // gradient g of the linear function with increments dv[i] along the edges
@@ -160,12 +146,116 @@ __device__ __forceinline__ double small_det(const double (&G)[DIM][DIM]) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Arithmetic used by the tent kernel.  The FP64 path computes in binary64.
+// The mixed path computes the assembly, the refinement residual and the
+// outflow in float-float ("double-float") arithmetic on the binary32 pipes,
+// which GB300 runs ~58x faster than binary64: a value is an unevaluated sum
+// hi + lo of two binary32 numbers (|lo| <= ulp(hi)/2, ~48 significant bits),
+// built from the error-free transformations TwoSum (Knuth), FastTwoSum
+// (Dekker) and TwoProd through the fused multiply-add.  The intrinsics
+// __fadd_rn/__fsub_rn/__fmul_rn keep the compiler from contracting them.
+// ---------------------------------------------------------------------------
+struct dd {
+  float hi, lo;
+};
+
+__device__ __forceinline__ dd two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ dd fast_two_sum(float a, float b) {   // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ dd dd_add(dd a, dd b) {
+  dd s = two_sum(a.hi, b.hi);
+  const dd t = two_sum(a.lo, b.lo);
+  s = fast_two_sum(s.hi, __fadd_rn(s.lo, t.hi));
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, t.lo));
+}
+__device__ __forceinline__ dd dd_mul(dd a, dd b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  return fast_two_sum(p, e);
+}
+__device__ __forceinline__ dd dd_mulf(dd a, float f) {   // f exact in binary32
+  const float p = __fmul_rn(a.hi, f);
+  float e = fmaf(a.hi, f, -p);
+  e = fmaf(a.lo, f, e);
+  return fast_two_sum(p, e);
+}
+
+template <typename T>
+struct Ar;
+
+template <>
+struct Ar<double> {
+  static __device__ __forceinline__ double zero() { return 0.0; }
+  static __device__ __forceinline__ double one() { return 1.0; }
+  static __device__ __forceinline__ double from(double x) { return x; }
+  static __device__ __forceinline__ double to(double x) { return x; }
+  static __device__ __forceinline__ double add(double a, double b) { return a + b; }
+  static __device__ __forceinline__ double sub(double a, double b) { return a - b; }
+  static __device__ __forceinline__ double mul(double a, double b) { return a * b; }
+  static __device__ __forceinline__ double mulf(double a, float f) { return a * (double)f; }
+  static __device__ __forceinline__ double fma(double a, double b, double c) { return ::fma(a, b, c); }
+  static __device__ __forceinline__ double coef(const KArgs& a, int e);
+};
+
+template <>
+struct Ar<dd> {
+  static __device__ __forceinline__ dd zero() { return {0.f, 0.f}; }
+  static __device__ __forceinline__ dd one() { return {1.f, 0.f}; }
+  static __device__ __forceinline__ dd from(double x) {
+    const float h = __double2float_rn(x);
+    return {h, __double2float_rn(x - (double)h)};
+  }
+  static __device__ __forceinline__ double to(dd x) { return (double)x.hi + (double)x.lo; }
+  static __device__ __forceinline__ dd add(dd a, dd b) { return dd_add(a, b); }
+  static __device__ __forceinline__ dd sub(dd a, dd b) { return dd_add(a, {-b.hi, -b.lo}); }
+  static __device__ __forceinline__ dd mul(dd a, dd b) { return dd_mul(a, b); }
+  static __device__ __forceinline__ dd mulf(dd a, float f) { return dd_mulf(a, f); }
+  static __device__ __forceinline__ dd fma(dd a, dd b, dd c) { return dd_add(dd_mul(a, b), c); }
+  static __device__ __forceinline__ dd coef(const KArgs& a, int e);
+};
+
+__device__ __forceinline__ double Ar<double>::coef(const KArgs& a, int e) { return __ldg(a.sp_coef + e); }
+__device__ __forceinline__ dd Ar<dd>::coef(const KArgs& a, int e) {
+  const float2 c = __ldg(a.sp_coef_dd + e);
+  return {c.x, c.y};
+}
+
+// monomials t^k x^alpha at (that, xhat) into m[0..nm): m[g] = m[parent[g]] * var
+template <int DIM, typename T>
+__device__ __forceinline__ void eval_monomials(const KArgs& a, T th, const T* xh, T* m) {
+  m[0] = Ar<T>::one();
+  for (int g = 1; g < a.nmono; ++g) {
+    const int vr = __ldg(a.mono_var + g);
+    const T s = (vr == 0) ? th : xh[vr - 1];
+    m[g] = Ar<T>::mul(m[__ldg(a.mono_parent + g)], s);
+  }
+}
+
+// U-value of basis function j: sum over its sparse monomial entries
+template <int DIM, typename T>
+__device__ __forceinline__ T sp_eval(const KArgs& a, int j, const T* m) {
+  constexpr int C = DIM + 2;
+  const int e0 = __ldg(a.sp_ptr + j * C), e1 = __ldg(a.sp_ptr + j * C + 1);
+  T s = Ar<T>::zero();
+  for (int e = e0; e < e1; ++e) s = Ar<T>::fma(Ar<T>::coef(a, e), m[__ldg(a.sp_mono + e)], s);
+  return s;
+}
+
 // U-values u_k = b_k(xhat, that) of every basis function at one point (times s if SCALE)
-template <int DIM, bool SCALE = true>
-__device__ __forceinline__ void eval_uvalues(const KArgs& a, double th, const double* xh, double* m,
-                                             double s, double* u) {
-  eval_monomials<DIM>(a, th, xh, m);
-  for (int k = 0; k < a.nb; ++k) u[k] = SCALE ? s * sp_eval<DIM>(a, k, 0, m) : sp_eval<DIM>(a, k, 0, m);
+template <int DIM, typename T, bool SCALE = true>
+__device__ __forceinline__ void eval_uvalues(const KArgs& a, T th, const T* xh, T* m, T s, T* u) {
+  eval_monomials<DIM, T>(a, th, xh, m);
+  for (int k = 0; k < a.nb; ++k) u[k] = SCALE ? Ar<T>::mul(s, sp_eval<DIM, T>(a, k, m)) : sp_eval<DIM, T>(a, k, m);
 }
 
 // packed upper-triangle index of (i, j), i, j < nb
@@ -176,28 +266,38 @@ __device__ __forceinline__ int pair_index(int i, int j, int nb) {
 
 // (D_va X D_vb^T)_ij for a packed symmetric X, D_var given by the relation
 // table: (D_var u)_j = sum over entries e of (j, var) of fac_e u[src_e]
-template <int DIM>
-__device__ __forceinline__ double congruence(const KArgs& a, int i, int va, int j, int vb, const double* X,
-                                             int nb) {
+// (the factors are small integers, exact in binary32)
+template <int DIM, typename T>
+__device__ __forceinline__ T congruence(const KArgs& a, int i, int va, int j, int vb, const T* X, int nb) {
   constexpr int NVAR = DIM + 1;
   const int a0 = __ldg(a.rel_ptr + i * NVAR + va), a1 = __ldg(a.rel_ptr + i * NVAR + va + 1);
   const int b0 = __ldg(a.rel_ptr + j * NVAR + vb), b1 = __ldg(a.rel_ptr + j * NVAR + vb + 1);
-  double s = 0.0;
+  T s = Ar<T>::zero();
   for (int e = a0; e < a1; ++e) {
     const int si = __ldg(a.rel_src + e);
-    double t = 0.0;
-    for (int f = b0; f < b1; ++f) t = fma(__ldg(a.rel_fac + f), X[pair_index(si, __ldg(a.rel_src + f), nb)], t);
-    s = fma(__ldg(a.rel_fac + e), t, s);
+    T t = Ar<T>::zero();
+    for (int f = b0; f < b1; ++f)
+      t = Ar<T>::add(t, Ar<T>::mulf(X[pair_index(si, __ldg(a.rel_src + f), nb)], __ldg(a.rel_facf + f)));
+    s = Ar<T>::add(s, Ar<T>::mulf(t, __ldg(a.rel_facf + e)));
   }
   return s;
 }
 
 // (D_var y)_i for a vector y
-template <int DIM>
-__device__ __forceinline__ double rel_apply(const KArgs& a, int i, int var, const double* y) {
+template <int DIM, typename T>
+__device__ __forceinline__ T rel_apply(const KArgs& a, int i, int var, const T* y) {
   const int e0 = __ldg(a.rel_ptr + i * (DIM + 1) + var), e1 = __ldg(a.rel_ptr + i * (DIM + 1) + var + 1);
-  double s = 0.0;
-  for (int e = e0; e < e1; ++e) s = fma(__ldg(a.rel_fac + e), y[__ldg(a.rel_src + e)], s);
+  T s = Ar<T>::zero();
+  for (int e = e0; e < e1; ++e) s = Ar<T>::add(s, Ar<T>::mulf(y[__ldg(a.rel_src + e)], __ldg(a.rel_facf + e)));
+  return s;
+}
+
+// (D_var^T y)_k through the transposed table
+template <int DIM, typename T>
+__device__ __forceinline__ T relT_apply(const KArgs& a, int k, int var, const T* y) {
+  const int e0 = __ldg(a.relT_ptr + k * (DIM + 1) + var), e1 = __ldg(a.relT_ptr + k * (DIM + 1) + var + 1);
+  T s = Ar<T>::zero();
+  for (int e = e0; e < e1; ++e) s = Ar<T>::add(s, Ar<T>::mulf(y[__ldg(a.relT_dst + e)], __ldg(a.relT_facf + e)));
   return s;
 }
 
@@ -231,9 +331,18 @@ __device__ __forceinline__ double recip(double x) {
 // delta = sum w g_D u, E = alpha_D (c/h) D_t - (1/h) sum_m n_m D_m,
 // E' = alpha_D (c/h) D_t + (1/h) sum_m n_m D_m.  Every CTA publishes its
 // partial Grams and moments; after a cluster barrier every CTA sums them in
-// rank order, forms A and b, factorises, and writes the outflow of its slice.
-template <int DIM>
-__global__ void __launch_bounds__(kThreads, 2) k_layer_fp64(const KArgs a, const int tent0) {
+// rank order, forms A and b, solves, and writes the outflow of its slice.
+//
+// MIXED = false: everything in binary64, LU with partial pivoting (none for
+// interior tents, whose A is symmetric positive definite).
+// MIXED = true: assembly, residual and outflow in float-float; A is
+// equilibrated (D A D, D = |diag A|^-1/2), factorised in binary32 and the
+// solution refined against the float-float A until the correction stops
+// shrinking (at most kMaxRefine steps; TP_ERR_NOCONV if it stalls high).
+template <int DIM, bool MIXED>
+__global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int tent0) {
+  using T = typename std::conditional<MIXED, dd, double>::type;
+  using R = Ar<T>;
   constexpr int NV = DIM + 1;   // vertices per element
   constexpr int C = DIM + 2;    // U, v, sigma  (and gamma, alpha, beta_m moments)
   extern __shared__ __align__(16) double sm[];
@@ -248,33 +357,36 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer_fp64(const KArgs a, const
   __shared__ double s_fP[tp::kMaxFacets][NV][DIM + 1];   // Dirichlet face simplices (x, t)
   __shared__ double s_fscale[tp::kMaxFacets], s_fn[tp::kMaxFacets][DIM];
   __shared__ int s_piv;
+  __shared__ float s_red[2][kThreads / 32];
+  __shared__ int s_stop;
 
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
   const int CS = (int)cluster.num_blocks();
   const int tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
   const int tent = tent0 + blockIdx.x / CS;
   const int nb = a.nb, Q = a.Q, nrhs = a.nrhs, CH = a.CH;
   const int npair = nb * (nb + 1) / 2;
   const int nmom = nrhs * C * nb;
-  double* sA = sm;                     // nb*nb      assembled A, then LU factors
-  double* sb = sm + a.off_b;           // nrhs*nb    assembled b, then x
-  double* sPG = sm + a.off_pg;         // npair      this CTA: G (top)
-  double* sPH = sm + a.off_ph;         // DIM*npair  this CTA: H_m
-  double* sPGb = sm + a.off_pgb;       // npair      this CTA: G (bottom, recovery)
-  double* sPM = sm + a.off_pm;         // nmom       this CTA: moments (gamma, alpha, beta_m) per rhs
-  double* sPD = sm + a.off_pd;         // nb*nb      this CTA: Dirichlet A part
-  double* sPBD = sm + a.off_pbd;       // nrhs*nb    this CTA: Dirichlet b part
-  double* sSG = sm + a.off_sg;         // (DIM+2)*npair  summed G, H_m, Gbot
-  double* sSM = sm + a.off_sm;         // nmom       summed moments
-  double* sF = sm + a.off_f;           // npair      facet Gram
-  double* sDel = sm + a.off_del;       // nrhs*nb    facet moments delta
-  double* sU = sm + a.off_u;           // 2*CH*nb    U-values (scaled) per (side, point)
-  double* sM = sm + a.off_mono;        // 2*CH*mono_stride
-  double* sCB = sm + a.off_cb;         // CH*nrhs*C  bottom data coefficients
-  double* sGd = sm + a.off_gd;         // CH*nrhs    Dirichlet data coefficients
-  double* sY = sm + a.off_y;           // nrhs*C*nb  outflow coefficient vectors
-  double* sRD = sm + a.off_rd;         // nb         reciprocal pivots
+  T* sA = reinterpret_cast<T*>(sm);                  // nb*nb      assembled A, then LU factors
+  T* sb = reinterpret_cast<T*>(sm + a.off_b);        // nrhs*nb    assembled b, then x
+  T* sPG = reinterpret_cast<T*>(sm + a.off_pg);      // npair      this CTA: G (top)
+  T* sPH = reinterpret_cast<T*>(sm + a.off_ph);      // DIM*npair  this CTA: H_m
+  T* sPGb = reinterpret_cast<T*>(sm + a.off_pgb);    // npair      this CTA: G (bottom, recovery)
+  T* sPM = reinterpret_cast<T*>(sm + a.off_pm);      // nmom       this CTA: moments (gamma, alpha, beta_m) per rhs
+  T* sPD = reinterpret_cast<T*>(sm + a.off_pd);      // nb*nb      this CTA: Dirichlet A part
+  T* sPBD = reinterpret_cast<T*>(sm + a.off_pbd);    // nrhs*nb    this CTA: Dirichlet b part
+  T* sSG = reinterpret_cast<T*>(sm + a.off_sg);      // (DIM+2)*npair  summed G, H_m, Gbot
+  T* sSM = reinterpret_cast<T*>(sm + a.off_sm);      // nmom       summed moments
+  T* sF = reinterpret_cast<T*>(sm + a.off_f);        // npair      facet Gram
+  T* sDel = reinterpret_cast<T*>(sm + a.off_del);    // nrhs*nb    facet moments delta
+  T* sU = reinterpret_cast<T*>(sm + a.off_u);        // 2*CH*nb    U-values (scaled) per (side, point)
+  T* sM = reinterpret_cast<T*>(sm + a.off_mono);     // 2*CH*mono_stride
+  T* sCB = reinterpret_cast<T*>(sm + a.off_cb);      // CH*nrhs*C  bottom data coefficients
+  T* sGd = reinterpret_cast<T*>(sm + a.off_gd);      // CH*nrhs    Dirichlet data coefficients
+  T* sY = reinterpret_cast<T*>(sm + a.off_y);        // nrhs*C*nb  outflow coefficient vectors
+  double* sRD = sm + a.off_rd;                       // nb         reciprocal pivots (binary64 path)
 
   // ---------------- phase 0: tent and patch geometry ----------------
   if (tid == 0) {
@@ -292,7 +404,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer_fp64(const KArgs a, const
     for (int d = 0; d < DIM; ++d) s_xv[d] = a.X[(int64_t)v * DIM + d];
     s_nfac = a.vfac_ptr[v + 1] - a.vfac_ptr[v];
   }
-  for (int id = tid; id < nmom; id += blockDim.x) sPM[id] = 0.0;
+  for (int id = tid; id < nmom; id += blockDim.x) sPM[id] = R::zero();
   __syncthreads();
   const int P = s_P, v = s_v, nfac = s_nfac;
   for (int k = tid; k < P; k += blockDim.x) {
@@ -353,7 +465,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer_fp64(const KArgs a, const
   }
   // Gram pairs owned by this thread (upper triangle, i <= j, row-major order)
   int pi[kMaxPair], pj[kMaxPair];
-  double aK[kMaxPair], aG[kMaxPair], aH[kMaxPair][DIM], aB[kMaxPair];
+  T aK[kMaxPair], aG[kMaxPair], aH[kMaxPair][DIM], aB[kMaxPair];
 #pragma unroll
   for (int s = 0; s < kMaxPair; ++s) {
     const int id = tid + s * kThreads;
@@ -368,9 +480,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer_fp64(const KArgs a, const
     }
     pi[s] = i;
     pj[s] = j;
-    aK[s] = aG[s] = aB[s] = 0.0;
+    aK[s] = aG[s] = aB[s] = R::zero();
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) aH[s][d] = 0.0;
+    for (int d = 0; d < DIM; ++d) aH[s][d] = R::zero();
   }
   __syncthreads();
 
@@ -394,11 +506,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer_fp64(const KArgs a, const
           for (int d = 0; d < DIM; ++d) x[d] = fma(l, s_X[k][i][d], x[d]);
           tt = fma(l, side == 0 ? s_tt[k][i] : s_tb[k][i], tt);
         }
-        double xh[DIM];
-        for (int d = 0; d < DIM; ++d) xh[d] = (x[d] - s_xv[d]) * ih;
-        const double th = c * (tt - tc) * ih;
+        T xh[DIM];
+        for (int d = 0; d < DIM; ++d) xh[d] = R::from((x[d] - s_xv[d]) * ih);
+        const T th = R::from(c * (tt - tc) * ih);
         const double sw = __ldg(a.sqw + q) * s_sdet[k];
-        eval_uvalues<DIM>(a, th, xh, sM + tid * a.mono_stride, sw, sU + (size_t)tid * nb);
+        eval_uvalues<DIM, T>(a, th, xh, sM + tid * a.mono_stride, R::from(sw), sU + (size_t)tid * nb);
         if (side == 1) {
           const int el = s_el[k];
           for (int r = 0; r < nrhs; ++r) {
@@ -406,10 +518,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer_fp64(const KArgs a, const
             const double Ub = f[0], vb = f[1];
             double sg = 0.0;
             for (int d = 0; d < DIM; ++d) sg = fma(f[2 + d], s_gb[k][d], sg);
-            double* cb = sCB + ((size_t)ql * nrhs + r) * C;
-            cb[0] = sw * Ub;                       // gamma
-            cb[1] = sw * (ic2 * vb - sg);          // alpha
-            for (int d = 0; d < DIM; ++d) cb[2 + d] = sw * (f[2 + d] - vb * s_gb[k][d]);   // beta_m
+            T* cb = sCB + ((size_t)ql * nrhs + r) * C;
+            cb[0] = R::from(sw * Ub);                       // gamma
+            cb[1] = R::from(sw * (ic2 * vb - sg));          // alpha
+            for (int d = 0; d < DIM; ++d) cb[2 + d] = R::from(sw * (f[2 + d] - vb * s_gb[k][d]));   // beta_m
           }
         }
       }
@@ -419,61 +531,67 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer_fp64(const KArgs a, const
     for (int ql = 0; ql < nq; ++ql) {
       const int k = (base + ql) / Q;
       if (k != curk) {
+        T g[DIM];
+        for (int d = 0; d < DIM; ++d) g[d] = R::from(s_gt[curk][d]);
 #pragma unroll
         for (int s = 0; s < kMaxPair; ++s) {
-          aG[s] += aK[s];
+          aG[s] = R::add(aG[s], aK[s]);
 #pragma unroll
-          for (int d = 0; d < DIM; ++d) aH[s][d] = fma(s_gt[curk][d], aK[s], aH[s][d]);
-          aK[s] = 0.0;
+          for (int d = 0; d < DIM; ++d) aH[s][d] = R::fma(g[d], aK[s], aH[s][d]);
+          aK[s] = R::zero();
         }
         curk = k;
       }
-      const double* ut = sU + (size_t)ql * nb;
-      const double* ub = sU + (size_t)(CH + ql) * nb;
+      const T* ut = sU + (size_t)ql * nb;
+      const T* ub = sU + (size_t)(CH + ql) * nb;
 #pragma unroll
       for (int s = 0; s < kMaxPair; ++s) {
         if (tid + s * kThreads < npair) {
-          aK[s] = fma(ut[pi[s]], ut[pj[s]], aK[s]);
-          aB[s] = fma(ub[pi[s]], ub[pj[s]], aB[s]);
+          aK[s] = R::fma(ut[pi[s]], ut[pj[s]], aK[s]);
+          aB[s] = R::fma(ub[pi[s]], ub[pj[s]], aB[s]);
         }
       }
     }
     // (c) moments of the bottom data
     for (int id = tid; id < nmom; id += blockDim.x) {
       const int r = id / (C * nb), rem = id % (C * nb), cc = rem / nb, i = rem % nb;
-      double t = sPM[id];
+      T t = sPM[id];
       for (int ql = 0; ql < nq; ++ql)
-        t = fma(sCB[((size_t)ql * nrhs + r) * C + cc], sU[(size_t)(CH + ql) * nb + i], t);
+        t = R::fma(sCB[((size_t)ql * nrhs + r) * C + cc], sU[(size_t)(CH + ql) * nb + i], t);
       sPM[id] = t;
     }
     __syncthreads();
   }
   // publish this CTA's Grams
+  {
+    T g[DIM];
+    for (int d = 0; d < DIM; ++d) g[d] = R::from(q1 > q0 ? s_gt[curk][d] : 0.0);
 #pragma unroll
-  for (int s = 0; s < kMaxPair; ++s) {
-    const int id = tid + s * kThreads;
-    if (id < npair) {
-      sPG[id] = aG[s] + aK[s];
+    for (int s = 0; s < kMaxPair; ++s) {
+      const int id = tid + s * kThreads;
+      if (id < npair) {
+        sPG[id] = R::add(aG[s], aK[s]);
 #pragma unroll
-      for (int d = 0; d < DIM; ++d) sPH[d * npair + id] = (q1 > q0) ? fma(s_gt[curk][d], aK[s], aH[s][d]) : aH[s][d];
-      sPGb[id] = aB[s];
+        for (int d = 0; d < DIM; ++d) sPH[d * npair + id] = R::fma(g[d], aK[s], aH[s][d]);
+        sPGb[id] = aB[s];
+      }
     }
   }
 
   // ---------------- phase 2: Dirichlet faces (this CTA's slice of each facet's points) ----------------
   if (nfac > 0) {
-    for (int id = tid; id < nb * nb; id += blockDim.x) sPD[id] = 0.0;
+    for (int id = tid; id < nb * nb; id += blockDim.x) sPD[id] = R::zero();
     for (int id = tid; id < nrhs * nb; id += blockDim.x) {
-      sPBD[id] = 0.0;
-      sDel[id] = 0.0;
+      sPBD[id] = R::zero();
+      sDel[id] = R::zero();
     }
     const int fsl = (Q + CS - 1) / CS;
     const int f0 = min(Q, rank * fsl), f1 = min(Q, f0 + fsl);
     __syncthreads();
     for (int f = 0; f < nfac; ++f) {
-      double aF[kMaxPair];
+      T aF[kMaxPair];
 #pragma unroll
-      for (int s = 0; s < kMaxPair; ++s) aF[s] = 0.0;
+      for (int s = 0; s < kMaxPair; ++s) aF[s] = R::zero();
       for (int base = f0; base < f1; base += CH) {
         const int nq = min(CH, f1 - base);
         if (tid < nq) {
@@ -484,26 +602,26 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer_fp64(const KArgs a, const
             const double l = __ldg(a.bary + q * NV + i);
             for (int d = 0; d <= DIM; ++d) xt[d] = fma(l, s_fP[f][i][d], xt[d]);
           }
-          double xh[DIM];
-          for (int d = 0; d < DIM; ++d) xh[d] = (xt[d] - s_xv[d]) * ih;
-          const double th = c * (xt[DIM] - tc) * ih;
+          T xh[DIM];
+          for (int d = 0; d < DIM; ++d) xh[d] = R::from((xt[d] - s_xv[d]) * ih);
+          const T th = R::from(c * (xt[DIM] - tc) * ih);
           const double sw = sqrt(__ldg(a.wref + q) * s_fscale[f]);
-          eval_uvalues<DIM>(a, th, xh, sM + tid * a.mono_stride, sw, sU + (size_t)tid * nb);
+          eval_uvalues<DIM, T>(a, th, xh, sM + tid * a.mono_stride, R::from(sw), sU + (size_t)tid * nb);
           const long long goff = a.tent_gdoff[tent] + (long long)f * Q + q;
           for (int r = 0; r < nrhs; ++r)
-            sGd[tid * nrhs + r] = (a.gD != nullptr) ? sw * a.gD[(long long)r * a.n_bnd + goff] : 0.0;
+            sGd[tid * nrhs + r] = R::from((a.gD != nullptr) ? sw * a.gD[(long long)r * a.n_bnd + goff] : 0.0);
         }
         __syncthreads();
         for (int ql = 0; ql < nq; ++ql) {
-          const double* u = sU + (size_t)ql * nb;
+          const T* u = sU + (size_t)ql * nb;
 #pragma unroll
           for (int s = 0; s < kMaxPair; ++s)
-            if (tid + s * kThreads < npair) aF[s] = fma(u[pi[s]], u[pj[s]], aF[s]);
+            if (tid + s * kThreads < npair) aF[s] = R::fma(u[pi[s]], u[pj[s]], aF[s]);
         }
         for (int id = tid; id < nrhs * nb; id += blockDim.x) {
           const int r = id / nb, i = id % nb;
-          double t = sDel[id];
-          for (int ql = 0; ql < nq; ++ql) t = fma(sGd[ql * nrhs + r], sU[(size_t)ql * nb + i], t);
+          T t = sDel[id];
+          for (int ql = 0; ql < nq; ++ql) t = R::fma(sGd[ql * nrhs + r], sU[(size_t)ql * nb + i], t);
           sDel[id] = t;
         }
         __syncthreads();
@@ -512,22 +630,27 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer_fp64(const KArgs a, const
       for (int s = 0; s < kMaxPair; ++s)
         if (tid + s * kThreads < npair) sF[tid + s * kThreads] = aF[s];
       __syncthreads();
-      const double ac = a.alpha * c * ih;
+      const T ac = R::from(a.alpha * c * ih), cih = R::from(c * ih);
+      T mn[DIM], pn[DIM];
+      for (int d = 0; d < DIM; ++d) {
+        mn[d] = R::from(-ih * s_fn[f][d]);
+        pn[d] = R::from(ih * s_fn[f][d]);
+      }
       for (int id = tid; id < nb * nb; id += blockDim.x) {
         const int i = id / nb, j = id % nb;
-        double t = ac * congruence<DIM>(a, i, 0, j, 0, sF, nb);
-        for (int d = 0; d < DIM; ++d) t = fma(-ih * s_fn[f][d], congruence<DIM>(a, i, 0, j, 1 + d, sF, nb), t);
-        sPD[id] = fma(c * ih, t, sPD[id]);
+        T t = R::mul(ac, congruence<DIM, T>(a, i, 0, j, 0, sF, nb));
+        for (int d = 0; d < DIM; ++d) t = R::fma(mn[d], congruence<DIM, T>(a, i, 0, j, 1 + d, sF, nb), t);
+        sPD[id] = R::fma(cih, t, sPD[id]);
       }
       for (int id = tid; id < nrhs * nb; id += blockDim.x) {
         const int r = id / nb, i = id % nb;
-        const double* del = sDel + (size_t)r * nb;
-        double t = ac * rel_apply<DIM>(a, i, 0, del);
-        for (int d = 0; d < DIM; ++d) t = fma(ih * s_fn[f][d], rel_apply<DIM>(a, i, 1 + d, del), t);
-        sPBD[id] += t;
+        const T* del = sDel + (size_t)r * nb;
+        T t = R::mul(ac, rel_apply<DIM, T>(a, i, 0, del));
+        for (int d = 0; d < DIM; ++d) t = R::fma(pn[d], rel_apply<DIM, T>(a, i, 1 + d, del), t);
+        sPBD[id] = R::add(sPBD[id], t);
       }
       __syncthreads();
-      for (int id = tid; id < nrhs * nb; id += blockDim.x) sDel[id] = 0.0;
+      for (int id = tid; id < nrhs * nb; id += blockDim.x) sDel[id] = R::zero();
       __syncthreads();
     }
   }
@@ -536,146 +659,280 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer_fp64(const KArgs a, const
   cluster.sync();
   for (int id = tid; id < (DIM + 2) * npair; id += blockDim.x) {
     const int blk = id / npair, pid = id % npair;   // 0: G, 1..DIM: H_m, DIM+1: Gbot
-    const double* src = (blk == 0) ? sPG : (blk <= DIM ? sPH + (blk - 1) * npair : sPGb);
-    double t = 0.0;
-    for (int r = 0; r < CS; ++r) t += cluster.map_shared_rank(src, r)[pid];
+    const T* src = (blk == 0) ? sPG : (blk <= DIM ? sPH + (blk - 1) * npair : sPGb);
+    T t = R::zero();
+    for (int r = 0; r < CS; ++r) t = R::add(t, cluster.map_shared_rank(src, r)[pid]);
     sSG[id] = t;
   }
   for (int id = tid; id < nmom; id += blockDim.x) {
-    double t = 0.0;
-    for (int r = 0; r < CS; ++r) t += cluster.map_shared_rank(sPM, r)[id];
+    T t = R::zero();
+    for (int r = 0; r < CS; ++r) t = R::add(t, cluster.map_shared_rank(sPM, r)[id]);
     sSM[id] = t;
   }
   for (int id = tid; id < nb * nb; id += blockDim.x) {
-    double t = 0.0;
+    T t = R::zero();
     if (nfac > 0)
-      for (int r = 0; r < CS; ++r) t += cluster.map_shared_rank(sPD, r)[id];
+      for (int r = 0; r < CS; ++r) t = R::add(t, cluster.map_shared_rank(sPD, r)[id]);
     sA[id] = t;
   }
   for (int id = tid; id < nrhs * nb; id += blockDim.x) {
-    double t = 0.0;
+    T t = R::zero();
     if (nfac > 0)
-      for (int r = 0; r < CS; ++r) t += cluster.map_shared_rank(sPBD, r)[id];
+      for (int r = 0; r < CS; ++r) t = R::add(t, cluster.map_shared_rank(sPBD, r)[id]);
     sb[id] = t;
   }
   cluster.sync();   // no CTA leaves or reuses its partials while another still reads them
   {
-    const double* SG = sSG;
-    const double* SGb = sSG + (DIM + 1) * npair;
-    const double ih2 = ih * ih;
+    const T* SG = sSG;
+    const T* SGb = sSG + (DIM + 1) * npair;
+    const T ih2 = R::from(ih * ih), cc_ = R::from(c), cih = R::from(c * ih), mih = R::from(-ih);
     for (int id = tid; id < nb * nb; id += blockDim.x) {
       const int i = id / nb, j = id % nb;
-      double t = congruence<DIM>(a, i, 0, j, 0, SG, nb);
+      T t = congruence<DIM, T>(a, i, 0, j, 0, SG, nb);
       for (int d = 0; d < DIM; ++d) {
-        const double* H = sSG + (1 + d) * npair;
-        t += congruence<DIM>(a, i, 1 + d, j, 1 + d, SG, nb);
-        t = fma(c, congruence<DIM>(a, i, 1 + d, j, 0, H, nb) + congruence<DIM>(a, i, 0, j, 1 + d, H, nb), t);
+        const T* H = sSG + (1 + d) * npair;
+        t = R::add(t, congruence<DIM, T>(a, i, 1 + d, j, 1 + d, SG, nb));
+        t = R::fma(cc_, R::add(congruence<DIM, T>(a, i, 1 + d, j, 0, H, nb), congruence<DIM, T>(a, i, 0, j, 1 + d, H, nb)), t);
       }
-      sA[id] += fma(ih2, t, SGb[pair_index(i, j, nb)]);
+      sA[id] = R::add(sA[id], R::fma(ih2, t, SGb[pair_index(i, j, nb)]));
     }
     for (int id = tid; id < nrhs * nb; id += blockDim.x) {
       const int r = id / nb, i = id % nb;
-      const double* M = sSM + (size_t)r * C * nb;   // gamma, alpha, beta_1..beta_n
-      double t = M[i] + c * ih * rel_apply<DIM>(a, i, 0, M + nb);
-      for (int d = 0; d < DIM; ++d) t = fma(-ih, rel_apply<DIM>(a, i, 1 + d, M + (2 + d) * nb), t);
-      sb[id] += t;
+      const T* M = sSM + (size_t)r * C * nb;   // gamma, alpha, beta_1..beta_n
+      T t = R::fma(cih, rel_apply<DIM, T>(a, i, 0, M + nb), M[i]);
+      for (int d = 0; d < DIM; ++d) t = R::fma(mih, rel_apply<DIM, T>(a, i, 1 + d, M + (2 + d) * nb), t);
+      sb[id] = R::add(sb[id], t);
     }
   }
   __syncthreads();
 
-  // ---------------- phase 3: LU (no pivoting for interior tents: A is SPD), solve ----------------
-  const int lane = tid & 31, warp = tid >> 5;
+  // ---------------- phase 3: solve ----------------
   const bool pivoting = (nfac > 0);
-  for (int k = 0; k < nb; ++k) {
-    if (pivoting) {
+  if constexpr (!MIXED) {
+    // LU (no pivoting for interior tents: A is SPD), forward elimination of b alongside
+    for (int k = 0; k < nb; ++k) {
+      if (pivoting) {
+        if (warp == 0) {
+          // |a_ik| compared through the bit patterns (non-negative doubles order as integers)
+          unsigned long long best = 0ull;
+          int bi = k;
+          for (int i = k + lane; i < nb; i += 32) {
+            const unsigned long long bits = (unsigned long long)__double_as_longlong(fabs(sA[i * nb + k]));
+            if (bits > best || (bits == best && i < bi)) {
+              best = bits;
+              bi = i;
+            }
+          }
+          for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long ob = __shfl_down_sync(0xffffffffu, best, o);
+            const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+            if (ob > best || (ob == best && oi < bi)) {
+              best = ob;
+              bi = oi;
+            }
+          }
+          if (lane == 0) s_piv = bi;
+        }
+        __syncthreads();
+        const int pr = s_piv;
+        if (pr != k) {
+          for (int j = tid; j < nb; j += blockDim.x) {
+            const double t = sA[k * nb + j];
+            sA[k * nb + j] = sA[pr * nb + j];
+            sA[pr * nb + j] = t;
+          }
+          for (int r = tid; r < nrhs; r += blockDim.x) {
+            const double t = sb[r * nb + k];
+            sb[r * nb + k] = sb[r * nb + pr];
+            sb[r * nb + pr] = t;
+          }
+        }
+        __syncthreads();
+      }
+      if (tid == 0) {
+        double piv = sA[k * nb + k];
+        if (!(fabs(piv) > 0.0) || !isfinite(piv)) {
+          if (rank == 0) flag_error(a, TP_ERR_SINGULAR, tent);
+          piv = 1.0;
+        }
+        sRD[k] = recip(piv);
+      }
+      __syncthreads();
+      const double rp = sRD[k];
+      const int rem = nb - k - 1;
+      for (int i = k + 1 + tid; i < nb; i += blockDim.x) sA[i * nb + k] *= rp;   // multipliers
+      __syncthreads();
+      for (int id = tid; id < rem * (rem + nrhs); id += blockDim.x) {
+        const int i = k + 1 + id / (rem + nrhs), jj = id % (rem + nrhs);
+        const double l = sA[i * nb + k];
+        if (jj < rem) {
+          const int j = k + 1 + jj;
+          sA[i * nb + j] = fma(-l, sA[k * nb + j], sA[i * nb + j]);
+        } else {
+          const int r = jj - rem;
+          sb[r * nb + i] = fma(-l, sb[r * nb + k], sb[r * nb + i]);
+        }
+      }
+      __syncthreads();
+    }
+    for (int k = nb - 1; k >= 0; --k) {
+      for (int r = tid; r < nrhs; r += blockDim.x) sb[r * nb + k] *= sRD[k];
+      __syncthreads();
+      for (int id = tid; id < k * nrhs; id += blockDim.x) {
+        const int r = id / k, i = id % k;
+        sb[r * nb + i] = fma(-sA[i * nb + k], sb[r * nb + k], sb[r * nb + i]);
+      }
+      __syncthreads();
+    }
+  } else {
+    float* sAL = reinterpret_cast<float*>(sm + a.off_al);   // nb*nb   equilibrated binary32 LU
+    float* sEq = reinterpret_cast<float*>(sm + a.off_eq);   // nb      equilibration scales
+    int* sPerm = reinterpret_cast<int*>(sm + a.off_perm);   // nb      row interchanges
+    float* sZ = reinterpret_cast<float*>(sm + a.off_z);     // nrhs*nb correction (binary32)
+    T* sX = reinterpret_cast<T*>(sm + a.off_x);             // nrhs*nb iterate
+    for (int i = tid; i < nb; i += blockDim.x) {
+      const float d = fabsf(sA[i * nb + i].hi);
+      sEq[i] = (d > 0.f && isfinite(d)) ? rsqrtf(d) : 1.f;
+    }
+    for (int id = tid; id < nrhs * nb; id += blockDim.x) sX[id] = R::zero();
+    __syncthreads();
+    for (int id = tid; id < nb * nb; id += blockDim.x) sAL[id] = sA[id].hi * sEq[id / nb] * sEq[id % nb];
+    __syncthreads();
+    // binary32 LU of D A D by warp 0 (lane owns rows lane, lane+32, ...)
+    if (warp == 0) {
+      for (int k = 0; k < nb; ++k) {
+        int pr = k;
+        if (pivoting) {
+          float best = -1.f;
+          int bi = k;
+          for (int i = k + lane; i < nb; i += 32) {
+            const float val = fabsf(sAL[i * nb + k]);
+            if (val > best) {
+              best = val;
+              bi = i;
+            }
+          }
+          for (int o = 16; o > 0; o >>= 1) {
+            const float ob = __shfl_down_sync(0xffffffffu, best, o);
+            const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+            if (ob > best || (ob == best && oi < bi)) {
+              best = ob;
+              bi = oi;
+            }
+          }
+          pr = __shfl_sync(0xffffffffu, bi, 0);
+          if (pr != k)
+            for (int j = lane; j < nb; j += 32) {
+              const float t = sAL[k * nb + j];
+              sAL[k * nb + j] = sAL[pr * nb + j];
+              sAL[pr * nb + j] = t;
+            }
+          __syncwarp();
+        }
+        if (lane == 0) sPerm[k] = pr;
+        float piv = sAL[k * nb + k];
+        if (!(fabsf(piv) > 0.f) || !isfinite(piv)) {
+          if (lane == 0 && rank == 0) flag_error(a, TP_ERR_SINGULAR, tent);
+          piv = 1.f;
+        }
+        const float rp = 1.f / piv;
+        for (int i = k + 1 + lane; i < nb; i += 32) {
+          const float l = sAL[i * nb + k] * rp;
+          sAL[i * nb + k] = l;
+          for (int j = k + 1; j < nb; ++j) sAL[i * nb + j] = fmaf(-l, sAL[k * nb + j], sAL[i * nb + j]);
+        }
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    // refinement: r = b - A x (float-float), z = (D A D)^-1 D r, x += D z
+    float prev = 3.4e38f;
+    for (int it = 0; it < kMaxRefine; ++it) {
+      for (int id = tid; id < nrhs * nb; id += blockDim.x) {
+        const int r = id / nb, i = id % nb;
+        T t = sb[id];
+        const T* xr = sX + (size_t)r * nb;
+        for (int j = 0; j < nb; ++j) t = R::sub(t, R::mul(sA[i * nb + j], xr[j]));
+        sZ[id] = sEq[i] * t.hi;
+      }
+      __syncthreads();
       if (warp == 0) {
-        // |a_ik| compared through the bit patterns (non-negative doubles order as integers)
-        unsigned long long best = 0ull;
-        int bi = k;
-        for (int i = k + lane; i < nb; i += 32) {
-          const unsigned long long bits = (unsigned long long)__double_as_longlong(fabs(sA[i * nb + k]));
-          if (bits > best || (bits == best && i < bi)) {
-            best = bits;
-            bi = i;
+        for (int r = 0; r < nrhs; ++r) {
+          float* z = sZ + (size_t)r * nb;
+          if (lane == 0)   // row interchanges in factorisation order (L is stored permuted)
+            for (int k = 0; k < nb; ++k) {
+              const int pr = sPerm[k];
+              if (pr != k) {
+                const float t = z[k];
+                z[k] = z[pr];
+                z[pr] = t;
+              }
+            }
+          __syncwarp();
+          for (int k = 0; k < nb; ++k) {   // L (unit lower)
+            const float zk = z[k];
+            for (int i = k + 1 + lane; i < nb; i += 32) z[i] = fmaf(-sAL[i * nb + k], zk, z[i]);
+            __syncwarp();
           }
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-          const unsigned long long ob = __shfl_down_sync(0xffffffffu, best, o);
-          const int oi = __shfl_down_sync(0xffffffffu, bi, o);
-          if (ob > best || (ob == best && oi < bi)) {
-            best = ob;
-            bi = oi;
+          for (int k = nb - 1; k >= 0; --k) {   // U
+            if (lane == 0) z[k] = z[k] / sAL[k * nb + k];
+            __syncwarp();
+            const float zk = z[k];
+            for (int i = lane; i < k; i += 32) z[i] = fmaf(-sAL[i * nb + k], zk, z[i]);
+            __syncwarp();
           }
-        }
-        if (lane == 0) s_piv = bi;
-      }
-      __syncthreads();
-      const int pr = s_piv;
-      if (pr != k) {
-        for (int j = tid; j < nb; j += blockDim.x) {
-          const double t = sA[k * nb + j];
-          sA[k * nb + j] = sA[pr * nb + j];
-          sA[pr * nb + j] = t;
-        }
-        for (int r = tid; r < nrhs; r += blockDim.x) {
-          const double t = sb[r * nb + k];
-          sb[r * nb + k] = sb[r * nb + pr];
-          sb[r * nb + pr] = t;
         }
       }
       __syncthreads();
-    }
-    if (tid == 0) {
-      double piv = sA[k * nb + k];
-      if (!(fabs(piv) > 0.0) || !isfinite(piv)) {
-        if (rank == 0) flag_error(a, TP_ERR_SINGULAR, tent);
-        piv = 1.0;
+      float dmax = 0.f, xmax = 0.f;
+      for (int id = tid; id < nrhs * nb; id += blockDim.x) {
+        const float dx = sEq[id % nb] * sZ[id];
+        sX[id] = R::add(sX[id], T{dx, 0.f});
+        dmax = fmaxf(dmax, fabsf(dx));
+        xmax = fmaxf(xmax, fabsf(sX[id].hi));
       }
-      sRD[k] = recip(piv);
-    }
-    __syncthreads();
-    const double rp = sRD[k];
-    const int rem = nb - k - 1;
-    for (int i = k + 1 + tid; i < nb; i += blockDim.x) sA[i * nb + k] *= rp;   // multipliers
-    __syncthreads();
-    for (int id = tid; id < rem * (rem + nrhs); id += blockDim.x) {
-      const int i = k + 1 + id / (rem + nrhs), jj = id % (rem + nrhs);
-      const double l = sA[i * nb + k];
-      if (jj < rem) {
-        const int j = k + 1 + jj;
-        sA[i * nb + j] = fma(-l, sA[k * nb + j], sA[i * nb + j]);
-      } else {
-        const int r = jj - rem;
-        sb[r * nb + i] = fma(-l, sb[r * nb + k], sb[r * nb + i]);
+      for (int o = 16; o > 0; o >>= 1) {
+        dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+        xmax = fmaxf(xmax, __shfl_xor_sync(0xffffffffu, xmax, o));
       }
+      if (lane == 0) {
+        s_red[0][warp] = dmax;
+        s_red[1][warp] = xmax;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        float dm = 0.f, xm = 0.f;
+        for (int w = 0; w < kThreads / 32; ++w) {
+          dm = fmaxf(dm, s_red[0][w]);
+          xm = fmaxf(xm, s_red[1][w]);
+        }
+        // stop once the correction is at the float-float resolution or stops shrinking
+        const bool done = (dm <= 4e-15f * xm) || (it >= 2 && dm > 0.5f * prev);
+        s_stop = done ? 1 : 0;
+        if (it == kMaxRefine - 1 && dm > 1e-9f * xm && rank == 0) flag_error(a, TP_ERR_NOCONV, tent);
+        s_red[0][0] = dm;
+      }
+      __syncthreads();
+      prev = s_red[0][0];
+      const int stop = s_stop;
+      __syncthreads();
+      if (stop) break;
     }
-    __syncthreads();
-  }
-  for (int k = nb - 1; k >= 0; --k) {
-    for (int r = tid; r < nrhs; r += blockDim.x) sb[r * nb + k] *= sRD[k];
-    __syncthreads();
-    for (int id = tid; id < k * nrhs; id += blockDim.x) {
-      const int r = id / k, i = id % k;
-      sb[r * nb + i] = fma(-sA[i * nb + k], sb[r * nb + k], sb[r * nb + i]);
-    }
+    for (int id = tid; id < nrhs * nb; id += blockDim.x) sb[id] = sX[id];
     __syncthreads();
   }
 
   // ---------------- phase 4: outflow at this CTA's top points ----------------
   // coefficient vectors of U_h, v_h, sigma_h in terms of U-values: y = D^T x
-  for (int id = tid; id < nmom; id += blockDim.x) {
-    const int r = id / (C * nb), rem = id % (C * nb), cc = rem / nb, kk = rem % nb;
-    double t;
-    if (cc == 0) {
-      t = sb[r * nb + kk];
-    } else {
-      const int e0 = __ldg(a.relT_ptr + kk * (DIM + 1) + cc - 1);
-      const int e1 = __ldg(a.relT_ptr + kk * (DIM + 1) + cc);
-      t = 0.0;
-      for (int e = e0; e < e1; ++e) t = fma(__ldg(a.relT_fac + e), sb[r * nb + __ldg(a.relT_dst + e)], t);
-      t *= (cc == 1) ? c * ih : -ih;
+  {
+    const T cih = R::from(c * ih), mih = R::from(-ih);
+    for (int id = tid; id < nmom; id += blockDim.x) {
+      const int r = id / (C * nb), rem = id % (C * nb), cc = rem / nb, kk = rem % nb;
+      T t;
+      if (cc == 0) t = sb[r * nb + kk];
+      else t = R::mul(cc == 1 ? cih : mih, relT_apply<DIM, T>(a, kk, cc - 1, sb + (size_t)r * nb));
+      sY[id] = t;
     }
-    sY[id] = t;
   }
   for (int base = q0; base < q1; base += 2 * CH) {
     const int nq = min(2 * CH, q1 - base);
@@ -688,20 +945,20 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer_fp64(const KArgs a, const
         for (int d = 0; d < DIM; ++d) x[d] = fma(l, s_X[k][i][d], x[d]);
         tt = fma(l, s_tt[k][i], tt);
       }
-      double xh[DIM];
-      for (int d = 0; d < DIM; ++d) xh[d] = (x[d] - s_xv[d]) * ih;
-      const double th = c * (tt - tc) * ih;
-      eval_uvalues<DIM, false>(a, th, xh, sM + tid * a.mono_stride, 1.0, sU + (size_t)tid * nb);
+      T xh[DIM];
+      for (int d = 0; d < DIM; ++d) xh[d] = R::from((x[d] - s_xv[d]) * ih);
+      const T th = R::from(c * (tt - tc) * ih);
+      eval_uvalues<DIM, T, false>(a, th, xh, sM + tid * a.mono_stride, R::one(), sU + (size_t)tid * nb);
     }
     __syncthreads();
     for (int id = tid; id < nq * nrhs * C; id += blockDim.x) {
       const int ql = id / (nrhs * C), rc = id % (nrhs * C), r = rc / C, cc = rc % C;
       const int qg = base + ql, k = qg / Q, q = qg % Q;
-      const double* u = sU + (size_t)ql * nb;
-      const double* y = sY + ((size_t)r * C + cc) * nb;
-      double t = 0.0;
-      for (int j = 0; j < nb; ++j) t = fma(y[j], u[j], t);
-      a.front[(((int64_t)r * a.ne + s_el[k]) * Q + q) * C + cc] = t;
+      const T* u = sU + (size_t)ql * nb;
+      const T* y = sY + ((size_t)r * C + cc) * nb;
+      T t = R::zero();
+      for (int j = 0; j < nb; ++j) t = R::fma(y[j], u[j], t);
+      a.front[(((int64_t)r * a.ne + s_el[k]) * Q + q) * C + cc] = R::to(t);
     }
     __syncthreads();
   }
@@ -794,6 +1051,7 @@ struct tp_ctx {
   cudaStream_t cap_stream = nullptr;
   cudaStream_t last_stream = nullptr;
   int n_sm = 152, max_cs = 1;
+  bool mixed = false;
   std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
   int device = 0;
 };
@@ -813,7 +1071,9 @@ constexpr size_t kTwoPerSmSmem = 95 * 1024;  // plan that leaves room for two CT
 // the attribute is set to the plan's cap, so contexts of any size can share the kernel
 template <int DIM>
 int set_smem_attr() {
-  TP_CUDA_OK(cudaFuncSetAttribute(k_layer_fp64<DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  TP_CUDA_OK(cudaFuncSetAttribute(k_layer<DIM, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)kMaxDynSmem));
+  TP_CUDA_OK(cudaFuncSetAttribute(k_layer<DIM, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)kMaxDynSmem));
   return TP_OK;
 }
@@ -832,7 +1092,8 @@ cudaError_t launch_cluster(tp_ctx* ctx, int nt, int cs, int t0, cudaStream_t st)
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_layer_fp64<DIM>, ctx->args, t0);
+  if (ctx->mixed) return cudaLaunchKernelEx(&cfg, k_layer<DIM, true>, ctx->args, t0);
+  return cudaLaunchKernelEx(&cfg, k_layer<DIM, false>, ctx->args, t0);
 }
 
 // cluster size for a level of nt tents: a power of two <= max_cs with
@@ -872,9 +1133,9 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
     tp::set_error("tp_create: dim/p/n_vert mismatch between mesh, tents, basis and params");
     return TP_ERR_ARG;
   }
-  if (prm->precision != TP_FP64) {
-    tp::set_error("tp_create: only TP_FP64 is available in this build");
-    return TP_ERR_UNSUPPORTED;
+  if (prm->precision != TP_FP64 && prm->precision != TP_MIXED) {
+    tp::set_error("tp_create: precision must be TP_FP64 or TP_MIXED");
+    return TP_ERR_ARG;
   }
   auto* ctx = new tp_ctx();
   auto fail = [&](int rc) {
@@ -891,6 +1152,7 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
   ctx->C = n + 2;
   ctx->nrhs = prm->nrhs;
   ctx->alpha = prm->alpha;
+  ctx->mixed = (prm->precision == TP_MIXED);
   ctx->nv = T.nv;
   ctx->ne = T.ne;
   ctx->rule = tp::simplex_rule(n, basis->p + 1);
@@ -978,6 +1240,15 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
   double *dX, *dc, *dnrm, *dbary, *dw, *dsqw, *dttop, *dh, *dspc;
   int *del, *dsp, *dse, *dvp, *dvf, *dfv, *dtv, *dspp, *dspm, *dpar, *dvar, *drp, *drs, *dtp, *dtd;
   double *drf, *dtf;
+  float2* dcdd;
+  float *drff, *dtff;
+  std::vector<float2> coef_dd(basis->sp_coef.size());
+  for (size_t i = 0; i < coef_dd.size(); ++i) {
+    const float hi = (float)basis->sp_coef[i];
+    coef_dd[i] = make_float2(hi, (float)(basis->sp_coef[i] - (double)hi));
+  }
+  std::vector<float> rel_ff(basis->rel_fac.begin(), basis->rel_fac.end());
+  std::vector<float> relT_ff(basis->relT_fac.begin(), basis->relT_fac.end());
   long long* dgo;
   std::vector<double> sqw(Q);
   for (int q = 0; q < Q; ++q) sqw[q] = std::sqrt(ctx->rule.w[q]);
@@ -996,7 +1267,8 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
       (rc = ctx_upload(ctx, &dvar, basis->var)) || (rc = ctx_upload(ctx, &drp, basis->rel_ptr)) ||
       (rc = ctx_upload(ctx, &drs, basis->rel_src)) || (rc = ctx_upload(ctx, &drf, basis->rel_fac)) ||
       (rc = ctx_upload(ctx, &dtp, basis->relT_ptr)) || (rc = ctx_upload(ctx, &dtd, basis->relT_dst)) ||
-      (rc = ctx_upload(ctx, &dtf, basis->relT_fac)))
+      (rc = ctx_upload(ctx, &dtf, basis->relT_fac)) || (rc = ctx_upload(ctx, &dcdd, coef_dd)) ||
+      (rc = ctx_upload(ctx, &drff, rel_ff)) || (rc = ctx_upload(ctx, &dtff, relT_ff)))
     return fail(rc == TP_ERR_CUDA ? TP_ERR_OOM : rc);
   const size_t nfront = (size_t)ctx->nrhs * T.ne * Q * ctx->C;
   if (cudaMalloc(&ctx->d_front, nfront * sizeof(double)) != cudaSuccess ||
@@ -1053,6 +1325,9 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
   a.relT_ptr = dtp;
   a.relT_dst = dtd;
   a.relT_fac = dtf;
+  a.sp_coef_dd = dcdd;
+  a.rel_facf = drff;
+  a.relT_facf = dtff;
   a.tau = ctx->d_tau;
   a.front = ctx->d_front;
   a.gD = nullptr;
@@ -1093,6 +1368,12 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
     take(&a.off_gd, (size_t)CH * ctx->nrhs);
     take(&a.off_y, nmom);
     take(&a.off_rd, nb);
+    const size_t half_nb = ((size_t)nb + 1) / 2, half_rb = ((size_t)ctx->nrhs * nb + 1) / 2;
+    take(&a.off_al, ((size_t)nb * nb + 1) / 2);      // binary32 words, two per double slot
+    take(&a.off_eq, half_nb);
+    take(&a.off_perm, half_nb);
+    take(&a.off_z, half_rb);
+    take(&a.off_x, (size_t)ctx->nrhs * nb);
     return off * sizeof(double);
   };
   int CH = 0;

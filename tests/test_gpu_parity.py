@@ -24,11 +24,12 @@ def _rel(a, b):
 
 
 def _gpu_run(mesh, p, T, kappa, init, dirichlet, nrhs_inits=None, alpha=0.5, levels=None,
-             layerwise=False):
+             layerwise=False, precision="fp64"):
     import torch
     import paper_1907_02367_gb300 as pkg
     inits = nrhs_inits or [init]
-    s = pkg.Solver(mesh.coords, mesh.elems, mesh.c, p, T, kappa, alpha=alpha, nrhs=len(inits))
+    s = pkg.Solver(mesh.coords, mesh.elems, mesh.c, p, T, kappa, alpha=alpha, nrhs=len(inits),
+                   precision=precision)
     xq, wq = s.front_points()
     f0 = np.stack([np.asarray(f(xq)) for f in inits])
     front0 = torch.tensor(f0, dtype=torch.float64, device="cuda").contiguous()
@@ -215,3 +216,67 @@ def test_non_causal_pitch_is_reported(cuda_device):
     m = inputs.mesh_interval(4)
     s, got, tau, st = _gpu_run(m, 3, 0.5, 1.0, lambda x: inputs.plane_wave_1d(x, 0.0), None)
     assert st[0] == 2
+
+
+# ---------------------------------------------------------------------------
+# mixed path: float-float assembly, binary32 factorisation + refinement;
+# bar: relative L2 <= 1e-8 against the FP64 oracle
+# ---------------------------------------------------------------------------
+MIXED_TOL = 1e-8
+
+
+@pytest.mark.parametrize("name", WORKLOADS)
+def test_mixed_sweep_matches_oracle(cuda_device, name):
+    w = inputs.workload(name)
+    m = w.mesh
+    s, got, tau, st = _gpu_run(m, w.p, w.T, w.kappa, w.init, w.dirichlet, precision="mixed")
+    assert st == (0, 0)
+    ref, rtau, _ = _oracle(m, w.p, w.T, w.kappa, w.init, w.dirichlet)
+    assert np.array_equal(tau, rtau)
+    rel = _rel(got.reshape(ref.shape), ref)
+    assert rel <= MIXED_TOL, rel
+
+
+def test_mixed_full_size_2d(cuda_device):
+    w = inputs.workload("standing2d")
+    m = w.mesh
+    s, got, tau, st = _gpu_run(m, w.p, w.T, w.kappa, w.init, None, precision="mixed")
+    assert st == (0, 0)
+    ref, rtau, _ = _oracle(m, w.p, w.T, w.kappa, w.init, None)
+    rel = _rel(got.reshape(ref.shape), ref)
+    assert rel <= MIXED_TOL, rel
+
+
+@pytest.mark.parametrize("dim,p,which,cval", [(1, 5, 1, 2.0), (2, 4, 1, 1.0), (2, 5, 0, 0.5),
+                                              (3, 3, 1, 1.0)])
+def test_mixed_polynomial_reproduction(cuda_device, dim, p, which, cval):
+    mesh = {1: inputs.mesh_interval(6), 2: inputs.mesh_square(3, 0.2, seed=5),
+            3: inputs.mesh_cube(1, 0.0, seed=3)}[dim]
+    mesh.c[:] = cval
+    base = inputs.polynomial_solution(dim, which)
+
+    def sol(x, t):
+        out = base(x, cval * np.asarray(t, dtype=np.float64))
+        out[:, 1] *= cval
+        return out
+
+    T = 0.3 / cval
+    s, got, tau, st = _gpu_run(mesh, p, T, inputs.pitch_kappa(mesh), lambda x: sol(x, 0.0),
+                               lambda x, t: sol(x, t)[:, 1], precision="mixed")
+    assert st == (0, 0)
+    xq, _ = s.front_points()
+    ex = sol(xq, T)
+    assert np.abs(got.reshape(ex.shape) - ex).max() <= 1e-9 * max(1.0, np.abs(ex).max())
+
+
+def test_mixed_many_rhs(cuda_device):
+    m = inputs.mesh_square(4, 0.2, seed=6)
+    kappa = inputs.pitch_kappa(m)
+    inits = [inputs.gaussian_pulse((0.4, 0.5), 0.2), lambda x: inputs.standing_wave_2d(x, 0.0),
+             inputs.gaussian_pulse((0.6, 0.3), 0.15)]
+    s, got, tau, st = _gpu_run(m, 3, 0.3, kappa, None, None, nrhs_inits=inits, precision="mixed")
+    assert st == (0, 0)
+    got = got.reshape(len(inits), m.n_elem, -1, 4)
+    for r, f in enumerate(inits):
+        ref, _, _ = _oracle(m, 3, 0.3, kappa, f, None)
+        assert _rel(got[r], ref) <= MIXED_TOL, r
