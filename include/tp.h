@@ -140,6 +140,16 @@ int tp_advance(tp_ctx* ctx, int32_t level_begin, int32_t level_end, void* stream
  * - 2 v sigma.grad tau_K) for every rhs r; equals the paper's E on a flat
  * front.  d_out: device array of nrhs doubles. */
 int tp_energy(tp_ctx* ctx, double* d_out, void* stream);
+/* Adjoint sweep.  With the tents fixed and g_D = 0 the sweep is a linear map
+ * F: front(t = 0) -> front(T), a composition of the tent maps
+ * b = B f_bot, A x = b, f_top = E x of eq. (4.1) with the Section 5 recovery
+ * terms.  tp_adjoint applies F^* tent by tent in reverse level order
+ * (mu = A^-T E^T lambda_top, lambda_bot = B^T mu), in binary64:
+ * d_lambda_T (device, front layout, nrhs sets) is the gradient of a
+ * functional with respect to the final front, d_lambda_0 (device, same
+ * layout) receives its gradient with respect to the initial front.  The
+ * forward state is not touched; the reverse sweep is one CUDA graph. */
+int tp_adjoint(tp_ctx* ctx, const double* d_lambda_T, double* d_lambda_0, void* stream);
 /* Copies the front (device, front layout) and/or the vertex front times
  * (device, n_vert doubles); either may be NULL. */
 int tp_get_state(const tp_ctx* ctx, double* d_front, double* d_tau, void* stream);

@@ -1,0 +1,131 @@
+"""Adjoint of the tent sweep (TEST INFRASTRUCTURE; see oracle/__init__.py).
+
+With the space-time mesh fixed and g_D = 0, every tent maps the stored front
+values at its bottom points linearly to the values at its top points
+(Section 4.1, eq. (4.1) with the Section 5 recovery terms):
+
+    b = B f_bot,    A x = b,    f_top = E x,
+
+B the bottom-face bilinear form of eq. (4.1) as a map from the stored
+(U, v, sigma) values to the right-hand side, E the evaluation of
+(U_h, dU_h/dt, -grad U_h) at the top points.  The sweep is the composition
+of these maps in the pitched order, so its adjoint runs the tents in reverse
+order with
+
+    mu = A^-T (E^T lambda_top),    lambda_bot = B^T mu
+
+(the top and bottom points of a tent are the same stored front points, so
+lambda_bot overwrites lambda_top there).  The paper has no adjoint; this
+module writes the transpose of the oracle's own tent maps explicitly, and
+tests pin it with the dot-product identity <lambda, F f> = <F^* lambda, f>
+against oracle.tdg and with finite differences.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import basis as _basis
+from . import tdg as _tdg
+from . import quadrature as _quad
+
+
+def _tent_maps(coords, elems, c, p, lay, B, star, vfac, tau, v, t_top, alpha):
+    """A (nb x nb), Bmat (nb x P*Q*C), Emat (P*Q*C x nb) of one tent."""
+    n = coords.shape[1]
+    Q = lay.wq.shape[1]
+    t_bot = float(tau[v])
+    patch = star[v]
+    ct = float(c[patch][0])
+    c2 = 1.0 / (ct * ct)
+    pv = sorted({a for k in patch for a in elems[k].tolist()} - {v})
+    tv = [np.append(coords[v], t_bot), np.append(coords[v], t_top)]
+    tv += [np.append(coords[w], tau[w]) for w in pv]
+    h = _tdg.anisotropic_diameter(np.array(tv), ct)
+    xc, tc = coords[v], 0.5 * (t_bot + t_top)
+    ids = elems[patch]
+    tb = tau[ids]
+    tt = np.where(ids == v, t_top, tb)
+    Xk = coords[ids]
+    J = Xk[:, 1:, :] - Xk[:, :1, :]
+    g_b = np.linalg.solve(J, (tb[:, 1:] - tb[:, :1])[..., None])[..., 0]
+    g_t = np.linalg.solve(J, (tt[:, 1:] - tt[:, :1])[..., None])[..., 0]
+    x = lay.xq[patch].reshape(-1, n)
+    w = lay.wq[patch].reshape(-1)
+    gb = np.repeat(g_b, Q, axis=0)
+    gt = np.repeat(g_t, Q, axis=0)
+    Ut, Vt, St = B.eval_phys(x, (tt @ lay.bary.T).reshape(-1), xc, tc, h, ct)
+    Ub, Vb, Sb = B.eval_phys(x, (tb @ lay.bary.T).reshape(-1), xc, tc, h, ct)
+    Sgt = np.einsum("qdj,qd->qj", St, gt)
+    A = (w[:, None] * c2 * Vt).T @ Vt + np.einsum("q,qdi,qdj->ij", w, St, St)
+    A -= (w[:, None] * Sgt).T @ Vt + (w[:, None] * Vt).T @ Sgt
+    A += (w[:, None] * Ub).T @ Ub
+    _, wref_face, bary_face = _quad.simplex_rule(n, p + 1)
+    for (fac, nrm) in vfac[v]:
+        others = [a for a in fac if a != v]
+        Pf = [np.append(coords[v], t_bot), np.append(coords[v], t_top)]
+        Pf += [np.append(coords[a], tau[a]) for a in others]
+        Pf = np.array(Pf)
+        Ed = (Pf[1:] - Pf[0]).T
+        xt = bary_face @ Pf
+        wf = wref_face * np.sqrt(abs(np.linalg.det(Ed.T @ Ed)))
+        _, Vd, Sd = B.eval_phys(xt[:, :n], xt[:, n], xc, tc, h, ct)
+        Sn = np.einsum("qdj,d->qj", Sd, nrm)
+        A += np.einsum("q,qi,qj->ij", wf, Vd, Sn + alpha * Vd)
+    # B: d b_i / d(U_b, v_b, sigma_b) at every bottom point (eq. 4.1 bottom face + recovery)
+    C = n + 2
+    NP = x.shape[0]
+    Bm = np.zeros((B.nb, NP, C))
+    Sgb = np.einsum("qdj,qd->qj", Sb, gb)
+    Bm[:, :, 0] = (w[:, None] * Ub).T
+    Bm[:, :, 1] = (w[:, None] * (c2 * Vb - Sgb)).T
+    for m in range(n):
+        Bm[:, :, 2 + m] = (w[:, None] * (Sb[:, m, :] - gb[:, m:m + 1] * Vb)).T
+    # E: (U, v, sigma) at the top points
+    Em = np.zeros((NP, C, B.nb))
+    Em[:, 0, :] = Ut
+    Em[:, 1, :] = Vt
+    Em[:, 2:, :] = St
+    return A, Bm.reshape(B.nb, NP * C), Em.reshape(NP * C, B.nb), patch
+
+
+def adjoint_sweep(coords, elems, c, p, tents, lam_T, alpha=0.5):
+    """lambda_0 = F^* lambda_T for the sweep with g_D = 0.
+
+    lam_T: (E, Q, n+2) array (the same layout as the front).  Returns lambda_0."""
+    coords = np.asarray(coords, dtype=np.float64)
+    elems = np.asarray(elems)
+    c = np.asarray(c, dtype=np.float64)
+    n = coords.shape[1]
+    nv = coords.shape[0]
+    lay = _tdg.front_layout(coords, elems, p)
+    B = _basis.TrefftzBasis(n, p)
+    star = _tdg.vertex_star(elems, nv)
+    vfac = [[] for _ in range(nv)]
+    for (f, nrm, k) in _tdg.boundary_facets(coords, elems):
+        for a in f:
+            vfac[a].append((f, nrm))
+    # front times before every tent (the geometry does not depend on the data)
+    tau = np.zeros(nv)
+    before = []
+    for it in range(len(tents["vert"])):
+        before.append(tau.copy())
+        tau[int(tents["vert"][it])] = float(tents["t_top"][it])
+    lam = np.array(lam_T, dtype=np.float64).copy()
+    E, Q, C = lam.shape
+    for it in reversed(range(len(tents["vert"]))):
+        v = int(tents["vert"][it])
+        A, Bm, Em, patch = _tent_maps(coords, elems, c, p, lay, B, star, vfac, before[it], v,
+                                      float(tents["t_top"][it]), alpha)
+        lt = lam[patch].reshape(-1)
+        mu = np.linalg.solve(A.T, Em.T @ lt)
+        lam[patch] = (Bm.T @ mu).reshape(len(patch), Q, C)
+    return lam
+
+
+def misfit_gradient(front_T, obs_T, wq):
+    """J = 1/2 sum_q w_q (U_h - U_obs)^2 at T (L2 misfit of U); returns (J, dJ/dfront_T)."""
+    d = front_T[:, :, 0] - obs_T[:, :, 0]
+    J = 0.5 * float(np.sum(wq * d * d))
+    g = np.zeros_like(front_T)
+    g[:, :, 0] = wq * d
+    return J, g

@@ -14,7 +14,7 @@ import numpy as np
 
 from . import _binding as B
 
-__all__ = ["Tents", "Basis", "Solver", "pitch_mesh", "build_basis", "load_library"]
+__all__ = ["Tents", "Basis", "Solver", "TentSweep", "pitch_mesh", "build_basis", "load_library"]
 
 
 def load_library():
@@ -160,6 +160,17 @@ class Solver:
             level_end = self.n_levels + 1
         B.check(B.load().tp_advance(self.handle, int(level_begin), int(level_end), B.stream_ptr(stream)))
 
+    def adjoint(self, lam_T, out=None, stream=None):
+        """Gradient with respect to the initial front of a functional whose
+        gradient with respect to the final front is lam_T (tp_adjoint)."""
+        import torch
+        assert lam_T.is_cuda and lam_T.dtype == torch.float64 and lam_T.is_contiguous()
+        assert lam_T.numel() == self.nrhs * self.n_front * self.n_comp
+        if out is None:
+            out = torch.empty(self.front_shape(), dtype=torch.float64, device="cuda")
+        B.check(B.load().tp_adjoint(self.handle, B.tensor_ptr(lam_T), B.tensor_ptr(out), B.stream_ptr(stream)))
+        return out
+
     def energy(self, out=None, stream=None):
         import torch
         if out is None:
@@ -190,3 +201,38 @@ class Solver:
         if getattr(self, "handle", None) and B._lib is not None:
             B._lib.tp_destroy_ctx(self.handle)
             self.handle = None
+
+
+def _make_tent_sweep():
+    import torch
+
+    class TentSweep(torch.autograd.Function):
+        """front(T) = F(front(0)) through libtp, differentiable: the backward
+        pass is the reverse tent sweep (tp_adjoint).  g_D must be zero (the
+        map is then linear)."""
+
+        @staticmethod
+        def forward(ctx, front0, solver):
+            solver.set_state(front0.contiguous())
+            solver.advance()
+            out, _ = solver.get_state()
+            ctx.solver = solver
+            return out
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            return ctx.solver.adjoint(grad_out.contiguous()), None
+
+    return TentSweep
+
+
+class _LazyTentSweep:
+    _cls = None
+
+    def apply(self, front0, solver):
+        if _LazyTentSweep._cls is None:
+            _LazyTentSweep._cls = _make_tent_sweep()
+        return _LazyTentSweep._cls.apply(front0, solver)
+
+
+TentSweep = _LazyTentSweep()

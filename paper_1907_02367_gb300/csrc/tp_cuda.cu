@@ -69,6 +69,7 @@ struct KArgs {
   const double* sqw;      // Q, sqrt(wref)
   const int* tent_v;
   const double* tent_ttop;
+  const double* tent_tbot;
   const double* tent_h;
   const long long* tent_gdoff;
   const int* sp_ptr;
@@ -339,7 +340,17 @@ __device__ __forceinline__ double recip(double x) {
 // equilibrated (D A D, D = |diag A|^-1/2), factorised in binary32 and the
 // solution refined against the float-float A until the correction stops
 // shrinking (at most kMaxRefine steps; TP_ERR_NOCONV if it stalls high).
-template <int DIM, bool MIXED>
+//
+// ADJ = true: the adjoint tent map (reverse sweep).  With g_D = 0 a tent maps
+// its bottom values linearly to its top values, b = B f_bot, A x = b,
+// f_top = E x; the adjoint takes lambda at the top points to
+// mu = A^-T (E^T lambda) and lambda_bot = B^T mu at the bottom points.  In the
+// U-value form E^T lambda = zeta_U + (c/h) D_t zeta_v - (1/h) sum_m D_m zeta_m,
+// zeta = sum_q lambda_q u_q over the top points (the moment formula of b), and
+// B^T mu at a bottom point is w (s0, c^-2 s_t - g_b.s, s_m - g_b,m s_t) with
+// s0 = u.mu, s_t = (c/h) u.D_t^T mu, s_m = -(1/h) u.D_m^T mu.  The front and
+// time arrays of the arguments are then the adjoint state (tau runs backwards).
+template <int DIM, bool MIXED, bool ADJ>
 __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int tent0) {
   using T = typename std::conditional<MIXED, dd, double>::type;
   using R = Ar<T>;
@@ -395,7 +406,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
     const int p0 = a.star_ptr[v], p1 = a.star_ptr[v + 1];
     s_P = p1 - p0;
     s_ttop = a.tent_ttop[tent];
-    s_tbot = a.tau[v];
+    s_tbot = ADJ ? a.tent_tbot[tent] : a.tau[v];
     s_tc = 0.5 * (s_tbot + s_ttop);
     s_ih = 1.0 / a.tent_h[tent];
     const double c = a.cK[a.star_el[p0]];
@@ -413,9 +424,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
     for (int i = 0; i < NV; ++i) {
       const int vi = a.elems[(int64_t)el * NV + i];
       for (int d = 0; d < DIM; ++d) s_X[k][i][d] = a.X[(int64_t)vi * DIM + d];
-      const double tb = a.tau[vi];
-      s_tb[k][i] = tb;
-      s_tt[k][i] = (vi == v) ? s_ttop : tb;
+      const double tv = a.tau[vi];
+      s_tb[k][i] = (vi == v) ? s_tbot : tv;
+      s_tt[k][i] = (vi == v) ? s_ttop : tv;
     }
     double e[DIM][DIM], db[DIM], dt[DIM];
     for (int i = 0; i < DIM; ++i) {
@@ -443,7 +454,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
       s_fP[f][1][d] = a.X[(int64_t)v * DIM + d];
       s_fn[f][d] = a.facet_nrm[(int64_t)fid * DIM + d];
     }
-    s_fP[f][0][DIM] = a.tau[v];
+    s_fP[f][0][DIM] = ADJ ? a.tent_tbot[tent] : a.tau[v];
     s_fP[f][1][DIM] = a.tent_ttop[tent];
     int c2 = 2;
     for (int i = 0; i < DIM; ++i) {
@@ -511,7 +522,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
         const T th = R::from(c * (tt - tc) * ih);
         const double sw = __ldg(a.sqw + q) * s_sdet[k];
         eval_uvalues<DIM, T>(a, th, xh, sM + tid * a.mono_stride, R::from(sw), sU + (size_t)tid * nb);
-        if (side == 1) {
+        if (ADJ && side == 0) {
+          // adjoint: zeta = sum_q lambda_q u_q over the top points
+          const int el = s_el[k];
+          const double isw = 1.0 / sw;
+          for (int r = 0; r < nrhs; ++r) {
+            const double* f = a.front + (((int64_t)r * a.ne + el) * Q + q) * C;
+            T* cb = sCB + ((size_t)ql * nrhs + r) * C;
+            for (int cc = 0; cc < C; ++cc) cb[cc] = R::from(f[cc] * isw);
+          }
+        }
+        if (!ADJ && side == 1) {
           const int el = s_el[k];
           for (int r = 0; r < nrhs; ++r) {
             const double* f = a.front + (((int64_t)r * a.ne + el) * Q + q) * C;
@@ -556,8 +577,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
     for (int id = tid; id < nmom; id += blockDim.x) {
       const int r = id / (C * nb), rem = id % (C * nb), cc = rem / nb, i = rem % nb;
       T t = sPM[id];
+      const int row0 = ADJ ? 0 : CH;   // adjoint moments use the top points
       for (int ql = 0; ql < nq; ++ql)
-        t = R::fma(sCB[((size_t)ql * nrhs + r) * C + cc], sU[(size_t)(CH + ql) * nb + i], t);
+        t = R::fma(sCB[((size_t)ql * nrhs + r) * C + cc], sU[(size_t)(row0 + ql) * nb + i], t);
       sPM[id] = t;
     }
     __syncthreads();
@@ -609,7 +631,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
           eval_uvalues<DIM, T>(a, th, xh, sM + tid * a.mono_stride, R::from(sw), sU + (size_t)tid * nb);
           const long long goff = a.tent_gdoff[tent] + (long long)f * Q + q;
           for (int r = 0; r < nrhs; ++r)
-            sGd[tid * nrhs + r] = R::from((a.gD != nullptr) ? sw * a.gD[(long long)r * a.n_bnd + goff] : 0.0);
+            sGd[tid * nrhs + r] = R::from((!ADJ && a.gD != nullptr) ? sw * a.gD[(long long)r * a.n_bnd + goff] : 0.0);
         }
         __syncthreads();
         for (int ql = 0; ql < nq; ++ql) {
@@ -705,6 +727,18 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
     }
   }
   __syncthreads();
+
+  if constexpr (ADJ) {   // solve with A^T
+    for (int id = tid; id < nb * nb; id += blockDim.x) {
+      const int i = id / nb, j = id % nb;
+      if (i < j) {
+        const T t = sA[id];
+        sA[id] = sA[j * nb + i];
+        sA[j * nb + i] = t;
+      }
+    }
+    __syncthreads();
+  }
 
   // ---------------- phase 3: solve ----------------
   const bool pivoting = (nfac > 0);
@@ -943,7 +977,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
       for (int i = 0; i < NV; ++i) {
         const double l = __ldg(a.bary + q * NV + i);
         for (int d = 0; d < DIM; ++d) x[d] = fma(l, s_X[k][i][d], x[d]);
-        tt = fma(l, s_tt[k][i], tt);
+        tt = fma(l, ADJ ? s_tb[k][i] : s_tt[k][i], tt);   // adjoint: bottom points
       }
       T xh[DIM];
       for (int d = 0; d < DIM; ++d) xh[d] = R::from((x[d] - s_xv[d]) * ih);
@@ -951,18 +985,42 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
       eval_uvalues<DIM, T, false>(a, th, xh, sM + tid * a.mono_stride, R::one(), sU + (size_t)tid * nb);
     }
     __syncthreads();
-    for (int id = tid; id < nq * nrhs * C; id += blockDim.x) {
-      const int ql = id / (nrhs * C), rc = id % (nrhs * C), r = rc / C, cc = rc % C;
-      const int qg = base + ql, k = qg / Q, q = qg % Q;
-      const T* u = sU + (size_t)ql * nb;
-      const T* y = sY + ((size_t)r * C + cc) * nb;
-      T t = R::zero();
-      for (int j = 0; j < nb; ++j) t = R::fma(y[j], u[j], t);
-      a.front[(((int64_t)r * a.ne + s_el[k]) * Q + q) * C + cc] = R::to(t);
+    if constexpr (!ADJ) {
+      for (int id = tid; id < nq * nrhs * C; id += blockDim.x) {
+        const int ql = id / (nrhs * C), rc = id % (nrhs * C), r = rc / C, cc = rc % C;
+        const int qg = base + ql, k = qg / Q, q = qg % Q;
+        const T* u = sU + (size_t)ql * nb;
+        const T* y = sY + ((size_t)r * C + cc) * nb;
+        T t = R::zero();
+        for (int j = 0; j < nb; ++j) t = R::fma(y[j], u[j], t);
+        a.front[(((int64_t)r * a.ne + s_el[k]) * Q + q) * C + cc] = R::to(t);
+      }
+    } else {
+      // lambda_bot = w (s0, c^-2 s_t - g_b.s, s_m - g_b,m s_t)
+      for (int id = tid; id < nq * nrhs; id += blockDim.x) {
+        const int ql = id / nrhs, r = id % nrhs;
+        const int qg = base + ql, k = qg / Q, q = qg % Q;
+        const T* u = sU + (size_t)ql * nb;
+        double sv[C];
+        for (int cc = 0; cc < C; ++cc) {
+          const T* y = sY + ((size_t)r * C + cc) * nb;
+          T t = R::zero();
+          for (int j = 0; j < nb; ++j) t = R::fma(y[j], u[j], t);
+          sv[cc] = R::to(t);
+        }
+        const double sq = __ldg(a.sqw + q) * s_sdet[k];
+        const double w = sq * sq;
+        double gs = 0.0;
+        for (int d = 0; d < DIM; ++d) gs = fma(s_gb[k][d], sv[2 + d], gs);
+        double* f = a.front + (((int64_t)r * a.ne + s_el[k]) * Q + q) * C;
+        f[0] = w * sv[0];
+        f[1] = w * (ic2 * sv[1] - gs);
+        for (int d = 0; d < DIM; ++d) f[2 + d] = w * (sv[2 + d] - s_gb[k][d] * sv[1]);
+      }
     }
     __syncthreads();
   }
-  if (tid == 0 && rank == 0) a.tau[v] = s_ttop;
+  if (tid == 0 && rank == 0) a.tau[v] = ADJ ? s_tbot : s_ttop;
 }
 
 // energy flux through the front, per (rhs, element) partial sums
@@ -1039,6 +1097,11 @@ struct tp_ctx {
   tp::SimplexRule rule;
   std::vector<double> bnd_xt;
   KArgs args{};
+  KArgs args_adj{};        // same tables; front/tau point at the adjoint state
+  double T_final = 0.0;
+  double* d_adj = nullptr;
+  double* d_tau_adj = nullptr;
+  cudaGraphExec_t adj_graph = nullptr;
   size_t smem_bytes = 0;
   int energy_blocks = 0;
   std::vector<void*> allocs;
@@ -1071,15 +1134,17 @@ constexpr size_t kTwoPerSmSmem = 95 * 1024;  // plan that leaves room for two CT
 // the attribute is set to the plan's cap, so contexts of any size can share the kernel
 template <int DIM>
 int set_smem_attr() {
-  TP_CUDA_OK(cudaFuncSetAttribute(k_layer<DIM, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  TP_CUDA_OK(cudaFuncSetAttribute(k_layer<DIM, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)kMaxDynSmem));
-  TP_CUDA_OK(cudaFuncSetAttribute(k_layer<DIM, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  TP_CUDA_OK(cudaFuncSetAttribute(k_layer<DIM, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)kMaxDynSmem));
+  TP_CUDA_OK(cudaFuncSetAttribute(k_layer<DIM, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)kMaxDynSmem));
   return TP_OK;
 }
 
 template <int DIM>
-cudaError_t launch_cluster(tp_ctx* ctx, int nt, int cs, int t0, cudaStream_t st) {
+cudaError_t launch_cluster(tp_ctx* ctx, int nt, int cs, int t0, cudaStream_t st, bool adj) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(nt * cs));
   cfg.blockDim = dim3(kThreads);
@@ -1092,8 +1157,9 @@ cudaError_t launch_cluster(tp_ctx* ctx, int nt, int cs, int t0, cudaStream_t st)
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  if (ctx->mixed) return cudaLaunchKernelEx(&cfg, k_layer<DIM, true>, ctx->args, t0);
-  return cudaLaunchKernelEx(&cfg, k_layer<DIM, false>, ctx->args, t0);
+  if (adj) return cudaLaunchKernelEx(&cfg, k_layer<DIM, false, true>, ctx->args_adj, t0);
+  if (ctx->mixed) return cudaLaunchKernelEx(&cfg, k_layer<DIM, true, false>, ctx->args, t0);
+  return cudaLaunchKernelEx(&cfg, k_layer<DIM, false, false>, ctx->args, t0);
 }
 
 // cluster size for a level of nt tents: a power of two <= max_cs with
@@ -1104,16 +1170,16 @@ int level_cluster_size(const tp_ctx* ctx, int64_t nt) {
   return cs;
 }
 
-int launch_level(tp_ctx* ctx, int32_t L, cudaStream_t st) {
+int launch_level(tp_ctx* ctx, int32_t L, cudaStream_t st, bool adj = false) {
   const int64_t t0 = ctx->level_ptr[L - 1], t1 = ctx->level_ptr[L];
   if (t1 <= t0) return TP_OK;
   const int nt = (int)(t1 - t0);
   const int cs = level_cluster_size(ctx, nt);
   cudaError_t e;
   switch (ctx->dim) {
-    case 1: e = launch_cluster<1>(ctx, nt, cs, (int)t0, st); break;
-    case 2: e = launch_cluster<2>(ctx, nt, cs, (int)t0, st); break;
-    default: e = launch_cluster<3>(ctx, nt, cs, (int)t0, st); break;
+    case 1: e = launch_cluster<1>(ctx, nt, cs, (int)t0, st, adj); break;
+    case 2: e = launch_cluster<2>(ctx, nt, cs, (int)t0, st, adj); break;
+    default: e = launch_cluster<3>(ctx, nt, cs, (int)t0, st, adj); break;
   }
   TP_CUDA_OK(e);
   TP_CUDA_OK(cudaGetLastError());
@@ -1253,6 +1319,8 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
   std::vector<double> sqw(Q);
   for (int q = 0; q < Q; ++q) sqw[q] = std::sqrt(ctx->rule.w[q]);
   std::vector<double> ttop(tents->t_top.begin(), tents->t_top.end());
+  std::vector<double> tbot(tents->t_bot.begin(), tents->t_bot.end());
+  double* dtbot = nullptr;
   std::vector<int> tv(tents->vert.begin(), tents->vert.end());
   if ((rc = ctx_upload(ctx, &dX, T.X)) || (rc = ctx_upload(ctx, &dc, T.c)) ||
       (rc = ctx_upload(ctx, &del, T.elems)) || (rc = ctx_upload(ctx, &dsp, T.star_ptr)) ||
@@ -1261,6 +1329,7 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
       (rc = ctx_upload(ctx, &dnrm, T.facet_nrm)) || (rc = ctx_upload(ctx, &dbary, ctx->rule.bary)) ||
       (rc = ctx_upload(ctx, &dw, ctx->rule.w)) || (rc = ctx_upload(ctx, &dsqw, sqw)) ||
       (rc = ctx_upload(ctx, &dtv, tv)) || (rc = ctx_upload(ctx, &dttop, ttop)) ||
+      (rc = ctx_upload(ctx, &dtbot, tbot)) ||
       (rc = ctx_upload(ctx, &dh, tent_h)) || (rc = ctx_upload(ctx, &dgo, gdoff)) ||
       (rc = ctx_upload(ctx, &dspp, basis->sp_ptr)) || (rc = ctx_upload(ctx, &dspm, basis->sp_mono)) ||
       (rc = ctx_upload(ctx, &dspc, basis->sp_coef)) || (rc = ctx_upload(ctx, &dpar, basis->parent)) ||
@@ -1280,6 +1349,12 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
     tp::set_error("tp_create: device allocation of the front state failed");
     return fail(TP_ERR_OOM);
   }
+  if (cudaMalloc(&ctx->d_adj, nfront * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&ctx->d_tau_adj, T.nv * sizeof(double)) != cudaSuccess) {
+    tp::set_error("tp_create: device allocation of the adjoint state failed");
+    return fail(TP_ERR_OOM);
+  }
+  ctx->T_final = tents->T;
   ctx->energy_blocks = (int)std::min<int64_t>(1024, (T.ne + kThreads - 1) / kThreads);
   if (cudaMalloc(&ctx->d_partial, (size_t)ctx->nrhs * ctx->energy_blocks * sizeof(double)) != cudaSuccess) {
     tp::set_error("tp_create: device allocation failed");
@@ -1312,6 +1387,7 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
   a.sqw = dsqw;
   a.tent_v = dtv;
   a.tent_ttop = dttop;
+  a.tent_tbot = dtbot;
   a.tent_h = dh;
   a.tent_gdoff = dgo;
   a.sp_ptr = dspp;
@@ -1389,6 +1465,10 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
   }
   bytes = plan(CH);
   a.CH = CH;
+  ctx->args_adj = a;
+  ctx->args_adj.front = ctx->d_adj;
+  ctx->args_adj.tau = ctx->d_tau_adj;
+  ctx->args_adj.gD = nullptr;
   ctx->smem_bytes = bytes;
   switch (n) {
     case 1: rc = set_smem_attr<1>(); break;
@@ -1533,6 +1613,47 @@ extern "C" int tp_advance(tp_ctx* ctx, int32_t level_begin, int32_t level_end, v
   return TP_OK;
 }
 
+namespace {
+__global__ void k_fill(double* p, int64_t n, double v) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = v;
+}
+}  // namespace
+
+extern "C" int tp_adjoint(tp_ctx* ctx, const double* d_lambda_T, double* d_lambda_0, void* stream) {
+  if (!ctx || !d_lambda_T || !d_lambda_0) {
+    tp::set_error("tp_adjoint: null argument");
+    return TP_ERR_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t nfront = (size_t)ctx->nrhs * ctx->ne * ctx->Q * ctx->C;
+  TP_CUDA_OK(cudaMemcpyAsync(ctx->d_adj, d_lambda_T, nfront * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  k_fill<<<(unsigned)std::min<int64_t>(1024, (ctx->nv + 255) / 256), 256, 0, st>>>(ctx->d_tau_adj, ctx->nv,
+                                                                                 ctx->T_final);
+  TP_CUDA_OK(cudaGetLastError());
+  if (ctx->n_levels > 0) {
+    if (!ctx->adj_graph) {
+      cudaGraph_t g = nullptr;
+      TP_CUDA_OK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+      int rc = TP_OK;
+      for (int32_t L = ctx->n_levels; L >= 1 && rc == TP_OK; --L) rc = launch_level(ctx, L, ctx->cap_stream, true);
+      cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &g);
+      if (rc != TP_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+      }
+      TP_CUDA_OK(e);
+      e = cudaGraphInstantiate(&ctx->adj_graph, g, 0);
+      cudaGraphDestroy(g);
+      TP_CUDA_OK(e);
+    }
+    TP_CUDA_OK(cudaGraphLaunch(ctx->adj_graph, st));
+  }
+  TP_CUDA_OK(cudaMemcpyAsync(d_lambda_0, ctx->d_adj, nfront * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  ctx->last_stream = st;
+  return TP_OK;
+}
+
 extern "C" int tp_energy(tp_ctx* ctx, double* d_out, void* stream) {
   if (!ctx || !d_out) {
     tp::set_error("tp_energy: null argument");
@@ -1589,6 +1710,9 @@ extern "C" void tp_destroy_ctx(tp_ctx* ctx) {
   cudaFree(ctx->d_tau);
   cudaFree(ctx->d_gD);
   cudaFree(ctx->d_partial);
+  cudaFree(ctx->d_adj);
+  cudaFree(ctx->d_tau_adj);
+  if (ctx->adj_graph) cudaGraphExecDestroy(ctx->adj_graph);
   cudaFree(ctx->d_status);
   cudaFree(ctx->d_info);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
