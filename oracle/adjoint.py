@@ -35,6 +35,8 @@ def _tent_maps(coords, elems, c, p, lay, B, star, vfac, tau, v, t_top, alpha):
     Q = lay.wq.shape[1]
     t_bot = float(tau[v])
     patch = star[v]
+    if np.any(c[patch] != c[patch][0]):
+        raise NotImplementedError("adjoint of interface tents")
     ct = float(c[patch][0])
     c2 = 1.0 / (ct * ct)
     pv = sorted({a for k in patch for a in elems[k].tolist()} - {v})
@@ -60,7 +62,7 @@ def _tent_maps(coords, elems, c, p, lay, B, star, vfac, tau, v, t_top, alpha):
     A -= (w[:, None] * Sgt).T @ Vt + (w[:, None] * Vt).T @ Sgt
     A += (w[:, None] * Ub).T @ Ub
     _, wref_face, bary_face = _quad.simplex_rule(n, p + 1)
-    for (fac, nrm) in vfac[v]:
+    for (fac, nrm, _k) in vfac[v]:
         others = [a for a in fac if a != v]
         Pf = [np.append(coords[v], t_bot), np.append(coords[v], t_top)]
         Pf += [np.append(coords[a], tau[a]) for a in others]
@@ -103,7 +105,7 @@ def adjoint_sweep(coords, elems, c, p, tents, lam_T, alpha=0.5):
     vfac = [[] for _ in range(nv)]
     for (f, nrm, k) in _tdg.boundary_facets(coords, elems):
         for a in f:
-            vfac[a].append((f, nrm))
+            vfac[a].append((f, nrm, k))
     # front times before every tent (the geometry does not depend on the data)
     tau = np.zeros(nv)
     before = []

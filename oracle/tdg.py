@@ -27,7 +27,12 @@ Readings of the paper taken here (each listed in the design notes):
     dissipative sign sigma + alpha (v - g_D) n, not the sign printed in the
     flux table;
   * basis centre x_c = x_v, t_c = (t_bot + t_top)/2, scale h = anisotropic
-    diameter eq. (3.3) over the tent vertices (affects only rounding).
+    diameter eq. (3.3) over the tent vertices with the tent's largest speed
+    (affects only rounding);
+  * piecewise-constant c (Section 4.2): one polynomial per material of the
+    tent (its own c in the Remark 3.1 map), coupled on the time-like facets
+    through v by the F^time terms of eq. (2.5); the facet's + side is the
+    element with the lower index in the vertex star, n its outward normal.
 
 Parity unpinned: none of the above beyond what tests/test_oracle_*.py pin
 (polynomial reproduction, energy identity, convergence rates).
@@ -121,7 +126,7 @@ def anisotropic_diameter(pts_xt: np.ndarray, c: float) -> float:
 # the sweep
 # ----------------------------------------------------------------------------
 def sweep(coords, elems, c, p, tents, init, dirichlet=None, alpha=0.5,
-          record=None, front0=None, tau0=None, tent_range=None):
+          record=None, front0=None, tau0=None, tent_range=None, beta=0.5):
     """Run the tent sweep.
 
     coords (Nv, n), elems (E, n+1), c (E,), p: Trefftz degree of U^p,
@@ -143,7 +148,7 @@ def sweep(coords, elems, c, p, tents, init, dirichlet=None, alpha=0.5,
     vfac = [[] for _ in range(nv)]
     for (f, nrm, k) in bfac:
         for a in f:
-            vfac[a].append((f, nrm))
+            vfac[a].append((f, nrm, k))
     E, Q = lay.wq.shape
     if front0 is None:
         front = np.asarray(init(lay.xq.reshape(-1, n)), dtype=np.float64).reshape(E, Q, n + 2).copy()
@@ -158,54 +163,63 @@ def sweep(coords, elems, c, p, tents, init, dirichlet=None, alpha=0.5,
         t_top = float(tents["t_top"][it])
         t_bot = float(tau[v])
         patch = star[v]
-        cs = c[patch]
-        if np.any(cs != cs[0]):
-            raise NotImplementedError("multi-material tent")
-        ct = float(cs[0])
-        c2 = 1.0 / (ct * ct)
-        # Remark 3.1: centre and anisotropic diameter
+        # Section 4.2: one Trefftz polynomial per material (bitwise-equal c) of the tent
+        speeds = []
+        for k in patch:
+            if float(c[k]) not in speeds:
+                speeds.append(float(c[k]))
+        grp = {k: speeds.index(float(c[k])) for k in patch}
+        ng = len(speeds)
+        cmax = max(speeds)
+        # Remark 3.1: centre and anisotropic diameter (with the largest speed of the tent)
         pv = sorted({a for k in patch for a in elems[k].tolist()} - {v})
         tv = [np.append(coords[v], t_bot), np.append(coords[v], t_top)]
         tv += [np.append(coords[w], tau[w]) for w in pv]
-        h = anisotropic_diameter(np.array(tv), ct)
+        h = anisotropic_diameter(np.array(tv), cmax)
         xc, tc = coords[v], 0.5 * (t_bot + t_top)
 
-        # gather the patch: every front point of every element K in star(v)
-        P = len(patch)
-        ids = elems[patch]                                   # (P, n+1)
-        tb = tau[ids]                                        # bottom front times at the vertices
-        tt = np.where(ids == v, t_top, tb)                   # top: tau_v -> t_top
-        Xk = coords[ids]                                     # (P, n+1, n)
-        J = Xk[:, 1:, :] - Xk[:, :1, :]
-        g_b = np.linalg.solve(J, (tb[:, 1:] - tb[:, :1])[..., None])[..., 0]   # (P, n)
-        g_t = np.linalg.solve(J, (tt[:, 1:] - tt[:, :1])[..., None])[..., 0]
-        x = lay.xq[patch].reshape(-1, n)                     # (P*Q, n)
-        w = lay.wq[patch].reshape(-1)
-        t_b = (tb @ lay.bary.T).reshape(-1)
-        t_t = (tt @ lay.bary.T).reshape(-1)
-        gb = np.repeat(g_b, Q, axis=0)                       # (P*Q, n)
-        gt = np.repeat(g_t, Q, axis=0)
-        Ut, Vt, St = B.eval_phys(x, t_t, xc, tc, h, ct)
-        Ub, Vb, Sb = B.eval_phys(x, t_b, xc, tc, h, ct)
-        # top face (LHS): c^-2 v_j w_i + s_j.t_i - v_j (t_i.g) - (s_j.g) w_i
-        Sgt = np.einsum("qdj,qd->qj", St, gt)
-        A = (w[:, None] * c2 * Vt).T @ Vt
-        A += np.einsum("q,qdi,qdj->ij", w, St, St)
-        A -= (w[:, None] * Sgt).T @ Vt
-        A -= (w[:, None] * Vt).T @ Sgt
-        # recovery on the bottom face (LHS): U_j V_i
-        A += (w[:, None] * Ub).T @ Ub
-        # bottom face data (RHS)
-        f = front[patch].reshape(-1, n + 2)
-        Uf, vf, sf = f[:, 0], f[:, 1], f[:, 2:]
-        Sgb = np.einsum("qdj,qd->qj", Sb, gb)
-        b = (w * c2 * vf) @ Vb
-        b += np.einsum("q,qd,qdi->i", w, sf, Sb)
-        b -= (w * vf) @ Sgb
-        b -= (w * np.sum(sf * gb, axis=1)) @ Vb
-        b += (w * Uf) @ Ub
-        # Dirichlet vertical faces through v
-        for (fac, nrm) in vfac[v]:
+        nb = B.nb
+        A = np.zeros((ng * nb, ng * nb))
+        b = np.zeros(ng * nb)
+        tops = []
+        for k in patch:
+            g = grp[k]
+            ck = speeds[g]
+            c2 = 1.0 / (ck * ck)
+            blk = slice(g * nb, (g + 1) * nb)
+            ids = elems[k]
+            tb = tau[ids]                                   # bottom front times at the vertices
+            tt = np.where(ids == v, t_top, tb)              # top: tau_v -> t_top
+            Xk = coords[ids]
+            J = Xk[1:] - Xk[0]
+            g_b = np.linalg.solve(J, tb[1:] - tb[0])
+            g_t = np.linalg.solve(J, tt[1:] - tt[0])
+            x = lay.xq[k]
+            w = lay.wq[k]
+            Ut, Vt, St = B.eval_phys(x, lay.bary @ tt, xc, tc, h, ck)
+            Ub, Vb, Sb = B.eval_phys(x, lay.bary @ tb, xc, tc, h, ck)
+            # top face (LHS): c^-2 v_j w_i + s_j.t_i - v_j (t_i.g) - (s_j.g) w_i
+            Sgt = np.einsum("qdj,d->qj", St, g_t)
+            Ak = (w[:, None] * c2 * Vt).T @ Vt
+            Ak += np.einsum("q,qdi,qdj->ij", w, St, St)
+            Ak -= (w[:, None] * Sgt).T @ Vt
+            Ak -= (w[:, None] * Vt).T @ Sgt
+            # recovery on the bottom face (LHS): U_j V_i
+            Ak += (w[:, None] * Ub).T @ Ub
+            A[blk, blk] += Ak
+            # bottom face data (RHS)
+            f = front[k]
+            Uf, vf, sf = f[:, 0], f[:, 1], f[:, 2:]
+            Sgb = np.einsum("qdj,d->qj", Sb, g_b)
+            bk = (w * c2 * vf) @ Vb
+            bk += np.einsum("q,qd,qdi->i", w, sf, Sb)
+            bk -= (w * vf) @ Sgb
+            bk -= (w * (sf @ g_b)) @ Vb
+            bk += (w * Uf) @ Ub
+            b[blk] += bk
+            tops.append((k, g, Ut, Vt, St))
+
+        def face_simplex(fac):
             # the n-simplex {x in F, tau_bot(x) <= t <= tau_top(x)} with vertices
             # (x_v, t_bot), (x_v, t_top), (x_w, tau_w) for the other facet vertices w
             others = [a for a in fac if a != v]
@@ -215,24 +229,81 @@ def sweep(coords, elems, c, p, tents, init, dirichlet=None, alpha=0.5,
             Ed = (Pf[1:] - Pf[0]).T                          # (n+1, n)
             scale = math.sqrt(abs(np.linalg.det(Ed.T @ Ed)))  # n! * n-volume
             xt = bary_face @ Pf
-            wf = wref_face * scale
-            Ud, Vd, Sd = B.eval_phys(xt[:, :n], xt[:, n], xc, tc, h, ct)
+            return xt, wref_face * scale
+
+        # Dirichlet vertical faces through v (eq. 4.1)
+        for (fac, nrm, kf) in vfac[v]:
+            g = grp[kf]
+            blk = slice(g * nb, (g + 1) * nb)
+            xt, wf = face_simplex(fac)
+            Ud, Vd, Sd = B.eval_phys(xt[:, :n], xt[:, n], xc, tc, h, speeds[g])
             Sn = np.einsum("qdj,d->qj", Sd, nrm)
-            A += np.einsum("q,qi,qj->ij", wf, Vd, Sn + alpha * Vd)     # (s_j.n + alpha v_j) w_i
+            A[blk, blk] += np.einsum("q,qi,qj->ij", wf, Vd, Sn + alpha * Vd)     # (s_j.n + alpha v_j) w_i
             gd = np.zeros(len(wf)) if dirichlet is None else np.asarray(dirichlet(xt[:, :n], xt[:, n]))
-            b += np.einsum("q,qi->i", wf * gd, alpha * Vd - Sn)        # g_D (alpha w_i - t_i.n)
+            b[blk] += np.einsum("q,qi->i", wf * gd, alpha * Vd - Sn)           # g_D (alpha w_i - t_i.n)
+
+        # time-like interface faces between materials (Section 4.2, A of eq. 2.5):
+        # {v}[[t]]_N + {s}.[[w]]_N + alpha [[v]]_N.[[w]]_N + beta [[s]]_N [[t]]_N
+        for (fac, kp, km, nrm) in interface_facets(coords, elems, patch, v, grp):
+            xt, wf = face_simplex(fac)
+            side = {}
+            for sgn, kk in ((1.0, kp), (-1.0, km)):
+                g = grp[kk]
+                _, Vf, Sf = B.eval_phys(xt[:, :n], xt[:, n], xc, tc, h, speeds[g])
+                side[sgn] = (g, Vf, np.einsum("qdj,d->qj", Sf, nrm))
+            for st in (1.0, -1.0):            # test side
+                gt, Vt_, Snt = side[st]
+                for ss in (1.0, -1.0):        # trial side
+                    gs, Vs_, Sns = side[ss]
+                    blk = (slice(gt * nb, (gt + 1) * nb), slice(gs * nb, (gs + 1) * nb))
+                    A[blk] += 0.5 * st * (np.einsum("q,qi,qj->ij", wf, Snt, Vs_)
+                                          + np.einsum("q,qi,qj->ij", wf, Vt_, Sns))
+                    A[blk] += st * ss * (alpha * np.einsum("q,qi,qj->ij", wf, Vt_, Vs_)
+                                         + beta * np.einsum("q,qi,qj->ij", wf, Snt, Sns))
 
         xs = np.linalg.solve(A, b)
         if record is not None:
             record(it, dict(v=v, t_bot=t_bot, t_top=t_top, A=A, b=b, x=xs, h=h,
-                            xc=xc, tc=tc, c=ct, patch=list(patch),
+                            xc=xc, tc=tc, c=speeds[0], speeds=speeds, groups=grp, patch=list(patch),
                             front_before={k: front[k].copy() for k in patch},
                             tau_before=tau.copy(), basis=B))
-        out = np.concatenate([(Ut @ xs)[:, None], (Vt @ xs)[:, None],
-                              np.einsum("qdj,j->qd", St, xs)], axis=1)
-        front[patch] = out.reshape(P, Q, n + 2)
+        for (k, g, Ut, Vt, St) in tops:
+            xg = xs[g * nb:(g + 1) * nb]
+            front[k][:, 0] = Ut @ xg
+            front[k][:, 1] = Vt @ xg
+            front[k][:, 2:] = np.einsum("qdj,j->qd", St, xg)
         tau[v] = t_top
     return front, tau
+
+
+def interface_facets(coords, elems, patch, v, grp):
+    """Facets through v shared by two patch elements of different materials:
+    list of (facet vertices, K+, K-, unit normal pointing out of K+)."""
+    n = coords.shape[1]
+    out = []
+    pl = list(patch)
+    for a in range(len(pl)):
+        for bb in range(a + 1, len(pl)):
+            ka, kb = pl[a], pl[bb]
+            if grp[ka] == grp[kb]:
+                continue
+            common = sorted(set(elems[ka].tolist()) & set(elems[kb].tolist()))
+            if len(common) != n or v not in common:
+                continue
+            opp = [x for x in elems[ka].tolist() if x not in common][0]
+            P = coords[common]
+            if n == 1:
+                nrm = np.array([1.0])
+            elif n == 2:
+                t = P[1] - P[0]
+                nrm = np.array([t[1], -t[0]])
+            else:
+                nrm = np.cross(P[1] - P[0], P[2] - P[0])
+            nrm = nrm / np.linalg.norm(nrm)
+            if np.dot(coords[opp] - P[0], nrm) > 0:
+                nrm = -nrm
+            out.append((tuple(common), ka, kb, nrm))
+    return out
 
 
 def front_points(coords, elems, p):

@@ -340,3 +340,39 @@ def workload(name: str) -> Workload:
         return Workload(name, m, 3, 0.2, pitch_kappa(m), standing_wave_3d,
                         lambda x: standing_wave_3d(x, 0.0), None)
     raise KeyError(name)
+
+
+def interface_solution(dim: int, a: float, c1: float, c2: float):
+    """Exact piecewise-quadratic solution across the interface x_1 = a between
+    speeds c1 (x_1 < a) and c2 (x_1 > a):
+        U_i = alpha_i x^2 + beta t^2 + gamma_i x + e_i + 0.4 y  (x = x_1, y = x_2 in 2D)
+    with alpha_1 = c2^2, alpha_2 = c1^2, beta = c1^2 c2^2, so that each piece
+    solves -Lap U + c_i^-2 U_tt = 0, and gamma_2, e_2 chosen so that U and
+    dU/dx_1 (hence v and sigma.n) are continuous at x_1 = a.
+    Returns (sol(x, t) -> (N, n+2), speed(x) -> c)."""
+    al1, al2 = c2 * c2, c1 * c1
+    be = c1 * c1 * c2 * c2
+    g1, e1 = 0.3, 0.1
+    g2 = g1 + 2.0 * (al1 - al2) * a
+    e2 = e1 + (al1 - al2) * a * a + (g1 - g2) * a
+
+    def sol(x, t):
+        x = np.asarray(x, dtype=np.float64).reshape(-1, dim)
+        t = np.broadcast_to(np.asarray(t, dtype=np.float64), x.shape[:1])
+        X = x[:, 0]
+        left = X < a
+        al = np.where(left, al1, al2)
+        g = np.where(left, g1, g2)
+        e = np.where(left, e1, e2)
+        U = al * X * X + be * t * t + g * X + e
+        cols = [U, 2.0 * be * t, -(2.0 * al * X + g)]
+        if dim == 2:
+            U = U + 0.4 * x[:, 1]
+            cols[0] = U
+            cols.append(np.full_like(X, -0.4))
+        return np.stack(cols, axis=1)
+
+    def speed(xc):
+        xc = np.asarray(xc, dtype=np.float64).reshape(-1, dim)
+        return np.where(xc[:, 0] < a, c1, c2)
+    return sol, speed

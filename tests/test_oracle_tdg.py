@@ -207,3 +207,115 @@ def test_polynomial_reproduction_wave_speed(dim, p, which, cval):
     F, tau, ex, _, _ = _run(mesh, p, T, sol, inputs.pitch_kappa(mesh))
     assert np.all(tau == T)
     assert np.abs(F - ex).max() <= 1e-11 * max(1.0, np.abs(ex).max())
+
+
+@pytest.mark.parametrize("dim,p,c1,c2", [(1, 2, 1.0, 2.5), (1, 4, 3.0, 1.0), (2, 2, 1.0, 3.0),
+                                         (2, 3, 2.0, 1.0)])
+def test_interface_reproduction(dim, p, c1, c2):
+    """Section 4.2: tents that straddle a jump of c carry one polynomial per
+    material, coupled on the time-like facets; an exact piecewise-quadratic
+    solution with continuous U and sigma.n is reproduced to rounding."""
+    mesh = inputs.mesh_interval(6) if dim == 1 else inputs.mesh_square(4, 0.0, seed=1)
+    sol, speed = inputs.interface_solution(dim, 0.5, c1, c2)
+    mesh.c[:] = speed(mesh.coords[mesh.elems].mean(axis=1))
+    T = 0.2
+    F, tau, ex, _, _ = _run(mesh, p, T, sol, inputs.pitch_kappa(mesh))
+    assert np.all(tau == T)
+    assert np.abs(F - ex).max() <= 1e-11 * max(1.0, np.abs(ex).max())
+
+
+def test_interface_mismatched_speed_not_reproduced():
+    """Sanity for the test above: with speeds that do not match the solution
+    the piecewise quadratic is not a discrete solution and is not reproduced."""
+    mesh = inputs.mesh_interval(6)
+    sol, speed = inputs.interface_solution(1, 0.5, 1.0, 2.5)
+    mesh.c[:] = speed(mesh.coords[mesh.elems].mean(axis=1))
+    mesh.c[mesh.c > 1.5] = 2.0          # speeds no longer match the solution
+    F, tau, ex, _, _ = _run(mesh, 2, 0.2, sol, inputs.pitch_kappa(mesh))
+    assert np.abs(F - ex).max() > 1e-6
+
+
+def test_interface_energy_decreases():
+    """With interface tents the sweep stays dissipative (Section 6.5)."""
+    mesh = inputs.mesh_square(4, 0.2, seed=3)
+    cen = mesh.coords[mesh.elems].mean(axis=1)
+    mesh.c[:] = np.where(np.linalg.norm(cen - 0.5, axis=1) < 0.3, 3.0, 1.0)
+    p = 3
+    lay = tdg.front_layout(mesh.coords, mesh.elems, p)
+    f0 = inputs.gaussian_pulse((0.5, 0.5), 0.2)
+    E0 = energy.front_energy(f0(lay.xq.reshape(-1, 2)).reshape(lay.wq.shape + (4,)), lay.wq, mesh.c)
+    r = pitching.pitch(mesh.coords, mesh.elems, mesh.c, inputs.pitch_kappa(mesh), 0.3)
+    F, tau = tdg.sweep(mesh.coords, mesh.elems, mesh.c, p, r, f0, None)
+    E1 = energy.front_energy(F, lay.wq, mesh.c)
+    assert E1 < E0
+
+
+def test_interface_energy_identity_1d():
+    """Energy identity of an interface tent (V = U_h, g_D = 0): the centred
+    interface terms reproduce the physical flux v+ s+ - v- s-, so
+        1/2 int_top Q(u) = 1/2 int_bot Q(u_b) - 1/2 int_bot Q(u - u_b)
+                           - int_bot (U - U_b) U - alpha int_F [[v]]^2 - beta int_F [[s]]^2
+    on the time-like face F = {x_v} x [t_bot, t_top] (Section 4.2)."""
+    mesh = inputs.mesh_interval(6)
+    cen = mesh.coords[mesh.elems].mean(axis=1)[:, 0]
+    mesh.c[:] = np.where(cen < 0.5, 1.0, 2.5)
+    p, alpha, beta = 3, 0.5, 0.5
+    lay = tdg.front_layout(mesh.coords, mesh.elems, p)
+    nodes, wts = np.polynomial.legendre.leggauss(12)
+    checked = []
+
+    def rec(it, d):
+        if len(d["speeds"]) < 2:
+            return
+        B, v, nb = d["basis"], d["v"], d["basis"].nb
+        tau = d["tau_before"]
+        top = rhs = 0.0
+        for k in d["patch"]:
+            g = d["groups"][k]
+            ck = d["speeds"][g]
+            xg = d["x"][g * nb:(g + 1) * nb]
+            ids = mesh.elems[k]
+            tb = tau[ids]
+            tt = np.where(ids == v, d["t_top"], tb)
+            X = mesh.coords[ids]
+            gb = (tb[1] - tb[0]) / (X[1, 0] - X[0, 0])
+            gt = (tt[1] - tt[0]) / (X[1, 0] - X[0, 0])
+            x, w = lay.xq[k], lay.wq[k]
+
+            def f(t):
+                U, V, S = B.eval_phys(x, t, d["xc"], d["tc"], d["h"], ck)
+                return U @ xg, V @ xg, S[:, 0, :] @ xg
+
+            Ut, Vt, St = f(lay.bary @ tt)
+            Ub, Vb, Sb = f(lay.bary @ tb)
+            fb = d["front_before"][k]
+
+            def Qg(vv, ss, gg):
+                return vv * vv / ck ** 2 + ss * ss - 2 * vv * ss * gg
+
+            top += 0.5 * np.sum(w * Qg(Vt, St, gt))
+            rhs += 0.5 * np.sum(w * Qg(fb[:, 1], fb[:, 2], gb))
+            rhs -= 0.5 * np.sum(w * Qg(Vb - fb[:, 1], Sb - fb[:, 2], gb))
+            rhs -= np.sum(w * (Ub - fb[:, 0]) * Ub)
+        tq = d["t_bot"] + (d["t_top"] - d["t_bot"]) * 0.5 * (nodes + 1)
+        xv = np.full((len(tq), 1), mesh.coords[v, 0])
+        vals = {}
+        for k in d["patch"]:
+            g = d["groups"][k]
+            _, V, S = B.eval_phys(xv, tq, d["xc"], d["tc"], d["h"], d["speeds"][g])
+            vals[k] = (V @ d["x"][g * nb:(g + 1) * nb], S[:, 0, :] @ d["x"][g * nb:(g + 1) * nb])
+        kl, kr = sorted(d["patch"])
+        jw = 0.5 * (d["t_top"] - d["t_bot"]) * wts
+        rhs -= alpha * np.sum(jw * (vals[kl][0] - vals[kr][0]) ** 2)
+        rhs -= beta * np.sum(jw * (vals[kl][1] - vals[kr][1]) ** 2)
+        checked.append(abs(top - rhs) / (abs(top) + 1e-30))
+
+    r = pitching.pitch(mesh.coords, mesh.elems, mesh.c, 0.9, 0.5)
+    tdg.sweep(mesh.coords, mesh.elems, mesh.c, p, r, _sinsin_1d_init, None, alpha=alpha, beta=beta,
+              record=rec)
+    assert len(checked) >= 3
+    assert max(checked) < 1e-12
+
+
+def _sinsin_1d_init(x):
+    return _sinsin_1d(x, 0.3)
