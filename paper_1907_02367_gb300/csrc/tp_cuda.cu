@@ -49,12 +49,12 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kMaxPair = 4;      // Gram pairs per thread (nb (nb+1)/2 <= 4 * 256)
-constexpr int kMaxRefine = 8;    // refinement steps of the mixed path
+constexpr int kMaxRefine = 40;   // refinement steps of the mixed path
 
 struct KArgs {
-  int nb, nmono, Q, nrhs, CH, mono_stride;
+  int nb, nmono, Q, nrhs, CH, mono_stride, ngmax;
   int64_t ne, n_bnd;
-  double alpha;
+  double alpha, beta;
   const double* X;
   const int* elems;
   const double* cK;
@@ -64,6 +64,12 @@ struct KArgs {
   const int* vfac;
   const int* facet_vert;
   const double* facet_nrm;
+  const int* facet_elem;      // element owning each boundary facet
+  const int* ifac_ptr;        // per vertex: time-like interface facets through it (CSR)
+  const int* ifac_vert;       // dim vertex ids per interface facet
+  const double* ifac_nrm;     // unit normal out of the + element
+  const int* ifac_kp;         // + element (lower index of the two)
+  const int* ifac_km;         // - element
   const double* bary;     // Q * (dim+1)
   const double* wref;     // Q
   const double* sqw;      // Q, sqrt(wref)
@@ -93,8 +99,8 @@ struct KArgs {
   const float* rel_facf;      // relation factors (small integers) in binary32
   const float* relT_facf;
   int off_al, off_eq, off_perm, off_z, off_x;   // mixed path: binary32 LU and refinement
-  int off_b, off_pg, off_ph, off_pgb, off_pm, off_pd, off_pbd, off_sg, off_sm, off_f, off_del, off_u,
-      off_mono, off_cb, off_gd, off_y, off_rd;
+  int off_b, off_pg, off_ph, off_pgb, off_pm, off_pd, off_pbd, off_sg, off_sm, off_f, off_f2, off_fpm, off_del,
+      off_u, off_mono, off_cb, off_gd, off_y, off_rd;
 };
 
 __device__ __forceinline__ void flag_error(const KArgs& a, int code, long long info) {
@@ -315,27 +321,80 @@ __device__ __forceinline__ double recip(double x) {
   return fma(r, e, r);
 }
 
+// (D_va X D_vb^T)_ij for a full row-major nb x nb X (or X^T when TR)
+template <int DIM, typename T, bool TR>
+__device__ __forceinline__ T congruence_full(const KArgs& a, int i, int va, int j, int vb, const T* X, int nb) {
+  constexpr int NVAR = DIM + 1;
+  const int a0 = __ldg(a.rel_ptr + i * NVAR + va), a1 = __ldg(a.rel_ptr + i * NVAR + va + 1);
+  const int b0 = __ldg(a.rel_ptr + j * NVAR + vb), b1 = __ldg(a.rel_ptr + j * NVAR + vb + 1);
+  T s = Ar<T>::zero();
+  for (int e = a0; e < a1; ++e) {
+    const int si = __ldg(a.rel_src + e);
+    T t = Ar<T>::zero();
+    for (int f = b0; f < b1; ++f) {
+      const int sj = __ldg(a.rel_src + f);
+      t = Ar<T>::add(t, Ar<T>::mulf(TR ? X[sj * nb + si] : X[si * nb + sj], __ldg(a.rel_facf + f)));
+    }
+    s = Ar<T>::add(s, Ar<T>::mulf(t, __ldg(a.rel_facf + e)));
+  }
+  return s;
+}
+
+// n-weighted normal-derivative congruences: (D_a X D_b^T) with a, b in {t, n}
+// where D_n = sum_m n_m D_m.  SYM: X packed symmetric, else full (TR: X^T).
+template <int DIM, typename T, int MODE>
+__device__ __forceinline__ T cong_any(const KArgs& a, int i, int va, int j, int vb, const T* X, int nb) {
+  if constexpr (MODE == 0) return congruence<DIM, T>(a, i, va, j, vb, X, nb);
+  else if constexpr (MODE == 1) return congruence_full<DIM, T, false>(a, i, va, j, vb, X, nb);
+  else return congruence_full<DIM, T, true>(a, i, va, j, vb, X, nb);
+}
+template <int DIM, typename T, int MODE>
+__device__ __forceinline__ void iface_terms(const KArgs& a, int i, int j, const T* X, int nb, const T* nrm,
+                                            T* ntn, T* ntt, T* ttn, T* nnn) {
+  // ntt = (D_n X D_t^T), ttn = (D_t X D_n^T), nnn = (D_n X D_n^T), ntn unused slot kept for symmetry
+  T a1 = Ar<T>::zero(), a2 = Ar<T>::zero(), a3 = Ar<T>::zero();
+  for (int m = 0; m < DIM; ++m) {
+    a1 = Ar<T>::fma(nrm[m], cong_any<DIM, T, MODE>(a, i, 1 + m, j, 0, X, nb), a1);
+    a2 = Ar<T>::fma(nrm[m], cong_any<DIM, T, MODE>(a, i, 0, j, 1 + m, X, nb), a2);
+    for (int m2 = 0; m2 < DIM; ++m2)
+      a3 = Ar<T>::fma(Ar<T>::mul(nrm[m], nrm[m2]), cong_any<DIM, T, MODE>(a, i, 1 + m, j, 1 + m2, X, nb), a3);
+  }
+  *ntt = a1;
+  *ttn = a2;
+  *nnn = a3;
+  *ntn = cong_any<DIM, T, MODE>(a, i, 0, j, 0, X, nb);   // (D_t X D_t^T)
+}
+
 // One tent per thread-block cluster of CS CTAs (CS = gridDim.x / tents in the
 // launch, 1..8).  Each CTA takes a slice of the patch's points.
 //
+// Materials (Section 4.2).  The patch elements are grouped by wave speed; each
+// group g carries its own polynomial x_g in U^p mapped with its own c_g
+// (Remark 3.1), so the tent system has ng*nb unknowns.
+//
 // Assembly through Grams of U-values.  With u the vector of the nb U-values
 // at a point and the exact derivative maps of U^p, v = (c/h) D_t u,
-// sigma_m = -(1/h) D_m u, the top-face form summed over the points of the
-// patch is
+// sigma_m = -(1/h) D_m u, the top-face form of group g summed over its points is
 //   A_top = h^-2 [ D_t G D_t^T + sum_m D_m G D_m^T + c sum_m (D_m H_m D_t^T + D_t H_m D_m^T) ],
 //   G = sum_q w u u^T,  H_m = sum_K g_{K,m} G_K  (g = top front gradient on K),
 // the recovery term is A_bot = sum_q w u_b u_b^T, the bottom data give
 //   b = gamma + (c/h) D_t alpha - (1/h) sum_m D_m beta_m
 // with moments gamma = sum w U_b u_b, alpha = sum w (c^-2 v_b - s_b.g_b) u_b,
-// beta_m = sum w (s_b,m - v_b g_b,m) u_b, and a Dirichlet facet with normal n
+// beta_m = sum w (s_b,m - v_b g_b,m) u_b.  A Dirichlet facet with normal n
 // adds A_D = (c/h) D_t F E^T, b_D = E' delta, F = sum w u u^T,
-// delta = sum w g_D u, E = alpha_D (c/h) D_t - (1/h) sum_m n_m D_m,
-// E' = alpha_D (c/h) D_t + (1/h) sum_m n_m D_m.  Every CTA publishes its
-// partial Grams and moments; after a cluster barrier every CTA sums them in
-// rank order, forms A and b, solves, and writes the outflow of its slice.
+// delta = sum w g_D u, E = alpha_D (c/h) D_t - (1/h) D_n, E' = alpha_D (c/h) D_t + (1/h) D_n,
+// D_n = sum_m n_m D_m.  A time-like facet between groups + and - (normal n out
+// of +) adds, for test side t and trial side s (signs s_+ = 1, s_- = -1),
+//   A^{ts} = s_t h^-2 [ -c_s/2 D_n F^{ts} D_t^T - c_t/2 D_t F^{ts} D_n^T ]
+//          + s_t s_s h^-2 [ alpha c_s c_t D_t F^{ts} D_t^T + beta D_n F^{ts} D_n^T ],
+//   F^{ts} = sum w u^t u^s^T,
+// the {v}[[tau]]_N + {s}.[[w]]_N + alpha [[v]]_N.[[w]]_N + beta [[s]]_N [[tau]]_N
+// terms of eq. (2.5).  Every CTA publishes its partial Grams and moments;
+// after a cluster barrier every CTA sums them in rank order, forms A and b,
+// solves, and writes the outflow of its slice.
 //
 // MIXED = false: everything in binary64, LU with partial pivoting (none for
-// interior tents, whose A is symmetric positive definite).
+// single-material interior tents, whose A is symmetric positive definite).
 // MIXED = true: assembly, residual and outflow in float-float; A is
 // equilibrated (D A D, D = |diag A|^-1/2), factorised in binary32 and the
 // solution refined against the float-float A until the correction stops
@@ -357,16 +416,19 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
   constexpr int NV = DIM + 1;   // vertices per element
   constexpr int C = DIM + 2;    // U, v, sigma  (and gamma, alpha, beta_m moments)
   extern __shared__ __align__(16) double sm[];
-  __shared__ int s_P, s_v, s_nfac;
-  __shared__ double s_ttop, s_tbot, s_tc, s_ih, s_c, s_ic2;
+  __shared__ int s_P, s_v, s_nfac, s_nif, s_ng;
+  __shared__ double s_ttop, s_tbot, s_tc, s_ih;
+  __shared__ double s_gc[tp::kMaxGroups];
   __shared__ double s_xv[DIM];
-  __shared__ int s_el[tp::kMaxPatch];
+  __shared__ int s_el[tp::kMaxPatch], s_grp[tp::kMaxPatch];
   __shared__ double s_X[tp::kMaxPatch][NV][DIM];
   __shared__ double s_tb[tp::kMaxPatch][NV], s_tt[tp::kMaxPatch][NV];
   __shared__ double s_gb[tp::kMaxPatch][DIM], s_gt[tp::kMaxPatch][DIM];
   __shared__ double s_sdet[tp::kMaxPatch];
-  __shared__ double s_fP[tp::kMaxFacets][NV][DIM + 1];   // Dirichlet face simplices (x, t)
+  __shared__ double s_fP[tp::kMaxFacets][NV][DIM + 1];   // vertical face simplices (x, t)
   __shared__ double s_fscale[tp::kMaxFacets], s_fn[tp::kMaxFacets][DIM];
+  __shared__ int s_fg[tp::kMaxFacets], s_fg2[tp::kMaxFacets];   // groups (Dirichlet: one; interface: +, -)
+  __shared__ int s_pgrp[2 * 64];
   __shared__ int s_piv;
   __shared__ float s_red[2][kThreads / 32];
   __shared__ int s_stop;
@@ -377,50 +439,70 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
   const int tent = tent0 + blockIdx.x / CS;
-  const int nb = a.nb, Q = a.Q, nrhs = a.nrhs, CH = a.CH;
+  const int nb = a.nb, Q = a.Q, nrhs = a.nrhs, CH = a.CH, NG = a.ngmax;
   const int npair = nb * (nb + 1) / 2;
   const int nmom = nrhs * C * nb;
-  T* sA = reinterpret_cast<T*>(sm);                  // nb*nb      assembled A, then LU factors
-  T* sb = reinterpret_cast<T*>(sm + a.off_b);        // nrhs*nb    assembled b, then x
-  T* sPG = reinterpret_cast<T*>(sm + a.off_pg);      // npair      this CTA: G (top)
-  T* sPH = reinterpret_cast<T*>(sm + a.off_ph);      // DIM*npair  this CTA: H_m
-  T* sPGb = reinterpret_cast<T*>(sm + a.off_pgb);    // npair      this CTA: G (bottom, recovery)
-  T* sPM = reinterpret_cast<T*>(sm + a.off_pm);      // nmom       this CTA: moments (gamma, alpha, beta_m) per rhs
-  T* sPD = reinterpret_cast<T*>(sm + a.off_pd);      // nb*nb      this CTA: Dirichlet A part
-  T* sPBD = reinterpret_cast<T*>(sm + a.off_pbd);    // nrhs*nb    this CTA: Dirichlet b part
-  T* sSG = reinterpret_cast<T*>(sm + a.off_sg);      // (DIM+2)*npair  summed G, H_m, Gbot
-  T* sSM = reinterpret_cast<T*>(sm + a.off_sm);      // nmom       summed moments
-  T* sF = reinterpret_cast<T*>(sm + a.off_f);        // npair      facet Gram
+  T* sA = reinterpret_cast<T*>(sm);                  // N*N        assembled A, then LU factors
+  T* sb = reinterpret_cast<T*>(sm + a.off_b);        // nrhs*N     assembled b, then x
+  T* sPG = reinterpret_cast<T*>(sm + a.off_pg);      // NG*npair   this CTA: G (top) per group
+  T* sPH = reinterpret_cast<T*>(sm + a.off_ph);      // NG*DIM*npair  H_m
+  T* sPGb = reinterpret_cast<T*>(sm + a.off_pgb);    // NG*npair   G (bottom, recovery)
+  T* sPM = reinterpret_cast<T*>(sm + a.off_pm);      // NG*nmom    moments (gamma, alpha, beta_m) per rhs
+  T* sPD = reinterpret_cast<T*>(sm + a.off_pd);      // N*N        Dirichlet and interface blocks
+  T* sPBD = reinterpret_cast<T*>(sm + a.off_pbd);    // nrhs*N     Dirichlet right-hand side
+  T* sSG = reinterpret_cast<T*>(sm + a.off_sg);      // NG*(DIM+2)*npair  summed G, H_m, Gbot
+  T* sSM = reinterpret_cast<T*>(sm + a.off_sm);      // NG*nmom    summed moments
+  T* sF = reinterpret_cast<T*>(sm + a.off_f);        // npair      facet Gram (+ side)
+  T* sF2 = reinterpret_cast<T*>(sm + a.off_f2);      // npair      facet Gram (- side)
+  T* sFpm = reinterpret_cast<T*>(sm + a.off_fpm);    // nb*nb      facet Gram (+ test, - trial)
   T* sDel = reinterpret_cast<T*>(sm + a.off_del);    // nrhs*nb    facet moments delta
   T* sU = reinterpret_cast<T*>(sm + a.off_u);        // 2*CH*nb    U-values (scaled) per (side, point)
   T* sM = reinterpret_cast<T*>(sm + a.off_mono);     // 2*CH*mono_stride
-  T* sCB = reinterpret_cast<T*>(sm + a.off_cb);      // CH*nrhs*C  bottom data coefficients
+  T* sCB = reinterpret_cast<T*>(sm + a.off_cb);      // CH*nrhs*C  data coefficients
   T* sGd = reinterpret_cast<T*>(sm + a.off_gd);      // CH*nrhs    Dirichlet data coefficients
-  T* sY = reinterpret_cast<T*>(sm + a.off_y);        // nrhs*C*nb  outflow coefficient vectors
-  double* sRD = sm + a.off_rd;                       // nb         reciprocal pivots (binary64 path)
+  T* sY = reinterpret_cast<T*>(sm + a.off_y);        // NG*nmom    outflow coefficient vectors
+  double* sRD = sm + a.off_rd;                       // N          reciprocal pivots (binary64 path)
 
-  // ---------------- phase 0: tent and patch geometry ----------------
+  // ---------------- phase 0: tent, materials and patch geometry ----------------
   if (tid == 0) {
     const int v = a.tent_v[tent];
     s_v = v;
     const int p0 = a.star_ptr[v], p1 = a.star_ptr[v + 1];
-    s_P = p1 - p0;
+    const int P = p1 - p0;
+    s_P = P;
     s_ttop = a.tent_ttop[tent];
     s_tbot = ADJ ? a.tent_tbot[tent] : a.tau[v];
     s_tc = 0.5 * (s_tbot + s_ttop);
     s_ih = 1.0 / a.tent_h[tent];
-    const double c = a.cK[a.star_el[p0]];
-    s_c = c;
-    s_ic2 = 1.0 / (c * c);
     for (int d = 0; d < DIM; ++d) s_xv[d] = a.X[(int64_t)v * DIM + d];
     s_nfac = a.vfac_ptr[v + 1] - a.vfac_ptr[v];
+    s_nif = a.ifac_ptr[v + 1] - a.ifac_ptr[v];
+    // materials by bitwise-equal c in order of first appearance; elements sorted by material
+    int ng = 0, tmp[tp::kMaxPatch];
+    for (int k = 0; k < P; ++k) {
+      const double ck = a.cK[a.star_el[p0 + k]];
+      int g = 0;
+      while (g < ng && s_gc[g] != ck) ++g;
+      if (g == ng) s_gc[ng++] = ck;
+      tmp[k] = g;
+    }
+    int pos = 0;
+    for (int g = 0; g < ng; ++g)
+      for (int k = 0; k < P; ++k)
+        if (tmp[k] == g) {
+          s_el[pos] = a.star_el[p0 + k];
+          s_grp[pos++] = g;
+        }
+    s_ng = ng;
   }
-  for (int id = tid; id < nmom; id += blockDim.x) sPM[id] = R::zero();
+  for (int id = tid; id < NG * nmom; id += blockDim.x) sPM[id] = R::zero();
+  for (int id = tid; id < NG * (DIM + 2) * npair; id += blockDim.x) sPG[id] = R::zero();   // PG, PH, PGb contiguous
   __syncthreads();
-  const int P = s_P, v = s_v, nfac = s_nfac;
+  const int P = s_P, v = s_v, nfac = s_nfac, nif = s_nif, ng = s_ng;
+  const int N = ng * nb;
+  const bool extra = (nfac > 0 || nif > 0);
   for (int k = tid; k < P; k += blockDim.x) {
-    const int el = a.star_el[a.star_ptr[v] + k];
-    s_el[k] = el;
+    const int el = s_el[k];
     for (int i = 0; i < NV; ++i) {
       const int vi = a.elems[(int64_t)el * NV + i];
       for (int d = 0; d < DIM; ++d) s_X[k][i][d] = a.X[(int64_t)vi * DIM + d];
@@ -444,21 +526,26 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
       g2 += gt[d] * gt[d];
     }
     s_sdet[k] = sqrt(fabs(det));
-    if (!(s_ic2 - g2 > 0.0)) flag_error(a, TP_ERR_CAUSALITY, tent);   // space-like top face
+    const double ck = s_gc[s_grp[k]];
+    if (!(1.0 / (ck * ck) - g2 > 0.0)) flag_error(a, TP_ERR_CAUSALITY, tent);   // space-like top face
   }
-  // Dirichlet face simplices (x_v, t_bot), (x_v, t_top), (x_w, tau_w)
-  for (int f = tid; f < nfac; f += blockDim.x) {
-    const int fid = a.vfac[a.vfac_ptr[v] + f];
+  // vertical face simplices (x_v, t_bot), (x_v, t_top), (x_w, tau_w): Dirichlet facets
+  // first, then the time-like interface facets
+  for (int f = tid; f < nfac + nif; f += blockDim.x) {
+    const bool dir = f < nfac;
+    const int fid = dir ? a.vfac[a.vfac_ptr[v] + f] : a.ifac_ptr[v] + (f - nfac);
+    const int* fv = dir ? a.facet_vert + (int64_t)fid * DIM : a.ifac_vert + (int64_t)fid * DIM;
+    const double* fn = dir ? a.facet_nrm + (int64_t)fid * DIM : a.ifac_nrm + (int64_t)fid * DIM;
     for (int d = 0; d < DIM; ++d) {
       s_fP[f][0][d] = a.X[(int64_t)v * DIM + d];
       s_fP[f][1][d] = a.X[(int64_t)v * DIM + d];
-      s_fn[f][d] = a.facet_nrm[(int64_t)fid * DIM + d];
+      s_fn[f][d] = fn[d];
     }
-    s_fP[f][0][DIM] = ADJ ? a.tent_tbot[tent] : a.tau[v];
-    s_fP[f][1][DIM] = a.tent_ttop[tent];
+    s_fP[f][0][DIM] = s_tbot;
+    s_fP[f][1][DIM] = s_ttop;
     int c2 = 2;
     for (int i = 0; i < DIM; ++i) {
-      const int w = a.facet_vert[(int64_t)fid * DIM + i];
+      const int w = fv[i];
       if (w == v) continue;
       for (int d = 0; d < DIM; ++d) s_fP[f][c2][d] = a.X[(int64_t)w * DIM + d];
       s_fP[f][c2][DIM] = a.tau[w];
@@ -473,6 +560,20 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
         G[i][j] = s;
       }
     s_fscale[f] = sqrt(fabs(small_det<DIM>(G)));
+    // groups of the facet's element(s), found by their wave speed
+    auto group_of = [&](int el) {
+      const double ce = a.cK[el];
+      int g = 0;
+      while (g < ng - 1 && s_gc[g] != ce) ++g;
+      return g;
+    };
+    if (dir) {
+      s_fg[f] = group_of(a.facet_elem[fid]);
+      s_fg2[f] = s_fg[f];
+    } else {
+      s_fg[f] = group_of(a.ifac_kp[fid]);
+      s_fg2[f] = group_of(a.ifac_km[fid]);
+    }
   }
   // Gram pairs owned by this thread (upper triangle, i <= j, row-major order)
   int pi[kMaxPair], pj[kMaxPair];
@@ -501,15 +602,46 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
   const int NP = P * Q;
   const int slice = (NP + CS - 1) / CS;
   const int q0 = min(NP, rank * slice), q1 = min(NP, q0 + slice);
-  const double c = s_c, ih = s_ih, ic2 = s_ic2, tc = s_tc;
+  const double ih = s_ih, tc = s_tc;
   int curk = q0 / Q;
+  int curg = (q1 > q0) ? s_grp[curk] : 0;
+  // element flush: G += G_K, H_m += g_{K,m} G_K;  group flush: publish G, H, Gbot of the group
+  auto flush_element = [&](int k) {
+    T g[DIM];
+    for (int d = 0; d < DIM; ++d) g[d] = R::from(s_gt[k][d]);
+#pragma unroll
+    for (int s = 0; s < kMaxPair; ++s) {
+      aG[s] = R::add(aG[s], aK[s]);
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) aH[s][d] = R::fma(g[d], aK[s], aH[s][d]);
+      aK[s] = R::zero();
+    }
+  };
+  auto flush_group = [&](int g) {
+#pragma unroll
+    for (int s = 0; s < kMaxPair; ++s) {
+      const int id = tid + s * kThreads;
+      if (id < npair) {
+        sPG[g * npair + id] = R::add(sPG[g * npair + id], aG[s]);
+#pragma unroll
+        for (int d = 0; d < DIM; ++d)
+          sPH[(g * DIM + d) * npair + id] = R::add(sPH[(g * DIM + d) * npair + id], aH[s][d]);
+        sPGb[g * npair + id] = R::add(sPGb[g * npair + id], aB[s]);
+      }
+      aG[s] = aB[s] = R::zero();
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) aH[s][d] = R::zero();
+    }
+  };
   for (int base = q0; base < q1; base += CH) {
     const int nq = min(CH, q1 - base);
-    // (a) one thread per (side, point): sqrt(w)-scaled U-values, bottom data coefficients
+    // (a) one thread per (side, point): sqrt(w)-scaled U-values, data coefficients
     if (tid < 2 * CH) {
       const int side = tid / CH, ql = tid % CH, qg = base + ql;
       if (ql < nq) {
-        const int k = qg / Q, q = qg % Q;
+        const int k = qg / Q, q = qg % Q, g = s_grp[k];
+        const double cg = s_gc[g], ic2 = 1.0 / (cg * cg);
+        if (side == 0) s_pgrp[ql] = g;
         double x[DIM], tt = 0.0;
         for (int d = 0; d < DIM; ++d) x[d] = 0.0;
         for (int i = 0; i < NV; ++i) {
@@ -519,12 +651,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
         }
         T xh[DIM];
         for (int d = 0; d < DIM; ++d) xh[d] = R::from((x[d] - s_xv[d]) * ih);
-        const T th = R::from(c * (tt - tc) * ih);
+        const T th = R::from(cg * (tt - tc) * ih);
         const double sw = __ldg(a.sqw + q) * s_sdet[k];
         eval_uvalues<DIM, T>(a, th, xh, sM + tid * a.mono_stride, R::from(sw), sU + (size_t)tid * nb);
+        const int el = s_el[k];
         if (ADJ && side == 0) {
           // adjoint: zeta = sum_q lambda_q u_q over the top points
-          const int el = s_el[k];
           const double isw = 1.0 / sw;
           for (int r = 0; r < nrhs; ++r) {
             const double* f = a.front + (((int64_t)r * a.ne + el) * Q + q) * C;
@@ -533,7 +665,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
           }
         }
         if (!ADJ && side == 1) {
-          const int el = s_el[k];
           for (int r = 0; r < nrhs; ++r) {
             const double* f = a.front + (((int64_t)r * a.ne + el) * Q + q) * C;
             const double Ub = f[0], vb = f[1];
@@ -548,18 +679,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
       }
     }
     __syncthreads();
-    // (b) Grams of U-values: top per element (flushed into G and H_m), bottom
+    // (b) Grams of U-values: top per element (flushed into G and H_m), bottom; per material
     for (int ql = 0; ql < nq; ++ql) {
       const int k = (base + ql) / Q;
       if (k != curk) {
-        T g[DIM];
-        for (int d = 0; d < DIM; ++d) g[d] = R::from(s_gt[curk][d]);
-#pragma unroll
-        for (int s = 0; s < kMaxPair; ++s) {
-          aG[s] = R::add(aG[s], aK[s]);
-#pragma unroll
-          for (int d = 0; d < DIM; ++d) aH[s][d] = R::fma(g[d], aK[s], aH[s][d]);
-          aK[s] = R::zero();
+        flush_element(curk);
+        if (s_grp[k] != curg) {
+          flush_group(curg);
+          curg = s_grp[k];
         }
         curk = k;
       }
@@ -573,47 +700,39 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
         }
       }
     }
-    // (c) moments of the bottom data
-    for (int id = tid; id < nmom; id += blockDim.x) {
-      const int r = id / (C * nb), rem = id % (C * nb), cc = rem / nb, i = rem % nb;
+    // (c) moments of the data (forward: bottom points; adjoint: top points), per material
+    const int row0 = ADJ ? 0 : CH;
+    for (int id = tid; id < ng * nmom; id += blockDim.x) {
+      const int g = id / nmom, rest = id % nmom;
+      const int r = rest / (C * nb), rem = rest % (C * nb), cc = rem / nb, i = rem % nb;
       T t = sPM[id];
-      const int row0 = ADJ ? 0 : CH;   // adjoint moments use the top points
       for (int ql = 0; ql < nq; ++ql)
-        t = R::fma(sCB[((size_t)ql * nrhs + r) * C + cc], sU[(size_t)(row0 + ql) * nb + i], t);
+        if (s_pgrp[ql] == g) t = R::fma(sCB[((size_t)ql * nrhs + r) * C + cc], sU[(size_t)(row0 + ql) * nb + i], t);
       sPM[id] = t;
     }
     __syncthreads();
   }
-  // publish this CTA's Grams
-  {
-    T g[DIM];
-    for (int d = 0; d < DIM; ++d) g[d] = R::from(q1 > q0 ? s_gt[curk][d] : 0.0);
-#pragma unroll
-    for (int s = 0; s < kMaxPair; ++s) {
-      const int id = tid + s * kThreads;
-      if (id < npair) {
-        sPG[id] = R::add(aG[s], aK[s]);
-#pragma unroll
-        for (int d = 0; d < DIM; ++d) sPH[d * npair + id] = R::fma(g[d], aK[s], aH[s][d]);
-        sPGb[id] = aB[s];
-      }
-    }
+  if (q1 > q0) {
+    flush_element(curk);
+    flush_group(curg);
   }
 
-  // ---------------- phase 2: Dirichlet faces (this CTA's slice of each facet's points) ----------------
-  if (nfac > 0) {
-    for (int id = tid; id < nb * nb; id += blockDim.x) sPD[id] = R::zero();
-    for (int id = tid; id < nrhs * nb; id += blockDim.x) {
-      sPBD[id] = R::zero();
-      sDel[id] = R::zero();
-    }
+  // ---------------- phase 2: vertical faces (this CTA's slice of each facet's points) ----------------
+  if (extra) {
+    for (int id = tid; id < N * N; id += blockDim.x) sPD[id] = R::zero();
+    for (int id = tid; id < nrhs * N; id += blockDim.x) sPBD[id] = R::zero();
+    for (int id = tid; id < nrhs * nb; id += blockDim.x) sDel[id] = R::zero();
+    for (int id = tid; id < nb * nb; id += blockDim.x) sFpm[id] = R::zero();
     const int fsl = (Q + CS - 1) / CS;
     const int f0 = min(Q, rank * fsl), f1 = min(Q, f0 + fsl);
     __syncthreads();
-    for (int f = 0; f < nfac; ++f) {
-      T aF[kMaxPair];
+    for (int f = 0; f < nfac + nif; ++f) {
+      const bool dir = f < nfac;
+      const int gp = s_fg[f], gm = s_fg2[f];
+      const double cp = s_gc[gp], cm = s_gc[gm];
+      T aF[kMaxPair], aF2[kMaxPair];
 #pragma unroll
-      for (int s = 0; s < kMaxPair; ++s) aF[s] = R::zero();
+      for (int s = 0; s < kMaxPair; ++s) aF[s] = aF2[s] = R::zero();
       for (int base = f0; base < f1; base += CH) {
         const int nq = min(CH, f1 - base);
         if (tid < nq) {
@@ -626,78 +745,127 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
           }
           T xh[DIM];
           for (int d = 0; d < DIM; ++d) xh[d] = R::from((xt[d] - s_xv[d]) * ih);
-          const T th = R::from(c * (xt[DIM] - tc) * ih);
           const double sw = sqrt(__ldg(a.wref + q) * s_fscale[f]);
-          eval_uvalues<DIM, T>(a, th, xh, sM + tid * a.mono_stride, R::from(sw), sU + (size_t)tid * nb);
-          const long long goff = a.tent_gdoff[tent] + (long long)f * Q + q;
-          for (int r = 0; r < nrhs; ++r)
-            sGd[tid * nrhs + r] = R::from((!ADJ && a.gD != nullptr) ? sw * a.gD[(long long)r * a.n_bnd + goff] : 0.0);
+          eval_uvalues<DIM, T>(a, R::from(cp * (xt[DIM] - tc) * ih), xh, sM + tid * a.mono_stride, R::from(sw),
+                               sU + (size_t)tid * nb);
+          if (!dir)
+            eval_uvalues<DIM, T>(a, R::from(cm * (xt[DIM] - tc) * ih), xh, sM + (CH + tid) * a.mono_stride,
+                                 R::from(sw), sU + (size_t)(CH + tid) * nb);
+          if (dir) {
+            const long long goff = a.tent_gdoff[tent] + (long long)f * Q + q;
+            for (int r = 0; r < nrhs; ++r)
+              sGd[tid * nrhs + r] = R::from((!ADJ && a.gD != nullptr) ? sw * a.gD[(long long)r * a.n_bnd + goff] : 0.0);
+          }
         }
         __syncthreads();
         for (int ql = 0; ql < nq; ++ql) {
           const T* u = sU + (size_t)ql * nb;
+          const T* u2 = sU + (size_t)(CH + ql) * nb;
 #pragma unroll
           for (int s = 0; s < kMaxPair; ++s)
-            if (tid + s * kThreads < npair) aF[s] = R::fma(u[pi[s]], u[pj[s]], aF[s]);
+            if (tid + s * kThreads < npair) {
+              aF[s] = R::fma(u[pi[s]], u[pj[s]], aF[s]);
+              if (!dir) aF2[s] = R::fma(u2[pi[s]], u2[pj[s]], aF2[s]);
+            }
         }
-        for (int id = tid; id < nrhs * nb; id += blockDim.x) {
-          const int r = id / nb, i = id % nb;
-          T t = sDel[id];
-          for (int ql = 0; ql < nq; ++ql) t = R::fma(sGd[ql * nrhs + r], sU[(size_t)ql * nb + i], t);
-          sDel[id] = t;
+        if (dir) {
+          for (int id = tid; id < nrhs * nb; id += blockDim.x) {
+            const int r = id / nb, i = id % nb;
+            T t = sDel[id];
+            for (int ql = 0; ql < nq; ++ql) t = R::fma(sGd[ql * nrhs + r], sU[(size_t)ql * nb + i], t);
+            sDel[id] = t;
+          }
+        } else {
+          for (int id = tid; id < nb * nb; id += blockDim.x) {
+            const int i = id / nb, j = id % nb;
+            T t = sFpm[id];
+            for (int ql = 0; ql < nq; ++ql) t = R::fma(sU[(size_t)ql * nb + i], sU[(size_t)(CH + ql) * nb + j], t);
+            sFpm[id] = t;
+          }
         }
         __syncthreads();
       }
 #pragma unroll
       for (int s = 0; s < kMaxPair; ++s)
-        if (tid + s * kThreads < npair) sF[tid + s * kThreads] = aF[s];
+        if (tid + s * kThreads < npair) {
+          sF[tid + s * kThreads] = aF[s];
+          sF2[tid + s * kThreads] = aF2[s];
+        }
       __syncthreads();
-      const T ac = R::from(a.alpha * c * ih), cih = R::from(c * ih);
-      T mn[DIM], pn[DIM];
-      for (int d = 0; d < DIM; ++d) {
-        mn[d] = R::from(-ih * s_fn[f][d]);
-        pn[d] = R::from(ih * s_fn[f][d]);
-      }
-      for (int id = tid; id < nb * nb; id += blockDim.x) {
-        const int i = id / nb, j = id % nb;
-        T t = R::mul(ac, congruence<DIM, T>(a, i, 0, j, 0, sF, nb));
-        for (int d = 0; d < DIM; ++d) t = R::fma(mn[d], congruence<DIM, T>(a, i, 0, j, 1 + d, sF, nb), t);
-        sPD[id] = R::fma(cih, t, sPD[id]);
-      }
-      for (int id = tid; id < nrhs * nb; id += blockDim.x) {
-        const int r = id / nb, i = id % nb;
-        const T* del = sDel + (size_t)r * nb;
-        T t = R::mul(ac, rel_apply<DIM, T>(a, i, 0, del));
-        for (int d = 0; d < DIM; ++d) t = R::fma(pn[d], rel_apply<DIM, T>(a, i, 1 + d, del), t);
-        sPBD[id] = R::add(sPBD[id], t);
+      T nrm[DIM];
+      for (int d = 0; d < DIM; ++d) nrm[d] = R::from(s_fn[f][d]);
+      if (dir) {
+        const T ac = R::from(a.alpha * cp * ih), cih = R::from(cp * ih), mih = R::from(-ih), pih = R::from(ih);
+        for (int id = tid; id < nb * nb; id += blockDim.x) {
+          const int i = id / nb, j = id % nb;
+          T tt_, tn_, nt_, nn_;
+          iface_terms<DIM, T, 0>(a, i, j, sF, nb, nrm, &tt_, &nt_, &tn_, &nn_);
+          // A_D = (c/h) D_t F E^T,  E = alpha (c/h) D_t - (1/h) D_n
+          const T t = R::fma(mih, tn_, R::mul(ac, tt_));
+          T* dst = sPD + (size_t)(gp * nb + i) * N + gp * nb + j;
+          *dst = R::fma(cih, t, *dst);
+        }
+        for (int id = tid; id < nrhs * nb; id += blockDim.x) {
+          const int r = id / nb, i = id % nb;
+          const T* del = sDel + (size_t)r * nb;
+          T dn = R::zero();
+          for (int d = 0; d < DIM; ++d) dn = R::fma(nrm[d], rel_apply<DIM, T>(a, i, 1 + d, del), dn);
+          // b_D = E' delta,  E' = alpha (c/h) D_t + (1/h) D_n
+          const T t = R::fma(pih, dn, R::mul(ac, rel_apply<DIM, T>(a, i, 0, del)));
+          T* dst = sPBD + (size_t)r * N + gp * nb + i;
+          *dst = R::add(*dst, t);
+        }
+      } else {
+        const double ih2 = ih * ih;
+        for (int id = tid; id < 4 * nb * nb; id += blockDim.x) {
+          const int blk = id / (nb * nb), rem = id % (nb * nb), i = rem / nb, j = rem % nb;
+          const int tside = blk >> 1, sside = blk & 1;   // 0: +, 1: -
+          const double st = tside ? -1.0 : 1.0, ss = sside ? -1.0 : 1.0;
+          const double ct = tside ? cm : cp, cs = sside ? cm : cp;
+          T tt_, nt_, tn_, nn_;
+          if (tside == sside) {
+            iface_terms<DIM, T, 0>(a, i, j, tside ? sF2 : sF, nb, nrm, &tt_, &nt_, &tn_, &nn_);
+          } else if (tside == 0) {
+            iface_terms<DIM, T, 1>(a, i, j, sFpm, nb, nrm, &tt_, &nt_, &tn_, &nn_);
+          } else {
+            iface_terms<DIM, T, 2>(a, i, j, sFpm, nb, nrm, &tt_, &nt_, &tn_, &nn_);
+          }
+          T t = R::mul(R::from(-0.5 * st * cs * ih2), nt_);
+          t = R::fma(R::from(-0.5 * st * ct * ih2), tn_, t);
+          t = R::fma(R::from(st * ss * a.alpha * cs * ct * ih2), tt_, t);
+          t = R::fma(R::from(st * ss * a.beta * ih2), nn_, t);
+          const int gr = tside ? gm : gp, gcl = sside ? gm : gp;
+          T* dst = sPD + (size_t)(gr * nb + i) * N + gcl * nb + j;
+          *dst = R::add(*dst, t);
+        }
       }
       __syncthreads();
       for (int id = tid; id < nrhs * nb; id += blockDim.x) sDel[id] = R::zero();
+      for (int id = tid; id < nb * nb; id += blockDim.x) sFpm[id] = R::zero();
       __syncthreads();
     }
   }
 
   // ---------------- cluster reduction (rank order) ----------------
   cluster.sync();
-  for (int id = tid; id < (DIM + 2) * npair; id += blockDim.x) {
-    const int blk = id / npair, pid = id % npair;   // 0: G, 1..DIM: H_m, DIM+1: Gbot
-    const T* src = (blk == 0) ? sPG : (blk <= DIM ? sPH + (blk - 1) * npair : sPGb);
+  // layout [G (NG*npair) | H_m (NG*DIM*npair) | Gbot (NG*npair)]; unused groups hold zeros
+  for (int id = tid; id < NG * (DIM + 2) * npair; id += blockDim.x) {
     T t = R::zero();
-    for (int r = 0; r < CS; ++r) t = R::add(t, cluster.map_shared_rank(src, r)[pid]);
+    for (int r = 0; r < CS; ++r) t = R::add(t, cluster.map_shared_rank(sPG, r)[id]);
     sSG[id] = t;
   }
-  for (int id = tid; id < nmom; id += blockDim.x) {
+  for (int id = tid; id < ng * nmom; id += blockDim.x) {
     T t = R::zero();
     for (int r = 0; r < CS; ++r) t = R::add(t, cluster.map_shared_rank(sPM, r)[id]);
     sSM[id] = t;
   }
-  for (int id = tid; id < nb * nb; id += blockDim.x) {
+  for (int id = tid; id < N * N; id += blockDim.x) {
     T t = R::zero();
-    if (nfac > 0)
+    if (extra)
       for (int r = 0; r < CS; ++r) t = R::add(t, cluster.map_shared_rank(sPD, r)[id]);
     sA[id] = t;
   }
-  for (int id = tid; id < nrhs * nb; id += blockDim.x) {
+  for (int id = tid; id < nrhs * N; id += blockDim.x) {
     T t = R::zero();
     if (nfac > 0)
       for (int r = 0; r < CS; ++r) t = R::add(t, cluster.map_shared_rank(sPBD, r)[id]);
@@ -705,53 +873,55 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
   }
   cluster.sync();   // no CTA leaves or reuses its partials while another still reads them
   {
-    const T* SG = sSG;
-    const T* SGb = sSG + (DIM + 1) * npair;
-    const T ih2 = R::from(ih * ih), cc_ = R::from(c), cih = R::from(c * ih), mih = R::from(-ih);
-    for (int id = tid; id < nb * nb; id += blockDim.x) {
-      const int i = id / nb, j = id % nb;
+    const T ih2 = R::from(ih * ih), mih = R::from(-ih);
+    for (int id = tid; id < ng * nb * nb; id += blockDim.x) {
+      const int g = id / (nb * nb), rem = id % (nb * nb), i = rem / nb, j = rem % nb;
+      const T* SG = sSG + (size_t)g * npair;
+      const T* SGb = sSG + (size_t)(NG * (DIM + 1) + g) * npair;
+      const T cc_ = R::from(s_gc[g]);
       T t = congruence<DIM, T>(a, i, 0, j, 0, SG, nb);
       for (int d = 0; d < DIM; ++d) {
-        const T* H = sSG + (1 + d) * npair;
+        const T* H = sSG + (size_t)(NG + g * DIM + d) * npair;
         t = R::add(t, congruence<DIM, T>(a, i, 1 + d, j, 1 + d, SG, nb));
         t = R::fma(cc_, R::add(congruence<DIM, T>(a, i, 1 + d, j, 0, H, nb), congruence<DIM, T>(a, i, 0, j, 1 + d, H, nb)), t);
       }
-      sA[id] = R::add(sA[id], R::fma(ih2, t, SGb[pair_index(i, j, nb)]));
+      T* dst = sA + (size_t)(g * nb + i) * N + g * nb + j;
+      *dst = R::add(*dst, R::fma(ih2, t, SGb[pair_index(i, j, nb)]));
     }
-    for (int id = tid; id < nrhs * nb; id += blockDim.x) {
-      const int r = id / nb, i = id % nb;
-      const T* M = sSM + (size_t)r * C * nb;   // gamma, alpha, beta_1..beta_n
-      T t = R::fma(cih, rel_apply<DIM, T>(a, i, 0, M + nb), M[i]);
+    for (int id = tid; id < ng * nrhs * nb; id += blockDim.x) {
+      const int g = id / (nrhs * nb), rem = id % (nrhs * nb), r = rem / nb, i = rem % nb;
+      const T* M = sSM + (size_t)g * nmom + (size_t)r * C * nb;   // gamma, alpha, beta_1..beta_n
+      T t = R::fma(R::from(s_gc[g] * ih), rel_apply<DIM, T>(a, i, 0, M + nb), M[i]);
       for (int d = 0; d < DIM; ++d) t = R::fma(mih, rel_apply<DIM, T>(a, i, 1 + d, M + (2 + d) * nb), t);
-      sb[id] = R::add(sb[id], t);
+      T* dst = sb + (size_t)r * N + g * nb + i;
+      *dst = R::add(*dst, t);
     }
   }
   __syncthreads();
-
   if constexpr (ADJ) {   // solve with A^T
-    for (int id = tid; id < nb * nb; id += blockDim.x) {
-      const int i = id / nb, j = id % nb;
+    for (int id = tid; id < N * N; id += blockDim.x) {
+      const int i = id / N, j = id % N;
       if (i < j) {
         const T t = sA[id];
-        sA[id] = sA[j * nb + i];
-        sA[j * nb + i] = t;
+        sA[id] = sA[j * N + i];
+        sA[j * N + i] = t;
       }
     }
     __syncthreads();
   }
 
   // ---------------- phase 3: solve ----------------
-  const bool pivoting = (nfac > 0);
+  const bool pivoting = extra || ng > 1;
   if constexpr (!MIXED) {
-    // LU (no pivoting for interior tents: A is SPD), forward elimination of b alongside
-    for (int k = 0; k < nb; ++k) {
+    // LU (no pivoting for single-material interior tents: A is SPD), forward elimination of b alongside
+    for (int k = 0; k < N; ++k) {
       if (pivoting) {
         if (warp == 0) {
           // |a_ik| compared through the bit patterns (non-negative doubles order as integers)
           unsigned long long best = 0ull;
           int bi = k;
-          for (int i = k + lane; i < nb; i += 32) {
-            const unsigned long long bits = (unsigned long long)__double_as_longlong(fabs(sA[i * nb + k]));
+          for (int i = k + lane; i < N; i += 32) {
+            const unsigned long long bits = (unsigned long long)__double_as_longlong(fabs(sA[i * N + k]));
             if (bits > best || (bits == best && i < bi)) {
               best = bits;
               bi = i;
@@ -770,21 +940,21 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
         __syncthreads();
         const int pr = s_piv;
         if (pr != k) {
-          for (int j = tid; j < nb; j += blockDim.x) {
-            const double t = sA[k * nb + j];
-            sA[k * nb + j] = sA[pr * nb + j];
-            sA[pr * nb + j] = t;
+          for (int j = tid; j < N; j += blockDim.x) {
+            const double t = sA[k * N + j];
+            sA[k * N + j] = sA[pr * N + j];
+            sA[pr * N + j] = t;
           }
           for (int r = tid; r < nrhs; r += blockDim.x) {
-            const double t = sb[r * nb + k];
-            sb[r * nb + k] = sb[r * nb + pr];
-            sb[r * nb + pr] = t;
+            const double t = sb[r * N + k];
+            sb[r * N + k] = sb[r * N + pr];
+            sb[r * N + pr] = t;
           }
         }
         __syncthreads();
       }
       if (tid == 0) {
-        double piv = sA[k * nb + k];
+        double piv = sA[k * N + k];
         if (!(fabs(piv) > 0.0) || !isfinite(piv)) {
           if (rank == 0) flag_error(a, TP_ERR_SINGULAR, tent);
           piv = 1.0;
@@ -793,54 +963,54 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
       }
       __syncthreads();
       const double rp = sRD[k];
-      const int rem = nb - k - 1;
-      for (int i = k + 1 + tid; i < nb; i += blockDim.x) sA[i * nb + k] *= rp;   // multipliers
+      const int rem = N - k - 1;
+      for (int i = k + 1 + tid; i < N; i += blockDim.x) sA[i * N + k] *= rp;   // multipliers
       __syncthreads();
       for (int id = tid; id < rem * (rem + nrhs); id += blockDim.x) {
         const int i = k + 1 + id / (rem + nrhs), jj = id % (rem + nrhs);
-        const double l = sA[i * nb + k];
+        const double l = sA[i * N + k];
         if (jj < rem) {
           const int j = k + 1 + jj;
-          sA[i * nb + j] = fma(-l, sA[k * nb + j], sA[i * nb + j]);
+          sA[i * N + j] = fma(-l, sA[k * N + j], sA[i * N + j]);
         } else {
           const int r = jj - rem;
-          sb[r * nb + i] = fma(-l, sb[r * nb + k], sb[r * nb + i]);
+          sb[r * N + i] = fma(-l, sb[r * N + k], sb[r * N + i]);
         }
       }
       __syncthreads();
     }
-    for (int k = nb - 1; k >= 0; --k) {
-      for (int r = tid; r < nrhs; r += blockDim.x) sb[r * nb + k] *= sRD[k];
+    for (int k = N - 1; k >= 0; --k) {
+      for (int r = tid; r < nrhs; r += blockDim.x) sb[r * N + k] *= sRD[k];
       __syncthreads();
       for (int id = tid; id < k * nrhs; id += blockDim.x) {
         const int r = id / k, i = id % k;
-        sb[r * nb + i] = fma(-sA[i * nb + k], sb[r * nb + k], sb[r * nb + i]);
+        sb[r * N + i] = fma(-sA[i * N + k], sb[r * N + k], sb[r * N + i]);
       }
       __syncthreads();
     }
   } else {
-    float* sAL = reinterpret_cast<float*>(sm + a.off_al);   // nb*nb   equilibrated binary32 LU
-    float* sEq = reinterpret_cast<float*>(sm + a.off_eq);   // nb      equilibration scales
-    int* sPerm = reinterpret_cast<int*>(sm + a.off_perm);   // nb      row interchanges
-    float* sZ = reinterpret_cast<float*>(sm + a.off_z);     // nrhs*nb correction (binary32)
-    T* sX = reinterpret_cast<T*>(sm + a.off_x);             // nrhs*nb iterate
-    for (int i = tid; i < nb; i += blockDim.x) {
-      const float d = fabsf(sA[i * nb + i].hi);
+    float* sAL = reinterpret_cast<float*>(sm + a.off_al);   // N*N     equilibrated binary32 LU
+    float* sEq = reinterpret_cast<float*>(sm + a.off_eq);   // N       equilibration scales
+    int* sPerm = reinterpret_cast<int*>(sm + a.off_perm);   // N       row interchanges
+    float* sZ = reinterpret_cast<float*>(sm + a.off_z);     // nrhs*N  correction (binary32)
+    T* sX = reinterpret_cast<T*>(sm + a.off_x);             // nrhs*N  iterate
+    for (int i = tid; i < N; i += blockDim.x) {
+      const float d = fabsf(sA[i * N + i].hi);
       sEq[i] = (d > 0.f && isfinite(d)) ? rsqrtf(d) : 1.f;
     }
-    for (int id = tid; id < nrhs * nb; id += blockDim.x) sX[id] = R::zero();
+    for (int id = tid; id < nrhs * N; id += blockDim.x) sX[id] = R::zero();
     __syncthreads();
-    for (int id = tid; id < nb * nb; id += blockDim.x) sAL[id] = sA[id].hi * sEq[id / nb] * sEq[id % nb];
+    for (int id = tid; id < N * N; id += blockDim.x) sAL[id] = sA[id].hi * sEq[id / N] * sEq[id % N];
     __syncthreads();
     // binary32 LU of D A D by warp 0 (lane owns rows lane, lane+32, ...)
     if (warp == 0) {
-      for (int k = 0; k < nb; ++k) {
+      for (int k = 0; k < N; ++k) {
         int pr = k;
         if (pivoting) {
           float best = -1.f;
           int bi = k;
-          for (int i = k + lane; i < nb; i += 32) {
-            const float val = fabsf(sAL[i * nb + k]);
+          for (int i = k + lane; i < N; i += 32) {
+            const float val = fabsf(sAL[i * N + k]);
             if (val > best) {
               best = val;
               bi = i;
@@ -856,24 +1026,24 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
           }
           pr = __shfl_sync(0xffffffffu, bi, 0);
           if (pr != k)
-            for (int j = lane; j < nb; j += 32) {
-              const float t = sAL[k * nb + j];
-              sAL[k * nb + j] = sAL[pr * nb + j];
-              sAL[pr * nb + j] = t;
+            for (int j = lane; j < N; j += 32) {
+              const float t = sAL[k * N + j];
+              sAL[k * N + j] = sAL[pr * N + j];
+              sAL[pr * N + j] = t;
             }
           __syncwarp();
         }
         if (lane == 0) sPerm[k] = pr;
-        float piv = sAL[k * nb + k];
+        float piv = sAL[k * N + k];
         if (!(fabsf(piv) > 0.f) || !isfinite(piv)) {
           if (lane == 0 && rank == 0) flag_error(a, TP_ERR_SINGULAR, tent);
           piv = 1.f;
         }
         const float rp = 1.f / piv;
-        for (int i = k + 1 + lane; i < nb; i += 32) {
-          const float l = sAL[i * nb + k] * rp;
-          sAL[i * nb + k] = l;
-          for (int j = k + 1; j < nb; ++j) sAL[i * nb + j] = fmaf(-l, sAL[k * nb + j], sAL[i * nb + j]);
+        for (int i = k + 1 + lane; i < N; i += 32) {
+          const float l = sAL[i * N + k] * rp;
+          sAL[i * N + k] = l;
+          for (int j = k + 1; j < N; ++j) sAL[i * N + j] = fmaf(-l, sAL[k * N + j], sAL[i * N + j]);
         }
         __syncwarp();
       }
@@ -882,19 +1052,19 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
     // refinement: r = b - A x (float-float), z = (D A D)^-1 D r, x += D z
     float prev = 3.4e38f;
     for (int it = 0; it < kMaxRefine; ++it) {
-      for (int id = tid; id < nrhs * nb; id += blockDim.x) {
-        const int r = id / nb, i = id % nb;
+      for (int id = tid; id < nrhs * N; id += blockDim.x) {
+        const int r = id / N, i = id % N;
         T t = sb[id];
-        const T* xr = sX + (size_t)r * nb;
-        for (int j = 0; j < nb; ++j) t = R::sub(t, R::mul(sA[i * nb + j], xr[j]));
+        const T* xr = sX + (size_t)r * N;
+        for (int j = 0; j < N; ++j) t = R::sub(t, R::mul(sA[i * N + j], xr[j]));
         sZ[id] = sEq[i] * t.hi;
       }
       __syncthreads();
       if (warp == 0) {
         for (int r = 0; r < nrhs; ++r) {
-          float* z = sZ + (size_t)r * nb;
+          float* z = sZ + (size_t)r * N;
           if (lane == 0)   // row interchanges in factorisation order (L is stored permuted)
-            for (int k = 0; k < nb; ++k) {
+            for (int k = 0; k < N; ++k) {
               const int pr = sPerm[k];
               if (pr != k) {
                 const float t = z[k];
@@ -903,24 +1073,24 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
               }
             }
           __syncwarp();
-          for (int k = 0; k < nb; ++k) {   // L (unit lower)
+          for (int k = 0; k < N; ++k) {   // L (unit lower)
             const float zk = z[k];
-            for (int i = k + 1 + lane; i < nb; i += 32) z[i] = fmaf(-sAL[i * nb + k], zk, z[i]);
+            for (int i = k + 1 + lane; i < N; i += 32) z[i] = fmaf(-sAL[i * N + k], zk, z[i]);
             __syncwarp();
           }
-          for (int k = nb - 1; k >= 0; --k) {   // U
-            if (lane == 0) z[k] = z[k] / sAL[k * nb + k];
+          for (int k = N - 1; k >= 0; --k) {   // U
+            if (lane == 0) z[k] = z[k] / sAL[k * N + k];
             __syncwarp();
             const float zk = z[k];
-            for (int i = lane; i < k; i += 32) z[i] = fmaf(-sAL[i * nb + k], zk, z[i]);
+            for (int i = lane; i < k; i += 32) z[i] = fmaf(-sAL[i * N + k], zk, z[i]);
             __syncwarp();
           }
         }
       }
       __syncthreads();
       float dmax = 0.f, xmax = 0.f;
-      for (int id = tid; id < nrhs * nb; id += blockDim.x) {
-        const float dx = sEq[id % nb] * sZ[id];
+      for (int id = tid; id < nrhs * N; id += blockDim.x) {
+        const float dx = sEq[id % N] * sZ[id];
         sX[id] = R::add(sX[id], T{dx, 0.f});
         dmax = fmaxf(dmax, fabsf(dx));
         xmax = fmaxf(xmax, fabsf(sX[id].hi));
@@ -940,10 +1110,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
           dm = fmaxf(dm, s_red[0][w]);
           xm = fmaxf(xm, s_red[1][w]);
         }
-        // stop once the correction is at the float-float resolution or stops shrinking
-        const bool done = (dm <= 4e-15f * xm) || (it >= 2 && dm > 0.5f * prev);
+        // stop once the correction is at the float-float resolution, or once it
+        // stops shrinking below 1e-10 of the solution (the float-float residual
+        // then limits the accuracy); a correction above 1e-8 of the solution
+        // after kMaxRefine steps is reported
+        const bool done = (dm <= 4e-15f * xm) || (it >= 2 && dm > 0.5f * prev && dm <= 1e-10f * xm);
         s_stop = done ? 1 : 0;
-        if (it == kMaxRefine - 1 && dm > 1e-9f * xm && rank == 0) flag_error(a, TP_ERR_NOCONV, tent);
+        if (!done && it == kMaxRefine - 1 && dm > 1e-8f * xm && rank == 0) flag_error(a, TP_ERR_NOCONV, tent);
         s_red[0][0] = dm;
       }
       __syncthreads();
@@ -952,36 +1125,36 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
       __syncthreads();
       if (stop) break;
     }
-    for (int id = tid; id < nrhs * nb; id += blockDim.x) sb[id] = sX[id];
+    for (int id = tid; id < nrhs * N; id += blockDim.x) sb[id] = sX[id];
     __syncthreads();
   }
 
-  // ---------------- phase 4: outflow at this CTA's top points ----------------
-  // coefficient vectors of U_h, v_h, sigma_h in terms of U-values: y = D^T x
-  {
-    const T cih = R::from(c * ih), mih = R::from(-ih);
-    for (int id = tid; id < nmom; id += blockDim.x) {
-      const int r = id / (C * nb), rem = id % (C * nb), cc = rem / nb, kk = rem % nb;
-      T t;
-      if (cc == 0) t = sb[r * nb + kk];
-      else t = R::mul(cc == 1 ? cih : mih, relT_apply<DIM, T>(a, kk, cc - 1, sb + (size_t)r * nb));
-      sY[id] = t;
-    }
+  // ---------------- phase 4: outflow at this CTA's top points (adjoint: bottom points) ----------------
+  // coefficient vectors of U_h, v_h, sigma_h in terms of U-values, per material: y = D^T x_g
+  for (int id = tid; id < ng * nmom; id += blockDim.x) {
+    const int g = id / nmom, rest = id % nmom;
+    const int r = rest / (C * nb), rem = rest % (C * nb), cc = rem / nb, kk = rem % nb;
+    const T* xg = sb + (size_t)r * N + g * nb;
+    T t;
+    if (cc == 0) t = xg[kk];
+    else t = R::mul(R::from(cc == 1 ? s_gc[g] * ih : -ih), relT_apply<DIM, T>(a, kk, cc - 1, xg));
+    sY[id] = t;
   }
   for (int base = q0; base < q1; base += 2 * CH) {
     const int nq = min(2 * CH, q1 - base);
     if (tid < nq) {
       const int qg = base + tid, k = qg / Q, q = qg % Q;
+      const double cg = s_gc[s_grp[k]];
       double x[DIM], tt = 0.0;
       for (int d = 0; d < DIM; ++d) x[d] = 0.0;
       for (int i = 0; i < NV; ++i) {
         const double l = __ldg(a.bary + q * NV + i);
         for (int d = 0; d < DIM; ++d) x[d] = fma(l, s_X[k][i][d], x[d]);
-        tt = fma(l, ADJ ? s_tb[k][i] : s_tt[k][i], tt);   // adjoint: bottom points
+        tt = fma(l, ADJ ? s_tb[k][i] : s_tt[k][i], tt);
       }
       T xh[DIM];
       for (int d = 0; d < DIM; ++d) xh[d] = R::from((x[d] - s_xv[d]) * ih);
-      const T th = R::from(c * (tt - tc) * ih);
+      const T th = R::from(cg * (tt - tc) * ih);
       eval_uvalues<DIM, T, false>(a, th, xh, sM + tid * a.mono_stride, R::one(), sU + (size_t)tid * nb);
     }
     __syncthreads();
@@ -990,7 +1163,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
         const int ql = id / (nrhs * C), rc = id % (nrhs * C), r = rc / C, cc = rc % C;
         const int qg = base + ql, k = qg / Q, q = qg % Q;
         const T* u = sU + (size_t)ql * nb;
-        const T* y = sY + ((size_t)r * C + cc) * nb;
+        const T* y = sY + (size_t)s_grp[k] * nmom + ((size_t)r * C + cc) * nb;
         T t = R::zero();
         for (int j = 0; j < nb; ++j) t = R::fma(y[j], u[j], t);
         a.front[(((int64_t)r * a.ne + s_el[k]) * Q + q) * C + cc] = R::to(t);
@@ -1003,18 +1176,19 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
         const T* u = sU + (size_t)ql * nb;
         double sv[C];
         for (int cc = 0; cc < C; ++cc) {
-          const T* y = sY + ((size_t)r * C + cc) * nb;
+          const T* y = sY + (size_t)s_grp[k] * nmom + ((size_t)r * C + cc) * nb;
           T t = R::zero();
           for (int j = 0; j < nb; ++j) t = R::fma(y[j], u[j], t);
           sv[cc] = R::to(t);
         }
+        const double cg = s_gc[s_grp[k]];
         const double sq = __ldg(a.sqw + q) * s_sdet[k];
         const double w = sq * sq;
         double gs = 0.0;
         for (int d = 0; d < DIM; ++d) gs = fma(s_gb[k][d], sv[2 + d], gs);
         double* f = a.front + (((int64_t)r * a.ne + s_el[k]) * Q + q) * C;
         f[0] = w * sv[0];
-        f[1] = w * (ic2 * sv[1] - gs);
+        f[1] = w * (sv[1] / (cg * cg) - gs);
         for (int d = 0; d < DIM; ++d) f[2 + d] = w * (sv[2 + d] - s_gb[k][d] * sv[1]);
       }
     }
@@ -1226,23 +1400,27 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
   ctx->ntents = (int64_t)tents->vert.size();
   ctx->n_levels = tents->n_levels;
   ctx->level_ptr = tents->level_ptr;
-  // patch checks: size limit and single material per tent
+  // patch checks: size limits; materials (distinct wave speeds) per tent
+  int ngmax = 1;
   for (int64_t v = 0; v < T.nv; ++v) {
     const int p0 = T.star_ptr[v], p1 = T.star_ptr[v + 1];
-    if (T.vfac_ptr[v + 1] - T.vfac_ptr[v] > tp::kMaxFacets) {
-      tp::set_error("tp_create: vertex " + std::to_string(v) + " lies on more than 16 boundary facets");
+    if ((T.vfac_ptr[v + 1] - T.vfac_ptr[v]) + (T.ifac_ptr[v + 1] - T.ifac_ptr[v]) > tp::kMaxFacets) {
+      tp::set_error("tp_create: vertex " + std::to_string(v) + " lies on more than 16 boundary or interface facets");
       return fail(TP_ERR_UNSUPPORTED);
     }
     if (p1 - p0 > tp::kMaxPatch) {
       tp::set_error("tp_create: vertex " + std::to_string(v) + " has more than 64 elements");
       return fail(TP_ERR_UNSUPPORTED);
     }
+    std::vector<double> speeds;
     for (int e = p0; e < p1; ++e)
-      if (T.c[T.star_el[e]] != T.c[T.star_el[p0]]) {
-        tp::set_error("tp_create: tent at vertex " + std::to_string(v) +
-                      " mixes wave speeds (interface tents are not in this build)");
-        return fail(TP_ERR_UNSUPPORTED);
-      }
+      if (std::find(speeds.begin(), speeds.end(), T.c[T.star_el[e]]) == speeds.end())
+        speeds.push_back(T.c[T.star_el[e]]);
+    ngmax = std::max(ngmax, (int)speeds.size());
+  }
+  if (ngmax > tp::kMaxGroups) {
+    tp::set_error("tp_create: a tent has more than 4 materials (wave speeds)");
+    return fail(TP_ERR_UNSUPPORTED);
   }
   // replay the tents on the host: anisotropic diameter (eq. 3.3) and the
   // Dirichlet quadrature points of every tent
@@ -1251,7 +1429,9 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
   const int Q = ctx->Q;
   for (int64_t it = 0; it < ctx->ntents; ++it) {
     const int v = tents->vert[it];
-    const double tb = tau[v], tt = tents->t_top[it], c = T.c[T.star_el[T.star_ptr[v]]];
+    double c = 0.0;   // the largest speed of the tent
+    for (int e = T.star_ptr[v]; e < T.star_ptr[v + 1]; ++e) c = std::max(c, T.c[T.star_el[e]]);
+    const double tb = tau[v], tt = tents->t_top[it];
     std::vector<std::vector<double>> pts;
     auto push = [&](int w, double t) {
       std::vector<double> pnt(n + 1);
@@ -1305,6 +1485,8 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
   KArgs& a = ctx->args;
   double *dX, *dc, *dnrm, *dbary, *dw, *dsqw, *dttop, *dh, *dspc;
   int *del, *dsp, *dse, *dvp, *dvf, *dfv, *dtv, *dspp, *dspm, *dpar, *dvar, *drp, *drs, *dtp, *dtd;
+  int *dfe, *dip, *div, *dikp, *dikm;
+  double* dinrm;
   double *drf, *dtf;
   float2* dcdd;
   float *drff, *dtff;
@@ -1327,6 +1509,9 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
       (rc = ctx_upload(ctx, &dse, T.star_el)) || (rc = ctx_upload(ctx, &dvp, T.vfac_ptr)) ||
       (rc = ctx_upload(ctx, &dvf, T.vfac)) || (rc = ctx_upload(ctx, &dfv, T.facet_vert)) ||
       (rc = ctx_upload(ctx, &dnrm, T.facet_nrm)) || (rc = ctx_upload(ctx, &dbary, ctx->rule.bary)) ||
+      (rc = ctx_upload(ctx, &dfe, T.facet_elem)) || (rc = ctx_upload(ctx, &dip, T.ifac_ptr)) ||
+      (rc = ctx_upload(ctx, &div, T.ifac_vert)) || (rc = ctx_upload(ctx, &dinrm, T.ifac_nrm)) ||
+      (rc = ctx_upload(ctx, &dikp, T.ifac_kp)) || (rc = ctx_upload(ctx, &dikm, T.ifac_km)) ||
       (rc = ctx_upload(ctx, &dw, ctx->rule.w)) || (rc = ctx_upload(ctx, &dsqw, sqw)) ||
       (rc = ctx_upload(ctx, &dtv, tv)) || (rc = ctx_upload(ctx, &dttop, ttop)) ||
       (rc = ctx_upload(ctx, &dtbot, tbot)) ||
@@ -1373,6 +1558,14 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
   a.ne = T.ne;
   a.n_bnd = ctx->n_bnd;
   a.alpha = ctx->alpha;
+  a.beta = prm->beta;
+  a.ngmax = ngmax;
+  a.facet_elem = dfe;
+  a.ifac_ptr = dip;
+  a.ifac_vert = div;
+  a.ifac_nrm = dinrm;
+  a.ifac_kp = dikp;
+  a.ifac_km = dikm;
   a.X = dX;
   a.elems = del;
   a.cK = dc;
@@ -1426,30 +1619,33 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
       off += count;
     };
     const size_t nmom = (size_t)ctx->nrhs * C * nb;
-    take(nullptr, (size_t)nb * nb);                  // A at offset 0
-    take(&a.off_b, (size_t)ctx->nrhs * nb);
-    take(&a.off_pg, npair);
-    take(&a.off_ph, (size_t)n * npair);
-    take(&a.off_pgb, npair);
-    take(&a.off_pm, nmom);
-    take(&a.off_pd, (size_t)nb * nb);
-    take(&a.off_pbd, (size_t)ctx->nrhs * nb);
-    take(&a.off_sg, (size_t)(n + 2) * npair);
-    take(&a.off_sm, nmom);
+    const size_t NB = (size_t)ngmax * nb;          // unknowns of the largest tent
+    take(nullptr, NB * NB);                        // A at offset 0
+    take(&a.off_b, (size_t)ctx->nrhs * NB);
+    take(&a.off_pg, (size_t)ngmax * npair);        // G, H_m, Gbot contiguous
+    take(&a.off_ph, (size_t)ngmax * n * npair);
+    take(&a.off_pgb, (size_t)ngmax * npair);
+    take(&a.off_pm, (size_t)ngmax * nmom);
+    take(&a.off_pd, NB * NB);
+    take(&a.off_pbd, (size_t)ctx->nrhs * NB);
+    take(&a.off_sg, (size_t)ngmax * (n + 2) * npair);
+    take(&a.off_sm, (size_t)ngmax * nmom);
     take(&a.off_f, npair);
+    take(&a.off_f2, npair);
+    take(&a.off_fpm, (size_t)nb * nb);
     take(&a.off_del, (size_t)ctx->nrhs * nb);
     take(&a.off_u, (size_t)2 * CH * nb);
     take(&a.off_mono, (size_t)2 * CH * a.mono_stride);
     take(&a.off_cb, (size_t)CH * ctx->nrhs * C);
     take(&a.off_gd, (size_t)CH * ctx->nrhs);
-    take(&a.off_y, nmom);
-    take(&a.off_rd, nb);
-    const size_t half_nb = ((size_t)nb + 1) / 2, half_rb = ((size_t)ctx->nrhs * nb + 1) / 2;
-    take(&a.off_al, ((size_t)nb * nb + 1) / 2);      // binary32 words, two per double slot
+    take(&a.off_y, (size_t)ngmax * nmom);
+    take(&a.off_rd, NB);
+    const size_t half_nb = (NB + 1) / 2, half_rb = ((size_t)ctx->nrhs * NB + 1) / 2;
+    take(&a.off_al, (NB * NB + 1) / 2);            // binary32 words, two per double slot
     take(&a.off_eq, half_nb);
     take(&a.off_perm, half_nb);
     take(&a.off_z, half_rb);
-    take(&a.off_x, (size_t)ctx->nrhs * nb);
+    take(&a.off_x, (size_t)ctx->nrhs * NB);
     return off * sizeof(double);
   };
   int CH = 0;

@@ -95,46 +95,93 @@ bool build_topology(const tp_mesh_desc* m, Topology* t) {
   std::sort(fs.begin(), fs.end(), [](const F& a, const F& b) { return a.v < b.v; });
   t->facet_vert.clear();
   t->facet_nrm.clear();
+  t->facet_elem.clear();
+  // unit normal of facet f pointing away from vertex opp
+  auto facet_normal = [&](const F& f, int32_t opp, double* nrm) {
+    nrm[0] = nrm[1] = nrm[2] = 0.0;
+    const double* P0 = &t->X[(int64_t)f.v[0] * n];
+    if (n == 1) {
+      nrm[0] = 1.0;
+    } else if (n == 2) {
+      const double* P1 = &t->X[(int64_t)f.v[1] * n];
+      nrm[0] = P1[1] - P0[1];
+      nrm[1] = -(P1[0] - P0[0]);
+    } else {
+      const double* P1 = &t->X[(int64_t)f.v[1] * n];
+      const double* P2 = &t->X[(int64_t)f.v[2] * n];
+      double a[3] = {P1[0] - P0[0], P1[1] - P0[1], P1[2] - P0[2]};
+      double b[3] = {P2[0] - P0[0], P2[1] - P0[1], P2[2] - P0[2]};
+      nrm[0] = a[1] * b[2] - a[2] * b[1];
+      nrm[1] = a[2] * b[0] - a[0] * b[2];
+      nrm[2] = a[0] * b[1] - a[1] * b[0];
+    }
+    double len = 0.0, dotp = 0.0;
+    for (int d = 0; d < n; ++d) len += nrm[d] * nrm[d];
+    len = std::sqrt(len);
+    for (int d = 0; d < n; ++d) {
+      nrm[d] /= len;
+      dotp += (t->X[(int64_t)opp * n + d] - P0[d]) * nrm[d];
+    }
+    if (dotp > 0)
+      for (int d = 0; d < n; ++d) nrm[d] = -nrm[d];
+  };
+  struct IF {
+    std::array<int32_t, 3> v;
+    int32_t kp, km;
+    double nrm[3];
+  };
+  std::vector<IF> ifs;
   for (size_t i = 0; i < fs.size();) {
     size_t j = i;
     while (j < fs.size() && fs[j].v == fs[i].v) ++j;
     if (j - i == 1) {
       const F& f = fs[i];
-      double nrm[3] = {0, 0, 0};
-      const double* P0 = &t->X[f.v[0] * n];
-      if (n == 1) {
-        nrm[0] = 1.0;
-      } else if (n == 2) {
-        const double* P1 = &t->X[f.v[1] * n];
-        nrm[0] = P1[1] - P0[1];
-        nrm[1] = -(P1[0] - P0[0]);
-      } else {
-        const double* P1 = &t->X[f.v[1] * n];
-        const double* P2 = &t->X[f.v[2] * n];
-        double a[3] = {P1[0] - P0[0], P1[1] - P0[1], P1[2] - P0[2]};
-        double b[3] = {P2[0] - P0[0], P2[1] - P0[1], P2[2] - P0[2]};
-        nrm[0] = a[1] * b[2] - a[2] * b[1];
-        nrm[1] = a[2] * b[0] - a[0] * b[2];
-        nrm[2] = a[0] * b[1] - a[1] * b[0];
-      }
-      double len = 0.0, dotp = 0.0;
-      for (int d = 0; d < n; ++d) len += nrm[d] * nrm[d];
-      len = std::sqrt(len);
-      for (int d = 0; d < n; ++d) {
-        nrm[d] /= len;
-        dotp += (t->X[f.opp * n + d] - P0[d]) * nrm[d];
-      }
-      if (dotp > 0)
-        for (int d = 0; d < n; ++d) nrm[d] = -nrm[d];
+      double nrm[3];
+      facet_normal(f, f.opp, nrm);
       for (int d = 0; d < n; ++d) {
         t->facet_vert.push_back(f.v[d]);
         t->facet_nrm.push_back(nrm[d]);
       }
-    } else if (j - i > 2) {
+      t->facet_elem.push_back(f.elem);
+    } else if (j - i == 2) {
+      const F& f1 = fs[i];
+      const F& f2 = fs[i + 1];
+      if (t->c[f1.elem] != t->c[f2.elem]) {   // time-like interface facet (Section 4.2)
+        const F& fp = (f1.elem < f2.elem) ? f1 : f2;
+        const F& fm = (f1.elem < f2.elem) ? f2 : f1;
+        IF rec;
+        rec.v = fp.v;
+        rec.kp = fp.elem;
+        rec.km = fm.elem;
+        facet_normal(fp, fp.opp, rec.nrm);
+        ifs.push_back(rec);
+      }
+    } else {
       set_error("tp: non-manifold mesh (a facet has more than two elements)");
       return false;
     }
     i = j;
+  }
+  {
+    std::vector<std::vector<int32_t>> vi(t->nv);
+    for (size_t f = 0; f < ifs.size(); ++f)
+      for (int d = 0; d < n; ++d) vi[ifs[f].v[d]].push_back((int32_t)f);
+    t->ifac_ptr.assign(t->nv + 1, 0);
+    t->ifac_vert.clear();
+    t->ifac_nrm.clear();
+    t->ifac_kp.clear();
+    t->ifac_km.clear();
+    for (int64_t v = 0; v < t->nv; ++v) {
+      for (int32_t f : vi[v]) {
+        for (int d = 0; d < n; ++d) {
+          t->ifac_vert.push_back(ifs[f].v[d]);
+          t->ifac_nrm.push_back(ifs[f].nrm[d]);
+        }
+        t->ifac_kp.push_back(ifs[f].kp);
+        t->ifac_km.push_back(ifs[f].km);
+      }
+      t->ifac_ptr[v + 1] = (int32_t)t->ifac_kp.size();
+    }
   }
   const int64_t nf = (int64_t)t->facet_vert.size() / n;
   std::vector<std::vector<int32_t>> vf(t->nv);

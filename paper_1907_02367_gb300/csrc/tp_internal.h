@@ -15,7 +15,8 @@ void set_error(const std::string& msg);
 constexpr int kMaxDim = 3;
 constexpr int kMaxP = 8;
 constexpr int kMaxPatch = 64;     // elements in one vertex star handled by one CTA
-constexpr int kMaxFacets = 16;    // boundary facets through one vertex
+constexpr int kMaxFacets = 16;    // Dirichlet + interface facets through one vertex
+constexpr int kMaxGroups = 4;     // materials (distinct wave speeds) in one tent
 
 // ---------------------------------------------------------------------------
 // mesh topology built on the host
@@ -31,6 +32,12 @@ struct Topology {
   std::vector<int32_t> facet_vert;            // boundary facets: dim sorted vertex ids each
   std::vector<double> facet_nrm;              // boundary facets: outward unit normal (dim)
   std::vector<int32_t> vfac_ptr, vfac;        // boundary facets through a vertex (facet order)
+  std::vector<int32_t> facet_elem;            // boundary facets: owning element
+  // time-like interface facets (different wave speed on the two sides), listed
+  // per vertex of the facet: dim vertex ids, the two elements (+ = lower index),
+  // the unit normal out of the + element
+  std::vector<int32_t> ifac_ptr, ifac_vert, ifac_kp, ifac_km;
+  std::vector<double> ifac_nrm;
 };
 
 bool build_topology(const tp_mesh_desc* m, Topology* t);

@@ -322,6 +322,9 @@ def workload(name: str) -> Workload:
                    p=4, T=1, standing wave (v = 0 on the boundary).
     small2d      : unit square, 6x6 jittered grid (72 triangles), p=4, T=0.25.
     standing3d_small : unit cube 3^3 hexes (162 tets), p=3, T=0.2.
+    inclusion_small : unit square 8x8 jittered grid (128 triangles), c = 3 in the
+                   disc |x - (0.5,0.5)| < 0.2 (by element centroid), c = 1 outside,
+                   p=3, T=0.15, Gaussian pulse (Section 6.7 shape, small).
     """
     if name == "plane1d":
         m = mesh_interval(16)
@@ -339,6 +342,12 @@ def workload(name: str) -> Workload:
         m = mesh_cube(3, 0.1, seed=4)
         return Workload(name, m, 3, 0.2, pitch_kappa(m), standing_wave_3d,
                         lambda x: standing_wave_3d(x, 0.0), None)
+    if name == "inclusion_small":
+        m = mesh_square(8, 0.2, seed=13)
+        cen = m.coords[m.elems].mean(axis=1)
+        m.c[:] = np.where(np.linalg.norm(cen - 0.5, axis=1) < 0.2, 3.0, 1.0)
+        pulse = gaussian_pulse((0.42, 0.55), 0.15)
+        return Workload(name, m, 3, 0.15, pitch_kappa(m), None, pulse, None)
     raise KeyError(name)
 
 
