@@ -202,6 +202,9 @@ struct Ar;
 
 template <>
 struct Ar<double> {
+  static __device__ __forceinline__ float hi(double x) { return (float)x; }
+  static __device__ __forceinline__ double addf(double a, float f) { return a + (double)f; }
+  static __device__ __forceinline__ double fms(double t, double a, double b) { return ::fma(-a, b, t); }
   static __device__ __forceinline__ double zero() { return 0.0; }
   static __device__ __forceinline__ double one() { return 1.0; }
   static __device__ __forceinline__ double from(double x) { return x; }
@@ -216,6 +219,12 @@ struct Ar<double> {
 
 template <>
 struct Ar<dd> {
+  static __device__ __forceinline__ float hi(dd x) { return x.hi; }
+  static __device__ __forceinline__ dd addf(dd a, float f) { return dd_add(a, {f, 0.f}); }
+  static __device__ __forceinline__ dd fms(dd t, dd a, dd b) {
+    const dd p = dd_mul(a, b);
+    return dd_add(t, {-p.hi, -p.lo});
+  }
   static __device__ __forceinline__ dd zero() { return {0.f, 0.f}; }
   static __device__ __forceinline__ dd one() { return {1.f, 0.f}; }
   static __device__ __forceinline__ dd from(double x) {
@@ -431,7 +440,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
   __shared__ int s_pgrp[2 * 64];
   __shared__ int s_piv;
   __shared__ float s_red[2][kThreads / 32];
-  __shared__ int s_stop;
+  __shared__ int s_stop, s_conv;
 
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
@@ -911,102 +920,30 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
   }
 
   // ---------------- phase 3: solve ----------------
+  // MIXED: binary32 LU of the equilibrated matrix D A D (D = |diag A|^-1/2),
+  // then refinement x += D (D A D)^-1 D (b - A x) with a float-float residual.
+  // binary64: direct LU (a binary32 factor + binary64 refinement was measured
+  // slower on this part, whose binary64 pipe is the bottleneck either way).
   const bool pivoting = extra || ng > 1;
-  if constexpr (!MIXED) {
-    // LU (no pivoting for single-material interior tents: A is SPD), forward elimination of b alongside
-    for (int k = 0; k < N; ++k) {
-      if (pivoting) {
-        if (warp == 0) {
-          // |a_ik| compared through the bit patterns (non-negative doubles order as integers)
-          unsigned long long best = 0ull;
-          int bi = k;
-          for (int i = k + lane; i < N; i += 32) {
-            const unsigned long long bits = (unsigned long long)__double_as_longlong(fabs(sA[i * N + k]));
-            if (bits > best || (bits == best && i < bi)) {
-              best = bits;
-              bi = i;
-            }
-          }
-          for (int o = 16; o > 0; o >>= 1) {
-            const unsigned long long ob = __shfl_down_sync(0xffffffffu, best, o);
-            const int oi = __shfl_down_sync(0xffffffffu, bi, o);
-            if (ob > best || (ob == best && oi < bi)) {
-              best = ob;
-              bi = oi;
-            }
-          }
-          if (lane == 0) s_piv = bi;
-        }
-        __syncthreads();
-        const int pr = s_piv;
-        if (pr != k) {
-          for (int j = tid; j < N; j += blockDim.x) {
-            const double t = sA[k * N + j];
-            sA[k * N + j] = sA[pr * N + j];
-            sA[pr * N + j] = t;
-          }
-          for (int r = tid; r < nrhs; r += blockDim.x) {
-            const double t = sb[r * N + k];
-            sb[r * N + k] = sb[r * N + pr];
-            sb[r * N + pr] = t;
-          }
-        }
-        __syncthreads();
-      }
-      if (tid == 0) {
-        double piv = sA[k * N + k];
-        if (!(fabs(piv) > 0.0) || !isfinite(piv)) {
-          if (rank == 0) flag_error(a, TP_ERR_SINGULAR, tent);
-          piv = 1.0;
-        }
-        sRD[k] = recip(piv);
-      }
-      __syncthreads();
-      const double rp = sRD[k];
-      const int rem = N - k - 1;
-      for (int i = k + 1 + tid; i < N; i += blockDim.x) sA[i * N + k] *= rp;   // multipliers
-      __syncthreads();
-      for (int id = tid; id < rem * (rem + nrhs); id += blockDim.x) {
-        const int i = k + 1 + id / (rem + nrhs), jj = id % (rem + nrhs);
-        const double l = sA[i * N + k];
-        if (jj < rem) {
-          const int j = k + 1 + jj;
-          sA[i * N + j] = fma(-l, sA[k * N + j], sA[i * N + j]);
-        } else {
-          const int r = jj - rem;
-          sb[r * N + i] = fma(-l, sb[r * N + k], sb[r * N + i]);
-        }
-      }
-      __syncthreads();
-    }
-    for (int k = N - 1; k >= 0; --k) {
-      for (int r = tid; r < nrhs; r += blockDim.x) sb[r * N + k] *= sRD[k];
-      __syncthreads();
-      for (int id = tid; id < k * nrhs; id += blockDim.x) {
-        const int r = id / k, i = id % k;
-        sb[r * N + i] = fma(-sA[i * N + k], sb[r * N + k], sb[r * N + i]);
-      }
-      __syncthreads();
-    }
-  } else {
+  if constexpr (MIXED) {
     float* sAL = reinterpret_cast<float*>(sm + a.off_al);   // N*N     equilibrated binary32 LU
     float* sEq = reinterpret_cast<float*>(sm + a.off_eq);   // N       equilibration scales
     int* sPerm = reinterpret_cast<int*>(sm + a.off_perm);   // N       row interchanges
     float* sZ = reinterpret_cast<float*>(sm + a.off_z);     // nrhs*N  correction (binary32)
     T* sX = reinterpret_cast<T*>(sm + a.off_x);             // nrhs*N  iterate
     for (int i = tid; i < N; i += blockDim.x) {
-      const float d = fabsf(sA[i * N + i].hi);
+      const float d = fabsf(R::hi(sA[i * N + i]));
       sEq[i] = (d > 0.f && isfinite(d)) ? rsqrtf(d) : 1.f;
     }
     for (int id = tid; id < nrhs * N; id += blockDim.x) sX[id] = R::zero();
     __syncthreads();
-    for (int id = tid; id < N * N; id += blockDim.x) sAL[id] = sA[id].hi * sEq[id / N] * sEq[id % N];
+    for (int id = tid; id < N * N; id += blockDim.x) sAL[id] = R::hi(sA[id]) * sEq[id / N] * sEq[id % N];
     __syncthreads();
-    // binary32 LU of D A D by warp 0 (lane owns rows lane, lane+32, ...)
-    if (warp == 0) {
-      for (int k = 0; k < N; ++k) {
-        int pr = k;
-        if (pivoting) {
+    // binary32 LU of D A D (row interchanges on whole rows, multipliers kept
+    // below the diagonal, reciprocal pivots in sRD)
+    for (int k = 0; k < N; ++k) {
+      if (pivoting) {
+        if (warp == 0) {
           float best = -1.f;
           int bi = k;
           for (int i = k + lane; i < N; i += 32) {
@@ -1024,40 +961,62 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
               bi = oi;
             }
           }
-          pr = __shfl_sync(0xffffffffu, bi, 0);
-          if (pr != k)
-            for (int j = lane; j < N; j += 32) {
-              const float t = sAL[k * N + j];
-              sAL[k * N + j] = sAL[pr * N + j];
-              sAL[pr * N + j] = t;
-            }
-          __syncwarp();
+          if (lane == 0) s_piv = bi;
         }
-        if (lane == 0) sPerm[k] = pr;
-        float piv = sAL[k * N + k];
-        if (!(fabsf(piv) > 0.f) || !isfinite(piv)) {
-          if (lane == 0 && rank == 0) flag_error(a, TP_ERR_SINGULAR, tent);
-          piv = 1.f;
-        }
-        const float rp = 1.f / piv;
-        for (int i = k + 1 + lane; i < N; i += 32) {
-          const float l = sAL[i * N + k] * rp;
-          sAL[i * N + k] = l;
-          for (int j = k + 1; j < N; ++j) sAL[i * N + j] = fmaf(-l, sAL[k * N + j], sAL[i * N + j]);
-        }
-        __syncwarp();
+        __syncthreads();
+        const int pr = s_piv;
+        if (pr != k)
+          for (int j = tid; j < N; j += blockDim.x) {
+            const float t = sAL[k * N + j];
+            sAL[k * N + j] = sAL[pr * N + j];
+            sAL[pr * N + j] = t;
+          }
+        if (tid == 0) sPerm[k] = pr;
+        __syncthreads();
+      } else if (tid == 0) {
+        sPerm[k] = k;
       }
+      float piv = sAL[k * N + k];
+      if (!(fabsf(piv) > 0.f) || !isfinite(piv)) {
+        if (tid == 0 && rank == 0) flag_error(a, TP_ERR_SINGULAR, tent);
+        piv = 1.f;
+      }
+      const float rp = 1.f / piv;
+      const int rem = N - k - 1;
+      for (int id = tid; id < rem * rem; id += blockDim.x) {
+        const int i = k + 1 + id / rem, j = k + 1 + id % rem;
+        sAL[i * N + j] = fmaf(-sAL[i * N + k] * rp, sAL[k * N + j], sAL[i * N + j]);
+      }
+      __syncthreads();
+      for (int i = k + 1 + tid; i < N; i += blockDim.x) sAL[i * N + k] *= rp;
+      if (tid == 0) sRD[k] = (double)rp;
+      __syncthreads();
     }
-    __syncthreads();
     // refinement: r = b - A x (float-float), z = (D A D)^-1 D r, x += D z
     float prev = 3.4e38f;
-    for (int it = 0; it < kMaxRefine; ++it) {
-      for (int id = tid; id < nrhs * N; id += blockDim.x) {
-        const int r = id / N, i = id % N;
-        T t = sb[id];
-        const T* xr = sX + (size_t)r * N;
-        for (int j = 0; j < N; ++j) t = R::sub(t, R::mul(sA[i * N + j], xr[j]));
-        sZ[id] = sEq[i] * t.hi;
+    const int maxit = kMaxRefine;
+    if (tid == 0) s_conv = 0;
+    for (int it = 0; it < maxit; ++it) {
+      // r = b - A x, each row split over 8 lanes of one warp
+      for (int base8 = 0; base8 < nrhs * N * 8; base8 += blockDim.x) {
+        const int id = base8 + tid, item = id >> 3, sub = id & 7;
+        T t = R::zero();
+        if (item < nrhs * N) {
+          const int r = item / N, i = item % N;
+          const T* xr = sX + (size_t)r * N;
+          for (int j = sub; j < N; j += 8) t = R::fms(t, sA[i * N + j], xr[j]);
+        }
+        for (int o = 4; o > 0; o >>= 1) {
+          T u;
+          if constexpr (MIXED) {
+            u.hi = __shfl_xor_sync(0xffffffffu, t.hi, o);
+            u.lo = __shfl_xor_sync(0xffffffffu, t.lo, o);
+          } else {
+            u = __shfl_xor_sync(0xffffffffu, t, o);
+          }
+          t = R::add(t, u);
+        }
+        if (sub == 0 && item < nrhs * N) sZ[item] = sEq[item % N] * R::hi(R::add(sb[item], t));
       }
       __syncthreads();
       if (warp == 0) {
@@ -1079,7 +1038,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
             __syncwarp();
           }
           for (int k = N - 1; k >= 0; --k) {   // U
-            if (lane == 0) z[k] = z[k] / sAL[k * N + k];
+            if (lane == 0) z[k] = z[k] * (float)sRD[k];
             __syncwarp();
             const float zk = z[k];
             for (int i = lane; i < k; i += 32) z[i] = fmaf(-sAL[i * N + k], zk, z[i]);
@@ -1091,9 +1050,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
       float dmax = 0.f, xmax = 0.f;
       for (int id = tid; id < nrhs * N; id += blockDim.x) {
         const float dx = sEq[id % N] * sZ[id];
-        sX[id] = R::add(sX[id], T{dx, 0.f});
+        sX[id] = R::addf(sX[id], dx);
         dmax = fmaxf(dmax, fabsf(dx));
-        xmax = fmaxf(xmax, fabsf(sX[id].hi));
+        xmax = fmaxf(xmax, fabsf(R::hi(sX[id])));
       }
       for (int o = 16; o > 0; o >>= 1) {
         dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
@@ -1114,9 +1073,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
         // stops shrinking below 1e-10 of the solution (the float-float residual
         // then limits the accuracy); a correction above 1e-8 of the solution
         // after kMaxRefine steps is reported
-        const bool done = (dm <= 4e-15f * xm) || (it >= 2 && dm > 0.5f * prev && dm <= 1e-10f * xm);
+        const float tiny = 4e-15f, floor_ = 1e-10f;
+        const bool done = (dm <= tiny * xm) || (it >= 2 && dm > 0.5f * prev && dm <= floor_ * xm);
         s_stop = done ? 1 : 0;
-        if (!done && it == kMaxRefine - 1 && dm > 1e-8f * xm && rank == 0) flag_error(a, TP_ERR_NOCONV, tent);
+        if (done) s_conv = 1;
+        if (!done && it == maxit - 1 && dm > 1e-8f * xm && rank == 0) flag_error(a, TP_ERR_NOCONV, tent);
         s_red[0][0] = dm;
       }
       __syncthreads();
@@ -1127,6 +1088,87 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
     }
     for (int id = tid; id < nrhs * N; id += blockDim.x) sb[id] = sX[id];
     __syncthreads();
+  }
+  if constexpr (!MIXED) {
+    {
+      __syncthreads();
+    // LU (no pivoting for single-material interior tents: A is SPD), forward elimination of b alongside
+      for (int k = 0; k < N; ++k) {
+        if (pivoting) {
+          if (warp == 0) {
+            // |a_ik| compared through the bit patterns (non-negative doubles order as integers)
+            unsigned long long best = 0ull;
+            int bi = k;
+            for (int i = k + lane; i < N; i += 32) {
+              const unsigned long long bits = (unsigned long long)__double_as_longlong(fabs(sA[i * N + k]));
+              if (bits > best || (bits == best && i < bi)) {
+                best = bits;
+                bi = i;
+              }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+              const unsigned long long ob = __shfl_down_sync(0xffffffffu, best, o);
+              const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+              if (ob > best || (ob == best && oi < bi)) {
+                best = ob;
+                bi = oi;
+              }
+            }
+            if (lane == 0) s_piv = bi;
+          }
+          __syncthreads();
+          const int pr = s_piv;
+          if (pr != k) {
+            for (int j = tid; j < N; j += blockDim.x) {
+              const double t = sA[k * N + j];
+              sA[k * N + j] = sA[pr * N + j];
+              sA[pr * N + j] = t;
+            }
+            for (int r = tid; r < nrhs; r += blockDim.x) {
+              const double t = sb[r * N + k];
+              sb[r * N + k] = sb[r * N + pr];
+              sb[r * N + pr] = t;
+            }
+          }
+          __syncthreads();
+        }
+        if (tid == 0) {
+          double piv = sA[k * N + k];
+          if (!(fabs(piv) > 0.0) || !isfinite(piv)) {
+            if (rank == 0) flag_error(a, TP_ERR_SINGULAR, tent);
+            piv = 1.0;
+          }
+          sRD[k] = recip(piv);
+        }
+        __syncthreads();
+        const double rp = sRD[k];
+        const int rem = N - k - 1;
+        for (int i = k + 1 + tid; i < N; i += blockDim.x) sA[i * N + k] *= rp;   // multipliers
+        __syncthreads();
+        for (int id = tid; id < rem * (rem + nrhs); id += blockDim.x) {
+          const int i = k + 1 + id / (rem + nrhs), jj = id % (rem + nrhs);
+          const double l = sA[i * N + k];
+          if (jj < rem) {
+            const int j = k + 1 + jj;
+            sA[i * N + j] = fma(-l, sA[k * N + j], sA[i * N + j]);
+          } else {
+            const int r = jj - rem;
+            sb[r * N + i] = fma(-l, sb[r * N + k], sb[r * N + i]);
+          }
+        }
+        __syncthreads();
+      }
+      for (int k = N - 1; k >= 0; --k) {
+        for (int r = tid; r < nrhs; r += blockDim.x) sb[r * N + k] *= sRD[k];
+        __syncthreads();
+        for (int id = tid; id < k * nrhs; id += blockDim.x) {
+          const int r = id / k, i = id % k;
+          sb[r * N + i] = fma(-sA[i * N + k], sb[r * N + k], sb[r * N + i]);
+        }
+        __syncthreads();
+      }
+  
+    }
   }
 
   // ---------------- phase 4: outflow at this CTA's top points (adjoint: bottom points) ----------------
