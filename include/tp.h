@@ -43,6 +43,7 @@ enum {
 };
 
 enum { TP_FP64 = 0, TP_MIXED = 1 };
+enum { TP_SCHED_DATAFLOW = 0, TP_SCHED_LEVELS = 1 };
 
 /* Spatial mesh (Section 2.1): simplices aligned with the jumps of the
  * piecewise-constant wave speed c.  dim in {1,2,3}; coords n_vert x dim;
@@ -62,7 +63,12 @@ typedef struct tp_mesh_desc {
  * penalty of eq. (2.5) (the paper uses 0.5); beta: time-like penalty (unused
  * until interface faces are built); kappa: pitching slope factor (edge-slope
  * limit delta_e = kappa l_e / c_e); T: final time; precision: TP_FP64;
- * nrhs: right-hand sides advanced together (same tents, same matrices). */
+ * nrhs: right-hand sides advanced together (same tents, same matrices);
+ * schedule: how tp_advance runs the levels -- TP_SCHED_DATAFLOW (default):
+ * one resident kernel whose clusters take the tents in level order and each
+ * start as soon as the earlier tents of its vertex and neighbours are done
+ * (bounded waits; TP_ERR_TIMEOUT if one gives up), or TP_SCHED_LEVELS: one
+ * launch per level. */
 typedef struct tp_params {
   int32_t p;
   double alpha;
@@ -71,6 +77,7 @@ typedef struct tp_params {
   double T;
   int32_t precision;
   int32_t nrhs;
+  int32_t schedule;
 } tp_params;
 
 typedef struct tp_tents tp_tents;

@@ -97,7 +97,8 @@ class Solver:
     stream is passed to every call."""
 
     def __init__(self, coords, elems, c, p: int, T: float, kappa: float, alpha: float = 0.5,
-                 nrhs: int = 1, tents: Tents | None = None, precision: str = "fp64"):
+                 nrhs: int = 1, tents: Tents | None = None, precision: str = "fp64",
+                 schedule: str = "dataflow"):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("libtp Solver needs a CUDA device")
@@ -108,8 +109,12 @@ class Solver:
         if precision not in ("fp64", "mixed"):
             raise ValueError("precision must be 'fp64' or 'mixed'")
         self.precision = precision
+        if schedule not in ("dataflow", "levels"):
+            raise ValueError("schedule must be 'dataflow' or 'levels'")
         self.params = B.make_params(p, T, kappa, alpha=alpha, nrhs=nrhs,
-                                    precision=B.TP_FP64 if precision == "fp64" else B.TP_MIXED)
+                                    precision=B.TP_FP64 if precision == "fp64" else B.TP_MIXED,
+                                    schedule=B.TP_SCHED_DATAFLOW if schedule == "dataflow"
+                                    else B.TP_SCHED_LEVELS)
         h = ct.c_void_p()
         B.check(lib.tp_create(ct.byref(self._mesh.desc), self.tents.handle, self.basis.handle,
                               ct.byref(self.params), ct.byref(h)))

@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libtp.so")
 TP_OK, TP_ERR_ARG, TP_ERR_CAUSALITY, TP_ERR_SINGULAR, TP_ERR_NOCONV = 0, 1, 2, 3, 4
 TP_ERR_TIMEOUT, TP_ERR_CUDA, TP_ERR_OOM, TP_ERR_UNSUPPORTED = 5, 6, 7, 8
 TP_FP64, TP_MIXED = 0, 1
+TP_SCHED_DATAFLOW, TP_SCHED_LEVELS = 0, 1
 
 EXPORTED = [
     "tp_last_error", "tp_pitch_mesh", "tp_tents_info", "tp_tents_export", "tp_destroy_tents",
@@ -41,7 +42,7 @@ class MeshDesc(ct.Structure):
 class Params(ct.Structure):
     _fields_ = [("p", ct.c_int32), ("alpha", ct.c_double), ("beta", ct.c_double),
                 ("kappa", ct.c_double), ("T", ct.c_double), ("precision", ct.c_int32),
-                ("nrhs", ct.c_int32)]
+                ("nrhs", ct.c_int32), ("schedule", ct.c_int32)]
 
 
 _lib = None
@@ -112,8 +113,10 @@ class _MeshArrays:
                              self.elems.shape[0], _ptr(self.elems), _ptr(self.c))
 
 
-def make_params(p, T, kappa, alpha=0.5, beta=0.5, precision=TP_FP64, nrhs=1) -> Params:
-    return Params(int(p), float(alpha), float(beta), float(kappa), float(T), int(precision), int(nrhs))
+def make_params(p, T, kappa, alpha=0.5, beta=0.5, precision=TP_FP64, nrhs=1,
+                schedule=TP_SCHED_DATAFLOW) -> Params:
+    return Params(int(p), float(alpha), float(beta), float(kappa), float(T), int(precision), int(nrhs),
+                  int(schedule))
 
 
 def stream_ptr(stream=None) -> int:

@@ -43,1201 +43,10 @@
     }                                                                                 \
   } while (0)
 
-namespace cg = cooperative_groups;
+#include "tp_kernel.cuh"
 
 namespace {
-
-constexpr int kThreads = 256;
-constexpr int kMaxPair = 4;      // Gram pairs per thread (nb (nb+1)/2 <= 4 * 256)
-constexpr int kMaxRefine = 40;   // refinement steps of the mixed path
-
-struct KArgs {
-  int nb, nmono, Q, nrhs, CH, mono_stride, ngmax;
-  int64_t ne, n_bnd;
-  double alpha, beta;
-  const double* X;
-  const int* elems;
-  const double* cK;
-  const int* star_ptr;
-  const int* star_el;
-  const int* vfac_ptr;
-  const int* vfac;
-  const int* facet_vert;
-  const double* facet_nrm;
-  const int* facet_elem;      // element owning each boundary facet
-  const int* ifac_ptr;        // per vertex: time-like interface facets through it (CSR)
-  const int* ifac_vert;       // dim vertex ids per interface facet
-  const double* ifac_nrm;     // unit normal out of the + element
-  const int* ifac_kp;         // + element (lower index of the two)
-  const int* ifac_km;         // - element
-  const double* bary;     // Q * (dim+1)
-  const double* wref;     // Q
-  const double* sqw;      // Q, sqrt(wref)
-  const int* tent_v;
-  const double* tent_ttop;
-  const double* tent_tbot;
-  const double* tent_h;
-  const long long* tent_gdoff;
-  const int* sp_ptr;
-  const int* sp_mono;
-  const double* sp_coef;
-  const float2* sp_coef_dd;   // (hi, lo) binary32 pair of every sp_coef entry
-  const int* mono_parent;
-  const int* mono_var;
-  double* tau;
-  double* front;
-  const double* gD;
-  int* status;
-  long long* status_info;
-  // shared-memory carve (offsets in doubles)
-  const int* rel_ptr;
-  const int* rel_src;
-  const double* rel_fac;
-  const int* relT_ptr;
-  const int* relT_dst;
-  const double* relT_fac;
-  const float* rel_facf;      // relation factors (small integers) in binary32
-  const float* relT_facf;
-  int off_al, off_eq, off_perm, off_z, off_x;   // mixed path: binary32 LU and refinement
-  int off_b, off_pg, off_ph, off_pgb, off_pm, off_pd, off_pbd, off_sg, off_sm, off_f, off_f2, off_fpm, off_del,
-      off_u, off_mono, off_cb, off_gd, off_y, off_rd;
-};
-
-__device__ __forceinline__ void flag_error(const KArgs& a, int code, long long info) {
-  if (atomicCAS(a.status, 0, code) == 0) *a.status_info = info;
-}
-
-// gradient g of the linear function with increments dv[i] along the edges
-// e[i] = X_{i+1} - X_0 (solves e g = dv); returns det(e)
-template <int DIM>
-__device__ __forceinline__ double lin_grad(const double (&e)[DIM][DIM], const double* dv, double* g) {
-  if constexpr (DIM == 1) {
-    g[0] = dv[0] / e[0][0];
-    return e[0][0];
-  } else if constexpr (DIM == 2) {
-    const double det = e[0][0] * e[1][1] - e[0][1] * e[1][0];
-    const double id = 1.0 / det;
-    g[0] = (e[1][1] * dv[0] - e[0][1] * dv[1]) * id;
-    g[1] = (-e[1][0] * dv[0] + e[0][0] * dv[1]) * id;
-    return det;
-  } else {
-    // rows of e^-1^T: (e1 x e2, e2 x e0, e0 x e1) / det
-    double c0[3], c1[3], c2[3];
-    c0[0] = e[1][1] * e[2][2] - e[1][2] * e[2][1];
-    c0[1] = e[1][2] * e[2][0] - e[1][0] * e[2][2];
-    c0[2] = e[1][0] * e[2][1] - e[1][1] * e[2][0];
-    c1[0] = e[2][1] * e[0][2] - e[2][2] * e[0][1];
-    c1[1] = e[2][2] * e[0][0] - e[2][0] * e[0][2];
-    c1[2] = e[2][0] * e[0][1] - e[2][1] * e[0][0];
-    c2[0] = e[0][1] * e[1][2] - e[0][2] * e[1][1];
-    c2[1] = e[0][2] * e[1][0] - e[0][0] * e[1][2];
-    c2[2] = e[0][0] * e[1][1] - e[0][1] * e[1][0];
-    const double det = e[0][0] * c0[0] + e[0][1] * c0[1] + e[0][2] * c0[2];
-    const double id = 1.0 / det;
-    for (int d = 0; d < 3; ++d) g[d] = (dv[0] * c0[d] + dv[1] * c1[d] + dv[2] * c2[d]) * id;
-    return det;
-  }
-}
-
-// determinant of a small symmetric Gram matrix
-template <int DIM>
-__device__ __forceinline__ double small_det(const double (&G)[DIM][DIM]) {
-  if constexpr (DIM == 1) {
-    return G[0][0];
-  } else if constexpr (DIM == 2) {
-    return G[0][0] * G[1][1] - G[0][1] * G[1][0];
-  } else {
-    return G[0][0] * (G[1][1] * G[2][2] - G[1][2] * G[2][1]) -
-           G[0][1] * (G[1][0] * G[2][2] - G[1][2] * G[2][0]) +
-           G[0][2] * (G[1][0] * G[2][1] - G[1][1] * G[2][0]);
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Arithmetic used by the tent kernel.  The FP64 path computes in binary64.
-// The mixed path computes the assembly, the refinement residual and the
-// outflow in float-float ("double-float") arithmetic on the binary32 pipes,
-// which GB300 runs ~58x faster than binary64: a value is an unevaluated sum
-// hi + lo of two binary32 numbers (|lo| <= ulp(hi)/2, ~48 significant bits),
-// built from the error-free transformations TwoSum (Knuth), FastTwoSum
-// (Dekker) and TwoProd through the fused multiply-add.  The intrinsics
-// __fadd_rn/__fsub_rn/__fmul_rn keep the compiler from contracting them.
-// ---------------------------------------------------------------------------
-struct dd {
-  float hi, lo;
-};
-
-__device__ __forceinline__ dd two_sum(float a, float b) {
-  const float s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-  return {s, e};
-}
-__device__ __forceinline__ dd fast_two_sum(float a, float b) {   // |a| >= |b|
-  const float s = __fadd_rn(a, b);
-  return {s, __fsub_rn(b, __fsub_rn(s, a))};
-}
-__device__ __forceinline__ dd dd_add(dd a, dd b) {
-  dd s = two_sum(a.hi, b.hi);
-  const dd t = two_sum(a.lo, b.lo);
-  s = fast_two_sum(s.hi, __fadd_rn(s.lo, t.hi));
-  return fast_two_sum(s.hi, __fadd_rn(s.lo, t.lo));
-}
-__device__ __forceinline__ dd dd_mul(dd a, dd b) {
-  const float p = __fmul_rn(a.hi, b.hi);
-  float e = fmaf(a.hi, b.hi, -p);
-  e = fmaf(a.hi, b.lo, e);
-  e = fmaf(a.lo, b.hi, e);
-  return fast_two_sum(p, e);
-}
-__device__ __forceinline__ dd dd_mulf(dd a, float f) {   // f exact in binary32
-  const float p = __fmul_rn(a.hi, f);
-  float e = fmaf(a.hi, f, -p);
-  e = fmaf(a.lo, f, e);
-  return fast_two_sum(p, e);
-}
-
-template <typename T>
-struct Ar;
-
-template <>
-struct Ar<double> {
-  static __device__ __forceinline__ float hi(double x) { return (float)x; }
-  static __device__ __forceinline__ double addf(double a, float f) { return a + (double)f; }
-  static __device__ __forceinline__ double fms(double t, double a, double b) { return ::fma(-a, b, t); }
-  static __device__ __forceinline__ double zero() { return 0.0; }
-  static __device__ __forceinline__ double one() { return 1.0; }
-  static __device__ __forceinline__ double from(double x) { return x; }
-  static __device__ __forceinline__ double to(double x) { return x; }
-  static __device__ __forceinline__ double add(double a, double b) { return a + b; }
-  static __device__ __forceinline__ double sub(double a, double b) { return a - b; }
-  static __device__ __forceinline__ double mul(double a, double b) { return a * b; }
-  static __device__ __forceinline__ double mulf(double a, float f) { return a * (double)f; }
-  static __device__ __forceinline__ double fma(double a, double b, double c) { return ::fma(a, b, c); }
-  static __device__ __forceinline__ double coef(const KArgs& a, int e);
-};
-
-template <>
-struct Ar<dd> {
-  static __device__ __forceinline__ float hi(dd x) { return x.hi; }
-  static __device__ __forceinline__ dd addf(dd a, float f) { return dd_add(a, {f, 0.f}); }
-  static __device__ __forceinline__ dd fms(dd t, dd a, dd b) {
-    const dd p = dd_mul(a, b);
-    return dd_add(t, {-p.hi, -p.lo});
-  }
-  static __device__ __forceinline__ dd zero() { return {0.f, 0.f}; }
-  static __device__ __forceinline__ dd one() { return {1.f, 0.f}; }
-  static __device__ __forceinline__ dd from(double x) {
-    const float h = __double2float_rn(x);
-    return {h, __double2float_rn(x - (double)h)};
-  }
-  static __device__ __forceinline__ double to(dd x) { return (double)x.hi + (double)x.lo; }
-  static __device__ __forceinline__ dd add(dd a, dd b) { return dd_add(a, b); }
-  static __device__ __forceinline__ dd sub(dd a, dd b) { return dd_add(a, {-b.hi, -b.lo}); }
-  static __device__ __forceinline__ dd mul(dd a, dd b) { return dd_mul(a, b); }
-  static __device__ __forceinline__ dd mulf(dd a, float f) { return dd_mulf(a, f); }
-  static __device__ __forceinline__ dd fma(dd a, dd b, dd c) { return dd_add(dd_mul(a, b), c); }
-  static __device__ __forceinline__ dd coef(const KArgs& a, int e);
-};
-
-__device__ __forceinline__ double Ar<double>::coef(const KArgs& a, int e) { return __ldg(a.sp_coef + e); }
-__device__ __forceinline__ dd Ar<dd>::coef(const KArgs& a, int e) {
-  const float2 c = __ldg(a.sp_coef_dd + e);
-  return {c.x, c.y};
-}
-
-// monomials t^k x^alpha at (that, xhat) into m[0..nm): m[g] = m[parent[g]] * var
-template <int DIM, typename T>
-__device__ __forceinline__ void eval_monomials(const KArgs& a, T th, const T* xh, T* m) {
-  m[0] = Ar<T>::one();
-  for (int g = 1; g < a.nmono; ++g) {
-    const int vr = __ldg(a.mono_var + g);
-    const T s = (vr == 0) ? th : xh[vr - 1];
-    m[g] = Ar<T>::mul(m[__ldg(a.mono_parent + g)], s);
-  }
-}
-
-// U-value of basis function j: sum over its sparse monomial entries
-template <int DIM, typename T>
-__device__ __forceinline__ T sp_eval(const KArgs& a, int j, const T* m) {
-  constexpr int C = DIM + 2;
-  const int e0 = __ldg(a.sp_ptr + j * C), e1 = __ldg(a.sp_ptr + j * C + 1);
-  T s = Ar<T>::zero();
-  for (int e = e0; e < e1; ++e) s = Ar<T>::fma(Ar<T>::coef(a, e), m[__ldg(a.sp_mono + e)], s);
-  return s;
-}
-
-// U-values u_k = b_k(xhat, that) of every basis function at one point (times s if SCALE)
-template <int DIM, typename T, bool SCALE = true>
-__device__ __forceinline__ void eval_uvalues(const KArgs& a, T th, const T* xh, T* m, T s, T* u) {
-  eval_monomials<DIM, T>(a, th, xh, m);
-  for (int k = 0; k < a.nb; ++k) u[k] = SCALE ? Ar<T>::mul(s, sp_eval<DIM, T>(a, k, m)) : sp_eval<DIM, T>(a, k, m);
-}
-
-// packed upper-triangle index of (i, j), i, j < nb
-__device__ __forceinline__ int pair_index(int i, int j, int nb) {
-  const int lo = min(i, j), hi = max(i, j);
-  return lo * nb - lo * (lo - 1) / 2 + (hi - lo);
-}
-
-// (D_va X D_vb^T)_ij for a packed symmetric X, D_var given by the relation
-// table: (D_var u)_j = sum over entries e of (j, var) of fac_e u[src_e]
-// (the factors are small integers, exact in binary32)
-template <int DIM, typename T>
-__device__ __forceinline__ T congruence(const KArgs& a, int i, int va, int j, int vb, const T* X, int nb) {
-  constexpr int NVAR = DIM + 1;
-  const int a0 = __ldg(a.rel_ptr + i * NVAR + va), a1 = __ldg(a.rel_ptr + i * NVAR + va + 1);
-  const int b0 = __ldg(a.rel_ptr + j * NVAR + vb), b1 = __ldg(a.rel_ptr + j * NVAR + vb + 1);
-  T s = Ar<T>::zero();
-  for (int e = a0; e < a1; ++e) {
-    const int si = __ldg(a.rel_src + e);
-    T t = Ar<T>::zero();
-    for (int f = b0; f < b1; ++f)
-      t = Ar<T>::add(t, Ar<T>::mulf(X[pair_index(si, __ldg(a.rel_src + f), nb)], __ldg(a.rel_facf + f)));
-    s = Ar<T>::add(s, Ar<T>::mulf(t, __ldg(a.rel_facf + e)));
-  }
-  return s;
-}
-
-// (D_var y)_i for a vector y
-template <int DIM, typename T>
-__device__ __forceinline__ T rel_apply(const KArgs& a, int i, int var, const T* y) {
-  const int e0 = __ldg(a.rel_ptr + i * (DIM + 1) + var), e1 = __ldg(a.rel_ptr + i * (DIM + 1) + var + 1);
-  T s = Ar<T>::zero();
-  for (int e = e0; e < e1; ++e) s = Ar<T>::add(s, Ar<T>::mulf(y[__ldg(a.rel_src + e)], __ldg(a.rel_facf + e)));
-  return s;
-}
-
-// (D_var^T y)_k through the transposed table
-template <int DIM, typename T>
-__device__ __forceinline__ T relT_apply(const KArgs& a, int k, int var, const T* y) {
-  const int e0 = __ldg(a.relT_ptr + k * (DIM + 1) + var), e1 = __ldg(a.relT_ptr + k * (DIM + 1) + var + 1);
-  T s = Ar<T>::zero();
-  for (int e = e0; e < e1; ++e) s = Ar<T>::add(s, Ar<T>::mulf(y[__ldg(a.relT_dst + e)], __ldg(a.relT_facf + e)));
-  return s;
-}
-
-// 1/x by two Newton-Raphson steps r <- r + r (1 - x r) from the binary32
-// reciprocal (quadratic convergence: 24 -> 48 -> 96 bits); falls back to the
-// division outside the binary32 range.
-__device__ __forceinline__ double recip(double x) {
-  const double ax = fabs(x);
-  if (!(ax > 1e-30 && ax < 1e30)) return 1.0 / x;
-  double r = (double)__frcp_rn((float)x);
-  double e = fma(-x, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-x, r, 1.0);
-  return fma(r, e, r);
-}
-
-// (D_va X D_vb^T)_ij for a full row-major nb x nb X (or X^T when TR)
-template <int DIM, typename T, bool TR>
-__device__ __forceinline__ T congruence_full(const KArgs& a, int i, int va, int j, int vb, const T* X, int nb) {
-  constexpr int NVAR = DIM + 1;
-  const int a0 = __ldg(a.rel_ptr + i * NVAR + va), a1 = __ldg(a.rel_ptr + i * NVAR + va + 1);
-  const int b0 = __ldg(a.rel_ptr + j * NVAR + vb), b1 = __ldg(a.rel_ptr + j * NVAR + vb + 1);
-  T s = Ar<T>::zero();
-  for (int e = a0; e < a1; ++e) {
-    const int si = __ldg(a.rel_src + e);
-    T t = Ar<T>::zero();
-    for (int f = b0; f < b1; ++f) {
-      const int sj = __ldg(a.rel_src + f);
-      t = Ar<T>::add(t, Ar<T>::mulf(TR ? X[sj * nb + si] : X[si * nb + sj], __ldg(a.rel_facf + f)));
-    }
-    s = Ar<T>::add(s, Ar<T>::mulf(t, __ldg(a.rel_facf + e)));
-  }
-  return s;
-}
-
-// n-weighted normal-derivative congruences: (D_a X D_b^T) with a, b in {t, n}
-// where D_n = sum_m n_m D_m.  SYM: X packed symmetric, else full (TR: X^T).
-template <int DIM, typename T, int MODE>
-__device__ __forceinline__ T cong_any(const KArgs& a, int i, int va, int j, int vb, const T* X, int nb) {
-  if constexpr (MODE == 0) return congruence<DIM, T>(a, i, va, j, vb, X, nb);
-  else if constexpr (MODE == 1) return congruence_full<DIM, T, false>(a, i, va, j, vb, X, nb);
-  else return congruence_full<DIM, T, true>(a, i, va, j, vb, X, nb);
-}
-template <int DIM, typename T, int MODE>
-__device__ __forceinline__ void iface_terms(const KArgs& a, int i, int j, const T* X, int nb, const T* nrm,
-                                            T* ntn, T* ntt, T* ttn, T* nnn) {
-  // ntt = (D_n X D_t^T), ttn = (D_t X D_n^T), nnn = (D_n X D_n^T), ntn unused slot kept for symmetry
-  T a1 = Ar<T>::zero(), a2 = Ar<T>::zero(), a3 = Ar<T>::zero();
-  for (int m = 0; m < DIM; ++m) {
-    a1 = Ar<T>::fma(nrm[m], cong_any<DIM, T, MODE>(a, i, 1 + m, j, 0, X, nb), a1);
-    a2 = Ar<T>::fma(nrm[m], cong_any<DIM, T, MODE>(a, i, 0, j, 1 + m, X, nb), a2);
-    for (int m2 = 0; m2 < DIM; ++m2)
-      a3 = Ar<T>::fma(Ar<T>::mul(nrm[m], nrm[m2]), cong_any<DIM, T, MODE>(a, i, 1 + m, j, 1 + m2, X, nb), a3);
-  }
-  *ntt = a1;
-  *ttn = a2;
-  *nnn = a3;
-  *ntn = cong_any<DIM, T, MODE>(a, i, 0, j, 0, X, nb);   // (D_t X D_t^T)
-}
-
-// One tent per thread-block cluster of CS CTAs (CS = gridDim.x / tents in the
-// launch, 1..8).  Each CTA takes a slice of the patch's points.
-//
-// Materials (Section 4.2).  The patch elements are grouped by wave speed; each
-// group g carries its own polynomial x_g in U^p mapped with its own c_g
-// (Remark 3.1), so the tent system has ng*nb unknowns.
-//
-// Assembly through Grams of U-values.  With u the vector of the nb U-values
-// at a point and the exact derivative maps of U^p, v = (c/h) D_t u,
-// sigma_m = -(1/h) D_m u, the top-face form of group g summed over its points is
-//   A_top = h^-2 [ D_t G D_t^T + sum_m D_m G D_m^T + c sum_m (D_m H_m D_t^T + D_t H_m D_m^T) ],
-//   G = sum_q w u u^T,  H_m = sum_K g_{K,m} G_K  (g = top front gradient on K),
-// the recovery term is A_bot = sum_q w u_b u_b^T, the bottom data give
-//   b = gamma + (c/h) D_t alpha - (1/h) sum_m D_m beta_m
-// with moments gamma = sum w U_b u_b, alpha = sum w (c^-2 v_b - s_b.g_b) u_b,
-// beta_m = sum w (s_b,m - v_b g_b,m) u_b.  A Dirichlet facet with normal n
-// adds A_D = (c/h) D_t F E^T, b_D = E' delta, F = sum w u u^T,
-// delta = sum w g_D u, E = alpha_D (c/h) D_t - (1/h) D_n, E' = alpha_D (c/h) D_t + (1/h) D_n,
-// D_n = sum_m n_m D_m.  A time-like facet between groups + and - (normal n out
-// of +) adds, for test side t and trial side s (signs s_+ = 1, s_- = -1),
-//   A^{ts} = s_t h^-2 [ -c_s/2 D_n F^{ts} D_t^T - c_t/2 D_t F^{ts} D_n^T ]
-//          + s_t s_s h^-2 [ alpha c_s c_t D_t F^{ts} D_t^T + beta D_n F^{ts} D_n^T ],
-//   F^{ts} = sum w u^t u^s^T,
-// the {v}[[tau]]_N + {s}.[[w]]_N + alpha [[v]]_N.[[w]]_N + beta [[s]]_N [[tau]]_N
-// terms of eq. (2.5).  Every CTA publishes its partial Grams and moments;
-// after a cluster barrier every CTA sums them in rank order, forms A and b,
-// solves, and writes the outflow of its slice.
-//
-// MIXED = false: everything in binary64, LU with partial pivoting (none for
-// single-material interior tents, whose A is symmetric positive definite).
-// MIXED = true: assembly, residual and outflow in float-float; A is
-// equilibrated (D A D, D = |diag A|^-1/2), factorised in binary32 and the
-// solution refined against the float-float A until the correction stops
-// shrinking (at most kMaxRefine steps; TP_ERR_NOCONV if it stalls high).
-//
-// ADJ = true: the adjoint tent map (reverse sweep).  With g_D = 0 a tent maps
-// its bottom values linearly to its top values, b = B f_bot, A x = b,
-// f_top = E x; the adjoint takes lambda at the top points to
-// mu = A^-T (E^T lambda) and lambda_bot = B^T mu at the bottom points.  In the
-// U-value form E^T lambda = zeta_U + (c/h) D_t zeta_v - (1/h) sum_m D_m zeta_m,
-// zeta = sum_q lambda_q u_q over the top points (the moment formula of b), and
-// B^T mu at a bottom point is w (s0, c^-2 s_t - g_b.s, s_m - g_b,m s_t) with
-// s0 = u.mu, s_t = (c/h) u.D_t^T mu, s_m = -(1/h) u.D_m^T mu.  The front and
-// time arrays of the arguments are then the adjoint state (tau runs backwards).
-template <int DIM, bool MIXED, bool ADJ>
-__global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int tent0) {
-  using T = typename std::conditional<MIXED, dd, double>::type;
-  using R = Ar<T>;
-  constexpr int NV = DIM + 1;   // vertices per element
-  constexpr int C = DIM + 2;    // U, v, sigma  (and gamma, alpha, beta_m moments)
-  extern __shared__ __align__(16) double sm[];
-  __shared__ int s_P, s_v, s_nfac, s_nif, s_ng;
-  __shared__ double s_ttop, s_tbot, s_tc, s_ih;
-  __shared__ double s_gc[tp::kMaxGroups];
-  __shared__ double s_xv[DIM];
-  __shared__ int s_el[tp::kMaxPatch], s_grp[tp::kMaxPatch];
-  __shared__ double s_X[tp::kMaxPatch][NV][DIM];
-  __shared__ double s_tb[tp::kMaxPatch][NV], s_tt[tp::kMaxPatch][NV];
-  __shared__ double s_gb[tp::kMaxPatch][DIM], s_gt[tp::kMaxPatch][DIM];
-  __shared__ double s_sdet[tp::kMaxPatch];
-  __shared__ double s_fP[tp::kMaxFacets][NV][DIM + 1];   // vertical face simplices (x, t)
-  __shared__ double s_fscale[tp::kMaxFacets], s_fn[tp::kMaxFacets][DIM];
-  __shared__ int s_fg[tp::kMaxFacets], s_fg2[tp::kMaxFacets];   // groups (Dirichlet: one; interface: +, -)
-  __shared__ int s_pgrp[2 * 64];
-  __shared__ int s_piv;
-  __shared__ float s_red[2][kThreads / 32];
-  __shared__ int s_stop, s_conv;
-
-  cg::cluster_group cluster = cg::this_cluster();
-  const int rank = (int)cluster.block_rank();
-  const int CS = (int)cluster.num_blocks();
-  const int tid = threadIdx.x;
-  const int lane = tid & 31, warp = tid >> 5;
-  const int tent = tent0 + blockIdx.x / CS;
-  const int nb = a.nb, Q = a.Q, nrhs = a.nrhs, CH = a.CH, NG = a.ngmax;
-  const int npair = nb * (nb + 1) / 2;
-  const int nmom = nrhs * C * nb;
-  T* sA = reinterpret_cast<T*>(sm);                  // N*N        assembled A, then LU factors
-  T* sb = reinterpret_cast<T*>(sm + a.off_b);        // nrhs*N     assembled b, then x
-  T* sPG = reinterpret_cast<T*>(sm + a.off_pg);      // NG*npair   this CTA: G (top) per group
-  T* sPH = reinterpret_cast<T*>(sm + a.off_ph);      // NG*DIM*npair  H_m
-  T* sPGb = reinterpret_cast<T*>(sm + a.off_pgb);    // NG*npair   G (bottom, recovery)
-  T* sPM = reinterpret_cast<T*>(sm + a.off_pm);      // NG*nmom    moments (gamma, alpha, beta_m) per rhs
-  T* sPD = reinterpret_cast<T*>(sm + a.off_pd);      // N*N        Dirichlet and interface blocks
-  T* sPBD = reinterpret_cast<T*>(sm + a.off_pbd);    // nrhs*N     Dirichlet right-hand side
-  T* sSG = reinterpret_cast<T*>(sm + a.off_sg);      // NG*(DIM+2)*npair  summed G, H_m, Gbot
-  T* sSM = reinterpret_cast<T*>(sm + a.off_sm);      // NG*nmom    summed moments
-  T* sF = reinterpret_cast<T*>(sm + a.off_f);        // npair      facet Gram (+ side)
-  T* sF2 = reinterpret_cast<T*>(sm + a.off_f2);      // npair      facet Gram (- side)
-  T* sFpm = reinterpret_cast<T*>(sm + a.off_fpm);    // nb*nb      facet Gram (+ test, - trial)
-  T* sDel = reinterpret_cast<T*>(sm + a.off_del);    // nrhs*nb    facet moments delta
-  T* sU = reinterpret_cast<T*>(sm + a.off_u);        // 2*CH*nb    U-values (scaled) per (side, point)
-  T* sM = reinterpret_cast<T*>(sm + a.off_mono);     // 2*CH*mono_stride
-  T* sCB = reinterpret_cast<T*>(sm + a.off_cb);      // CH*nrhs*C  data coefficients
-  T* sGd = reinterpret_cast<T*>(sm + a.off_gd);      // CH*nrhs    Dirichlet data coefficients
-  T* sY = reinterpret_cast<T*>(sm + a.off_y);        // NG*nmom    outflow coefficient vectors
-  double* sRD = sm + a.off_rd;                       // N          reciprocal pivots (binary64 path)
-
-  // ---------------- phase 0: tent, materials and patch geometry ----------------
-  if (tid == 0) {
-    const int v = a.tent_v[tent];
-    s_v = v;
-    const int p0 = a.star_ptr[v], p1 = a.star_ptr[v + 1];
-    const int P = p1 - p0;
-    s_P = P;
-    s_ttop = a.tent_ttop[tent];
-    s_tbot = ADJ ? a.tent_tbot[tent] : a.tau[v];
-    s_tc = 0.5 * (s_tbot + s_ttop);
-    s_ih = 1.0 / a.tent_h[tent];
-    for (int d = 0; d < DIM; ++d) s_xv[d] = a.X[(int64_t)v * DIM + d];
-    s_nfac = a.vfac_ptr[v + 1] - a.vfac_ptr[v];
-    s_nif = a.ifac_ptr[v + 1] - a.ifac_ptr[v];
-    // materials by bitwise-equal c in order of first appearance; elements sorted by material
-    int ng = 0, tmp[tp::kMaxPatch];
-    for (int k = 0; k < P; ++k) {
-      const double ck = a.cK[a.star_el[p0 + k]];
-      int g = 0;
-      while (g < ng && s_gc[g] != ck) ++g;
-      if (g == ng) s_gc[ng++] = ck;
-      tmp[k] = g;
-    }
-    int pos = 0;
-    for (int g = 0; g < ng; ++g)
-      for (int k = 0; k < P; ++k)
-        if (tmp[k] == g) {
-          s_el[pos] = a.star_el[p0 + k];
-          s_grp[pos++] = g;
-        }
-    s_ng = ng;
-  }
-  for (int id = tid; id < NG * nmom; id += blockDim.x) sPM[id] = R::zero();
-  for (int id = tid; id < NG * (DIM + 2) * npair; id += blockDim.x) sPG[id] = R::zero();   // PG, PH, PGb contiguous
-  __syncthreads();
-  const int P = s_P, v = s_v, nfac = s_nfac, nif = s_nif, ng = s_ng;
-  const int N = ng * nb;
-  const bool extra = (nfac > 0 || nif > 0);
-  for (int k = tid; k < P; k += blockDim.x) {
-    const int el = s_el[k];
-    for (int i = 0; i < NV; ++i) {
-      const int vi = a.elems[(int64_t)el * NV + i];
-      for (int d = 0; d < DIM; ++d) s_X[k][i][d] = a.X[(int64_t)vi * DIM + d];
-      const double tv = a.tau[vi];
-      s_tb[k][i] = (vi == v) ? s_tbot : tv;
-      s_tt[k][i] = (vi == v) ? s_ttop : tv;
-    }
-    double e[DIM][DIM], db[DIM], dt[DIM];
-    for (int i = 0; i < DIM; ++i) {
-      for (int d = 0; d < DIM; ++d) e[i][d] = s_X[k][i + 1][d] - s_X[k][0][d];
-      db[i] = s_tb[k][i + 1] - s_tb[k][0];
-      dt[i] = s_tt[k][i + 1] - s_tt[k][0];
-    }
-    double gb[DIM], gt[DIM];
-    const double det = lin_grad<DIM>(e, db, gb);
-    lin_grad<DIM>(e, dt, gt);
-    double g2 = 0.0;
-    for (int d = 0; d < DIM; ++d) {
-      s_gb[k][d] = gb[d];
-      s_gt[k][d] = gt[d];
-      g2 += gt[d] * gt[d];
-    }
-    s_sdet[k] = sqrt(fabs(det));
-    const double ck = s_gc[s_grp[k]];
-    if (!(1.0 / (ck * ck) - g2 > 0.0)) flag_error(a, TP_ERR_CAUSALITY, tent);   // space-like top face
-  }
-  // vertical face simplices (x_v, t_bot), (x_v, t_top), (x_w, tau_w): Dirichlet facets
-  // first, then the time-like interface facets
-  for (int f = tid; f < nfac + nif; f += blockDim.x) {
-    const bool dir = f < nfac;
-    const int fid = dir ? a.vfac[a.vfac_ptr[v] + f] : a.ifac_ptr[v] + (f - nfac);
-    const int* fv = dir ? a.facet_vert + (int64_t)fid * DIM : a.ifac_vert + (int64_t)fid * DIM;
-    const double* fn = dir ? a.facet_nrm + (int64_t)fid * DIM : a.ifac_nrm + (int64_t)fid * DIM;
-    for (int d = 0; d < DIM; ++d) {
-      s_fP[f][0][d] = a.X[(int64_t)v * DIM + d];
-      s_fP[f][1][d] = a.X[(int64_t)v * DIM + d];
-      s_fn[f][d] = fn[d];
-    }
-    s_fP[f][0][DIM] = s_tbot;
-    s_fP[f][1][DIM] = s_ttop;
-    int c2 = 2;
-    for (int i = 0; i < DIM; ++i) {
-      const int w = fv[i];
-      if (w == v) continue;
-      for (int d = 0; d < DIM; ++d) s_fP[f][c2][d] = a.X[(int64_t)w * DIM + d];
-      s_fP[f][c2][DIM] = a.tau[w];
-      ++c2;
-    }
-    // n! * n-volume = sqrt(det(E^T E)), E = [P_i - P_0] ((n+1) x n)
-    double G[DIM][DIM];
-    for (int i = 0; i < DIM; ++i)
-      for (int j = 0; j < DIM; ++j) {
-        double s = 0.0;
-        for (int d = 0; d <= DIM; ++d) s += (s_fP[f][i + 1][d] - s_fP[f][0][d]) * (s_fP[f][j + 1][d] - s_fP[f][0][d]);
-        G[i][j] = s;
-      }
-    s_fscale[f] = sqrt(fabs(small_det<DIM>(G)));
-    // groups of the facet's element(s), found by their wave speed
-    auto group_of = [&](int el) {
-      const double ce = a.cK[el];
-      int g = 0;
-      while (g < ng - 1 && s_gc[g] != ce) ++g;
-      return g;
-    };
-    if (dir) {
-      s_fg[f] = group_of(a.facet_elem[fid]);
-      s_fg2[f] = s_fg[f];
-    } else {
-      s_fg[f] = group_of(a.ifac_kp[fid]);
-      s_fg2[f] = group_of(a.ifac_km[fid]);
-    }
-  }
-  // Gram pairs owned by this thread (upper triangle, i <= j, row-major order)
-  int pi[kMaxPair], pj[kMaxPair];
-  T aK[kMaxPair], aG[kMaxPair], aH[kMaxPair][DIM], aB[kMaxPair];
-#pragma unroll
-  for (int s = 0; s < kMaxPair; ++s) {
-    const int id = tid + s * kThreads;
-    int i = 0, j = 0;
-    if (id < npair) {
-      int rem = id;
-      while (rem >= nb - i) {
-        rem -= nb - i;
-        ++i;
-      }
-      j = i + rem;
-    }
-    pi[s] = i;
-    pj[s] = j;
-    aK[s] = aG[s] = aB[s] = R::zero();
-#pragma unroll
-    for (int d = 0; d < DIM; ++d) aH[s][d] = R::zero();
-  }
-  __syncthreads();
-
-  // ---------------- phase 1: this CTA's slice of the patch points ----------------
-  const int NP = P * Q;
-  const int slice = (NP + CS - 1) / CS;
-  const int q0 = min(NP, rank * slice), q1 = min(NP, q0 + slice);
-  const double ih = s_ih, tc = s_tc;
-  int curk = q0 / Q;
-  int curg = (q1 > q0) ? s_grp[curk] : 0;
-  // element flush: G += G_K, H_m += g_{K,m} G_K;  group flush: publish G, H, Gbot of the group
-  auto flush_element = [&](int k) {
-    T g[DIM];
-    for (int d = 0; d < DIM; ++d) g[d] = R::from(s_gt[k][d]);
-#pragma unroll
-    for (int s = 0; s < kMaxPair; ++s) {
-      aG[s] = R::add(aG[s], aK[s]);
-#pragma unroll
-      for (int d = 0; d < DIM; ++d) aH[s][d] = R::fma(g[d], aK[s], aH[s][d]);
-      aK[s] = R::zero();
-    }
-  };
-  auto flush_group = [&](int g) {
-#pragma unroll
-    for (int s = 0; s < kMaxPair; ++s) {
-      const int id = tid + s * kThreads;
-      if (id < npair) {
-        sPG[g * npair + id] = R::add(sPG[g * npair + id], aG[s]);
-#pragma unroll
-        for (int d = 0; d < DIM; ++d)
-          sPH[(g * DIM + d) * npair + id] = R::add(sPH[(g * DIM + d) * npair + id], aH[s][d]);
-        sPGb[g * npair + id] = R::add(sPGb[g * npair + id], aB[s]);
-      }
-      aG[s] = aB[s] = R::zero();
-#pragma unroll
-      for (int d = 0; d < DIM; ++d) aH[s][d] = R::zero();
-    }
-  };
-  for (int base = q0; base < q1; base += CH) {
-    const int nq = min(CH, q1 - base);
-    // (a) one thread per (side, point): sqrt(w)-scaled U-values, data coefficients
-    if (tid < 2 * CH) {
-      const int side = tid / CH, ql = tid % CH, qg = base + ql;
-      if (ql < nq) {
-        const int k = qg / Q, q = qg % Q, g = s_grp[k];
-        const double cg = s_gc[g], ic2 = 1.0 / (cg * cg);
-        if (side == 0) s_pgrp[ql] = g;
-        double x[DIM], tt = 0.0;
-        for (int d = 0; d < DIM; ++d) x[d] = 0.0;
-        for (int i = 0; i < NV; ++i) {
-          const double l = __ldg(a.bary + q * NV + i);
-          for (int d = 0; d < DIM; ++d) x[d] = fma(l, s_X[k][i][d], x[d]);
-          tt = fma(l, side == 0 ? s_tt[k][i] : s_tb[k][i], tt);
-        }
-        T xh[DIM];
-        for (int d = 0; d < DIM; ++d) xh[d] = R::from((x[d] - s_xv[d]) * ih);
-        const T th = R::from(cg * (tt - tc) * ih);
-        const double sw = __ldg(a.sqw + q) * s_sdet[k];
-        eval_uvalues<DIM, T>(a, th, xh, sM + tid * a.mono_stride, R::from(sw), sU + (size_t)tid * nb);
-        const int el = s_el[k];
-        if (ADJ && side == 0) {
-          // adjoint: zeta = sum_q lambda_q u_q over the top points
-          const double isw = 1.0 / sw;
-          for (int r = 0; r < nrhs; ++r) {
-            const double* f = a.front + (((int64_t)r * a.ne + el) * Q + q) * C;
-            T* cb = sCB + ((size_t)ql * nrhs + r) * C;
-            for (int cc = 0; cc < C; ++cc) cb[cc] = R::from(f[cc] * isw);
-          }
-        }
-        if (!ADJ && side == 1) {
-          for (int r = 0; r < nrhs; ++r) {
-            const double* f = a.front + (((int64_t)r * a.ne + el) * Q + q) * C;
-            const double Ub = f[0], vb = f[1];
-            double sg = 0.0;
-            for (int d = 0; d < DIM; ++d) sg = fma(f[2 + d], s_gb[k][d], sg);
-            T* cb = sCB + ((size_t)ql * nrhs + r) * C;
-            cb[0] = R::from(sw * Ub);                       // gamma
-            cb[1] = R::from(sw * (ic2 * vb - sg));          // alpha
-            for (int d = 0; d < DIM; ++d) cb[2 + d] = R::from(sw * (f[2 + d] - vb * s_gb[k][d]));   // beta_m
-          }
-        }
-      }
-    }
-    __syncthreads();
-    // (b) Grams of U-values: top per element (flushed into G and H_m), bottom; per material
-    for (int ql = 0; ql < nq; ++ql) {
-      const int k = (base + ql) / Q;
-      if (k != curk) {
-        flush_element(curk);
-        if (s_grp[k] != curg) {
-          flush_group(curg);
-          curg = s_grp[k];
-        }
-        curk = k;
-      }
-      const T* ut = sU + (size_t)ql * nb;
-      const T* ub = sU + (size_t)(CH + ql) * nb;
-#pragma unroll
-      for (int s = 0; s < kMaxPair; ++s) {
-        if (tid + s * kThreads < npair) {
-          aK[s] = R::fma(ut[pi[s]], ut[pj[s]], aK[s]);
-          aB[s] = R::fma(ub[pi[s]], ub[pj[s]], aB[s]);
-        }
-      }
-    }
-    // (c) moments of the data (forward: bottom points; adjoint: top points), per material
-    const int row0 = ADJ ? 0 : CH;
-    for (int id = tid; id < ng * nmom; id += blockDim.x) {
-      const int g = id / nmom, rest = id % nmom;
-      const int r = rest / (C * nb), rem = rest % (C * nb), cc = rem / nb, i = rem % nb;
-      T t = sPM[id];
-      for (int ql = 0; ql < nq; ++ql)
-        if (s_pgrp[ql] == g) t = R::fma(sCB[((size_t)ql * nrhs + r) * C + cc], sU[(size_t)(row0 + ql) * nb + i], t);
-      sPM[id] = t;
-    }
-    __syncthreads();
-  }
-  if (q1 > q0) {
-    flush_element(curk);
-    flush_group(curg);
-  }
-
-  // ---------------- phase 2: vertical faces (this CTA's slice of each facet's points) ----------------
-  if (extra) {
-    for (int id = tid; id < N * N; id += blockDim.x) sPD[id] = R::zero();
-    for (int id = tid; id < nrhs * N; id += blockDim.x) sPBD[id] = R::zero();
-    for (int id = tid; id < nrhs * nb; id += blockDim.x) sDel[id] = R::zero();
-    for (int id = tid; id < nb * nb; id += blockDim.x) sFpm[id] = R::zero();
-    const int fsl = (Q + CS - 1) / CS;
-    const int f0 = min(Q, rank * fsl), f1 = min(Q, f0 + fsl);
-    __syncthreads();
-    for (int f = 0; f < nfac + nif; ++f) {
-      const bool dir = f < nfac;
-      const int gp = s_fg[f], gm = s_fg2[f];
-      const double cp = s_gc[gp], cm = s_gc[gm];
-      T aF[kMaxPair], aF2[kMaxPair];
-#pragma unroll
-      for (int s = 0; s < kMaxPair; ++s) aF[s] = aF2[s] = R::zero();
-      for (int base = f0; base < f1; base += CH) {
-        const int nq = min(CH, f1 - base);
-        if (tid < nq) {
-          const int q = base + tid;
-          double xt[DIM + 1];
-          for (int d = 0; d <= DIM; ++d) xt[d] = 0.0;
-          for (int i = 0; i < NV; ++i) {
-            const double l = __ldg(a.bary + q * NV + i);
-            for (int d = 0; d <= DIM; ++d) xt[d] = fma(l, s_fP[f][i][d], xt[d]);
-          }
-          T xh[DIM];
-          for (int d = 0; d < DIM; ++d) xh[d] = R::from((xt[d] - s_xv[d]) * ih);
-          const double sw = sqrt(__ldg(a.wref + q) * s_fscale[f]);
-          eval_uvalues<DIM, T>(a, R::from(cp * (xt[DIM] - tc) * ih), xh, sM + tid * a.mono_stride, R::from(sw),
-                               sU + (size_t)tid * nb);
-          if (!dir)
-            eval_uvalues<DIM, T>(a, R::from(cm * (xt[DIM] - tc) * ih), xh, sM + (CH + tid) * a.mono_stride,
-                                 R::from(sw), sU + (size_t)(CH + tid) * nb);
-          if (dir) {
-            const long long goff = a.tent_gdoff[tent] + (long long)f * Q + q;
-            for (int r = 0; r < nrhs; ++r)
-              sGd[tid * nrhs + r] = R::from((!ADJ && a.gD != nullptr) ? sw * a.gD[(long long)r * a.n_bnd + goff] : 0.0);
-          }
-        }
-        __syncthreads();
-        for (int ql = 0; ql < nq; ++ql) {
-          const T* u = sU + (size_t)ql * nb;
-          const T* u2 = sU + (size_t)(CH + ql) * nb;
-#pragma unroll
-          for (int s = 0; s < kMaxPair; ++s)
-            if (tid + s * kThreads < npair) {
-              aF[s] = R::fma(u[pi[s]], u[pj[s]], aF[s]);
-              if (!dir) aF2[s] = R::fma(u2[pi[s]], u2[pj[s]], aF2[s]);
-            }
-        }
-        if (dir) {
-          for (int id = tid; id < nrhs * nb; id += blockDim.x) {
-            const int r = id / nb, i = id % nb;
-            T t = sDel[id];
-            for (int ql = 0; ql < nq; ++ql) t = R::fma(sGd[ql * nrhs + r], sU[(size_t)ql * nb + i], t);
-            sDel[id] = t;
-          }
-        } else {
-          for (int id = tid; id < nb * nb; id += blockDim.x) {
-            const int i = id / nb, j = id % nb;
-            T t = sFpm[id];
-            for (int ql = 0; ql < nq; ++ql) t = R::fma(sU[(size_t)ql * nb + i], sU[(size_t)(CH + ql) * nb + j], t);
-            sFpm[id] = t;
-          }
-        }
-        __syncthreads();
-      }
-#pragma unroll
-      for (int s = 0; s < kMaxPair; ++s)
-        if (tid + s * kThreads < npair) {
-          sF[tid + s * kThreads] = aF[s];
-          sF2[tid + s * kThreads] = aF2[s];
-        }
-      __syncthreads();
-      T nrm[DIM];
-      for (int d = 0; d < DIM; ++d) nrm[d] = R::from(s_fn[f][d]);
-      if (dir) {
-        const T ac = R::from(a.alpha * cp * ih), cih = R::from(cp * ih), mih = R::from(-ih), pih = R::from(ih);
-        for (int id = tid; id < nb * nb; id += blockDim.x) {
-          const int i = id / nb, j = id % nb;
-          T tt_, tn_, nt_, nn_;
-          iface_terms<DIM, T, 0>(a, i, j, sF, nb, nrm, &tt_, &nt_, &tn_, &nn_);
-          // A_D = (c/h) D_t F E^T,  E = alpha (c/h) D_t - (1/h) D_n
-          const T t = R::fma(mih, tn_, R::mul(ac, tt_));
-          T* dst = sPD + (size_t)(gp * nb + i) * N + gp * nb + j;
-          *dst = R::fma(cih, t, *dst);
-        }
-        for (int id = tid; id < nrhs * nb; id += blockDim.x) {
-          const int r = id / nb, i = id % nb;
-          const T* del = sDel + (size_t)r * nb;
-          T dn = R::zero();
-          for (int d = 0; d < DIM; ++d) dn = R::fma(nrm[d], rel_apply<DIM, T>(a, i, 1 + d, del), dn);
-          // b_D = E' delta,  E' = alpha (c/h) D_t + (1/h) D_n
-          const T t = R::fma(pih, dn, R::mul(ac, rel_apply<DIM, T>(a, i, 0, del)));
-          T* dst = sPBD + (size_t)r * N + gp * nb + i;
-          *dst = R::add(*dst, t);
-        }
-      } else {
-        const double ih2 = ih * ih;
-        for (int id = tid; id < 4 * nb * nb; id += blockDim.x) {
-          const int blk = id / (nb * nb), rem = id % (nb * nb), i = rem / nb, j = rem % nb;
-          const int tside = blk >> 1, sside = blk & 1;   // 0: +, 1: -
-          const double st = tside ? -1.0 : 1.0, ss = sside ? -1.0 : 1.0;
-          const double ct = tside ? cm : cp, cs = sside ? cm : cp;
-          T tt_, nt_, tn_, nn_;
-          if (tside == sside) {
-            iface_terms<DIM, T, 0>(a, i, j, tside ? sF2 : sF, nb, nrm, &tt_, &nt_, &tn_, &nn_);
-          } else if (tside == 0) {
-            iface_terms<DIM, T, 1>(a, i, j, sFpm, nb, nrm, &tt_, &nt_, &tn_, &nn_);
-          } else {
-            iface_terms<DIM, T, 2>(a, i, j, sFpm, nb, nrm, &tt_, &nt_, &tn_, &nn_);
-          }
-          T t = R::mul(R::from(-0.5 * st * cs * ih2), nt_);
-          t = R::fma(R::from(-0.5 * st * ct * ih2), tn_, t);
-          t = R::fma(R::from(st * ss * a.alpha * cs * ct * ih2), tt_, t);
-          t = R::fma(R::from(st * ss * a.beta * ih2), nn_, t);
-          const int gr = tside ? gm : gp, gcl = sside ? gm : gp;
-          T* dst = sPD + (size_t)(gr * nb + i) * N + gcl * nb + j;
-          *dst = R::add(*dst, t);
-        }
-      }
-      __syncthreads();
-      for (int id = tid; id < nrhs * nb; id += blockDim.x) sDel[id] = R::zero();
-      for (int id = tid; id < nb * nb; id += blockDim.x) sFpm[id] = R::zero();
-      __syncthreads();
-    }
-  }
-
-  // ---------------- cluster reduction (rank order) ----------------
-  cluster.sync();
-  // layout [G (NG*npair) | H_m (NG*DIM*npair) | Gbot (NG*npair)]; unused groups hold zeros
-  for (int id = tid; id < NG * (DIM + 2) * npair; id += blockDim.x) {
-    T t = R::zero();
-    for (int r = 0; r < CS; ++r) t = R::add(t, cluster.map_shared_rank(sPG, r)[id]);
-    sSG[id] = t;
-  }
-  for (int id = tid; id < ng * nmom; id += blockDim.x) {
-    T t = R::zero();
-    for (int r = 0; r < CS; ++r) t = R::add(t, cluster.map_shared_rank(sPM, r)[id]);
-    sSM[id] = t;
-  }
-  for (int id = tid; id < N * N; id += blockDim.x) {
-    T t = R::zero();
-    if (extra)
-      for (int r = 0; r < CS; ++r) t = R::add(t, cluster.map_shared_rank(sPD, r)[id]);
-    sA[id] = t;
-  }
-  for (int id = tid; id < nrhs * N; id += blockDim.x) {
-    T t = R::zero();
-    if (nfac > 0)
-      for (int r = 0; r < CS; ++r) t = R::add(t, cluster.map_shared_rank(sPBD, r)[id]);
-    sb[id] = t;
-  }
-  cluster.sync();   // no CTA leaves or reuses its partials while another still reads them
-  {
-    const T ih2 = R::from(ih * ih), mih = R::from(-ih);
-    for (int id = tid; id < ng * nb * nb; id += blockDim.x) {
-      const int g = id / (nb * nb), rem = id % (nb * nb), i = rem / nb, j = rem % nb;
-      const T* SG = sSG + (size_t)g * npair;
-      const T* SGb = sSG + (size_t)(NG * (DIM + 1) + g) * npair;
-      const T cc_ = R::from(s_gc[g]);
-      T t = congruence<DIM, T>(a, i, 0, j, 0, SG, nb);
-      for (int d = 0; d < DIM; ++d) {
-        const T* H = sSG + (size_t)(NG + g * DIM + d) * npair;
-        t = R::add(t, congruence<DIM, T>(a, i, 1 + d, j, 1 + d, SG, nb));
-        t = R::fma(cc_, R::add(congruence<DIM, T>(a, i, 1 + d, j, 0, H, nb), congruence<DIM, T>(a, i, 0, j, 1 + d, H, nb)), t);
-      }
-      T* dst = sA + (size_t)(g * nb + i) * N + g * nb + j;
-      *dst = R::add(*dst, R::fma(ih2, t, SGb[pair_index(i, j, nb)]));
-    }
-    for (int id = tid; id < ng * nrhs * nb; id += blockDim.x) {
-      const int g = id / (nrhs * nb), rem = id % (nrhs * nb), r = rem / nb, i = rem % nb;
-      const T* M = sSM + (size_t)g * nmom + (size_t)r * C * nb;   // gamma, alpha, beta_1..beta_n
-      T t = R::fma(R::from(s_gc[g] * ih), rel_apply<DIM, T>(a, i, 0, M + nb), M[i]);
-      for (int d = 0; d < DIM; ++d) t = R::fma(mih, rel_apply<DIM, T>(a, i, 1 + d, M + (2 + d) * nb), t);
-      T* dst = sb + (size_t)r * N + g * nb + i;
-      *dst = R::add(*dst, t);
-    }
-  }
-  __syncthreads();
-  if constexpr (ADJ) {   // solve with A^T
-    for (int id = tid; id < N * N; id += blockDim.x) {
-      const int i = id / N, j = id % N;
-      if (i < j) {
-        const T t = sA[id];
-        sA[id] = sA[j * N + i];
-        sA[j * N + i] = t;
-      }
-    }
-    __syncthreads();
-  }
-
-  // ---------------- phase 3: solve ----------------
-  // MIXED: binary32 LU of the equilibrated matrix D A D (D = |diag A|^-1/2),
-  // then refinement x += D (D A D)^-1 D (b - A x) with a float-float residual.
-  // binary64: direct LU (a binary32 factor + binary64 refinement was measured
-  // slower on this part, whose binary64 pipe is the bottleneck either way).
-  const bool pivoting = extra || ng > 1;
-  if constexpr (MIXED) {
-    float* sAL = reinterpret_cast<float*>(sm + a.off_al);   // N*N     equilibrated binary32 LU
-    float* sEq = reinterpret_cast<float*>(sm + a.off_eq);   // N       equilibration scales
-    int* sPerm = reinterpret_cast<int*>(sm + a.off_perm);   // N       row interchanges
-    float* sZ = reinterpret_cast<float*>(sm + a.off_z);     // nrhs*N  correction (binary32)
-    T* sX = reinterpret_cast<T*>(sm + a.off_x);             // nrhs*N  iterate
-    for (int i = tid; i < N; i += blockDim.x) {
-      const float d = fabsf(R::hi(sA[i * N + i]));
-      sEq[i] = (d > 0.f && isfinite(d)) ? rsqrtf(d) : 1.f;
-    }
-    for (int id = tid; id < nrhs * N; id += blockDim.x) sX[id] = R::zero();
-    __syncthreads();
-    for (int id = tid; id < N * N; id += blockDim.x) sAL[id] = R::hi(sA[id]) * sEq[id / N] * sEq[id % N];
-    __syncthreads();
-    // binary32 LU of D A D (row interchanges on whole rows, multipliers kept
-    // below the diagonal, reciprocal pivots in sRD)
-    for (int k = 0; k < N; ++k) {
-      if (pivoting) {
-        if (warp == 0) {
-          float best = -1.f;
-          int bi = k;
-          for (int i = k + lane; i < N; i += 32) {
-            const float val = fabsf(sAL[i * N + k]);
-            if (val > best) {
-              best = val;
-              bi = i;
-            }
-          }
-          for (int o = 16; o > 0; o >>= 1) {
-            const float ob = __shfl_down_sync(0xffffffffu, best, o);
-            const int oi = __shfl_down_sync(0xffffffffu, bi, o);
-            if (ob > best || (ob == best && oi < bi)) {
-              best = ob;
-              bi = oi;
-            }
-          }
-          if (lane == 0) s_piv = bi;
-        }
-        __syncthreads();
-        const int pr = s_piv;
-        if (pr != k)
-          for (int j = tid; j < N; j += blockDim.x) {
-            const float t = sAL[k * N + j];
-            sAL[k * N + j] = sAL[pr * N + j];
-            sAL[pr * N + j] = t;
-          }
-        if (tid == 0) sPerm[k] = pr;
-        __syncthreads();
-      } else if (tid == 0) {
-        sPerm[k] = k;
-      }
-      float piv = sAL[k * N + k];
-      if (!(fabsf(piv) > 0.f) || !isfinite(piv)) {
-        if (tid == 0 && rank == 0) flag_error(a, TP_ERR_SINGULAR, tent);
-        piv = 1.f;
-      }
-      const float rp = 1.f / piv;
-      const int rem = N - k - 1;
-      for (int id = tid; id < rem * rem; id += blockDim.x) {
-        const int i = k + 1 + id / rem, j = k + 1 + id % rem;
-        sAL[i * N + j] = fmaf(-sAL[i * N + k] * rp, sAL[k * N + j], sAL[i * N + j]);
-      }
-      __syncthreads();
-      for (int i = k + 1 + tid; i < N; i += blockDim.x) sAL[i * N + k] *= rp;
-      if (tid == 0) sRD[k] = (double)rp;
-      __syncthreads();
-    }
-    // refinement: r = b - A x (float-float), z = (D A D)^-1 D r, x += D z
-    float prev = 3.4e38f;
-    const int maxit = kMaxRefine;
-    if (tid == 0) s_conv = 0;
-    for (int it = 0; it < maxit; ++it) {
-      // r = b - A x, each row split over 8 lanes of one warp
-      for (int base8 = 0; base8 < nrhs * N * 8; base8 += blockDim.x) {
-        const int id = base8 + tid, item = id >> 3, sub = id & 7;
-        T t = R::zero();
-        if (item < nrhs * N) {
-          const int r = item / N, i = item % N;
-          const T* xr = sX + (size_t)r * N;
-          for (int j = sub; j < N; j += 8) t = R::fms(t, sA[i * N + j], xr[j]);
-        }
-        for (int o = 4; o > 0; o >>= 1) {
-          T u;
-          if constexpr (MIXED) {
-            u.hi = __shfl_xor_sync(0xffffffffu, t.hi, o);
-            u.lo = __shfl_xor_sync(0xffffffffu, t.lo, o);
-          } else {
-            u = __shfl_xor_sync(0xffffffffu, t, o);
-          }
-          t = R::add(t, u);
-        }
-        if (sub == 0 && item < nrhs * N) sZ[item] = sEq[item % N] * R::hi(R::add(sb[item], t));
-      }
-      __syncthreads();
-      if (warp == 0) {
-        for (int r = 0; r < nrhs; ++r) {
-          float* z = sZ + (size_t)r * N;
-          if (lane == 0)   // row interchanges in factorisation order (L is stored permuted)
-            for (int k = 0; k < N; ++k) {
-              const int pr = sPerm[k];
-              if (pr != k) {
-                const float t = z[k];
-                z[k] = z[pr];
-                z[pr] = t;
-              }
-            }
-          __syncwarp();
-          for (int k = 0; k < N; ++k) {   // L (unit lower)
-            const float zk = z[k];
-            for (int i = k + 1 + lane; i < N; i += 32) z[i] = fmaf(-sAL[i * N + k], zk, z[i]);
-            __syncwarp();
-          }
-          for (int k = N - 1; k >= 0; --k) {   // U
-            if (lane == 0) z[k] = z[k] * (float)sRD[k];
-            __syncwarp();
-            const float zk = z[k];
-            for (int i = lane; i < k; i += 32) z[i] = fmaf(-sAL[i * N + k], zk, z[i]);
-            __syncwarp();
-          }
-        }
-      }
-      __syncthreads();
-      float dmax = 0.f, xmax = 0.f;
-      for (int id = tid; id < nrhs * N; id += blockDim.x) {
-        const float dx = sEq[id % N] * sZ[id];
-        sX[id] = R::addf(sX[id], dx);
-        dmax = fmaxf(dmax, fabsf(dx));
-        xmax = fmaxf(xmax, fabsf(R::hi(sX[id])));
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
-        xmax = fmaxf(xmax, __shfl_xor_sync(0xffffffffu, xmax, o));
-      }
-      if (lane == 0) {
-        s_red[0][warp] = dmax;
-        s_red[1][warp] = xmax;
-      }
-      __syncthreads();
-      if (tid == 0) {
-        float dm = 0.f, xm = 0.f;
-        for (int w = 0; w < kThreads / 32; ++w) {
-          dm = fmaxf(dm, s_red[0][w]);
-          xm = fmaxf(xm, s_red[1][w]);
-        }
-        // stop once the correction is at the float-float resolution, or once it
-        // stops shrinking below 1e-10 of the solution (the float-float residual
-        // then limits the accuracy); a correction above 1e-8 of the solution
-        // after kMaxRefine steps is reported
-        const float tiny = 4e-15f, floor_ = 1e-10f;
-        const bool done = (dm <= tiny * xm) || (it >= 2 && dm > 0.5f * prev && dm <= floor_ * xm);
-        s_stop = done ? 1 : 0;
-        if (done) s_conv = 1;
-        if (!done && it == maxit - 1 && dm > 1e-8f * xm && rank == 0) flag_error(a, TP_ERR_NOCONV, tent);
-        s_red[0][0] = dm;
-      }
-      __syncthreads();
-      prev = s_red[0][0];
-      const int stop = s_stop;
-      __syncthreads();
-      if (stop) break;
-    }
-    for (int id = tid; id < nrhs * N; id += blockDim.x) sb[id] = sX[id];
-    __syncthreads();
-  }
-  if constexpr (!MIXED) {
-    {
-      __syncthreads();
-    // LU (no pivoting for single-material interior tents: A is SPD), forward elimination of b alongside
-      for (int k = 0; k < N; ++k) {
-        if (pivoting) {
-          if (warp == 0) {
-            // |a_ik| compared through the bit patterns (non-negative doubles order as integers)
-            unsigned long long best = 0ull;
-            int bi = k;
-            for (int i = k + lane; i < N; i += 32) {
-              const unsigned long long bits = (unsigned long long)__double_as_longlong(fabs(sA[i * N + k]));
-              if (bits > best || (bits == best && i < bi)) {
-                best = bits;
-                bi = i;
-              }
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-              const unsigned long long ob = __shfl_down_sync(0xffffffffu, best, o);
-              const int oi = __shfl_down_sync(0xffffffffu, bi, o);
-              if (ob > best || (ob == best && oi < bi)) {
-                best = ob;
-                bi = oi;
-              }
-            }
-            if (lane == 0) s_piv = bi;
-          }
-          __syncthreads();
-          const int pr = s_piv;
-          if (pr != k) {
-            for (int j = tid; j < N; j += blockDim.x) {
-              const double t = sA[k * N + j];
-              sA[k * N + j] = sA[pr * N + j];
-              sA[pr * N + j] = t;
-            }
-            for (int r = tid; r < nrhs; r += blockDim.x) {
-              const double t = sb[r * N + k];
-              sb[r * N + k] = sb[r * N + pr];
-              sb[r * N + pr] = t;
-            }
-          }
-          __syncthreads();
-        }
-        if (tid == 0) {
-          double piv = sA[k * N + k];
-          if (!(fabs(piv) > 0.0) || !isfinite(piv)) {
-            if (rank == 0) flag_error(a, TP_ERR_SINGULAR, tent);
-            piv = 1.0;
-          }
-          sRD[k] = recip(piv);
-        }
-        __syncthreads();
-        const double rp = sRD[k];
-        const int rem = N - k - 1;
-        for (int i = k + 1 + tid; i < N; i += blockDim.x) sA[i * N + k] *= rp;   // multipliers
-        __syncthreads();
-        for (int id = tid; id < rem * (rem + nrhs); id += blockDim.x) {
-          const int i = k + 1 + id / (rem + nrhs), jj = id % (rem + nrhs);
-          const double l = sA[i * N + k];
-          if (jj < rem) {
-            const int j = k + 1 + jj;
-            sA[i * N + j] = fma(-l, sA[k * N + j], sA[i * N + j]);
-          } else {
-            const int r = jj - rem;
-            sb[r * N + i] = fma(-l, sb[r * N + k], sb[r * N + i]);
-          }
-        }
-        __syncthreads();
-      }
-      for (int k = N - 1; k >= 0; --k) {
-        for (int r = tid; r < nrhs; r += blockDim.x) sb[r * N + k] *= sRD[k];
-        __syncthreads();
-        for (int id = tid; id < k * nrhs; id += blockDim.x) {
-          const int r = id / k, i = id % k;
-          sb[r * N + i] = fma(-sA[i * N + k], sb[r * N + k], sb[r * N + i]);
-        }
-        __syncthreads();
-      }
-  
-    }
-  }
-
-  // ---------------- phase 4: outflow at this CTA's top points (adjoint: bottom points) ----------------
-  // coefficient vectors of U_h, v_h, sigma_h in terms of U-values, per material: y = D^T x_g
-  for (int id = tid; id < ng * nmom; id += blockDim.x) {
-    const int g = id / nmom, rest = id % nmom;
-    const int r = rest / (C * nb), rem = rest % (C * nb), cc = rem / nb, kk = rem % nb;
-    const T* xg = sb + (size_t)r * N + g * nb;
-    T t;
-    if (cc == 0) t = xg[kk];
-    else t = R::mul(R::from(cc == 1 ? s_gc[g] * ih : -ih), relT_apply<DIM, T>(a, kk, cc - 1, xg));
-    sY[id] = t;
-  }
-  for (int base = q0; base < q1; base += 2 * CH) {
-    const int nq = min(2 * CH, q1 - base);
-    if (tid < nq) {
-      const int qg = base + tid, k = qg / Q, q = qg % Q;
-      const double cg = s_gc[s_grp[k]];
-      double x[DIM], tt = 0.0;
-      for (int d = 0; d < DIM; ++d) x[d] = 0.0;
-      for (int i = 0; i < NV; ++i) {
-        const double l = __ldg(a.bary + q * NV + i);
-        for (int d = 0; d < DIM; ++d) x[d] = fma(l, s_X[k][i][d], x[d]);
-        tt = fma(l, ADJ ? s_tb[k][i] : s_tt[k][i], tt);
-      }
-      T xh[DIM];
-      for (int d = 0; d < DIM; ++d) xh[d] = R::from((x[d] - s_xv[d]) * ih);
-      const T th = R::from(cg * (tt - tc) * ih);
-      eval_uvalues<DIM, T, false>(a, th, xh, sM + tid * a.mono_stride, R::one(), sU + (size_t)tid * nb);
-    }
-    __syncthreads();
-    if constexpr (!ADJ) {
-      for (int id = tid; id < nq * nrhs * C; id += blockDim.x) {
-        const int ql = id / (nrhs * C), rc = id % (nrhs * C), r = rc / C, cc = rc % C;
-        const int qg = base + ql, k = qg / Q, q = qg % Q;
-        const T* u = sU + (size_t)ql * nb;
-        const T* y = sY + (size_t)s_grp[k] * nmom + ((size_t)r * C + cc) * nb;
-        T t = R::zero();
-        for (int j = 0; j < nb; ++j) t = R::fma(y[j], u[j], t);
-        a.front[(((int64_t)r * a.ne + s_el[k]) * Q + q) * C + cc] = R::to(t);
-      }
-    } else {
-      // lambda_bot = w (s0, c^-2 s_t - g_b.s, s_m - g_b,m s_t)
-      for (int id = tid; id < nq * nrhs; id += blockDim.x) {
-        const int ql = id / nrhs, r = id % nrhs;
-        const int qg = base + ql, k = qg / Q, q = qg % Q;
-        const T* u = sU + (size_t)ql * nb;
-        double sv[C];
-        for (int cc = 0; cc < C; ++cc) {
-          const T* y = sY + (size_t)s_grp[k] * nmom + ((size_t)r * C + cc) * nb;
-          T t = R::zero();
-          for (int j = 0; j < nb; ++j) t = R::fma(y[j], u[j], t);
-          sv[cc] = R::to(t);
-        }
-        const double cg = s_gc[s_grp[k]];
-        const double sq = __ldg(a.sqw + q) * s_sdet[k];
-        const double w = sq * sq;
-        double gs = 0.0;
-        for (int d = 0; d < DIM; ++d) gs = fma(s_gb[k][d], sv[2 + d], gs);
-        double* f = a.front + (((int64_t)r * a.ne + s_el[k]) * Q + q) * C;
-        f[0] = w * sv[0];
-        f[1] = w * (sv[1] / (cg * cg) - gs);
-        for (int d = 0; d < DIM; ++d) f[2 + d] = w * (sv[2 + d] - s_gb[k][d] * sv[1]);
-      }
-    }
-    __syncthreads();
-  }
-  if (tid == 0 && rank == 0) a.tau[v] = ADJ ? s_tbot : s_ttop;
-}
+using namespace tp;
 
 // energy flux through the front, per (rhs, element) partial sums
 template <int DIM>
@@ -1331,6 +140,12 @@ struct tp_ctx {
   cudaStream_t last_stream = nullptr;
   int n_sm = 152, max_cs = 1;
   bool mixed = false;
+  // persistent dataflow sweep
+  bool persistent = true;
+  int persist_clusters = 0;
+  int* d_queue = nullptr;
+  int* d_done = nullptr;
+  int* d_tent_vert = nullptr;
   std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
   int device = 0;
 };
@@ -1348,34 +163,21 @@ constexpr size_t kMaxDynSmem = 200 * 1024;   // cap of the shared-memory plan
 constexpr size_t kTwoPerSmSmem = 95 * 1024;  // plan that leaves room for two CTAs per SM
 
 // the attribute is set to the plan's cap, so contexts of any size can share the kernel
-template <int DIM>
-int set_smem_attr() {
-  TP_CUDA_OK(cudaFuncSetAttribute(k_layer<DIM, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)kMaxDynSmem));
-  TP_CUDA_OK(cudaFuncSetAttribute(k_layer<DIM, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)kMaxDynSmem));
-  TP_CUDA_OK(cudaFuncSetAttribute(k_layer<DIM, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)kMaxDynSmem));
+int set_smem_attr(int dim) {
+  cudaError_t e = dim == 1 ? tp::layer_attrs_d1(kMaxDynSmem)
+                : dim == 2 ? tp::layer_attrs_d2(kMaxDynSmem)
+                           : tp::layer_attrs_d3(kMaxDynSmem);
+  TP_CUDA_OK(e);
   return TP_OK;
 }
 
-template <int DIM>
-cudaError_t launch_cluster(tp_ctx* ctx, int nt, int cs, int t0, cudaStream_t st, bool adj) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(nt * cs));
-  cfg.blockDim = dim3(kThreads);
-  cfg.dynamicSmemBytes = ctx->smem_bytes;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = (unsigned)cs;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  if (adj) return cudaLaunchKernelEx(&cfg, k_layer<DIM, false, true>, ctx->args_adj, t0);
-  if (ctx->mixed) return cudaLaunchKernelEx(&cfg, k_layer<DIM, true, false>, ctx->args, t0);
-  return cudaLaunchKernelEx(&cfg, k_layer<DIM, false, false>, ctx->args, t0);
+cudaError_t launch_layer(tp_ctx* ctx, const KArgs& a, int n_cluster, int cs, int t0, cudaStream_t st, int mode,
+                         bool persistent) {
+  switch (ctx->dim) {
+    case 1: return tp::launch_layer_d1(a, n_cluster, cs, t0, ctx->smem_bytes, st, mode, persistent);
+    case 2: return tp::launch_layer_d2(a, n_cluster, cs, t0, ctx->smem_bytes, st, mode, persistent);
+    default: return tp::launch_layer_d3(a, n_cluster, cs, t0, ctx->smem_bytes, st, mode, persistent);
+  }
 }
 
 // cluster size for a level of nt tents: a power of two <= max_cs with
@@ -1391,12 +193,8 @@ int launch_level(tp_ctx* ctx, int32_t L, cudaStream_t st, bool adj = false) {
   if (t1 <= t0) return TP_OK;
   const int nt = (int)(t1 - t0);
   const int cs = level_cluster_size(ctx, nt);
-  cudaError_t e;
-  switch (ctx->dim) {
-    case 1: e = launch_cluster<1>(ctx, nt, cs, (int)t0, st, adj); break;
-    case 2: e = launch_cluster<2>(ctx, nt, cs, (int)t0, st, adj); break;
-    default: e = launch_cluster<3>(ctx, nt, cs, (int)t0, st, adj); break;
-  }
+  const int mode = adj ? 2 : (ctx->mixed ? 1 : 0);
+  cudaError_t e = launch_layer(ctx, adj ? ctx->args_adj : ctx->args, nt, cs, (int)t0, st, mode, false);
   TP_CUDA_OK(e);
   TP_CUDA_OK(cudaGetLastError());
   return TP_OK;
@@ -1435,6 +233,7 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
   ctx->nrhs = prm->nrhs;
   ctx->alpha = prm->alpha;
   ctx->mixed = (prm->precision == TP_MIXED);
+  ctx->persistent = (prm->schedule == TP_SCHED_DATAFLOW);
   ctx->nv = T.nv;
   ctx->ne = T.ne;
   ctx->rule = tp::simplex_rule(n, basis->p + 1);
@@ -1522,12 +321,34 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
   ctx->n_bnd = gdoff[ctx->ntents];
   gdoff.pop_back();
 
+  // dependencies of the dataflow sweep: tent (v, L) waits until every vertex w
+  // of {v} and its neighbours has completed its tents of level < L
+  std::vector<int32_t> dep_ptr(ctx->ntents + 1, 0), dep_vert, dep_need;
+  {
+    std::vector<std::vector<int32_t>> lev_at(T.nv);
+    for (int64_t it = 0; it < ctx->ntents; ++it) lev_at[tents->vert[it]].push_back(tents->level[it]);
+    for (int64_t it = 0; it < ctx->ntents; ++it) {
+      const int v = tents->vert[it], L = tents->level[it];
+      auto add = [&](int w) {
+        const auto& lv = lev_at[w];
+        const int need = (int)(std::lower_bound(lv.begin(), lv.end(), L) - lv.begin());
+        if (need > 0) {
+          dep_vert.push_back(w);
+          dep_need.push_back(need);
+        }
+      };
+      add(v);
+      for (int e = T.nbr_ptr[v]; e < T.nbr_ptr[v + 1]; ++e) add(T.nbr[e]);
+      dep_ptr[it + 1] = (int32_t)dep_vert.size();
+    }
+  }
+
   // device uploads
   int rc = TP_OK;
   KArgs& a = ctx->args;
   double *dX, *dc, *dnrm, *dbary, *dw, *dsqw, *dttop, *dh, *dspc;
   int *del, *dsp, *dse, *dvp, *dvf, *dfv, *dtv, *dspp, *dspm, *dpar, *dvar, *drp, *drs, *dtp, *dtd;
-  int *dfe, *dip, *div, *dikp, *dikm;
+  int *dfe, *dip, *div, *dikp, *dikm, *ddp, *ddv, *ddn;
   double* dinrm;
   double *drf, *dtf;
   float2* dcdd;
@@ -1554,6 +375,8 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
       (rc = ctx_upload(ctx, &dfe, T.facet_elem)) || (rc = ctx_upload(ctx, &dip, T.ifac_ptr)) ||
       (rc = ctx_upload(ctx, &div, T.ifac_vert)) || (rc = ctx_upload(ctx, &dinrm, T.ifac_nrm)) ||
       (rc = ctx_upload(ctx, &dikp, T.ifac_kp)) || (rc = ctx_upload(ctx, &dikm, T.ifac_km)) ||
+      (rc = ctx_upload(ctx, &ddp, dep_ptr)) || (rc = ctx_upload(ctx, &ddv, dep_vert)) ||
+      (rc = ctx_upload(ctx, &ddn, dep_need)) ||
       (rc = ctx_upload(ctx, &dw, ctx->rule.w)) || (rc = ctx_upload(ctx, &dsqw, sqw)) ||
       (rc = ctx_upload(ctx, &dtv, tv)) || (rc = ctx_upload(ctx, &dttop, ttop)) ||
       (rc = ctx_upload(ctx, &dtbot, tbot)) ||
@@ -1582,6 +405,11 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
     return fail(TP_ERR_OOM);
   }
   ctx->T_final = tents->T;
+  if (cudaMalloc(&ctx->d_queue, sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&ctx->d_done, T.nv * sizeof(int)) != cudaSuccess) {
+    tp::set_error("tp_create: device allocation failed");
+    return fail(TP_ERR_OOM);
+  }
   ctx->energy_blocks = (int)std::min<int64_t>(1024, (T.ne + kThreads - 1) / kThreads);
   if (cudaMalloc(&ctx->d_partial, (size_t)ctx->nrhs * ctx->energy_blocks * sizeof(double)) != cudaSuccess) {
     tp::set_error("tp_create: device allocation failed");
@@ -1608,6 +436,9 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
   a.ifac_nrm = dinrm;
   a.ifac_kp = dikp;
   a.ifac_km = dikm;
+  a.dep_ptr = ddp;
+  a.dep_vert = ddv;
+  a.dep_need = ddn;
   a.X = dX;
   a.elems = del;
   a.cK = dc;
@@ -1640,6 +471,9 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
   a.rel_facf = drff;
   a.relT_facf = dtff;
   a.tau = ctx->d_tau;
+  a.queue = ctx->d_queue;
+  a.done = ctx->d_done;
+  a.tent_end = (int)ctx->ntents;
   a.front = ctx->d_front;
   a.gD = nullptr;
   a.status = ctx->d_status;
@@ -1708,11 +542,7 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
   ctx->args_adj.tau = ctx->d_tau_adj;
   ctx->args_adj.gD = nullptr;
   ctx->smem_bytes = bytes;
-  switch (n) {
-    case 1: rc = set_smem_attr<1>(); break;
-    case 2: rc = set_smem_attr<2>(); break;
-    default: rc = set_smem_attr<3>(); break;
-  }
+  rc = set_smem_attr(n);
   if (rc) return fail(rc);
   {
     int nsm = 0;
@@ -1722,6 +552,19 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
     int cs = 1;
     while (cs < 8 && avg_pts / (2.0 * cs) >= CH) cs *= 2;
     ctx->max_cs = cs;
+  }
+  if (ctx->persistent) {
+    int nclu = 0;
+    const int mode = ctx->mixed ? 1 : 0;
+    cudaError_t e = n == 1 ? tp::max_clusters_d1(ctx->max_cs, ctx->smem_bytes, mode, &nclu)
+                  : n == 2 ? tp::max_clusters_d2(ctx->max_cs, ctx->smem_bytes, mode, &nclu)
+                           : tp::max_clusters_d3(ctx->max_cs, ctx->smem_bytes, mode, &nclu);
+    if (e != cudaSuccess || nclu < 1) {
+      cudaGetLastError();
+      ctx->persistent = false;   // fall back to one launch per level
+    } else {
+      ctx->persist_clusters = nclu;
+    }
   }
   if (cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
     tp::set_error("tp_create: stream creation failed");
@@ -1821,6 +664,15 @@ extern "C" int tp_solve_layer(tp_ctx* ctx, int32_t level, void* stream) {
   return launch_level(ctx, level, (cudaStream_t)stream);
 }
 
+namespace {
+__global__ void k_sweep_setup(const int* vert, int t_begin, int* done, int* queue) {
+  // completed tents before the range, per vertex; queue head at the range start
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < t_begin; t += gridDim.x * blockDim.x)
+    atomicAdd(done + vert[t], 1);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *queue = t_begin;
+}
+}  // namespace
+
 extern "C" int tp_advance(tp_ctx* ctx, int32_t level_begin, int32_t level_end, void* stream) {
   if (!ctx || level_begin < 1 || level_end > ctx->n_levels + 1 || level_end < level_begin) {
     tp::set_error("tp_advance: level range out of bounds");
@@ -1833,7 +685,25 @@ extern "C" int tp_advance(tp_ctx* ctx, int32_t level_begin, int32_t level_end, v
     cudaGraph_t g = nullptr;
     TP_CUDA_OK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
     int rc = TP_OK;
-    for (int32_t L = level_begin; L < level_end && rc == TP_OK; ++L) rc = launch_level(ctx, L, ctx->cap_stream);
+    if (ctx->persistent) {
+      const int t_begin = (int)ctx->level_ptr[level_begin - 1], t_end = (int)ctx->level_ptr[level_end - 1];
+      KArgs a = ctx->args;
+      a.tent_end = t_end;
+      cudaError_t e = cudaMemsetAsync(ctx->d_done, 0, ctx->nv * sizeof(int), ctx->cap_stream);
+      if (e == cudaSuccess) {
+        k_sweep_setup<<<std::max(1, std::min(1024, (t_begin + 255) / 256)), 256, 0, ctx->cap_stream>>>(
+            ctx->args.tent_v, t_begin, ctx->d_done, ctx->d_queue);
+        e = cudaGetLastError();
+      }
+      if (e == cudaSuccess)
+        e = launch_layer(ctx, a, ctx->persist_clusters, ctx->max_cs, 0, ctx->cap_stream, ctx->mixed ? 1 : 0, true);
+      if (e != cudaSuccess) {
+        tp::set_error(std::string("tp_advance: CUDA error ") + cudaGetErrorString(e));
+        rc = TP_ERR_CUDA;
+      }
+    } else {
+      for (int32_t L = level_begin; L < level_end && rc == TP_OK; ++L) rc = launch_level(ctx, L, ctx->cap_stream);
+    }
     cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &g);
     if (rc != TP_OK) {
       if (g) cudaGraphDestroy(g);
@@ -1949,6 +819,8 @@ extern "C" void tp_destroy_ctx(tp_ctx* ctx) {
   cudaFree(ctx->d_gD);
   cudaFree(ctx->d_partial);
   cudaFree(ctx->d_adj);
+  cudaFree(ctx->d_queue);
+  cudaFree(ctx->d_done);
   cudaFree(ctx->d_tau_adj);
   if (ctx->adj_graph) cudaGraphExecDestroy(ctx->adj_graph);
   cudaFree(ctx->d_status);

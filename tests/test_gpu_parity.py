@@ -24,12 +24,12 @@ def _rel(a, b):
 
 
 def _gpu_run(mesh, p, T, kappa, init, dirichlet, nrhs_inits=None, alpha=0.5, levels=None,
-             layerwise=False, precision="fp64"):
+             layerwise=False, precision="fp64", schedule="dataflow"):
     import torch
     import paper_1907_02367_gb300 as pkg
     inits = nrhs_inits or [init]
     s = pkg.Solver(mesh.coords, mesh.elems, mesh.c, p, T, kappa, alpha=alpha, nrhs=len(inits),
-                   precision=precision)
+                   precision=precision, schedule=schedule)
     xq, wq = s.front_points()
     f0 = np.stack([np.asarray(f(xq)) for f in inits])
     front0 = torch.tensor(f0, dtype=torch.float64, device="cuda").contiguous()
@@ -126,11 +126,31 @@ def test_front_points_match_oracle_layout(cuda_device):
 
 
 def test_layerwise_equals_graph(cuda_device):
+    """tp_solve_layer level by level equals the per-level graph bit for bit."""
     w = inputs.workload("small2d")
     m = w.mesh
-    _, a, ta, _ = _gpu_run(m, w.p, w.T, w.kappa, w.init, None)
+    _, a, ta, _ = _gpu_run(m, w.p, w.T, w.kappa, w.init, None, schedule="levels")
     _, b, tb, _ = _gpu_run(m, w.p, w.T, w.kappa, w.init, None, layerwise=True)
     assert np.array_equal(a, b) and np.array_equal(ta, tb)
+
+
+@pytest.mark.parametrize("name,precision", [("small2d", "fp64"), ("standing2d", "fp64"),
+                                            ("standing3d_small", "fp64"), ("inclusion_small", "fp64"),
+                                            ("standing2d", "mixed")])
+def test_dataflow_matches_levels(cuda_device, name, precision):
+    """The persistent dataflow sweep (clusters of fixed size pulling tents as
+    their inputs complete) gives the per-level result up to rounding (the
+    slicing of a tent over its cluster differs), identical front times, and
+    repeated sweeps are reproducible."""
+    w = inputs.workload(name)
+    m = w.mesh
+    _, a, ta, sa = _gpu_run(m, w.p, w.T, w.kappa, w.init, None, schedule="levels", precision=precision)
+    _, b, tb, sb = _gpu_run(m, w.p, w.T, w.kappa, w.init, None, schedule="dataflow", precision=precision)
+    _, c, tc, sc = _gpu_run(m, w.p, w.T, w.kappa, w.init, None, schedule="dataflow", precision=precision)
+    assert sa == sb == sc == (0, 0)
+    assert np.array_equal(ta, tb) and np.array_equal(tb, tc)
+    assert _rel(b, a) <= 1e-13
+    assert np.array_equal(b, c)
 
 
 def test_partial_sweep_and_energy_on_curved_front(cuda_device):
