@@ -142,6 +142,15 @@ int tp_solve_layer(tp_ctx* ctx, int32_t level, void* stream);
 /* Levels [level_begin, level_end) (1-based, end exclusive) as one CUDA graph
  * (captured on first use for that range, then replayed). */
 int tp_advance(tp_ctx* ctx, int32_t level_begin, int32_t level_end, void* stream);
+/* Autotuner of the sweep schedule (the paper has no counterpart): times a
+ * full forward sweep of this context with one launch per level and with the
+ * dataflow schedule at cluster sizes 1, 2, 4 and 8 (state saved and
+ * restored), keeps the fastest for later tp_advance calls and caches it for
+ * this process under (dim, p, nrhs, precision, rounded mean vertex-star size),
+ * so contexts created later with the same key start from it.  *chosen = 0 for
+ * one launch per level, else the cluster size; *best_ms = its sweep time.
+ * Allocates a scratch copy of the state; synchronises `stream`. */
+int tp_autotune(tp_ctx* ctx, void* stream, int32_t* chosen, double* best_ms);
 /* Energy flux through the current front (Section 6.5 energy generalised to
  * a front t = tau(x)):  E_r = 1/2 sum_K sum_q w_q (c_K^-2 v^2 + |sigma|^2
  * - 2 v sigma.grad tau_K) for every rhs r; equals the paper's E on a flat

@@ -176,6 +176,15 @@ class Solver:
         B.check(B.load().tp_adjoint(self.handle, B.tensor_ptr(lam_T), B.tensor_ptr(out), B.stream_ptr(stream)))
         return out
 
+    def autotune(self, stream=None):
+        """tp_autotune: pick the sweep schedule (one launch per level, or the
+        dataflow sweep with clusters of 1/2/4/8 CTAs) by timing full sweeps.
+        Returns (chosen, ms): chosen = 0 for per-level launches, else the
+        cluster size."""
+        c, ms = ct.c_int32(), ct.c_double()
+        B.check(B.load().tp_autotune(self.handle, B.stream_ptr(stream), ct.byref(c), ct.byref(ms)))
+        return int(c.value), float(ms.value)
+
     def energy(self, out=None, stream=None):
         import torch
         if out is None:

@@ -23,7 +23,7 @@ EXPORTED = [
     "tp_last_error", "tp_pitch_mesh", "tp_tents_info", "tp_tents_export", "tp_destroy_tents",
     "tp_build_basis", "tp_basis_info", "tp_basis_export", "tp_destroy_basis", "tp_create",
     "tp_ctx_info", "tp_front_points", "tp_boundary_points", "tp_set_state", "tp_solve_layer",
-    "tp_advance", "tp_adjoint", "tp_energy", "tp_get_state", "tp_sync_status", "tp_destroy_ctx",
+    "tp_advance", "tp_adjoint", "tp_autotune", "tp_energy", "tp_get_state", "tp_sync_status", "tp_destroy_ctx",
     "tp_front_energy_noalloc",
 ]
 
@@ -77,6 +77,7 @@ def load(path: str = LIB_PATH):
         "tp_advance": (ct.c_int, [vp, i32, i32, vp]),
         "tp_energy": (ct.c_int, [vp, vp, vp]),
         "tp_adjoint": (ct.c_int, [vp, vp, vp, vp]),
+        "tp_autotune": (ct.c_int, [vp, vp, P(i32), P(d)]),
         "tp_get_state": (ct.c_int, [vp, vp, vp, vp]),
         "tp_sync_status": (ct.c_int, [vp, P(i32), P(i64)]),
         "tp_destroy_ctx": (None, [vp]),

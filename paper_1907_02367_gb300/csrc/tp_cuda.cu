@@ -143,6 +143,8 @@ struct tp_ctx {
   // persistent dataflow sweep
   bool persistent = true;
   int persist_clusters = 0;
+  int persist_cs = 1;
+  int tune_key[5] = {0, 0, 0, 0, 0};   // (dim, p, nrhs, mixed, patch bucket) of the autotuner cache
   int* d_queue = nullptr;
   int* d_done = nullptr;
   int* d_tent_vert = nullptr;
@@ -178,6 +180,35 @@ cudaError_t launch_layer(tp_ctx* ctx, const KArgs& a, int n_cluster, int cs, int
     case 2: return tp::launch_layer_d2(a, n_cluster, cs, t0, ctx->smem_bytes, st, mode, persistent);
     default: return tp::launch_layer_d3(a, n_cluster, cs, t0, ctx->smem_bytes, st, mode, persistent);
   }
+}
+
+// resident clusters of the persistent kernel for cluster size cs
+int set_persist_cs(tp_ctx* ctx, int cs) {
+  int nclu = 0;
+  const int mode = ctx->mixed ? 1 : 0;
+  cudaError_t e = ctx->dim == 1 ? tp::max_clusters_d1(cs, ctx->smem_bytes, mode, &nclu)
+                : ctx->dim == 2 ? tp::max_clusters_d2(cs, ctx->smem_bytes, mode, &nclu)
+                                : tp::max_clusters_d3(cs, ctx->smem_bytes, mode, &nclu);
+  if (e != cudaSuccess || nclu < 1) {
+    cudaGetLastError();
+    return TP_ERR_UNSUPPORTED;
+  }
+  ctx->persist_cs = cs;
+  ctx->persist_clusters = nclu;
+  return TP_OK;
+}
+
+// autotuner results for this process: (dim, p, nrhs, mixed, patch bucket) -> (cs, dataflow?)
+std::mutex g_tune_mu;
+std::map<std::vector<int>, std::pair<int, bool>> g_tuned;
+
+bool tuned_lookup(const int* key, int* cs, bool* dataflow) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tuned.find(std::vector<int>(key, key + 5));
+  if (it == g_tuned.end()) return false;
+  *cs = it->second.first;
+  *dataflow = it->second.second;
+  return true;
 }
 
 // cluster size for a level of nt tents: a power of two <= max_cs with
@@ -553,18 +584,16 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
     while (cs < 8 && avg_pts / (2.0 * cs) >= CH) cs *= 2;
     ctx->max_cs = cs;
   }
+  {
+    const double avg_star = (double)T.star_el.size() / (double)T.nv;
+    const int key[5] = {n, ctx->p, ctx->nrhs, ctx->mixed ? 1 : 0, (int)std::lround(avg_star)};
+    std::copy(key, key + 5, ctx->tune_key);
+  }
   if (ctx->persistent) {
-    int nclu = 0;
-    const int mode = ctx->mixed ? 1 : 0;
-    cudaError_t e = n == 1 ? tp::max_clusters_d1(ctx->max_cs, ctx->smem_bytes, mode, &nclu)
-                  : n == 2 ? tp::max_clusters_d2(ctx->max_cs, ctx->smem_bytes, mode, &nclu)
-                           : tp::max_clusters_d3(ctx->max_cs, ctx->smem_bytes, mode, &nclu);
-    if (e != cudaSuccess || nclu < 1) {
-      cudaGetLastError();
-      ctx->persistent = false;   // fall back to one launch per level
-    } else {
-      ctx->persist_clusters = nclu;
-    }
+    int cs = ctx->max_cs;
+    bool sched_dataflow = true;
+    if (tuned_lookup(ctx->tune_key, &cs, &sched_dataflow)) ctx->persistent = sched_dataflow;
+    if (ctx->persistent && set_persist_cs(ctx, cs) != TP_OK) ctx->persistent = false;   // one launch per level
   }
   if (cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
     tp::set_error("tp_create: stream creation failed");
@@ -696,7 +725,7 @@ extern "C" int tp_advance(tp_ctx* ctx, int32_t level_begin, int32_t level_end, v
         e = cudaGetLastError();
       }
       if (e == cudaSuccess)
-        e = launch_layer(ctx, a, ctx->persist_clusters, ctx->max_cs, 0, ctx->cap_stream, ctx->mixed ? 1 : 0, true);
+        e = launch_layer(ctx, a, ctx->persist_clusters, ctx->persist_cs, 0, ctx->cap_stream, ctx->mixed ? 1 : 0, true);
       if (e != cudaSuccess) {
         tp::set_error(std::string("tp_advance: CUDA error ") + cudaGetErrorString(e));
         rc = TP_ERR_CUDA;
@@ -760,6 +789,77 @@ extern "C" int tp_adjoint(tp_ctx* ctx, const double* d_lambda_T, double* d_lambd
   TP_CUDA_OK(cudaMemcpyAsync(d_lambda_0, ctx->d_adj, nfront * sizeof(double), cudaMemcpyDeviceToDevice, st));
   ctx->last_stream = st;
   return TP_OK;
+}
+
+extern "C" int tp_autotune(tp_ctx* ctx, void* stream, int32_t* chosen, double* best_ms) {
+  if (!ctx) {
+    tp::set_error("tp_autotune: null context");
+    return TP_ERR_ARG;
+  }
+  if (ctx->n_levels < 1) return TP_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t nfront = (size_t)ctx->nrhs * ctx->ne * ctx->Q * ctx->C;
+  double *save_f = nullptr, *save_t = nullptr;
+  if (cudaMalloc(&save_f, nfront * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&save_t, ctx->nv * sizeof(double)) != cudaSuccess) {
+    cudaFree(save_f);
+    tp::set_error("tp_autotune: allocation failed");
+    return TP_ERR_OOM;
+  }
+  int rc = TP_OK;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaMemcpyAsync(save_f, ctx->d_front, nfront * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(save_t, ctx->d_tau, ctx->nv * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  // candidates: 0 = one launch per level, else the dataflow sweep with clusters of that size
+  const int cand[5] = {0, 1, 2, 4, 8};
+  int best = -1;
+  float best_t = 3.4e38f;
+  for (int ci = 0; ci < 5 && rc == TP_OK; ++ci) {
+    const int c = cand[ci];
+    if (c == 0) {
+      ctx->persistent = false;
+    } else {
+      if (c > ctx->max_cs * 2 || set_persist_cs(ctx, c) != TP_OK) continue;
+      ctx->persistent = true;
+    }
+    for (auto& kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
+    ctx->graphs.clear();
+    float t = 0.f;
+    for (int rep = 0; rep < 2 && rc == TP_OK; ++rep) {
+      cudaMemcpyAsync(ctx->d_front, save_f, nfront * sizeof(double), cudaMemcpyDeviceToDevice, st);
+      cudaMemcpyAsync(ctx->d_tau, save_t, ctx->nv * sizeof(double), cudaMemcpyDeviceToDevice, st);
+      cudaEventRecord(e0, st);
+      rc = tp_advance(ctx, 1, ctx->n_levels + 1, stream);
+      cudaEventRecord(e1, st);
+      if (cudaEventSynchronize(e1) != cudaSuccess) rc = TP_ERR_CUDA;
+      cudaEventElapsedTime(&t, e0, e1);
+    }
+    if (rc == TP_OK && t < best_t) {
+      best_t = t;
+      best = c;
+    }
+  }
+  if (rc == TP_OK && best >= 0) {
+    ctx->persistent = best > 0;
+    if (best > 0) set_persist_cs(ctx, best);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned[std::vector<int>(ctx->tune_key, ctx->tune_key + 5)] = {best > 0 ? best : 1, best > 0};
+  }
+  for (auto& kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
+  ctx->graphs.clear();
+  cudaMemcpyAsync(ctx->d_front, save_f, nfront * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(ctx->d_tau, save_t, ctx->nv * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  cudaStreamSynchronize(st);
+  cudaFree(save_f);
+  cudaFree(save_t);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (chosen) *chosen = best;
+  if (best_ms) *best_ms = best_t;
+  ctx->last_stream = st;
+  return rc;
 }
 
 extern "C" int tp_energy(tp_ctx* ctx, double* d_out, void* stream) {

@@ -300,3 +300,25 @@ def test_mixed_many_rhs(cuda_device):
     for r, f in enumerate(inits):
         ref, _, _ = _oracle(m, 3, 0.3, kappa, f, None)
         assert _rel(got[r], ref) <= MIXED_TOL, r
+
+
+def test_autotune_keeps_results(cuda_device):
+    """tp_autotune restores the state it found and the schedule it picks
+    reproduces the oracle."""
+    import torch
+    import paper_1907_02367_gb300 as pkg
+    w = inputs.workload("small2d")
+    m = w.mesh
+    s = pkg.Solver(m.coords, m.elems, m.c, w.p, w.T, w.kappa)
+    xq, _ = s.front_points()
+    f0 = torch.tensor(w.init(xq), device="cuda").reshape(s.front_shape()).contiguous()
+    s.set_state(f0)
+    chosen, ms = s.autotune()
+    assert chosen in (0, 1, 2, 4, 8) and ms > 0
+    before, tau0 = s.get_state()
+    assert torch.equal(before, f0) and float(tau0.abs().max()) == 0.0
+    s.advance()
+    got, tau = s.get_state()
+    ref, rtau, _ = _oracle(m, w.p, w.T, w.kappa, w.init, None)
+    assert np.array_equal(tau.cpu().numpy(), rtau)
+    assert _rel(got.cpu().numpy().reshape(ref.shape), ref) <= TOL
