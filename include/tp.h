@@ -60,9 +60,13 @@ typedef struct tp_mesh_desc {
 
 /* p: degree of the second-order Trefftz space U^p (Section 3; unknowns per
  * single-material tent dim U^p = C(p+n,n) + C(p-1+n,n)); alpha: Dirichlet
- * penalty of eq. (2.5) (the paper uses 0.5); beta: time-like penalty (unused
- * until interface faces are built); kappa: pitching slope factor (edge-slope
- * limit delta_e = kappa l_e / c_e); T: final time; precision: TP_FP64;
+ * penalty of eq. (2.5) (the paper uses 0.5); beta: penalty of the [[sigma]]_N
+ * term on time-like interface facets (eq. 2.5, Section 4.2; the paper uses
+ * 0.5); kappa: pitching slope factor (edge-slope limit delta_e = kappa l_e /
+ * c_e); T: final time; precision: TP_FP64 (every step in binary64) or
+ * TP_MIXED (assembly, residual and outflow in float-float on the binary32
+ * pipes, binary32 LU of the equilibrated local matrix, iterative refinement
+ * to binary64 accuracy; TP_ERR_NOCONV if it stalls);
  * nrhs: right-hand sides advanced together (same tents, same matrices);
  * schedule: how tp_advance runs the levels -- TP_SCHED_DATAFLOW (default):
  * one resident kernel whose clusters take the tents in level order and each
@@ -115,9 +119,13 @@ int tp_basis_export(const tp_basis* basis, int32_t* exps, double* coef);
 void tp_destroy_basis(tp_basis* basis);
 
 /* Uploads mesh, tents, basis and quadrature tables to the current device and
- * allocates the front state (n_elem * Q * (dim+2) * nrhs doubles).
- * Errors: TP_ERR_ARG on mismatched dim/p, TP_ERR_UNSUPPORTED when a tent's
- * patch mixes wave speeds or exceeds the kernel's patch limit, TP_ERR_OOM. */
+ * allocates the front state (n_elem * Q * (dim+2) * nrhs doubles).  A tent
+ * whose patch holds elements of several wave speeds gets one polynomial of
+ * U^p per speed (Section 4.2), coupled through the time-like interface
+ * facets.  Errors: TP_ERR_ARG on mismatched dim/p; TP_ERR_UNSUPPORTED when a
+ * patch has more than 4 wave speeds, more than 64 elements or more than 16
+ * boundary plus interface facets, or the shared-memory plan (dim U^p,
+ * materials, nrhs) does not fit one CTA; TP_ERR_OOM. */
 int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const tp_basis* basis,
               const tp_params* prm, tp_ctx** out);
 /* n_front = n_elem * Q points, n_comp = dim + 2, n_bnd = number of Dirichlet
@@ -136,11 +144,15 @@ int tp_boundary_points(const tp_ctx* ctx, double* xt);
  * copied; the front times are reset to 0.  Asynchronous on `stream`. */
 int tp_set_state(tp_ctx* ctx, const double* d_front, const double* d_gD, void* stream);
 /* Solves every tent of one level (1-based) of the sorted tent list:
- * assembly of eq. (4.1) with the Section 5 recovery terms, LU solve,
- * outflow written at the top points (Section 4.1). */
+ * assembly of eq. (4.1) with the Section 5 recovery terms (and the
+ * interface terms of eq. 2.5 on multi-material tents), LU solve in the
+ * context's precision, outflow written at the top points (Section 4.1).
+ * One launch; levels must be solved in increasing order. */
 int tp_solve_layer(tp_ctx* ctx, int32_t level, void* stream);
 /* Levels [level_begin, level_end) (1-based, end exclusive) as one CUDA graph
- * (captured on first use for that range, then replayed). */
+ * (captured on first use for that range, then replayed).  With the dataflow
+ * schedule the graph holds one small setup kernel and one persistent sweep
+ * kernel; with TP_SCHED_LEVELS, one launch per level. */
 int tp_advance(tp_ctx* ctx, int32_t level_begin, int32_t level_end, void* stream);
 /* Autotuner of the sweep schedule (the paper has no counterpart): times a
  * full forward sweep of this context with one launch per level and with the
@@ -170,7 +182,11 @@ int tp_adjoint(tp_ctx* ctx, const double* d_lambda_T, double* d_lambda_0, void* 
  * (device, n_vert doubles); either may be NULL. */
 int tp_get_state(const tp_ctx* ctx, double* d_front, double* d_tau, void* stream);
 /* Synchronises the context's last stream and reports the device status:
- * *status = TP_OK or TP_ERR_SINGULAR, *info = first failing tent index. */
+ * *status = TP_OK, TP_ERR_CAUSALITY (a top face not space-like),
+ * TP_ERR_SINGULAR (zero or non-finite pivot), TP_ERR_NOCONV (mixed-precision
+ * refinement stalled) or TP_ERR_TIMEOUT (a bounded dependency wait of the
+ * dataflow sweep gave up); *info = index of the first failing tent in the
+ * sorted list.  The first error wins; tp_set_state clears it. */
 int tp_sync_status(tp_ctx* ctx, int32_t* status, int64_t* info);
 void tp_destroy_ctx(tp_ctx* ctx);
 
