@@ -462,6 +462,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
             flag_error(a, TP_ERR_TIMEOUT, tent);
             break;
           }
+          // once any tent has flagged an error the sweep's result is void:
+          // stop waiting so that the launch ends promptly
+          if ((spins & 255) == 0 && ld_acquire(a.status) != 0) break;
           __nanosleep(128);
         }
       }

@@ -114,3 +114,14 @@ def test_heterogeneous_speed_uses_edge_max():
     first = {int(v): float(t) for v, t, L in zip(r["vert"], r["t_top"], r["level"]) if L == 1}
     assert first[0] == (0.9 * 0.25) / 1.0
     assert first[2] == (0.9 * 0.25) / 3.0
+
+
+def test_invariants_2d_heterogeneous():
+    """An edge between a slow and a fast element is limited by the fast speed,
+    so every front stays space-like on both (c_K |grad tau|_K < 1, Section 2.2).
+    In 1D every edge is one element, so only 2D/3D meshes tell max from min."""
+    m = inputs.mesh_square(6, 0.2, seed=3)
+    cen = m.coords[m.elems].mean(axis=1)
+    m.c[:] = np.where(np.linalg.norm(cen - 0.5, axis=1) < 0.3, 3.0, 1.0)
+    r, worst = _replay_and_check(m, inputs.pitch_kappa(m), 0.3)
+    assert worst <= 0.9 + 1e-12
