@@ -454,6 +454,17 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
 
   a.nb = ctx->nb;
   a.nmono = ctx->nmono;
+  a.p = basis->p;
+  {
+    // the monomial list is ordered by total degree: offsets of each degree
+    std::vector<int> cnt(basis->p + 2, 0);
+    for (int g = 0; g < basis->nmono; ++g) {
+      int deg = 0;
+      for (int d = 0; d <= n; ++d) deg += basis->exps[g * (n + 1) + d];
+      ++cnt[deg + 1];
+    }
+    for (int d = 0; d <= basis->p + 1; ++d) a.mono_lv[d] = (d ? a.mono_lv[d - 1] : 0) + cnt[d];
+  }
   a.Q = Q;
   a.nrhs = ctx->nrhs;
   a.ne = T.ne;
@@ -543,6 +554,7 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
     take(&a.off_del, (size_t)ctx->nrhs * nb);
     take(&a.off_u, (size_t)2 * CH * nb);
     take(&a.off_mono, (size_t)2 * CH * a.mono_stride);
+    take(&a.off_pt, (size_t)2 * CH * (n + 2));
     take(&a.off_cb, (size_t)CH * ctx->nrhs * C);
     take(&a.off_gd, (size_t)CH * ctx->nrhs);
     take(&a.off_y, (size_t)ngmax * nmom);

@@ -32,6 +32,8 @@ __device__ __forceinline__ void red_release_add(int* p, int v) {
 
 struct KArgs {
   int nb, nmono, Q, nrhs, CH, mono_stride, ngmax;
+  int p;                          // degree of U^p
+  int mono_lv[kMaxP + 2];         // monomials of total degree d: [mono_lv[d], mono_lv[d+1])
   int64_t ne, n_bnd;
   double alpha, beta;
   const double* X;
@@ -87,6 +89,7 @@ struct KArgs {
   const float* rel_facf;      // relation factors (small integers) in binary32
   const float* relT_facf;
   int off_al, off_eq, off_perm, off_z, off_x;   // mixed path: binary32 LU and refinement
+  int off_pt;                                   // per-point (that, xhat, scale) of the block-wide evaluation
   int off_b, off_pg, off_ph, off_pgb, off_pm, off_pd, off_pbd, off_sg, off_sm, off_f, off_f2, off_fpm, off_del,
       off_u, off_mono, off_cb, off_gd, off_y, off_rd;
 };
@@ -234,17 +237,6 @@ __device__ __forceinline__ dd Ar<dd>::coef(const KArgs& a, int e) {
   return {c.x, c.y};
 }
 
-// monomials t^k x^alpha at (that, xhat) into m[0..nm): m[g] = m[parent[g]] * var
-template <int DIM, typename T>
-__device__ __forceinline__ void eval_monomials(const KArgs& a, T th, const T* xh, T* m) {
-  m[0] = Ar<T>::one();
-  for (int g = 1; g < a.nmono; ++g) {
-    const int vr = __ldg(a.mono_var + g);
-    const T s = (vr == 0) ? th : xh[vr - 1];
-    m[g] = Ar<T>::mul(m[__ldg(a.mono_parent + g)], s);
-  }
-}
-
 // U-value of basis function j: sum over its sparse monomial entries
 template <int DIM, typename T>
 __device__ __forceinline__ T sp_eval(const KArgs& a, int j, const T* m) {
@@ -255,11 +247,31 @@ __device__ __forceinline__ T sp_eval(const KArgs& a, int j, const T* m) {
   return s;
 }
 
-// U-values u_k = b_k(xhat, that) of every basis function at one point (times s if SCALE)
+// U-values at npt points with the whole block: the points' (that, xhat_1..xhat_n,
+// scale) are in pt[q * (DIM + 2)]; one pass per monomial degree (m = parent
+// monomial times one variable), then the sparse sums u_j = scale * sum c m.
+// Monomials go to m[q * mono_stride], U-values to u[q * nb].  Callers write pt
+// before the call; the first and last statements that touch shared memory
+// are separated from them by barriers.
 template <int DIM, typename T, bool SCALE = true>
-__device__ __forceinline__ void eval_uvalues(const KArgs& a, T th, const T* xh, T* m, T s, T* u) {
-  eval_monomials<DIM, T>(a, th, xh, m);
-  for (int k = 0; k < a.nb; ++k) u[k] = SCALE ? Ar<T>::mul(s, sp_eval<DIM, T>(a, k, m)) : sp_eval<DIM, T>(a, k, m);
+__device__ __forceinline__ void eval_uvalues_block(const KArgs& a, int npt, const T* pt, T* m, T* u) {
+  const int tid = threadIdx.x, ms = a.mono_stride, nb = a.nb;
+  for (int q = tid; q < npt; q += blockDim.x) m[q * ms] = Ar<T>::one();
+  for (int d = 1; d <= a.p; ++d) {
+    __syncthreads();   // pt, and the monomials of degree d - 1
+    const int g0 = a.mono_lv[d], cnt = a.mono_lv[d + 1] - g0;
+    for (int id = tid; id < npt * cnt; id += blockDim.x) {
+      const int q = id / cnt, g = g0 + id % cnt;
+      m[q * ms + g] = Ar<T>::mul(m[q * ms + __ldg(a.mono_parent + g)], pt[q * (DIM + 2) + __ldg(a.mono_var + g)]);
+    }
+  }
+  __syncthreads();
+  for (int id = tid; id < npt * nb; id += blockDim.x) {
+    const int q = id / nb, j = id % nb;
+    const T v = sp_eval<DIM, T>(a, j, m + q * ms);
+    u[q * nb + j] = SCALE ? Ar<T>::mul(pt[q * (DIM + 2) + DIM + 1], v) : v;
+  }
+  __syncthreads();
 }
 
 // packed upper-triangle index of (i, j), i, j < nb
@@ -491,6 +503,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
   T* sFpm = reinterpret_cast<T*>(sm + a.off_fpm);    // nb*nb      facet Gram (+ test, - trial)
   T* sDel = reinterpret_cast<T*>(sm + a.off_del);    // nrhs*nb    facet moments delta
   T* sU = reinterpret_cast<T*>(sm + a.off_u);        // 2*CH*nb    U-values (scaled) per (side, point)
+  T* sPt = reinterpret_cast<T*>(sm + a.off_pt);      // 2*CH*(DIM+2)  (that, xhat, scale) per point
   T* sM = reinterpret_cast<T*>(sm + a.off_mono);     // 2*CH*mono_stride
   T* sCB = reinterpret_cast<T*>(sm + a.off_cb);      // CH*nrhs*C  data coefficients
   T* sGd = reinterpret_cast<T*>(sm + a.off_gd);      // CH*nrhs    Dirichlet data coefficients
@@ -669,52 +682,53 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
   };
   for (int base = q0; base < q1; base += CH) {
     const int nq = min(CH, q1 - base);
-    // (a) one thread per (side, point): sqrt(w)-scaled U-values, data coefficients
-    if (tid < 2 * CH) {
-      const int side = tid / CH, ql = tid % CH, qg = base + ql;
-      if (ql < nq) {
-        const int k = qg / Q, q = qg % Q, g = s_grp[k];
-        const double cg = s_gc[g], ic2 = 1.0 / (cg * cg);
-        if (side == 0) s_pgrp[ql] = g;
-        double x[DIM], tt = 0.0;
-        for (int d = 0; d < DIM; ++d) x[d] = 0.0;
-        for (int i = 0; i < NV; ++i) {
-          const double l = __ldg(a.bary + q * NV + i);
-          for (int d = 0; d < DIM; ++d) x[d] = fma(l, s_X[k][i][d], x[d]);
-          tt = fma(l, side == 0 ? s_tt[k][i] : s_tb[k][i], tt);
+    // (a) one thread per (side, point): mapped coordinates, sqrt(w), data
+    // coefficients; then the U-values of all 2 nq points with the whole block
+    // (point q = side * nq + ql)
+    const int npt = 2 * nq;
+    for (int id = tid; id < npt; id += blockDim.x) {
+      const int side = id / nq, ql = id % nq, qg = base + ql;
+      const int k = qg / Q, q = qg % Q, g = s_grp[k];
+      const double cg = s_gc[g], ic2 = 1.0 / (cg * cg);
+      if (side == 0) s_pgrp[ql] = g;
+      double x[DIM], tt = 0.0;
+      for (int d = 0; d < DIM; ++d) x[d] = 0.0;
+      for (int i = 0; i < NV; ++i) {
+        const double l = __ldg(a.bary + q * NV + i);
+        for (int d = 0; d < DIM; ++d) x[d] = fma(l, s_X[k][i][d], x[d]);
+        tt = fma(l, side == 0 ? s_tt[k][i] : s_tb[k][i], tt);
+      }
+      T* pp = sPt + id * (DIM + 2);
+      pp[0] = R::from(cg * (tt - tc) * ih);
+      for (int d = 0; d < DIM; ++d) pp[1 + d] = R::from((x[d] - s_xv[d]) * ih);
+      const double sw = __ldg(a.sqw + q) * s_sdet[k];
+      pp[DIM + 1] = R::from(sw);
+      const int el = s_el[k];
+      if (ADJ && side == 0) {
+        // adjoint: zeta = sum_q lambda_q u_q over the top points
+        const double isw = 1.0 / sw;
+        for (int r = 0; r < nrhs; ++r) {
+          const double* f = a.front + (((int64_t)r * a.ne + el) * Q + q) * C;
+          T* cb = sCB + ((size_t)ql * nrhs + r) * C;
+          for (int cc = 0; cc < C; ++cc) cb[cc] = R::from(__ldcg(f + cc) * isw);
         }
-        T xh[DIM];
-        for (int d = 0; d < DIM; ++d) xh[d] = R::from((x[d] - s_xv[d]) * ih);
-        const T th = R::from(cg * (tt - tc) * ih);
-        const double sw = __ldg(a.sqw + q) * s_sdet[k];
-        eval_uvalues<DIM, T>(a, th, xh, sM + tid * a.mono_stride, R::from(sw), sU + (size_t)tid * nb);
-        const int el = s_el[k];
-        if (ADJ && side == 0) {
-          // adjoint: zeta = sum_q lambda_q u_q over the top points
-          const double isw = 1.0 / sw;
-          for (int r = 0; r < nrhs; ++r) {
-            const double* f = a.front + (((int64_t)r * a.ne + el) * Q + q) * C;
-            T* cb = sCB + ((size_t)ql * nrhs + r) * C;
-            for (int cc = 0; cc < C; ++cc) cb[cc] = R::from(__ldcg(f + cc) * isw);
-          }
-        }
-        if (!ADJ && side == 1) {
-          for (int r = 0; r < nrhs; ++r) {
-            const double* f = a.front + (((int64_t)r * a.ne + el) * Q + q) * C;
-            double fv[C];
-            for (int cc = 0; cc < C; ++cc) fv[cc] = __ldcg(f + cc);
-            const double Ub = fv[0], vb = fv[1];
-            double sg = 0.0;
-            for (int d = 0; d < DIM; ++d) sg = fma(fv[2 + d], s_gb[k][d], sg);
-            T* cb = sCB + ((size_t)ql * nrhs + r) * C;
-            cb[0] = R::from(sw * Ub);                       // gamma
-            cb[1] = R::from(sw * (ic2 * vb - sg));          // alpha
-            for (int d = 0; d < DIM; ++d) cb[2 + d] = R::from(sw * (fv[2 + d] - vb * s_gb[k][d]));   // beta_m
-          }
+      }
+      if (!ADJ && side == 1) {
+        for (int r = 0; r < nrhs; ++r) {
+          const double* f = a.front + (((int64_t)r * a.ne + el) * Q + q) * C;
+          double fv[C];
+          for (int cc = 0; cc < C; ++cc) fv[cc] = __ldcg(f + cc);
+          const double Ub = fv[0], vb = fv[1];
+          double sg = 0.0;
+          for (int d = 0; d < DIM; ++d) sg = fma(fv[2 + d], s_gb[k][d], sg);
+          T* cb = sCB + ((size_t)ql * nrhs + r) * C;
+          cb[0] = R::from(sw * Ub);                       // gamma
+          cb[1] = R::from(sw * (ic2 * vb - sg));          // alpha
+          for (int d = 0; d < DIM; ++d) cb[2 + d] = R::from(sw * (fv[2 + d] - vb * s_gb[k][d]));   // beta_m
         }
       }
     }
-    __syncthreads();
+    eval_uvalues_block<DIM, T>(a, npt, sPt, sM, sU);
     // (b) Grams of U-values: top per element (flushed into G and H_m), bottom; per material
     for (int ql = 0; ql < nq; ++ql) {
       const int k = (base + ql) / Q;
@@ -727,7 +741,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
         curk = k;
       }
       const T* ut = sU + (size_t)ql * nb;
-      const T* ub = sU + (size_t)(CH + ql) * nb;
+      const T* ub = sU + (size_t)(nq + ql) * nb;
 #pragma unroll
       for (int s = 0; s < kMaxPair; ++s) {
         if (tid + s * kThreads < npair) {
@@ -737,13 +751,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
       }
     }
     // (c) moments of the data (forward: bottom points; adjoint: top points), per material
-    const int row0 = ADJ ? 0 : CH;
+    const int prow = ADJ ? 0 : nq;
     for (int id = tid; id < ng * nmom; id += blockDim.x) {
       const int g = id / nmom, rest = id % nmom;
       const int r = rest / (C * nb), rem = rest % (C * nb), cc = rem / nb, i = rem % nb;
       T t = sPM[id];
       for (int ql = 0; ql < nq; ++ql)
-        if (s_pgrp[ql] == g) t = R::fma(sCB[((size_t)ql * nrhs + r) * C + cc], sU[(size_t)(row0 + ql) * nb + i], t);
+        if (s_pgrp[ql] == g) t = R::fma(sCB[((size_t)ql * nrhs + r) * C + cc], sU[(size_t)(prow + ql) * nb + i], t);
       sPM[id] = t;
     }
     __syncthreads();
@@ -771,32 +785,36 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
       for (int s = 0; s < kMaxPair; ++s) aF[s] = aF2[s] = R::zero();
       for (int base = f0; base < f1; base += CH) {
         const int nq = min(CH, f1 - base);
-        if (tid < nq) {
-          const int q = base + tid;
+        const int npt = dir ? nq : 2 * nq;   // interface: + side points, then - side
+        for (int id = tid; id < nq; id += blockDim.x) {
+          const int q = base + id;
           double xt[DIM + 1];
           for (int d = 0; d <= DIM; ++d) xt[d] = 0.0;
           for (int i = 0; i < NV; ++i) {
             const double l = __ldg(a.bary + q * NV + i);
             for (int d = 0; d <= DIM; ++d) xt[d] = fma(l, s_fP[f][i][d], xt[d]);
           }
-          T xh[DIM];
-          for (int d = 0; d < DIM; ++d) xh[d] = R::from((xt[d] - s_xv[d]) * ih);
           const double sw = sqrt(__ldg(a.wref + q) * s_fscale[f]);
-          eval_uvalues<DIM, T>(a, R::from(cp * (xt[DIM] - tc) * ih), xh, sM + tid * a.mono_stride, R::from(sw),
-                               sU + (size_t)tid * nb);
-          if (!dir)
-            eval_uvalues<DIM, T>(a, R::from(cm * (xt[DIM] - tc) * ih), xh, sM + (CH + tid) * a.mono_stride,
-                                 R::from(sw), sU + (size_t)(CH + tid) * nb);
+          T* pp = sPt + id * (DIM + 2);
+          pp[0] = R::from(cp * (xt[DIM] - tc) * ih);
+          for (int d = 0; d < DIM; ++d) pp[1 + d] = R::from((xt[d] - s_xv[d]) * ih);
+          pp[DIM + 1] = R::from(sw);
+          if (!dir) {
+            T* p2 = sPt + (nq + id) * (DIM + 2);
+            p2[0] = R::from(cm * (xt[DIM] - tc) * ih);
+            for (int d = 0; d < DIM; ++d) p2[1 + d] = pp[1 + d];
+            p2[DIM + 1] = pp[DIM + 1];
+          }
           if (dir) {
             const long long goff = a.tent_gdoff[tent] + (long long)f * Q + q;
             for (int r = 0; r < nrhs; ++r)
-              sGd[tid * nrhs + r] = R::from((!ADJ && a.gD != nullptr) ? sw * a.gD[(long long)r * a.n_bnd + goff] : 0.0);
+              sGd[id * nrhs + r] = R::from((!ADJ && a.gD != nullptr) ? sw * a.gD[(long long)r * a.n_bnd + goff] : 0.0);
           }
         }
-        __syncthreads();
+        eval_uvalues_block<DIM, T>(a, npt, sPt, sM, sU);
         for (int ql = 0; ql < nq; ++ql) {
           const T* u = sU + (size_t)ql * nb;
-          const T* u2 = sU + (size_t)(CH + ql) * nb;
+          const T* u2 = sU + (size_t)(nq + ql) * nb;
 #pragma unroll
           for (int s = 0; s < kMaxPair; ++s)
             if (tid + s * kThreads < npair) {
@@ -815,7 +833,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
           for (int id = tid; id < nb * nb; id += blockDim.x) {
             const int i = id / nb, j = id % nb;
             T t = sFpm[id];
-            for (int ql = 0; ql < nq; ++ql) t = R::fma(sU[(size_t)ql * nb + i], sU[(size_t)(CH + ql) * nb + j], t);
+            for (int ql = 0; ql < nq; ++ql) t = R::fma(sU[(size_t)ql * nb + i], sU[(size_t)(nq + ql) * nb + j], t);
             sFpm[id] = t;
           }
         }
@@ -883,35 +901,39 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
   }
 
   // ---------------- cluster reduction (rank order) ----------------
+  // every CTA sums every CTA's partials in rank order (all remote loads of an
+  // entry are issued before the additions)
+  auto cluster_sum = [&](T* src, int id) {
+    T t = R::zero();
+    for (int r0 = 0; r0 < CS; r0 += 4) {
+      T v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (r0 + u < CS) v[u] = cluster.map_shared_rank(src, r0 + u)[id];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (r0 + u < CS) t = R::add(t, v[u]);
+    }
+    return t;
+  };
   cluster.sync();
   // layout [G (NG*npair) | H_m (NG*DIM*npair) | Gbot (NG*npair)]; unused groups hold zeros
-  for (int id = tid; id < NG * (DIM + 2) * npair; id += blockDim.x) {
-    T t = R::zero();
-    for (int r = 0; r < CS; ++r) t = R::add(t, cluster.map_shared_rank(sPG, r)[id]);
-    sSG[id] = t;
-  }
-  for (int id = tid; id < ng * nmom; id += blockDim.x) {
-    T t = R::zero();
-    for (int r = 0; r < CS; ++r) t = R::add(t, cluster.map_shared_rank(sPM, r)[id]);
-    sSM[id] = t;
-  }
-  for (int id = tid; id < N * N; id += blockDim.x) {
-    T t = R::zero();
-    if (extra)
-      for (int r = 0; r < CS; ++r) t = R::add(t, cluster.map_shared_rank(sPD, r)[id]);
-    sA[id] = t;
-  }
-  for (int id = tid; id < nrhs * N; id += blockDim.x) {
-    T t = R::zero();
-    if (nfac > 0)
-      for (int r = 0; r < CS; ++r) t = R::add(t, cluster.map_shared_rank(sPBD, r)[id]);
-    sb[id] = t;
-  }
+  for (int id = tid; id < NG * (DIM + 2) * npair; id += blockDim.x) sSG[id] = cluster_sum(sPG, id);
+  for (int id = tid; id < ng * nmom; id += blockDim.x) sSM[id] = cluster_sum(sPM, id);
+  for (int id = tid; id < N * N; id += blockDim.x) sA[id] = extra ? cluster_sum(sPD, id) : R::zero();
+  for (int id = tid; id < nrhs * N; id += blockDim.x) sb[id] = nfac > 0 ? cluster_sum(sPBD, id) : R::zero();
   cluster.sync();   // no CTA leaves or reuses its partials while another still reads them
+  // congruence: rank r forms rows [N r / CS, N (r + 1) / CS) of A and b and
+  // stores them into rank 0's A and b; rank 0 alone solves.  Every CTA holds
+  // the same summed partials, so the rows do not depend on which rank forms them.
+  T* A0 = cluster.map_shared_rank(sA, 0);
+  T* b0 = cluster.map_shared_rank(sb, 0);
+  const int row0 = (N * rank) / CS, nrow = (N * (rank + 1)) / CS - row0;
   {
     const T ih2 = R::from(ih * ih), mih = R::from(-ih);
-    for (int id = tid; id < ng * nb * nb; id += blockDim.x) {
-      const int g = id / (nb * nb), rem = id % (nb * nb), i = rem / nb, j = rem % nb;
+    for (int id = tid; id < nrow * nb; id += blockDim.x) {
+      const int Rw = row0 + id / nb, j = id % nb;
+      const int g = Rw / nb, i = Rw % nb;
       const T* SG = sSG + (size_t)g * npair;
       const T* SGb = sSG + (size_t)(NG * (DIM + 1) + g) * npair;
       const T cc_ = R::from(s_gc[g]);
@@ -921,19 +943,21 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
         t = R::add(t, congruence<DIM, T>(a, i, 1 + d, j, 1 + d, SG, nb));
         t = R::fma(cc_, R::add(congruence<DIM, T>(a, i, 1 + d, j, 0, H, nb), congruence<DIM, T>(a, i, 0, j, 1 + d, H, nb)), t);
       }
-      T* dst = sA + (size_t)(g * nb + i) * N + g * nb + j;
-      *dst = R::add(*dst, R::fma(ih2, t, SGb[pair_index(i, j, nb)]));
+      const size_t o = (size_t)Rw * N + g * nb + j;
+      A0[o] = R::add(sA[o], R::fma(ih2, t, SGb[pair_index(i, j, nb)]));
     }
-    for (int id = tid; id < ng * nrhs * nb; id += blockDim.x) {
-      const int g = id / (nrhs * nb), rem = id % (nrhs * nb), r = rem / nb, i = rem % nb;
+    for (int id = tid; id < nrhs * nrow; id += blockDim.x) {
+      const int r = id / nrow, Rw = row0 + id % nrow;
+      const int g = Rw / nb, i = Rw % nb;
       const T* M = sSM + (size_t)g * nmom + (size_t)r * C * nb;   // gamma, alpha, beta_1..beta_n
       T t = R::fma(R::from(s_gc[g] * ih), rel_apply<DIM, T>(a, i, 0, M + nb), M[i]);
       for (int d = 0; d < DIM; ++d) t = R::fma(mih, rel_apply<DIM, T>(a, i, 1 + d, M + (2 + d) * nb), t);
-      T* dst = sb + (size_t)r * N + g * nb + i;
-      *dst = R::add(*dst, t);
+      const size_t o = (size_t)r * N + Rw;
+      b0[o] = R::add(sb[o], t);
     }
   }
-  __syncthreads();
+  cluster.sync();   // rank 0 holds the assembled A and b
+  if (rank == 0) {
   if constexpr (ADJ) {   // solve with A^T
     for (int id = tid; id < N * N; id += blockDim.x) {
       const int i = id / N, j = id % N;
@@ -1117,64 +1141,87 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
     __syncthreads();
   }
   if constexpr (!MIXED) {
-    {
+    __syncthreads();
+    double* sXd = reinterpret_cast<double*>(sm + a.off_x);   // nrhs*N  solution during back substitution
+    auto pivot_recip = [&](double piv, int k) {
+      if (!(fabs(piv) > 0.0) || !isfinite(piv)) {
+        flag_error(a, TP_ERR_SINGULAR, tent);
+        piv = 1.0;
+      }
+      sRD[k] = recip(piv);
+    };
+    if (!pivoting) {
+      // A is symmetric positive definite: LU without interchanges, b eliminated
+      // alongside, one barrier per step.  Step k updates rows and columns > k;
+      // every thread forms the multiplier a_ik / a_kk it needs, and the thread
+      // that updates a_{k+1,k+1} forms the next reciprocal pivot.
+      if (tid == 0) pivot_recip(sA[0], 0);
       __syncthreads();
-    // LU (no pivoting for single-material interior tents: A is SPD), forward elimination of b alongside
-      for (int k = 0; k < N; ++k) {
-        if (pivoting) {
-          if (warp == 0) {
-            // |a_ik| compared through the bit patterns (non-negative doubles order as integers)
-            unsigned long long best = 0ull;
-            int bi = k;
-            for (int i = k + lane; i < N; i += 32) {
-              const unsigned long long bits = (unsigned long long)__double_as_longlong(fabs(sA[i * N + k]));
-              if (bits > best || (bits == best && i < bi)) {
-                best = bits;
-                bi = i;
-              }
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-              const unsigned long long ob = __shfl_down_sync(0xffffffffu, best, o);
-              const int oi = __shfl_down_sync(0xffffffffu, bi, o);
-              if (ob > best || (ob == best && oi < bi)) {
-                best = ob;
-                bi = oi;
-              }
-            }
-            if (lane == 0) s_piv = bi;
-          }
-          __syncthreads();
-          const int pr = s_piv;
-          if (pr != k) {
-            for (int j = tid; j < N; j += blockDim.x) {
-              const double t = sA[k * N + j];
-              sA[k * N + j] = sA[pr * N + j];
-              sA[pr * N + j] = t;
-            }
-            for (int r = tid; r < nrhs; r += blockDim.x) {
-              const double t = sb[r * N + k];
-              sb[r * N + k] = sb[r * N + pr];
-              sb[r * N + pr] = t;
-            }
-          }
-          __syncthreads();
-        }
-        if (tid == 0) {
-          double piv = sA[k * N + k];
-          if (!(fabs(piv) > 0.0) || !isfinite(piv)) {
-            if (rank == 0) flag_error(a, TP_ERR_SINGULAR, tent);
-            piv = 1.0;
-          }
-          sRD[k] = recip(piv);
-        }
-        __syncthreads();
+      for (int k = 0; k + 1 < N; ++k) {
         const double rp = sRD[k];
-        const int rem = N - k - 1;
-        for (int i = k + 1 + tid; i < N; i += blockDim.x) sA[i * N + k] *= rp;   // multipliers
+        const int rem = N - k - 1, wdt = rem + nrhs;
+        for (int id = tid; id < rem * wdt; id += blockDim.x) {
+          const int i = k + 1 + id / wdt, jj = id % wdt;
+          const double l = sA[i * N + k] * rp;
+          if (jj < rem) {
+            const int j = k + 1 + jj;
+            const double t = fma(-l, sA[k * N + j], sA[i * N + j]);
+            sA[i * N + j] = t;
+            if (id == 0) pivot_recip(t, k + 1);
+          } else {
+            const int r = jj - rem;
+            sb[r * N + i] = fma(-l, sb[r * N + k], sb[r * N + i]);
+          }
+        }
         __syncthreads();
-        for (int id = tid; id < rem * (rem + nrhs); id += blockDim.x) {
-          const int i = k + 1 + id / (rem + nrhs), jj = id % (rem + nrhs);
-          const double l = sA[i * N + k];
+      }
+    } else {
+      // LU with partial pivoting (Dirichlet and interface tents), b eliminated alongside
+      for (int k = 0; k < N; ++k) {
+        if (warp == 0) {
+          // |a_ik| compared through the bit patterns (non-negative doubles order as integers)
+          unsigned long long best = 0ull;
+          int bi = k;
+          for (int i = k + lane; i < N; i += 32) {
+            const unsigned long long bits = (unsigned long long)__double_as_longlong(fabs(sA[i * N + k]));
+            if (bits > best || (bits == best && i < bi)) {
+              best = bits;
+              bi = i;
+            }
+          }
+          for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long ob = __shfl_down_sync(0xffffffffu, best, o);
+            const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+            if (ob > best || (ob == best && oi < bi)) {
+              best = ob;
+              bi = oi;
+            }
+          }
+          if (lane == 0) {
+            s_piv = bi;
+            pivot_recip(sA[bi * N + k], k);
+          }
+        }
+        __syncthreads();
+        const int pr = s_piv;
+        if (pr != k) {
+          for (int j = tid; j < N; j += blockDim.x) {
+            const double t = sA[k * N + j];
+            sA[k * N + j] = sA[pr * N + j];
+            sA[pr * N + j] = t;
+          }
+          for (int r = tid; r < nrhs; r += blockDim.x) {
+            const double t = sb[r * N + k];
+            sb[r * N + k] = sb[r * N + pr];
+            sb[r * N + pr] = t;
+          }
+          __syncthreads();
+        }
+        const double rp = sRD[k];
+        const int rem = N - k - 1, wdt = rem + nrhs;
+        for (int id = tid; id < rem * wdt; id += blockDim.x) {
+          const int i = k + 1 + id / wdt, jj = id % wdt;
+          const double l = sA[i * N + k] * rp;
           if (jj < rem) {
             const int j = k + 1 + jj;
             sA[i * N + j] = fma(-l, sA[k * N + j], sA[i * N + j]);
@@ -1185,18 +1232,26 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
         }
         __syncthreads();
       }
-      for (int k = N - 1; k >= 0; --k) {
-        for (int r = tid; r < nrhs; r += blockDim.x) sb[r * N + k] *= sRD[k];
-        __syncthreads();
-        for (int id = tid; id < k * nrhs; id += blockDim.x) {
-          const int r = id / k, i = id % k;
-          sb[r * N + i] = fma(-sA[i * N + k], sb[r * N + k], sb[r * N + i]);
-        }
-        __syncthreads();
-      }
-  
     }
+    // back substitution, one barrier per step: x_k = b_k / u_kk into sXd, and
+    // b_i -= u_ik x_k for i < k (every thread forms x_k itself)
+    for (int k = N - 1; k >= 0; --k) {
+      const double rp = sRD[k];
+      for (int id = tid; id < (k + 1) * nrhs; id += blockDim.x) {
+        const int r = id / (k + 1), i = id % (k + 1);
+        const double xk = sb[r * N + k] * rp;
+        if (i == k) sXd[r * N + k] = xk;
+        else sb[r * N + i] = fma(-sA[i * N + k], xk, sb[r * N + i]);
+      }
+      __syncthreads();
+    }
+    for (int id = tid; id < nrhs * N; id += blockDim.x) sb[id] = sXd[id];
   }
+  }   // rank 0
+  cluster.sync();   // the solution is in rank 0's b
+  if (rank != 0)
+    for (int id = tid; id < nrhs * N; id += blockDim.x) sb[id] = b0[id];
+  __syncthreads();
 
   // ---------------- phase 4: outflow at this CTA's top points (adjoint: bottom points) ----------------
   // coefficient vectors of U_h, v_h, sigma_h in terms of U-values, per material: y = D^T x_g
@@ -1211,8 +1266,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
   }
   for (int base = q0; base < q1; base += 2 * CH) {
     const int nq = min(2 * CH, q1 - base);
-    if (tid < nq) {
-      const int qg = base + tid, k = qg / Q, q = qg % Q;
+    for (int id = tid; id < nq; id += blockDim.x) {
+      const int qg = base + id, k = qg / Q, q = qg % Q;
       const double cg = s_gc[s_grp[k]];
       double x[DIM], tt = 0.0;
       for (int d = 0; d < DIM; ++d) x[d] = 0.0;
@@ -1221,12 +1276,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
         for (int d = 0; d < DIM; ++d) x[d] = fma(l, s_X[k][i][d], x[d]);
         tt = fma(l, ADJ ? s_tb[k][i] : s_tt[k][i], tt);
       }
-      T xh[DIM];
-      for (int d = 0; d < DIM; ++d) xh[d] = R::from((x[d] - s_xv[d]) * ih);
-      const T th = R::from(cg * (tt - tc) * ih);
-      eval_uvalues<DIM, T, false>(a, th, xh, sM + tid * a.mono_stride, R::one(), sU + (size_t)tid * nb);
+      T* pp = sPt + id * (DIM + 2);
+      pp[0] = R::from(cg * (tt - tc) * ih);
+      for (int d = 0; d < DIM; ++d) pp[1 + d] = R::from((x[d] - s_xv[d]) * ih);
+      pp[DIM + 1] = R::one();
     }
-    __syncthreads();
+    eval_uvalues_block<DIM, T, false>(a, nq, sPt, sM, sU);
     if constexpr (!ADJ) {
       for (int id = tid; id < nq * nrhs * C; id += blockDim.x) {
         const int ql = id / (nrhs * C), rc = id % (nrhs * C), r = rc / C, cc = rc % C;
@@ -1269,6 +1324,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
     cluster.sync();
     if (rank == 0 && tid == 0) red_release_add(a.done + v, 1);
   } else {
+    cluster.sync();   // rank 0's b stays valid until every CTA has read the solution
     break;
   }
   }   // tent loop
