@@ -273,9 +273,10 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
   ctx->n_levels = tents->n_levels;
   ctx->level_ptr = tents->level_ptr;
   // patch checks: size limits; materials (distinct wave speeds) per tent
-  int ngmax = 1;
+  int ngmax = 1, pmax = 1;
   for (int64_t v = 0; v < T.nv; ++v) {
     const int p0 = T.star_ptr[v], p1 = T.star_ptr[v + 1];
+    pmax = std::max(pmax, p1 - p0);
     if ((T.vfac_ptr[v + 1] - T.vfac_ptr[v]) + (T.ifac_ptr[v + 1] - T.ifac_ptr[v]) > tp::kMaxFacets) {
       tp::set_error("tp_create: vertex " + std::to_string(v) + " lies on more than 16 boundary or interface facets");
       return fail(TP_ERR_UNSUPPORTED);
@@ -398,6 +399,33 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
   std::vector<double> tbot(tents->t_bot.begin(), tents->t_bot.end());
   double* dtbot = nullptr;
   std::vector<int> tv(tents->vert.begin(), tents->vert.end());
+  // vertex stars grouped by material: speeds in order of first appearance
+  // (bitwise-equal c), elements of each material in star order
+  std::vector<int> star_sorted(T.star_el.size()), star_grp(T.star_el.size()), vert_ng(T.nv);
+  std::vector<double> vert_gc((size_t)T.nv * tp::kMaxGroups, 0.0);
+  for (int64_t v = 0; v < T.nv; ++v) {
+    const int p0 = T.star_ptr[v], p1 = T.star_ptr[v + 1];
+    int ng = 0;
+    for (int e = p0; e < p1; ++e) {
+      const double ck = T.c[T.star_el[e]];
+      int g = 0;
+      while (g < ng && vert_gc[(size_t)v * tp::kMaxGroups + g] != ck) ++g;
+      if (g == ng) vert_gc[(size_t)v * tp::kMaxGroups + ng++] = ck;
+    }
+    vert_ng[v] = ng;
+    int pos = p0;
+    for (int g = 0; g < ng; ++g)
+      for (int e = p0; e < p1; ++e)
+        if (T.c[T.star_el[e]] == vert_gc[(size_t)v * tp::kMaxGroups + g]) {
+          star_sorted[pos] = T.star_el[e];
+          star_grp[pos++] = g;
+        }
+  }
+  int *dsso = nullptr, *dsgr = nullptr, *dvng = nullptr;
+  double* dvgc = nullptr;
+  if ((rc = ctx_upload(ctx, &dsso, star_sorted)) || (rc = ctx_upload(ctx, &dsgr, star_grp)) ||
+      (rc = ctx_upload(ctx, &dvng, vert_ng)) || (rc = ctx_upload(ctx, &dvgc, vert_gc)))
+    return fail(rc);
   if ((rc = ctx_upload(ctx, &dX, T.X)) || (rc = ctx_upload(ctx, &dc, T.c)) ||
       (rc = ctx_upload(ctx, &del, T.elems)) || (rc = ctx_upload(ctx, &dsp, T.star_ptr)) ||
       (rc = ctx_upload(ctx, &dse, T.star_el)) || (rc = ctx_upload(ctx, &dvp, T.vfac_ptr)) ||
@@ -486,6 +514,10 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
   a.cK = dc;
   a.star_ptr = dsp;
   a.star_el = dse;
+  a.star_sorted = dsso;
+  a.star_grp = dsgr;
+  a.vert_ng = dvng;
+  a.vert_gc = dvgc;
   a.vfac_ptr = dvp;
   a.vfac = dvf;
   a.facet_vert = dfv;
@@ -530,7 +562,7 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
   a.mono_stride = ctx->nmono | 1;
   // shared-memory plan: the largest chunk of points that keeps two CTAs per SM,
   // else the largest that fits one
-  auto plan = [&](int CH) {
+  auto plan = [&](int CH, int keep) {
     size_t off = 0;
     auto take = [&](int* field, size_t count) {
       if (field) *field = (int)off;
@@ -560,26 +592,37 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
     take(&a.off_y, (size_t)ngmax * nmom);
     take(&a.off_rd, NB);
     const size_t half_nb = (NB + 1) / 2, half_rb = ((size_t)ctx->nrhs * NB + 1) / 2;
-    take(&a.off_al, (NB * NB + 1) / 2);            // binary32 words, two per double slot
+    take(&a.off_al, NB * NB);                      // two binary32 N x N sweep buffers
     take(&a.off_eq, half_nb);
     take(&a.off_perm, half_nb);
     take(&a.off_z, half_rb);
     take(&a.off_x, (size_t)ctx->nrhs * NB);
+    take(&a.off_keep, (size_t)keep * nb);          // top U-values of the CTA's slice, kept for the outflow
+    take(&a.off_keepw, (size_t)keep);
     return off * sizeof(double);
   };
   int CH = 0;
-  size_t bytes = 0;
+  size_t bytes = 0, cap_used = 0;
   for (size_t cap : {kTwoPerSmSmem, kMaxDynSmem}) {
     for (int ch = 32; ch >= 8 && CH == 0; ch /= 2)
-      if (plan(ch) <= cap) CH = ch;
-    if (CH) break;
+      if (plan(ch, 0) <= cap) CH = ch;
+    if (CH) {
+      cap_used = cap;
+      break;
+    }
   }
   if (CH == 0) {
     tp::set_error("tp_create: shared-memory plan does not fit (nb/nrhs too large)");
     return fail(TP_ERR_UNSUPPORTED);
   }
-  bytes = plan(CH);
+  // the rest of the budget keeps the top U-values of up to `keep` points per
+  // CTA (a slice that fits skips their second evaluation in the outflow)
+  int keep = (int)std::min<size_t>((cap_used - plan(CH, 0)) / ((size_t)(nb + 1) * sizeof(double)),
+                                   (size_t)pmax * Q);
+  while (keep > 0 && plan(CH, keep) > cap_used) --keep;
+  bytes = plan(CH, keep);
   a.CH = CH;
+  a.keep_pts = keep;
   ctx->args_adj = a;
   ctx->args_adj.front = ctx->d_adj;
   ctx->args_adj.tau = ctx->d_tau_adj;

@@ -41,6 +41,10 @@ struct KArgs {
   const double* cK;
   const int* star_ptr;
   const int* star_el;
+  const int* star_sorted;     // vertex stars with the elements grouped by wave speed
+  const int* star_grp;        // material group of each entry of star_sorted
+  const int* vert_ng;         // materials (distinct wave speeds) in each vertex star
+  const double* vert_gc;      // their speeds, kMaxGroups per vertex, in order of first appearance
   const int* vfac_ptr;
   const int* vfac;
   const int* facet_vert;
@@ -90,6 +94,7 @@ struct KArgs {
   const float* relT_facf;
   int off_al, off_eq, off_perm, off_z, off_x;   // mixed path: binary32 LU and refinement
   int off_pt;                                   // per-point (that, xhat, scale) of the block-wide evaluation
+  int keep_pts, off_keep, off_keepw;            // kept top U-values (scaled) and 1/sqrt(w) of a CTA's slice
   int off_b, off_pg, off_ph, off_pgb, off_pm, off_pd, off_pbd, off_sg, off_sm, off_f, off_f2, off_fpm, off_del,
       off_u, off_mono, off_cb, off_gd, off_y, off_rd;
 };
@@ -433,7 +438,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
   constexpr int NV = DIM + 1;   // vertices per element
   constexpr int C = DIM + 2;    // U, v, sigma  (and gamma, alpha, beta_m moments)
   extern __shared__ __align__(16) double sm[];
-  __shared__ int s_P, s_v, s_nfac, s_nif, s_ng;
+  __shared__ int s_P, s_v, s_nfac, s_nif, s_ng, s_p0;
   __shared__ double s_ttop, s_tbot, s_tc, s_ih;
   __shared__ double s_gc[tp::kMaxGroups];
   __shared__ double s_xv[DIM];
@@ -524,22 +529,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
     for (int d = 0; d < DIM; ++d) s_xv[d] = a.X[(int64_t)v * DIM + d];
     s_nfac = a.vfac_ptr[v + 1] - a.vfac_ptr[v];
     s_nif = a.ifac_ptr[v + 1] - a.ifac_ptr[v];
-    // materials by bitwise-equal c in order of first appearance; elements sorted by material
-    int ng = 0, tmp[tp::kMaxPatch];
-    for (int k = 0; k < P; ++k) {
-      const double ck = a.cK[a.star_el[p0 + k]];
-      int g = 0;
-      while (g < ng && s_gc[g] != ck) ++g;
-      if (g == ng) s_gc[ng++] = ck;
-      tmp[k] = g;
-    }
-    int pos = 0;
-    for (int g = 0; g < ng; ++g)
-      for (int k = 0; k < P; ++k)
-        if (tmp[k] == g) {
-          s_el[pos] = a.star_el[p0 + k];
-          s_grp[pos++] = g;
-        }
+    s_p0 = p0;
+    // materials by bitwise-equal c in order of first appearance (host tables)
+    const int ng = a.vert_ng[v];
+    for (int g = 0; g < ng; ++g) s_gc[g] = a.vert_gc[(int64_t)v * tp::kMaxGroups + g];
     s_ng = ng;
   }
   for (int id = tid; id < NG * nmom; id += blockDim.x) sPM[id] = R::zero();
@@ -549,7 +542,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
   const int N = ng * nb;
   const bool extra = (nfac > 0 || nif > 0);
   for (int k = tid; k < P; k += blockDim.x) {
-    const int el = s_el[k];
+    const int el = a.star_sorted[s_p0 + k];   // elements sorted by material
+    s_el[k] = el;
+    s_grp[k] = a.star_grp[s_p0 + k];
     for (int i = 0; i < NV; ++i) {
       const int vi = a.elems[(int64_t)el * NV + i];
       for (int d = 0; d < DIM; ++d) s_X[k][i][d] = a.X[(int64_t)vi * DIM + d];
@@ -652,6 +647,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
   const double ih = s_ih, tc = s_tc;
   int curk = q0 / Q;
   int curg = (q1 > q0) ? s_grp[curk] : 0;
+  // forward sweep: the top U-values of a slice that fits the keep buffer are
+  // kept for the outflow instead of being evaluated a second time
+  const bool keep = !ADJ && (q1 - q0) <= a.keep_pts;
+  T* sKeep = reinterpret_cast<T*>(sm + a.off_keep);   // keep_pts*nb  sqrt(w)-scaled top U-values
+  double* sKeepW = sm + a.off_keepw;                   // keep_pts     1 / sqrt(w)
   // element flush: G += G_K, H_m += g_{K,m} G_K;  group flush: publish G, H, Gbot of the group
   auto flush_element = [&](int k) {
     T g[DIM];
@@ -703,6 +703,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
       for (int d = 0; d < DIM; ++d) pp[1 + d] = R::from((x[d] - s_xv[d]) * ih);
       const double sw = __ldg(a.sqw + q) * s_sdet[k];
       pp[DIM + 1] = R::from(sw);
+      if (keep && side == 0) sKeepW[base - q0 + ql] = recip(sw);
       const int el = s_el[k];
       if (ADJ && side == 0) {
         // adjoint: zeta = sum_q lambda_q u_q over the top points
@@ -729,6 +730,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
       }
     }
     eval_uvalues_block<DIM, T>(a, npt, sPt, sM, sU);
+    if (keep)
+      for (int id = tid; id < nq * nb; id += blockDim.x) sKeep[(size_t)(base - q0) * nb + id] = sU[id];
     // (b) Grams of U-values: top per element (flushed into G and H_m), bottom; per material
     for (int ql = 0; ql < nq; ++ql) {
       const int k = (base + ql) / Q;
@@ -971,16 +974,19 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
   }
 
   // ---------------- phase 3: solve ----------------
-  // MIXED: binary32 LU of the equilibrated matrix D A D (D = |diag A|^-1/2),
-  // then refinement x += D (D A D)^-1 D (b - A x) with a float-float residual.
-  // binary64: direct LU (a binary32 factor + binary64 refinement was measured
-  // slower on this part, whose binary64 pipe is the bottleneck either way).
+  // Both precisions: the equilibrated matrix D A D (D = |diag A|^-1/2) is
+  // inverted in binary32 by Gauss-Jordan sweeps (two ping-pong copies, one
+  // barrier per sweep; row interchanges on Dirichlet and interface tents),
+  // then x += D F D (b - A x) with the residual in the path's precision
+  // (binary64, or float-float for MIXED) until the correction stops shrinking.
+  // binary64: a refinement that does not settle falls back to a direct LU.
   const bool pivoting = extra || ng > 1;
-  if constexpr (MIXED) {
-    float* sAL = reinterpret_cast<float*>(sm + a.off_al);   // N*N     equilibrated binary32 LU
+  bool refined = false;
+  {
+    float* sG = reinterpret_cast<float*>(sm + a.off_al);    // 2*N*N   ping-pong sweep buffers
     float* sEq = reinterpret_cast<float*>(sm + a.off_eq);   // N       equilibration scales
-    int* sPerm = reinterpret_cast<int*>(sm + a.off_perm);   // N       row interchanges
-    float* sZ = reinterpret_cast<float*>(sm + a.off_z);     // nrhs*N  correction (binary32)
+    int* sPerm = reinterpret_cast<int*>(sm + a.off_perm);   // N       pivot rows, then their composition
+    float* sZ = reinterpret_cast<float*>(sm + a.off_z);     // nrhs*N  scaled, permuted residual (binary32)
     T* sX = reinterpret_cast<T*>(sm + a.off_x);             // nrhs*N  iterate
     for (int i = tid; i < N; i += blockDim.x) {
       const float d = fabsf(R::hi(sA[i * N + i]));
@@ -988,17 +994,20 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
     }
     for (int id = tid; id < nrhs * N; id += blockDim.x) sX[id] = R::zero();
     __syncthreads();
-    for (int id = tid; id < N * N; id += blockDim.x) sAL[id] = R::hi(sA[id]) * sEq[id / N] * sEq[id % N];
+    for (int id = tid; id < N * N; id += blockDim.x) sG[id] = R::hi(sA[id]) * sEq[id / N] * sEq[id % N];
     __syncthreads();
-    // binary32 LU of D A D (row interchanges on whole rows, multipliers kept
-    // below the diagonal, reciprocal pivots in sRD)
+    // Gauss-Jordan sweeps: step k reads buffer k % 2 (rows k and pr exchanged)
+    // and writes buffer (k + 1) % 2; the final buffer holds F with
+    // (D A D)^-1 v = F (P v), P the row interchanges applied in order
     for (int k = 0; k < N; ++k) {
+      const float* S = sG + (size_t)(k & 1) * N * N;
+      float* Gn = sG + (size_t)((k + 1) & 1) * N * N;
       if (pivoting) {
         if (warp == 0) {
           float best = -1.f;
           int bi = k;
           for (int i = k + lane; i < N; i += 32) {
-            const float val = fabsf(sAL[i * N + k]);
+            const float val = fabsf(S[i * N + k]);
             if (val > best) {
               best = val;
               bi = i;
@@ -1012,43 +1021,54 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
               bi = oi;
             }
           }
-          if (lane == 0) s_piv = bi;
-        }
-        __syncthreads();
-        const int pr = s_piv;
-        if (pr != k)
-          for (int j = tid; j < N; j += blockDim.x) {
-            const float t = sAL[k * N + j];
-            sAL[k * N + j] = sAL[pr * N + j];
-            sAL[pr * N + j] = t;
+          if (lane == 0) {
+            s_piv = bi;
+            sPerm[k] = bi;
           }
-        if (tid == 0) sPerm[k] = pr;
+        }
         __syncthreads();
       } else if (tid == 0) {
         sPerm[k] = k;
       }
-      float piv = sAL[k * N + k];
-      if (!(fabsf(piv) > 0.f) || !isfinite(piv)) {
-        if (tid == 0 && rank == 0) flag_error(a, TP_ERR_SINGULAR, tent);
-        piv = 1.f;
+      const int pr = pivoting ? s_piv : k;
+      float pv = S[pr * N + k];
+      if (!(fabsf(pv) > 0.f) || !isfinite(pv)) {
+        // binary64: the refinement then fails and the direct LU decides
+        if (MIXED && tid == 0) flag_error(a, TP_ERR_SINGULAR, tent);
+        pv = 1.f;
       }
-      const float rp = 1.f / piv;
-      const int rem = N - k - 1;
-      for (int id = tid; id < rem * rem; id += blockDim.x) {
-        const int i = k + 1 + id / rem, j = k + 1 + id % rem;
-        sAL[i * N + j] = fmaf(-sAL[i * N + k] * rp, sAL[k * N + j], sAL[i * N + j]);
+      const float rp = __frcp_rn(pv);
+      for (int i = warp; i < N; i += kThreads / 32) {   // rows over warps, columns over lanes
+        const int si = (i == k) ? pr : (i == pr ? k : i);
+        const float lik = -S[si * N + k] * rp;
+        for (int j = lane; j < N; j += 32) {
+          float g;
+          if (i == k) g = (j == k) ? rp : S[pr * N + j] * rp;
+          else if (j == k) g = lik;
+          else g = fmaf(lik, S[pr * N + j], S[si * N + j]);
+          Gn[i * N + j] = g;
+        }
       }
-      __syncthreads();
-      for (int i = k + 1 + tid; i < N; i += blockDim.x) sAL[i * N + k] *= rp;
-      if (tid == 0) sRD[k] = (double)rp;
       __syncthreads();
     }
-    // refinement: r = b - A x (float-float), z = (D A D)^-1 D r, x += D z
+    const float* F = sG + (size_t)(N & 1) * N * N;
+    if (tid == 0) {   // composition of the interchanges: (P v)_j = v[sPerm[j]]
+      int* idx = reinterpret_cast<int*>(sRD);   // scratch (the LU's reciprocal pivots are not live here)
+      for (int j = 0; j < N; ++j) idx[j] = j;
+      for (int k = 0; k < N; ++k) {
+        const int q = sPerm[k], t = idx[k];
+        idx[k] = idx[q];
+        idx[q] = t;
+      }
+      for (int j = 0; j < N; ++j) sPerm[j] = idx[j];
+    }
+    __syncthreads();
+    // refinement
     float prev = 3.4e38f;
     const int maxit = kMaxRefine;
-    if (tid == 0) s_conv = 0;
     for (int it = 0; it < maxit; ++it) {
-      // r = b - A x, each row split over 8 lanes of one warp
+      // residual b - A x, each row split over 8 lanes of one warp; stored
+      // scaled by D in binary32
       for (int base8 = 0; base8 < nrhs * N * 8; base8 += blockDim.x) {
         const int id = base8 + tid, item = id >> 3, sub = id & 7;
         T t = R::zero();
@@ -1070,40 +1090,23 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
         if (sub == 0 && item < nrhs * N) sZ[item] = sEq[item % N] * R::hi(R::add(sb[item], t));
       }
       __syncthreads();
-      if (warp == 0) {
-        for (int r = 0; r < nrhs; ++r) {
-          float* z = sZ + (size_t)r * N;
-          if (lane == 0)   // row interchanges in factorisation order (L is stored permuted)
-            for (int k = 0; k < N; ++k) {
-              const int pr = sPerm[k];
-              if (pr != k) {
-                const float t = z[k];
-                z[k] = z[pr];
-                z[pr] = t;
-              }
-            }
-          __syncwarp();
-          for (int k = 0; k < N; ++k) {   // L (unit lower)
-            const float zk = z[k];
-            for (int i = k + 1 + lane; i < N; i += 32) z[i] = fmaf(-sAL[i * N + k], zk, z[i]);
-            __syncwarp();
-          }
-          for (int k = N - 1; k >= 0; --k) {   // U
-            if (lane == 0) z[k] = z[k] * (float)sRD[k];
-            __syncwarp();
-            const float zk = z[k];
-            for (int i = lane; i < k; i += 32) z[i] = fmaf(-sAL[i * N + k], zk, z[i]);
-            __syncwarp();
-          }
-        }
-      }
-      __syncthreads();
+      // x += D F (P r), each row split over 8 lanes
       float dmax = 0.f, xmax = 0.f;
-      for (int id = tid; id < nrhs * N; id += blockDim.x) {
-        const float dx = sEq[id % N] * sZ[id];
-        sX[id] = R::addf(sX[id], dx);
-        dmax = fmaxf(dmax, fabsf(dx));
-        xmax = fmaxf(xmax, fabsf(R::hi(sX[id])));
+      for (int base8 = 0; base8 < nrhs * N * 8; base8 += blockDim.x) {
+        const int id = base8 + tid, item = id >> 3, sub = id & 7;
+        float z = 0.f;
+        if (item < nrhs * N) {
+          const int r = item / N, i = item % N;
+          const float* zr = sZ + (size_t)r * N;
+          for (int j = sub; j < N; j += 8) z = fmaf(F[i * N + j], zr[sPerm[j]], z);
+        }
+        for (int o = 4; o > 0; o >>= 1) z += __shfl_xor_sync(0xffffffffu, z, o);
+        if (sub == 0 && item < nrhs * N) {
+          const float dx = sEq[item % N] * z;
+          sX[item] = R::addf(sX[item], dx);
+          dmax = fmaxf(dmax, fabsf(dx));
+          xmax = fmaxf(xmax, fabsf(R::hi(sX[item])));
+        }
       }
       for (int o = 16; o > 0; o >>= 1) {
         dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
@@ -1114,33 +1117,36 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
         s_red[1][warp] = xmax;
       }
       __syncthreads();
-      if (tid == 0) {
-        float dm = 0.f, xm = 0.f;
-        for (int w = 0; w < kThreads / 32; ++w) {
-          dm = fmaxf(dm, s_red[0][w]);
-          xm = fmaxf(xm, s_red[1][w]);
-        }
-        // stop once the correction is at the float-float resolution, or once it
-        // stops shrinking below 1e-10 of the solution (the float-float residual
-        // then limits the accuracy); a correction above 1e-8 of the solution
-        // after kMaxRefine steps is reported
-        const float tiny = 4e-15f, floor_ = 1e-10f;
-        const bool done = (dm <= tiny * xm) || (it >= 2 && dm > 0.5f * prev && dm <= floor_ * xm);
-        s_stop = done ? 1 : 0;
-        if (done) s_conv = 1;
-        if (!done && it == maxit - 1 && dm > 1e-8f * xm && rank == 0) flag_error(a, TP_ERR_NOCONV, tent);
-        s_red[0][0] = dm;
+      float dm = 0.f, xm = 0.f;
+      for (int w = 0; w < kThreads / 32; ++w) {
+        dm = fmaxf(dm, s_red[0][w]);
+        xm = fmaxf(xm, s_red[1][w]);
       }
-      __syncthreads();
-      prev = s_red[0][0];
-      const int stop = s_stop;
-      __syncthreads();
-      if (stop) break;
+      // stop once the correction is at the resolution of the residual's
+      // precision, or once it stops shrinking at a small level (the residual's
+      // rounding then limits the accuracy)
+      const float tiny = MIXED ? 4e-15f : 2.5e-16f, floor_ = MIXED ? 1e-10f : 1e-12f;
+      if (!(isfinite(dm) && isfinite(xm))) {
+        if (MIXED && tid == 0) flag_error(a, TP_ERR_NOCONV, tent);
+        break;
+      }
+      const bool done = dm <= tiny * xm || (it >= 2 && dm > 0.5f * prev && dm <= floor_ * xm);
+      prev = dm;
+      if (done) {
+        refined = true;
+        break;
+      }
+      if (MIXED && it == maxit - 1 && dm > 1e-8f * xm && tid == 0) flag_error(a, TP_ERR_NOCONV, tent);
+      __syncthreads();   // every thread has read s_red before the next iteration writes it
     }
-    for (int id = tid; id < nrhs * N; id += blockDim.x) sb[id] = sX[id];
-    __syncthreads();
+    if (MIXED || refined) {
+      __syncthreads();
+      for (int id = tid; id < nrhs * N; id += blockDim.x) sb[id] = sX[id];
+      __syncthreads();
+    }
   }
   if constexpr (!MIXED) {
+  if (!refined) {   // direct binary64 LU
     __syncthreads();
     double* sXd = reinterpret_cast<double*>(sm + a.off_x);   // nrhs*N  solution during back substitution
     auto pivot_recip = [&](double piv, int k) {
@@ -1247,6 +1253,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
     }
     for (int id = tid; id < nrhs * N; id += blockDim.x) sb[id] = sXd[id];
   }
+  }
   }   // rank 0
   cluster.sync();   // the solution is in rank 0's b
   if (rank != 0)
@@ -1264,8 +1271,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
     else t = R::mul(R::from(cc == 1 ? s_gc[g] * ih : -ih), relT_apply<DIM, T>(a, kk, cc - 1, xg));
     sY[id] = t;
   }
+  __syncthreads();
   for (int base = q0; base < q1; base += 2 * CH) {
     const int nq = min(2 * CH, q1 - base);
+    if (!keep) {
     for (int id = tid; id < nq; id += blockDim.x) {
       const int qg = base + id, k = qg / Q, q = qg % Q;
       const double cg = s_gc[s_grp[k]];
@@ -1282,15 +1291,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
       pp[DIM + 1] = R::one();
     }
     eval_uvalues_block<DIM, T, false>(a, nq, sPt, sM, sU);
+    }
     if constexpr (!ADJ) {
       for (int id = tid; id < nq * nrhs * C; id += blockDim.x) {
         const int ql = id / (nrhs * C), rc = id % (nrhs * C), r = rc / C, cc = rc % C;
         const int qg = base + ql, k = qg / Q, q = qg % Q;
-        const T* u = sU + (size_t)ql * nb;
+        const T* u = keep ? sKeep + (size_t)(base - q0 + ql) * nb : sU + (size_t)ql * nb;
         const T* y = sY + (size_t)s_grp[k] * nmom + ((size_t)r * C + cc) * nb;
         T t = R::zero();
         for (int j = 0; j < nb; ++j) t = R::fma(y[j], u[j], t);
-        a.front[(((int64_t)r * a.ne + s_el[k]) * Q + q) * C + cc] = R::to(t);
+        const double val = keep ? R::to(t) * sKeepW[base - q0 + ql] : R::to(t);
+        a.front[(((int64_t)r * a.ne + s_el[k]) * Q + q) * C + cc] = val;
       }
     } else {
       // lambda_bot = w (s0, c^-2 s_t - g_b.s, s_m - g_b,m s_t)
