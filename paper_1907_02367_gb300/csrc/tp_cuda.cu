@@ -556,7 +556,7 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
   const int nb = ctx->nb, C = ctx->C;
   const int npair = nb * (nb + 1) / 2;
   if (npair > kMaxPair * kThreads) {
-    tp::set_error("tp_create: dim U^p too large for this kernel (nb (nb+1)/2 > 1024)");
+    tp::set_error("tp_create: dim U^p too large for this kernel (more than 38)");
     return fail(TP_ERR_UNSUPPORTED);
   }
   a.mono_stride = ctx->nmono | 1;

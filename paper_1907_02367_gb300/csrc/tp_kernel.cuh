@@ -17,7 +17,7 @@ namespace cg = cooperative_groups;
 namespace tp {
 
 constexpr int kThreads = 256;
-constexpr int kMaxPair = 4;      // Gram pairs per thread (nb (nb+1)/2 <= 4 * 256)
+constexpr int kMaxPair = 3;      // Gram pairs per thread (nb (nb+1)/2 <= 3 * 256: dim U^p <= 38)
 constexpr int kMaxRefine = 40;   // refinement steps of the mixed path
 constexpr long long kMaxSpin = 1LL << 20;   // bounded dependency wait (~0.15 s; then TP_ERR_TIMEOUT)
 
@@ -452,6 +452,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
   __shared__ int s_fg[tp::kMaxFacets], s_fg2[tp::kMaxFacets];   // groups (Dirichlet: one; interface: +, -)
   __shared__ int s_pgrp[2 * 64];
   __shared__ int s_piv;
+  __shared__ float s_prow[2][32], s_xrow[2][32], s_cval[kThreads / 32];   // register sweeps: pivot rows
+  __shared__ int s_cidx[kThreads / 32];
   __shared__ float s_red[2][kThreads / 32];
   __shared__ int s_stop, s_conv;
 
@@ -994,62 +996,140 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
     }
     for (int id = tid; id < nrhs * N; id += blockDim.x) sX[id] = R::zero();
     __syncthreads();
-    for (int id = tid; id < N * N; id += blockDim.x) sG[id] = R::hi(sA[id]) * sEq[id / N] * sEq[id % N];
-    __syncthreads();
-    // Gauss-Jordan sweeps: step k reads buffer k % 2 (rows k and pr exchanged)
-    // and writes buffer (k + 1) % 2; the final buffer holds F with
-    // (D A D)^-1 v = F (P v), P the row interchanges applied in order
-    for (int k = 0; k < N; ++k) {
-      const float* S = sG + (size_t)(k & 1) * N * N;
-      float* Gn = sG + (size_t)((k + 1) & 1) * N * N;
-      if (pivoting) {
-        if (warp == 0) {
+    // register path (N <= 32): row warp + 8 s of the sweep matrix in gr[s],
+    // column = lane; the pivot row goes through shared memory, the pivot
+    // column through warp shuffles
+    const bool regs = N <= 32;
+    float gr[4];
+    auto gsel = [&](int s_) { return s_ == 0 ? gr[0] : s_ == 1 ? gr[1] : s_ == 2 ? gr[2] : gr[3]; };
+    auto gset = [&](int s_, float v_) {
+      if (s_ == 0) gr[0] = v_;
+      else if (s_ == 1) gr[1] = v_;
+      else if (s_ == 2) gr[2] = v_;
+      else gr[3] = v_;
+    };
+    if (regs) {
+#pragma unroll
+      for (int s_ = 0; s_ < 4; ++s_) {
+        const int i = warp + 8 * s_;
+        gr[s_] = (i < N && lane < N) ? R::hi(sA[i * N + lane]) * sEq[i] * sEq[lane] : 0.f;
+      }
+      for (int k = 0; k < N; ++k) {
+        const int wk = k & 7, sk = k >> 3;
+        if (pivoting) {
+          // largest |a_ik|, i >= k: each warp's candidates, then all warps'
           float best = -1.f;
           int bi = k;
-          for (int i = k + lane; i < N; i += 32) {
-            const float val = fabsf(S[i * N + k]);
-            if (val > best) {
-              best = val;
+#pragma unroll
+          for (int s_ = 0; s_ < 4; ++s_) {
+            const int i = warp + 8 * s_;
+            const float v_ = fabsf(__shfl_sync(0xffffffffu, gr[s_], k));
+            if (i >= k && i < N && v_ > best) {
+              best = v_;
               bi = i;
             }
           }
-          for (int o = 16; o > 0; o >>= 1) {
-            const float ob = __shfl_down_sync(0xffffffffu, best, o);
-            const int oi = __shfl_down_sync(0xffffffffu, bi, o);
-            if (ob > best || (ob == best && oi < bi)) {
-              best = ob;
-              bi = oi;
+          if (lane == 0) {
+            s_cval[warp] = best;
+            s_cidx[warp] = bi;
+          }
+          __syncthreads();
+          int pr = k;
+          float bv = -1.f;
+          for (int w = 0; w < kThreads / 32; ++w)
+            if (s_cval[w] > bv || (s_cval[w] == bv && s_cidx[w] < pr)) {
+              bv = s_cval[w];
+              pr = s_cidx[w];
+            }
+          if (tid == 0) sPerm[k] = pr;
+          if (pr != k) {   // exchange rows k and pr
+            const int wp = pr & 7, sp = pr >> 3;
+            if (warp == wk) s_xrow[0][lane] = gsel(sk);
+            if (warp == wp) s_xrow[1][lane] = gsel(sp);
+            __syncthreads();
+            if (warp == wk) gset(sk, s_xrow[1][lane]);
+            if (warp == wp) gset(sp, s_xrow[0][lane]);
+          }
+        } else if (tid == 0) {
+          sPerm[k] = k;
+        }
+        if (warp == wk) {   // pivot row, normalised
+          const float rowv = gsel(sk);
+          float akk = __shfl_sync(0xffffffffu, rowv, k);
+          if (!(fabsf(akk) > 0.f) || !isfinite(akk)) {
+            if (MIXED && lane == 0) flag_error(a, TP_ERR_SINGULAR, tent);
+            akk = 1.f;
+          }
+          const float rp = __frcp_rn(akk);
+          s_prow[k & 1][lane] = (lane == k) ? rp : rowv * rp;
+        }
+        __syncthreads();
+        const float pj = s_prow[k & 1][lane];
+#pragma unroll
+        for (int s_ = 0; s_ < 4; ++s_) {
+          const int i = warp + 8 * s_;
+          const float aik = __shfl_sync(0xffffffffu, gr[s_], k);
+          gr[s_] = (i == k) ? pj : fmaf(-aik, pj, lane == k ? 0.f : gr[s_]);
+        }
+      }
+    } else {
+      for (int id = tid; id < N * N; id += blockDim.x) sG[id] = R::hi(sA[id]) * sEq[id / N] * sEq[id % N];
+      __syncthreads();
+      // Gauss-Jordan sweeps: step k reads buffer k % 2 (rows k and pr exchanged)
+      // and writes buffer (k + 1) % 2; the final buffer holds F with
+      // (D A D)^-1 v = F (P v), P the row interchanges applied in order
+      for (int k = 0; k < N; ++k) {
+        const float* S = sG + (size_t)(k & 1) * N * N;
+        float* Gn = sG + (size_t)((k + 1) & 1) * N * N;
+        if (pivoting) {
+          if (warp == 0) {
+            float best = -1.f;
+            int bi = k;
+            for (int i = k + lane; i < N; i += 32) {
+              const float val = fabsf(S[i * N + k]);
+              if (val > best) {
+                best = val;
+                bi = i;
+              }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+              const float ob = __shfl_down_sync(0xffffffffu, best, o);
+              const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+              if (ob > best || (ob == best && oi < bi)) {
+                best = ob;
+                bi = oi;
+              }
+            }
+            if (lane == 0) {
+              s_piv = bi;
+              sPerm[k] = bi;
             }
           }
-          if (lane == 0) {
-            s_piv = bi;
-            sPerm[k] = bi;
+          __syncthreads();
+        } else if (tid == 0) {
+          sPerm[k] = k;
+        }
+        const int pr = pivoting ? s_piv : k;
+        float pv = S[pr * N + k];
+        if (!(fabsf(pv) > 0.f) || !isfinite(pv)) {
+          // binary64: the refinement then fails and the direct LU decides
+          if (MIXED && tid == 0) flag_error(a, TP_ERR_SINGULAR, tent);
+          pv = 1.f;
+        }
+        const float rp = __frcp_rn(pv);
+        for (int i = warp; i < N; i += kThreads / 32) {   // rows over warps, columns over lanes
+          const int si = (i == k) ? pr : (i == pr ? k : i);
+          const float lik = -S[si * N + k] * rp;
+          for (int j = lane; j < N; j += 32) {
+            float g;
+            if (i == k) g = (j == k) ? rp : S[pr * N + j] * rp;
+            else if (j == k) g = lik;
+            else g = fmaf(lik, S[pr * N + j], S[si * N + j]);
+            Gn[i * N + j] = g;
           }
         }
         __syncthreads();
-      } else if (tid == 0) {
-        sPerm[k] = k;
       }
-      const int pr = pivoting ? s_piv : k;
-      float pv = S[pr * N + k];
-      if (!(fabsf(pv) > 0.f) || !isfinite(pv)) {
-        // binary64: the refinement then fails and the direct LU decides
-        if (MIXED && tid == 0) flag_error(a, TP_ERR_SINGULAR, tent);
-        pv = 1.f;
-      }
-      const float rp = __frcp_rn(pv);
-      for (int i = warp; i < N; i += kThreads / 32) {   // rows over warps, columns over lanes
-        const int si = (i == k) ? pr : (i == pr ? k : i);
-        const float lik = -S[si * N + k] * rp;
-        for (int j = lane; j < N; j += 32) {
-          float g;
-          if (i == k) g = (j == k) ? rp : S[pr * N + j] * rp;
-          else if (j == k) g = lik;
-          else g = fmaf(lik, S[pr * N + j], S[si * N + j]);
-          Gn[i * N + j] = g;
-        }
-      }
-      __syncthreads();
     }
     const float* F = sG + (size_t)(N & 1) * N * N;
     if (tid == 0) {   // composition of the interchanges: (P v)_j = v[sPerm[j]]
@@ -1090,9 +1170,28 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
         if (sub == 0 && item < nrhs * N) sZ[item] = sEq[item % N] * R::hi(R::add(sb[item], t));
       }
       __syncthreads();
-      // x += D F (P r), each row split over 8 lanes
+      // x += D F (P r): register path, one row per (warp, slot), summed over lanes
       float dmax = 0.f, xmax = 0.f;
-      for (int base8 = 0; base8 < nrhs * N * 8; base8 += blockDim.x) {
+      if (regs) {
+        for (int r = 0; r < nrhs; ++r) {
+          const float vj = (lane < N) ? sZ[(size_t)r * N + sPerm[lane]] : 0.f;
+#pragma unroll
+          for (int s_ = 0; s_ < 4; ++s_) {
+            const int i = warp + 8 * s_;
+            float z = gr[s_] * vj;
+            for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(0xffffffffu, z, o);
+            if (i < N && lane == s_) {
+              const float dx = sEq[i] * z;
+              const size_t o_ = (size_t)r * N + i;
+              sX[o_] = R::addf(sX[o_], dx);
+              dmax = fmaxf(dmax, fabsf(dx));
+              xmax = fmaxf(xmax, fabsf(R::hi(sX[o_])));
+            }
+          }
+        }
+      }
+      // shared-memory path: each row split over 8 lanes
+      for (int base8 = 0; base8 < (regs ? 0 : nrhs * N * 8); base8 += blockDim.x) {
         const int id = base8 + tid, item = id >> 3, sub = id & 7;
         float z = 0.f;
         if (item < nrhs * N) {
@@ -1137,7 +1236,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
         break;
       }
       if (MIXED && it == maxit - 1 && dm > 1e-8f * xm && tid == 0) flag_error(a, TP_ERR_NOCONV, tent);
-      __syncthreads();   // every thread has read s_red before the next iteration writes it
+      // (the next iteration writes s_red only after its first barrier)
     }
     if (MIXED || refined) {
       __syncthreads();
