@@ -242,16 +242,6 @@ __device__ __forceinline__ dd Ar<dd>::coef(const KArgs& a, int e) {
   return {c.x, c.y};
 }
 
-// U-value of basis function j: sum over its sparse monomial entries
-template <int DIM, typename T>
-__device__ __forceinline__ T sp_eval(const KArgs& a, int j, const T* m) {
-  constexpr int C = DIM + 2;
-  const int e0 = __ldg(a.sp_ptr + j * C), e1 = __ldg(a.sp_ptr + j * C + 1);
-  T s = Ar<T>::zero();
-  for (int e = e0; e < e1; ++e) s = Ar<T>::fma(Ar<T>::coef(a, e), m[__ldg(a.sp_mono + e)], s);
-  return s;
-}
-
 // U-values at npt points with the whole block: the points' (that, xhat_1..xhat_n,
 // scale) are in pt[q * (DIM + 2)]; one pass per monomial degree (m = parent
 // monomial times one variable), then the sparse sums u_j = scale * sum c m.
@@ -260,21 +250,45 @@ __device__ __forceinline__ T sp_eval(const KArgs& a, int j, const T* m) {
 // are separated from them by barriers.
 template <int DIM, typename T, bool SCALE = true>
 __device__ __forceinline__ void eval_uvalues_block(const KArgs& a, int npt, const T* pt, T* m, T* u) {
+  // Each thread takes one monomial (one basis function) at four points, so
+  // that four independent products are in flight per table lookup.
   const int tid = threadIdx.x, ms = a.mono_stride, nb = a.nb;
+  const int nq4 = (npt + 3) >> 2;
   for (int q = tid; q < npt; q += blockDim.x) m[q * ms] = Ar<T>::one();
   for (int d = 1; d <= a.p; ++d) {
     __syncthreads();   // pt, and the monomials of degree d - 1
     const int g0 = a.mono_lv[d], cnt = a.mono_lv[d + 1] - g0;
-    for (int id = tid; id < npt * cnt; id += blockDim.x) {
-      const int q = id / cnt, g = g0 + id % cnt;
-      m[q * ms + g] = Ar<T>::mul(m[q * ms + __ldg(a.mono_parent + g)], pt[q * (DIM + 2) + __ldg(a.mono_var + g)]);
+    for (int id = tid; id < cnt * nq4; id += blockDim.x) {
+      const int g = g0 + id % cnt, q0 = (id / cnt) << 2;
+      const int par = __ldg(a.mono_parent + g), vr = __ldg(a.mono_var + g);
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int q = min(q0 + t, npt - 1);
+        const T v = Ar<T>::mul(m[q * ms + par], pt[q * (DIM + 2) + vr]);
+        if (q0 + t < npt) m[q * ms + g] = v;
+      }
     }
   }
   __syncthreads();
-  for (int id = tid; id < npt * nb; id += blockDim.x) {
-    const int q = id / nb, j = id % nb;
-    const T v = sp_eval<DIM, T>(a, j, m + q * ms);
-    u[q * nb + j] = SCALE ? Ar<T>::mul(pt[q * (DIM + 2) + DIM + 1], v) : v;
+  for (int id = tid; id < nb * nq4; id += blockDim.x) {
+    const int j = id % nb, q0 = (id / nb) << 2;
+    const int e0 = __ldg(a.sp_ptr + j * (DIM + 2)), e1 = __ldg(a.sp_ptr + j * (DIM + 2) + 1);
+    int qq[4];
+    T acc[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      qq[t] = min(q0 + t, npt - 1);
+      acc[t] = Ar<T>::zero();
+    }
+    for (int e = e0; e < e1; ++e) {
+      const T c = Ar<T>::coef(a, e);
+      const int g = __ldg(a.sp_mono + e);
+#pragma unroll
+      for (int t = 0; t < 4; ++t) acc[t] = Ar<T>::fma(c, m[qq[t] * ms + g], acc[t]);
+    }
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+      if (q0 + t < npt) u[qq[t] * nb + j] = SCALE ? Ar<T>::mul(pt[qq[t] * (DIM + 2) + DIM + 1], acc[t]) : acc[t];
   }
   __syncthreads();
 }
@@ -455,7 +469,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
   __shared__ float s_prow[2][32], s_xrow[2][32], s_cval[kThreads / 32];   // register sweeps: pivot rows
   __shared__ int s_cidx[kThreads / 32];
   __shared__ float s_red[2][kThreads / 32];
-  __shared__ int s_stop, s_conv;
 
   __shared__ int s_tent;
   cg::cluster_group cluster = cg::this_cluster();
@@ -921,12 +934,25 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
     }
     return t;
   };
+  // reduce-scatter: rank r sums its share of every array over the cluster and
+  // stores the sums into every CTA's copy
+  auto cluster_reduce = [&](T* part, T* sum, int n) {
+    const int lo = (n * rank) / CS, hi = (n * (rank + 1)) / CS;
+    for (int id = lo + tid; id < hi; id += blockDim.x) {
+      const T t = cluster_sum(part, id);
+      for (int rr = 0; rr < CS; ++rr) cluster.map_shared_rank(sum, rr)[id] = t;
+    }
+  };
   cluster.sync();
   // layout [G (NG*npair) | H_m (NG*DIM*npair) | Gbot (NG*npair)]; unused groups hold zeros
-  for (int id = tid; id < NG * (DIM + 2) * npair; id += blockDim.x) sSG[id] = cluster_sum(sPG, id);
-  for (int id = tid; id < ng * nmom; id += blockDim.x) sSM[id] = cluster_sum(sPM, id);
-  for (int id = tid; id < N * N; id += blockDim.x) sA[id] = extra ? cluster_sum(sPD, id) : R::zero();
-  for (int id = tid; id < nrhs * N; id += blockDim.x) sb[id] = nfac > 0 ? cluster_sum(sPBD, id) : R::zero();
+  cluster_reduce(sPG, sSG, NG * (DIM + 2) * npair);
+  cluster_reduce(sPM, sSM, ng * nmom);
+  if (extra) cluster_reduce(sPD, sA, N * N);
+  else
+    for (int id = tid; id < N * N; id += blockDim.x) sA[id] = R::zero();
+  if (nfac > 0) cluster_reduce(sPBD, sb, nrhs * N);
+  else
+    for (int id = tid; id < nrhs * N; id += blockDim.x) sb[id] = R::zero();
   cluster.sync();   // no CTA leaves or reuses its partials while another still reads them
   // congruence: rank r forms rows [N r / CS, N (r + 1) / CS) of A and b and
   // stores them into rank 0's A and b; rank 0 alone solves.  Every CTA holds
@@ -1000,7 +1026,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
     // column = lane; the pivot row goes through shared memory, the pivot
     // column through warp shuffles
     const bool regs = N <= 32;
-    float gr[4];
+    float gr[4] = {0.f, 0.f, 0.f, 0.f};
     auto gsel = [&](int s_) { return s_ == 0 ? gr[0] : s_ == 1 ? gr[1] : s_ == 2 ? gr[2] : gr[3]; };
     auto gset = [&](int s_, float v_) {
       if (s_ == 0) gr[0] = v_;
@@ -1229,7 +1255,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
         if (MIXED && tid == 0) flag_error(a, TP_ERR_NOCONV, tent);
         break;
       }
-      const bool done = dm <= tiny * xm || (it >= 2 && dm > 0.5f * prev && dm <= floor_ * xm);
+      // (the next correction is predicted as dm * (dm / prev) once the
+      // corrections shrink fast; stop when that is below the resolution too)
+      const bool done = dm <= tiny * xm || (it >= 2 && dm > 0.5f * prev && dm <= floor_ * xm) ||
+                        (it >= 2 && dm <= 0.01f * prev && 4.f * dm * (dm / prev) <= tiny * xm);
       prev = dm;
       if (done) {
         refined = true;
