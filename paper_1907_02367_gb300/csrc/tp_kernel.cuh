@@ -457,6 +457,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
   __shared__ double s_gc[tp::kMaxGroups];
   __shared__ double s_xv[DIM];
   __shared__ int s_el[tp::kMaxPatch], s_grp[tp::kMaxPatch];
+  __shared__ int s_vid[tp::kMaxPatch][NV], s_fw[tp::kMaxFacets][NV];   // vertex ids of elements, facets
   __shared__ double s_X[tp::kMaxPatch][NV][DIM];
   __shared__ double s_tb[tp::kMaxPatch][NV], s_tt[tp::kMaxPatch][NV];
   __shared__ double s_gb[tp::kMaxPatch][DIM], s_gt[tp::kMaxPatch][DIM];
@@ -484,24 +485,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
     tent = *cluster.map_shared_rank(&s_tent, 0);
     cluster.sync();   // every CTA has read the tent index of rank 0
     if (tent >= a.tent_end) break;
-    if (rank == 0) {
-      const int d0 = a.dep_ptr[tent], d1 = a.dep_ptr[tent + 1];
-      for (int e = d0 + tid; e < d1; e += blockDim.x) {
-        const int w = a.dep_vert[e], need = a.dep_need[e];
-        long long spins = 0;
-        while (ld_acquire(a.done + w) < need) {
-          if (++spins > kMaxSpin) {
-            flag_error(a, TP_ERR_TIMEOUT, tent);
-            break;
-          }
-          // once any tent has flagged an error the sweep's result is void:
-          // stop waiting so that the launch ends promptly
-          if ((spins & 255) == 0 && ld_acquire(a.status) != 0) break;
-          __nanosleep(128);
-        }
-      }
-    }
-    cluster.sync();
   } else {
     tent = tent0 + blockIdx.x / CS;
   }
@@ -531,6 +514,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
   double* sRD = sm + a.off_rd;                       // N          reciprocal pivots (binary64 path)
 
   // ---------------- phase 0: tent, materials and patch geometry ----------------
+  // (a) what does not depend on earlier tents: vertex star, coordinates,
+  // materials, facets; in the dataflow sweep it is fetched while the tents
+  // this one depends on may still be running
   if (tid == 0) {
     const int v = a.tent_v[tent];
     s_v = v;
@@ -538,8 +524,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
     const int P = p1 - p0;
     s_P = P;
     s_ttop = a.tent_ttop[tent];
-    s_tbot = ADJ ? a.tent_tbot[tent] : __ldcg(a.tau + v);
-    s_tc = 0.5 * (s_tbot + s_ttop);
     s_ih = 1.0 / a.tent_h[tent];
     for (int d = 0; d < DIM; ++d) s_xv[d] = a.X[(int64_t)v * DIM + d];
     s_nfac = a.vfac_ptr[v + 1] - a.vfac_ptr[v];
@@ -562,9 +546,79 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
     s_grp[k] = a.star_grp[s_p0 + k];
     for (int i = 0; i < NV; ++i) {
       const int vi = a.elems[(int64_t)el * NV + i];
+      s_vid[k][i] = vi;
       for (int d = 0; d < DIM; ++d) s_X[k][i][d] = a.X[(int64_t)vi * DIM + d];
-      const double tv = __ldcg(a.tau + vi);
-      s_tb[k][i] = (vi == v) ? s_tbot : tv;
+    }
+  }
+  // vertical face simplices (x_v, t_bot), (x_v, t_top), (x_w, tau_w): Dirichlet facets
+  // first, then the time-like interface facets
+  for (int f = tid; f < nfac + nif; f += blockDim.x) {
+    const bool dir = f < nfac;
+    const int fid = dir ? a.vfac[a.vfac_ptr[v] + f] : a.ifac_ptr[v] + (f - nfac);
+    const int* fv = dir ? a.facet_vert + (int64_t)fid * DIM : a.ifac_vert + (int64_t)fid * DIM;
+    const double* fn = dir ? a.facet_nrm + (int64_t)fid * DIM : a.ifac_nrm + (int64_t)fid * DIM;
+    for (int d = 0; d < DIM; ++d) {
+      s_fP[f][0][d] = a.X[(int64_t)v * DIM + d];
+      s_fP[f][1][d] = a.X[(int64_t)v * DIM + d];
+      s_fn[f][d] = fn[d];
+    }
+    int c2 = 2;
+    for (int i = 0; i < DIM; ++i) {
+      const int w = fv[i];
+      if (w == v) continue;
+      for (int d = 0; d < DIM; ++d) s_fP[f][c2][d] = a.X[(int64_t)w * DIM + d];
+      s_fw[f][c2] = w;
+      ++c2;
+    }
+    // groups of the facet's element(s), found by their wave speed
+    auto group_of = [&](int el) {
+      const double ce = a.cK[el];
+      int g = 0;
+      while (g < ng - 1 && s_gc[g] != ce) ++g;
+      return g;
+    };
+    if (dir) {
+      s_fg[f] = group_of(a.facet_elem[fid]);
+      s_fg2[f] = s_fg[f];
+    } else {
+      s_fg[f] = group_of(a.ifac_kp[fid]);
+      s_fg2[f] = group_of(a.ifac_km[fid]);
+    }
+  }
+  if constexpr (PERSIST) {
+    // the earlier tents of this vertex and its neighbours must be complete
+    if (rank == 0) {
+      const int d0 = a.dep_ptr[tent], d1 = a.dep_ptr[tent + 1];
+      for (int e = d0 + tid; e < d1; e += blockDim.x) {
+        const int w = a.dep_vert[e], need = a.dep_need[e];
+        long long spins = 0;
+        while (ld_acquire(a.done + w) < need) {
+          if (++spins > kMaxSpin) {
+            flag_error(a, TP_ERR_TIMEOUT, tent);
+            break;
+          }
+          // once any tent has flagged an error the sweep's result is void:
+          // stop waiting so that the launch ends promptly
+          if ((spins & 255) == 0 && ld_acquire(a.status) != 0) break;
+          __nanosleep(128);
+        }
+      }
+    }
+    cluster.sync();
+  } else {
+    __syncthreads();
+  }
+  // (b) the front times: bottom and top fronts over every element, causality
+  const double tbot = ADJ ? a.tent_tbot[tent] : __ldcg(a.tau + v);
+  if (tid == 0) {
+    s_tbot = tbot;
+    s_tc = 0.5 * (tbot + s_ttop);
+  }
+  for (int k = tid; k < P; k += blockDim.x) {
+    for (int i = 0; i < NV; ++i) {
+      const int vi = s_vid[k][i];
+      const double tv = (vi == v) ? tbot : __ldcg(a.tau + vi);
+      s_tb[k][i] = tv;
       s_tt[k][i] = (vi == v) ? s_ttop : tv;
     }
     double e[DIM][DIM], db[DIM], dt[DIM];
@@ -586,51 +640,19 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
     const double ck = s_gc[s_grp[k]];
     if (!(1.0 / (ck * ck) - g2 > 0.0)) flag_error(a, TP_ERR_CAUSALITY, tent);   // space-like top face
   }
-  // vertical face simplices (x_v, t_bot), (x_v, t_top), (x_w, tau_w): Dirichlet facets
-  // first, then the time-like interface facets
   for (int f = tid; f < nfac + nif; f += blockDim.x) {
-    const bool dir = f < nfac;
-    const int fid = dir ? a.vfac[a.vfac_ptr[v] + f] : a.ifac_ptr[v] + (f - nfac);
-    const int* fv = dir ? a.facet_vert + (int64_t)fid * DIM : a.ifac_vert + (int64_t)fid * DIM;
-    const double* fn = dir ? a.facet_nrm + (int64_t)fid * DIM : a.ifac_nrm + (int64_t)fid * DIM;
-    for (int d = 0; d < DIM; ++d) {
-      s_fP[f][0][d] = a.X[(int64_t)v * DIM + d];
-      s_fP[f][1][d] = a.X[(int64_t)v * DIM + d];
-      s_fn[f][d] = fn[d];
-    }
-    s_fP[f][0][DIM] = s_tbot;
+    s_fP[f][0][DIM] = tbot;
     s_fP[f][1][DIM] = s_ttop;
-    int c2 = 2;
-    for (int i = 0; i < DIM; ++i) {
-      const int w = fv[i];
-      if (w == v) continue;
-      for (int d = 0; d < DIM; ++d) s_fP[f][c2][d] = a.X[(int64_t)w * DIM + d];
-      s_fP[f][c2][DIM] = __ldcg(a.tau + w);
-      ++c2;
-    }
+    for (int c2 = 2; c2 <= DIM; ++c2) s_fP[f][c2][DIM] = __ldcg(a.tau + s_fw[f][c2]);
     // n! * n-volume = sqrt(det(E^T E)), E = [P_i - P_0] ((n+1) x n)
     double G[DIM][DIM];
     for (int i = 0; i < DIM; ++i)
       for (int j = 0; j < DIM; ++j) {
-        double s = 0.0;
-        for (int d = 0; d <= DIM; ++d) s += (s_fP[f][i + 1][d] - s_fP[f][0][d]) * (s_fP[f][j + 1][d] - s_fP[f][0][d]);
-        G[i][j] = s;
+        double s_ = 0.0;
+        for (int d = 0; d <= DIM; ++d) s_ += (s_fP[f][i + 1][d] - s_fP[f][0][d]) * (s_fP[f][j + 1][d] - s_fP[f][0][d]);
+        G[i][j] = s_;
       }
     s_fscale[f] = sqrt(fabs(small_det<DIM>(G)));
-    // groups of the facet's element(s), found by their wave speed
-    auto group_of = [&](int el) {
-      const double ce = a.cK[el];
-      int g = 0;
-      while (g < ng - 1 && s_gc[g] != ce) ++g;
-      return g;
-    };
-    if (dir) {
-      s_fg[f] = group_of(a.facet_elem[fid]);
-      s_fg2[f] = s_fg[f];
-    } else {
-      s_fg[f] = group_of(a.ifac_kp[fid]);
-      s_fg2[f] = group_of(a.ifac_km[fid]);
-    }
   }
   // Gram pairs owned by this thread (upper triangle, i <= j, row-major order)
   int pi[kMaxPair], pj[kMaxPair];
