@@ -570,7 +570,18 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
     };
     const size_t nmom = (size_t)ctx->nrhs * C * nb;
     const size_t NB = (size_t)ngmax * nb;          // unknowns of the largest tent
-    take(nullptr, NB * NB);                        // A at offset 0
+    const size_t half_nb = (NB + 1) / 2, half_rb = ((size_t)ctx->nrhs * NB + 1) / 2;
+    // region used in turn by the monomials (point phases 1, 2, 4) and by A, the
+    // summed Grams and the solve buffers (reduction to solve); A at offset 0
+    const size_t solve_part = NB * NB + (size_t)ngmax * (n + 2) * npair + NB * NB + (size_t)ctx->nrhs * NB + half_rb;
+    const size_t mono_part = (size_t)2 * CH * a.mono_stride;
+    a.off_mono = 0;
+    take(nullptr, NB * NB);                        // A
+    take(&a.off_sg, (size_t)ngmax * (n + 2) * npair);
+    take(&a.off_al, NB * NB);                      // two binary32 N x N sweep buffers
+    take(&a.off_x, (size_t)ctx->nrhs * NB);
+    take(&a.off_z, half_rb);
+    off = std::max(solve_part, mono_part);
     take(&a.off_b, (size_t)ctx->nrhs * NB);
     take(&a.off_pg, (size_t)ngmax * npair);        // G, H_m, Gbot contiguous
     take(&a.off_ph, (size_t)ngmax * n * npair);
@@ -578,25 +589,19 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
     take(&a.off_pm, (size_t)ngmax * nmom);
     take(&a.off_pd, NB * NB);
     take(&a.off_pbd, (size_t)ctx->nrhs * NB);
-    take(&a.off_sg, (size_t)ngmax * (n + 2) * npair);
     take(&a.off_sm, (size_t)ngmax * nmom);
     take(&a.off_f, npair);
     take(&a.off_f2, npair);
     take(&a.off_fpm, (size_t)nb * nb);
     take(&a.off_del, (size_t)ctx->nrhs * nb);
     take(&a.off_u, (size_t)2 * CH * nb);
-    take(&a.off_mono, (size_t)2 * CH * a.mono_stride);
     take(&a.off_pt, (size_t)2 * CH * (n + 2));
     take(&a.off_cb, (size_t)CH * ctx->nrhs * C);
     take(&a.off_gd, (size_t)CH * ctx->nrhs);
     take(&a.off_y, (size_t)ngmax * nmom);
     take(&a.off_rd, NB);
-    const size_t half_nb = (NB + 1) / 2, half_rb = ((size_t)ctx->nrhs * NB + 1) / 2;
-    take(&a.off_al, NB * NB);                      // two binary32 N x N sweep buffers
     take(&a.off_eq, half_nb);
     take(&a.off_perm, half_nb);
-    take(&a.off_z, half_rb);
-    take(&a.off_x, (size_t)ctx->nrhs * NB);
     take(&a.off_keep, (size_t)keep * nb);          // top U-values of the CTA's slice, kept for the outflow
     take(&a.off_keepw, (size_t)keep);
     return off * sizeof(double);
@@ -604,8 +609,8 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
   int CH = 0;
   size_t bytes = 0, cap_used = 0;
   for (size_t cap : {kTwoPerSmSmem, kMaxDynSmem}) {
-    for (int ch = 32; ch >= 8 && CH == 0; ch /= 2)
-      if (plan(ch, 0) <= cap) CH = ch;
+    for (int ch : {48, 32, 16, 8})
+      if (CH == 0 && plan(ch, 0) <= cap) CH = ch;
     if (CH) {
       cap_used = cap;
       break;
@@ -636,7 +641,7 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
       ctx->n_sm = nsm;
     const double avg_pts = (double)T.star_el.size() / (double)T.nv * Q;
     int cs = 1;
-    while (cs < 8 && avg_pts / (2.0 * cs) >= CH) cs *= 2;
+    while (cs < 8 && avg_pts / (2.0 * cs) >= 32.0) cs *= 2;
     ctx->max_cs = cs;
   }
   {
