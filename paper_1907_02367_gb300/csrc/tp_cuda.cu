@@ -421,6 +421,13 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
           star_grp[pos++] = g;
         }
   }
+  int *dpij = nullptr, *dcgp = nullptr, *dcgi = nullptr, *dchp = nullptr, *dchi = nullptr;
+  float *dcgc = nullptr, *dchc = nullptr;
+  if ((rc = ctx_upload(ctx, &dpij, basis->pair_ij)) || (rc = ctx_upload(ctx, &dcgp, basis->cg_ptr)) ||
+      (rc = ctx_upload(ctx, &dcgi, basis->cg_idx)) || (rc = ctx_upload(ctx, &dchp, basis->ch_ptr)) ||
+      (rc = ctx_upload(ctx, &dchi, basis->ch_idx)) || (rc = ctx_upload(ctx, &dcgc, basis->cg_coef)) ||
+      (rc = ctx_upload(ctx, &dchc, basis->ch_coef)))
+    return fail(rc);
   int *dsso = nullptr, *dsgr = nullptr, *dvng = nullptr;
   double* dvgc = nullptr;
   if ((rc = ctx_upload(ctx, &dsso, star_sorted)) || (rc = ctx_upload(ctx, &dsgr, star_grp)) ||
@@ -514,6 +521,13 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
   a.cK = dc;
   a.star_ptr = dsp;
   a.star_el = dse;
+  a.pair_ij = dpij;
+  a.cg_ptr = dcgp;
+  a.cg_idx = dcgi;
+  a.ch_ptr = dchp;
+  a.ch_idx = dchi;
+  a.cg_coef = dcgc;
+  a.ch_coef = dchc;
   a.star_sorted = dsso;
   a.star_grp = dsgr;
   a.vert_ng = dvng;

@@ -470,6 +470,52 @@ extern "C" int tp_build_basis(int32_t dim, int32_t p, tp_basis** out) {
       }
       B->relT_ptr[r + 1] = (int32_t)B->relT_dst.size();
     }
+    // merged congruence tables of the top-face form (entries i <= j)
+    const int nb = B->nb;
+    auto pidx = [&](int i, int j) {
+      const int lo = std::min(i, j), hi = std::max(i, j);
+      return lo * nb - lo * (lo - 1) / 2 + (hi - lo);
+    };
+    auto rel_of = [&](int row, int v, int* b, int* e) {
+      *b = B->rel_ptr[(size_t)row * NVAR + v];
+      *e = B->rel_ptr[(size_t)row * NVAR + v + 1];
+    };
+    B->cg_ptr.assign(1, 0);
+    B->ch_ptr.assign(1, 0);
+    for (int i = 0; i < nb; ++i)
+      for (int j = i; j < nb; ++j) {
+        std::map<int, double> gm, hm;
+        for (int va = 0; va < NVAR; ++va) {   // D_t X D_t^T and D_m X D_m^T
+          int b0, e0, b1, e1;
+          rel_of(i, va, &b0, &e0);
+          rel_of(j, va, &b1, &e1);
+          for (int e = b0; e < e0; ++e)
+            for (int f = b1; f < e1; ++f) gm[pidx(B->rel_src[e], B->rel_src[f])] += B->rel_fac[e] * B->rel_fac[f];
+        }
+        for (int m = 1; m < NVAR; ++m) {      // D_m H_m D_t^T + D_t H_m D_m^T
+          for (int pass = 0; pass < 2; ++pass) {
+            int b0, e0, b1, e1;
+            rel_of(i, pass == 0 ? m : 0, &b0, &e0);
+            rel_of(j, pass == 0 ? 0 : m, &b1, &e1);
+            for (int e = b0; e < e0; ++e)
+              for (int f = b1; f < e1; ++f)
+                hm[((m - 1) << 16) | pidx(B->rel_src[e], B->rel_src[f])] += B->rel_fac[e] * B->rel_fac[f];
+          }
+        }
+        B->pair_ij.push_back((i << 16) | j);
+        for (auto& kv : gm)
+          if (kv.second != 0.0) {
+            B->cg_idx.push_back(kv.first);
+            B->cg_coef.push_back((float)kv.second);
+          }
+        for (auto& kv : hm)
+          if (kv.second != 0.0) {
+            B->ch_idx.push_back(kv.first);
+            B->ch_coef.push_back((float)kv.second);
+          }
+        B->cg_ptr.push_back((int32_t)B->cg_idx.size());
+        B->ch_ptr.push_back((int32_t)B->ch_idx.size());
+      }
   }
   B->coef.assign((size_t)B->nb * B->nmono, 0.0);
   B->sp_ptr.assign(B->nb * C + 1, 0);

@@ -84,4 +84,13 @@ struct tp_basis {
   // transposed: for (k, var): entries (j, fac) with b_k appearing in d b_j
   std::vector<int32_t> relT_ptr, relT_dst;
   std::vector<double> relT_fac;
+  // congruences of the top-face form, merged per entry (i <= j, packed order
+  // p = i nb - i (i - 1) / 2 + j - i):
+  //   (D_t X D_t^T + sum_m D_m X D_m^T)_ij = sum over [cg_ptr[p], cg_ptr[p+1]) of cg_coef * X[cg_idx]
+  //   (sum_m D_m H_m D_t^T + D_t H_m D_m^T)_ij = sum over [ch_ptr[p], ch_ptr[p+1]) of
+  //       ch_coef * H_{m}[ch_idx & 0xffff], m = ch_idx >> 16
+  // (X, H_m packed symmetric; the coefficients are exact integers)
+  std::vector<int32_t> pair_ij;     // (i << 16) | j of packed entry p
+  std::vector<int32_t> cg_ptr, cg_idx, ch_ptr, ch_idx;
+  std::vector<float> cg_coef, ch_coef;
 };

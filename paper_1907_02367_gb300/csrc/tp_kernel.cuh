@@ -69,6 +69,10 @@ struct KArgs {
   const float2* sp_coef_dd;   // (hi, lo) binary32 pair of every sp_coef entry
   const int* mono_parent;
   const int* mono_var;
+  // merged congruence tables of the top-face form (see tp_basis)
+  const int* pair_ij;
+  const int *cg_ptr, *cg_idx, *ch_ptr, *ch_idx;
+  const float *cg_coef, *ch_coef;
   double* tau;
   double* front;
   const double* gD;
@@ -209,6 +213,7 @@ struct Ar<double> {
   static __device__ __forceinline__ double sub(double a, double b) { return a - b; }
   static __device__ __forceinline__ double mul(double a, double b) { return a * b; }
   static __device__ __forceinline__ double mulf(double a, float f) { return a * (double)f; }
+  static __device__ __forceinline__ double fmac(double a, float f, double c) { return ::fma(a, (double)f, c); }
   static __device__ __forceinline__ double fma(double a, double b, double c) { return ::fma(a, b, c); }
   static __device__ __forceinline__ double coef(const KArgs& a, int e);
 };
@@ -232,6 +237,7 @@ struct Ar<dd> {
   static __device__ __forceinline__ dd sub(dd a, dd b) { return dd_add(a, {-b.hi, -b.lo}); }
   static __device__ __forceinline__ dd mul(dd a, dd b) { return dd_mul(a, b); }
   static __device__ __forceinline__ dd mulf(dd a, float f) { return dd_mulf(a, f); }
+  static __device__ __forceinline__ dd fmac(dd a, float f, dd c) { return dd_add(dd_mulf(a, f), c); }
   static __device__ __forceinline__ dd fma(dd a, dd b, dd c) { return dd_add(dd_mul(a, b), c); }
   static __device__ __forceinline__ dd coef(const KArgs& a, int e);
 };
@@ -984,20 +990,48 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
   const int row0 = (N * rank) / CS, nrow = (N * (rank + 1)) / CS - row0;
   {
     const T ih2 = R::from(ih * ih), mih = R::from(-ih);
-    for (int id = tid; id < nrow * nb; id += blockDim.x) {
-      const int Rw = row0 + id / nb, j = id % nb;
-      const int g = Rw / nb, i = Rw % nb;
+    // top-face form of every material block by the merged tables: entries
+    // i <= j of the packed upper triangle, split over the cluster; each entry
+    // is stored with its mirror (the form is symmetric, the Dirichlet and
+    // interface parts already in A are not)
+    const int nent = ng * npair, ent0 = (nent * rank) / CS, ent1 = (nent * (rank + 1)) / CS;
+    for (int id = ent0 + tid; id < ent1; id += blockDim.x) {
+      const int g = id / npair, pp = id % npair;
+      const int ij = __ldg(a.pair_ij + pp), i = ij >> 16, j = ij & 0xffff;
       const T* SG = sSG + (size_t)g * npair;
+      const T* SH = sSG + (size_t)(NG + g * DIM) * npair;
       const T* SGb = sSG + (size_t)(NG * (DIM + 1) + g) * npair;
-      const T cc_ = R::from(s_gc[g]);
-      T t = congruence<DIM, T>(a, i, 0, j, 0, SG, nb);
-      for (int d = 0; d < DIM; ++d) {
-        const T* H = sSG + (size_t)(NG + g * DIM + d) * npair;
-        t = R::add(t, congruence<DIM, T>(a, i, 1 + d, j, 1 + d, SG, nb));
-        t = R::fma(cc_, R::add(congruence<DIM, T>(a, i, 1 + d, j, 0, H, nb), congruence<DIM, T>(a, i, 0, j, 1 + d, H, nb)), t);
+      T tg0 = R::zero(), tg1 = R::zero(), th0 = R::zero(), th1 = R::zero();
+      {
+        const int e0 = __ldg(a.cg_ptr + pp), e1 = __ldg(a.cg_ptr + pp + 1);
+        int e = e0;
+        for (; e + 1 < e1; e += 2) {
+          tg0 = R::fmac(SG[__ldg(a.cg_idx + e)], __ldg(a.cg_coef + e), tg0);
+          tg1 = R::fmac(SG[__ldg(a.cg_idx + e + 1)], __ldg(a.cg_coef + e + 1), tg1);
+        }
+        if (e < e1) tg0 = R::fmac(SG[__ldg(a.cg_idx + e)], __ldg(a.cg_coef + e), tg0);
       }
-      const size_t o = (size_t)Rw * N + g * nb + j;
-      A0[o] = R::add(sA[o], R::fma(ih2, t, SGb[pair_index(i, j, nb)]));
+      {
+        const int e0 = __ldg(a.ch_ptr + pp), e1 = __ldg(a.ch_ptr + pp + 1);
+        int e = e0;
+        for (; e + 1 < e1; e += 2) {
+          const int c0 = __ldg(a.ch_idx + e), c1 = __ldg(a.ch_idx + e + 1);
+          th0 = R::fmac(SH[(c0 >> 16) * npair + (c0 & 0xffff)], __ldg(a.ch_coef + e), th0);
+          th1 = R::fmac(SH[(c1 >> 16) * npair + (c1 & 0xffff)], __ldg(a.ch_coef + e + 1), th1);
+        }
+        if (e < e1) {
+          const int c0 = __ldg(a.ch_idx + e);
+          th0 = R::fmac(SH[(c0 >> 16) * npair + (c0 & 0xffff)], __ldg(a.ch_coef + e), th0);
+        }
+      }
+      const T t = R::fma(R::from(s_gc[g]), R::add(th0, th1), R::add(tg0, tg1));
+      const T val = R::fma(ih2, t, SGb[pp]);
+      const size_t o = (size_t)(g * nb + i) * N + g * nb + j;
+      A0[o] = R::add(sA[o], val);
+      if (i != j) {
+        const size_t o2 = (size_t)(g * nb + j) * N + g * nb + i;
+        A0[o2] = R::add(sA[o2], val);
+      }
     }
     for (int id = tid; id < nrhs * nrow; id += blockDim.x) {
       const int r = id / nrow, Rw = row0 + id % nrow;
@@ -1196,8 +1230,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
     const int maxit = kMaxRefine;
     for (int it = 0; it < maxit; ++it) {
       // residual b - A x, each row split over 8 lanes of one warp; stored
-      // scaled by D in binary32
-      for (int base8 = 0; base8 < nrhs * N * 8; base8 += blockDim.x) {
+      // scaled by D in binary32 (the first iterate is x = 0: the residual is b)
+      if (it == 0)
+        for (int id = tid; id < nrhs * N; id += blockDim.x) sZ[id] = sEq[id % N] * R::hi(sb[id]);
+      for (int base8 = 0; base8 < (it == 0 ? 0 : nrhs * N * 8); base8 += blockDim.x) {
         const int id = base8 + tid, item = id >> 3, sub = id & 7;
         T t = R::zero();
         if (item < nrhs * N) {
@@ -1254,6 +1290,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
           dmax = fmaxf(dmax, fabsf(dx));
           xmax = fmaxf(xmax, fabsf(R::hi(sX[item])));
         }
+      }
+      if (it == 0) {   // the first correction is the whole binary32 solution: no test
+        __syncthreads();
+        continue;
       }
       for (int o = 16; o > 0; o >>= 1) {
         dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
