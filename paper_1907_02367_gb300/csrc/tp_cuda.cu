@@ -428,6 +428,45 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
       (rc = ctx_upload(ctx, &dchi, basis->ch_idx)) || (rc = ctx_upload(ctx, &dcgc, basis->cg_coef)) ||
       (rc = ctx_upload(ctx, &dchc, basis->ch_coef)))
     return fail(rc);
+  // per element: inverse of the edge matrix e (rows X_i - X_0), so that the
+  // gradient of a linear function is e^-1 (its increments along the edges), and sqrt|det e|
+  std::vector<double> einv((size_t)T.ne * n * n), esdet(T.ne);
+  for (int64_t k = 0; k < T.ne; ++k) {
+    double e[3][3] = {};
+    const int* vk = &T.elems[(size_t)k * (n + 1)];
+    for (int i = 0; i < n; ++i)
+      for (int d = 0; d < n; ++d) e[i][d] = T.X[(size_t)vk[i + 1] * n + d] - T.X[(size_t)vk[0] * n + d];
+    double inv[3][3] = {}, det;
+    if (n == 1) {
+      det = e[0][0];
+      inv[0][0] = 1.0 / det;
+    } else if (n == 2) {
+      det = e[0][0] * e[1][1] - e[0][1] * e[1][0];
+      inv[0][0] = e[1][1] / det;
+      inv[0][1] = -e[0][1] / det;
+      inv[1][0] = -e[1][0] / det;
+      inv[1][1] = e[0][0] / det;
+    } else {
+      double c[3][3];   // c[i] = cofactor column of edge i: rows of e^-T times det
+      c[0][0] = e[1][1] * e[2][2] - e[1][2] * e[2][1];
+      c[0][1] = e[1][2] * e[2][0] - e[1][0] * e[2][2];
+      c[0][2] = e[1][0] * e[2][1] - e[1][1] * e[2][0];
+      c[1][0] = e[2][1] * e[0][2] - e[2][2] * e[0][1];
+      c[1][1] = e[2][2] * e[0][0] - e[2][0] * e[0][2];
+      c[1][2] = e[2][0] * e[0][1] - e[2][1] * e[0][0];
+      c[2][0] = e[0][1] * e[1][2] - e[0][2] * e[1][1];
+      c[2][1] = e[0][2] * e[1][0] - e[0][0] * e[1][2];
+      c[2][2] = e[0][0] * e[1][1] - e[0][1] * e[1][0];
+      det = e[0][0] * c[0][0] + e[0][1] * c[0][1] + e[0][2] * c[0][2];
+      for (int d = 0; d < 3; ++d)
+        for (int i = 0; i < 3; ++i) inv[d][i] = c[i][d] / det;
+    }
+    for (int d = 0; d < n; ++d)
+      for (int i = 0; i < n; ++i) einv[((size_t)k * n + d) * n + i] = inv[d][i];
+    esdet[k] = std::sqrt(std::fabs(det));
+  }
+  double *deinv = nullptr, *desdet = nullptr;
+  if ((rc = ctx_upload(ctx, &deinv, einv)) || (rc = ctx_upload(ctx, &desdet, esdet))) return fail(rc);
   int *dsso = nullptr, *dsgr = nullptr, *dvng = nullptr;
   double* dvgc = nullptr;
   if ((rc = ctx_upload(ctx, &dsso, star_sorted)) || (rc = ctx_upload(ctx, &dsgr, star_grp)) ||
@@ -528,6 +567,8 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
   a.ch_idx = dchi;
   a.cg_coef = dcgc;
   a.ch_coef = dchc;
+  a.elem_einv = deinv;
+  a.elem_sdet = desdet;
   a.star_sorted = dsso;
   a.star_grp = dsgr;
   a.vert_ng = dvng;

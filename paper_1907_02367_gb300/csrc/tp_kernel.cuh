@@ -41,6 +41,8 @@ struct KArgs {
   const double* cK;
   const int* star_ptr;
   const int* star_el;
+  const double* elem_einv;    // per element: inverse of the edge matrix e (rows X_i - X_0), dim x dim
+  const double* elem_sdet;    // per element: sqrt(|det e|)
   const int* star_sorted;     // vertex stars with the elements grouped by wave speed
   const int* star_grp;        // material group of each entry of star_sorted
   const int* vert_ng;         // materials (distinct wave speeds) in each vertex star
@@ -260,7 +262,8 @@ __device__ __forceinline__ void eval_uvalues_block(const KArgs& a, int npt, cons
   // that four independent products are in flight per table lookup.
   const int tid = threadIdx.x, ms = a.mono_stride, nb = a.nb;
   const int nq4 = (npt + 3) >> 2;
-  for (int q = tid; q < npt; q += blockDim.x) m[q * ms] = Ar<T>::one();
+  // the constant monomial carries the scale, so every monomial and U-value is scaled
+  for (int q = tid; q < npt; q += blockDim.x) m[q * ms] = SCALE ? pt[q * (DIM + 2) + DIM + 1] : Ar<T>::one();
   for (int d = 1; d <= a.p; ++d) {
     __syncthreads();   // pt, and the monomials of degree d - 1
     const int g0 = a.mono_lv[d], cnt = a.mono_lv[d + 1] - g0;
@@ -294,7 +297,7 @@ __device__ __forceinline__ void eval_uvalues_block(const KArgs& a, int npt, cons
     }
 #pragma unroll
     for (int t = 0; t < 4; ++t)
-      if (q0 + t < npt) u[qq[t] * nb + j] = SCALE ? Ar<T>::mul(pt[qq[t] * (DIM + 2) + DIM + 1], acc[t]) : acc[t];
+      if (q0 + t < npt) u[qq[t] * nb + j] = acc[t];
   }
   __syncthreads();
 }
@@ -627,22 +630,26 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
       s_tb[k][i] = tv;
       s_tt[k][i] = (vi == v) ? s_ttop : tv;
     }
-    double e[DIM][DIM], db[DIM], dt[DIM];
+    // gradients of the linear fronts: g = e^-1 (tau_i - tau_0), e from the host
+    const int el = s_el[k];
+    double db[DIM], dt[DIM];
     for (int i = 0; i < DIM; ++i) {
-      for (int d = 0; d < DIM; ++d) e[i][d] = s_X[k][i + 1][d] - s_X[k][0][d];
       db[i] = s_tb[k][i + 1] - s_tb[k][0];
       dt[i] = s_tt[k][i + 1] - s_tt[k][0];
     }
-    double gb[DIM], gt[DIM];
-    const double det = lin_grad<DIM>(e, db, gb);
-    lin_grad<DIM>(e, dt, gt);
     double g2 = 0.0;
     for (int d = 0; d < DIM; ++d) {
-      s_gb[k][d] = gb[d];
-      s_gt[k][d] = gt[d];
-      g2 += gt[d] * gt[d];
+      double gb = 0.0, gt = 0.0;
+      for (int i = 0; i < DIM; ++i) {
+        const double ei = __ldg(a.elem_einv + ((int64_t)el * DIM + d) * DIM + i);
+        gb = fma(ei, db[i], gb);
+        gt = fma(ei, dt[i], gt);
+      }
+      s_gb[k][d] = gb;
+      s_gt[k][d] = gt;
+      g2 = fma(gt, gt, g2);
     }
-    s_sdet[k] = sqrt(fabs(det));
+    s_sdet[k] = __ldg(a.elem_sdet + el);
     const double ck = s_gc[s_grp[k]];
     if (!(1.0 / (ck * ck) - g2 > 0.0)) flag_error(a, TP_ERR_CAUSALITY, tent);   // space-like top face
   }
@@ -1233,15 +1240,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
       // scaled by D in binary32 (the first iterate is x = 0: the residual is b)
       if (it == 0)
         for (int id = tid; id < nrhs * N; id += blockDim.x) sZ[id] = sEq[id % N] * R::hi(sb[id]);
-      for (int base8 = 0; base8 < (it == 0 ? 0 : nrhs * N * 8); base8 += blockDim.x) {
-        const int id = base8 + tid, item = id >> 3, sub = id & 7;
+      for (int base4 = 0; base4 < (it == 0 ? 0 : nrhs * N * 4); base4 += blockDim.x) {
+        const int id = base4 + tid, item = id >> 2, sub = id & 3;
         T t = R::zero();
         if (item < nrhs * N) {
           const int r = item / N, i = item % N;
           const T* xr = sX + (size_t)r * N;
-          for (int j = sub; j < N; j += 8) t = R::fms(t, sA[i * N + j], xr[j]);
+          for (int j = sub; j < N; j += 4) t = R::fms(t, sA[i * N + j], xr[j]);
         }
-        for (int o = 4; o > 0; o >>= 1) {
+        for (int o = 2; o > 0; o >>= 1) {
           T u;
           if constexpr (MIXED) {
             u.hi = __shfl_xor_sync(0xffffffffu, t.hi, o);
@@ -1255,7 +1262,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
       }
       __syncthreads();
       // x += D F (P r): register path, one row per (warp, slot), summed over lanes
-      float dmax = 0.f, xmax = 0.f;
+      // (the scale |x| of the stop test is taken from the first iterate)
+      float dmax = 0.f;
       if (regs) {
         for (int r = 0; r < nrhs; ++r) {
           const float vj = (lane < N) ? sZ[(size_t)r * N + sPerm[lane]] : 0.f;
@@ -1269,7 +1277,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
               const size_t o_ = (size_t)r * N + i;
               sX[o_] = R::addf(sX[o_], dx);
               dmax = fmaxf(dmax, fabsf(dx));
-              xmax = fmaxf(xmax, fabsf(R::hi(sX[o_])));
             }
           }
         }
@@ -1288,21 +1295,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
           const float dx = sEq[item % N] * z;
           sX[item] = R::addf(sX[item], dx);
           dmax = fmaxf(dmax, fabsf(dx));
-          xmax = fmaxf(xmax, fabsf(R::hi(sX[item])));
         }
       }
+      for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
       if (it == 0) {   // the first correction is the whole binary32 solution: no test
+        if (lane == 0) s_red[1][warp] = dmax;
         __syncthreads();
         continue;
       }
-      for (int o = 16; o > 0; o >>= 1) {
-        dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
-        xmax = fmaxf(xmax, __shfl_xor_sync(0xffffffffu, xmax, o));
-      }
-      if (lane == 0) {
-        s_red[0][warp] = dmax;
-        s_red[1][warp] = xmax;
-      }
+      if (lane == 0) s_red[0][warp] = dmax;
       __syncthreads();
       float dm = 0.f, xm = 0.f;
       for (int w = 0; w < kThreads / 32; ++w) {
