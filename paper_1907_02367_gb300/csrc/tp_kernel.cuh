@@ -216,6 +216,11 @@ struct Ar<double> {
   static __device__ __forceinline__ double mul(double a, double b) { return a * b; }
   static __device__ __forceinline__ double mulf(double a, float f) { return a * (double)f; }
   static __device__ __forceinline__ double fmac(double a, float f, double c) { return ::fma(a, (double)f, c); }
+  // accumulation of a long sum of products (see the float-float version)
+  static __device__ __forceinline__ double acc(double s, double a, double b) { return ::fma(a, b, s); }
+  static __device__ __forceinline__ double accf(double s, double a, float f) { return ::fma(a, (double)f, s); }
+  static __device__ __forceinline__ double accn(double s, double a, double b) { return ::fma(-a, b, s); }
+  static __device__ __forceinline__ double norm(double s) { return s; }
   static __device__ __forceinline__ double fma(double a, double b, double c) { return ::fma(a, b, c); }
   static __device__ __forceinline__ double coef(const KArgs& a, int e);
 };
@@ -240,6 +245,29 @@ struct Ar<dd> {
   static __device__ __forceinline__ dd mul(dd a, dd b) { return dd_mul(a, b); }
   static __device__ __forceinline__ dd mulf(dd a, float f) { return dd_mulf(a, f); }
   static __device__ __forceinline__ dd fmac(dd a, float f, dd c) { return dd_add(dd_mulf(a, f), c); }
+  // s += a b for a long sum of products, compensated in the manner of Ogita,
+  // Rump and Oishi's Dot2: s = (p, e) holds the running binary32 sum p and
+  // the sum e of all rounding errors (of the products, exact by fmaf, and of
+  // the additions, exact by TwoSum); the pair is not normalised until norm().
+  static __device__ __forceinline__ dd acc(dd s, dd a, dd b) {
+    const float h = __fmul_rn(a.hi, b.hi);
+    float r = fmaf(a.hi, b.hi, -h);
+    r = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, r));
+    const float pn = __fadd_rn(s.hi, h);
+    const float bb = __fsub_rn(pn, s.hi);
+    const float q = __fadd_rn(__fsub_rn(s.hi, __fsub_rn(pn, bb)), __fsub_rn(h, bb));
+    return {pn, __fadd_rn(s.lo, __fadd_rn(q, r))};
+  }
+  static __device__ __forceinline__ dd accf(dd s, dd a, float f) {   // s += a f, f exact in binary32
+    const float h = __fmul_rn(a.hi, f);
+    const float r = fmaf(a.lo, f, fmaf(a.hi, f, -h));
+    const float pn = __fadd_rn(s.hi, h);
+    const float bb = __fsub_rn(pn, s.hi);
+    const float q = __fadd_rn(__fsub_rn(s.hi, __fsub_rn(pn, bb)), __fsub_rn(h, bb));
+    return {pn, __fadd_rn(s.lo, __fadd_rn(q, r))};
+  }
+  static __device__ __forceinline__ dd accn(dd s, dd a, dd b) { return acc(s, {-a.hi, -a.lo}, b); }   // s -= a b
+  static __device__ __forceinline__ dd norm(dd s) { return fast_two_sum(s.hi, s.lo); }
   static __device__ __forceinline__ dd fma(dd a, dd b, dd c) { return dd_add(dd_mul(a, b), c); }
   static __device__ __forceinline__ dd coef(const KArgs& a, int e);
 };
@@ -293,11 +321,11 @@ __device__ __forceinline__ void eval_uvalues_block(const KArgs& a, int npt, cons
       const T c = Ar<T>::coef(a, e);
       const int g = __ldg(a.sp_mono + e);
 #pragma unroll
-      for (int t = 0; t < 4; ++t) acc[t] = Ar<T>::fma(c, m[qq[t] * ms + g], acc[t]);
+      for (int t = 0; t < 4; ++t) acc[t] = Ar<T>::acc(acc[t], c, m[qq[t] * ms + g]);
     }
 #pragma unroll
     for (int t = 0; t < 4; ++t)
-      if (q0 + t < npt) u[qq[t] * nb + j] = acc[t];
+      if (q0 + t < npt) u[qq[t] * nb + j] = Ar<T>::norm(acc[t]);
   }
   __syncthreads();
 }
@@ -708,9 +736,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
     for (int d = 0; d < DIM; ++d) g[d] = R::from(s_gt[k][d]);
 #pragma unroll
     for (int s = 0; s < kMaxPair; ++s) {
-      aG[s] = R::add(aG[s], aK[s]);
+      const T k_ = R::norm(aK[s]);
+      aG[s] = R::add(aG[s], k_);
 #pragma unroll
-      for (int d = 0; d < DIM; ++d) aH[s][d] = R::fma(g[d], aK[s], aH[s][d]);
+      for (int d = 0; d < DIM; ++d) aH[s][d] = R::fma(g[d], k_, aH[s][d]);
       aK[s] = R::zero();
     }
   };
@@ -723,7 +752,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
 #pragma unroll
         for (int d = 0; d < DIM; ++d)
           sPH[(g * DIM + d) * npair + id] = R::add(sPH[(g * DIM + d) * npair + id], aH[s][d]);
-        sPGb[g * npair + id] = R::add(sPGb[g * npair + id], aB[s]);
+        sPGb[g * npair + id] = R::add(sPGb[g * npair + id], R::norm(aB[s]));
       }
       aG[s] = aB[s] = R::zero();
 #pragma unroll
@@ -798,8 +827,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
 #pragma unroll
       for (int s = 0; s < kMaxPair; ++s) {
         if (tid + s * kThreads < npair) {
-          aK[s] = R::fma(ut[pi[s]], ut[pj[s]], aK[s]);
-          aB[s] = R::fma(ub[pi[s]], ub[pj[s]], aB[s]);
+          aK[s] = R::acc(aK[s], ut[pi[s]], ut[pj[s]]);
+          aB[s] = R::acc(aB[s], ub[pi[s]], ub[pj[s]]);
         }
       }
     }
@@ -808,10 +837,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
     for (int id = tid; id < ng * nmom; id += blockDim.x) {
       const int g = id / nmom, rest = id % nmom;
       const int r = rest / (C * nb), rem = rest % (C * nb), cc = rem / nb, i = rem % nb;
-      T t = sPM[id];
+      T t = R::zero();
       for (int ql = 0; ql < nq; ++ql)
-        if (s_pgrp[ql] == g) t = R::fma(sCB[((size_t)ql * nrhs + r) * C + cc], sU[(size_t)(prow + ql) * nb + i], t);
-      sPM[id] = t;
+        if (s_pgrp[ql] == g) t = R::acc(t, sCB[((size_t)ql * nrhs + r) * C + cc], sU[(size_t)(prow + ql) * nb + i]);
+      sPM[id] = R::add(sPM[id], R::norm(t));
     }
     __syncthreads();
   }
@@ -1013,25 +1042,25 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
         const int e0 = __ldg(a.cg_ptr + pp), e1 = __ldg(a.cg_ptr + pp + 1);
         int e = e0;
         for (; e + 1 < e1; e += 2) {
-          tg0 = R::fmac(SG[__ldg(a.cg_idx + e)], __ldg(a.cg_coef + e), tg0);
-          tg1 = R::fmac(SG[__ldg(a.cg_idx + e + 1)], __ldg(a.cg_coef + e + 1), tg1);
+          tg0 = R::accf(tg0, SG[__ldg(a.cg_idx + e)], __ldg(a.cg_coef + e));
+          tg1 = R::accf(tg1, SG[__ldg(a.cg_idx + e + 1)], __ldg(a.cg_coef + e + 1));
         }
-        if (e < e1) tg0 = R::fmac(SG[__ldg(a.cg_idx + e)], __ldg(a.cg_coef + e), tg0);
+        if (e < e1) tg0 = R::accf(tg0, SG[__ldg(a.cg_idx + e)], __ldg(a.cg_coef + e));
       }
       {
         const int e0 = __ldg(a.ch_ptr + pp), e1 = __ldg(a.ch_ptr + pp + 1);
         int e = e0;
         for (; e + 1 < e1; e += 2) {
           const int c0 = __ldg(a.ch_idx + e), c1 = __ldg(a.ch_idx + e + 1);
-          th0 = R::fmac(SH[(c0 >> 16) * npair + (c0 & 0xffff)], __ldg(a.ch_coef + e), th0);
-          th1 = R::fmac(SH[(c1 >> 16) * npair + (c1 & 0xffff)], __ldg(a.ch_coef + e + 1), th1);
+          th0 = R::accf(th0, SH[(c0 >> 16) * npair + (c0 & 0xffff)], __ldg(a.ch_coef + e));
+          th1 = R::accf(th1, SH[(c1 >> 16) * npair + (c1 & 0xffff)], __ldg(a.ch_coef + e + 1));
         }
         if (e < e1) {
           const int c0 = __ldg(a.ch_idx + e);
-          th0 = R::fmac(SH[(c0 >> 16) * npair + (c0 & 0xffff)], __ldg(a.ch_coef + e), th0);
+          th0 = R::accf(th0, SH[(c0 >> 16) * npair + (c0 & 0xffff)], __ldg(a.ch_coef + e));
         }
       }
-      const T t = R::fma(R::from(s_gc[g]), R::add(th0, th1), R::add(tg0, tg1));
+      const T t = R::fma(R::from(s_gc[g]), R::add(R::norm(th0), R::norm(th1)), R::add(R::norm(tg0), R::norm(tg1)));
       const T val = R::fma(ih2, t, SGb[pp]);
       const size_t o = (size_t)(g * nb + i) * N + g * nb + j;
       A0[o] = R::add(sA[o], val);
@@ -1246,7 +1275,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
         if (item < nrhs * N) {
           const int r = item / N, i = item % N;
           const T* xr = sX + (size_t)r * N;
-          for (int j = sub; j < N; j += 4) t = R::fms(t, sA[i * N + j], xr[j]);
+          for (int j = sub; j < N; j += 4) t = R::accn(t, sA[i * N + j], xr[j]);
+          t = R::norm(t);
         }
         for (int o = 2; o > 0; o >>= 1) {
           T u;
@@ -1490,7 +1520,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
         const T* u = keep ? sKeep + (size_t)(base - q0 + ql) * nb : sU + (size_t)ql * nb;
         const T* y = sY + (size_t)s_grp[k] * nmom + ((size_t)r * C + cc) * nb;
         T t = R::zero();
-        for (int j = 0; j < nb; ++j) t = R::fma(y[j], u[j], t);
+        for (int j = 0; j < nb; ++j) t = R::acc(t, y[j], u[j]);
+        t = R::norm(t);
         const double val = keep ? R::to(t) * sKeepW[base - q0 + ql] : R::to(t);
         a.front[(((int64_t)r * a.ne + s_el[k]) * Q + q) * C + cc] = val;
       }
@@ -1504,7 +1535,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
         for (int cc = 0; cc < C; ++cc) {
           const T* y = sY + (size_t)s_grp[k] * nmom + ((size_t)r * C + cc) * nb;
           T t = R::zero();
-          for (int j = 0; j < nb; ++j) t = R::fma(y[j], u[j], t);
+          for (int j = 0; j < nb; ++j) t = R::acc(t, y[j], u[j]);
+          t = R::norm(t);
           sv[cc] = R::to(t);
         }
         const double cg = s_gc[s_grp[k]];

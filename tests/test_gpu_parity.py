@@ -149,7 +149,10 @@ def test_dataflow_matches_levels(cuda_device, name, precision):
     _, c, tc, sc = _gpu_run(m, w.p, w.T, w.kappa, w.init, None, schedule="dataflow", precision=precision)
     assert sa == sb == sc == (0, 0)
     assert np.array_equal(ta, tb) and np.array_equal(tb, tc)
-    assert _rel(b, a) <= 1e-13
+    # the two schedules slice a tent's points differently over its cluster, so
+    # the sums are taken in another order: rounding of binary64, or of the
+    # compensated float-float sums of the mixed path (~1e-13 relative)
+    assert _rel(b, a) <= (1e-13 if precision == "fp64" else 1e-11)
     assert np.array_equal(b, c)
 
 
