@@ -35,7 +35,7 @@ enum {
   TP_ERR_ARG = 1,          /* invalid argument (sizes, pointers, unsupported p/dim) */
   TP_ERR_CAUSALITY = 2,    /* a front or tent violates c|grad tau| < 1 (Section 2.2) */
   TP_ERR_SINGULAR = 3,     /* zero or non-finite pivot in a local system */
-  TP_ERR_NOCONV = 4,       /* iterative refinement did not converge */
+  TP_ERR_NOCONV = 4,       /* iterative refinement did not converge (reserved: stalled refinements fall back to a direct LU) */
   TP_ERR_TIMEOUT = 5,      /* a bounded device wait gave up */
   TP_ERR_CUDA = 6,         /* a CUDA runtime call failed */
   TP_ERR_OOM = 7,          /* allocation failed */
@@ -65,8 +65,9 @@ typedef struct tp_mesh_desc {
  * 0.5); kappa: pitching slope factor (edge-slope limit delta_e = kappa l_e /
  * c_e); T: final time; precision: TP_FP64 (every step in binary64) or
  * TP_MIXED (assembly, residual and outflow in float-float on the binary32
- * pipes, binary32 LU of the equilibrated local matrix, iterative refinement
- * to binary64 accuracy; TP_ERR_NOCONV if it stalls);
+ * pipes, binary32 inverse of the equilibrated local matrix, iterative
+ * refinement to float-float accuracy; a tent whose refinement does not
+ * settle is solved by a direct binary64 LU instead);
  * nrhs: right-hand sides advanced together (same tents, same matrices);
  * schedule: how tp_advance runs the levels -- TP_SCHED_DATAFLOW (default):
  * one resident kernel whose clusters take the tents in level order and each
@@ -183,8 +184,8 @@ int tp_adjoint(tp_ctx* ctx, const double* d_lambda_T, double* d_lambda_0, void* 
 int tp_get_state(const tp_ctx* ctx, double* d_front, double* d_tau, void* stream);
 /* Synchronises the context's last stream and reports the device status:
  * *status = TP_OK, TP_ERR_CAUSALITY (a top face not space-like),
- * TP_ERR_SINGULAR (zero or non-finite pivot), TP_ERR_NOCONV (mixed-precision
- * refinement stalled) or TP_ERR_TIMEOUT (a bounded dependency wait of the
+ * TP_ERR_SINGULAR (zero or non-finite pivot of the direct LU) or
+ * TP_ERR_TIMEOUT (a bounded dependency wait of the
  * dataflow sweep gave up); *info = index of the first failing tent in the
  * sorted list.  The first error wins; tp_set_state clears it. */
 int tp_sync_status(tp_ctx* ctx, int32_t* status, int64_t* info);

@@ -161,14 +161,28 @@ int ctx_upload(tp_ctx* ctx, T** d, const std::vector<T>& h) {
   return rc;
 }
 
-constexpr size_t kMaxDynSmem = 200 * 1024;   // cap of the shared-memory plan
 constexpr size_t kTwoPerSmSmem = 95 * 1024;  // plan that leaves room for two CTAs per SM
 
-// the attribute is set to the plan's cap, so contexts of any size can share the kernel
-int set_smem_attr(int dim) {
-  cudaError_t e = dim == 1 ? tp::layer_attrs_d1(kMaxDynSmem)
-                : dim == 2 ? tp::layer_attrs_d2(kMaxDynSmem)
-                           : tp::layer_attrs_d3(kMaxDynSmem);
+// cap of the shared-memory plan: the device's per-block limit less the
+// kernel's static shared memory; the attribute is set to it, so contexts of
+// any size can share the kernel
+int max_dyn_smem(int dim, size_t* cap) {
+  int dev = 0, optin = 0;
+  size_t stat = 0;
+  TP_CUDA_OK(cudaGetDevice(&dev));
+  TP_CUDA_OK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  TP_CUDA_OK(dim == 1 ? tp::layer_static_smem_d1(&stat) : dim == 2 ? tp::layer_static_smem_d2(&stat)
+                                                                     : tp::layer_static_smem_d3(&stat));
+  if ((size_t)optin <= stat + kTwoPerSmSmem) {
+    *cap = kTwoPerSmSmem;
+  } else {
+    *cap = ((size_t)optin - stat) & ~(size_t)1023;
+  }
+  return TP_OK;
+}
+
+int set_smem_attr(int dim, size_t cap) {
+  cudaError_t e = dim == 1 ? tp::layer_attrs_d1(cap) : dim == 2 ? tp::layer_attrs_d2(cap) : tp::layer_attrs_d3(cap);
   TP_CUDA_OK(e);
   return TP_OK;
 }
@@ -421,6 +435,12 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
           star_grp[pos++] = g;
         }
   }
+  int *dftp = nullptr, *dfti = nullptr, *dfmp = nullptr, *dfmi = nullptr;
+  float *dftc = nullptr, *dfmc = nullptr;
+  if ((rc = ctx_upload(ctx, &dftp, basis->ft_ptr)) || (rc = ctx_upload(ctx, &dfti, basis->ft_idx)) ||
+      (rc = ctx_upload(ctx, &dfmp, basis->fm_ptr)) || (rc = ctx_upload(ctx, &dfmi, basis->fm_idx)) ||
+      (rc = ctx_upload(ctx, &dftc, basis->ft_coef)) || (rc = ctx_upload(ctx, &dfmc, basis->fm_coef)))
+    return fail(rc);
   int *dpij = nullptr, *dcgp = nullptr, *dcgi = nullptr, *dchp = nullptr, *dchi = nullptr;
   float *dcgc = nullptr, *dchc = nullptr;
   if ((rc = ctx_upload(ctx, &dpij, basis->pair_ij)) || (rc = ctx_upload(ctx, &dcgp, basis->cg_ptr)) ||
@@ -560,6 +580,12 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
   a.cK = dc;
   a.star_ptr = dsp;
   a.star_el = dse;
+  a.ft_ptr = dftp;
+  a.ft_idx = dfti;
+  a.ft_coef = dftc;
+  a.fm_ptr = dfmp;
+  a.fm_idx = dfmi;
+  a.fm_coef = dfmc;
   a.pair_ij = dpij;
   a.cg_ptr = dcgp;
   a.cg_idx = dcgi;
@@ -628,12 +654,14 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
     const size_t half_nb = (NB + 1) / 2, half_rb = ((size_t)ctx->nrhs * NB + 1) / 2;
     // region used in turn by the monomials (point phases 1, 2, 4) and by A, the
     // summed Grams and the solve buffers (reduction to solve); A at offset 0
-    const size_t solve_part = NB * NB + (size_t)ngmax * (n + 2) * npair + NB * NB + (size_t)ctx->nrhs * NB + half_rb;
+    // (the binary32 sweep buffers of the solve reuse the summed Grams, dead after the congruence)
+    const size_t sg_al = std::max((size_t)ngmax * (n + 2) * npair, NB * NB);
+    const size_t solve_part = NB * NB + sg_al + (size_t)ctx->nrhs * NB + half_rb;
     const size_t mono_part = (size_t)2 * CH * a.mono_stride;
     a.off_mono = 0;
     take(nullptr, NB * NB);                        // A
-    take(&a.off_sg, (size_t)ngmax * (n + 2) * npair);
-    take(&a.off_al, NB * NB);                      // two binary32 N x N sweep buffers
+    a.off_al = (int)off;                           // two binary32 N x N sweep buffers
+    take(&a.off_sg, sg_al);
     take(&a.off_x, (size_t)ctx->nrhs * NB);
     take(&a.off_z, half_rb);
     off = std::max(solve_part, mono_part);
@@ -663,7 +691,9 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
   };
   int CH = 0;
   size_t bytes = 0, cap_used = 0;
-  for (size_t cap : {kTwoPerSmSmem, kMaxDynSmem}) {
+  size_t max_dyn = 0;
+  if ((rc = max_dyn_smem(n, &max_dyn)) != TP_OK) return fail(rc);
+  for (size_t cap : {kTwoPerSmSmem, max_dyn}) {
     for (int ch : {48, 32, 16, 8})
       if (CH == 0 && plan(ch, 0) <= cap) CH = ch;
     if (CH) {
@@ -688,7 +718,7 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
   ctx->args_adj.tau = ctx->d_tau_adj;
   ctx->args_adj.gD = nullptr;
   ctx->smem_bytes = bytes;
-  rc = set_smem_attr(n);
+  rc = set_smem_attr(n, max_dyn);
   if (rc) return fail(rc);
   {
     int nsm = 0;

@@ -516,6 +516,36 @@ extern "C" int tp_build_basis(int32_t dim, int32_t p, tp_basis** out) {
         B->cg_ptr.push_back((int32_t)B->cg_idx.size());
         B->ch_ptr.push_back((int32_t)B->ch_idx.size());
       }
+    // Dirichlet facet congruences (all entries: the forms are not symmetric)
+    B->ft_ptr.assign(1, 0);
+    B->fm_ptr.assign(1, 0);
+    for (int i = 0; i < nb; ++i)
+      for (int j = 0; j < nb; ++j) {
+        std::map<int, double> tm, mm;
+        int b0, e0, b1, e1;
+        rel_of(i, 0, &b0, &e0);
+        rel_of(j, 0, &b1, &e1);
+        for (int e = b0; e < e0; ++e)
+          for (int f = b1; f < e1; ++f) tm[pidx(B->rel_src[e], B->rel_src[f])] += B->rel_fac[e] * B->rel_fac[f];
+        for (int m = 1; m < NVAR; ++m) {
+          rel_of(j, m, &b1, &e1);
+          for (int e = b0; e < e0; ++e)
+            for (int f = b1; f < e1; ++f)
+              mm[((m - 1) << 16) | pidx(B->rel_src[e], B->rel_src[f])] += B->rel_fac[e] * B->rel_fac[f];
+        }
+        for (auto& kv : tm)
+          if (kv.second != 0.0) {
+            B->ft_idx.push_back(kv.first);
+            B->ft_coef.push_back((float)kv.second);
+          }
+        for (auto& kv : mm)
+          if (kv.second != 0.0) {
+            B->fm_idx.push_back(kv.first);
+            B->fm_coef.push_back((float)kv.second);
+          }
+        B->ft_ptr.push_back((int32_t)B->ft_idx.size());
+        B->fm_ptr.push_back((int32_t)B->fm_idx.size());
+      }
   }
   B->coef.assign((size_t)B->nb * B->nmono, 0.0);
   B->sp_ptr.assign(B->nb * C + 1, 0);

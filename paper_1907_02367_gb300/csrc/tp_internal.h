@@ -90,6 +90,11 @@ struct tp_basis {
   //   (sum_m D_m H_m D_t^T + D_t H_m D_m^T)_ij = sum over [ch_ptr[p], ch_ptr[p+1]) of
   //       ch_coef * H_{m}[ch_idx & 0xffff], m = ch_idx >> 16
   // (X, H_m packed symmetric; the coefficients are exact integers)
+  // Dirichlet facet congruences, every entry (i, j) of nb x nb (row-major):
+  //   (D_t F D_t^T)_ij = sum over [ft_ptr[ij], ft_ptr[ij+1]) of ft_coef * F[ft_idx]
+  //   (D_t F D_m^T)_ij = sum over [fm_ptr[ij], fm_ptr[ij+1]) of fm_coef * F[fm_idx & 0xffff], m = fm_idx >> 16
+  std::vector<int32_t> ft_ptr, ft_idx, fm_ptr, fm_idx;
+  std::vector<float> ft_coef, fm_coef;
   std::vector<int32_t> pair_ij;     // (i << 16) | j of packed entry p
   std::vector<int32_t> cg_ptr, cg_idx, ch_ptr, ch_idx;
   std::vector<float> cg_coef, ch_coef;

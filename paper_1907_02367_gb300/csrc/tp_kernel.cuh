@@ -75,6 +75,8 @@ struct KArgs {
   const int* pair_ij;
   const int *cg_ptr, *cg_idx, *ch_ptr, *ch_idx;
   const float *cg_coef, *ch_coef;
+  const int *ft_ptr, *ft_idx, *fm_ptr, *fm_idx;   // Dirichlet facet congruences (see tp_basis)
+  const float *ft_coef, *fm_coef;
   double* tau;
   double* front;
   const double* gD;
@@ -934,8 +936,21 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
         const T ac = R::from(a.alpha * cp * ih), cih = R::from(cp * ih), mih = R::from(-ih), pih = R::from(ih);
         for (int id = tid; id < nb * nb; id += blockDim.x) {
           const int i = id / nb, j = id % nb;
-          T tt_, tn_, nt_, nn_;
-          iface_terms<DIM, T, 0>(a, i, j, sF, nb, nrm, &tt_, &nt_, &tn_, &nn_);
+          // tt = (D_t F D_t^T)_ij, tn = (D_t F D_n^T)_ij from the merged tables
+          T tt_ = R::zero(), tm_[DIM];
+          for (int d = 0; d < DIM; ++d) tm_[d] = R::zero();
+          for (int e = __ldg(a.ft_ptr + id), e1 = __ldg(a.ft_ptr + id + 1); e < e1; ++e)
+            tt_ = R::accf(tt_, sF[__ldg(a.ft_idx + e)], __ldg(a.ft_coef + e));
+          for (int e = __ldg(a.fm_ptr + id), e1 = __ldg(a.fm_ptr + id + 1); e < e1; ++e) {
+            const int c0 = __ldg(a.fm_idx + e);
+            const int m = c0 >> 16;
+#pragma unroll
+            for (int d = 0; d < DIM; ++d)
+              if (d == m) tm_[d] = R::accf(tm_[d], sF[c0 & 0xffff], __ldg(a.fm_coef + e));
+          }
+          tt_ = R::norm(tt_);
+          T tn_ = R::zero();
+          for (int d = 0; d < DIM; ++d) tn_ = R::fma(nrm[d], R::norm(tm_[d]), tn_);
           // A_D = (c/h) D_t F E^T,  E = alpha (c/h) D_t - (1/h) D_n
           const T t = R::fma(mih, tn_, R::mul(ac, tt_));
           T* dst = sPD + (size_t)(gp * nb + i) * N + gp * nb + j;
@@ -1250,7 +1265,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
       }
     }
     const float* F = sG + (size_t)(N & 1) * N * N;
-    if (tid == 0) {   // composition of the interchanges: (P v)_j = v[sPerm[j]]
+    if (!pivoting) {   // no interchanges: sPerm already holds the identity
+    } else if (tid == 0) {   // composition of the interchanges: (P v)_j = v[sPerm[j]]
       int* idx = reinterpret_cast<int*>(sRD);   // scratch (the LU's reciprocal pivots are not live here)
       for (int j = 0; j < N; ++j) idx[j] = j;
       for (int k = 0; k < N; ++k) {
@@ -1343,32 +1359,43 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
       // stop once the correction is at the resolution of the residual's
       // precision, or once it stops shrinking at a small level (the residual's
       // rounding then limits the accuracy)
+      // (a correction that stalls above floor_ of the solution, or no
+      // convergence in kMaxRefine steps, sends the tent to the direct LU)
       const float tiny = MIXED ? 4e-15f : 2.5e-16f, floor_ = MIXED ? 1e-10f : 1e-12f;
-      if (!(isfinite(dm) && isfinite(xm))) {
-        if (MIXED && tid == 0) flag_error(a, TP_ERR_NOCONV, tent);
-        break;
-      }
+      const float stall = 0.5f;
+      if (!(isfinite(dm) && isfinite(xm))) break;   // the direct LU decides
       // (the next correction is predicted as dm * (dm / prev) once the
       // corrections shrink fast; stop when that is below the resolution too)
-      const bool done = dm <= tiny * xm || (it >= 2 && dm > 0.5f * prev && dm <= floor_ * xm) ||
+      const bool done = dm <= tiny * xm || (it >= 2 && dm > stall * prev && dm <= floor_ * xm) ||
                         (it >= 2 && dm <= 0.01f * prev && 4.f * dm * (dm / prev) <= tiny * xm);
       prev = dm;
       if (done) {
         refined = true;
         break;
       }
-      if (MIXED && it == maxit - 1 && dm > 1e-8f * xm && tid == 0) flag_error(a, TP_ERR_NOCONV, tent);
       // (the next iteration writes s_red only after its first barrier)
     }
-    if (MIXED || refined) {
+    if (refined) {
       __syncthreads();
       for (int id = tid; id < nrhs * N; id += blockDim.x) sb[id] = sX[id];
       __syncthreads();
     }
   }
-  if constexpr (!MIXED) {
-  if (!refined) {   // direct binary64 LU
+  if (!refined) {   // direct binary64 LU (the mixed path converts A and b to binary64 first)
     __syncthreads();
+    double* dA = reinterpret_cast<double*>(sA);   // in place: a float-float pair and a double share 8 bytes
+    double* db = reinterpret_cast<double*>(sb);
+    if constexpr (MIXED) {
+      for (int id = tid; id < N * N; id += blockDim.x) {
+        const T v = sA[id];
+        dA[id] = R::to(v);
+      }
+      for (int id = tid; id < nrhs * N; id += blockDim.x) {
+        const T v = sb[id];
+        db[id] = R::to(v);
+      }
+      __syncthreads();
+    }
     double* sXd = reinterpret_cast<double*>(sm + a.off_x);   // nrhs*N  solution during back substitution
     auto pivot_recip = [&](double piv, int k) {
       if (!(fabs(piv) > 0.0) || !isfinite(piv)) {
@@ -1382,22 +1409,22 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
       // alongside, one barrier per step.  Step k updates rows and columns > k;
       // every thread forms the multiplier a_ik / a_kk it needs, and the thread
       // that updates a_{k+1,k+1} forms the next reciprocal pivot.
-      if (tid == 0) pivot_recip(sA[0], 0);
+      if (tid == 0) pivot_recip(dA[0], 0);
       __syncthreads();
       for (int k = 0; k + 1 < N; ++k) {
         const double rp = sRD[k];
         const int rem = N - k - 1, wdt = rem + nrhs;
         for (int id = tid; id < rem * wdt; id += blockDim.x) {
           const int i = k + 1 + id / wdt, jj = id % wdt;
-          const double l = sA[i * N + k] * rp;
+          const double l = dA[i * N + k] * rp;
           if (jj < rem) {
             const int j = k + 1 + jj;
-            const double t = fma(-l, sA[k * N + j], sA[i * N + j]);
-            sA[i * N + j] = t;
+            const double t = fma(-l, dA[k * N + j], dA[i * N + j]);
+            dA[i * N + j] = t;
             if (id == 0) pivot_recip(t, k + 1);
           } else {
             const int r = jj - rem;
-            sb[r * N + i] = fma(-l, sb[r * N + k], sb[r * N + i]);
+            db[r * N + i] = fma(-l, db[r * N + k], db[r * N + i]);
           }
         }
         __syncthreads();
@@ -1410,7 +1437,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
           unsigned long long best = 0ull;
           int bi = k;
           for (int i = k + lane; i < N; i += 32) {
-            const unsigned long long bits = (unsigned long long)__double_as_longlong(fabs(sA[i * N + k]));
+            const unsigned long long bits = (unsigned long long)__double_as_longlong(fabs(dA[i * N + k]));
             if (bits > best || (bits == best && i < bi)) {
               best = bits;
               bi = i;
@@ -1426,21 +1453,21 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
           }
           if (lane == 0) {
             s_piv = bi;
-            pivot_recip(sA[bi * N + k], k);
+            pivot_recip(dA[bi * N + k], k);
           }
         }
         __syncthreads();
         const int pr = s_piv;
         if (pr != k) {
           for (int j = tid; j < N; j += blockDim.x) {
-            const double t = sA[k * N + j];
-            sA[k * N + j] = sA[pr * N + j];
-            sA[pr * N + j] = t;
+            const double t = dA[k * N + j];
+            dA[k * N + j] = dA[pr * N + j];
+            dA[pr * N + j] = t;
           }
           for (int r = tid; r < nrhs; r += blockDim.x) {
-            const double t = sb[r * N + k];
-            sb[r * N + k] = sb[r * N + pr];
-            sb[r * N + pr] = t;
+            const double t = db[r * N + k];
+            db[r * N + k] = db[r * N + pr];
+            db[r * N + pr] = t;
           }
           __syncthreads();
         }
@@ -1448,13 +1475,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
         const int rem = N - k - 1, wdt = rem + nrhs;
         for (int id = tid; id < rem * wdt; id += blockDim.x) {
           const int i = k + 1 + id / wdt, jj = id % wdt;
-          const double l = sA[i * N + k] * rp;
+          const double l = dA[i * N + k] * rp;
           if (jj < rem) {
             const int j = k + 1 + jj;
-            sA[i * N + j] = fma(-l, sA[k * N + j], sA[i * N + j]);
+            dA[i * N + j] = fma(-l, dA[k * N + j], dA[i * N + j]);
           } else {
             const int r = jj - rem;
-            sb[r * N + i] = fma(-l, sb[r * N + k], sb[r * N + i]);
+            db[r * N + i] = fma(-l, db[r * N + k], db[r * N + i]);
           }
         }
         __syncthreads();
@@ -1466,14 +1493,20 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
       const double rp = sRD[k];
       for (int id = tid; id < (k + 1) * nrhs; id += blockDim.x) {
         const int r = id / (k + 1), i = id % (k + 1);
-        const double xk = sb[r * N + k] * rp;
+        const double xk = db[r * N + k] * rp;
         if (i == k) sXd[r * N + k] = xk;
-        else sb[r * N + i] = fma(-sA[i * N + k], xk, sb[r * N + i]);
+        else db[r * N + i] = fma(-dA[i * N + k], xk, db[r * N + i]);
       }
       __syncthreads();
     }
-    for (int id = tid; id < nrhs * N; id += blockDim.x) sb[id] = sXd[id];
-  }
+    for (int id = tid; id < nrhs * N; id += blockDim.x) db[id] = sXd[id];
+    if constexpr (MIXED) {
+      __syncthreads();
+      for (int id = tid; id < nrhs * N; id += blockDim.x) {
+        const double v = db[id];
+        sb[id] = R::from(v);
+      }
+    }
   }
   }   // rank 0
   cluster.sync();   // the solution is in rank 0's b
@@ -1570,6 +1603,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
 // persistent: one resident grid of clusters pulling tents from a queue
 #define TP_DECLARE_LAUNCHERS(D)                                                                  \
   cudaError_t layer_attrs_d##D(size_t smem);                                                      \
+  cudaError_t layer_static_smem_d##D(size_t* bytes);                                              \
   cudaError_t launch_layer_d##D(const KArgs& a, int n_cluster, int cs, int t0, size_t smem,       \
                                 cudaStream_t st, int mode, bool persistent);                      \
   cudaError_t max_clusters_d##D(int cs, size_t smem, int mode, int* n);

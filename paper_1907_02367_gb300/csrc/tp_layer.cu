@@ -1,6 +1,8 @@
 // Instantiations and launchers of the tent kernel for one space dimension.
 // Compiled once per dimension with -DTP_DIM=1, 2 or 3 (the translation units
 // build in parallel).
+#include <algorithm>
+
 #include "tp_kernel.cuh"
 
 #ifndef TP_DIM
@@ -54,6 +56,24 @@ cudaError_t occupancy(int cs, size_t smem, int* n) {
 }
 
 }  // namespace
+
+// largest static shared memory of the instantiations (bytes)
+cudaError_t TP_CAT(layer_static_smem_d, TP_DIM)(size_t* bytes) {
+  size_t m = 0;
+  cudaFuncAttributes fa;
+  cudaError_t e;
+  if ((e = cudaFuncGetAttributes(&fa, k_layer<TP_DIM, false, false, false>)) != cudaSuccess) return e;
+  m = std::max(m, fa.sharedSizeBytes);
+  if ((e = cudaFuncGetAttributes(&fa, k_layer<TP_DIM, true, false, false>)) != cudaSuccess) return e;
+  m = std::max(m, fa.sharedSizeBytes);
+  if ((e = cudaFuncGetAttributes(&fa, k_layer<TP_DIM, false, true, false>)) != cudaSuccess) return e;
+  m = std::max(m, fa.sharedSizeBytes);
+  if ((e = cudaFuncGetAttributes(&fa, k_layer<TP_DIM, false, false, true>)) != cudaSuccess) return e;
+  m = std::max(m, fa.sharedSizeBytes);
+  if ((e = cudaFuncGetAttributes(&fa, k_layer<TP_DIM, true, false, true>)) != cudaSuccess) return e;
+  *bytes = std::max(m, fa.sharedSizeBytes);
+  return cudaSuccess;
+}
 
 cudaError_t TP_CAT(layer_attrs_d, TP_DIM)(size_t smem) {
   cudaError_t e;
