@@ -23,6 +23,7 @@
 #include <type_traits>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -288,6 +289,7 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
   ctx->level_ptr = tents->level_ptr;
   // patch checks: size limits; materials (distinct wave speeds) per tent
   int ngmax = 1, pmax = 1;
+  std::vector<std::array<int, 3>> facet_mix;   // distinct (materials, Dirichlet facets, interface facets)
   for (int64_t v = 0; v < T.nv; ++v) {
     const int p0 = T.star_ptr[v], p1 = T.star_ptr[v + 1];
     pmax = std::max(pmax, p1 - p0);
@@ -304,6 +306,9 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
       if (std::find(speeds.begin(), speeds.end(), T.c[T.star_el[e]]) == speeds.end())
         speeds.push_back(T.c[T.star_el[e]]);
     ngmax = std::max(ngmax, (int)speeds.size());
+    const std::array<int, 3> mix = {(int)speeds.size(), T.vfac_ptr[v + 1] - T.vfac_ptr[v],
+                                    T.ifac_ptr[v + 1] - T.ifac_ptr[v]};
+    if (std::find(facet_mix.begin(), facet_mix.end(), mix) == facet_mix.end()) facet_mix.push_back(mix);
   }
   if (ngmax > tp::kMaxGroups) {
     tp::set_error("tp_create: a tent has more than 4 materials (wave speeds)");
@@ -656,6 +661,12 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
     // summed Grams and the solve buffers (reduction to solve); A at offset 0
     // (the binary32 sweep buffers of the solve reuse the summed Grams, dead after the congruence)
     const size_t sg_al = std::max((size_t)ngmax * (n + 2) * npair, NB * NB);
+    // interface blocks (tents with interface facets) followed by the Dirichlet
+    // sums of every material (tents with Dirichlet facets), partials reduced in place
+    size_t pd = 0;
+    for (const auto& m : facet_mix)
+      pd = std::max(pd, (m[2] > 0 ? (size_t)m[0] * nb * m[0] * nb : 0) +
+                            (m[1] > 0 ? (size_t)m[0] * (n + 1) * (npair + (size_t)ctx->nrhs * nb) : 0));
     const size_t solve_part = NB * NB + sg_al + (size_t)ctx->nrhs * NB + half_rb;
     const size_t mono_part = (size_t)2 * CH * a.mono_stride;
     a.off_mono = 0;
@@ -670,8 +681,7 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
     take(&a.off_ph, (size_t)ngmax * n * npair);
     take(&a.off_pgb, (size_t)ngmax * npair);
     take(&a.off_pm, (size_t)ngmax * nmom);
-    take(&a.off_pd, NB * NB);
-    take(&a.off_pbd, (size_t)ctx->nrhs * NB);
+    take(&a.off_pd, pd);
     take(&a.off_sm, (size_t)ngmax * nmom);
     take(&a.off_f, npair);
     take(&a.off_f2, npair);

@@ -103,7 +103,7 @@ struct KArgs {
   int off_al, off_eq, off_perm, off_z, off_x;   // mixed path: binary32 LU and refinement
   int off_pt;                                   // per-point (that, xhat, scale) of the block-wide evaluation
   int keep_pts, off_keep, off_keepw;            // kept top U-values (scaled) and 1/sqrt(w) of a CTA's slice
-  int off_b, off_pg, off_ph, off_pgb, off_pm, off_pd, off_pbd, off_sg, off_sm, off_f, off_f2, off_fpm, off_del,
+  int off_b, off_pg, off_ph, off_pgb, off_pm, off_pd, off_sg, off_sm, off_f, off_f2, off_fpm, off_del,
       off_u, off_mono, off_cb, off_gd, off_y, off_rd;
 };
 
@@ -536,8 +536,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
   T* sPH = reinterpret_cast<T*>(sm + a.off_ph);      // NG*DIM*npair  H_m
   T* sPGb = reinterpret_cast<T*>(sm + a.off_pgb);    // NG*npair   G (bottom, recovery)
   T* sPM = reinterpret_cast<T*>(sm + a.off_pm);      // NG*nmom    moments (gamma, alpha, beta_m) per rhs
-  T* sPD = reinterpret_cast<T*>(sm + a.off_pd);      // N*N        Dirichlet and interface blocks
-  T* sPBD = reinterpret_cast<T*>(sm + a.off_pbd);    // nrhs*N     Dirichlet right-hand side
+  T* sPD = reinterpret_cast<T*>(sm + a.off_pd);      // N*N        interface blocks (tents with interface facets)
   T* sSG = reinterpret_cast<T*>(sm + a.off_sg);      // NG*(DIM+2)*npair  summed G, H_m, Gbot
   T* sSM = reinterpret_cast<T*>(sm + a.off_sm);      // NG*nmom    summed moments
   T* sF = reinterpret_cast<T*>(sm + a.off_f);        // npair      facet Gram (+ side)
@@ -852,9 +851,19 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
   }
 
   // ---------------- phase 2: vertical faces (this CTA's slice of each facet's points) ----------------
+  // Dirichlet facets, per material g, after the interface blocks: the facet
+  // Grams summed over g's facets, G_g, and weighted by the facets' normals,
+  // Gn_g[d] = sum_f n_f[d] F_f (layout [G_g | Gn_g[0..DIM)] of npair each),
+  // then the data moments in the same arrangement (nrhs*nb each).  The
+  // congruences with the derivative maps are linear, so these sums carry all
+  // a tent needs; they are formed after the cluster reduction.
+  T* sFD = sPD + (nif > 0 ? (size_t)N * N : 0);
+  T* sDD = sFD + (size_t)ng * (DIM + 1) * npair;
+  const int nfd = nfac > 0 ? ng * (DIM + 1) * (npair + nrhs * nb) : 0;
   if (extra) {
-    for (int id = tid; id < N * N; id += blockDim.x) sPD[id] = R::zero();
-    for (int id = tid; id < nrhs * N; id += blockDim.x) sPBD[id] = R::zero();
+    if (nif > 0)
+      for (int id = tid; id < N * N; id += blockDim.x) sPD[id] = R::zero();
+    for (int id = tid; id < nfd; id += blockDim.x) sFD[id] = R::zero();
     for (int id = tid; id < nrhs * nb; id += blockDim.x) sDel[id] = R::zero();
     for (int id = tid; id < nb * nb; id += blockDim.x) sFpm[id] = R::zero();
     const int fsl = (Q + CS - 1) / CS;
@@ -923,6 +932,27 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
         }
         __syncthreads();
       }
+      if (dir) {   // fold the facet into its material's sums
+        T nrm[DIM];
+        for (int d = 0; d < DIM; ++d) nrm[d] = R::from(s_fn[f][d]);
+        T* Fg = sFD + (size_t)gp * (DIM + 1) * npair;
+#pragma unroll
+        for (int s = 0; s < kMaxPair; ++s)
+          if (tid + s * kThreads < npair) {
+            const int q = tid + s * kThreads;
+            Fg[q] = R::add(Fg[q], aF[s]);
+            for (int d = 0; d < DIM; ++d) Fg[(1 + d) * npair + q] = R::fma(nrm[d], aF[s], Fg[(1 + d) * npair + q]);
+          }
+        T* Dg = sDD + (size_t)gp * (DIM + 1) * nrhs * nb;
+        for (int id = tid; id < nrhs * nb; id += blockDim.x) {
+          const T del = sDel[id];
+          Dg[id] = R::add(Dg[id], del);
+          for (int d = 0; d < DIM; ++d) Dg[(1 + d) * nrhs * nb + id] = R::fma(nrm[d], del, Dg[(1 + d) * nrhs * nb + id]);
+          sDel[id] = R::zero();
+        }
+        __syncthreads();
+        continue;
+      }
 #pragma unroll
       for (int s = 0; s < kMaxPair; ++s)
         if (tid + s * kThreads < npair) {
@@ -932,41 +962,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
       __syncthreads();
       T nrm[DIM];
       for (int d = 0; d < DIM; ++d) nrm[d] = R::from(s_fn[f][d]);
-      if (dir) {
-        const T ac = R::from(a.alpha * cp * ih), cih = R::from(cp * ih), mih = R::from(-ih), pih = R::from(ih);
-        for (int id = tid; id < nb * nb; id += blockDim.x) {
-          const int i = id / nb, j = id % nb;
-          // tt = (D_t F D_t^T)_ij, tn = (D_t F D_n^T)_ij from the merged tables
-          T tt_ = R::zero(), tm_[DIM];
-          for (int d = 0; d < DIM; ++d) tm_[d] = R::zero();
-          for (int e = __ldg(a.ft_ptr + id), e1 = __ldg(a.ft_ptr + id + 1); e < e1; ++e)
-            tt_ = R::accf(tt_, sF[__ldg(a.ft_idx + e)], __ldg(a.ft_coef + e));
-          for (int e = __ldg(a.fm_ptr + id), e1 = __ldg(a.fm_ptr + id + 1); e < e1; ++e) {
-            const int c0 = __ldg(a.fm_idx + e);
-            const int m = c0 >> 16;
-#pragma unroll
-            for (int d = 0; d < DIM; ++d)
-              if (d == m) tm_[d] = R::accf(tm_[d], sF[c0 & 0xffff], __ldg(a.fm_coef + e));
-          }
-          tt_ = R::norm(tt_);
-          T tn_ = R::zero();
-          for (int d = 0; d < DIM; ++d) tn_ = R::fma(nrm[d], R::norm(tm_[d]), tn_);
-          // A_D = (c/h) D_t F E^T,  E = alpha (c/h) D_t - (1/h) D_n
-          const T t = R::fma(mih, tn_, R::mul(ac, tt_));
-          T* dst = sPD + (size_t)(gp * nb + i) * N + gp * nb + j;
-          *dst = R::fma(cih, t, *dst);
-        }
-        for (int id = tid; id < nrhs * nb; id += blockDim.x) {
-          const int r = id / nb, i = id % nb;
-          const T* del = sDel + (size_t)r * nb;
-          T dn = R::zero();
-          for (int d = 0; d < DIM; ++d) dn = R::fma(nrm[d], rel_apply<DIM, T>(a, i, 1 + d, del), dn);
-          // b_D = E' delta,  E' = alpha (c/h) D_t + (1/h) D_n
-          const T t = R::fma(pih, dn, R::mul(ac, rel_apply<DIM, T>(a, i, 0, del)));
-          T* dst = sPBD + (size_t)r * N + gp * nb + i;
-          *dst = R::add(*dst, t);
-        }
-      } else {
+      {
         const double ih2 = ih * ih;
         for (int id = tid; id < 4 * nb * nb; id += blockDim.x) {
           const int blk = id / (nb * nb), rem = id % (nb * nb), i = rem / nb, j = rem % nb;
@@ -1026,12 +1022,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
   // layout [G (NG*npair) | H_m (NG*DIM*npair) | Gbot (NG*npair)]; unused groups hold zeros
   cluster_reduce(sPG, sSG, NG * (DIM + 2) * npair);
   cluster_reduce(sPM, sSM, ng * nmom);
-  if (extra) cluster_reduce(sPD, sA, N * N);
+  if (nif > 0) cluster_reduce(sPD, sA, N * N);   // interface blocks
   else
     for (int id = tid; id < N * N; id += blockDim.x) sA[id] = R::zero();
-  if (nfac > 0) cluster_reduce(sPBD, sb, nrhs * N);
-  else
-    for (int id = tid; id < nrhs * N; id += blockDim.x) sb[id] = R::zero();
+  for (int id = tid; id < nrhs * N; id += blockDim.x) sb[id] = R::zero();
+  // in place: each entry is read and rewritten by the one thread that owns it
+  if (nfac > 0) cluster_reduce(sFD, sFD, nfd);
   cluster.sync();   // no CTA leaves or reuses its partials while another still reads them
   // congruence: rank r forms rows [N r / CS, N (r + 1) / CS) of A and b and
   // stores them into rank 0's A and b; rank 0 alone solves.  Every CTA holds
@@ -1046,6 +1042,39 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
     // is stored with its mirror (the form is symmetric, the Dirichlet and
     // interface parts already in A are not)
     const int nent = ng * npair, ent0 = (nent * rank) / CS, ent1 = (nent * (rank + 1)) / CS;
+    unsigned gdir = 0;   // materials with Dirichlet facets
+    for (int f = 0; f < nfac; ++f) gdir |= 1u << s_fg[f];
+    if (nfac > 0) {
+      // Dirichlet facets, A_D = (c/h) D_t F E^T with E = alpha (c/h) D_t - (1/h) D_n
+      // summed over the material's facets, from G_g and Gn_g, added into this
+      // CTA's copy of A for the entries this rank forms (each entry and its
+      // mirror: one item each)
+      for (int id = tid; id < 2 * (ent1 - ent0); id += blockDim.x) {
+        const int e_ = ent0 + (id >> 1), g = e_ / npair, pp = e_ % npair;
+        const int ij = __ldg(a.pair_ij + pp);
+        int i = ij >> 16, j = ij & 0xffff;
+        if (((id & 1) && i == j) || !((gdir >> g) & 1u)) continue;
+        if (id & 1) {
+          const int t_ = i;
+          i = j;
+          j = t_;
+        }
+        const int e2 = i * nb + j;
+        const T* Fg = sFD + (size_t)g * (DIM + 1) * npair;
+        T a0 = R::zero(), am = R::zero();
+        for (int e = __ldg(a.ft_ptr + e2), e1 = __ldg(a.ft_ptr + e2 + 1); e < e1; ++e)
+          a0 = R::accf(a0, Fg[__ldg(a.ft_idx + e)], __ldg(a.ft_coef + e));
+        for (int e = __ldg(a.fm_ptr + e2), e1 = __ldg(a.fm_ptr + e2 + 1); e < e1; ++e) {
+          const int c0 = __ldg(a.fm_idx + e);   // (derivative direction << 16) | pair
+          am = R::accf(am, Fg[(size_t)(1 + (c0 >> 16)) * npair + (c0 & 0xffff)], __ldg(a.fm_coef + e));
+        }
+        const double cf = s_gc[g];
+        const T ad = R::mul(R::from(cf * ih), R::fma(mih, R::norm(am), R::mul(R::from(a.alpha * cf * ih), R::norm(a0))));
+        const size_t o = (size_t)(g * nb + i) * N + g * nb + j;
+        sA[o] = R::add(sA[o], ad);
+      }
+      __syncthreads();
+    }
     for (int id = ent0 + tid; id < ent1; id += blockDim.x) {
       const int g = id / npair, pp = id % npair;
       const int ij = __ldg(a.pair_ij + pp), i = ij >> 16, j = ij & 0xffff;
@@ -1090,6 +1119,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
       const T* M = sSM + (size_t)g * nmom + (size_t)r * C * nb;   // gamma, alpha, beta_1..beta_n
       T t = R::fma(R::from(s_gc[g] * ih), rel_apply<DIM, T>(a, i, 0, M + nb), M[i]);
       for (int d = 0; d < DIM; ++d) t = R::fma(mih, rel_apply<DIM, T>(a, i, 1 + d, M + (2 + d) * nb), t);
+      // Dirichlet data: b_D = E' delta summed over g's facets,
+      // E' = alpha (c/h) D_t + (1/h) D_n
+      if ((gdir >> g) & 1u) {
+        const T* Dg = sDD + (size_t)g * (DIM + 1) * nrhs * nb + (size_t)r * nb;
+        T dn = rel_apply<DIM, T>(a, i, 1, Dg + (size_t)nrhs * nb);
+        for (int d = 1; d < DIM; ++d) dn = R::add(dn, rel_apply<DIM, T>(a, i, 1 + d, Dg + (size_t)(1 + d) * nrhs * nb));
+        const T ac = R::from(a.alpha * s_gc[g] * ih);
+        t = R::add(t, R::fma(R::from(ih), dn, R::mul(ac, rel_apply<DIM, T>(a, i, 0, Dg))));
+      }
       const size_t o = (size_t)r * N + Rw;
       b0[o] = R::add(sb[o], t);
     }
@@ -1115,7 +1153,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
   // then x += D F D (b - A x) with the residual in the path's precision
   // (binary64, or float-float for MIXED) until the correction stops shrinking.
   // binary64: a refinement that does not settle falls back to a direct LU.
-  const bool pivoting = extra || ng > 1;
+  // Every tent matrix has a positive definite symmetric part (testing the
+  // tent system with V = U_h gives x^T A x = 1/2 int_top Q_g(u) + 1/2 int_bot
+  // Q_g(u_b) + int_bot U^2 + the dissipative boundary and interface terms > 0),
+  // so elimination without interchanges does not break down; the sweeps use
+  // none, and the direct LU of the fallback keeps partial pivoting.
+  const bool pivoting = false;
+  const bool lu_pivoting = extra || ng > 1;
   bool refined = false;
   {
     float* sG = reinterpret_cast<float*>(sm + a.off_al);    // 2*N*N   ping-pong sweep buffers
@@ -1404,7 +1448,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
       }
       sRD[k] = recip(piv);
     };
-    if (!pivoting) {
+    if (!lu_pivoting) {
       // A is symmetric positive definite: LU without interchanges, b eliminated
       // alongside, one barrier per step.  Step k updates rows and columns > k;
       // every thread forms the multiplier a_ik / a_kk it needs, and the thread

@@ -319,3 +319,31 @@ def test_interface_energy_identity_1d():
 
 def _sinsin_1d_init(x):
     return _sinsin_1d(x, 0.3)
+
+
+@pytest.mark.parametrize("dim,p", [(1, 3), (2, 3)])
+def test_tent_matrix_symmetric_part_positive_definite(dim, p):
+    """For Trefftz trial functions the tent form tested with the trial function
+    itself is 1/2 int_top Q + 1/2 int_bot Q + int_bot U^2 + alpha int_D v^2 +
+    the interface jumps (the energy flux through the tent's boundary, eq. (2.5)
+    with the upwind and Dirichlet fluxes of Section 4): the symmetric part of
+    every tent matrix, interior, Dirichlet and interface tents alike, is
+    positive definite, so elimination without row interchanges cannot break
+    down on it."""
+    mesh = inputs.mesh_interval(6) if dim == 1 else inputs.mesh_square(4, 0.2, seed=3)
+    cen = mesh.coords[mesh.elems].mean(axis=1)
+    mesh.c[:] = np.where(np.linalg.norm(cen - 0.5, axis=1) < 0.3, 3.0, 1.0)
+    kinds, worst = set(), np.inf
+    bnd = np.isclose(mesh.coords, 0.0).any(axis=1) | np.isclose(mesh.coords, 1.0).any(axis=1)
+
+    def rec(it, d):
+        nonlocal worst
+        A = d["A"]
+        lam = np.linalg.eigvalsh(0.5 * (A + A.T))
+        worst = min(worst, lam[0] / lam[-1])
+        kinds.add(("dirichlet" if bnd[d["v"]] else "interior", len(d["speeds"])))
+
+    sol = inputs.polynomial_solution(dim, 0)
+    _run(mesh, p, 0.2, sol, inputs.pitch_kappa(mesh), record=rec)
+    assert ("dirichlet", 1) in kinds and ("interior", 2) in kinds and ("interior", 1) in kinds
+    assert worst > 0.0, worst
