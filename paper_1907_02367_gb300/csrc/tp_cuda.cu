@@ -492,6 +492,77 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
   }
   double *deinv = nullptr, *desdet = nullptr;
   if ((rc = ctx_upload(ctx, &deinv, einv)) || (rc = ctx_upload(ctx, &desdet, esdet))) return fail(rc);
+  // per vertex: one record with all of its star that does not depend on the
+  // sweep, so that a tent reads it in one round of loads.
+  //   ints:    per element (el, material, vertex ids[n+1]); per facet (Dirichlet
+  //            first, then interface): (vertex ids other than v in slots 2..n,
+  //            material of the + element, of the - element)
+  //   doubles: x_v[n], speeds[kMaxGroups]; per element its vertex coordinates
+  //            [(n+1) n]; per facet its normal [n] and vertex coordinates [(n+1) n]
+  // per tent: (v, int offset, double offset, elements, Dirichlet facets,
+  // interface facets, materials, 0)
+  std::vector<int> rec_i, tent_hdr((size_t)ctx->ntents * 8, 0);
+  std::vector<double> rec_d;
+  std::vector<int> vrec_i(T.nv), vrec_d(T.nv);
+  {
+    const int NVn = n + 1;
+    auto grp_of = [&](int64_t v, double ck) {
+      int g = 0;
+      while (g < vert_ng[v] - 1 && vert_gc[(size_t)v * tp::kMaxGroups + g] != ck) ++g;
+      return g;
+    };
+    for (int64_t v = 0; v < T.nv; ++v) {
+      vrec_i[v] = (int)rec_i.size();
+      vrec_d[v] = (int)rec_d.size();
+      for (int d = 0; d < n; ++d) rec_d.push_back(T.X[(size_t)v * n + d]);
+      for (int g = 0; g < tp::kMaxGroups; ++g) rec_d.push_back(vert_gc[(size_t)v * tp::kMaxGroups + g]);
+      for (int e = T.star_ptr[v]; e < T.star_ptr[v + 1]; ++e) {
+        const int el = star_sorted[e];
+        rec_i.push_back(el);
+        rec_i.push_back(star_grp[e]);
+        for (int i = 0; i < NVn; ++i) {
+          const int vi = T.elems[(size_t)el * NVn + i];
+          rec_i.push_back(vi);
+          for (int d = 0; d < n; ++d) rec_d.push_back(T.X[(size_t)vi * n + d]);
+        }
+      }
+      const int nf = T.vfac_ptr[v + 1] - T.vfac_ptr[v], ni = T.ifac_ptr[v + 1] - T.ifac_ptr[v];
+      for (int f = 0; f < nf + ni; ++f) {
+        const bool dir = f < nf;
+        const int fid = dir ? T.vfac[T.vfac_ptr[v] + f] : T.ifac_ptr[v] + (f - nf);
+        const int* fv = dir ? &T.facet_vert[(size_t)fid * n] : &T.ifac_vert[(size_t)fid * n];
+        const double* fn = dir ? &T.facet_nrm[(size_t)fid * n] : &T.ifac_nrm[(size_t)fid * n];
+        int w_[4] = {(int)v, (int)v, -1, -1};
+        int c2 = 2;
+        for (int i = 0; i < n; ++i)
+          if (fv[i] != v) w_[c2++] = fv[i];
+        for (int i = 0; i < NVn; ++i) rec_i.push_back(w_[i]);
+        rec_i.push_back(grp_of(v, T.c[dir ? T.facet_elem[fid] : T.ifac_kp[fid]]));
+        rec_i.push_back(grp_of(v, T.c[dir ? T.facet_elem[fid] : T.ifac_km[fid]]));
+        for (int d = 0; d < n; ++d) rec_d.push_back(fn[d]);
+        for (int i = 0; i < NVn; ++i)
+          for (int d = 0; d < n; ++d) rec_d.push_back(w_[i] >= 0 ? T.X[(size_t)w_[i] * n + d] : 0.0);
+      }
+    }
+    for (int64_t it = 0; it < ctx->ntents; ++it) {
+      const int v = tents->vert[it];
+      int* h = &tent_hdr[(size_t)it * 8];
+      h[0] = v;
+      h[1] = vrec_i[v];
+      h[2] = vrec_d[v];
+      h[3] = T.star_ptr[v + 1] - T.star_ptr[v];
+      h[4] = T.vfac_ptr[v + 1] - T.vfac_ptr[v];
+      h[5] = T.ifac_ptr[v + 1] - T.ifac_ptr[v];
+      h[6] = vert_ng[v];
+    }
+  }
+  std::vector<double> tent_ih(ctx->ntents);
+  for (int64_t it = 0; it < ctx->ntents; ++it) tent_ih[it] = 1.0 / tent_h[it];
+  int *dthdr = nullptr, *dreci = nullptr;
+  double *drecd = nullptr, *dtih = nullptr;
+  if ((rc = ctx_upload(ctx, &dthdr, tent_hdr)) || (rc = ctx_upload(ctx, &dreci, rec_i)) ||
+      (rc = ctx_upload(ctx, &drecd, rec_d)) || (rc = ctx_upload(ctx, &dtih, tent_ih)))
+    return fail(rc);
   int *dsso = nullptr, *dsgr = nullptr, *dvng = nullptr;
   double* dvgc = nullptr;
   if ((rc = ctx_upload(ctx, &dsso, star_sorted)) || (rc = ctx_upload(ctx, &dsgr, star_grp)) ||
@@ -615,6 +686,10 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
   a.tent_ttop = dttop;
   a.tent_tbot = dtbot;
   a.tent_h = dh;
+  a.tent_ih = dtih;
+  a.tent_hdr = dthdr;
+  a.vrec_i = dreci;
+  a.vrec_d = drecd;
   a.tent_gdoff = dgo;
   a.sp_ptr = dspp;
   a.sp_mono = dspm;

@@ -64,6 +64,10 @@ struct KArgs {
   const double* tent_ttop;
   const double* tent_tbot;
   const double* tent_h;
+  const double* tent_ih;      // 1 / h
+  const int* tent_hdr;        // per tent: v, record offsets (int, double), elements, Dirichlet and interface facets, materials, 0
+  const int* vrec_i;          // per vertex: star record, ints (elements, facets)
+  const double* vrec_d;       // per vertex: star record, doubles (x_v, speeds, coordinates, normals)
   const long long* tent_gdoff;
   const int* sp_ptr;
   const int* sp_mono;
@@ -491,7 +495,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
   constexpr int NV = DIM + 1;   // vertices per element
   constexpr int C = DIM + 2;    // U, v, sigma  (and gamma, alpha, beta_m moments)
   extern __shared__ __align__(16) double sm[];
-  __shared__ int s_P, s_v, s_nfac, s_nif, s_ng, s_p0;
+  __shared__ int s_P, s_v, s_nfac, s_nif, s_ng;
   __shared__ double s_ttop, s_tbot, s_tc, s_ih;
   __shared__ double s_gc[tp::kMaxGroups];
   __shared__ double s_xv[DIM];
@@ -555,72 +559,49 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
   // (a) what does not depend on earlier tents: vertex star, coordinates,
   // materials, facets; in the dataflow sweep it is fetched while the tents
   // this one depends on may still be running
+  // one round of loads: the tent's header, then its vertex's star record
+  const int4 h0 = __ldg(reinterpret_cast<const int4*>(a.tent_hdr) + 2 * (size_t)tent);
+  const int4 h1 = __ldg(reinterpret_cast<const int4*>(a.tent_hdr) + 2 * (size_t)tent + 1);
+  const int v = h0.x, P = h0.w, nfac = h1.x, nif = h1.y, ng = h1.z;
   if (tid == 0) {
-    const int v = a.tent_v[tent];
     s_v = v;
-    const int p0 = a.star_ptr[v], p1 = a.star_ptr[v + 1];
-    const int P = p1 - p0;
     s_P = P;
     s_ttop = a.tent_ttop[tent];
-    s_ih = 1.0 / a.tent_h[tent];
-    for (int d = 0; d < DIM; ++d) s_xv[d] = a.X[(int64_t)v * DIM + d];
-    s_nfac = a.vfac_ptr[v + 1] - a.vfac_ptr[v];
-    s_nif = a.ifac_ptr[v + 1] - a.ifac_ptr[v];
-    s_p0 = p0;
-    // materials by bitwise-equal c in order of first appearance (host tables)
-    const int ng = a.vert_ng[v];
-    for (int g = 0; g < ng; ++g) s_gc[g] = a.vert_gc[(int64_t)v * tp::kMaxGroups + g];
+    s_ih = a.tent_ih[tent];
+    s_nfac = nfac;
+    s_nif = nif;
     s_ng = ng;
   }
   for (int id = tid; id < NG * nmom; id += blockDim.x) sPM[id] = R::zero();
   for (int id = tid; id < NG * (DIM + 2) * npair; id += blockDim.x) sPG[id] = R::zero();   // PG, PH, PGb contiguous
-  __syncthreads();
-  const int P = s_P, v = s_v, nfac = s_nfac, nif = s_nif, ng = s_ng;
   const int N = ng * nb;
   const bool extra = (nfac > 0 || nif > 0);
-  for (int k = tid; k < P; k += blockDim.x) {
-    const int el = a.star_sorted[s_p0 + k];   // elements sorted by material
-    s_el[k] = el;
-    s_grp[k] = a.star_grp[s_p0 + k];
-    for (int i = 0; i < NV; ++i) {
-      const int vi = a.elems[(int64_t)el * NV + i];
-      s_vid[k][i] = vi;
-      for (int d = 0; d < DIM; ++d) s_X[k][i][d] = a.X[(int64_t)vi * DIM + d];
+  {
+    const int* ri = a.vrec_i + h0.y;
+    const double* rd = a.vrec_d + h0.z;
+    if (tid < DIM) s_xv[tid] = __ldg(rd + tid);
+    if (tid < ng) s_gc[tid] = __ldg(rd + DIM + tid);
+    const double* rX = rd + DIM + tp::kMaxGroups;
+    for (int k = tid; k < P; k += blockDim.x) {
+      s_el[k] = __ldg(ri + k * (2 + NV));
+      s_grp[k] = __ldg(ri + k * (2 + NV) + 1);
+      for (int i = 0; i < NV; ++i) {
+        s_vid[k][i] = __ldg(ri + k * (2 + NV) + 2 + i);
+        for (int d = 0; d < DIM; ++d) s_X[k][i][d] = __ldg(rX + (k * NV + i) * DIM + d);
+      }
     }
-  }
-  // vertical face simplices (x_v, t_bot), (x_v, t_top), (x_w, tau_w): Dirichlet facets
-  // first, then the time-like interface facets
-  for (int f = tid; f < nfac + nif; f += blockDim.x) {
-    const bool dir = f < nfac;
-    const int fid = dir ? a.vfac[a.vfac_ptr[v] + f] : a.ifac_ptr[v] + (f - nfac);
-    const int* fv = dir ? a.facet_vert + (int64_t)fid * DIM : a.ifac_vert + (int64_t)fid * DIM;
-    const double* fn = dir ? a.facet_nrm + (int64_t)fid * DIM : a.ifac_nrm + (int64_t)fid * DIM;
-    for (int d = 0; d < DIM; ++d) {
-      s_fP[f][0][d] = a.X[(int64_t)v * DIM + d];
-      s_fP[f][1][d] = a.X[(int64_t)v * DIM + d];
-      s_fn[f][d] = fn[d];
-    }
-    int c2 = 2;
-    for (int i = 0; i < DIM; ++i) {
-      const int w = fv[i];
-      if (w == v) continue;
-      for (int d = 0; d < DIM; ++d) s_fP[f][c2][d] = a.X[(int64_t)w * DIM + d];
-      s_fw[f][c2] = w;
-      ++c2;
-    }
-    // groups of the facet's element(s), found by their wave speed
-    auto group_of = [&](int el) {
-      const double ce = a.cK[el];
-      int g = 0;
-      while (g < ng - 1 && s_gc[g] != ce) ++g;
-      return g;
-    };
-    if (dir) {
-      s_fg[f] = group_of(a.facet_elem[fid]);
-      s_fg2[f] = s_fg[f];
-    } else {
-      s_fg[f] = group_of(a.ifac_kp[fid]);
-      s_fg2[f] = group_of(a.ifac_km[fid]);
+    // vertical face simplices (x_v, t_bot), (x_v, t_top), (x_w, tau_w): Dirichlet
+    // facets first, then the time-like interface facets
+    const int* rfi = ri + P * (2 + NV);
+    const double* rfd = rX + P * NV * DIM;
+    for (int f = tid; f < nfac + nif; f += blockDim.x) {
+      for (int i = 2; i < NV; ++i) s_fw[f][i] = __ldg(rfi + f * (NV + 2) + i);
+      s_fg[f] = __ldg(rfi + f * (NV + 2) + NV);
+      s_fg2[f] = __ldg(rfi + f * (NV + 2) + NV + 1);
+      const double* fd = rfd + f * (DIM + NV * DIM);
+      for (int d = 0; d < DIM; ++d) s_fn[f][d] = __ldg(fd + d);
+      for (int i = 0; i < NV; ++i)
+        for (int d = 0; d < DIM; ++d) s_fP[f][i][d] = __ldg(fd + DIM + i * DIM + d);
     }
   }
   if constexpr (PERSIST) {
@@ -850,7 +831,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
     flush_group(curg);
   }
 
-  // ---------------- phase 2: vertical faces (this CTA's slice of each facet's points) ----------------
+  // ---------------- phase 2: vertical faces ----------------
   // Dirichlet facets, per material g, after the interface blocks: the facet
   // Grams summed over g's facets, G_g, and weighted by the facets' normals,
   // Gn_g[d] = sum_f n_f[d] F_f (layout [G_g | Gn_g[0..DIM)] of npair each),
@@ -866,11 +847,92 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
     for (int id = tid; id < nfd; id += blockDim.x) sFD[id] = R::zero();
     for (int id = tid; id < nrhs * nb; id += blockDim.x) sDel[id] = R::zero();
     for (int id = tid; id < nb * nb; id += blockDim.x) sFpm[id] = R::zero();
+    __syncthreads();
+    // (a) Dirichlet facets: the points of all of them (facet after facet) in
+    // one pass, split over the cluster; a facet's Gram and moments are folded
+    // into its material's sums where its points end
+    if (nfac > 0) {
+      const int NPD = nfac * Q, dsl = (NPD + CS - 1) / CS;
+      const int d0 = min(NPD, rank * dsl), d1 = min(NPD, d0 + dsl);
+      T aF[kMaxPair];
+#pragma unroll
+      for (int s = 0; s < kMaxPair; ++s) aF[s] = R::zero();
+      auto fold_gram = [&](int f) {
+        if (f >= nfac) return;
+        T* Fg = sFD + (size_t)s_fg[f] * (DIM + 1) * npair;
+#pragma unroll
+        for (int s = 0; s < kMaxPair; ++s)
+          if (tid + s * kThreads < npair) {
+            const int q = tid + s * kThreads;
+            Fg[q] = R::add(Fg[q], aF[s]);
+            for (int d = 0; d < DIM; ++d)
+              Fg[(1 + d) * npair + q] = R::fma(R::from(s_fn[f][d]), aF[s], Fg[(1 + d) * npair + q]);
+            aF[s] = R::zero();
+          }
+      };
+      auto fold_mom = [&](int f, int id, T t) {
+        if (f >= nfac) return;
+        T* Dg = sDD + (size_t)s_fg[f] * (DIM + 1) * nrhs * nb;
+        Dg[id] = R::add(Dg[id], t);
+        for (int d = 0; d < DIM; ++d)
+          Dg[(1 + d) * nrhs * nb + id] = R::fma(R::from(s_fn[f][d]), t, Dg[(1 + d) * nrhs * nb + id]);
+      };
+      int fc = d0 / Q;   // facet of the points being accumulated (uniform over the CTA)
+      for (int base = d0; base < d1; base += CH) {
+        const int nq = min(CH, d1 - base);
+        for (int id = tid; id < nq; id += blockDim.x) {
+          const int q = base + id, f = q / Q, qf = q - f * Q;
+          double xt[DIM + 1];
+          for (int d = 0; d <= DIM; ++d) xt[d] = 0.0;
+          for (int i = 0; i < NV; ++i) {
+            const double l = __ldg(a.bary + qf * NV + i);
+            for (int d = 0; d <= DIM; ++d) xt[d] = fma(l, s_fP[f][i][d], xt[d]);
+          }
+          const double sw = sqrt(__ldg(a.wref + qf) * s_fscale[f]);
+          T* pp = sPt + id * (DIM + 2);
+          pp[0] = R::from(s_gc[s_fg[f]] * (xt[DIM] - tc) * ih);
+          for (int d = 0; d < DIM; ++d) pp[1 + d] = R::from((xt[d] - s_xv[d]) * ih);
+          pp[DIM + 1] = R::from(sw);
+          const long long goff = a.tent_gdoff[tent] + q;
+          for (int r = 0; r < nrhs; ++r)
+            sGd[id * nrhs + r] = R::from((!ADJ && a.gD != nullptr) ? sw * a.gD[(long long)r * a.n_bnd + goff] : 0.0);
+        }
+        eval_uvalues_block<DIM, T>(a, nq, sPt, sM, sU);
+        const int fc0 = fc;
+        for (int ql = 0; ql < nq; ++ql) {
+          if (base + ql >= (fc + 1) * Q) fold_gram(fc++);
+          const T* u = sU + (size_t)ql * nb;
+#pragma unroll
+          for (int s = 0; s < kMaxPair; ++s)
+            if (tid + s * kThreads < npair) aF[s] = R::fma(u[pi[s]], u[pj[s]], aF[s]);
+        }
+        for (int id = tid; id < nrhs * nb; id += blockDim.x) {
+          const int r = id / nb, i = id % nb;
+          int f = fc0;
+          T t = sDel[id];
+          for (int ql = 0; ql < nq; ++ql) {
+            if (base + ql >= (f + 1) * Q) {
+              fold_mom(f++, id, t);
+              t = R::zero();
+            }
+            t = R::fma(sGd[ql * nrhs + r], sU[(size_t)ql * nb + i], t);
+          }
+          sDel[id] = t;
+        }
+        __syncthreads();
+      }
+      fold_gram(fc);
+      for (int id = tid; id < nrhs * nb; id += blockDim.x) {
+        fold_mom(fc, id, sDel[id]);
+        sDel[id] = R::zero();
+      }
+      __syncthreads();
+    }
+    // (b) time-like interface facets, one after the other, each facet's points
+    // split over the cluster; their blocks go into the partial A at once
     const int fsl = (Q + CS - 1) / CS;
     const int f0 = min(Q, rank * fsl), f1 = min(Q, f0 + fsl);
-    __syncthreads();
-    for (int f = 0; f < nfac + nif; ++f) {
-      const bool dir = f < nfac;
+    for (int f = nfac; f < nfac + nif; ++f) {
       const int gp = s_fg[f], gm = s_fg2[f];
       const double cp = s_gc[gp], cm = s_gc[gm];
       T aF[kMaxPair], aF2[kMaxPair];
@@ -878,7 +940,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
       for (int s = 0; s < kMaxPair; ++s) aF[s] = aF2[s] = R::zero();
       for (int base = f0; base < f1; base += CH) {
         const int nq = min(CH, f1 - base);
-        const int npt = dir ? nq : 2 * nq;   // interface: + side points, then - side
+        const int npt = 2 * nq;   // + side points, then - side
         for (int id = tid; id < nq; id += blockDim.x) {
           const int q = base + id;
           double xt[DIM + 1];
@@ -892,17 +954,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
           pp[0] = R::from(cp * (xt[DIM] - tc) * ih);
           for (int d = 0; d < DIM; ++d) pp[1 + d] = R::from((xt[d] - s_xv[d]) * ih);
           pp[DIM + 1] = R::from(sw);
-          if (!dir) {
-            T* p2 = sPt + (nq + id) * (DIM + 2);
-            p2[0] = R::from(cm * (xt[DIM] - tc) * ih);
-            for (int d = 0; d < DIM; ++d) p2[1 + d] = pp[1 + d];
-            p2[DIM + 1] = pp[DIM + 1];
-          }
-          if (dir) {
-            const long long goff = a.tent_gdoff[tent] + (long long)f * Q + q;
-            for (int r = 0; r < nrhs; ++r)
-              sGd[id * nrhs + r] = R::from((!ADJ && a.gD != nullptr) ? sw * a.gD[(long long)r * a.n_bnd + goff] : 0.0);
-          }
+          T* p2 = sPt + (nq + id) * (DIM + 2);
+          p2[0] = R::from(cm * (xt[DIM] - tc) * ih);
+          for (int d = 0; d < DIM; ++d) p2[1 + d] = pp[1 + d];
+          p2[DIM + 1] = pp[DIM + 1];
         }
         eval_uvalues_block<DIM, T>(a, npt, sPt, sM, sU);
         for (int ql = 0; ql < nq; ++ql) {
@@ -912,46 +967,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
           for (int s = 0; s < kMaxPair; ++s)
             if (tid + s * kThreads < npair) {
               aF[s] = R::fma(u[pi[s]], u[pj[s]], aF[s]);
-              if (!dir) aF2[s] = R::fma(u2[pi[s]], u2[pj[s]], aF2[s]);
+              aF2[s] = R::fma(u2[pi[s]], u2[pj[s]], aF2[s]);
             }
         }
-        if (dir) {
-          for (int id = tid; id < nrhs * nb; id += blockDim.x) {
-            const int r = id / nb, i = id % nb;
-            T t = sDel[id];
-            for (int ql = 0; ql < nq; ++ql) t = R::fma(sGd[ql * nrhs + r], sU[(size_t)ql * nb + i], t);
-            sDel[id] = t;
-          }
-        } else {
-          for (int id = tid; id < nb * nb; id += blockDim.x) {
-            const int i = id / nb, j = id % nb;
-            T t = sFpm[id];
-            for (int ql = 0; ql < nq; ++ql) t = R::fma(sU[(size_t)ql * nb + i], sU[(size_t)(nq + ql) * nb + j], t);
-            sFpm[id] = t;
-          }
+        for (int id = tid; id < nb * nb; id += blockDim.x) {
+          const int i = id / nb, j = id % nb;
+          T t = sFpm[id];
+          for (int ql = 0; ql < nq; ++ql) t = R::fma(sU[(size_t)ql * nb + i], sU[(size_t)(nq + ql) * nb + j], t);
+          sFpm[id] = t;
         }
         __syncthreads();
-      }
-      if (dir) {   // fold the facet into its material's sums
-        T nrm[DIM];
-        for (int d = 0; d < DIM; ++d) nrm[d] = R::from(s_fn[f][d]);
-        T* Fg = sFD + (size_t)gp * (DIM + 1) * npair;
-#pragma unroll
-        for (int s = 0; s < kMaxPair; ++s)
-          if (tid + s * kThreads < npair) {
-            const int q = tid + s * kThreads;
-            Fg[q] = R::add(Fg[q], aF[s]);
-            for (int d = 0; d < DIM; ++d) Fg[(1 + d) * npair + q] = R::fma(nrm[d], aF[s], Fg[(1 + d) * npair + q]);
-          }
-        T* Dg = sDD + (size_t)gp * (DIM + 1) * nrhs * nb;
-        for (int id = tid; id < nrhs * nb; id += blockDim.x) {
-          const T del = sDel[id];
-          Dg[id] = R::add(Dg[id], del);
-          for (int d = 0; d < DIM; ++d) Dg[(1 + d) * nrhs * nb + id] = R::fma(nrm[d], del, Dg[(1 + d) * nrhs * nb + id]);
-          sDel[id] = R::zero();
-        }
-        __syncthreads();
-        continue;
       }
 #pragma unroll
       for (int s = 0; s < kMaxPair; ++s)
@@ -987,7 +1012,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
         }
       }
       __syncthreads();
-      for (int id = tid; id < nrhs * nb; id += blockDim.x) sDel[id] = R::zero();
       for (int id = tid; id < nb * nb; id += blockDim.x) sFpm[id] = R::zero();
       __syncthreads();
     }
@@ -1357,17 +1381,20 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
       if (regs) {
         for (int r = 0; r < nrhs; ++r) {
           const float vj = (lane < N) ? sZ[(size_t)r * N + sPerm[lane]] : 0.f;
+          float zs = 0.f;   // lane s_ < 4 ends with the sum of slot s_
 #pragma unroll
           for (int s_ = 0; s_ < 4; ++s_) {
-            const int i = warp + 8 * s_;
             float z = gr[s_] * vj;
             for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(0xffffffffu, z, o);
-            if (i < N && lane == s_) {
-              const float dx = sEq[i] * z;
-              const size_t o_ = (size_t)r * N + i;
-              sX[o_] = R::addf(sX[o_], dx);
-              dmax = fmaxf(dmax, fabsf(dx));
-            }
+            if (lane == s_) zs = z;
+          }
+          // one update instruction per warp for its (up to) four rows
+          const int i = warp + 8 * lane;
+          if (lane < 4 && i < N) {
+            const float dx = sEq[i] * zs;
+            const size_t o_ = (size_t)r * N + i;
+            sX[o_] = R::addf(sX[o_], dx);
+            dmax = fmaxf(dmax, fabsf(dx));
           }
         }
       }
