@@ -635,6 +635,34 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
     }
     for (int d = 0; d <= basis->p + 1; ++d) a.mono_lv[d] = (d ? a.mono_lv[d - 1] : 0) + cnt[d];
   }
+  {
+    // U-value sums: functions ordered by their number of terms (key 0: one
+    // term of coefficient 1, a copy)
+    const int Cc = n + 2;
+    std::vector<std::pair<int, int>> key(basis->nb);
+    for (int j = 0; j < basis->nb; ++j) {
+      const int e0 = basis->sp_ptr[j * Cc], e1 = basis->sp_ptr[j * Cc + 1];
+      key[j] = {(e1 - e0 == 1 && basis->sp_coef[e0] == 1.0) ? 0 : e1 - e0, j};
+    }
+    std::sort(key.begin(), key.end());
+    std::vector<int> ev_order;
+    a.ev_ncls = 0;
+    for (int j = 0; j < basis->nb; ++j) {
+      if (j == 0 || key[j].first != key[j - 1].first) {
+        if (a.ev_ncls == tp::kMaxEvCls) {
+          tp::set_error("tp_create: basis functions with more than 16 distinct term counts");
+          return fail(TP_ERR_UNSUPPORTED);
+        }
+        a.ev_off[a.ev_ncls] = j;
+        a.ev_terms[a.ev_ncls++] = key[j].first;
+      }
+      ev_order.push_back(key[j].second);
+    }
+    a.ev_off[a.ev_ncls] = basis->nb;
+    int* devo = nullptr;
+    if ((rc = ctx_upload(ctx, &devo, ev_order))) return fail(rc);
+    a.ev_order = devo;
+  }
   a.Q = Q;
   a.nrhs = ctx->nrhs;
   a.ne = T.ne;

@@ -14,6 +14,7 @@ void set_error(const std::string& msg);
 
 constexpr int kMaxDim = 3;
 constexpr int kMaxP = 8;
+constexpr int kMaxEvCls = 16;   // classes of basis functions by term count
 constexpr int kMaxPatch = 64;     // elements in one vertex star handled by one CTA
 constexpr int kMaxFacets = 16;    // Dirichlet + interface facets through one vertex
 constexpr int kMaxGroups = 4;     // materials (distinct wave speeds) in one tent

@@ -34,6 +34,12 @@ struct KArgs {
   int nb, nmono, Q, nrhs, CH, mono_stride, ngmax;
   int p;                          // degree of U^p
   int mono_lv[kMaxP + 2];         // monomials of total degree d: [mono_lv[d], mono_lv[d+1])
+  // U-value sums: basis functions in classes of equal term count (class with
+  // ev_terms 0: one term of coefficient 1); class c is ev_order[ev_off[c] .. ev_off[c+1])
+  int ev_ncls;
+  int ev_off[kMaxEvCls + 1];
+  int ev_terms[kMaxEvCls];
+  const int* ev_order;
   int64_t ne, n_bnd;
   double alpha, beta;
   const double* X;
@@ -313,8 +319,13 @@ __device__ __forceinline__ void eval_uvalues_block(const KArgs& a, int npt, cons
     }
   }
   __syncthreads();
+  // items (function, four points) class after class, so that the lanes of a
+  // warp run loops of one length; a one-term function of coefficient 1 is a copy
   for (int id = tid; id < nb * nq4; id += blockDim.x) {
-    const int j = id % nb, q0 = (id / nb) << 2;
+    int c = 0;
+    while (id >= a.ev_off[c + 1] * nq4) ++c;
+    const int f0 = a.ev_off[c], nj = a.ev_off[c + 1] - f0, loc = id - f0 * nq4;
+    const int j = __ldg(a.ev_order + f0 + loc % nj), q0 = (loc / nj) << 2;
     const int e0 = __ldg(a.sp_ptr + j * (DIM + 2)), e1 = __ldg(a.sp_ptr + j * (DIM + 2) + 1);
     int qq[4];
     T acc[4];
@@ -322,6 +333,13 @@ __device__ __forceinline__ void eval_uvalues_block(const KArgs& a, int npt, cons
     for (int t = 0; t < 4; ++t) {
       qq[t] = min(q0 + t, npt - 1);
       acc[t] = Ar<T>::zero();
+    }
+    if (a.ev_terms[c] == 0) {
+      const int g = __ldg(a.sp_mono + e0);
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+        if (q0 + t < npt) u[qq[t] * nb + j] = m[qq[t] * ms + g];
+      continue;
     }
     for (int e = e0; e < e1; ++e) {
       const T c = Ar<T>::coef(a, e);
