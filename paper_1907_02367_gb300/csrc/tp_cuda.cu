@@ -1,8 +1,9 @@
-// libtp device side: context, the per-level tent kernel (FP64), the energy
-// reduction and the CUDA-graph sweep.
+// libtp device side: context, shared-memory plan, launches of the tent
+// kernel (per level in a CUDA graph, or one persistent dataflow launch), the
+// energy reduction.
 //
-// One CTA solves one tent (Section 4.1, eq. 4.1 with the Section 5 recovery
-// terms).  For a tent at vertex v with patch star(v), basis U_h = sum_j x_j b_j
+// One cluster of CTAs solves one tent (Section 4.1, eq. 4.1 with the Section 5
+// recovery terms).  For a tent at vertex v with patch star(v), basis U_h = sum_j x_j b_j
 // of U^p (Section 3, Remark 3.1 scaling) and front points q of every patch
 // element K (one spatial rule mapped onto the faces, Fig. 2):
 //
@@ -15,8 +16,10 @@
 //   bottom data (RHS):  b_i += w_q [ (c^-2 v_b - s_b.g_b) v_i + (s_b - v_b g_b).s_i + U_b U_i ];
 //   Dirichlet vertical faces (eq. 4.1):
 //     A_ij += w (s_j.n + alpha v_j) v_i,  b_i += w g_D (alpha v_i - s_i.n).
-// Then LU with partial pivoting, and (U, v, sigma) at the top points overwrite
-// the front (Section 4.1: only the latest values are stored).
+// Then the local solve (a binary32 inverse of the equilibrated matrix and
+// refinement in the path's precision, a direct binary64 LU as fallback), and
+// (U, v, sigma) at the top points overwrite the front (Section 4.1: only the
+// latest values are stored).
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
@@ -446,6 +449,13 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
       (rc = ctx_upload(ctx, &dfmp, basis->fm_ptr)) || (rc = ctx_upload(ctx, &dfmi, basis->fm_idx)) ||
       (rc = ctx_upload(ctx, &dftc, basis->ft_coef)) || (rc = ctx_upload(ctx, &dfmc, basis->fm_coef)))
     return fail(rc);
+  double *dcgd = nullptr, *dchd = nullptr, *dftd = nullptr, *dfmd = nullptr;   // binary64 copies (exact)
+  {
+    auto widen = [](const std::vector<float>& f) { return std::vector<double>(f.begin(), f.end()); };
+    if ((rc = ctx_upload(ctx, &dcgd, widen(basis->cg_coef))) || (rc = ctx_upload(ctx, &dchd, widen(basis->ch_coef))) ||
+        (rc = ctx_upload(ctx, &dftd, widen(basis->ft_coef))) || (rc = ctx_upload(ctx, &dfmd, widen(basis->fm_coef))))
+      return fail(rc);
+  }
   int *dpij = nullptr, *dcgp = nullptr, *dcgi = nullptr, *dchp = nullptr, *dchi = nullptr;
   float *dcgc = nullptr, *dchc = nullptr;
   if ((rc = ctx_upload(ctx, &dpij, basis->pair_ij)) || (rc = ctx_upload(ctx, &dcgp, basis->cg_ptr)) ||
@@ -697,6 +707,10 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
   a.ch_idx = dchi;
   a.cg_coef = dcgc;
   a.ch_coef = dchc;
+  a.cg_coefd = dcgd;
+  a.ch_coefd = dchd;
+  a.ft_coefd = dftd;
+  a.fm_coefd = dfmd;
   a.elem_einv = deinv;
   a.elem_sdet = desdet;
   a.star_sorted = dsso;
@@ -797,7 +811,6 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
     take(&a.off_y, (size_t)ngmax * nmom);
     take(&a.off_rd, NB);
     take(&a.off_eq, half_nb);
-    take(&a.off_perm, half_nb);
     take(&a.off_keep, (size_t)keep * nb);          // top U-values of the CTA's slice, kept for the outflow
     take(&a.off_keepw, (size_t)keep);
     return off * sizeof(double);

@@ -87,6 +87,7 @@ struct KArgs {
   const float *cg_coef, *ch_coef;
   const int *ft_ptr, *ft_idx, *fm_ptr, *fm_idx;   // Dirichlet facet congruences (see tp_basis)
   const float *ft_coef, *fm_coef;
+  const double *cg_coefd, *ch_coefd, *ft_coefd, *fm_coefd;   // the same coefficients in binary64
   double* tau;
   double* front;
   const double* gD;
@@ -110,7 +111,7 @@ struct KArgs {
   const double* relT_fac;
   const float* rel_facf;      // relation factors (small integers) in binary32
   const float* relT_facf;
-  int off_al, off_eq, off_perm, off_z, off_x;   // mixed path: binary32 LU and refinement
+  int off_al, off_eq, off_z, off_x;             // solve: binary32 inverse and refinement
   int off_pt;                                   // per-point (that, xhat, scale) of the block-wide evaluation
   int keep_pts, off_keep, off_keepw;            // kept top U-values (scaled) and 1/sqrt(w) of a CTA's slice
   int off_b, off_pg, off_ph, off_pgb, off_pm, off_pd, off_sg, off_sm, off_f, off_f2, off_fpm, off_del,
@@ -354,6 +355,31 @@ __device__ __forceinline__ void eval_uvalues_block(const KArgs& a, int npt, cons
   __syncthreads();
 }
 
+// s + y f for a factor f of a table of small exact numbers (derivative
+// relations, merged congruence tables): binary64 reads the table's binary64
+// copy and takes one fused multiply-add; float-float reads the binary32 copy
+// (add: exact product and float-float sum; acc: a compensated long-sum step)
+template <typename T>
+struct Fac;
+template <>
+struct Fac<double> {
+  static __device__ __forceinline__ double add(double s, double y, const float*, const double* fd, int e) {
+    return ::fma(y, __ldg(fd + e), s);
+  }
+  static __device__ __forceinline__ double acc(double s, double y, const float*, const double* fd, int e) {
+    return ::fma(y, __ldg(fd + e), s);
+  }
+};
+template <>
+struct Fac<dd> {
+  static __device__ __forceinline__ dd add(dd s, dd y, const float* ff, const double*, int e) {
+    return dd_add(s, dd_mulf(y, __ldg(ff + e)));
+  }
+  static __device__ __forceinline__ dd acc(dd s, dd y, const float* ff, const double*, int e) {
+    return Ar<dd>::accf(s, y, __ldg(ff + e));
+  }
+};
+
 // packed upper-triangle index of (i, j), i, j < nb
 __device__ __forceinline__ int pair_index(int i, int j, int nb) {
   const int lo = min(i, j), hi = max(i, j);
@@ -373,8 +399,8 @@ __device__ __forceinline__ T congruence(const KArgs& a, int i, int va, int j, in
     const int si = __ldg(a.rel_src + e);
     T t = Ar<T>::zero();
     for (int f = b0; f < b1; ++f)
-      t = Ar<T>::add(t, Ar<T>::mulf(X[pair_index(si, __ldg(a.rel_src + f), nb)], __ldg(a.rel_facf + f)));
-    s = Ar<T>::add(s, Ar<T>::mulf(t, __ldg(a.rel_facf + e)));
+      t = Fac<T>::add(t, X[pair_index(si, __ldg(a.rel_src + f), nb)], a.rel_facf, a.rel_fac, f);
+    s = Fac<T>::add(s, t, a.rel_facf, a.rel_fac, e);
   }
   return s;
 }
@@ -384,7 +410,7 @@ template <int DIM, typename T>
 __device__ __forceinline__ T rel_apply(const KArgs& a, int i, int var, const T* y) {
   const int e0 = __ldg(a.rel_ptr + i * (DIM + 1) + var), e1 = __ldg(a.rel_ptr + i * (DIM + 1) + var + 1);
   T s = Ar<T>::zero();
-  for (int e = e0; e < e1; ++e) s = Ar<T>::add(s, Ar<T>::mulf(y[__ldg(a.rel_src + e)], __ldg(a.rel_facf + e)));
+  for (int e = e0; e < e1; ++e) s = Fac<T>::add(s, y[__ldg(a.rel_src + e)], a.rel_facf, a.rel_fac, e);
   return s;
 }
 
@@ -393,8 +419,18 @@ template <int DIM, typename T>
 __device__ __forceinline__ T relT_apply(const KArgs& a, int k, int var, const T* y) {
   const int e0 = __ldg(a.relT_ptr + k * (DIM + 1) + var), e1 = __ldg(a.relT_ptr + k * (DIM + 1) + var + 1);
   T s = Ar<T>::zero();
-  for (int e = e0; e < e1; ++e) s = Ar<T>::add(s, Ar<T>::mulf(y[__ldg(a.relT_dst + e)], __ldg(a.relT_facf + e)));
+  for (int e = e0; e < e1; ++e) s = Fac<T>::add(s, y[__ldg(a.relT_dst + e)], a.relT_facf, a.relT_fac, e);
   return s;
+}
+
+// binary32 reciprocal of the hardware's approximate reciprocal instruction
+// (about 1 ulp): the binary32 inverse of the solve is refined against A, so its
+// last bit does not matter, and the correctly rounded reciprocal costs several
+// times as long on the critical path of the elimination
+__device__ __forceinline__ float rcp_fast(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
 }
 
 // 1/x by two Newton-Raphson steps r <- r + r (1 - x r) from the binary32
@@ -422,9 +458,9 @@ __device__ __forceinline__ T congruence_full(const KArgs& a, int i, int va, int 
     T t = Ar<T>::zero();
     for (int f = b0; f < b1; ++f) {
       const int sj = __ldg(a.rel_src + f);
-      t = Ar<T>::add(t, Ar<T>::mulf(TR ? X[sj * nb + si] : X[si * nb + sj], __ldg(a.rel_facf + f)));
+      t = Fac<T>::add(t, TR ? X[sj * nb + si] : X[si * nb + sj], a.rel_facf, a.rel_fac, f);
     }
-    s = Ar<T>::add(s, Ar<T>::mulf(t, __ldg(a.rel_facf + e)));
+    s = Fac<T>::add(s, t, a.rel_facf, a.rel_fac, e);
   }
   return s;
 }
@@ -482,12 +518,11 @@ __device__ __forceinline__ void iface_terms(const KArgs& a, int i, int j, const 
 // after a cluster barrier every CTA sums them in rank order, forms A and b,
 // solves, and writes the outflow of its slice.
 //
-// MIXED = false: everything in binary64, LU with partial pivoting (none for
-// single-material interior tents, whose A is symmetric positive definite).
-// MIXED = true: assembly, residual and outflow in float-float; A is
-// equilibrated (D A D, D = |diag A|^-1/2), factorised in binary32 and the
-// solution refined against the float-float A until the correction stops
-// shrinking (at most kMaxRefine steps; TP_ERR_NOCONV if it stalls high).
+// MIXED = false: assembly, residual and outflow in binary64; MIXED = true:
+// in float-float.  Both: A is equilibrated (D A D, D = |diag A|^-1/2),
+// inverted in binary32 and the solution refined against A in the path's
+// precision until the correction stops shrinking; a refinement that does not
+// settle falls back to a direct binary64 LU.
 //
 // ADJ = true: the adjoint tent map (reverse sweep).  With g_D = 0 a tent maps
 // its bottom values linearly to its top values, b = B f_bot, A x = b,
@@ -528,8 +563,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
   __shared__ int s_fg[tp::kMaxFacets], s_fg2[tp::kMaxFacets];   // groups (Dirichlet: one; interface: +, -)
   __shared__ int s_pgrp[2 * 64];
   __shared__ int s_piv;
-  __shared__ float s_prow[2][32], s_xrow[2][32], s_cval[kThreads / 32];   // register sweeps: pivot rows
-  __shared__ int s_cidx[kThreads / 32];
+  __shared__ float s_pb[2][4][32];   // register sweeps: the pivot rows of a block of four steps
   __shared__ float s_red[2][kThreads / 32];
 
   __shared__ int s_tent;
@@ -1105,10 +1139,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
         const T* Fg = sFD + (size_t)g * (DIM + 1) * npair;
         T a0 = R::zero(), am = R::zero();
         for (int e = __ldg(a.ft_ptr + e2), e1 = __ldg(a.ft_ptr + e2 + 1); e < e1; ++e)
-          a0 = R::accf(a0, Fg[__ldg(a.ft_idx + e)], __ldg(a.ft_coef + e));
+          a0 = Fac<T>::acc(a0, Fg[__ldg(a.ft_idx + e)], a.ft_coef, a.ft_coefd, e);
         for (int e = __ldg(a.fm_ptr + e2), e1 = __ldg(a.fm_ptr + e2 + 1); e < e1; ++e) {
           const int c0 = __ldg(a.fm_idx + e);   // (derivative direction << 16) | pair
-          am = R::accf(am, Fg[(size_t)(1 + (c0 >> 16)) * npair + (c0 & 0xffff)], __ldg(a.fm_coef + e));
+          am = Fac<T>::acc(am, Fg[(size_t)(1 + (c0 >> 16)) * npair + (c0 & 0xffff)], a.fm_coef, a.fm_coefd, e);
         }
         const double cf = s_gc[g];
         const T ad = R::mul(R::from(cf * ih), R::fma(mih, R::norm(am), R::mul(R::from(a.alpha * cf * ih), R::norm(a0))));
@@ -1128,22 +1162,22 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
         const int e0 = __ldg(a.cg_ptr + pp), e1 = __ldg(a.cg_ptr + pp + 1);
         int e = e0;
         for (; e + 1 < e1; e += 2) {
-          tg0 = R::accf(tg0, SG[__ldg(a.cg_idx + e)], __ldg(a.cg_coef + e));
-          tg1 = R::accf(tg1, SG[__ldg(a.cg_idx + e + 1)], __ldg(a.cg_coef + e + 1));
+          tg0 = Fac<T>::acc(tg0, SG[__ldg(a.cg_idx + e)], a.cg_coef, a.cg_coefd, e);
+          tg1 = Fac<T>::acc(tg1, SG[__ldg(a.cg_idx + e + 1)], a.cg_coef, a.cg_coefd, e + 1);
         }
-        if (e < e1) tg0 = R::accf(tg0, SG[__ldg(a.cg_idx + e)], __ldg(a.cg_coef + e));
+        if (e < e1) tg0 = Fac<T>::acc(tg0, SG[__ldg(a.cg_idx + e)], a.cg_coef, a.cg_coefd, e);
       }
       {
         const int e0 = __ldg(a.ch_ptr + pp), e1 = __ldg(a.ch_ptr + pp + 1);
         int e = e0;
         for (; e + 1 < e1; e += 2) {
           const int c0 = __ldg(a.ch_idx + e), c1 = __ldg(a.ch_idx + e + 1);
-          th0 = R::accf(th0, SH[(c0 >> 16) * npair + (c0 & 0xffff)], __ldg(a.ch_coef + e));
-          th1 = R::accf(th1, SH[(c1 >> 16) * npair + (c1 & 0xffff)], __ldg(a.ch_coef + e + 1));
+          th0 = Fac<T>::acc(th0, SH[(c0 >> 16) * npair + (c0 & 0xffff)], a.ch_coef, a.ch_coefd, e);
+          th1 = Fac<T>::acc(th1, SH[(c1 >> 16) * npair + (c1 & 0xffff)], a.ch_coef, a.ch_coefd, e + 1);
         }
         if (e < e1) {
           const int c0 = __ldg(a.ch_idx + e);
-          th0 = R::accf(th0, SH[(c0 >> 16) * npair + (c0 & 0xffff)], __ldg(a.ch_coef + e));
+          th0 = Fac<T>::acc(th0, SH[(c0 >> 16) * npair + (c0 & 0xffff)], a.ch_coef, a.ch_coefd, e);
         }
       }
       const T t = R::fma(R::from(s_gc[g]), R::add(R::norm(th0), R::norm(th1)), R::add(R::norm(tg0), R::norm(tg1)));
@@ -1190,24 +1224,22 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
 
   // ---------------- phase 3: solve ----------------
   // Both precisions: the equilibrated matrix D A D (D = |diag A|^-1/2) is
-  // inverted in binary32 by Gauss-Jordan sweeps (two ping-pong copies, one
-  // barrier per sweep; row interchanges on Dirichlet and interface tents),
-  // then x += D F D (b - A x) with the residual in the path's precision
-  // (binary64, or float-float for MIXED) until the correction stops shrinking.
-  // binary64: a refinement that does not settle falls back to a direct LU.
+  // inverted in binary32 by Gauss-Jordan without row interchanges, then
+  // x += D F D (b - A x) with the residual in the path's precision (binary64,
+  // or float-float for MIXED) until the correction stops shrinking; a
+  // refinement that does not settle falls back to a direct binary64 LU.
   // Every tent matrix has a positive definite symmetric part (testing the
   // tent system with V = U_h gives x^T A x = 1/2 int_top Q_g(u) + 1/2 int_bot
   // Q_g(u_b) + int_bot U^2 + the dissipative boundary and interface terms > 0),
-  // so elimination without interchanges does not break down; the sweeps use
-  // none, and the direct LU of the fallback keeps partial pivoting.
-  const bool pivoting = false;
+  // and so has each of its Schur complements: elimination without
+  // interchanges does not break down.  The direct LU of the fallback keeps
+  // partial pivoting on Dirichlet and interface tents.
   const bool lu_pivoting = extra || ng > 1;
   bool refined = false;
   {
     float* sG = reinterpret_cast<float*>(sm + a.off_al);    // 2*N*N   ping-pong sweep buffers
     float* sEq = reinterpret_cast<float*>(sm + a.off_eq);   // N       equilibration scales
-    int* sPerm = reinterpret_cast<int*>(sm + a.off_perm);   // N       pivot rows, then their composition
-    float* sZ = reinterpret_cast<float*>(sm + a.off_z);     // nrhs*N  scaled, permuted residual (binary32)
+    float* sZ = reinterpret_cast<float*>(sm + a.off_z);     // nrhs*N  scaled residual (binary32)
     T* sX = reinterpret_cast<T*>(sm + a.off_x);             // nrhs*N  iterate
     for (int i = tid; i < N; i += blockDim.x) {
       const float d = fabsf(R::hi(sA[i * N + i]));
@@ -1215,135 +1247,97 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
     }
     for (int id = tid; id < nrhs * N; id += blockDim.x) sX[id] = R::zero();
     __syncthreads();
+    auto bad_pivot = [&](float pv) {
+      // binary64: the refinement then fails and the direct LU decides
+      if (!(fabsf(pv) > 0.f) || !isfinite(pv)) {
+        if (MIXED && lane == 0) flag_error(a, TP_ERR_SINGULAR, tent);
+        return true;
+      }
+      return false;
+    };
     // register path (N <= 32): row warp + 8 s of the sweep matrix in gr[s],
-    // column = lane; the pivot row goes through shared memory, the pivot
-    // column through warp shuffles
+    // column = lane.  Blocks of four steps K = {k..k+3} per barrier: with S_K
+    // the block's pivot rows at its start, every warp reduces S_K by the four
+    // steps itself (P = [S_KK^-1 | S_KK^-1 S_KJ] in the pivot and the other
+    // columns), and a row i outside K becomes
+    //   (columns of K set to 0, the others kept) - sum_b s_{i,k+b} P_b,
+    // which is the four single steps taken at once (block Gauss-Jordan).
     const bool regs = N <= 32;
     float gr[4] = {0.f, 0.f, 0.f, 0.f};
-    auto gsel = [&](int s_) { return s_ == 0 ? gr[0] : s_ == 1 ? gr[1] : s_ == 2 ? gr[2] : gr[3]; };
-    auto gset = [&](int s_, float v_) {
-      if (s_ == 0) gr[0] = v_;
-      else if (s_ == 1) gr[1] = v_;
-      else if (s_ == 2) gr[2] = v_;
-      else gr[3] = v_;
-    };
     if (regs) {
 #pragma unroll
       for (int s_ = 0; s_ < 4; ++s_) {
         const int i = warp + 8 * s_;
         gr[s_] = (i < N && lane < N) ? R::hi(sA[i * N + lane]) * sEq[i] * sEq[lane] : 0.f;
       }
-      for (int k = 0; k < N; ++k) {
-        const int wk = k & 7, sk = k >> 3;
-        if (pivoting) {
-          // largest |a_ik|, i >= k: each warp's candidates, then all warps'
-          float best = -1.f;
-          int bi = k;
+      for (int k = 0, blk = 0; k < N; k += 4, ++blk) {
+        const int kb = min(4, N - k);
+        float(*pb)[32] = s_pb[blk & 1];
+        // the owners publish the block's pivot rows (rows k..k+3 are on warps
+        // (k & 7) .. (k & 7) + 3, slot k >> 3)
+        if (warp >= (k & 7) && warp < (k & 7) + kb) {
+          const int s_ = k >> 3;
+          pb[warp - (k & 7)][lane] = s_ == 0 ? gr[0] : s_ == 1 ? gr[1] : s_ == 2 ? gr[2] : gr[3];
+        }
+        // this warp's rows in the pivot columns (block-start values)
+        float ml[4][4];
 #pragma unroll
-          for (int s_ = 0; s_ < 4; ++s_) {
-            const int i = warp + 8 * s_;
-            const float v_ = fabsf(__shfl_sync(0xffffffffu, gr[s_], k));
-            if (i >= k && i < N && v_ > best) {
-              best = v_;
-              bi = i;
-            }
-          }
-          if (lane == 0) {
-            s_cval[warp] = best;
-            s_cidx[warp] = bi;
-          }
-          __syncthreads();
-          int pr = k;
-          float bv = -1.f;
-          for (int w = 0; w < kThreads / 32; ++w)
-            if (s_cval[w] > bv || (s_cval[w] == bv && s_cidx[w] < pr)) {
-              bv = s_cval[w];
-              pr = s_cidx[w];
-            }
-          if (tid == 0) sPerm[k] = pr;
-          if (pr != k) {   // exchange rows k and pr
-            const int wp = pr & 7, sp = pr >> 3;
-            if (warp == wk) s_xrow[0][lane] = gsel(sk);
-            if (warp == wp) s_xrow[1][lane] = gsel(sp);
-            __syncthreads();
-            if (warp == wk) gset(sk, s_xrow[1][lane]);
-            if (warp == wp) gset(sp, s_xrow[0][lane]);
-          }
-        } else if (tid == 0) {
-          sPerm[k] = k;
-        }
-        if (warp == wk) {   // pivot row, normalised
-          const float rowv = gsel(sk);
-          float akk = __shfl_sync(0xffffffffu, rowv, k);
-          if (!(fabsf(akk) > 0.f) || !isfinite(akk)) {
-            if (MIXED && lane == 0) flag_error(a, TP_ERR_SINGULAR, tent);
-            akk = 1.f;
-          }
-          const float rp = __frcp_rn(akk);
-          s_prow[k & 1][lane] = (lane == k) ? rp : rowv * rp;
-        }
+        for (int s_ = 0; s_ < 4; ++s_)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) ml[s_][b] = __shfl_sync(0xffffffffu, gr[s_], k + b);
         __syncthreads();
-        const float pj = s_prow[k & 1][lane];
+        float P[4];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) P[b] = b < kb ? pb[b][lane] : 0.f;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          if (b >= kb) break;
+          const int kc = k + b;
+          float mm[4];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) mm[c] = __shfl_sync(0xffffffffu, P[c], kc);
+          float pv = mm[b];
+          if (bad_pivot(pv)) pv = 1.f;
+          const float rp = rcp_fast(pv);
+          const float pn = (lane == kc) ? rp : P[b] * rp;
+#pragma unroll
+          for (int c = 0; c < 4; ++c)
+            if (c != b) P[c] = fmaf(-mm[c], pn, lane == kc ? 0.f : P[c]);
+          P[b] = pn;
+        }
+        const bool kcol = lane >= k && lane < k + kb;
 #pragma unroll
         for (int s_ = 0; s_ < 4; ++s_) {
           const int i = warp + 8 * s_;
-          const float aik = __shfl_sync(0xffffffffu, gr[s_], k);
-          gr[s_] = (i == k) ? pj : fmaf(-aik, pj, lane == k ? 0.f : gr[s_]);
+          const int bi = i - k;
+          if (bi >= 0 && bi < kb) {
+            gr[s_] = bi == 0 ? P[0] : bi == 1 ? P[1] : bi == 2 ? P[2] : P[3];
+          } else {
+            float x = kcol ? 0.f : gr[s_];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) x = fmaf(-ml[s_][b], P[b], x);
+            gr[s_] = x;
+          }
         }
       }
     } else {
       for (int id = tid; id < N * N; id += blockDim.x) sG[id] = R::hi(sA[id]) * sEq[id / N] * sEq[id % N];
       __syncthreads();
-      // Gauss-Jordan sweeps: step k reads buffer k % 2 (rows k and pr exchanged)
-      // and writes buffer (k + 1) % 2; the final buffer holds F with
-      // (D A D)^-1 v = F (P v), P the row interchanges applied in order
+      // Gauss-Jordan sweeps: step k reads buffer k % 2 and writes buffer
+      // (k + 1) % 2; the final buffer holds F = (D A D)^-1
       for (int k = 0; k < N; ++k) {
         const float* S = sG + (size_t)(k & 1) * N * N;
         float* Gn = sG + (size_t)((k + 1) & 1) * N * N;
-        if (pivoting) {
-          if (warp == 0) {
-            float best = -1.f;
-            int bi = k;
-            for (int i = k + lane; i < N; i += 32) {
-              const float val = fabsf(S[i * N + k]);
-              if (val > best) {
-                best = val;
-                bi = i;
-              }
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-              const float ob = __shfl_down_sync(0xffffffffu, best, o);
-              const int oi = __shfl_down_sync(0xffffffffu, bi, o);
-              if (ob > best || (ob == best && oi < bi)) {
-                best = ob;
-                bi = oi;
-              }
-            }
-            if (lane == 0) {
-              s_piv = bi;
-              sPerm[k] = bi;
-            }
-          }
-          __syncthreads();
-        } else if (tid == 0) {
-          sPerm[k] = k;
-        }
-        const int pr = pivoting ? s_piv : k;
-        float pv = S[pr * N + k];
-        if (!(fabsf(pv) > 0.f) || !isfinite(pv)) {
-          // binary64: the refinement then fails and the direct LU decides
-          if (MIXED && tid == 0) flag_error(a, TP_ERR_SINGULAR, tent);
-          pv = 1.f;
-        }
-        const float rp = __frcp_rn(pv);
+        float pv = S[k * N + k];
+        if (bad_pivot(pv)) pv = 1.f;
+        const float rp = rcp_fast(pv);
         for (int i = warp; i < N; i += kThreads / 32) {   // rows over warps, columns over lanes
-          const int si = (i == k) ? pr : (i == pr ? k : i);
-          const float lik = -S[si * N + k] * rp;
+          const float lik = -S[i * N + k] * rp;
           for (int j = lane; j < N; j += 32) {
             float g;
-            if (i == k) g = (j == k) ? rp : S[pr * N + j] * rp;
+            if (i == k) g = (j == k) ? rp : S[k * N + j] * rp;
             else if (j == k) g = lik;
-            else g = fmaf(lik, S[pr * N + j], S[si * N + j]);
+            else g = fmaf(lik, S[k * N + j], S[i * N + j]);
             Gn[i * N + j] = g;
           }
         }
@@ -1351,17 +1345,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
       }
     }
     const float* F = sG + (size_t)(N & 1) * N * N;
-    if (!pivoting) {   // no interchanges: sPerm already holds the identity
-    } else if (tid == 0) {   // composition of the interchanges: (P v)_j = v[sPerm[j]]
-      int* idx = reinterpret_cast<int*>(sRD);   // scratch (the LU's reciprocal pivots are not live here)
-      for (int j = 0; j < N; ++j) idx[j] = j;
-      for (int k = 0; k < N; ++k) {
-        const int q = sPerm[k], t = idx[k];
-        idx[k] = idx[q];
-        idx[q] = t;
-      }
-      for (int j = 0; j < N; ++j) sPerm[j] = idx[j];
-    }
     __syncthreads();
     // refinement
     float prev = 3.4e38f;
@@ -1393,12 +1376,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
         if (sub == 0 && item < nrhs * N) sZ[item] = sEq[item % N] * R::hi(R::add(sb[item], t));
       }
       __syncthreads();
-      // x += D F (P r): register path, one row per (warp, slot), summed over lanes
+      // x += D F r: register path, one row per (warp, slot), summed over lanes
       // (the scale |x| of the stop test is taken from the first iterate)
       float dmax = 0.f;
       if (regs) {
         for (int r = 0; r < nrhs; ++r) {
-          const float vj = (lane < N) ? sZ[(size_t)r * N + sPerm[lane]] : 0.f;
+          const float vj = (lane < N) ? sZ[(size_t)r * N + lane] : 0.f;
           float zs = 0.f;   // lane s_ < 4 ends with the sum of slot s_
 #pragma unroll
           for (int s_ = 0; s_ < 4; ++s_) {
@@ -1423,7 +1406,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
         if (item < nrhs * N) {
           const int r = item / N, i = item % N;
           const float* zr = sZ + (size_t)r * N;
-          for (int j = sub; j < N; j += 8) z = fmaf(F[i * N + j], zr[sPerm[j]], z);
+          for (int j = sub; j < N; j += 8) z = fmaf(F[i * N + j], zr[j], z);
         }
         for (int o = 4; o > 0; o >>= 1) z += __shfl_xor_sync(0xffffffffu, z, o);
         if (sub == 0 && item < nrhs * N) {
