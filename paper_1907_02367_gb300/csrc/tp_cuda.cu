@@ -500,14 +500,21 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
       for (int i = 0; i < n; ++i) einv[((size_t)k * n + d) * n + i] = inv[d][i];
     esdet[k] = std::sqrt(std::fabs(det));
   }
-  double *deinv = nullptr, *desdet = nullptr;
-  if ((rc = ctx_upload(ctx, &deinv, einv)) || (rc = ctx_upload(ctx, &desdet, esdet))) return fail(rc);
+  // reciprocals of sqrt|det e| and of the reference weights' square roots
+  // (the kept top U-values are unscaled by 1/sqrt(w) = 1/(sqrt(w_ref) sqrt|det e|))
+  std::vector<double> eisdet(T.ne), isqw(Q);
+  for (int64_t k = 0; k < T.ne; ++k) eisdet[k] = 1.0 / esdet[k];
+  for (int q = 0; q < Q; ++q) isqw[q] = 1.0 / sqw[q];
+  double *deinv = nullptr, *desdet = nullptr, *deisdet = nullptr, *disqw = nullptr;
+  if ((rc = ctx_upload(ctx, &deinv, einv)) || (rc = ctx_upload(ctx, &desdet, esdet)) ||
+      (rc = ctx_upload(ctx, &deisdet, eisdet)) || (rc = ctx_upload(ctx, &disqw, isqw)))
+    return fail(rc);
   // per vertex: one record with all of its star that does not depend on the
   // sweep, so that a tent reads it in one round of loads.
   //   ints:    per element (el, material, vertex ids[n+1]); per facet (Dirichlet
   //            first, then interface): (vertex ids other than v in slots 2..n,
   //            material of the + element, of the - element)
-  //   doubles: x_v[n], speeds[kMaxGroups]; per element its vertex coordinates
+  //   doubles: x_v[n], speeds[kMaxGroups], their 1/c^2 [kMaxGroups]; per element its vertex coordinates
   //            [(n+1) n]; per facet its normal [n] and vertex coordinates [(n+1) n]
   // per tent: (v, int offset, double offset, elements, Dirichlet facets,
   // interface facets, materials, 0)
@@ -526,6 +533,10 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
       vrec_d[v] = (int)rec_d.size();
       for (int d = 0; d < n; ++d) rec_d.push_back(T.X[(size_t)v * n + d]);
       for (int g = 0; g < tp::kMaxGroups; ++g) rec_d.push_back(vert_gc[(size_t)v * tp::kMaxGroups + g]);
+      for (int g = 0; g < tp::kMaxGroups; ++g) {
+        const double cg = vert_gc[(size_t)v * tp::kMaxGroups + g];
+        rec_d.push_back(g < vert_ng[v] ? 1.0 / (cg * cg) : 0.0);
+      }
       for (int e = T.star_ptr[v]; e < T.star_ptr[v + 1]; ++e) {
         const int el = star_sorted[e];
         rec_i.push_back(el);
@@ -713,6 +724,8 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
   a.fm_coefd = dfmd;
   a.elem_einv = deinv;
   a.elem_sdet = desdet;
+  a.elem_isdet = deisdet;
+  a.isqw = disqw;
   a.star_sorted = dsso;
   a.star_grp = dsgr;
   a.vert_ng = dvng;

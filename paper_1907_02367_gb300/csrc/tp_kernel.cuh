@@ -49,6 +49,7 @@ struct KArgs {
   const int* star_el;
   const double* elem_einv;    // per element: inverse of the edge matrix e (rows X_i - X_0), dim x dim
   const double* elem_sdet;    // per element: sqrt(|det e|)
+  const double* elem_isdet;   // per element: 1 / sqrt(|det e|)
   const int* star_sorted;     // vertex stars with the elements grouped by wave speed
   const int* star_grp;        // material group of each entry of star_sorted
   const int* vert_ng;         // materials (distinct wave speeds) in each vertex star
@@ -66,6 +67,7 @@ struct KArgs {
   const double* bary;     // Q * (dim+1)
   const double* wref;     // Q
   const double* sqw;      // Q, sqrt(wref)
+  const double* isqw;     // Q, 1 / sqrt(wref)
   const int* tent_v;
   const double* tent_ttop;
   const double* tent_tbot;
@@ -550,16 +552,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
   extern __shared__ __align__(16) double sm[];
   __shared__ int s_P, s_v, s_nfac, s_nif, s_ng;
   __shared__ double s_ttop, s_tbot, s_tc, s_ih;
-  __shared__ double s_gc[tp::kMaxGroups];
+  __shared__ double s_gc[tp::kMaxGroups], s_gic2[tp::kMaxGroups];   // speeds and 1/c^2 of the materials
   __shared__ double s_xv[DIM];
   __shared__ int s_el[tp::kMaxPatch], s_grp[tp::kMaxPatch];
   __shared__ int s_vid[tp::kMaxPatch][NV], s_fw[tp::kMaxFacets][NV];   // vertex ids of elements, facets
   __shared__ double s_X[tp::kMaxPatch][NV][DIM];
   __shared__ double s_tb[tp::kMaxPatch][NV], s_tt[tp::kMaxPatch][NV];
   __shared__ double s_gb[tp::kMaxPatch][DIM], s_gt[tp::kMaxPatch][DIM];
-  __shared__ double s_sdet[tp::kMaxPatch];
+  __shared__ double s_sdet[tp::kMaxPatch], s_isdet[tp::kMaxPatch];
   __shared__ double s_fP[tp::kMaxFacets][NV][DIM + 1];   // vertical face simplices (x, t)
-  __shared__ double s_fscale[tp::kMaxFacets], s_fn[tp::kMaxFacets][DIM];
+  __shared__ double s_fsq[tp::kMaxFacets], s_fn[tp::kMaxFacets][DIM];   // sqrt(n! volume), normal
   __shared__ int s_fg[tp::kMaxFacets], s_fg2[tp::kMaxFacets];   // groups (Dirichlet: one; interface: +, -)
   __shared__ int s_pgrp[2 * 64];
   __shared__ int s_piv;
@@ -632,8 +634,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
     const int* ri = a.vrec_i + h0.y;
     const double* rd = a.vrec_d + h0.z;
     if (tid < DIM) s_xv[tid] = __ldg(rd + tid);
-    if (tid < ng) s_gc[tid] = __ldg(rd + DIM + tid);
-    const double* rX = rd + DIM + tp::kMaxGroups;
+    if (tid < ng) {
+      s_gc[tid] = __ldg(rd + DIM + tid);
+      s_gic2[tid] = __ldg(rd + DIM + tp::kMaxGroups + tid);
+    }
+    const double* rX = rd + DIM + 2 * tp::kMaxGroups;
     for (int k = tid; k < P; k += blockDim.x) {
       s_el[k] = __ldg(ri + k * (2 + NV));
       s_grp[k] = __ldg(ri + k * (2 + NV) + 1);
@@ -712,8 +717,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
       g2 = fma(gt, gt, g2);
     }
     s_sdet[k] = __ldg(a.elem_sdet + el);
+    s_isdet[k] = __ldg(a.elem_isdet + el);
     const double ck = s_gc[s_grp[k]];
-    if (!(1.0 / (ck * ck) - g2 > 0.0)) flag_error(a, TP_ERR_CAUSALITY, tent);   // space-like top face
+    if (!(ck * ck * g2 < 1.0)) flag_error(a, TP_ERR_CAUSALITY, tent);   // space-like top face: c |g| < 1
   }
   for (int f = tid; f < nfac + nif; f += blockDim.x) {
     s_fP[f][0][DIM] = tbot;
@@ -727,7 +733,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
         for (int d = 0; d <= DIM; ++d) s_ += (s_fP[f][i + 1][d] - s_fP[f][0][d]) * (s_fP[f][j + 1][d] - s_fP[f][0][d]);
         G[i][j] = s_;
       }
-    s_fscale[f] = sqrt(fabs(small_det<DIM>(G)));
+    // sqrt(w) = sqrt(w_ref) sqrt(n! volume) at the facet's points
+    s_fsq[f] = sqrt(sqrt(fabs(small_det<DIM>(G))));
   }
   // Gram pairs owned by this thread (upper triangle, i <= j, row-major order)
   int pi[kMaxPair], pj[kMaxPair];
@@ -757,7 +764,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
   const int slice = (NP + CS - 1) / CS;
   const int q0 = min(NP, rank * slice), q1 = min(NP, q0 + slice);
   const double ih = s_ih, tc = s_tc;
-  int curk = q0 / Q;
+  int curk = q0 / Q, kend = (curk + 1) * Q;
   int curg = (q1 > q0) ? s_grp[curk] : 0;
   // forward sweep: the top U-values of a slice that fits the keep buffer are
   // kept for the outflow instead of being evaluated a second time
@@ -802,7 +809,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
     for (int id = tid; id < npt; id += blockDim.x) {
       const int side = id / nq, ql = id % nq, qg = base + ql;
       const int k = qg / Q, q = qg % Q, g = s_grp[k];
-      const double cg = s_gc[g], ic2 = 1.0 / (cg * cg);
+      const double cg = s_gc[g], ic2 = s_gic2[g];
       if (side == 0) s_pgrp[ql] = g;
       double x[DIM], tt = 0.0;
       for (int d = 0; d < DIM; ++d) x[d] = 0.0;
@@ -816,11 +823,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
       for (int d = 0; d < DIM; ++d) pp[1 + d] = R::from((x[d] - s_xv[d]) * ih);
       const double sw = __ldg(a.sqw + q) * s_sdet[k];
       pp[DIM + 1] = R::from(sw);
-      if (keep && side == 0) sKeepW[base - q0 + ql] = recip(sw);
+      if (keep && side == 0) sKeepW[base - q0 + ql] = __ldg(a.isqw + q) * s_isdet[k];
       const int el = s_el[k];
       if (ADJ && side == 0) {
         // adjoint: zeta = sum_q lambda_q u_q over the top points
-        const double isw = 1.0 / sw;
+        const double isw = __ldg(a.isqw + q) * s_isdet[k];
         for (int r = 0; r < nrhs; ++r) {
           const double* f = a.front + (((int64_t)r * a.ne + el) * Q + q) * C;
           T* cb = sCB + ((size_t)ql * nrhs + r) * C;
@@ -847,14 +854,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
       for (int id = tid; id < nq * nb; id += blockDim.x) sKeep[(size_t)(base - q0) * nb + id] = sU[id];
     // (b) Grams of U-values: top per element (flushed into G and H_m), bottom; per material
     for (int ql = 0; ql < nq; ++ql) {
-      const int k = (base + ql) / Q;
-      if (k != curk) {
+      if (base + ql >= kend) {   // the next element's points start
+        const int k = (base + ql) / Q;
         flush_element(curk);
         if (s_grp[k] != curg) {
           flush_group(curg);
           curg = s_grp[k];
         }
         curk = k;
+        kend = (k + 1) * Q;
       }
       const T* ut = sU + (size_t)ql * nb;
       const T* ub = sU + (size_t)(nq + ql) * nb;
@@ -940,7 +948,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
             const double l = __ldg(a.bary + qf * NV + i);
             for (int d = 0; d <= DIM; ++d) xt[d] = fma(l, s_fP[f][i][d], xt[d]);
           }
-          const double sw = sqrt(__ldg(a.wref + qf) * s_fscale[f]);
+          const double sw = __ldg(a.sqw + qf) * s_fsq[f];
           T* pp = sPt + id * (DIM + 2);
           pp[0] = R::from(s_gc[s_fg[f]] * (xt[DIM] - tc) * ih);
           for (int d = 0; d < DIM; ++d) pp[1 + d] = R::from((xt[d] - s_xv[d]) * ih);
@@ -1001,7 +1009,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
             const double l = __ldg(a.bary + q * NV + i);
             for (int d = 0; d <= DIM; ++d) xt[d] = fma(l, s_fP[f][i][d], xt[d]);
           }
-          const double sw = sqrt(__ldg(a.wref + q) * s_fscale[f]);
+          const double sw = __ldg(a.sqw + q) * s_fsq[f];
           T* pp = sPt + id * (DIM + 2);
           pp[0] = R::from(cp * (xt[DIM] - tc) * ih);
           for (int d = 0; d < DIM; ++d) pp[1 + d] = R::from((xt[d] - s_xv[d]) * ih);
