@@ -40,6 +40,11 @@ CONFIG = {"workload": "2+1D plain FP64 batched: unit square, 968-triangle seeded
           "n_elem": 968, "p": 4, "T": 1.0, "nrhs": 1, "precision": "fp64",
           "l2": "flushed between timed steps (256 MiB write); working set ~1 MB < L2"}
 FP64_PEAK_TFLOPS = 1.25      # nominal GB300 FP64 rate (152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz)
+# DRAM read + write bytes of one binary64 sweep launch of this workload, from the
+# ncu capture summarised in profiles/k_layer_dataflow_standing2d.md, and the
+# kernel source it was taken on
+SWEEP_DRAM_BYTES = 4.933888e6 + 0.100096e6
+SWEEP_DRAM_SOURCE = "ncu capture of k_layer<2,0,0,1> at commit ea89652"
 
 
 def max_over_ranks(x: float, world: int, device: str = "cuda") -> float:
@@ -274,7 +279,8 @@ def run_ours(args, rank, world, local):
                 "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
         "gpu_launches": n_launch * args.steps,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": SWEEP_DRAM_BYTES,
+                     "traffic_source": SWEEP_DRAM_SOURCE,
                      "kernel": "k_layer<dim 2, binary64> (tp_kernel.cuh)",
                      "sweep_ms": ms_sweep,
                      "note": "algorithmic FP64 flops of one sweep / mean duration of the sweep "
