@@ -103,6 +103,7 @@ struct KArgs {
   const int* dep_ptr;
   const int* dep_vert;
   const int* dep_need;
+  const int* queue_tent;      // tent at each queue position (level order, critical chains first)
   int tent_end;
   // shared-memory carve (offsets in doubles)
   const int* rel_ptr;
@@ -577,7 +578,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
   for (;;) {
   int tent;
   if constexpr (PERSIST) {
-    if (rank == 0 && tid == 0) s_tent = atomicAdd(a.queue, 1);
+    if (rank == 0 && tid == 0) {
+      const int pos = atomicAdd(a.queue, 1);
+      s_tent = pos < a.tent_end ? __ldg(a.queue_tent + pos) : a.tent_end;
+    }
     cluster.sync();
     tent = *cluster.map_shared_rank(&s_tent, 0);
     cluster.sync();   // every CTA has read the tent index of rank 0
