@@ -1005,10 +1005,11 @@ extern "C" int tp_solve_layer(tp_ctx* ctx, int32_t level, void* stream) {
 }
 
 namespace {
-__global__ void k_sweep_setup(const int* vert, int t_begin, int* done, int* queue) {
-  // completed tents before the range, per vertex; queue head at the range start
+__global__ void k_sweep_setup(const int* vert, int t_begin, int cs, int* done, int* queue) {
+  // completed tents before the range, per vertex (each tent counts once per
+  // CTA of its cluster); queue head at the range start
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < t_begin; t += gridDim.x * blockDim.x)
-    atomicAdd(done + vert[t], 1);
+    atomicAdd(done + vert[t], cs);
   if (blockIdx.x == 0 && threadIdx.x == 0) *queue = t_begin;
 }
 }  // namespace
@@ -1032,7 +1033,7 @@ extern "C" int tp_advance(tp_ctx* ctx, int32_t level_begin, int32_t level_end, v
       cudaError_t e = cudaMemsetAsync(ctx->d_done, 0, ctx->nv * sizeof(int), ctx->cap_stream);
       if (e == cudaSuccess) {
         k_sweep_setup<<<std::max(1, std::min(1024, (t_begin + 255) / 256)), 256, 0, ctx->cap_stream>>>(
-            ctx->args.tent_v, t_begin, ctx->d_done, ctx->d_queue);
+            ctx->args.tent_v, t_begin, ctx->persist_cs, ctx->d_done, ctx->d_queue);
         e = cudaGetLastError();
       }
       if (e == cudaSuccess)

@@ -578,13 +578,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
   for (;;) {
   int tent;
   if constexpr (PERSIST) {
+    // rank 0 takes the next tent and stores its index into every CTA of the
+    // cluster (each CTA read its copy of the previous index several cluster
+    // barriers ago)
     if (rank == 0 && tid == 0) {
       const int pos = atomicAdd(a.queue, 1);
-      s_tent = pos < a.tent_end ? __ldg(a.queue_tent + pos) : a.tent_end;
+      const int t_ = pos < a.tent_end ? __ldg(a.queue_tent + pos) : a.tent_end;
+      for (int r = 0; r < CS; ++r) *cluster.map_shared_rank(&s_tent, r) = t_;
     }
     cluster.sync();
-    tent = *cluster.map_shared_rank(&s_tent, 0);
-    cluster.sync();   // every CTA has read the tent index of rank 0
+    tent = s_tent;
     if (tent >= a.tent_end) break;
   } else {
     tent = tent0 + blockIdx.x / CS;
@@ -666,11 +669,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
     }
   }
   if constexpr (PERSIST) {
-    // the earlier tents of this vertex and its neighbours must be complete
-    if (rank == 0) {
+    // the earlier tents of this vertex and its neighbours must be complete:
+    // every CTA of a tent publishes its own completion, so a vertex whose
+    // first `need` tents are done has a count of need * CS; each CTA waits
+    // for (and acquires) the counts itself
+    {
       const int d0 = a.dep_ptr[tent], d1 = a.dep_ptr[tent + 1];
       for (int e = d0 + tid; e < d1; e += blockDim.x) {
-        const int w = a.dep_vert[e], need = a.dep_need[e];
+        const int w = a.dep_vert[e], need = a.dep_need[e] * CS;
         long long spins = 0;
         while (ld_acquire(a.done + w) < need) {
           if (++spins > kMaxSpin) {
@@ -684,7 +690,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
         }
       }
     }
-    cluster.sync();
+    __syncthreads();
   } else {
     __syncthreads();
   }
@@ -1671,9 +1677,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
   }
   if (tid == 0 && rank == 0) a.tau[v] = ADJ ? s_tbot : s_ttop;
   if constexpr (PERSIST) {
-    __threadfence();   // this CTA's front and time writes, then the completion count
-    cluster.sync();
-    if (rank == 0 && tid == 0) red_release_add(a.done + v, 1);
+    // this CTA's front (and rank 0's time) writes, then its completion count;
+    // no CTA reads another's shared memory after the solution copy, and the
+    // next tent's first cluster barrier keeps rank 0's b until all have copied it
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) red_release_add(a.done + v, 1);
   } else {
     cluster.sync();   // rank 0's b stays valid until every CTA has read the solution
     break;
