@@ -19,7 +19,7 @@ namespace tp {
 constexpr int kThreads = 256;
 constexpr int kMaxPair = 3;      // Gram pairs per thread (nb (nb+1)/2 <= 3 * 256: dim U^p <= 38)
 constexpr int kMaxRefine = 40;   // refinement steps of the mixed path
-constexpr long long kMaxSpin = 1LL << 20;   // bounded dependency wait (~0.15 s; then TP_ERR_TIMEOUT)
+constexpr long long kMaxSpin = 1LL << 20;   // bounded dependency wait: 2^20 polls (well under a second), then TP_ERR_TIMEOUT
 
 __device__ __forceinline__ int ld_acquire(const int* p) {
   int v;
@@ -686,7 +686,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
           // once any tent has flagged an error the sweep's result is void:
           // stop waiting so that the launch ends promptly
           if ((spins & 255) == 0 && ld_acquire(a.status) != 0) break;
-          __nanosleep(128);
+          __nanosleep(32);
         }
       }
     }
@@ -1259,11 +1259,22 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
     float* sEq = reinterpret_cast<float*>(sm + a.off_eq);   // N       equilibration scales
     float* sZ = reinterpret_cast<float*>(sm + a.off_z);     // nrhs*N  scaled residual (binary32)
     T* sX = reinterpret_cast<T*>(sm + a.off_x);             // nrhs*N  iterate
+    // register path with room for the right-hand sides: D b rides along as
+    // extra columns (lanes N .. N + nrhs - 1) and the elimination leaves the
+    // first iterate (D A D)^-1 D b in them
+    const bool regs = N <= 32, aug = regs && N + nrhs <= 32;
     for (int i = tid; i < N; i += blockDim.x) {
       const float d = fabsf(R::hi(sA[i * N + i]));
       sEq[i] = (d > 0.f && isfinite(d)) ? rsqrtf(d) : 1.f;
     }
-    for (int id = tid; id < nrhs * N; id += blockDim.x) sX[id] = R::zero();
+    // (items from warp 1 on, beside warp 0's scales)
+    for (int id = (tid + kThreads - 32) % kThreads; id < nrhs * N; id += blockDim.x) {
+      sX[id] = R::zero();
+      if (aug) {   // the same scale as sEq, formed here so that one barrier suffices
+        const float d = fabsf(R::hi(sA[(id % N) * (N + 1)]));
+        sZ[id] = ((d > 0.f && isfinite(d)) ? rsqrtf(d) : 1.f) * R::hi(sb[id]);
+      }
+    }
     __syncthreads();
     auto bad_pivot = [&](float pv) {
       // binary64: the refinement then fails and the direct LU decides
@@ -1280,13 +1291,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
     // columns), and a row i outside K becomes
     //   (columns of K set to 0, the others kept) - sum_b s_{i,k+b} P_b,
     // which is the four single steps taken at once (block Gauss-Jordan).
-    const bool regs = N <= 32;
     float gr[4] = {0.f, 0.f, 0.f, 0.f};
     if (regs) {
 #pragma unroll
       for (int s_ = 0; s_ < 4; ++s_) {
         const int i = warp + 8 * s_;
-        gr[s_] = (i < N && lane < N) ? R::hi(sA[i * N + lane]) * sEq[i] * sEq[lane] : 0.f;
+        if (i < N && lane < N) gr[s_] = R::hi(sA[i * N + lane]) * sEq[i] * sEq[lane];
+        else if (aug && i < N && lane < N + nrhs) gr[s_] = sZ[(lane - N) * N + i];
       }
       for (int k = 0, blk = 0; k < N; k += 4, ++blk) {
         const int kb = min(4, N - k);
@@ -1370,6 +1381,25 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
     for (int it = 0; it < maxit; ++it) {
       // residual b - A x, each row split over 8 lanes of one warp; stored
       // scaled by D in binary32 (the first iterate is x = 0: the residual is b)
+      if (it == 0 && aug) {
+        // the first iterate from the extra columns: x = D (D A D)^-1 D b
+#pragma unroll
+        for (int s_ = 0; s_ < 4; ++s_) {
+          const int i = warp + 8 * s_;
+          if (i < N && lane >= N && lane < N + nrhs) sZ[(lane - N) * N + i] = sEq[i] * gr[s_];
+        }
+        __syncthreads();
+        float dmax = 0.f;
+        for (int id = tid; id < nrhs * N; id += blockDim.x) {
+          const float dx = sZ[id];
+          sX[id] = R::addf(sX[id], dx);
+          dmax = fmaxf(dmax, fabsf(dx));
+        }
+        for (int o = 16; o > 0; o >>= 1) dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+        if (lane == 0) s_red[1][warp] = dmax;
+        __syncthreads();
+        continue;
+      }
       if (it == 0)
         for (int id = tid; id < nrhs * N; id += blockDim.x) sZ[id] = sEq[id % N] * R::hi(sb[id]);
       for (int base4 = 0; base4 < (it == 0 ? 0 : nrhs * N * 4); base4 += blockDim.x) {
