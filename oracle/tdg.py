@@ -8,9 +8,11 @@ with the second-order recovery terms of Section 5 and solved:
   LHS  A_ij =  int_top [ c^-2 v_j w_i + s_j.t_i - v_j (t_i.g) - (s_j.g) w_i ] dx
              + int_bot  U_j V_i dx                                   (Section 5)
              + int_D   (s_j.n + alpha v_j) w_i dS                    (eq. 4.1)
+             + int_N   v_j (t_i.n) + beta (s_j.n)(t_i.n) dS          (eq. 4.1)
   RHS  b_i  =  int_bot [ c^-2 v_b w_i + s_b.t_i - v_b (t_i.g_b) - (s_b.g_b) w_i ] dx
              + int_bot  U_b V_i dx                                   (Section 5)
              + int_D   g_D (alpha w_i - t_i.n) dS                    (eq. 4.1)
+             + int_N   g_N (beta t_i.n - w_i) dS                     (eq. 4.1)
 
 with trial fields (v_j, s_j) = (dU_j/dt, -grad U_j), test fields
 (w_i, t_i) = (dV_i/dt, -grad V_i), g the gradient of the top (resp. bottom)
@@ -125,14 +127,30 @@ def anisotropic_diameter(pts_xt: np.ndarray, c: float) -> float:
 # ----------------------------------------------------------------------------
 # the sweep
 # ----------------------------------------------------------------------------
+def facet_is_neumann(facet, k, elems, bnd_type) -> bool:
+    """Boundary facet `facet` of element k is Neumann when bnd_type[k, o] == 1,
+    o the local index of the element's vertex opposite the facet (None: all
+    boundary facets are Dirichlet)."""
+    if bnd_type is None:
+        return False
+    el = list(elems[k])
+    o = [i for i, a in enumerate(el) if a not in facet][0]
+    return int(bnd_type[k][o]) == 1
+
+
 def sweep(coords, elems, c, p, tents, init, dirichlet=None, alpha=0.5,
-          record=None, front0=None, tau0=None, tent_range=None, beta=0.5):
+          record=None, front0=None, tau0=None, tent_range=None, beta=0.5,
+          bnd_type=None, neumann=None):
     """Run the tent sweep.
 
     coords (Nv, n), elems (E, n+1), c (E,), p: Trefftz degree of U^p,
     tents: dict from oracle.pitching.pitch (sorted), init: callable x -> (N, n+2)
     initial (U, v, sigma) (ignored when front0 is given), dirichlet: callable
-    (x (N, n), t (N,)) -> (N,) values g_D of v on the boundary, or None for 0.
+    (x (N, n), t (N,)) -> (N,) values g_D of v on the Dirichlet boundary, or
+    None for 0.  bnd_type (E, n+1), optional: 1 marks the boundary facet
+    opposite local vertex o of element k as Neumann (sigma.n = g_N), else
+    Dirichlet; neumann: callable (x, t, n) -> (N,) values g_N, n the facet's
+    outward unit normal, or None for 0.
     record: optional callable(tent_index, dict) receiving the local data.
     Returns (front (E, Q, n+2), tau (Nv,)).
     """
@@ -231,13 +249,18 @@ def sweep(coords, elems, c, p, tents, init, dirichlet=None, alpha=0.5,
             xt = bary_face @ Pf
             return xt, wref_face * scale
 
-        # Dirichlet vertical faces through v (eq. 4.1)
+        # Dirichlet and Neumann vertical faces through v (eq. 4.1)
         for (fac, nrm, kf) in vfac[v]:
             g = grp[kf]
             blk = slice(g * nb, (g + 1) * nb)
             xt, wf = face_simplex(fac)
             Ud, Vd, Sd = B.eval_phys(xt[:, :n], xt[:, n], xc, tc, h, speeds[g])
             Sn = np.einsum("qdj,d->qj", Sd, nrm)
+            if facet_is_neumann(fac, kf, elems, bnd_type):
+                A[blk, blk] += np.einsum("q,qi,qj->ij", wf, Sn, Vd + beta * Sn)  # v_j (t_i.n) + beta (s_j.n)(t_i.n)
+                gn = np.zeros(len(wf)) if neumann is None else np.asarray(neumann(xt[:, :n], xt[:, n], nrm))
+                b[blk] += np.einsum("q,qi->i", wf * gn, beta * Sn - Vd)        # g_N (beta t_i.n - w_i)
+                continue
             A[blk, blk] += np.einsum("q,qi,qj->ij", wf, Vd, Sn + alpha * Vd)     # (s_j.n + alpha v_j) w_i
             gd = np.zeros(len(wf)) if dirichlet is None else np.asarray(dirichlet(xt[:, :n], xt[:, n]))
             b[blk] += np.einsum("q,qi->i", wf * gd, alpha * Vd - Sn)           # g_D (alpha w_i - t_i.n)

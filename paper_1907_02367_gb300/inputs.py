@@ -202,6 +202,28 @@ def element_slope_factor(mesh: Mesh) -> np.ndarray:
     return best
 
 
+def boundary_marker(mesh: Mesh, predicate) -> np.ndarray:
+    """Per element and local face (the face opposite local vertex o), 1 where
+    every vertex of the face satisfies predicate(x) and the face lies on the
+    boundary (belongs to one element only), else 0: an (n_elem, dim+1) int8
+    array for marking boundary facets (e.g. as Neumann)."""
+    E, nv1 = mesh.elems.shape
+    count: dict = {}
+    for k in range(E):
+        el = mesh.elems[k].tolist()
+        for o in range(nv1):
+            f = tuple(sorted(el[:o] + el[o + 1:]))
+            count[f] = count.get(f, 0) + 1
+    out = np.zeros((E, nv1), dtype=np.int8)
+    for k in range(E):
+        el = mesh.elems[k].tolist()
+        for o in range(nv1):
+            f = tuple(sorted(el[:o] + el[o + 1:]))
+            if count[f] == 1 and all(predicate(mesh.coords[a]) for a in f):
+                out[k, o] = 1
+    return out
+
+
 def pitch_kappa(mesh: Mesh, safety: float = 0.9) -> float:
     """kappa = safety / max_K C_K (1D: C_K = 1, so kappa = safety)."""
     return float(safety / element_slope_factor(mesh).max())

@@ -51,6 +51,8 @@ TDG_PINS = [
     lambda: Tz.test_interface_reproduction(1, 2, 1.0, 2.5),
     lambda: Tz.test_interface_reproduction(2, 2, 1.0, 3.0),
     lambda: Tz.test_interface_energy_identity_1d(),
+    lambda: Tz.test_polynomial_reproduction_with_neumann_faces(2, 3, 1),
+    lambda: Tz.test_tent_matrix_symmetric_part_positive_definite(2, 3, True),
 ]
 BASIS_PINS = [
     lambda: Bz.test_trefftz_property_exact(2, 3),
@@ -84,6 +86,9 @@ MUTATIONS = [
      'Sgb = np.einsum("qdj,d->qj", Sb, g_t)'),
     ("tdg-interface-side-sign", "tdg", "0.5 * st * (", "0.5 * ss * ("),
     ("tdg-interface-beta-sign", "tdg", "+ beta * np.einsum", "- beta * np.einsum"),
+    ("tdg-neumann-coupling-sign", "tdg", "wf, Sn, Vd + beta * Sn", "wf, Sn, -Vd + beta * Sn"),
+    ("tdg-neumann-penalty-sign", "tdg", "wf, Sn, Vd + beta * Sn", "wf, Sn, Vd - beta * Sn"),
+    ("tdg-neumann-data-sign", "tdg", "beta * Sn - Vd)", "beta * Sn + Vd)"),
     ("basis-recursion-denominator", "basis", "c2 / (k * (k - 1)) * s", "c2 / (k * (k + 1)) * s"),
     ("basis-recursion-factor", "basis", "(alpha[m] + 1) * (alpha[m] + 2) * prev",
      "(alpha[m] + 1) * (alpha[m] + 1) * prev"),

@@ -321,15 +321,15 @@ def _sinsin_1d_init(x):
     return _sinsin_1d(x, 0.3)
 
 
-@pytest.mark.parametrize("dim,p", [(1, 3), (2, 3)])
-def test_tent_matrix_symmetric_part_positive_definite(dim, p):
+@pytest.mark.parametrize("dim,p,neumann", [(1, 3, False), (2, 3, False), (2, 3, True)])
+def test_tent_matrix_symmetric_part_positive_definite(dim, p, neumann):
     """For Trefftz trial functions the tent form tested with the trial function
     itself is 1/2 int_top Q + 1/2 int_bot Q + int_bot U^2 + alpha int_D v^2 +
     the interface jumps (the energy flux through the tent's boundary, eq. (2.5)
     with the upwind and Dirichlet fluxes of Section 4): the symmetric part of
     every tent matrix, interior, Dirichlet and interface tents alike, is
     positive definite, so elimination without row interchanges cannot break
-    down on it."""
+    down on it.  On Neumann facets the term is beta int_N (sigma.n)^2."""
     mesh = inputs.mesh_interval(6) if dim == 1 else inputs.mesh_square(4, 0.2, seed=3)
     cen = mesh.coords[mesh.elems].mean(axis=1)
     mesh.c[:] = np.where(np.linalg.norm(cen - 0.5, axis=1) < 0.3, 3.0, 1.0)
@@ -344,6 +344,59 @@ def test_tent_matrix_symmetric_part_positive_definite(dim, p):
         kinds.add(("dirichlet" if bnd[d["v"]] else "interior", len(d["speeds"])))
 
     sol = inputs.polynomial_solution(dim, 0)
-    _run(mesh, p, 0.2, sol, inputs.pitch_kappa(mesh), record=rec)
+    if neumann:
+        marker = inputs.boundary_marker(mesh, lambda x: x[0] < 1e-12 or x[1] < 1e-12)
+        r = pitching.pitch(mesh.coords, mesh.elems, mesh.c, inputs.pitch_kappa(mesh), 0.2)
+        tdg.sweep(mesh.coords, mesh.elems, mesh.c, p, r, lambda x: sol(x, 0.0), None,
+                  bnd_type=marker, record=rec)
+    else:
+        _run(mesh, p, 0.2, sol, inputs.pitch_kappa(mesh), record=rec)
     assert ("dirichlet", 1) in kinds and ("interior", 2) in kinds and ("interior", 1) in kinds
     assert worst > 0.0, worst
+
+
+def _neumann_data(sol):
+    """g_N = sigma.n of a closed-form solution on a facet with outward normal n."""
+    return lambda x, t, nrm: sol(x, t)[:, 2:] @ np.asarray(nrm)
+
+
+@pytest.mark.parametrize("dim,p,which", [(1, 3, 1), (2, 3, 1), (2, 4, 0)])
+def test_polynomial_reproduction_with_neumann_faces(dim, p, which):
+    """eq. (4.1) with Neumann facets (sigma.n = g_N): a polynomial solution of
+    degree <= p with exact Dirichlet and Neumann data is reproduced to
+    rounding; the left (1D) or the left and top sides (2D) are Neumann."""
+    mesh = inputs.mesh_interval(6) if dim == 1 else inputs.mesh_square(3, 0.2, seed=5)
+    sol = inputs.polynomial_solution(dim, which)
+    if dim == 1:
+        marker = inputs.boundary_marker(mesh, lambda x: x[0] < 1e-12)
+    else:
+        marker = inputs.boundary_marker(mesh, lambda x: x[0] < 1e-12 or x[1] > 1 - 1e-12)
+    assert marker.sum() >= (1 if dim == 1 else 4)
+    r = pitching.pitch(mesh.coords, mesh.elems, mesh.c, inputs.pitch_kappa(mesh), 0.3)
+    F, tau = tdg.sweep(mesh.coords, mesh.elems, mesh.c, p, r, lambda x: sol(x, 0.0),
+                       lambda x, t: sol(x, t)[:, 1], bnd_type=marker, neumann=_neumann_data(sol))
+    lay = tdg.front_layout(mesh.coords, mesh.elems, p)
+    ex = sol(lay.xq.reshape(-1, dim), 0.3).reshape(F.shape)
+    assert np.all(tau == 0.3)
+    assert np.abs(F - ex).max() <= 1e-12 * max(1.0, np.abs(ex).max())
+    # the Neumann data matter: dropping them breaks the reproduction
+    F0, _ = tdg.sweep(mesh.coords, mesh.elems, mesh.c, p, r, lambda x: sol(x, 0.0),
+                      lambda x, t: sol(x, t)[:, 1], bnd_type=marker, neumann=None)
+    assert np.abs(F0 - ex).max() > 1e-6
+
+
+def test_energy_decreases_with_neumann_walls():
+    """With g_N = 0 on every wall the only energy flux out of a tent is the
+    beta (sigma.n)^2 dissipation of eq. (4.1): the front energy decreases."""
+    mesh = inputs.mesh_square(4, 0.2, seed=3)
+    marker = inputs.boundary_marker(mesh, lambda x: True)
+    p = 3
+    lay = tdg.front_layout(mesh.coords, mesh.elems, p)
+    init = lambda x: inputs.standing_wave_2d(x, 0.0)
+    E0 = energy.front_energy(init(lay.xq.reshape(-1, 2)).reshape(mesh.n_elem, -1, 4), lay.wq, mesh.c)
+    Es = []
+    for T in (0.1, 0.2):
+        r = pitching.pitch(mesh.coords, mesh.elems, mesh.c, inputs.pitch_kappa(mesh), T)
+        F, _ = tdg.sweep(mesh.coords, mesh.elems, mesh.c, p, r, init, None, bnd_type=marker)
+        Es.append(energy.front_energy(F, lay.wq, mesh.c))
+    assert E0 > Es[0] > Es[1] > 0.5 * E0
