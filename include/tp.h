@@ -47,8 +47,12 @@ enum { TP_SCHED_DATAFLOW = 0, TP_SCHED_LEVELS = 1 };
 
 /* Spatial mesh (Section 2.1): simplices aligned with the jumps of the
  * piecewise-constant wave speed c.  dim in {1,2,3}; coords n_vert x dim;
- * elems n_elem x (dim+1) vertex ids; c n_elem values > 0.  Every boundary
- * facet is a Dirichlet facet (v = g_D on Gamma_D, eq. 2.1). */
+ * elems n_elem x (dim+1) vertex ids; c n_elem values > 0.
+ * bnd_type (optional, NULL = every boundary facet Dirichlet): n_elem x
+ * (dim+1) host bytes, entry (k, o) for the facet of element k opposite its
+ * local vertex o: 0 = Dirichlet (v = g_D on Gamma_D), 1 = Neumann
+ * (sigma.n = g_N on Gamma_N), eq. 2.1; entries of interior facets are
+ * ignored, other values are TP_ERR_ARG. */
 typedef struct tp_mesh_desc {
   int32_t dim;
   int64_t n_vert;
@@ -56,6 +60,7 @@ typedef struct tp_mesh_desc {
   int64_t n_elem;
   const int32_t* elems;
   const double* c;
+  const int8_t* bnd_type;
 } tp_mesh_desc;
 
 /* p: degree of the second-order Trefftz space U^p (Section 3; unknowns per
@@ -136,12 +141,17 @@ int tp_ctx_info(const tp_ctx* ctx, int64_t* n_front, int32_t* n_comp, int64_t* n
 /* Front points (Section 4.1: one spatial rule mapped onto the faces):
  * host arrays xq (n_front x dim) and wq (n_front) physical weights. */
 int tp_front_points(const tp_ctx* ctx, double* xq, double* wq);
-/* Dirichlet quadrature points (x, t) on the vertical boundary faces of every
- * tent, in sweep order: host array xt (n_bnd x (dim+1)).  The caller
- * evaluates g_D there (eq. 2.1: v = g_D on Gamma_D). */
+/* Quadrature points (x, t) on the vertical boundary faces of every tent, in
+ * sweep order: host array xt (n_bnd x (dim+1)).  The caller evaluates the
+ * boundary data there: g_D on Dirichlet facets (eq. 2.1: v = g_D on
+ * Gamma_D), g_N on Neumann facets (sigma.n = g_N on Gamma_N). */
 int tp_boundary_points(const tp_ctx* ctx, double* xt);
+/* For the same points: host arrays nrm (n_bnd x dim, the facet's outward unit
+ * normal) and kind (n_bnd bytes, 0 = Dirichlet, 1 = Neumann); either may be NULL. */
+int tp_boundary_kinds(const tp_ctx* ctx, double* nrm, int8_t* kind);
 /* Sets the state at t = 0: d_front (device, front layout above, nrhs sets),
- * d_gD (device, nrhs x n_bnd values of g_D, or NULL for g_D = 0).  Both are
+ * d_gD (device, nrhs x n_bnd boundary data at the points of
+ * tp_boundary_points: g_D or g_N by the facet's kind; NULL for zero data).  Both are
  * copied; the front times are reset to 0.  Asynchronous on `stream`. */
 int tp_set_state(tp_ctx* ctx, const double* d_front, const double* d_gD, void* stream);
 /* Solves every tent of one level (1-based) of the sorted tent list:

@@ -98,12 +98,12 @@ class Solver:
 
     def __init__(self, coords, elems, c, p: int, T: float, kappa: float, alpha: float = 0.5,
                  nrhs: int = 1, tents: Tents | None = None, precision: str = "fp64",
-                 schedule: str = "dataflow"):
+                 schedule: str = "dataflow", bnd_type=None, beta: float = 0.5):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("libtp Solver needs a CUDA device")
         lib = B.load()
-        self._mesh = B._MeshArrays(coords, elems, c)
+        self._mesh = B._MeshArrays(coords, elems, c, bnd_type)
         self.tents = tents if tents is not None else Tents(coords, elems, c, kappa, T)
         self.basis = Basis(self._mesh.coords.shape[1], p)
         if precision not in ("fp64", "mixed"):
@@ -111,7 +111,7 @@ class Solver:
         self.precision = precision
         if schedule not in ("dataflow", "levels"):
             raise ValueError("schedule must be 'dataflow' or 'levels'")
-        self.params = B.make_params(p, T, kappa, alpha=alpha, nrhs=nrhs,
+        self.params = B.make_params(p, T, kappa, alpha=alpha, beta=beta, nrhs=nrhs,
                                     precision=B.TP_FP64 if precision == "fp64" else B.TP_MIXED,
                                     schedule=B.TP_SCHED_DATAFLOW if schedule == "dataflow"
                                     else B.TP_SCHED_LEVELS)
@@ -141,6 +141,15 @@ class Solver:
         if self.n_bnd:
             B.check(B.load().tp_boundary_points(self.handle, xt.ctypes.data))
         return xt
+
+    def boundary_kinds(self):
+        """Per boundary point: the facet's outward unit normal (n_bnd, dim) and
+        kind (n_bnd,), 0 = Dirichlet (data g_D), 1 = Neumann (data g_N)."""
+        nrm = np.zeros((max(self.n_bnd, 0), self.dim))
+        kind = np.zeros(max(self.n_bnd, 0), np.int8)
+        if self.n_bnd:
+            B.check(B.load().tp_boundary_kinds(self.handle, nrm.ctypes.data, kind.ctypes.data))
+        return nrm, kind
 
     # -- device state ------------------------------------------------------
     def front_shape(self):

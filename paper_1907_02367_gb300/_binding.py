@@ -22,7 +22,7 @@ TP_SCHED_DATAFLOW, TP_SCHED_LEVELS = 0, 1
 EXPORTED = [
     "tp_last_error", "tp_pitch_mesh", "tp_tents_info", "tp_tents_export", "tp_destroy_tents",
     "tp_build_basis", "tp_basis_info", "tp_basis_export", "tp_destroy_basis", "tp_create",
-    "tp_ctx_info", "tp_front_points", "tp_boundary_points", "tp_set_state", "tp_solve_layer",
+    "tp_ctx_info", "tp_front_points", "tp_boundary_points", "tp_boundary_kinds", "tp_set_state", "tp_solve_layer",
     "tp_advance", "tp_adjoint", "tp_autotune", "tp_energy", "tp_get_state", "tp_sync_status", "tp_destroy_ctx",
     "tp_front_energy_noalloc",
 ]
@@ -36,7 +36,8 @@ class TpError(RuntimeError):
 
 class MeshDesc(ct.Structure):
     _fields_ = [("dim", ct.c_int32), ("n_vert", ct.c_int64), ("coords", ct.c_void_p),
-                ("n_elem", ct.c_int64), ("elems", ct.c_void_p), ("c", ct.c_void_p)]
+                ("n_elem", ct.c_int64), ("elems", ct.c_void_p), ("c", ct.c_void_p),
+                ("bnd_type", ct.c_void_p)]
 
 
 class Params(ct.Structure):
@@ -72,6 +73,7 @@ def load(path: str = LIB_PATH):
         "tp_ctx_info": (ct.c_int, [vp, P(i64), P(i32), P(i64), P(i32)]),
         "tp_front_points": (ct.c_int, [vp, vp, vp]),
         "tp_boundary_points": (ct.c_int, [vp, vp]),
+        "tp_boundary_kinds": (ct.c_int, [vp, vp, vp]),
         "tp_set_state": (ct.c_int, [vp, vp, vp, vp]),
         "tp_solve_layer": (ct.c_int, [vp, i32, vp]),
         "tp_advance": (ct.c_int, [vp, i32, i32, vp]),
@@ -104,14 +106,20 @@ def _ptr(a: np.ndarray) -> int:
 class _MeshArrays:
     """Keeps contiguous copies alive while a MeshDesc points at them."""
 
-    def __init__(self, coords, elems, c):
+    def __init__(self, coords, elems, c, bnd_type=None):
         self.coords = np.ascontiguousarray(coords, dtype=np.float64)
         if self.coords.ndim == 1:
             self.coords = self.coords[:, None].copy()
         self.elems = np.ascontiguousarray(elems, dtype=np.int32)
         self.c = np.ascontiguousarray(c, dtype=np.float64)
+        self.bnd_type = None
+        if bnd_type is not None:
+            self.bnd_type = np.ascontiguousarray(bnd_type, dtype=np.int8)
+            if self.bnd_type.shape != self.elems.shape:
+                raise ValueError("bnd_type must have the shape of elems (n_elem, dim+1)")
         self.desc = MeshDesc(self.coords.shape[1], self.coords.shape[0], _ptr(self.coords),
-                             self.elems.shape[0], _ptr(self.elems), _ptr(self.c))
+                             self.elems.shape[0], _ptr(self.elems), _ptr(self.c),
+                             _ptr(self.bnd_type) if self.bnd_type is not None else None)
 
 
 def make_params(p, T, kappa, alpha=0.5, beta=0.5, precision=TP_FP64, nrhs=1,

@@ -124,7 +124,9 @@ struct tp_ctx {
   std::vector<int64_t> level_ptr;
   tp::Topology topo;
   tp::SimplexRule rule;
-  std::vector<double> bnd_xt;
+  std::vector<double> bnd_xt, bnd_nrm;
+  bool neumann = false;     // the mesh has Neumann facets
+  std::vector<int8_t> bnd_kind;
   KArgs args{};
   KArgs args_adj{};        // same tables; front/tau point at the adjoint state
   double T_final = 0.0;
@@ -193,6 +195,7 @@ int set_smem_attr(int dim, size_t cap) {
 
 cudaError_t launch_layer(tp_ctx* ctx, const KArgs& a, int n_cluster, int cs, int t0, cudaStream_t st, int mode,
                          bool persistent) {
+  if (ctx->neumann) mode |= 4;   // the kernel variant with the Neumann facet code
   switch (ctx->dim) {
     case 1: return tp::launch_layer_d1(a, n_cluster, cs, t0, ctx->smem_bytes, st, mode, persistent);
     case 2: return tp::launch_layer_d2(a, n_cluster, cs, t0, ctx->smem_bytes, st, mode, persistent);
@@ -203,7 +206,7 @@ cudaError_t launch_layer(tp_ctx* ctx, const KArgs& a, int n_cluster, int cs, int
 // resident clusters of the persistent kernel for cluster size cs
 int set_persist_cs(tp_ctx* ctx, int cs) {
   int nclu = 0;
-  const int mode = ctx->mixed ? 1 : 0;
+  const int mode = (ctx->mixed ? 1 : 0) | (ctx->neumann ? 4 : 0);
   cudaError_t e = ctx->dim == 1 ? tp::max_clusters_d1(cs, ctx->smem_bytes, mode, &nclu)
                 : ctx->dim == 2 ? tp::max_clusters_d2(cs, ctx->smem_bytes, mode, &nclu)
                                 : tp::max_clusters_d3(cs, ctx->smem_bytes, mode, &nclu);
@@ -290,9 +293,10 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
   ctx->ntents = (int64_t)tents->vert.size();
   ctx->n_levels = tents->n_levels;
   ctx->level_ptr = tents->level_ptr;
+  ctx->neumann = std::find(T.facet_kind.begin(), T.facet_kind.end(), (int8_t)1) != T.facet_kind.end();
   // patch checks: size limits; materials (distinct wave speeds) per tent
   int ngmax = 1, pmax = 1;
-  std::vector<std::array<int, 3>> facet_mix;   // distinct (materials, Dirichlet facets, interface facets)
+  std::vector<std::array<int, 4>> facet_mix;   // distinct (materials, Dirichlet, interface, Neumann facets)
   for (int64_t v = 0; v < T.nv; ++v) {
     const int p0 = T.star_ptr[v], p1 = T.star_ptr[v + 1];
     pmax = std::max(pmax, p1 - p0);
@@ -309,8 +313,10 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
       if (std::find(speeds.begin(), speeds.end(), T.c[T.star_el[e]]) == speeds.end())
         speeds.push_back(T.c[T.star_el[e]]);
     ngmax = std::max(ngmax, (int)speeds.size());
-    const std::array<int, 3> mix = {(int)speeds.size(), T.vfac_ptr[v + 1] - T.vfac_ptr[v],
-                                    T.ifac_ptr[v + 1] - T.ifac_ptr[v]};
+    int nneu_v = 0;
+    for (int e = T.vfac_ptr[v]; e < T.vfac_ptr[v + 1]; ++e) nneu_v += T.facet_kind[T.vfac[e]];
+    const std::array<int, 4> mix = {(int)speeds.size(), T.vfac_ptr[v + 1] - T.vfac_ptr[v] - nneu_v,
+                                    T.ifac_ptr[v + 1] - T.ifac_ptr[v], nneu_v};
     if (std::find(facet_mix.begin(), facet_mix.end(), mix) == facet_mix.end()) facet_mix.push_back(mix);
   }
   if (ngmax > tp::kMaxGroups) {
@@ -363,12 +369,15 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
         P[c2][n] = tau[w];
         ++c2;
       }
-      for (int q = 0; q < Q; ++q)
+      for (int q = 0; q < Q; ++q) {
         for (int d = 0; d <= n; ++d) {
           double s = 0.0;
           for (int i = 0; i <= n; ++i) s += ctx->rule.bary[q * (n + 1) + i] * P[i][d];
           ctx->bnd_xt.push_back(s);
         }
+        for (int d = 0; d < n; ++d) ctx->bnd_nrm.push_back(T.facet_nrm[(int64_t)fid * n + d]);
+        ctx->bnd_kind.push_back(T.facet_kind[fid]);
+      }
     }
     tau[v] = tt;
   }
@@ -538,12 +547,13 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
   // per vertex: one record with all of its star that does not depend on the
   // sweep, so that a tent reads it in one round of loads.
   //   ints:    per element (el, material, vertex ids[n+1]); per facet (Dirichlet
-  //            first, then interface): (vertex ids other than v in slots 2..n,
-  //            material of the + element, of the - element)
+  //            first, then interface, then Neumann): (vertex ids other than v in
+  //            slots 2..n, material of the + element, of the - element, position
+  //            among the vertex's boundary facets = block of its boundary data)
   //   doubles: x_v[n], speeds[kMaxGroups], their 1/c^2 [kMaxGroups]; per element its vertex coordinates
   //            [(n+1) n]; per facet its normal [n] and vertex coordinates [(n+1) n]
   // per tent: (v, int offset, double offset, elements, Dirichlet facets,
-  // interface facets, materials, 0)
+  // interface facets, materials, Neumann facets)
   std::vector<int> rec_i, tent_hdr((size_t)ctx->ntents * 8, 0);
   std::vector<double> rec_d;
   std::vector<int> vrec_i(T.nv), vrec_d(T.nv);
@@ -573,19 +583,32 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
           for (int d = 0; d < n; ++d) rec_d.push_back(T.X[(size_t)vi * n + d]);
         }
       }
-      const int nf = T.vfac_ptr[v + 1] - T.vfac_ptr[v], ni = T.ifac_ptr[v + 1] - T.ifac_ptr[v];
-      for (int f = 0; f < nf + ni; ++f) {
-        const bool dir = f < nf;
-        const int fid = dir ? T.vfac[T.vfac_ptr[v] + f] : T.ifac_ptr[v] + (f - nf);
-        const int* fv = dir ? &T.facet_vert[(size_t)fid * n] : &T.ifac_vert[(size_t)fid * n];
-        const double* fn = dir ? &T.facet_nrm[(size_t)fid * n] : &T.ifac_nrm[(size_t)fid * n];
+      const int nb_v = T.vfac_ptr[v + 1] - T.vfac_ptr[v], ni = T.ifac_ptr[v + 1] - T.ifac_ptr[v];
+      // (kind, id, data block): Dirichlet facets, interface facets, Neumann facets
+      std::vector<std::array<int, 3>> order;
+      for (int pass = 0; pass < 3; ++pass) {
+        if (pass == 1) {
+          for (int f = 0; f < ni; ++f) order.push_back({2, T.ifac_ptr[v] + f, -1});
+          continue;
+        }
+        for (int f = 0; f < nb_v; ++f) {
+          const int fid = T.vfac[T.vfac_ptr[v] + f];
+          if (T.facet_kind[fid] == (pass == 0 ? 0 : 1)) order.push_back({pass == 0 ? 0 : 1, fid, f});
+        }
+      }
+      for (const auto& fo : order) {
+        const bool bnd = fo[0] != 2;
+        const int fid = fo[1];
+        const int* fv = bnd ? &T.facet_vert[(size_t)fid * n] : &T.ifac_vert[(size_t)fid * n];
+        const double* fn = bnd ? &T.facet_nrm[(size_t)fid * n] : &T.ifac_nrm[(size_t)fid * n];
         int w_[4] = {(int)v, (int)v, -1, -1};
         int c2 = 2;
         for (int i = 0; i < n; ++i)
           if (fv[i] != v) w_[c2++] = fv[i];
         for (int i = 0; i < NVn; ++i) rec_i.push_back(w_[i]);
-        rec_i.push_back(grp_of(v, T.c[dir ? T.facet_elem[fid] : T.ifac_kp[fid]]));
-        rec_i.push_back(grp_of(v, T.c[dir ? T.facet_elem[fid] : T.ifac_km[fid]]));
+        rec_i.push_back(grp_of(v, T.c[bnd ? T.facet_elem[fid] : T.ifac_kp[fid]]));
+        rec_i.push_back(grp_of(v, T.c[bnd ? T.facet_elem[fid] : T.ifac_km[fid]]));
+        rec_i.push_back(fo[2]);
         for (int d = 0; d < n; ++d) rec_d.push_back(fn[d]);
         for (int i = 0; i < NVn; ++i)
           for (int d = 0; d < n; ++d) rec_d.push_back(w_[i] >= 0 ? T.X[(size_t)w_[i] * n + d] : 0.0);
@@ -598,9 +621,12 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
       h[1] = vrec_i[v];
       h[2] = vrec_d[v];
       h[3] = T.star_ptr[v + 1] - T.star_ptr[v];
-      h[4] = T.vfac_ptr[v + 1] - T.vfac_ptr[v];
+      int nneu = 0;
+      for (int e = T.vfac_ptr[v]; e < T.vfac_ptr[v + 1]; ++e) nneu += T.facet_kind[T.vfac[e]];
+      h[4] = T.vfac_ptr[v + 1] - T.vfac_ptr[v] - nneu;   // Dirichlet facets
       h[5] = T.ifac_ptr[v + 1] - T.ifac_ptr[v];
       h[6] = vert_ng[v];
+      h[7] = nneu;
     }
   }
   std::vector<double> tent_ih(ctx->ntents);
@@ -820,10 +846,12 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
     const size_t sg_al = std::max((size_t)ngmax * (n + 2) * npair, NB * NB);
     // interface blocks (tents with interface facets) followed by the Dirichlet
     // sums of every material (tents with Dirichlet facets), partials reduced in place
+    // (and for tents with Neumann facets the blocks plus a partial b)
     size_t pd = 0;
     for (const auto& m : facet_mix)
-      pd = std::max(pd, (m[2] > 0 ? (size_t)m[0] * nb * m[0] * nb : 0) +
-                            (m[1] > 0 ? (size_t)m[0] * (n + 1) * (npair + (size_t)ctx->nrhs * nb) : 0));
+      pd = std::max(pd, (m[2] > 0 || m[3] > 0 ? (size_t)m[0] * nb * m[0] * nb : 0) +
+                            (m[1] > 0 ? (size_t)m[0] * (n + 1) * (npair + (size_t)ctx->nrhs * nb) : 0) +
+                            (m[3] > 0 ? (size_t)ctx->nrhs * m[0] * nb : 0));
     const size_t solve_part = NB * NB + sg_al + (size_t)ctx->nrhs * NB + half_rb;
     const size_t mono_part = (size_t)2 * CH * a.mono_stride;
     a.off_mono = 0;
@@ -967,6 +995,16 @@ extern "C" int tp_boundary_points(const tp_ctx* ctx, double* xt) {
     return TP_ERR_ARG;
   }
   std::copy(ctx->bnd_xt.begin(), ctx->bnd_xt.end(), xt);
+  return TP_OK;
+}
+
+extern "C" int tp_boundary_kinds(const tp_ctx* ctx, double* nrm, int8_t* kind) {
+  if (!ctx) {
+    tp::set_error("tp_boundary_kinds: null context");
+    return TP_ERR_ARG;
+  }
+  if (nrm) std::copy(ctx->bnd_nrm.begin(), ctx->bnd_nrm.end(), nrm);
+  if (kind) std::copy(ctx->bnd_kind.begin(), ctx->bnd_kind.end(), kind);
   return TP_OK;
 }
 

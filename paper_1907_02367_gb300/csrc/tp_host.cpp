@@ -78,13 +78,14 @@ bool build_topology(const tp_mesh_desc* m, Topology* t) {
   struct F {
     std::array<int32_t, 3> v;
     int32_t elem, opp;
+    int32_t o;   // local index of opp in the element
   };
   std::vector<F> fs;
   fs.reserve(t->ne * (n + 1));
   for (int64_t k = 0; k < t->ne; ++k) {
     const int32_t* el = &t->elems[k * (n + 1)];
     for (int o = 0; o <= n; ++o) {
-      F f{{-1, -1, -1}, (int32_t)k, el[o]};
+      F f{{-1, -1, -1}, (int32_t)k, el[o], o};
       int c = 0;
       for (int i = 0; i <= n; ++i)
         if (i != o) f.v[c++] = el[i];
@@ -96,6 +97,7 @@ bool build_topology(const tp_mesh_desc* m, Topology* t) {
   t->facet_vert.clear();
   t->facet_nrm.clear();
   t->facet_elem.clear();
+  t->facet_kind.clear();
   // unit normal of facet f pointing away from vertex opp
   auto facet_normal = [&](const F& f, int32_t opp, double* nrm) {
     nrm[0] = nrm[1] = nrm[2] = 0.0;
@@ -143,6 +145,12 @@ bool build_topology(const tp_mesh_desc* m, Topology* t) {
         t->facet_nrm.push_back(nrm[d]);
       }
       t->facet_elem.push_back(f.elem);
+      const int8_t kind = m->bnd_type ? m->bnd_type[(int64_t)f.elem * (n + 1) + f.o] : 0;
+      if (kind != 0 && kind != 1) {
+        set_error("tp: bnd_type of element " + std::to_string(f.elem) + " is neither 0 (Dirichlet) nor 1 (Neumann)");
+        return false;
+      }
+      t->facet_kind.push_back(kind);
     } else if (j - i == 2) {
       const F& f1 = fs[i];
       const F& f2 = fs[i + 1];

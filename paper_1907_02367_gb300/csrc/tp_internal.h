@@ -34,6 +34,7 @@ struct Topology {
   std::vector<double> facet_nrm;              // boundary facets: outward unit normal (dim)
   std::vector<int32_t> vfac_ptr, vfac;        // boundary facets through a vertex (facet order)
   std::vector<int32_t> facet_elem;            // boundary facets: owning element
+  std::vector<int8_t> facet_kind;             // boundary facets: 0 Dirichlet, 1 Neumann
   // time-like interface facets (different wave speed on the two sides), listed
   // per vertex of the facet: dim vertex ids, the two elements (+ = lower index),
   // the unit normal out of the + element

@@ -73,7 +73,7 @@ struct KArgs {
   const double* tent_tbot;
   const double* tent_h;
   const double* tent_ih;      // 1 / h
-  const int* tent_hdr;        // per tent: v, record offsets (int, double), elements, Dirichlet and interface facets, materials, 0
+  const int* tent_hdr;        // per tent: v, record offsets (int, double), elements, Dirichlet and interface facets, materials, Neumann facets
   const int* vrec_i;          // per vertex: star record, ints (elements, facets)
   const double* vrec_d;       // per vertex: star record, doubles (x_v, speeds, coordinates, normals)
   const long long* tent_gdoff;
@@ -544,19 +544,21 @@ __device__ __forceinline__ void iface_terms(const KArgs& a, int i, int j, const 
 // awaited tent is held by a running cluster: no launch per level, and a tent
 // starts as soon as its own inputs are ready.  The front and the front times
 // are read through L2 (ld.global.cg) so that no stale L1 line is used.
-template <int DIM, bool MIXED, bool ADJ, bool PERSIST>
+template <int DIM, bool MIXED, bool ADJ, bool PERSIST, bool NEU>
 __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int tent0) {
   using T = typename std::conditional<MIXED, dd, double>::type;
   using R = Ar<T>;
   constexpr int NV = DIM + 1;   // vertices per element
   constexpr int C = DIM + 2;    // U, v, sigma  (and gamma, alpha, beta_m moments)
   extern __shared__ __align__(16) double sm[];
-  __shared__ int s_P, s_v, s_nfac, s_nif, s_ng;
+  __shared__ int s_P, s_v, s_nfac, s_nif, s_ng, s_nneu;
   __shared__ double s_ttop, s_tbot, s_tc, s_ih;
   __shared__ double s_gc[tp::kMaxGroups], s_gic2[tp::kMaxGroups];   // speeds and 1/c^2 of the materials
   __shared__ double s_xv[DIM];
   __shared__ int s_el[tp::kMaxPatch], s_grp[tp::kMaxPatch];
-  __shared__ int s_vid[tp::kMaxPatch][NV], s_fw[tp::kMaxFacets][NV];   // vertex ids of elements, facets
+  // vertex ids of elements; of facets (slots 2..): for boundary facets slot 0
+  // holds the block of their data among the vertex's boundary facets
+  __shared__ int s_vid[tp::kMaxPatch][NV], s_fw[tp::kMaxFacets][NV];
   __shared__ double s_X[tp::kMaxPatch][NV][DIM];
   __shared__ double s_tb[tp::kMaxPatch][NV], s_tt[tp::kMaxPatch][NV];
   __shared__ double s_gb[tp::kMaxPatch][DIM], s_gt[tp::kMaxPatch][DIM];
@@ -623,7 +625,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
   // one round of loads: the tent's header, then its vertex's star record
   const int4 h0 = __ldg(reinterpret_cast<const int4*>(a.tent_hdr) + 2 * (size_t)tent);
   const int4 h1 = __ldg(reinterpret_cast<const int4*>(a.tent_hdr) + 2 * (size_t)tent + 1);
-  const int v = h0.x, P = h0.w, nfac = h1.x, nif = h1.y, ng = h1.z;
+  const int v = h0.x, P = h0.w, nfac = h1.x, nif = h1.y, ng = h1.z;   // Neumann facets: h1.w, s_nneu
   if (tid == 0) {
     s_v = v;
     s_P = P;
@@ -632,11 +634,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
     s_nfac = nfac;
     s_nif = nif;
     s_ng = ng;
+    s_nneu = h1.w;
   }
   for (int id = tid; id < NG * nmom; id += blockDim.x) sPM[id] = R::zero();
   for (int id = tid; id < NG * (DIM + 2) * npair; id += blockDim.x) sPG[id] = R::zero();   // PG, PH, PGb contiguous
   const int N = ng * nb;
-  const bool extra = (nfac > 0 || nif > 0);
+  const bool extra = (nfac > 0 || nif > 0 || (NEU && h1.w > 0));
   {
     const int* ri = a.vrec_i + h0.y;
     const double* rd = a.vrec_d + h0.z;
@@ -655,13 +658,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
       }
     }
     // vertical face simplices (x_v, t_bot), (x_v, t_top), (x_w, tau_w): Dirichlet
-    // facets first, then the time-like interface facets
+    // facets first, then the time-like interface facets, then Neumann facets
     const int* rfi = ri + P * (2 + NV);
     const double* rfd = rX + P * NV * DIM;
-    for (int f = tid; f < nfac + nif; f += blockDim.x) {
-      for (int i = 2; i < NV; ++i) s_fw[f][i] = __ldg(rfi + f * (NV + 2) + i);
-      s_fg[f] = __ldg(rfi + f * (NV + 2) + NV);
-      s_fg2[f] = __ldg(rfi + f * (NV + 2) + NV + 1);
+    for (int f = tid; f < nfac + nif + (NEU ? h1.w : 0); f += blockDim.x) {
+      for (int i = 2; i < NV; ++i) s_fw[f][i] = __ldg(rfi + f * (NV + 3) + i);
+      s_fg[f] = __ldg(rfi + f * (NV + 3) + NV);
+      s_fg2[f] = __ldg(rfi + f * (NV + 3) + NV + 1);
+      s_fw[f][0] = __ldg(rfi + f * (NV + 3) + NV + 2);
       const double* fd = rfd + f * (DIM + NV * DIM);
       for (int d = 0; d < DIM; ++d) s_fn[f][d] = __ldg(fd + d);
       for (int i = 0; i < NV; ++i)
@@ -731,7 +735,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
     const double ck = s_gc[s_grp[k]];
     if (!(ck * ck * g2 < 1.0)) flag_error(a, TP_ERR_CAUSALITY, tent);   // space-like top face: c |g| < 1
   }
-  for (int f = tid; f < nfac + nif; f += blockDim.x) {
+  for (int f = tid; f < nfac + nif + (NEU ? s_nneu : 0); f += blockDim.x) {
     s_fP[f][0][DIM] = tbot;
     s_fP[f][1][DIM] = s_ttop;
     for (int c2 = 2; c2 <= DIM; ++c2) s_fP[f][c2][DIM] = __ldcg(a.tau + s_fw[f][c2]);
@@ -908,13 +912,21 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
   // then the data moments in the same arrangement (nrhs*nb each).  The
   // congruences with the derivative maps are linear, so these sums carry all
   // a tent needs; they are formed after the cluster reduction.
-  T* sFD = sPD + (nif > 0 ? (size_t)N * N : 0);
+  // Interface and Neumann facets add their blocks to the partial A (N*N)
+  // at once; Neumann facets also to a partial b (nrhs*N, after the
+  // Dirichlet sums).
+  const int nneu = NEU ? s_nneu : 0;   // (kernels for meshes without Neumann facets leave out their code)
+  const bool pblk = nif > 0 || nneu > 0;
+  T* sFD = sPD + (pblk ? (size_t)N * N : 0);
   T* sDD = sFD + (size_t)ng * (DIM + 1) * npair;
   const int nfd = nfac > 0 ? ng * (DIM + 1) * (npair + nrhs * nb) : 0;
+  T* sPBN = sFD + nfd;
   if (extra) {
-    if (nif > 0)
+    if (pblk)
       for (int id = tid; id < N * N; id += blockDim.x) sPD[id] = R::zero();
     for (int id = tid; id < nfd; id += blockDim.x) sFD[id] = R::zero();
+    if (nneu > 0)
+      for (int id = tid; id < nrhs * N; id += blockDim.x) sPBN[id] = R::zero();
     for (int id = tid; id < nrhs * nb; id += blockDim.x) sDel[id] = R::zero();
     for (int id = tid; id < nb * nb; id += blockDim.x) sFpm[id] = R::zero();
     __syncthreads();
@@ -963,7 +975,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
           pp[0] = R::from(s_gc[s_fg[f]] * (xt[DIM] - tc) * ih);
           for (int d = 0; d < DIM; ++d) pp[1 + d] = R::from((xt[d] - s_xv[d]) * ih);
           pp[DIM + 1] = R::from(sw);
-          const long long goff = a.tent_gdoff[tent] + q;
+          // the facet's block of boundary data (without Neumann facets: the facet's own index)
+          const long long goff = a.tent_gdoff[tent] + (NEU ? (long long)s_fw[f][0] * Q + qf : (long long)q);
           for (int r = 0; r < nrhs; ++r)
             sGd[id * nrhs + r] = R::from((!ADJ && a.gD != nullptr) ? sw * a.gD[(long long)r * a.n_bnd + goff] : 0.0);
         }
@@ -998,11 +1011,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
       }
       __syncthreads();
     }
-    // (b) time-like interface facets, one after the other, each facet's points
-    // split over the cluster; their blocks go into the partial A at once
+    // (b) time-like interface facets, then Neumann facets, one after the
+    // other, each facet's points split over the cluster; their blocks go into
+    // the partial A at once.  Neumann facets (eq. 4.1), with F the facet Gram
+    // of U-values and delta = sum w g_N u:
+    //   A_N = -(c/h^2) D_n F D_t^T + (beta/h^2) D_n F D_n^T,
+    //   b_N = -(c/h) D_t delta - (beta/h) D_n delta
+    // (v = (c/h) D_t u, sigma.n = -(1/h) D_n u, D_n = sum_m n_m D_m)
     const int fsl = (Q + CS - 1) / CS;
     const int f0 = min(Q, rank * fsl), f1 = min(Q, f0 + fsl);
-    for (int f = nfac; f < nfac + nif; ++f) {
+    for (int f = nfac; f < nfac + nif + nneu; ++f) {
+      const bool neu = NEU && f >= nfac + nif;
       const int gp = s_fg[f], gm = s_fg2[f];
       const double cp = s_gc[gp], cm = s_gc[gm];
       T aF[kMaxPair], aF2[kMaxPair];
@@ -1010,7 +1029,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
       for (int s = 0; s < kMaxPair; ++s) aF[s] = aF2[s] = R::zero();
       for (int base = f0; base < f1; base += CH) {
         const int nq = min(CH, f1 - base);
-        const int npt = 2 * nq;   // + side points, then - side
+        const int npt = neu ? nq : 2 * nq;   // interface: + side points, then - side
         for (int id = tid; id < nq; id += blockDim.x) {
           const int q = base + id;
           double xt[DIM + 1];
@@ -1024,10 +1043,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
           pp[0] = R::from(cp * (xt[DIM] - tc) * ih);
           for (int d = 0; d < DIM; ++d) pp[1 + d] = R::from((xt[d] - s_xv[d]) * ih);
           pp[DIM + 1] = R::from(sw);
-          T* p2 = sPt + (nq + id) * (DIM + 2);
-          p2[0] = R::from(cm * (xt[DIM] - tc) * ih);
-          for (int d = 0; d < DIM; ++d) p2[1 + d] = pp[1 + d];
-          p2[DIM + 1] = pp[DIM + 1];
+          if (neu) {
+            const long long goff = a.tent_gdoff[tent] + (long long)s_fw[f][0] * Q + q;
+            for (int r = 0; r < nrhs; ++r)
+              sGd[id * nrhs + r] = R::from((!ADJ && a.gD != nullptr) ? sw * a.gD[(long long)r * a.n_bnd + goff] : 0.0);
+          } else {
+            T* p2 = sPt + (nq + id) * (DIM + 2);
+            p2[0] = R::from(cm * (xt[DIM] - tc) * ih);
+            for (int d = 0; d < DIM; ++d) p2[1 + d] = pp[1 + d];
+            p2[DIM + 1] = pp[DIM + 1];
+          }
         }
         eval_uvalues_block<DIM, T>(a, npt, sPt, sM, sU);
         for (int ql = 0; ql < nq; ++ql) {
@@ -1037,14 +1062,23 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
           for (int s = 0; s < kMaxPair; ++s)
             if (tid + s * kThreads < npair) {
               aF[s] = R::fma(u[pi[s]], u[pj[s]], aF[s]);
-              aF2[s] = R::fma(u2[pi[s]], u2[pj[s]], aF2[s]);
+              if (!neu) aF2[s] = R::fma(u2[pi[s]], u2[pj[s]], aF2[s]);
             }
         }
-        for (int id = tid; id < nb * nb; id += blockDim.x) {
-          const int i = id / nb, j = id % nb;
-          T t = sFpm[id];
-          for (int ql = 0; ql < nq; ++ql) t = R::fma(sU[(size_t)ql * nb + i], sU[(size_t)(nq + ql) * nb + j], t);
-          sFpm[id] = t;
+        if (neu) {
+          for (int id = tid; id < nrhs * nb; id += blockDim.x) {
+            const int r = id / nb, i = id % nb;
+            T t = sDel[id];
+            for (int ql = 0; ql < nq; ++ql) t = R::fma(sGd[ql * nrhs + r], sU[(size_t)ql * nb + i], t);
+            sDel[id] = t;
+          }
+        } else {
+          for (int id = tid; id < nb * nb; id += blockDim.x) {
+            const int i = id / nb, j = id % nb;
+            T t = sFpm[id];
+            for (int ql = 0; ql < nq; ++ql) t = R::fma(sU[(size_t)ql * nb + i], sU[(size_t)(nq + ql) * nb + j], t);
+            sFpm[id] = t;
+          }
         }
         __syncthreads();
       }
@@ -1057,6 +1091,30 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
       __syncthreads();
       T nrm[DIM];
       for (int d = 0; d < DIM; ++d) nrm[d] = R::from(s_fn[f][d]);
+      if (neu) {
+        const double ih2 = ih * ih;
+        for (int id = tid; id < nb * nb; id += blockDim.x) {
+          const int i = id / nb, j = id % nb;
+          T tt_, nt_, tn_, nn_;
+          iface_terms<DIM, T, 0>(a, i, j, sF, nb, nrm, &tt_, &nt_, &tn_, &nn_);
+          const T t = R::fma(R::from(-cp * ih2), nt_, R::mul(R::from(a.beta * ih2), nn_));
+          T* dst = sPD + (size_t)(gp * nb + i) * N + gp * nb + j;
+          *dst = R::add(*dst, t);
+        }
+        for (int id = tid; id < nrhs * nb; id += blockDim.x) {
+          const int r = id / nb, i = id % nb;
+          const T* del = sDel + (size_t)r * nb;
+          T dn = R::zero();
+          for (int d = 0; d < DIM; ++d) dn = R::fma(nrm[d], rel_apply<DIM, T>(a, i, 1 + d, del), dn);
+          const T t = R::fma(R::from(-a.beta * ih), dn, R::mul(R::from(-cp * ih), rel_apply<DIM, T>(a, i, 0, del)));
+          T* dst = sPBN + (size_t)r * N + gp * nb + i;
+          *dst = R::add(*dst, t);
+        }
+        __syncthreads();
+        for (int id = tid; id < nrhs * nb; id += blockDim.x) sDel[id] = R::zero();
+        __syncthreads();
+        continue;
+      }
       {
         const double ih2 = ih * ih;
         for (int id = tid; id < 4 * nb * nb; id += blockDim.x) {
@@ -1116,10 +1174,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
   // layout [G (NG*npair) | H_m (NG*DIM*npair) | Gbot (NG*npair)]; unused groups hold zeros
   cluster_reduce(sPG, sSG, NG * (DIM + 2) * npair);
   cluster_reduce(sPM, sSM, ng * nmom);
-  if (nif > 0) cluster_reduce(sPD, sA, N * N);   // interface blocks
+  if (pblk) cluster_reduce(sPD, sA, N * N);   // interface and Neumann blocks
   else
     for (int id = tid; id < N * N; id += blockDim.x) sA[id] = R::zero();
-  for (int id = tid; id < nrhs * N; id += blockDim.x) sb[id] = R::zero();
+  if (NEU && s_nneu > 0) cluster_reduce(sFD + nfd, sb, nrhs * N);   // Neumann data (after the Dirichlet sums)
+  else
+    for (int id = tid; id < nrhs * N; id += blockDim.x) sb[id] = R::zero();
   // in place: each entry is read and rewritten by the one thread that owns it
   if (nfac > 0) cluster_reduce(sFD, sFD, nfd);
   cluster.sync();   // no CTA leaves or reuses its partials while another still reads them
@@ -1722,7 +1782,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
 
 
 // launchers, one translation unit per space dimension (tp_layer_d<n>.cu)
-// mode: 0 forward binary64, 1 forward mixed, 2 adjoint binary64;
+// mode: 0 forward binary64, 1 forward mixed, 2 adjoint binary64, plus 4 for
+// meshes with Neumann facets;
 // persistent: one resident grid of clusters pulling tents from a queue
 #define TP_DECLARE_LAUNCHERS(D)                                                                  \
   cudaError_t layer_attrs_d##D(size_t smem);                                                      \

@@ -18,11 +18,14 @@ namespace {
 
 template <bool MIXED, bool ADJ, bool PERSIST>
 cudaError_t set_attr(size_t smem) {
-  return cudaFuncSetAttribute(k_layer<TP_DIM, MIXED, ADJ, PERSIST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_layer<TP_DIM, MIXED, ADJ, PERSIST, false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_layer<TP_DIM, MIXED, ADJ, PERSIST, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)smem);
 }
 
-template <bool MIXED, bool ADJ, bool PERSIST>
+template <bool MIXED, bool ADJ, bool PERSIST, bool NEU>
 cudaError_t launch(const KArgs& a, int n_cluster, int cs, int t0, size_t smem, cudaStream_t st) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(n_cluster * cs));
@@ -36,10 +39,10 @@ cudaError_t launch(const KArgs& a, int n_cluster, int cs, int t0, size_t smem, c
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_layer<TP_DIM, MIXED, ADJ, PERSIST>, a, t0);
+  return cudaLaunchKernelEx(&cfg, k_layer<TP_DIM, MIXED, ADJ, PERSIST, NEU>, a, t0);
 }
 
-template <bool MIXED, bool ADJ, bool PERSIST>
+template <bool MIXED, bool ADJ, bool PERSIST, bool NEU>
 cudaError_t occupancy(int cs, size_t smem, int* n) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)cs);
@@ -52,7 +55,7 @@ cudaError_t occupancy(int cs, size_t smem, int* n) {
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaOccupancyMaxActiveClusters(n, k_layer<TP_DIM, MIXED, ADJ, PERSIST>, &cfg);
+  return cudaOccupancyMaxActiveClusters(n, k_layer<TP_DIM, MIXED, ADJ, PERSIST, NEU>, &cfg);
 }
 
 }  // namespace
@@ -62,16 +65,17 @@ cudaError_t TP_CAT(layer_static_smem_d, TP_DIM)(size_t* bytes) {
   size_t m = 0;
   cudaFuncAttributes fa;
   cudaError_t e;
-  if ((e = cudaFuncGetAttributes(&fa, k_layer<TP_DIM, false, false, false>)) != cudaSuccess) return e;
-  m = std::max(m, fa.sharedSizeBytes);
-  if ((e = cudaFuncGetAttributes(&fa, k_layer<TP_DIM, true, false, false>)) != cudaSuccess) return e;
-  m = std::max(m, fa.sharedSizeBytes);
-  if ((e = cudaFuncGetAttributes(&fa, k_layer<TP_DIM, false, true, false>)) != cudaSuccess) return e;
-  m = std::max(m, fa.sharedSizeBytes);
-  if ((e = cudaFuncGetAttributes(&fa, k_layer<TP_DIM, false, false, true>)) != cudaSuccess) return e;
-  m = std::max(m, fa.sharedSizeBytes);
-  if ((e = cudaFuncGetAttributes(&fa, k_layer<TP_DIM, true, false, true>)) != cudaSuccess) return e;
-  *bytes = std::max(m, fa.sharedSizeBytes);
+  const void* k[] = {
+      (const void*)k_layer<TP_DIM, false, false, false, false>, (const void*)k_layer<TP_DIM, true, false, false, false>,
+      (const void*)k_layer<TP_DIM, false, true, false, false>, (const void*)k_layer<TP_DIM, false, false, true, false>,
+      (const void*)k_layer<TP_DIM, true, false, true, false>, (const void*)k_layer<TP_DIM, false, false, false, true>,
+      (const void*)k_layer<TP_DIM, true, false, false, true>, (const void*)k_layer<TP_DIM, false, true, false, true>,
+      (const void*)k_layer<TP_DIM, false, false, true, true>, (const void*)k_layer<TP_DIM, true, false, true, true>};
+  for (const void* f : k) {
+    if ((e = cudaFuncGetAttributes(&fa, f)) != cudaSuccess) return e;
+    m = std::max(m, fa.sharedSizeBytes);
+  }
+  *bytes = m;
   return cudaSuccess;
 }
 
@@ -86,18 +90,29 @@ cudaError_t TP_CAT(layer_attrs_d, TP_DIM)(size_t smem) {
 
 cudaError_t TP_CAT(launch_layer_d, TP_DIM)(const KArgs& a, int n_cluster, int cs, int t0, size_t smem,
                                            cudaStream_t st, int mode, bool persistent) {
+  const bool neu = (mode & 4) != 0;
+  mode &= 3;
   if (persistent) {
-    if (mode == 1) return launch<true, false, true>(a, n_cluster, cs, t0, smem, st);
-    return launch<false, false, true>(a, n_cluster, cs, t0, smem, st);
+    if (mode == 1)
+      return neu ? launch<true, false, true, true>(a, n_cluster, cs, t0, smem, st)
+                 : launch<true, false, true, false>(a, n_cluster, cs, t0, smem, st);
+    return neu ? launch<false, false, true, true>(a, n_cluster, cs, t0, smem, st)
+               : launch<false, false, true, false>(a, n_cluster, cs, t0, smem, st);
   }
-  if (mode == 2) return launch<false, true, false>(a, n_cluster, cs, t0, smem, st);
-  if (mode == 1) return launch<true, false, false>(a, n_cluster, cs, t0, smem, st);
-  return launch<false, false, false>(a, n_cluster, cs, t0, smem, st);
+  if (mode == 2)
+    return neu ? launch<false, true, false, true>(a, n_cluster, cs, t0, smem, st)
+               : launch<false, true, false, false>(a, n_cluster, cs, t0, smem, st);
+  if (mode == 1)
+    return neu ? launch<true, false, false, true>(a, n_cluster, cs, t0, smem, st)
+               : launch<true, false, false, false>(a, n_cluster, cs, t0, smem, st);
+  return neu ? launch<false, false, false, true>(a, n_cluster, cs, t0, smem, st)
+             : launch<false, false, false, false>(a, n_cluster, cs, t0, smem, st);
 }
 
 cudaError_t TP_CAT(max_clusters_d, TP_DIM)(int cs, size_t smem, int mode, int* n) {
-  if (mode == 1) return occupancy<true, false, true>(cs, smem, n);
-  return occupancy<false, false, true>(cs, smem, n);
+  const bool neu = (mode & 4) != 0;
+  if ((mode & 3) == 1) return neu ? occupancy<true, false, true, true>(cs, smem, n) : occupancy<true, false, true, false>(cs, smem, n);
+  return neu ? occupancy<false, false, true, true>(cs, smem, n) : occupancy<false, false, true, false>(cs, smem, n);
 }
 
 }  // namespace tp
