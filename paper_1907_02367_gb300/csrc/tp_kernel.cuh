@@ -511,7 +511,10 @@ __device__ __forceinline__ void iface_terms(const KArgs& a, int i, int j, const 
 // beta_m = sum w (s_b,m - v_b g_b,m) u_b.  A Dirichlet facet with normal n
 // adds A_D = (c/h) D_t F E^T, b_D = E' delta, F = sum w u u^T,
 // delta = sum w g_D u, E = alpha_D (c/h) D_t - (1/h) D_n, E' = alpha_D (c/h) D_t + (1/h) D_n,
-// D_n = sum_m n_m D_m.  A time-like facet between groups + and - (normal n out
+// D_n = sum_m n_m D_m.  A Neumann facet (sigma.n = g_N) adds
+// A_N = -(c/h^2) D_n F D_t^T + (beta/h^2) D_n F D_n^T and
+// b_N = -(c/h) D_t delta - (beta/h) D_n delta, delta = sum w g_N u (eq. 4.1; the
+// code is compiled in only when NEU).  A time-like facet between groups + and - (normal n out
 // of +) adds, for test side t and trial side s (signs s_+ = 1, s_- = -1),
 //   A^{ts} = s_t h^-2 [ -c_s/2 D_n F^{ts} D_t^T - c_t/2 D_t F^{ts} D_n^T ]
 //          + s_t s_s h^-2 [ alpha c_s c_t D_t F^{ts} D_t^T + beta D_n F^{ts} D_n^T ],
