@@ -865,9 +865,9 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
     take(&a.off_pg, (size_t)ngmax * npair);        // G, H_m, Gbot contiguous
     take(&a.off_ph, (size_t)ngmax * n * npair);
     take(&a.off_pgb, (size_t)ngmax * npair);
-    take(&a.off_pm, (size_t)ngmax * nmom);
+    take(&a.off_pm, (size_t)ngmax * nmom);        // moments: partials, summed in place, then the outflow vectors
+    a.off_sm = a.off_y = a.off_pm;
     take(&a.off_pd, pd);
-    take(&a.off_sm, (size_t)ngmax * nmom);
     take(&a.off_f, npair);
     take(&a.off_f2, npair);
     take(&a.off_fpm, (size_t)nb * nb);
@@ -876,7 +876,6 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
     take(&a.off_pt, (size_t)2 * CH * (n + 2));
     take(&a.off_cb, (size_t)CH * ctx->nrhs * C);
     take(&a.off_gd, (size_t)CH * ctx->nrhs);
-    take(&a.off_y, (size_t)ngmax * nmom);
     take(&a.off_rd, NB);
     take(&a.off_eq, half_nb);
     take(&a.off_keep, (size_t)keep * nb);          // top U-values of the CTA's slice, kept for the outflow

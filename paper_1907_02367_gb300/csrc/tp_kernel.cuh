@@ -605,10 +605,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
   T* sPG = reinterpret_cast<T*>(sm + a.off_pg);      // NG*npair   this CTA: G (top) per group
   T* sPH = reinterpret_cast<T*>(sm + a.off_ph);      // NG*DIM*npair  H_m
   T* sPGb = reinterpret_cast<T*>(sm + a.off_pgb);    // NG*npair   G (bottom, recovery)
-  T* sPM = reinterpret_cast<T*>(sm + a.off_pm);      // NG*nmom    moments (gamma, alpha, beta_m) per rhs
+  T* sPM = reinterpret_cast<T*>(sm + a.off_pm);      // NG*nmom    moments (gamma, alpha, beta_m) per rhs, this CTA
   T* sPD = reinterpret_cast<T*>(sm + a.off_pd);      // N*N        interface blocks (tents with interface facets)
   T* sSG = reinterpret_cast<T*>(sm + a.off_sg);      // NG*(DIM+2)*npair  summed G, H_m, Gbot
-  T* sSM = reinterpret_cast<T*>(sm + a.off_sm);      // NG*nmom    summed moments
+  T* sSM = reinterpret_cast<T*>(sm + a.off_sm);      // NG*nmom    summed moments (in place of sPM)
   T* sF = reinterpret_cast<T*>(sm + a.off_f);        // npair      facet Gram (+ side)
   T* sF2 = reinterpret_cast<T*>(sm + a.off_f2);      // npair      facet Gram (- side)
   T* sFpm = reinterpret_cast<T*>(sm + a.off_fpm);    // nb*nb      facet Gram (+ test, - trial)
@@ -618,7 +618,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
   T* sM = reinterpret_cast<T*>(sm + a.off_mono);     // 2*CH*mono_stride
   T* sCB = reinterpret_cast<T*>(sm + a.off_cb);      // CH*nrhs*C  data coefficients
   T* sGd = reinterpret_cast<T*>(sm + a.off_gd);      // CH*nrhs    Dirichlet data coefficients
-  T* sY = reinterpret_cast<T*>(sm + a.off_y);        // NG*nmom    outflow coefficient vectors
+  T* sY = reinterpret_cast<T*>(sm + a.off_y);        // NG*nmom    outflow coefficient vectors (sPM, dead after the congruence)
   double* sRD = sm + a.off_rd;                       // N          reciprocal pivots (binary64 path)
 
   // ---------------- phase 0: tent, materials and patch geometry ----------------
@@ -1176,7 +1176,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
   cluster.sync();
   // layout [G (NG*npair) | H_m (NG*DIM*npair) | Gbot (NG*npair)]; unused groups hold zeros
   cluster_reduce(sPG, sSG, NG * (DIM + 2) * npair);
-  cluster_reduce(sPM, sSM, ng * nmom);
+  cluster_reduce(sPM, sSM, ng * nmom);   // in place (sSM == sPM): each entry has one owner
   if (pblk) cluster_reduce(sPD, sA, N * N);   // interface and Neumann blocks
   else
     for (int id = tid; id < N * N; id += blockDim.x) sA[id] = R::zero();
