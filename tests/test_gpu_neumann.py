@@ -118,3 +118,24 @@ def test_neumann_adjoint_dot_product(cuda_device):
     lhs = float(torch.sum(lam * Ff))
     rhs = float(torch.sum(Fl * f))
     assert abs(lhs - rhs) <= 1e-11 * float(torch.linalg.norm(lam) * torch.linalg.norm(Ff))
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("mixed", 1e-8)])
+def test_interface_meeting_neumann_and_dirichlet_walls(cuda_device, precision, tol):
+    """Two materials (c = 1 left of x = 1/2, c = 2.5 right of it) whose interface
+    meets a Neumann wall (y = 0) and a Dirichlet wall (y = 1): tents at the
+    junctions carry interface, Neumann and Dirichlet facets and two
+    polynomials at once; against the oracle."""
+    mesh = inputs.mesh_square(4, 0.0, seed=1)
+    cen = mesh.coords[mesh.elems].mean(axis=1)
+    mesh.c[:] = np.where(cen[:, 0] > 0.5, 2.5, 1.0)
+    marker = inputs.boundary_marker(mesh, lambda x: x[1] < 1e-12)
+    pulse = inputs.gaussian_pulse(np.array([0.45, 0.3]), 0.25)
+    p, T = 3, 0.2
+    s = _solver(mesh, p, T, marker, precision)
+    got, tau, st = _run(s, pulse)
+    assert st == (0, 0)
+    r = pitching.pitch(mesh.coords, mesh.elems, mesh.c, inputs.pitch_kappa(mesh), T)
+    ref, tau_ref = tdg.sweep(mesh.coords, mesh.elems, mesh.c, p, r, pulse, None, bnd_type=marker)
+    assert np.array_equal(tau, tau_ref)
+    assert _rel(got.reshape(ref.shape), ref) <= tol
