@@ -73,7 +73,10 @@ typedef struct tp_mesh_desc {
  * pipes, binary32 inverse of the equilibrated local matrix, iterative
  * refinement to float-float accuracy; a tent whose refinement does not
  * settle is solved by a direct binary64 LU instead);
- * nrhs: right-hand sides advanced together (same tents, same matrices);
+ * nrhs: right-hand sides advanced together (same tents, same matrices;
+ * when one CTA's shared memory cannot hold all of them, tp_create picks the
+ * largest divisor of nrhs that fits and every sweep runs the groups of that
+ * size one after the other, each assembling its own tent matrices);
  * schedule: how tp_advance runs the levels -- TP_SCHED_DATAFLOW (default):
  * one resident kernel whose clusters take the tents in level order and each
  * start as soon as the earlier tents of its vertex and neighbours are done
@@ -131,7 +134,7 @@ void tp_destroy_basis(tp_basis* basis);
  * facets.  Errors: TP_ERR_ARG on mismatched dim/p; TP_ERR_UNSUPPORTED when a
  * patch has more than 4 wave speeds, more than 64 elements or more than 16
  * boundary plus interface facets, or the shared-memory plan (dim U^p,
- * materials, nrhs) does not fit one CTA; TP_ERR_OOM. */
+ * materials) does not fit one CTA even for one right-hand side; TP_ERR_OOM. */
 int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const tp_basis* basis,
               const tp_params* prm, tp_ctx** out);
 /* n_front = n_elem * Q points, n_comp = dim + 2, n_bnd = number of Dirichlet

@@ -132,6 +132,10 @@ struct tp_ctx {
   double T_final = 0.0;
   double* d_adj = nullptr;
   double* d_tau_adj = nullptr;
+  // right-hand sides in groups of nrhs_g (the shared-memory plan holds one
+  // group; each sweep runs group after group from the same front times)
+  int rhs_groups = 1, nrhs_g = 1;
+  double* d_tau_save = nullptr;
   cudaGraphExec_t adj_graph = nullptr;
   size_t smem_bytes = 0;
   int energy_blocks = 0;
@@ -240,15 +244,33 @@ int level_cluster_size(const tp_ctx* ctx, int64_t nt) {
   return cs;
 }
 
-int launch_level(tp_ctx* ctx, int32_t L, cudaStream_t st, bool adj = false) {
+// the arguments of right-hand-side group k: its slice of the front and of
+// the boundary data (both right-hand-side major)
+KArgs group_args(const tp_ctx* ctx, KArgs a, int k) {
+  a.front += (size_t)k * ctx->nrhs_g * ctx->ne * ctx->Q * ctx->C;
+  if (a.gD) a.gD += (size_t)k * ctx->nrhs_g * ctx->n_bnd;
+  return a;
+}
+
+// one level; group < 0: every right-hand-side group, each from the front
+// times before the level (saved, and restored before every group after the first)
+int launch_level(tp_ctx* ctx, int32_t L, cudaStream_t st, bool adj = false, int group = -1) {
   const int64_t t0 = ctx->level_ptr[L - 1], t1 = ctx->level_ptr[L];
   if (t1 <= t0) return TP_OK;
   const int nt = (int)(t1 - t0);
   const int cs = level_cluster_size(ctx, nt);
   const int mode = adj ? 2 : (ctx->mixed ? 1 : 0);
-  cudaError_t e = launch_layer(ctx, adj ? ctx->args_adj : ctx->args, nt, cs, (int)t0, st, mode, false);
-  TP_CUDA_OK(e);
-  TP_CUDA_OK(cudaGetLastError());
+  double* tau = adj ? ctx->d_tau_adj : ctx->d_tau;
+  const int k0 = group < 0 ? 0 : group, k1 = group < 0 ? ctx->rhs_groups : group + 1;
+  const bool restore = group < 0 && ctx->rhs_groups > 1;
+  if (restore) TP_CUDA_OK(cudaMemcpyAsync(ctx->d_tau_save, tau, ctx->nv * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  for (int k = k0; k < k1; ++k) {
+    if (restore && k > 0)
+      TP_CUDA_OK(cudaMemcpyAsync(tau, ctx->d_tau_save, ctx->nv * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    cudaError_t e = launch_layer(ctx, group_args(ctx, adj ? ctx->args_adj : ctx->args, k), nt, cs, (int)t0, st, mode, false);
+    TP_CUDA_OK(e);
+    TP_CUDA_OK(cudaGetLastError());
+  }
   return TP_OK;
 }
 
@@ -831,15 +853,16 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
   a.mono_stride = ctx->nmono | 1;
   // shared-memory plan: the largest chunk of points that keeps two CTAs per SM,
   // else the largest that fits one
+  int nrg = ctx->nrhs;   // right-hand sides per group
   auto plan = [&](int CH, int keep) {
     size_t off = 0;
     auto take = [&](int* field, size_t count) {
       if (field) *field = (int)off;
       off += count;
     };
-    const size_t nmom = (size_t)ctx->nrhs * C * nb;
+    const size_t nmom = (size_t)nrg * C * nb;
     const size_t NB = (size_t)ngmax * nb;          // unknowns of the largest tent
-    const size_t half_nb = (NB + 1) / 2, half_rb = ((size_t)ctx->nrhs * NB + 1) / 2;
+    const size_t half_nb = (NB + 1) / 2, half_rb = ((size_t)nrg * NB + 1) / 2;
     // region used in turn by the monomials (point phases 1, 2, 4) and by A, the
     // summed Grams and the solve buffers (reduction to solve); A at offset 0
     // (the binary32 sweep buffers of the solve reuse the summed Grams, dead after the congruence)
@@ -850,18 +873,18 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
     size_t pd = 0;
     for (const auto& m : facet_mix)
       pd = std::max(pd, (m[2] > 0 || m[3] > 0 ? (size_t)m[0] * nb * m[0] * nb : 0) +
-                            (m[1] > 0 ? (size_t)m[0] * (n + 1) * (npair + (size_t)ctx->nrhs * nb) : 0) +
-                            (m[3] > 0 ? (size_t)ctx->nrhs * m[0] * nb : 0));
-    const size_t solve_part = NB * NB + sg_al + (size_t)ctx->nrhs * NB + half_rb;
+                            (m[1] > 0 ? (size_t)m[0] * (n + 1) * (npair + (size_t)nrg * nb) : 0) +
+                            (m[3] > 0 ? (size_t)nrg * m[0] * nb : 0));
+    const size_t solve_part = NB * NB + sg_al + (size_t)nrg * NB + half_rb;
     const size_t mono_part = (size_t)2 * CH * a.mono_stride;
     a.off_mono = 0;
     take(nullptr, NB * NB);                        // A
     a.off_al = (int)off;                           // two binary32 N x N sweep buffers
     take(&a.off_sg, sg_al);
-    take(&a.off_x, (size_t)ctx->nrhs * NB);
+    take(&a.off_x, (size_t)nrg * NB);
     take(&a.off_z, half_rb);
     off = std::max(solve_part, mono_part);
-    take(&a.off_b, (size_t)ctx->nrhs * NB);
+    take(&a.off_b, (size_t)nrg * NB);
     take(&a.off_pg, (size_t)ngmax * npair);        // G, H_m, Gbot contiguous
     take(&a.off_ph, (size_t)ngmax * n * npair);
     take(&a.off_pgb, (size_t)ngmax * npair);
@@ -871,11 +894,11 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
     take(&a.off_f, npair);
     take(&a.off_f2, npair);
     take(&a.off_fpm, (size_t)nb * nb);
-    take(&a.off_del, (size_t)ctx->nrhs * nb);
+    take(&a.off_del, (size_t)nrg * nb);
     take(&a.off_u, (size_t)2 * CH * nb);
     take(&a.off_pt, (size_t)2 * CH * (n + 2));
-    take(&a.off_cb, (size_t)CH * ctx->nrhs * C);
-    take(&a.off_gd, (size_t)CH * ctx->nrhs);
+    take(&a.off_cb, (size_t)CH * nrg * C);
+    take(&a.off_gd, (size_t)CH * nrg);
     take(&a.off_rd, NB);
     take(&a.off_eq, half_nb);
     take(&a.off_keep, (size_t)keep * nb);          // top U-values of the CTA's slice, kept for the outflow
@@ -886,13 +909,18 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
   size_t bytes = 0, cap_used = 0;
   size_t max_dyn = 0;
   if ((rc = max_dyn_smem(n, &max_dyn)) != TP_OK) return fail(rc);
-  for (size_t cap : {kTwoPerSmSmem, max_dyn}) {
-    for (int ch : {48, 32, 16, 8})
-      if (CH == 0 && plan(ch, 0) <= cap) CH = ch;
-    if (CH) {
-      cap_used = cap;
-      break;
+  // the most right-hand sides per group (a divisor of nrhs) whose plan fits
+  for (nrg = ctx->nrhs; nrg >= 1 && CH == 0; --nrg) {
+    if (ctx->nrhs % nrg) continue;
+    for (size_t cap : {kTwoPerSmSmem, max_dyn}) {
+      for (int ch : {48, 32, 16, 8})
+        if (CH == 0 && plan(ch, 0) <= cap) CH = ch;
+      if (CH) {
+        cap_used = cap;
+        break;
+      }
     }
+    if (CH) break;
   }
   if (CH == 0) {
     tp::set_error("tp_create: shared-memory plan does not fit (nb/nrhs too large)");
@@ -906,6 +934,13 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
   bytes = plan(CH, keep);
   a.CH = CH;
   a.keep_pts = keep;
+  a.nrhs = nrg;
+  ctx->nrhs_g = nrg;
+  ctx->rhs_groups = ctx->nrhs / nrg;
+  if (ctx->rhs_groups > 1 && cudaMalloc(&ctx->d_tau_save, T.nv * sizeof(double)) != cudaSuccess) {
+    tp::set_error("tp_create: out of device memory");
+    return fail(TP_ERR_OOM);
+  }
   ctx->args_adj = a;
   ctx->args_adj.front = ctx->d_adj;
   ctx->args_adj.tau = ctx->d_tau_adj;
@@ -1063,24 +1098,40 @@ extern "C" int tp_advance(tp_ctx* ctx, int32_t level_begin, int32_t level_end, v
     cudaGraph_t g = nullptr;
     TP_CUDA_OK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
     int rc = TP_OK;
-    if (ctx->persistent) {
-      const int t_begin = (int)ctx->level_ptr[level_begin - 1], t_end = (int)ctx->level_ptr[level_end - 1];
-      KArgs a = ctx->args;
-      a.tent_end = t_end;
-      cudaError_t e = cudaMemsetAsync(ctx->d_done, 0, ctx->nv * sizeof(int), ctx->cap_stream);
-      if (e == cudaSuccess) {
-        k_sweep_setup<<<std::max(1, std::min(1024, (t_begin + 255) / 256)), 256, 0, ctx->cap_stream>>>(
-            ctx->args.tent_v, t_begin, ctx->persist_cs, ctx->d_done, ctx->d_queue);
-        e = cudaGetLastError();
-      }
-      if (e == cudaSuccess)
-        e = launch_layer(ctx, a, ctx->persist_clusters, ctx->persist_cs, 0, ctx->cap_stream, ctx->mixed ? 1 : 0, true);
-      if (e != cudaSuccess) {
-        tp::set_error(std::string("tp_advance: CUDA error ") + cudaGetErrorString(e));
+    // right-hand-side groups one after the other, each from the front times
+    // at the start of the range
+    const size_t tau_bytes = ctx->nv * sizeof(double);
+    cudaError_t e0 = cudaSuccess;
+    if (ctx->rhs_groups > 1)
+      e0 = cudaMemcpyAsync(ctx->d_tau_save, ctx->d_tau, tau_bytes, cudaMemcpyDeviceToDevice, ctx->cap_stream);
+    for (int k = 0; k < ctx->rhs_groups && rc == TP_OK; ++k) {
+      if (k > 0 && e0 == cudaSuccess)
+        e0 = cudaMemcpyAsync(ctx->d_tau, ctx->d_tau_save, tau_bytes, cudaMemcpyDeviceToDevice, ctx->cap_stream);
+      if (e0 != cudaSuccess) {
+        tp::set_error(std::string("tp_advance: CUDA error ") + cudaGetErrorString(e0));
         rc = TP_ERR_CUDA;
+        break;
       }
-    } else {
-      for (int32_t L = level_begin; L < level_end && rc == TP_OK; ++L) rc = launch_level(ctx, L, ctx->cap_stream);
+      if (ctx->persistent) {
+        const int t_begin = (int)ctx->level_ptr[level_begin - 1], t_end = (int)ctx->level_ptr[level_end - 1];
+        KArgs a = group_args(ctx, ctx->args, k);
+        a.tent_end = t_end;
+        cudaError_t e = cudaMemsetAsync(ctx->d_done, 0, ctx->nv * sizeof(int), ctx->cap_stream);
+        if (e == cudaSuccess) {
+          k_sweep_setup<<<std::max(1, std::min(1024, (t_begin + 255) / 256)), 256, 0, ctx->cap_stream>>>(
+              ctx->args.tent_v, t_begin, ctx->persist_cs, ctx->d_done, ctx->d_queue);
+          e = cudaGetLastError();
+        }
+        if (e == cudaSuccess)
+          e = launch_layer(ctx, a, ctx->persist_clusters, ctx->persist_cs, 0, ctx->cap_stream, ctx->mixed ? 1 : 0, true);
+        if (e != cudaSuccess) {
+          tp::set_error(std::string("tp_advance: CUDA error ") + cudaGetErrorString(e));
+          rc = TP_ERR_CUDA;
+        }
+      } else {
+        for (int32_t L = level_begin; L < level_end && rc == TP_OK; ++L)
+          rc = launch_level(ctx, L, ctx->cap_stream, false, k);
+      }
     }
     cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &g);
     if (rc != TP_OK) {
@@ -1122,7 +1173,14 @@ extern "C" int tp_adjoint(tp_ctx* ctx, const double* d_lambda_T, double* d_lambd
       cudaGraph_t g = nullptr;
       TP_CUDA_OK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
       int rc = TP_OK;
-      for (int32_t L = ctx->n_levels; L >= 1 && rc == TP_OK; --L) rc = launch_level(ctx, L, ctx->cap_stream, true);
+      for (int k = 0; k < ctx->rhs_groups && rc == TP_OK; ++k) {   // groups from the final time each
+        if (k > 0) {
+          k_fill<<<(unsigned)std::min<int64_t>(1024, (ctx->nv + 255) / 256), 256, 0, ctx->cap_stream>>>(
+              ctx->d_tau_adj, ctx->nv, ctx->T_final);
+          if (cudaGetLastError() != cudaSuccess) rc = TP_ERR_CUDA;
+        }
+        for (int32_t L = ctx->n_levels; L >= 1 && rc == TP_OK; --L) rc = launch_level(ctx, L, ctx->cap_stream, true, k);
+      }
       cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &g);
       if (rc != TP_OK) {
         if (g) cudaGraphDestroy(g);
@@ -1271,6 +1329,7 @@ extern "C" void tp_destroy_ctx(tp_ctx* ctx) {
   cudaFree(ctx->d_queue);
   cudaFree(ctx->d_done);
   cudaFree(ctx->d_tau_adj);
+  cudaFree(ctx->d_tau_save);
   if (ctx->adj_graph) cudaGraphExecDestroy(ctx->adj_graph);
   cudaFree(ctx->d_status);
   cudaFree(ctx->d_info);

@@ -61,6 +61,27 @@ def test_dot_product_identity_gpu(cuda_device, name):
     assert abs(lhs - rhs) <= 1e-11 * float(torch.linalg.norm(lam) * torch.linalg.norm(Ff))
 
 
+def test_dot_product_identity_rhs_groups(cuda_device):
+    """64 right-hand sides in 3D at p = 3 run as two groups of 32 in both the
+    forward and the reverse sweep: the identity holds for every column."""
+    import torch
+    import paper_1907_02367_gb300 as pkg
+    m = inputs.mesh_cube(2, 0.1, seed=4)
+    s = pkg.Solver(m.coords, m.elems, m.c, 3, 0.1, inputs.pitch_kappa(m), nrhs=64)
+    rng = np.random.default_rng(5)
+    f = torch.tensor(rng.standard_normal(s.front_shape()), device="cuda")
+    lam = torch.tensor(rng.standard_normal(s.front_shape()), device="cuda")
+    s.set_state(f)
+    s.advance()
+    Ff, _ = s.get_state()
+    Fl = s.adjoint(lam)
+    assert s.sync_status() == (0, 0)
+    for r in (0, 31, 40, 63):
+        lhs = float(torch.sum(lam[r] * Ff[r]))
+        rhs = float(torch.sum(Fl[r] * f[r]))
+        assert abs(lhs - rhs) <= 1e-11 * float(torch.linalg.norm(lam[r]) * torch.linalg.norm(Ff[r]))
+
+
 def test_autograd_gradient_finite_differences(cuda_device):
     import torch
     import paper_1907_02367_gb300 as pkg

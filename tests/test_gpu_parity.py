@@ -323,6 +323,27 @@ def test_many_rhs_3d(cuda_device, precision, tol):
         assert _rel(got[r], ref) <= tol, r
 
 
+@pytest.mark.parametrize("precision,tol,schedule", [("fp64", TOL, "dataflow"), ("mixed", MIXED_TOL, "dataflow"),
+                                                     ("fp64", TOL, "levels")])
+def test_many_rhs_3d_in_groups(cuda_device, precision, tol, schedule):
+    """Sixty-four Gaussian pulses in 3D at p = 3: more right-hand sides than
+    one CTA's shared memory holds, so the library sweeps them in two groups
+    of 32 from the same front times; columns of both groups against the
+    oracle, and the front times after the sweep are the pitched ones."""
+    m = inputs.mesh_cube(2, 0.1, seed=4)
+    kappa = inputs.pitch_kappa(m)
+    rng = np.random.default_rng(44)
+    inits = [inputs.gaussian_pulse(rng.uniform(0.25, 0.75, 3), rng.uniform(0.15, 0.3)) for _ in range(64)]
+    s, got, tau, st = _gpu_run(m, 3, 0.1, kappa, None, None, nrhs_inits=inits, precision=precision,
+                               schedule=schedule)
+    assert st == (0, 0)
+    got = got.reshape(len(inits), m.n_elem, -1, 5)
+    for r in (0, 31, 32, 63):
+        ref, tau_ref, _ = _oracle(m, 3, 0.1, kappa, inits[r], None)
+        assert _rel(got[r], ref) <= tol, r
+    assert np.array_equal(tau, tau_ref)
+
+
 def test_autotune_keeps_results(cuda_device):
     """tp_autotune restores the state it found and the schedule it picks
     reproduces the oracle."""
