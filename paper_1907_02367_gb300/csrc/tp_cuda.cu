@@ -457,10 +457,9 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
   // device uploads
   int rc = TP_OK;
   KArgs& a = ctx->args;
-  double *dX, *dc, *dnrm, *dbary, *dw, *dsqw, *dttop, *dh, *dspc;
-  int *del, *dsp, *dse, *dvp, *dvf, *dfv, *dtv, *dspp, *dspm, *dpar, *dvar, *drp, *drs, *dtp, *dtd;
-  int *dfe, *dip, *div, *dikp, *dikm, *ddp, *ddv, *ddn, *dqt;
-  double* dinrm;
+  double *dX, *dc, *dbary, *dw, *dsqw, *dttop, *dspc;
+  int *del, *dtv, *dspp, *dspm, *dpar, *dvar, *drp, *drs, *dtp, *dtd;
+  int *ddp, *ddv, *ddn, *dqt;
   double *drf, *dtf;
   float2* dcdd;
   float *drff, *dtff;
@@ -658,25 +657,14 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
   if ((rc = ctx_upload(ctx, &dthdr, tent_hdr)) || (rc = ctx_upload(ctx, &dreci, rec_i)) ||
       (rc = ctx_upload(ctx, &drecd, rec_d)) || (rc = ctx_upload(ctx, &dtih, tent_ih)))
     return fail(rc);
-  int *dsso = nullptr, *dsgr = nullptr, *dvng = nullptr;
-  double* dvgc = nullptr;
-  if ((rc = ctx_upload(ctx, &dsso, star_sorted)) || (rc = ctx_upload(ctx, &dsgr, star_grp)) ||
-      (rc = ctx_upload(ctx, &dvng, vert_ng)) || (rc = ctx_upload(ctx, &dvgc, vert_gc)))
-    return fail(rc);
   if ((rc = ctx_upload(ctx, &dX, T.X)) || (rc = ctx_upload(ctx, &dc, T.c)) ||
-      (rc = ctx_upload(ctx, &del, T.elems)) || (rc = ctx_upload(ctx, &dsp, T.star_ptr)) ||
-      (rc = ctx_upload(ctx, &dse, T.star_el)) || (rc = ctx_upload(ctx, &dvp, T.vfac_ptr)) ||
-      (rc = ctx_upload(ctx, &dvf, T.vfac)) || (rc = ctx_upload(ctx, &dfv, T.facet_vert)) ||
-      (rc = ctx_upload(ctx, &dnrm, T.facet_nrm)) || (rc = ctx_upload(ctx, &dbary, ctx->rule.bary)) ||
-      (rc = ctx_upload(ctx, &dfe, T.facet_elem)) || (rc = ctx_upload(ctx, &dip, T.ifac_ptr)) ||
-      (rc = ctx_upload(ctx, &div, T.ifac_vert)) || (rc = ctx_upload(ctx, &dinrm, T.ifac_nrm)) ||
-      (rc = ctx_upload(ctx, &dikp, T.ifac_kp)) || (rc = ctx_upload(ctx, &dikm, T.ifac_km)) ||
+      (rc = ctx_upload(ctx, &del, T.elems)) || (rc = ctx_upload(ctx, &dbary, ctx->rule.bary)) ||
       (rc = ctx_upload(ctx, &ddp, dep_ptr)) || (rc = ctx_upload(ctx, &ddv, dep_vert)) ||
       (rc = ctx_upload(ctx, &ddn, dep_need)) || (rc = ctx_upload(ctx, &dqt, queue_tent)) ||
       (rc = ctx_upload(ctx, &dw, ctx->rule.w)) || (rc = ctx_upload(ctx, &dsqw, sqw)) ||
       (rc = ctx_upload(ctx, &dtv, tv)) || (rc = ctx_upload(ctx, &dttop, ttop)) ||
       (rc = ctx_upload(ctx, &dtbot, tbot)) ||
-      (rc = ctx_upload(ctx, &dh, tent_h)) || (rc = ctx_upload(ctx, &dgo, gdoff)) ||
+      (rc = ctx_upload(ctx, &dgo, gdoff)) ||
       (rc = ctx_upload(ctx, &dspp, basis->sp_ptr)) || (rc = ctx_upload(ctx, &dspm, basis->sp_mono)) ||
       (rc = ctx_upload(ctx, &dspc, basis->sp_coef)) || (rc = ctx_upload(ctx, &dpar, basis->parent)) ||
       (rc = ctx_upload(ctx, &dvar, basis->var)) || (rc = ctx_upload(ctx, &drp, basis->rel_ptr)) ||
@@ -765,12 +753,6 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
   a.alpha = ctx->alpha;
   a.beta = prm->beta;
   a.ngmax = ngmax;
-  a.facet_elem = dfe;
-  a.ifac_ptr = dip;
-  a.ifac_vert = div;
-  a.ifac_nrm = dinrm;
-  a.ifac_kp = dikp;
-  a.ifac_km = dikm;
   a.dep_ptr = ddp;
   a.dep_vert = ddv;
   a.dep_need = ddn;
@@ -778,8 +760,6 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
   a.X = dX;
   a.elems = del;
   a.cK = dc;
-  a.star_ptr = dsp;
-  a.star_el = dse;
   a.ft_ptr = dftp;
   a.ft_idx = dfti;
   a.ft_coef = dftc;
@@ -801,21 +781,12 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
   a.elem_sdet = desdet;
   a.elem_isdet = deisdet;
   a.isqw = disqw;
-  a.star_sorted = dsso;
-  a.star_grp = dsgr;
-  a.vert_ng = dvng;
-  a.vert_gc = dvgc;
-  a.vfac_ptr = dvp;
-  a.vfac = dvf;
-  a.facet_vert = dfv;
-  a.facet_nrm = dnrm;
   a.bary = dbary;
   a.wref = dw;
   a.sqw = dsqw;
   a.tent_v = dtv;
   a.tent_ttop = dttop;
   a.tent_tbot = dtbot;
-  a.tent_h = dh;
   a.tent_ih = dtih;
   a.tent_hdr = dthdr;
   a.vrec_i = dreci;

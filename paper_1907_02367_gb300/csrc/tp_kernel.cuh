@@ -45,25 +45,9 @@ struct KArgs {
   const double* X;
   const int* elems;
   const double* cK;
-  const int* star_ptr;
-  const int* star_el;
   const double* elem_einv;    // per element: inverse of the edge matrix e (rows X_i - X_0), dim x dim
   const double* elem_sdet;    // per element: sqrt(|det e|)
   const double* elem_isdet;   // per element: 1 / sqrt(|det e|)
-  const int* star_sorted;     // vertex stars with the elements grouped by wave speed
-  const int* star_grp;        // material group of each entry of star_sorted
-  const int* vert_ng;         // materials (distinct wave speeds) in each vertex star
-  const double* vert_gc;      // their speeds, kMaxGroups per vertex, in order of first appearance
-  const int* vfac_ptr;
-  const int* vfac;
-  const int* facet_vert;
-  const double* facet_nrm;
-  const int* facet_elem;      // element owning each boundary facet
-  const int* ifac_ptr;        // per vertex: time-like interface facets through it (CSR)
-  const int* ifac_vert;       // dim vertex ids per interface facet
-  const double* ifac_nrm;     // unit normal out of the + element
-  const int* ifac_kp;         // + element (lower index of the two)
-  const int* ifac_km;         // - element
   const double* bary;     // Q * (dim+1)
   const double* wref;     // Q
   const double* sqw;      // Q, sqrt(wref)
@@ -71,7 +55,6 @@ struct KArgs {
   const int* tent_v;
   const double* tent_ttop;
   const double* tent_tbot;
-  const double* tent_h;
   const double* tent_ih;      // 1 / h
   const int* tent_hdr;        // per tent: v, record offsets (int, double), elements, Dirichlet and interface facets, materials, Neumann facets
   const int* vrec_i;          // per vertex: star record, ints (elements, facets)
