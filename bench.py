@@ -43,8 +43,8 @@ FP64_PEAK_TFLOPS = 1.25      # nominal GB300 FP64 rate (152 SMs x 2 DFMA/clk x 2
 # DRAM read + write bytes of one binary64 sweep launch of this workload, from the
 # ncu capture summarised in profiles/k_layer_dataflow_standing2d.md, and the
 # kernel source it was taken on
-SWEEP_DRAM_BYTES = 4.995840e6 + 0.165888e6
-SWEEP_DRAM_SOURCE = "ncu capture of k_layer<2,0,0,1,0> at commit 049d31d"
+SWEEP_DRAM_BYTES = 5.153536e6 + 0.393984e6
+SWEEP_DRAM_SOURCE = "ncu capture of k_layer<2,0,0,1,0> at commit d48bde1"
 
 
 def max_over_ranks(x: float, world: int, device: str = "cuda") -> float:
