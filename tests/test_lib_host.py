@@ -90,3 +90,25 @@ def test_argument_errors(libtp):
     assert libtp.tp_pitch_mesh(ct.byref(bad.desc), ct.byref(prm), ct.byref(h)) == B.TP_ERR_ARG
     neg = B._MeshArrays(m.coords, m.elems, -m.c)
     assert libtp.tp_pitch_mesh(ct.byref(neg.desc), ct.byref(prm), ct.byref(h)) == B.TP_ERR_ARG
+
+
+def test_boundary_kind_markers(libtp):
+    """tp_mesh_desc.bnd_type: 0/1 per element face are accepted (entries of
+    interior faces are ignored), any other value of a boundary face is an
+    argument error naming the element; a wrongly shaped marker array is
+    refused by the binding."""
+    h = ct.c_void_p()
+    prm = B.make_params(3, 0.5, 0.9)
+    m = inputs.mesh_square(3, 0.2, seed=5)
+    ok = inputs.boundary_marker(m, lambda x: x[0] < 1e-12)
+    arrs = B._MeshArrays(m.coords, m.elems, m.c, ok)
+    assert libtp.tp_pitch_mesh(ct.byref(arrs.desc), ct.byref(prm), ct.byref(h)) == B.TP_OK
+    libtp.tp_destroy_tents(h)
+    bad = ok.copy()
+    k, o = np.argwhere(inputs.boundary_marker(m, lambda x: True) == 1)[0]
+    bad[k, o] = 2
+    arrs = B._MeshArrays(m.coords, m.elems, m.c, bad)
+    assert libtp.tp_pitch_mesh(ct.byref(arrs.desc), ct.byref(prm), ct.byref(h)) == B.TP_ERR_ARG
+    assert b"bnd_type" in libtp.tp_last_error()
+    with pytest.raises(ValueError):
+        B._MeshArrays(m.coords, m.elems, m.c, ok[:, :2])
