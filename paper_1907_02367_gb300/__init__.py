@@ -90,11 +90,18 @@ def build_basis(dim, p) -> Basis:
 class Solver:
     """A tp_ctx: device-resident mesh, tents, tables and front state.
 
-    precision "fp64": every step in binary64.  "mixed": assembly, residual
-    and outflow in float-float on the binary32 pipes, binary32 factorisation
-    of the equilibrated local matrix, iterative refinement.  All device
-    memory handed to libtp is torch CUDA float64 memory; the current torch
-    stream is passed to every call."""
+    precision "fp64": assembly, residual and outflow in binary64.  "mixed":
+    the same in float-float on the binary32 pipes.  Both invert the
+    equilibrated local matrix in binary32 and refine the solution in their
+    own precision (a direct binary64 LU where the refinement does not settle).
+    alpha, beta: the penalties of eq. (2.5) (Dirichlet, interface and Neumann
+    facets).  bnd_type: optional (n_elem, dim+1) array, 1 marks the boundary
+    facet opposite local vertex o of element k as Neumann (sigma.n = g_N),
+    else Dirichlet; boundary_kinds() tells which data each boundary point
+    takes.  nrhs right-hand sides share the tents and their matrices (in
+    groups when one CTA cannot hold all of them).  All device memory handed
+    to libtp is torch CUDA float64 memory; the current torch stream is
+    passed to every call."""
 
     def __init__(self, coords, elems, c, p: int, T: float, kappa: float, alpha: float = 0.5,
                  nrhs: int = 1, tents: Tents | None = None, precision: str = "fp64",
