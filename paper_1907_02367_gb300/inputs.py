@@ -133,6 +133,63 @@ def mesh_square(nx: int, jitter: float = 0.2, seed: int = 2, c: float = 1.0) -> 
                 meta={"h": h, "seed": seed, "jitter": jitter})
 
 
+def mesh_inclusion_graded(h_max: float = 0.015, ratio: float = 10.0, growth: float = 1.25,
+                          radius: float = 0.2, center=(0.5, 0.5), seed: int = 3,
+                          c_in: float = 3.0, c_out: float = 1.0) -> Mesh:
+    """Unit square graded `ratio` times finer around a circular inclusion.
+
+    Points: the circle |x - center| = radius at spacing h_min = h_max / ratio;
+    rings inside and outside it whose spacing grows by `growth` per ring up
+    to h_max (each ring rotated by a seeded phase); a jittered grid of
+    spacing h_max beyond the rings and on the square's boundary.  Their
+    Delaunay triangulation (counter-clockwise triangles); c = c_in on the
+    triangles whose centroid lies inside the circle, c_out elsewhere, so the
+    jump of c follows element edges.  h_max = 0.015 gives about 21 000
+    triangles."""
+    from scipy.spatial import Delaunay
+    rng = np.random.default_rng(seed)
+    cx, cy = float(center[0]), float(center[1])
+    h_min = h_max / ratio
+    pts = []
+
+    def ring(rad, sp):
+        n = max(3, int(math.ceil(2.0 * math.pi * rad / sp)))
+        a = rng.uniform(0.0, 2.0 * math.pi / n) + 2.0 * math.pi * np.arange(n) / n
+        return np.stack([cx + rad * np.cos(a), cy + rad * np.sin(a)], axis=1)
+
+    pts.append(ring(radius, h_min))
+    sp, rad = h_min, radius
+    while sp < h_max:                       # outward rings
+        sp = min(h_max, sp * growth)
+        rad += sp
+        pts.append(ring(rad, sp))
+    band = rad - radius
+    sp, rad = h_min, radius
+    while True:                             # inward rings down to the centre
+        sp = min(h_max, sp * growth)
+        rad -= sp
+        if rad < sp:
+            break
+        pts.append(ring(rad, sp))
+    pts.append(np.array([[cx, cy]]))
+    n = int(round(1.0 / h_max))
+    h = 1.0 / n
+    g = np.array([[i * h, j * h] for j in range(n + 1) for i in range(n + 1)], dtype=np.float64)
+    interior = (g[:, 0] > 0) & (g[:, 0] < 1) & (g[:, 1] > 0) & (g[:, 1] < 1)
+    g[interior] += rng.uniform(-0.2 * h, 0.2 * h, size=g[interior].shape)
+    d = np.hypot(g[:, 0] - cx, g[:, 1] - cy)
+    pts.append(g[(d > radius + band + 0.5 * h) | ~interior])
+    P = np.ascontiguousarray(np.concatenate(pts), dtype=np.float64)
+    tris = Delaunay(P).simplices.astype(np.int32)
+    for t in tris:
+        if _orient2(P[t[0]], P[t[1]], P[t[2]]) < 0:
+            t[1], t[2] = t[2], t[1]
+    cen = P[tris].mean(axis=1)
+    c = np.where(np.hypot(cen[:, 0] - cx, cen[:, 1] - cy) < radius, c_in, c_out).astype(np.float64)
+    return Mesh(P, tris, c, name="inclusion_graded",
+                meta={"h_max": h_max, "h_min": h_min, "seed": seed, "radius": radius})
+
+
 # ----------------------------------------------------------------------------
 # 3D: jittered hex grid, 6 Kuhn tetrahedra per hex
 # ----------------------------------------------------------------------------
@@ -347,6 +404,9 @@ def workload(name: str) -> Workload:
     inclusion_small : unit square 8x8 jittered grid (128 triangles), c = 3 in the
                    disc |x - (0.5,0.5)| < 0.2 (by element centroid), c = 1 outside,
                    p=3, T=0.15, Gaussian pulse (Section 6.7 shape, small).
+    inclusion_graded: the same inclusion on about 21 000 triangles graded 10x
+                   finer around the circle (mesh_inclusion_graded), p=5, T=2,
+                   Gaussian pulse of width 0.05 at a seeded centre.
     """
     if name == "plane1d":
         m = mesh_interval(16)
@@ -370,6 +430,11 @@ def workload(name: str) -> Workload:
         m.c[:] = np.where(np.linalg.norm(cen - 0.5, axis=1) < 0.2, 3.0, 1.0)
         pulse = gaussian_pulse((0.42, 0.55), 0.15)
         return Workload(name, m, 3, 0.15, pitch_kappa(m), None, pulse, None)
+    if name == "inclusion_graded":
+        m = mesh_inclusion_graded()
+        rng = np.random.default_rng(17)
+        pulse = gaussian_pulse(rng.uniform(0.3, 0.7, 2), 0.05)
+        return Workload(name, m, 5, 2.0, pitch_kappa(m), None, pulse, None)
     raise KeyError(name)
 
 
