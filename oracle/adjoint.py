@@ -131,3 +131,27 @@ def misfit_gradient(front_T, obs_T, wq):
     g = np.zeros_like(front_T)
     g[:, :, 0] = wq * d
     return J, g
+
+
+def speed_gradient(coords, elems, c, p, tents, init, lam_T, rel_step=1e-6, **sweep_kw):
+    """Gradient of J(c) = <lam_T, front_T(c)> with respect to the wave speed
+    of each material (the distinct values of c, every element of a material
+    moving together), the pitched tents held fixed: central differences of
+    the oracle's own sweep, dJ/dc_m ~ (J(c_m (1 + s)) - J(c_m (1 - s))) /
+    (2 s c_m) with s = rel_step.  The paper has no gradient; this is the
+    definition of the derivative written out (truncation O(s^2), rounding
+    O(u / s)).  sweep_kw goes to oracle.tdg.sweep (boundary data and kinds).
+    Returns (speeds (M,), dJ/dc (M,))."""
+    c = np.asarray(c, dtype=np.float64)
+    speeds = np.unique(c)
+    grad = np.zeros(len(speeds))
+    lam = np.asarray(lam_T, dtype=np.float64)
+    for m, cm in enumerate(speeds):
+        J = []
+        for sgn in (1.0, -1.0):
+            cp = c.copy()
+            cp[c == cm] = cm * (1.0 + sgn * rel_step)
+            F, _ = _tdg.sweep(coords, elems, cp, p, tents, init, **sweep_kw)
+            J.append(float(np.sum(lam.reshape(F.shape) * F)))
+        grad[m] = (J[0] - J[1]) / (2.0 * rel_step * cm)
+    return speeds, grad

@@ -58,3 +58,58 @@ def test_misfit_gradient_finite_differences():
     fd = (J(f0 + eps * d)[0] - J(f0 - eps * d)[0]) / (2 * eps)
     an = float(np.sum(g0 * d))
     assert abs(fd - an) <= 1e-6 * max(abs(an), 1e-12)
+
+
+def test_speed_gradient_closed_form():
+    """U = x^2 + c^2 t^2 on [0, 1] (v = 2 c^2 t, sigma = -2x) has initial data
+    U0 = x^2, v0 = 0, sigma0 = -2x and Neumann data sigma.n = 0 at x = 0, -2
+    at x = 1, none of which depend on c; at p >= 2 the sweep reproduces it for
+    every c, so J(c) = sum lam . (x^2 + c^2 T^2, 2 c^2 T, -2x) and
+    dJ/dc = sum 2 c T^2 lam_U + 4 c T lam_v exactly."""
+    mesh = inputs.mesh_interval(5)
+    cval, T, p = 1.3, 0.4, 3
+    mesh.c[:] = cval
+    marker = inputs.boundary_marker(mesh, lambda x: True)
+    r = pitching.pitch(mesh.coords, mesh.elems, mesh.c, inputs.pitch_kappa(mesh), T)
+
+    def init(x):
+        x = np.asarray(x).reshape(-1)
+        return np.stack([x * x, 0.0 * x, -2.0 * x], axis=1)
+
+    def neumann(x, t, nrm):
+        return -2.0 * np.asarray(x)[:, 0] * float(nrm[0])
+
+    lay = tdg.front_layout(mesh.coords, mesh.elems, p)
+    rng = np.random.default_rng(8)
+    lam = rng.standard_normal((mesh.n_elem, lay.wq.shape[1], 3))
+    speeds, g = adjoint.speed_gradient(mesh.coords, mesh.elems, mesh.c, p, r, init, lam,
+                                       bnd_type=marker, neumann=neumann)
+    exact = np.sum(2.0 * cval * T * T * lam[..., 0] + 4.0 * cval * T * lam[..., 1])
+    assert speeds.tolist() == [cval]
+    assert abs(g[0] - exact) <= 1e-7 * max(1.0, abs(exact))
+
+
+def test_speed_gradient_two_materials_matches_swept_difference():
+    """Two materials: each component equals the slope of J along that
+    material's speed alone over a wider step (a second, independent
+    difference), and the components differ (each material moves alone)."""
+    mesh = inputs.mesh_interval(6)
+    cen = mesh.coords[mesh.elems].mean(axis=1)[:, 0]
+    mesh.c[:] = np.where(cen > 0.5, 2.0, 1.0)
+    p, T = 3, 0.2
+    r = pitching.pitch(mesh.coords, mesh.elems, mesh.c, inputs.pitch_kappa(mesh), T)
+    pulse = inputs.gaussian_pulse(np.array([0.4]), 0.15)
+    lay = tdg.front_layout(mesh.coords, mesh.elems, p)
+    lam = np.random.default_rng(3).standard_normal((mesh.n_elem, lay.wq.shape[1], 3))
+    speeds, g = adjoint.speed_gradient(mesh.coords, mesh.elems, mesh.c, p, r, pulse, lam)
+    assert speeds.tolist() == [1.0, 2.0]
+    for m, cm in enumerate(speeds):
+        J = []
+        for d in (1e-4, -1e-4):
+            cp = mesh.c.copy()
+            cp[mesh.c == cm] = cm + d
+            F, _ = tdg.sweep(mesh.coords, mesh.elems, cp, p, r, pulse)
+            J.append(float(np.sum(lam.reshape(F.shape) * F)))
+        slope = (J[0] - J[1]) / 2e-4
+        assert abs(g[m] - slope) <= 1e-6 * max(1.0, abs(slope)), (m, g[m], slope)
+    assert abs(g[0] - g[1]) > 1e-6 * max(abs(g[0]), abs(g[1]))
