@@ -112,3 +112,22 @@ def test_boundary_kind_markers(libtp):
     assert b"bnd_type" in libtp.tp_last_error()
     with pytest.raises(ValueError):
         B._MeshArrays(m.coords, m.elems, m.c, ok[:, :2])
+
+
+def test_no_cpu_fallback(libtp, tmp_path):
+    """The product path fails loudly without a GPU or without the built
+    library: the Solver refuses to run on a machine without CUDA (this test
+    only runs there), and loading a library that was not built raises."""
+    import torch
+    import paper_1907_02367_gb300 as pkg
+    if not torch.cuda.is_available():
+        m = inputs.mesh_interval(4)
+        with pytest.raises(RuntimeError, match="CUDA"):
+            pkg.Solver(m.coords, m.elems, m.c, 3, 0.5, 0.9)
+    saved = B._lib
+    try:
+        B._lib = None
+        with pytest.raises(OSError, match="not built"):
+            B.load(str(tmp_path / "missing_libtp.so"))
+    finally:
+        B._lib = saved
