@@ -73,6 +73,8 @@ ADJ_PINS = [
     lambda: Az.test_dot_product_identity(1),
     lambda: Az.test_dot_product_identity(2),
     lambda: Az.test_misfit_gradient_finite_differences(),
+    lambda: Az.test_speed_gradient_closed_form(),
+    lambda: Az.test_speed_gradient_two_materials_matches_swept_difference(),
 ]
 
 # (id, oracle module, original text, planted text)
@@ -106,6 +108,10 @@ MUTATIONS = [
     ("adjoint-untransposed-solve", "adjoint", "mu = np.linalg.solve(A.T, Em.T @ lt)",
      "mu = np.linalg.solve(A, Em.T @ lt)"),
     ("adjoint-bottom-sign", "adjoint", "(w[:, None] * (c2 * Vb - Sgb)).T", "(w[:, None] * (c2 * Vb + Sgb)).T"),
+    ("adjoint-speed-step-not-relative", "adjoint", "(2.0 * rel_step * cm)", "(2.0 * rel_step)"),
+    ("adjoint-speed-moves-every-material", "adjoint", "cp[c == cm] = cm * (1.0 + sgn * rel_step)",
+     "cp[:] = c * (1.0 + sgn * rel_step)"),
+    ("adjoint-speed-one-sided", "adjoint", "(J[0] - J[1]) / (2.0", "(J[0] - J[1]) / (1.0"),
 ]
 
 
