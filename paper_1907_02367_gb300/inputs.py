@@ -13,6 +13,8 @@ Workloads (Section 6 of the paper; sizes as stated in each generator):
     standing wave cos(sqrt2 pi t) sin(pi x) sin(pi y)  (Section 6.4 shape).
   * 3+1D: unit cube, jittered hex grid, six Kuhn tetrahedra per hex,
     Gaussian pulses with v0 = 0.
+  * 2+1D L-shape (Section 6.6): uniform and corner-graded meshes of
+    [-1,1]^2 minus [0,1]x[-1,0], singular solution cos(10t) sin(2phi/3) J_2/3(10r).
 """
 from __future__ import annotations
 
@@ -190,6 +192,104 @@ def mesh_inclusion_graded(h_max: float = 0.015, ratio: float = 10.0, growth: flo
                 meta={"h_max": h_max, "h_min": h_min, "seed": seed, "radius": radius})
 
 
+def _ring_polyline(s: float, h: float):
+    """The part of the square |x|_inf = s inside the L-shape (Section 6.6):
+    four straight pieces from (0,-s) over (-s,-s), (-s,s), (s,s) to (s,0),
+    each cut into pieces of length <= h.  Returns a list of four point
+    arrays, consecutive pieces sharing their end point."""
+    corners = [(0.0, -s), (-s, -s), (-s, s), (s, s), (s, 0.0)]
+    out = []
+    for (ax, ay), (bx, by) in zip(corners[:-1], corners[1:]):
+        m = max(1, int(math.ceil(math.hypot(bx - ax, by - ay) / h - 1e-9)))
+        u = np.arange(m + 1) / m
+        out.append(np.stack([ax + u * (bx - ax), ay + u * (by - ay)], axis=1))
+    return out
+
+
+def mesh_lshape(h_max: float, mu: float = 1.0 / 3.0, c: float = 1.0) -> Mesh:
+    """The L-shaped domain [-1,1]^2 minus [0,1]x[-1,0] of Section 6.6, its
+    reentrant corner at the origin, meshed with local size
+    h(r) = max(h_max r^(1-mu), h_min), h_min = h_max^(1/mu) (the paper's
+    grading law; mu = 1 gives a uniform mesh of size h_max).
+
+    Vertices lie on the squares |x|_inf = s_k around the corner, s_0 = 0
+    (the corner itself) < s_1 < ... < s_K = 1 (the outer boundary), with
+    s_{k+1} - s_k = h(s_k) (graded) or 1/ceil(1/h_max) (uniform), the whole
+    sequence scaled so that s_K = 1; on each square the spacing is at most
+    h(s_k).  Uniform: a fan from the corner to the first square, then
+    between consecutive squares a strip over each of the four straight
+    pieces, zipped by matching the pieces' normalised arc lengths (the
+    pieces of two squares are parallel and seen from the corner under the
+    same angles, so every strip triangle lies in a convex trapezoid): 6 n^2
+    right isosceles triangles.  Graded: the Delaunay triangulation of the
+    same points with the triangles inside the cut-out quadrant dropped
+    (consecutive points on the two cut edges are Gabriel edges, so the
+    triangulation keeps them); it avoids the flat triangles that strips
+    leave at the squares' corners where s grows fast near the origin.
+    Counter-clockwise triangles; no random numbers."""
+    if mu >= 1.0:
+        n = int(math.ceil(1.0 / h_max - 1e-9))
+        s = np.arange(n + 1) / n
+        h_min = 1.0 / n
+        sizes = np.full(n + 1, 1.0 / n)
+    else:
+        h_min = h_max ** (1.0 / mu)
+        seq = [0.0, h_min]
+        while seq[-1] < 1.0:
+            seq.append(seq[-1] + max(h_max * seq[-1] ** (1.0 - mu), h_min))
+        s = np.array(seq) / seq[-1]
+        sizes = np.maximum(h_max * s ** (1.0 - mu), h_min)
+    s[-1] = 1.0
+    pts = [np.zeros((1, 2))]
+    rings = []                     # per square: four arrays of vertex ids
+    nv = 1
+    for k in range(1, len(s)):
+        pieces = _ring_polyline(float(s[k]), float(sizes[k]))
+        ids, flat = [], []
+        for j, pc in enumerate(pieces):
+            start = nv if j == 0 else ids[-1][-1]
+            new = pc if j == 0 else pc[1:]
+            idx = np.arange(nv, nv + len(new))
+            ids.append(idx if j == 0 else np.concatenate([[start], idx]))
+            flat.append(new)
+            nv += len(new)
+        pts.append(np.concatenate(flat))
+        rings.append(ids)
+    P = np.ascontiguousarray(np.concatenate(pts), dtype=np.float64)
+    P[np.abs(P) < 1e-15] = 0.0
+    if mu < 1.0:
+        from scipy.spatial import Delaunay
+        tris = Delaunay(P).simplices.astype(np.int32)
+        cen = P[tris].mean(axis=1)
+        tris = np.ascontiguousarray(tris[~((cen[:, 0] > 0.0) & (cen[:, 1] < 0.0))])
+        for t in tris:
+            if _orient2(P[t[0]], P[t[1]], P[t[2]]) < 0:
+                t[1], t[2] = t[2], t[1]
+        return Mesh(P, tris, np.full(len(tris), c, dtype=np.float64), name="lshape_graded",
+                    meta={"h_max": h_max, "h_min": h_min, "mu": mu, "n_squares": len(s) - 1})
+    tris = []
+    for piece in rings[0]:
+        for a, b in zip(piece[:-1], piece[1:]):
+            tris.append([0, int(a), int(b)])
+    for inner, outer in zip(rings[:-1], rings[1:]):
+        for pi, po in zip(inner, outer):
+            mi, mo = len(pi) - 1, len(po) - 1
+            i = j = 0
+            while i < mi or j < mo:
+                if j == mo or (i < mi and (i + 1) * mo <= (j + 1) * mi):
+                    tris.append([int(pi[i]), int(pi[i + 1]), int(po[j])])
+                    i += 1
+                else:
+                    tris.append([int(pi[i]), int(po[j + 1]), int(po[j])])
+                    j += 1
+    tris = np.array(tris, dtype=np.int32)
+    for t in tris:
+        if _orient2(P[t[0]], P[t[1]], P[t[2]]) < 0:
+            t[1], t[2] = t[2], t[1]
+    return Mesh(P, tris, np.full(len(tris), c, dtype=np.float64), name="lshape_uniform",
+                meta={"h_max": h_max, "h_min": h_min, "mu": mu, "n_squares": len(s) - 1})
+
+
 # ----------------------------------------------------------------------------
 # 3D: jittered hex grid, 6 Kuhn tetrahedra per hex
 # ----------------------------------------------------------------------------
@@ -323,6 +423,43 @@ def standing_wave_3d(x: np.ndarray, t) -> np.ndarray:
                      -math.pi * ct * co[:, 0] * s[:, 1] * s[:, 2],
                      -math.pi * ct * s[:, 0] * co[:, 1] * s[:, 2],
                      -math.pi * ct * s[:, 0] * s[:, 1] * co[:, 2]], axis=1)
+
+
+def corner_angle(x: np.ndarray) -> np.ndarray:
+    """Polar angle phi in [-pi/4, 7pi/4) about the L-shape's reentrant
+    corner: the cut lies in the middle of the removed quadrant, so the two
+    cut edges sit at phi = 0 and phi = 3pi/2 and points that rounding puts
+    just outside them stay on the right branch."""
+    x = np.asarray(x, dtype=np.float64).reshape(-1, 2)
+    phi = np.arctan2(x[:, 1], x[:, 0])
+    return np.where(phi < -0.25 * math.pi, phi + 2.0 * math.pi, phi)
+
+
+def bessel_corner_solution(a: float = 10.0, nu: float = 2.0 / 3.0):
+    """U(r, phi, t) = cos(a t) sin(nu phi) J_nu(a r), c = 1 (Section 6.6): the
+    singular solution on the L-shape; U = 0 on both cut edges for nu = 2/3,
+    and grad U ~ r^(nu - 1) at the corner.  Returns sol(x, t) -> (N, 4)
+    holding (U, v, sigma_1, sigma_2) with sigma = -(U_r e_r + U_phi / r e_phi).
+    At r = 0 sigma is set to 0 (it is unbounded there; no quadrature point
+    lies at the corner)."""
+    from scipy.special import jv, jvp
+
+    def sol(x: np.ndarray, t) -> np.ndarray:
+        x = np.asarray(x, dtype=np.float64).reshape(-1, 2)
+        t = np.broadcast_to(np.asarray(t, dtype=np.float64), x.shape[:1])
+        r = np.hypot(x[:, 0], x[:, 1])
+        phi = corner_angle(x)
+        J = jv(nu, a * r)
+        s, c = np.sin(nu * phi), np.cos(nu * phi)
+        ct, st = np.cos(a * t), np.sin(a * t)
+        rs = np.where(r > 0.0, r, 1.0)
+        f_r = np.where(r > 0.0, a * jvp(nu, a * rs) * s, 0.0)
+        f_phi_r = np.where(r > 0.0, nu * J * c / rs, 0.0)
+        cp, sp = x[:, 0] / rs, x[:, 1] / rs
+        gx = f_r * cp - f_phi_r * sp
+        gy = f_r * sp + f_phi_r * cp
+        return np.stack([ct * s * J, -a * st * s * J, -ct * gx, -ct * gy], axis=1)
+    return sol
 
 
 def gaussian_pulse(center, delta: float):

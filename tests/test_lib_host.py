@@ -32,6 +32,8 @@ MESHES = [
     ("square5", lambda: inputs.mesh_square(5, 0.2, seed=3), None, 0.7),
     ("square22", lambda: inputs.mesh_square(22, 0.2, seed=2), None, 1.0),
     ("cube2", lambda: inputs.mesh_cube(2, 0.1, seed=4), None, 0.4),
+    ("lshape_uniform8", lambda: inputs.mesh_lshape(0.125, 1.0), None, 1.0),
+    ("lshape_graded035", lambda: inputs.mesh_lshape(0.35, 1.0 / 3.0), None, 1.0),
 ]
 
 
