@@ -398,6 +398,16 @@ def plane_wave_1d(x: np.ndarray, t) -> np.ndarray:
     return np.stack([np.sin(ph), -math.pi * np.cos(ph), -math.pi * np.cos(ph)], axis=1)
 
 
+def sine_product_1d(x: np.ndarray, t) -> np.ndarray:
+    """U = sin(pi x) sin(pi t), c = 1 (Section 6.5): v = 0 at x = 0 and 1, and
+    the energy 1/2 int (v^2 + sigma^2) dx = pi^2 / 4 at every t."""
+    x = np.asarray(x, dtype=np.float64).reshape(-1)
+    t = np.broadcast_to(np.asarray(t, dtype=np.float64), x.shape)
+    sx, cx = np.sin(math.pi * x), np.cos(math.pi * x)
+    st, ct = np.sin(math.pi * t), np.cos(math.pi * t)
+    return np.stack([sx * st, math.pi * sx * ct, -math.pi * cx * st], axis=1)
+
+
 def standing_wave_2d(x: np.ndarray, t) -> np.ndarray:
     """U = cos(sqrt2 pi t) sin(pi x) sin(pi y), c = 1 (v = 0 on the boundary)."""
     x = np.asarray(x, dtype=np.float64).reshape(-1, 2)

@@ -157,3 +157,17 @@ def test_bessel_corner_solution_is_a_wave():
     assert np.abs(sol(cut, 0.37)[:, :2]).max() < 1e-14
     g = [np.linalg.norm(sol(np.array([[-rr, rr]]) / np.sqrt(2), 0.0)[0, 2:]) for rr in (1e-4, 1e-6)]
     assert abs(np.log(g[1] / g[0]) / np.log(1e-2) - (2.0 / 3.0 - 1.0)) < 1e-3
+
+
+def test_sine_product_1d_is_a_wave_with_constant_energy():
+    x = np.linspace(0.0, 1.0, 2001)
+    h = 1e-5
+    for t in (0.0, 0.3, 7.1):
+        F = inputs.sine_product_1d(x, t)
+        U = lambda y, s: inputs.sine_product_1d(y, s)[:, 0]    # noqa: E731
+        assert np.allclose((U(x, t + h) - U(x, t - h)) / (2 * h), F[:, 1], atol=1e-6)
+        assert np.allclose(-(U(x + h, t) - U(x - h, t)) / (2 * h), F[:, 2], atol=1e-6)
+        dens = 0.5 * (F[:, 1] ** 2 + F[:, 2] ** 2)
+        E = float(np.sum(0.5 * (dens[1:] + dens[:-1])) * (x[1] - x[0]))
+        assert abs(E - np.pi ** 2 / 4) < 1e-6
+        assert abs(F[0, 1]) < 1e-15 and abs(F[-1, 1]) < 1e-12

@@ -416,3 +416,21 @@ def test_lshape_bessel_solution_converges():
         err.append(math.sqrt(float(np.sum(lay.wq * (F[..., 0] - ex[..., 0]) ** 2))))
     assert err[1] < err[0] / 3.0, err
     assert err[1] < 0.06, err
+
+
+def test_long_time_energy_dissipation():
+    """Section 6.5: U = sin(pi x) sin(pi t) on 5 elements (energy pi^2/4 at
+    every t).  The numerical energy at T lies below the exact one, the gap
+    grows about linearly in T (doubling T doubles it within 25 %), and it
+    falls by more than 10x per degree from p = 2 to p = 4."""
+    m = inputs.mesh_interval(5)
+    E0 = math.pi ** 2 / 4.0
+    rel = {}
+    for p in (2, 3, 4):
+        for T in (4.0, 8.0):
+            F, _, _, lay, _ = _run(m, p, T, inputs.sine_product_1d, 0.9)
+            rel[p, T] = (E0 - energy.front_energy(F, lay.wq, m.c)) / E0
+    for p in (2, 3, 4):
+        assert rel[p, 4.0] > 0 and rel[p, 8.0] > 0
+        assert 1.5 <= rel[p, 8.0] / rel[p, 4.0] <= 2.5, (p, rel[p, 8.0] / rel[p, 4.0])
+    assert rel[3, 8.0] < rel[2, 8.0] / 10 and rel[4, 8.0] < rel[3, 8.0] / 10
