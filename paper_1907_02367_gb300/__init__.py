@@ -14,7 +14,8 @@ import numpy as np
 
 from . import _binding as B
 
-__all__ = ["Tents", "Basis", "Solver", "TentSweep", "pitch_mesh", "build_basis", "load_library"]
+__all__ = ["Tents", "Basis", "Solver", "TentSweep", "speed_gradient", "pitch_mesh", "build_basis",
+           "load_library"]
 
 
 def load_library():
@@ -266,3 +267,40 @@ class _LazyTentSweep:
 
 
 TentSweep = _LazyTentSweep()
+
+
+def speed_gradient(coords, elems, c, p: int, T: float, kappa: float, front0, lam_T, gD=None,
+                   rel_step: float = 1e-6, **solver_kw):
+    """Gradient of J(c) = <lam_T, front_T(c)> with respect to the wave speed of
+    each material (the distinct values of c, all elements of a material
+    moving together), the tents pitched once with c and held fixed.
+
+    Central differences of two GPU sweeps per material,
+    dJ/dc_m ~ (J(c_m (1 + s)) - J(c_m (1 - s))) / (2 s c_m), s = rel_step:
+    each sweep runs in a context created with the perturbed speeds over the
+    same Tents (tp_create reads the speeds from the mesh and the tent times
+    from the pitched tents).  front0, lam_T: CUDA float64 tensors of
+    front_shape(); gD: boundary data as for Solver.set_state (independent of
+    c: the boundary points depend only on the mesh and the tents).
+    solver_kw goes to Solver (precision, bnd_type, alpha, beta, schedule).
+    Returns (speeds (M,) float64, dJ/dc (M,) float64) as numpy arrays."""
+    import torch
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    tents = Tents(coords, elems, c, kappa, T)
+    speeds = np.unique(c)
+    grad = np.zeros(len(speeds))
+    for m, cm in enumerate(speeds):
+        J = []
+        for sgn in (1.0, -1.0):
+            cp = c.copy()
+            cp[c == cm] = cm * (1.0 + sgn * rel_step)
+            s = Solver(coords, elems, cp, p, T, kappa, tents=tents, **solver_kw)
+            s.set_state(front0, gD)
+            s.advance()
+            F, _ = s.get_state()
+            st = s.sync_status()
+            if st[0] != 0:
+                raise RuntimeError(f"speed_gradient: device status {st[0]} at tent {st[1]}")
+            J.append(float(torch.sum(lam_T * F)))
+        grad[m] = (J[0] - J[1]) / (2.0 * rel_step * cm)
+    return speeds, grad
