@@ -155,3 +155,79 @@ def speed_gradient(coords, elems, c, p, tents, init, lam_T, rel_step=1e-6, **swe
             J.append(float(np.sum(lam.reshape(F.shape) * F)))
         grad[m] = (J[0] - J[1]) / (2.0 * rel_step * cm)
     return speeds, grad
+
+
+def _global_system(coords, elems, c, p, tents, alpha=0.5):
+    """The whole space-time system of the sweep at once (g_D = 0, single-material
+    tents).  Unknowns: the coefficients x_t of every tent, stacked in the
+    pitched order.  Block row t: A_t x_t = B_t f_t, where f_t holds, for each
+    element K of the tent's patch, the front on K just before tent t: the
+    top values E_t' x_t' of the last earlier tent t' over K, or the initial
+    data on K.  Moving the E_t' x_t' terms to the left gives M x = R f_0 with
+    M block lower triangular; the final front is S x + P f_0 (P keeps the
+    initial data on elements no tent touches).
+    Returns (M, R, S, P, nb) as dense arrays."""
+    coords = np.asarray(coords, dtype=np.float64)
+    elems = np.asarray(elems)
+    c = np.asarray(c, dtype=np.float64)
+    n = coords.shape[1]
+    nv, ne = coords.shape[0], elems.shape[0]
+    lay = _tdg.front_layout(coords, elems, p)
+    Bas = _basis.TrefftzBasis(n, p)
+    star = _tdg.vertex_star(elems, nv)
+    vfac = [[] for _ in range(nv)]
+    for (f, nrm, k) in _tdg.boundary_facets(coords, elems):
+        for a in f:
+            vfac[a].append((f, nrm, k))
+    Q = lay.wq.shape[1]
+    C = n + 2
+    blk = Q * C                                     # front values of one element
+    nb = Bas.nb
+    nt = len(tents["vert"])
+    M = np.zeros((nt * nb, nt * nb))
+    R = np.zeros((nt * nb, ne * blk))
+    tau = np.zeros(nv)
+    last = [None] * ne                              # (tent, E rows of K) of the last tent over K
+    for it in range(nt):
+        v = int(tents["vert"][it])
+        A, Bm, Em, patch = _tent_maps(coords, elems, c, p, lay, Bas, star, vfac, tau.copy(), v,
+                                      float(tents["t_top"][it]), alpha)
+        rows = slice(it * nb, (it + 1) * nb)
+        M[rows, rows] += A
+        for j, K in enumerate(np.asarray(patch).tolist()):
+            cols = slice(j * blk, (j + 1) * blk)
+            if last[K] is None:
+                R[rows, K * blk:(K + 1) * blk] += Bm[:, cols]
+            else:
+                tp, Ep = last[K]
+                M[rows, tp * nb:(tp + 1) * nb] -= Bm[:, cols] @ Ep
+        for j, K in enumerate(np.asarray(patch).tolist()):
+            last[K] = (it, Em[j * blk:(j + 1) * blk, :])
+        tau[v] = float(tents["t_top"][it])
+    S = np.zeros((ne * blk, nt * nb))
+    P = np.zeros((ne * blk, ne * blk))
+    for K in range(ne):
+        if last[K] is None:
+            P[K * blk:(K + 1) * blk, K * blk:(K + 1) * blk] = np.eye(blk)
+        else:
+            tp, Ep = last[K]
+            S[K * blk:(K + 1) * blk, tp * nb:(tp + 1) * nb] = Ep
+    return M, R, S, P, nb
+
+
+def global_solve(coords, elems, c, p, tents, front0, alpha=0.5):
+    """Final front of the sweep from one dense LU of the whole space-time
+    system (see _global_system).  front0: (E, Q, n+2).  Returns (E, Q, n+2)."""
+    M, R, S, P, _ = _global_system(coords, elems, c, p, tents, alpha)
+    f0 = np.asarray(front0, dtype=np.float64).reshape(-1)
+    x = np.linalg.solve(M, R @ f0)
+    return (S @ x + P @ f0).reshape(np.shape(front0))
+
+
+def global_adjoint(coords, elems, c, p, tents, lam_T, alpha=0.5):
+    """F^* lambda_T from the transposed whole system:
+    R^T M^-T S^T lambda + P^T lambda.  lam_T: (E, Q, n+2)."""
+    M, R, S, P, _ = _global_system(coords, elems, c, p, tents, alpha)
+    lt = np.asarray(lam_T, dtype=np.float64).reshape(-1)
+    y = np.linalg.solve(M.T, S.T @ lt)
+    return (R.T @ y + P.T @ lt).reshape(np.shape(lam_T))

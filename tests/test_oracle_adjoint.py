@@ -2,7 +2,10 @@
 
 * dot-product identity with the forward oracle: for the linear sweep F
   (g_D = 0, fixed tents), <lambda, F f> = <F^* lambda, f> for random f, lambda;
-* finite differences of the L2 misfit J(f0) = 1/2 ||U_h(T) - U_obs||^2.
+* finite differences of the L2 misfit J(f0) = 1/2 ||U_h(T) - U_obs||^2;
+* the speed gradient against a closed form and a second, wider difference;
+* brute force: the whole space-time system solved at once equals the sweep,
+  and its transpose the reverse sweep.
 """
 import numpy as np
 import pytest
@@ -113,3 +116,39 @@ def test_speed_gradient_two_materials_matches_swept_difference():
         slope = (J[0] - J[1]) / 2e-4
         assert abs(g[m] - slope) <= 1e-6 * max(1.0, abs(slope)), (m, g[m], slope)
     assert abs(g[0] - g[1]) > 1e-6 * max(abs(g[0]), abs(g[1]))
+
+
+GLOBAL_CASES = [
+    (1, lambda: inputs.mesh_interval(5), 3, 1.0),
+    (2, lambda: inputs.mesh_square(3, 0.2, seed=3), 2, 0.5),
+    (3, lambda: inputs.mesh_cube(1, 0.1, seed=3), 2, 1.5),
+]
+
+
+@pytest.mark.parametrize("dim,mk,p,T", GLOBAL_CASES, ids=["1d", "2d", "3d"])
+def test_global_space_time_solve_equals_sweep(dim, mk, p, T):
+    """Brute force: the whole space-time system of all tents (each tent's
+    eq. (4.1) block, coupled to the earlier tents whose top faces form its
+    bottom), assembled densely and solved by one LU, gives the tent-by-tent
+    sweep's final front to round-off; its transpose gives the reverse
+    sweep's F^* lambda.  The matrix is block lower triangular in the pitched
+    order (causality), and every vertex carries several tents."""
+    m = mk()
+    r = pitching.pitch(m.coords, m.elems, m.c, inputs.pitch_kappa(m), T)
+    nt = len(r["vert"])
+    assert nt >= 2 * m.n_vert
+    lay = tdg.front_layout(m.coords, m.elems, p)
+    rng = np.random.default_rng(dim)
+    f0 = rng.standard_normal((m.n_elem, lay.wq.shape[1], dim + 2))
+    lam = rng.standard_normal(f0.shape)
+    M, _, _, _, nb = adjoint._global_system(m.coords, m.elems, m.c, p, r)
+    assert M.shape == (nt * nb, nt * nb)
+    for t in range(nt - 1):
+        assert not np.any(M[t * nb:(t + 1) * nb, (t + 1) * nb:])
+    assert np.any(M[nb:, :nb])                      # later tents read earlier ones
+    Fg = adjoint.global_solve(m.coords, m.elems, m.c, p, r, f0)
+    Fs, _ = tdg.sweep(m.coords, m.elems, m.c, p, r, None, None, front0=f0)
+    assert np.linalg.norm(Fg - Fs) <= 1e-12 * np.linalg.norm(Fs)
+    Lg = adjoint.global_adjoint(m.coords, m.elems, m.c, p, r, lam)
+    Ls = adjoint.adjoint_sweep(m.coords, m.elems, m.c, p, r, lam)
+    assert np.linalg.norm(Lg - Ls) <= 1e-12 * np.linalg.norm(Ls)

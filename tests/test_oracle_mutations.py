@@ -75,6 +75,7 @@ ADJ_PINS = [
     lambda: Az.test_misfit_gradient_finite_differences(),
     lambda: Az.test_speed_gradient_closed_form(),
     lambda: Az.test_speed_gradient_two_materials_matches_swept_difference(),
+    lambda: Az.test_global_space_time_solve_equals_sweep(*Az.GLOBAL_CASES[1]),
 ]
 
 # (id, oracle module, original text, planted text)
@@ -112,6 +113,10 @@ MUTATIONS = [
     ("adjoint-speed-moves-every-material", "adjoint", "cp[c == cm] = cm * (1.0 + sgn * rel_step)",
      "cp[:] = c * (1.0 + sgn * rel_step)"),
     ("adjoint-speed-one-sided", "adjoint", "(J[0] - J[1]) / (2.0", "(J[0] - J[1]) / (1.0"),
+    ("adjoint-global-coupling-sign", "adjoint", "M[rows, tp * nb:(tp + 1) * nb] -= Bm[:, cols] @ Ep",
+     "M[rows, tp * nb:(tp + 1) * nb] += Bm[:, cols] @ Ep"),
+    ("adjoint-global-stale-front", "adjoint", "            last[K] = (it, Em[j * blk:(j + 1) * blk, :])",
+     "            last[K] = last[K] or (it, Em[j * blk:(j + 1) * blk, :])"),
 ]
 
 
