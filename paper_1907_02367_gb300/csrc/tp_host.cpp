@@ -652,25 +652,35 @@ extern "C" int tp_pitch_mesh(const tp_mesh_desc* mesh, const tp_params* prm, tp_
   };
   std::vector<Rec> recs;
   std::vector<int32_t> R;
-  for (int32_t rnd = 1;; ++rnd) {
-    bool any = false;
-    for (int64_t v = 0; v < nv; ++v)
-      if (tau[v] < T) {
-        any = true;
-        break;
-      }
-    if (!any) break;
+  // R0 of a round: tau_v < T and tau_v <= tau_w for every neighbour w.  Only
+  // the pitched vertices and their neighbours change tau or see a change, so
+  // the set is kept up to date instead of rescanned; it iterates in
+  // increasing vertex order, the order of the greedy independent subset.
+  auto in_r0 = [&](int64_t v) {
+    if (!(tau[v] < T)) return false;
+    for (int32_t e = topo.nbr_ptr[v]; e < topo.nbr_ptr[v + 1]; ++e)
+      if (!(tau[v] <= tau[topo.nbr[e]])) return false;
+    return true;
+  };
+  std::vector<char> is_r0(nv, 0);
+  std::vector<int32_t> r0, r0_next, added;   // r0 sorted by vertex index
+  for (int64_t v = 0; v < nv; ++v)
+    if (in_r0(v)) {
+      is_r0[v] = 1;
+      r0.push_back((int32_t)v);
+    }
+  int64_t below_T = nv;                     // vertices with tau < T (all, as T > 0)
+  std::vector<int32_t> touched;
+  std::vector<char> mark(nv, 0);
+  for (int32_t rnd = 1; below_T > 0; ++rnd) {
     R.clear();
-    for (int64_t v = 0; v < nv; ++v) {
-      if (!(tau[v] < T)) continue;
+    for (int32_t v : r0) {
       bool ok = true;
-      for (int32_t e = topo.nbr_ptr[v]; e < topo.nbr_ptr[v + 1] && ok; ++e)
-        if (!(tau[v] <= tau[topo.nbr[e]])) ok = false;
       for (int32_t e = topo.nbr_ptr[v]; e < topo.nbr_ptr[v + 1] && ok; ++e)
         if (kept[topo.nbr[e]]) ok = false;
       if (ok) {
         kept[v] = 1;
-        R.push_back((int32_t)v);
+        R.push_back(v);
       }
     }
     if (R.empty()) {
@@ -688,26 +698,68 @@ extern "C" int tp_pitch_mesh(const tp_mesh_desc* mesh, const tp_params* prm, tp_
       }
       recs.push_back({lv + 1, rnd, v, tau[v], tt});
     }
+    touched.clear();
     for (size_t i = first; i < recs.size(); ++i) {
-      tau[recs[i].v] = recs[i].tt;
-      lam[recs[i].v] = recs[i].level;
-      kept[recs[i].v] = 0;
+      const int32_t v = recs[i].v;
+      tau[v] = recs[i].tt;
+      lam[v] = recs[i].level;
+      kept[v] = 0;
+      if (!(tau[v] < T)) --below_T;
+      if (!mark[v]) {
+        mark[v] = 1;
+        touched.push_back(v);
+      }
+      for (int32_t e = topo.nbr_ptr[v]; e < topo.nbr_ptr[v + 1]; ++e)
+        if (!mark[topo.nbr[e]]) {
+          mark[topo.nbr[e]] = 1;
+          touched.push_back(topo.nbr[e]);
+        }
     }
+    added.clear();
+    for (int32_t u : touched) {
+      mark[u] = 0;
+      const char now = in_r0(u) ? 1 : 0;
+      if (now && !is_r0[u]) added.push_back(u);
+      is_r0[u] = now;
+    }
+    std::sort(added.begin(), added.end());
+    r0_next.clear();
+    size_t a = 0;
+    for (int32_t v : r0) {                  // merge the kept members with the new ones
+      if (!is_r0[v]) continue;
+      while (a < added.size() && added[a] < v) r0_next.push_back(added[a++]);
+      r0_next.push_back(v);
+    }
+    while (a < added.size()) r0_next.push_back(added[a++]);
+    r0.swap(r0_next);
   }
-  std::stable_sort(recs.begin(), recs.end(), [](const Rec& a, const Rec& b) { return a.level < b.level; });
+  // order (level, round, v): recs are in (round, v) order already, so a
+  // counting sort on the level keeps the rest
+  int32_t n_levels = 0;
+  for (const Rec& r : recs) n_levels = std::max(n_levels, r.level);
+  std::vector<int64_t> at((size_t)n_levels + 2, 0);
+  for (const Rec& r : recs) at[r.level + 1]++;
+  for (int32_t L = 1; L <= n_levels + 1; ++L) at[L] += at[L - 1];
   auto* tt = new tp_tents();
   tt->dim = n;
   tt->nv = nv;
   tt->T = T;
   tt->kappa = prm->kappa;
+  const size_t nt = recs.size();
+  tt->vert.resize(nt);
+  tt->level.resize(nt);
+  tt->round.resize(nt);
+  tt->t_bot.resize(nt);
+  tt->t_top.resize(nt);
   for (const Rec& r : recs) {
-    tt->vert.push_back(r.v);
-    tt->level.push_back(r.level);
-    tt->round.push_back(r.round);
-    tt->t_bot.push_back(r.tb);
-    tt->t_top.push_back(r.tt);
+    const int64_t i = at[r.level]++;
+    tt->vert[i] = r.v;
+    tt->level[i] = r.level;
+    tt->round[i] = r.round;
+    tt->t_bot[i] = r.tb;
+    tt->t_top[i] = r.tt;
   }
-  tt->n_levels = recs.empty() ? 0 : recs.back().level;
+  tt->n_levels = n_levels;
   tt->level_ptr.assign(tt->n_levels + 1, 0);
   for (const Rec& r : recs) tt->level_ptr[r.level]++;
   for (int32_t L = 1; L <= tt->n_levels; ++L) tt->level_ptr[L] += tt->level_ptr[L - 1];

@@ -34,6 +34,7 @@ MESHES = [
     ("cube2", lambda: inputs.mesh_cube(2, 0.1, seed=4), None, 0.4),
     ("lshape_uniform8", lambda: inputs.mesh_lshape(0.125, 1.0), None, 1.0),
     ("lshape_graded035", lambda: inputs.mesh_lshape(0.35, 1.0 / 3.0), None, 1.0),
+    ("inclusion_graded005", lambda: inputs.mesh_inclusion_graded(h_max=0.05), None, 0.5),
 ]
 
 
