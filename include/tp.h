@@ -131,7 +131,12 @@ void tp_destroy_basis(tp_basis* basis);
  * allocates the front state (n_elem * Q * (dim+2) * nrhs doubles).  A tent
  * whose patch holds elements of several wave speeds gets one polynomial of
  * U^p per speed (Section 4.2), coupled through the time-like interface
- * facets.  Errors: TP_ERR_ARG on mismatched dim/p; TP_ERR_UNSUPPORTED when a
+ * facets.  The wave speeds are read from mesh, the tent times from tents:
+ * tents pitched with other speeds on the same mesh are accepted (e.g. the
+ * speeds perturbed with the space-time mesh held fixed); a top face that is
+ * not space-like for the mesh's speeds is reported by the sweep
+ * (TP_ERR_CAUSALITY through tp_sync_status).
+ * Errors: TP_ERR_ARG on mismatched dim/p; TP_ERR_UNSUPPORTED when a
  * patch has more than 4 wave speeds, more than 64 elements or more than 16
  * boundary plus interface facets, or the shared-memory plan (dim U^p,
  * materials) does not fit one CTA even for one right-hand side; TP_ERR_OOM. */
