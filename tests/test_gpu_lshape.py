@@ -3,7 +3,10 @@ singular solution cos(10 t) sin(2 phi / 3) J_2/3(10 r) as initial and
 Dirichlet data, p = 3, T = 1): the front after the sweep against the
 oracle element by element on a graded and a uniform mesh, and the rows of
 the Table 1 study (tents, dofs, L2 error at T) against the oracle's."""
+import importlib.util
+import json
 import math
+import os
 
 import numpy as np
 import pytest
@@ -32,6 +35,11 @@ def _oracle(mesh):
 
 
 def _gpu(mesh, precision):
+    front, tau, status, _, _ = _gpu_full(mesh, precision)
+    return front, tau, status
+
+
+def _gpu_full(mesh, precision):
     import torch
     import paper_1907_02367_gb300 as pkg
     sol = _sol()
@@ -44,7 +52,8 @@ def _gpu(mesh, precision):
     s.set_state(f0, gD)
     s.advance()
     front, tau = s.get_state()
-    return front.cpu().numpy(), tau.cpu().numpy(), s.sync_status()
+    xq, wq = s.front_points()
+    return front.cpu().numpy(), tau.cpu().numpy(), s.sync_status(), xq, wq
 
 
 @pytest.mark.parametrize("h_max,mu,precision,tol", [
@@ -79,3 +88,48 @@ def test_lshape_study_rows_match_oracle(cuda_device):
         assert abs(row["l2_error"] - err) <= 1e-7, (row["l2_error"], err)
     assert rows[1]["l2_error"] < rows[0]["l2_error"] and rows[1]["dof_rate"] > 0
     assert rows[0]["dof_rate"] is None and rows[2]["dof_rate"] is None
+
+
+GOLDEN_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _golden_maker():
+    spec = importlib.util.spec_from_file_location(
+        "make_lshape_oracle", os.path.join(GOLDEN_DIR, "make_lshape_oracle.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def _stored():
+    with open(os.path.join(GOLDEN_DIR, "lshape_oracle.json")) as f:
+        return json.load(f)["meshes"]
+
+
+@pytest.mark.parametrize("idx", range(4))
+def test_lshape_table1_sizes_match_stored_oracle(cuda_device, idx):
+    """At the mesh sizes of the paper's Table 1 (uniform h_max = 0.07, 0.05,
+    0.03 and graded 0.12; 13 000 to 150 000 tents) the oracle takes minutes,
+    so its results are stored (tests/golden/make_lshape_oracle.py): the
+    binary64 sweep matches them at 256 seeded front entries within the
+    parity bound 1e-11 of the front's norm, in the front's norm and in the
+    L2 error of U at T.  A graded mesh that this platform triangulates
+    differently (its point set has mirror symmetry, so Delaunay has ties)
+    cannot be compared and is skipped."""
+    mk = _golden_maker()
+    g = _stored()[idx]
+    mesh = inputs.mesh_lshape(g["h_max"], g["mu"])
+    if mk.mesh_checksum(mesh) != g["checksum"]:
+        assert g["mu"] < 1.0, "the uniform meshes are built without ties and must match"
+        pytest.skip("graded mesh triangulated differently from the stored one")
+    front, tau, st, xq, wq = _gpu_full(mesh, "fp64")
+    assert st == (0, 0)
+    assert np.all(tau == T)
+    flat = front.reshape(-1)
+    pos = np.asarray(g["sample_pos"])
+    ref = np.asarray(g["sample_val"])
+    assert np.max(np.abs(flat[pos] - ref)) <= 1e-11 * g["front_norm"]
+    assert abs(float(np.linalg.norm(flat)) - g["front_norm"]) <= 1e-11 * g["front_norm"]
+    ex = _sol()(xq, T)[:, 0]
+    err = math.sqrt(float(np.sum(wq * (front.reshape(len(wq), -1)[:, 0] - ex) ** 2)))
+    assert abs(err - g["l2_error"]) <= 1e-9, (err, g["l2_error"])
