@@ -485,6 +485,16 @@ def gaussian_pulse(center, delta: float):
     return f
 
 
+def gaussian_pulses_3d(n: int = 64, seed: int = 64) -> list:
+    """n Gaussian pulses in the unit cube (v0 = 0): centres uniform in
+    [0.25, 0.75]^3, widths uniform in [0.05, 0.15], seeded; the right-hand
+    sides of the 3+1D many-right-hand-side runs."""
+    rng = np.random.default_rng(seed)
+    cen = rng.uniform(0.25, 0.75, (n, 3))
+    wid = rng.uniform(0.05, 0.15, n)
+    return [gaussian_pulse(cen[i], float(wid[i])) for i in range(n)]
+
+
 def polynomial_solution(dim: int, which: int = 0):
     """Polynomial solutions of -Lap U + U_tt = 0 (c = 1), used for the
     reproduction property: U in the discrete Trefftz space is recovered
@@ -554,6 +564,8 @@ def workload(name: str) -> Workload:
     inclusion_graded: the same inclusion on about 21 000 triangles graded 10x
                    finer around the circle (mesh_inclusion_graded), p=5, T=2,
                    Gaussian pulse of width 0.05 at a seeded centre.
+    many_rhs_3d  : unit cube 20^3 hexes (48 000 tets, jitter 0.1, seed 4), p=3,
+                   T=1; init is the first of the 64 pulses of gaussian_pulses_3d().
     """
     if name == "plane1d":
         m = mesh_interval(16)
@@ -582,6 +594,9 @@ def workload(name: str) -> Workload:
         rng = np.random.default_rng(17)
         pulse = gaussian_pulse(rng.uniform(0.3, 0.7, 2), 0.05)
         return Workload(name, m, 5, 2.0, pitch_kappa(m), None, pulse, None)
+    if name == "many_rhs_3d":
+        m = mesh_cube(20, 0.1, seed=4)
+        return Workload(name, m, 3, 1.0, pitch_kappa(m), None, gaussian_pulses_3d()[0], None)
     raise KeyError(name)
 
 

@@ -134,3 +134,19 @@ def test_no_cpu_fallback(libtp, tmp_path):
             B.load(str(tmp_path / "missing_libtp.so"))
     finally:
         B._lib = saved
+
+
+def test_many_rhs_3d_stored_oracle_matches_the_pitching(libtp):
+    """The stored oracle values of the full-size 3+1D workload
+    (tests/golden/many_rhs_3d_oracle.json) cover the tents of levels 1-2 of
+    the library's pitching of that mesh."""
+    import json
+    import os
+    import paper_1907_02367_gb300 as pkg
+    with open(os.path.join(os.path.dirname(__file__), "golden", "many_rhs_3d_oracle.json")) as f:
+        g = json.load(f)
+    w = inputs.workload("many_rhs_3d")
+    assert w.mesh.n_elem == 48000
+    lev = pkg.Tents(w.mesh.coords, w.mesh.elems, w.mesh.c, w.kappa, w.T).export()["level"]
+    assert int(np.sum(lev <= g["levels"])) == g["n_tents"]
+    assert [c["column"] for c in g["columns"]] == [0, 63] and len(inputs.gaussian_pulses_3d()) == 64
