@@ -25,3 +25,26 @@ def test_energy_study_matches_oracle(cuda_device, p):
     assert row["n_tents"] == len(r["level"])
     assert abs(row["energy"] - E) <= 1e-11 * E, (row["energy"], E)
     assert row["rel_energy_error"] > 0
+
+
+def test_energy_study_at_the_paper_times_matches_stored_oracle(cuda_device):
+    """The paper's final times T = 100, 1000, 10 000 (up to about 165 000
+    tents in as many levels as a 1D sweep needs) for p = 2 ... 8: the
+    library's energy of the final front against the oracle's, stored by
+    tests/golden/make_energy_oracle.py (the oracle takes about a minute per
+    degree at T = 10 000), within 1e-9 of the larger of the stored energy and
+    1e-3 of the initial energy pi^2/4 (rounding differences of the two
+    binary64 sweeps may add up over that many tents; at p = 2 nearly all of
+    the energy is dissipated by T = 1000)."""
+    import json
+    import os
+    from paper_1907_02367_gb300 import energy_study
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "energy_oracle.json")
+    with open(path) as f:
+        rows = json.load(f)["rows"]
+    for ref in rows:
+        got = energy_study.run(ref["p"], ref["T"])
+        assert got["status"] == [0, 0], ref
+        assert got["n_tents"] == ref["n_tents"]
+        scale = max(ref["energy"], 1e-3 * energy_study.EXACT_ENERGY)
+        assert abs(got["energy"] - ref["energy"]) <= 1e-9 * scale, (ref, got["energy"])

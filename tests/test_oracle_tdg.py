@@ -434,3 +434,24 @@ def test_long_time_energy_dissipation():
         assert rel[p, 4.0] > 0 and rel[p, 8.0] > 0
         assert 1.5 <= rel[p, 8.0] / rel[p, 4.0] <= 2.5, (p, rel[p, 8.0] / rel[p, 4.0])
     assert rel[3, 8.0] < rel[2, 8.0] / 10 and rel[4, 8.0] < rel[3, 8.0] / 10
+
+
+def test_long_time_energy_at_the_paper_times():
+    """Section 6.5 at the paper's final times, on the oracle's values stored by
+    tests/golden/make_energy_oracle.py (5 elements, T = 100, 1000, 10 000,
+    p = 2 ... 8): the numerical energy stays below the exact pi^2/4; for
+    p >= 4 the relative error grows linearly in T (x10 per decade, within
+    20 %) and falls by more than 4x per degree at every T."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "energy_oracle.json")
+    with open(path) as f:
+        rows = json.load(f)["rows"]
+    err = {(r["p"], r["T"]): r["rel_energy_error"] for r in rows}
+    assert all(e > 0 for e in err.values())
+    for p in range(4, 9):
+        for T0, T1 in ((100.0, 1000.0), (1000.0, 10000.0)):
+            assert 8.0 <= err[p, T1] / err[p, T0] <= 12.0, (p, T0, err[p, T1] / err[p, T0])
+    for T in (100.0, 1000.0, 10000.0):
+        for p in range(3, 8):
+            assert err[p + 1, T] < err[p, T] / 4.0, (p, T)
