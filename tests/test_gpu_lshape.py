@@ -106,14 +106,15 @@ def _stored():
         return json.load(f)["meshes"]
 
 
+@pytest.mark.parametrize("precision,tol,err_tol", [("fp64", 1e-11, 1e-9), ("mixed", 1e-8, 1e-6)])
 @pytest.mark.parametrize("idx", range(4))
-def test_lshape_table1_sizes_match_stored_oracle(cuda_device, idx):
+def test_lshape_table1_sizes_match_stored_oracle(cuda_device, idx, precision, tol, err_tol):
     """At the mesh sizes of the paper's Table 1 (uniform h_max = 0.07, 0.05,
     0.03 and graded 0.12; 13 000 to 150 000 tents) the oracle takes minutes,
     so its results are stored (tests/golden/make_lshape_oracle.py): the
-    binary64 sweep matches them at 256 seeded front entries within the
-    parity bound 1e-11 of the front's norm, in the front's norm and in the
-    L2 error of U at T.  A graded mesh that this platform triangulates
+    binary64 and mixed sweeps match them at 256 seeded front entries within
+    the parity bound (1e-11, 1e-8) times the front's norm, in the front's
+    norm and in the L2 error of U at T.  A graded mesh that this platform triangulates
     differently (its point set has mirror symmetry, so Delaunay has ties)
     cannot be compared and is skipped."""
     mk = _golden_maker()
@@ -122,14 +123,14 @@ def test_lshape_table1_sizes_match_stored_oracle(cuda_device, idx):
     if mk.mesh_checksum(mesh) != g["checksum"]:
         assert g["mu"] < 1.0, "the uniform meshes are built without ties and must match"
         pytest.skip("graded mesh triangulated differently from the stored one")
-    front, tau, st, xq, wq = _gpu_full(mesh, "fp64")
+    front, tau, st, xq, wq = _gpu_full(mesh, precision)
     assert st == (0, 0)
     assert np.all(tau == T)
     flat = front.reshape(-1)
     pos = np.asarray(g["sample_pos"])
     ref = np.asarray(g["sample_val"])
-    assert np.max(np.abs(flat[pos] - ref)) <= 1e-11 * g["front_norm"]
-    assert abs(float(np.linalg.norm(flat)) - g["front_norm"]) <= 1e-11 * g["front_norm"]
+    assert np.max(np.abs(flat[pos] - ref)) <= tol * g["front_norm"]
+    assert abs(float(np.linalg.norm(flat)) - g["front_norm"]) <= tol * g["front_norm"]
     ex = _sol()(xq, T)[:, 0]
     err = math.sqrt(float(np.sum(wq * (front.reshape(len(wq), -1)[:, 0] - ex) ** 2)))
-    assert abs(err - g["l2_error"]) <= 1e-9, (err, g["l2_error"])
+    assert abs(err - g["l2_error"]) <= err_tol, (err, g["l2_error"])
