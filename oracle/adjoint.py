@@ -231,3 +231,31 @@ def global_adjoint(coords, elems, c, p, tents, lam_T, alpha=0.5):
     lt = np.asarray(lam_T, dtype=np.float64).reshape(-1)
     y = np.linalg.solve(M.T, S.T @ lt)
     return (R.T @ y + P.T @ lt).reshape(np.shape(lam_T))
+
+
+def speed_gradient_transposed(coords, elems, c, p, tents, front0, lam_T, rel_step=1e-6, alpha=0.5):
+    """dJ/dc of J = <lam_T, front_T> on a single-material mesh (every element
+    at the speed c_0), the tents held fixed and g_D = 0, through the
+    transposed whole system (see _global_system): with M x = R f_0 and
+    front_T = S x + P f_0,
+
+        dJ/dc = lam^T S' x + y^T (R' f_0 - M' x),    y = M^-T S^T lam,
+
+    M', R', S' the derivatives of the assembled system with respect to c
+    (central differences of the assembly with step rel_step * c_0).  A second
+    route to the speed gradient besides differencing whole sweeps
+    (speed_gradient).  Returns dJ/dc_0."""
+    c = np.asarray(c, dtype=np.float64)
+    c0 = float(c[0])
+    if np.any(c != c0):
+        raise NotImplementedError("speed_gradient_transposed needs a single material")
+    f0 = np.asarray(front0, dtype=np.float64).reshape(-1)
+    lt = np.asarray(lam_T, dtype=np.float64).reshape(-1)
+    M, R, S, _, _ = _global_system(coords, elems, c, p, tents, alpha)
+    x = np.linalg.solve(M, R @ f0)
+    y = np.linalg.solve(M.T, S.T @ lt)
+    Mp, Rp, Sp, _, _ = _global_system(coords, elems, c * (1.0 + rel_step), p, tents, alpha)
+    Mm, Rm, Sm, _, _ = _global_system(coords, elems, c * (1.0 - rel_step), p, tents, alpha)
+    d = 2.0 * rel_step * c0
+    dM, dR, dS = (Mp - Mm) / d, (Rp - Rm) / d, (Sp - Sm) / d
+    return float(lt @ (dS @ x) + y @ (dR @ f0 - dM @ x))

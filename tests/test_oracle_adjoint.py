@@ -152,3 +152,24 @@ def test_global_space_time_solve_equals_sweep(dim, mk, p, T):
     Lg = adjoint.global_adjoint(m.coords, m.elems, m.c, p, r, lam)
     Ls = adjoint.adjoint_sweep(m.coords, m.elems, m.c, p, r, lam)
     assert np.linalg.norm(Lg - Ls) <= 1e-12 * np.linalg.norm(Ls)
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+def test_speed_gradient_transposed_system_equals_swept_difference(dim):
+    """Two routes to dJ/dc on one material with the tents fixed: the adjoint
+    state of the whole space-time system contracted with the derivative of
+    its assembly, and central differences of whole sweeps; they agree to
+    1e-8 relative (both carry O(s^2) truncation)."""
+    if dim == 1:
+        m, p, T, cv = inputs.mesh_interval(5), 3, 0.6, 1.3
+    else:
+        m, p, T, cv = inputs.mesh_square(3, 0.2, seed=3), 2, 0.3, 0.8
+    m.c[:] = cv
+    r = pitching.pitch(m.coords, m.elems, m.c, inputs.pitch_kappa(m), T)
+    lay = tdg.front_layout(m.coords, m.elems, p)
+    rng = np.random.default_rng(5)
+    f0 = rng.standard_normal((m.n_elem, lay.wq.shape[1], dim + 2))
+    lam = rng.standard_normal(f0.shape)
+    g_t = adjoint.speed_gradient_transposed(m.coords, m.elems, m.c, p, r, f0, lam)
+    _, g_d = adjoint.speed_gradient(m.coords, m.elems, m.c, p, r, None, lam, front0=f0)
+    assert abs(g_t - g_d[0]) <= 1e-8 * abs(g_d[0]), (g_t, g_d[0])

@@ -76,6 +76,7 @@ ADJ_PINS = [
     lambda: Az.test_speed_gradient_closed_form(),
     lambda: Az.test_speed_gradient_two_materials_matches_swept_difference(),
     lambda: Az.test_global_space_time_solve_equals_sweep(*Az.GLOBAL_CASES[1]),
+    lambda: Az.test_speed_gradient_transposed_system_equals_swept_difference(2),
 ]
 
 # (id, oracle module, original text, planted text)
@@ -117,6 +118,7 @@ MUTATIONS = [
      "M[rows, tp * nb:(tp + 1) * nb] += Bm[:, cols] @ Ep"),
     ("adjoint-global-stale-front", "adjoint", "            last[K] = (it, Em[j * blk:(j + 1) * blk, :])",
      "            last[K] = last[K] or (it, Em[j * blk:(j + 1) * blk, :])"),
+    ("adjoint-transposed-gradient-sign", "adjoint", "y @ (dR @ f0 - dM @ x)", "y @ (dR @ f0 + dM @ x)"),
 ]
 
 
