@@ -150,3 +150,25 @@ def test_many_rhs_3d_stored_oracle_matches_the_pitching(libtp):
     lev = pkg.Tents(w.mesh.coords, w.mesh.elems, w.mesh.c, w.kappa, w.T).export()["level"]
     assert int(np.sum(lev <= g["levels"])) == g["n_tents"]
     assert [c["column"] for c in g["columns"]] == [0, 63] and len(inputs.gaussian_pulses_3d()) == 64
+
+
+def test_inclusion_graded_stored_oracle_matches_the_pitching(libtp):
+    """The stored oracle values of the full-size graded inclusion workload
+    (tests/golden/inclusion_graded_oracle.json) were computed on the mesh
+    built here, and the library's pitching of it has the stored number of
+    tents, in total and in levels 1-2."""
+    import importlib.util
+    import json
+    import os
+    import paper_1907_02367_gb300 as pkg
+    here = os.path.join(os.path.dirname(__file__), "golden")
+    spec = importlib.util.spec_from_file_location("mk", os.path.join(here, "make_inclusion_graded_oracle.py"))
+    mk = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mk)
+    with open(os.path.join(here, "inclusion_graded_oracle.json")) as f:
+        g = json.load(f)
+    w = inputs.workload("inclusion_graded")
+    assert mk.mesh_checksum(w.mesh) == g["checksum"]
+    lev = pkg.Tents(w.mesh.coords, w.mesh.elems, w.mesh.c, w.kappa, w.T).export()["level"]
+    assert len(lev) == g["n_tents_total"]
+    assert int(np.sum(lev <= g["levels"])) == g["n_tents"]
