@@ -4,7 +4,9 @@ wave equation (Perugia, Schoberl, Stocker, Wintersteiger).
 The numerics run in libtp (C ABI, include/tp.h): host C++ for pitching and
 tables, hand-written sm_103a CUDA kernels for the layer-by-layer tent solve.
 This package is the thin Python layer over it: `Tents`, `Basis` and `Solver`
-mirror tp_pitch_mesh / tp_build_basis / tp_create ... tp_energy.
+mirror tp_pitch_mesh / tp_build_basis / tp_create ... tp_energy; `TentSweep`
+and `speed_gradient` differentiate the sweep.  `inputs` builds the seeded
+workloads; `lshape` and `energy_study` run the studies of Section 6.
 """
 from __future__ import annotations
 
@@ -100,9 +102,11 @@ class Solver:
     facet opposite local vertex o of element k as Neumann (sigma.n = g_N),
     else Dirichlet; boundary_kinds() tells which data each boundary point
     takes.  nrhs right-hand sides share the tents and their matrices (in
-    groups when one CTA cannot hold all of them).  All device memory handed
-    to libtp is torch CUDA float64 memory; the current torch stream is
-    passed to every call."""
+    groups when one CTA cannot hold all of them).  tents: a Tents object to
+    sweep over instead of pitching the mesh with c (the wave speeds always
+    come from c; see speed_gradient).  All device memory handed to libtp is
+    torch CUDA float64 memory; the current torch stream is passed to every
+    call."""
 
     def __init__(self, coords, elems, c, p: int, T: float, kappa: float, alpha: float = 0.5,
                  nrhs: int = 1, tents: Tents | None = None, precision: str = "fp64",
