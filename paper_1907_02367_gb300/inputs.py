@@ -566,6 +566,11 @@ def workload(name: str) -> Workload:
                    Gaussian pulse of width 0.05 at a seeded centre.
     many_rhs_3d  : unit cube 20^3 hexes (48 000 tets, jitter 0.1, seed 4), p=3,
                    T=1; init is the first of the 64 pulses of gaussian_pulses_3d().
+    lognormal2d  : unit square 100x100 jittered grid (20 000 triangles, seed 5),
+                   c_K = exp(N(-0.045, 0.3^2)) per element (seed 5, mean about 1),
+                   p=4, T=1; init is the first of 16 pulses of width 0.05
+                   (centres uniform in [0.2, 0.8]^2, seed 55): the adjoint
+                   configuration's forward problem.
     """
     if name == "plane1d":
         m = mesh_interval(16)
@@ -594,6 +599,11 @@ def workload(name: str) -> Workload:
         rng = np.random.default_rng(17)
         pulse = gaussian_pulse(rng.uniform(0.3, 0.7, 2), 0.05)
         return Workload(name, m, 5, 2.0, pitch_kappa(m), None, pulse, None)
+    if name == "lognormal2d":
+        m = mesh_square(100, 0.2, seed=5)
+        m.c[:] = np.exp(np.random.default_rng(5).normal(-0.045, 0.3, m.n_elem))
+        cen = np.random.default_rng(55).uniform(0.2, 0.8, (16, 2))
+        return Workload(name, m, 4, 1.0, pitch_kappa(m), None, gaussian_pulse(cen[0], 0.05), None)
     if name == "many_rhs_3d":
         m = mesh_cube(20, 0.1, seed=4)
         return Workload(name, m, 3, 1.0, pitch_kappa(m), None, gaussian_pulses_3d()[0], None)

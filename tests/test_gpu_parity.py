@@ -364,3 +364,19 @@ def test_autotune_keeps_results(cuda_device):
     ref, rtau, _ = _oracle(m, w.p, w.T, w.kappa, w.init, None)
     assert np.array_equal(tau.cpu().numpy(), rtau)
     assert _rel(got.cpu().numpy().reshape(ref.shape), ref) <= TOL
+
+
+def test_more_than_four_materials_is_refused_cleanly(cuda_device):
+    """The per-element log-normal medium gives tents with up to 8 speeds;
+    tp_create refuses it with TP_ERR_UNSUPPORTED before any device work,
+    and the library stays usable for the next context."""
+    import paper_1907_02367_gb300 as pkg
+    from paper_1907_02367_gb300 import _binding as B
+    w = inputs.workload("lognormal2d")
+    m = w.mesh
+    with pytest.raises(B.TpError) as exc:
+        pkg.Solver(m.coords, m.elems, m.c, w.p, w.T, w.kappa)
+    assert exc.value.code == B.TP_ERR_UNSUPPORTED and "materials" in str(exc.value)
+    s = inputs.workload("small2d")
+    ok = pkg.Solver(s.mesh.coords, s.mesh.elems, s.mesh.c, s.p, s.T, s.kappa)
+    assert ok.n_levels > 0

@@ -171,3 +171,19 @@ def test_sine_product_1d_is_a_wave_with_constant_energy():
         E = float(np.sum(0.5 * (dens[1:] + dens[:-1])) * (x[1] - x[0]))
         assert abs(E - np.pi ** 2 / 4) < 1e-6
         assert abs(F[0, 1]) < 1e-15 and abs(F[-1, 1]) < 1e-12
+
+
+def test_lognormal_speeds_exceed_four_materials_per_star():
+    """The adjoint configuration's medium: c_K = exp(N(-0.045, 0.3^2)) per
+    element has mean about 1, and more than 90 % of the vertex stars hold
+    more than 4 distinct speeds (the most one tent of the library holds),
+    up to 8."""
+    w = inputs.workload("lognormal2d")
+    m = w.mesh
+    assert m.n_elem == 20000 and abs(m.c.mean() - 1.0) < 0.02
+    star = [[] for _ in range(m.n_vert)]
+    for k, el in enumerate(m.elems.tolist()):
+        for v in el:
+            star[v].append(k)
+    nmat = np.array([len(set(m.c[s].tolist())) for s in star])
+    assert np.mean(nmat > 4) > 0.9 and nmat.max() <= 8
