@@ -455,3 +455,46 @@ def test_long_time_energy_at_the_paper_times():
     for T in (100.0, 1000.0, 10000.0):
         for p in range(3, 8):
             assert err[p + 1, T] < err[p, T] / 4.0, (p, T)
+
+
+def test_multi_material_tent_matrix_is_block_sparse():
+    """With one speed per element (a log-normal-like medium), a 2D tent over
+    vertex v has one polynomial per element of its star (Section 4.2).  The
+    block of A coupling two materials is nonzero exactly when they share an
+    edge through v (an interface facet, eq. 2.5); around an interior vertex
+    the elements form a cycle, so every material has two neighbours and A is
+    block cyclic tridiagonal.  Tents here hold up to 8 materials."""
+    m = inputs.mesh_square(4, 0.2, seed=9)
+    m.c[:] = np.exp(np.random.default_rng(3).normal(0.0, 0.3, m.n_elem))
+    p = 2
+    nb = (p + 1) ** 2
+    kappa = inputs.pitch_kappa(m)
+    r = pitching.pitch(m.coords, m.elems, m.c, kappa, 0.1)
+    seen = []
+
+    def rec(it, d):
+        seen.append(d)
+
+    tdg.sweep(m.coords, m.elems, m.c, p, r, inputs.gaussian_pulse((0.5, 0.5), 0.3), None, record=rec)
+    nmax, checked_interior = 0, 0
+    for d in seen:
+        v, A, grp = d["v"], d["A"], d["groups"]
+        ng = len(d["speeds"])
+        nmax = max(nmax, ng)
+        adj = np.zeros((ng, ng), dtype=bool)
+        patch = d["patch"]
+        for i, ka in enumerate(patch):
+            for kb in patch[i + 1:]:
+                shared = set(m.elems[ka].tolist()) & set(m.elems[kb].tolist())
+                if v in shared and len(shared) == 2 and grp[ka] != grp[kb]:
+                    adj[grp[ka], grp[kb]] = adj[grp[kb], grp[ka]] = True
+        for a in range(ng):
+            for b in range(ng):
+                if a == b:
+                    continue
+                blk = A[a * nb:(a + 1) * nb, b * nb:(b + 1) * nb]
+                assert (np.abs(blk).max() > 0) == adj[a, b], (v, a, b)
+        if ng == len(patch) and adj.sum(axis=1).min() == 2:
+            checked_interior += 1
+            assert np.all(adj.sum(axis=1) == 2)
+    assert nmax > 4 and checked_interior > 0
