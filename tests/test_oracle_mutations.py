@@ -53,6 +53,7 @@ TDG_PINS = [
     lambda: Tz.test_interface_energy_identity_1d(),
     lambda: Tz.test_polynomial_reproduction_with_neumann_faces(2, 3, 1),
     lambda: Tz.test_tent_matrix_symmetric_part_positive_definite(2, 3, True),
+    lambda: Tz.test_energy_identity_1d_with_neumann(3, 1.7),
 ]
 BASIS_PINS = [
     lambda: Bz.test_trefftz_property_exact(2, 3),
@@ -93,6 +94,7 @@ MUTATIONS = [
     ("tdg-neumann-coupling-sign", "tdg", "wf, Sn, Vd + beta * Sn", "wf, Sn, -Vd + beta * Sn"),
     ("tdg-neumann-penalty-sign", "tdg", "wf, Sn, Vd + beta * Sn", "wf, Sn, Vd - beta * Sn"),
     ("tdg-neumann-data-sign", "tdg", "beta * Sn - Vd)", "beta * Sn + Vd)"),
+    ("tdg-neumann-penalty-scale", "tdg", "wf, Sn, Vd + beta * Sn", "wf, Sn, Vd + 2.0 * beta * Sn"),
     ("basis-recursion-denominator", "basis", "c2 / (k * (k - 1)) * s", "c2 / (k * (k + 1)) * s"),
     ("basis-recursion-factor", "basis", "(alpha[m] + 1) * (alpha[m] + 2) * prev",
      "(alpha[m] + 1) * (alpha[m] + 1) * prev"),

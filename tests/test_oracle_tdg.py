@@ -56,7 +56,7 @@ def test_reproduction_fails_for_degree_above_p():
     assert np.abs(F - ex).max() > 1e-6
 
 
-def _energy_identity_check(mesh, p, T, sol, alpha=0.5):
+def _energy_identity_check(mesh, p, T, sol, alpha=0.5, neumann=False, beta=0.5):
     lay = tdg.front_layout(mesh.coords, mesh.elems, p)
     n = mesh.dim
     nodes, wts = np.polynomial.legendre.leggauss(12)
@@ -98,9 +98,13 @@ def _energy_identity_check(mesh, p, T, sol, alpha=0.5):
         if v in bverts:
             tq = d["t_bot"] + (d["t_top"] - d["t_bot"]) * 0.5 * (nodes + 1)
             xv = np.full((len(tq), 1), mesh.coords[v, 0])
-            _, Vd, _ = B.eval_phys(xv, tq, d["xc"], d["tc"], d["h"], d["c"])
-            vd = Vd @ d["x"]
-            rhs -= alpha * np.sum(0.5 * (d["t_top"] - d["t_bot"]) * wts * vd * vd)
+            _, Vd, Sd = B.eval_phys(xv, tq, d["xc"], d["tc"], d["h"], d["c"])
+            if neumann:                     # g_N = 0: dissipation beta int (sigma.n)^2
+                sd = Sd[:, 0, :] @ d["x"]
+                rhs -= beta * np.sum(0.5 * (d["t_top"] - d["t_bot"]) * wts * sd * sd)
+            else:                           # g_D = 0: dissipation alpha int v^2
+                vd = Vd @ d["x"]
+                rhs -= alpha * np.sum(0.5 * (d["t_top"] - d["t_bot"]) * wts * vd * vd)
         elif n > 1 and _on_boundary(mesh, v):
             return
         scale = abs(top) + abs(0.5 * np.sum(w * Qg(fb[:, 1], fb[:, 2:], g_b))) + 1e-30
@@ -108,8 +112,9 @@ def _energy_identity_check(mesh, p, T, sol, alpha=0.5):
         checked[0] += 1
 
     r = pitching.pitch(mesh.coords, mesh.elems, mesh.c, inputs.pitch_kappa(mesh), T)
+    marker = inputs.boundary_marker(mesh, lambda x: True) if neumann else None
     F, tau = tdg.sweep(mesh.coords, mesh.elems, mesh.c, p, r, lambda x: sol(x, 0.0), None,
-                       alpha=alpha, record=rec)
+                       alpha=alpha, record=rec, bnd_type=marker, beta=beta)
     return worst[0], checked[0], F, lay
 
 
@@ -131,6 +136,19 @@ def _sinsin_1d(x, t):
 def test_energy_identity_1d_with_dirichlet(p):
     mesh = inputs.mesh_interval(5)           # Section 6.5: 5 elements
     worst, checked, F, lay = _energy_identity_check(mesh, p, 0.7, _sinsin_1d)
+    assert checked > 10
+    assert worst < 1e-12
+
+
+@pytest.mark.parametrize("p,beta", [(2, 0.5), (3, 0.5), (3, 1.7)])
+def test_energy_identity_1d_with_neumann(p, beta):
+    """Per-tent energy identity with Neumann walls (g_N = 0): the boundary
+    term of eq. (4.1) tested with the tent's own solution leaves the
+    dissipation beta int (sigma.n)^2 on the vertical faces, in place of the
+    Dirichlet alpha int v^2; pins the size of the Neumann penalty, which
+    exact solutions (sigma.n = g_N) cannot see."""
+    mesh = inputs.mesh_interval(5)
+    worst, checked, F, lay = _energy_identity_check(mesh, p, 0.7, _sinsin_1d, neumann=True, beta=beta)
     assert checked > 10
     assert worst < 1e-12
 
