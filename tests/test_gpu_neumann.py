@@ -139,3 +139,35 @@ def test_interface_meeting_neumann_and_dirichlet_walls(cuda_device, precision, t
     ref, tau_ref = tdg.sweep(mesh.coords, mesh.elems, mesh.c, p, r, pulse, None, bnd_type=marker)
     assert np.array_equal(tau, tau_ref)
     assert _rel(got.reshape(ref.shape), ref) <= tol
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("mixed", 1e-8)])
+def test_penalty_beta_other_than_half(cuda_device, precision, tol):
+    """beta = 1.7 (eq. 2.5) instead of the paper's 0.5: Neumann walls in 1D, and
+    the inclusion's interface facets in 2D (with Dirichlet walls), against the
+    oracle with the same beta."""
+    import paper_1907_02367_gb300 as pkg
+    beta = 1.7
+    # 1D, Neumann walls, g_N = 0
+    mesh = inputs.mesh_interval(5)
+    marker = inputs.boundary_marker(mesh, lambda x: True)
+    init = lambda x: inputs.sine_product_1d(x, 0.3)          # noqa: E731
+    p, T = 3, 0.7
+    s = pkg.Solver(mesh.coords, mesh.elems, mesh.c, p, T, 0.9, precision=precision, bnd_type=marker,
+                   beta=beta)
+    got, tau, st = _run(s, init)
+    assert st == (0, 0)
+    r = pitching.pitch(mesh.coords, mesh.elems, mesh.c, 0.9, T)
+    ref, tau_ref = tdg.sweep(mesh.coords, mesh.elems, mesh.c, p, r, init, None, bnd_type=marker, beta=beta)
+    assert np.array_equal(tau, tau_ref)
+    assert _rel(got.reshape(ref.shape), ref) <= tol
+    # 2D, interface facets (c = 3 in the disc, 1 outside)
+    w = inputs.workload("inclusion_small")
+    m = w.mesh
+    s = pkg.Solver(m.coords, m.elems, m.c, w.p, w.T, w.kappa, precision=precision, beta=beta)
+    got, tau, st = _run(s, w.init)
+    assert st == (0, 0)
+    r = pitching.pitch(m.coords, m.elems, m.c, w.kappa, w.T)
+    ref, tau_ref = tdg.sweep(m.coords, m.elems, m.c, w.p, r, w.init, None, beta=beta)
+    assert np.array_equal(tau, tau_ref)
+    assert _rel(got.reshape(ref.shape), ref) <= tol
