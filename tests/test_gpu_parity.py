@@ -380,3 +380,20 @@ def test_more_than_four_materials_is_refused_cleanly(cuda_device):
     s = inputs.workload("small2d")
     ok = pkg.Solver(s.mesh.coords, s.mesh.elems, s.mesh.c, s.p, s.T, s.kappa)
     assert ok.n_levels > 0
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", TOL), ("mixed", MIXED_TOL)])
+@pytest.mark.parametrize("name", ["small2d", "inclusion_small"])
+def test_penalty_alpha_other_than_half(cuda_device, name, precision, tol):
+    """alpha = 1.3 (eq. 2.5) instead of the paper's 0.5, on the Dirichlet
+    walls and, for the inclusion, the interface jumps of v; against the
+    oracle with the same alpha (alpha moves the oracle's fronts by 1e-4 and
+    8e-2 relative on these two workloads)."""
+    w = inputs.workload(name)
+    m = w.mesh
+    dfun = (lambda x, t: w.solution(x, t)[:, 1]) if w.solution is not None else None
+    s, got, tau, st = _gpu_run(m, w.p, w.T, w.kappa, w.init, dfun, alpha=1.3, precision=precision)
+    assert st == (0, 0)
+    ref, tau_ref, _ = _oracle(m, w.p, w.T, w.kappa, w.init, dfun, alpha=1.3)
+    assert np.array_equal(tau, tau_ref)
+    assert _rel(got.reshape(ref.shape), ref) <= tol
