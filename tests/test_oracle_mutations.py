@@ -70,6 +70,10 @@ PITCH_PINS = [
     lambda: Pz.test_heterogeneous_speed_uses_edge_max(),
     lambda: Pz.test_invariants_2d_heterogeneous(),
 ]
+ENERGY_PINS = [
+    lambda: Tz.test_energy_through_a_curved_front_is_conserved_for_exact_solutions(2.0),
+    lambda: Tz.test_energy_decreases_1d(),
+]
 ADJ_PINS = [
     lambda: Az.test_dot_product_identity(1),
     lambda: Az.test_dot_product_identity(2),
@@ -109,6 +113,8 @@ MUTATIONS = [
     ("pitch-edge-min-speed", "pitching", "ck > ce[key]", "ck < ce[key]"),
     ("pitch-level-ignores-neighbours", "pitching", "level = 1 + max([lam[v]] + [lam[w] for w in nbr[v]])",
      "level = 1 + lam[v]"),
+    ("energy-gradient-term-sign", "energy", "dens = dens - 2.0 * v", "dens = dens + 2.0 * v"),
+    ("energy-drop-c", "energy", "v * v / (c[:, None] ** 2)", "v * v"),
     ("adjoint-untransposed-solve", "adjoint", "mu = np.linalg.solve(A.T, Em.T @ lt)",
      "mu = np.linalg.solve(A, Em.T @ lt)"),
     ("adjoint-bottom-sign", "adjoint", "(w[:, None] * (c2 * Vb - Sgb)).T", "(w[:, None] * (c2 * Vb + Sgb)).T"),
@@ -138,6 +144,9 @@ def _install(monkeypatch, name, mod):
     if name == "pitching":
         monkeypatch.setattr(Pz, "pitching", mod)
         return PITCH_PINS
+    if name == "energy":
+        monkeypatch.setattr(Tz, "energy", mod)
+        return ENERGY_PINS
     if name == "adjoint":
         monkeypatch.setattr(Az, "adjoint", mod)
         return ADJ_PINS
@@ -158,7 +167,7 @@ def test_planted_mistake_fails_a_pin(monkeypatch, mid, name, old, new):
     assert caught, f"no pin fails for the planted mistake {mid}"
 
 
-@pytest.mark.parametrize("name", ["tdg", "basis", "quadrature", "pitching", "adjoint"])
+@pytest.mark.parametrize("name", ["tdg", "basis", "quadrature", "pitching", "energy", "adjoint"])
 def test_unplanted_copy_passes_every_pin(monkeypatch, name):
     """The loader itself changes nothing: an unmodified copy passes the pins."""
     pins = _install(monkeypatch, name, _mutant(name, "from __future__ import annotations",

@@ -516,3 +516,40 @@ def test_multi_material_tent_matrix_is_block_sparse():
             checked_interior += 1
             assert np.all(adj.sum(axis=1) == 2)
     assert nmax > 4 and checked_interior > 0
+
+
+@pytest.mark.parametrize("cval", [1.0, 2.0])
+def test_energy_through_a_curved_front_is_conserved_for_exact_solutions(cval):
+    """energy.front_energy on a front t = tau(x) that is not flat: for an exact
+    solution the energy crossing any space-like front equals the energy at
+    t = 0 when nothing crosses the walls (here v = 0 there).  The flux
+    through the front is 1/2 int (c^-2 v^2 + |sigma|^2 - 2 v sigma.grad tau) dx
+    (n dS = (-grad tau, 1) dx, Section 6.5's density on a graph); the front is
+    the one the pitching leaves after 9 levels.  Standing wave at speed c:
+    U = cos(sqrt2 pi c t) sin(pi x) sin(pi y)."""
+    m = inputs.mesh_square(6, 0.2, seed=7)
+    m.c[:] = cval
+    p = 8
+    lay = tdg.front_layout(m.coords, m.elems, p)
+    r = pitching.pitch(m.coords, m.elems, m.c, inputs.pitch_kappa(m), 1.0)
+    tau = np.zeros(m.n_vert)
+    for it in range(len(r["vert"])):
+        if r["level"][it] > 9:
+            break
+        tau[r["vert"][it]] = r["t_top"][it]
+    assert tau.max() > tau.min() > 0
+
+    def sol(x, t):
+        f = inputs.standing_wave_2d(x, cval * np.asarray(t))
+        f[:, 1] *= cval
+        return f
+
+    tq = np.einsum("qi,ei->eq", lay.bary, tau[m.elems]).reshape(-1)
+    F = sol(lay.xq.reshape(-1, 2), tq).reshape(m.n_elem, -1, 4)
+    F0 = sol(lay.xq.reshape(-1, 2), 0.0).reshape(m.n_elem, -1, 4)
+    g = energy.element_gradients(m.coords, m.elems, tau)
+    assert np.all(cval * np.linalg.norm(g, axis=1) < 1.0)
+    E0 = energy.front_energy(F0, lay.wq, m.c)
+    assert abs(E0 - np.pi ** 2 / 4) < 1e-10
+    assert abs(energy.front_energy(F, lay.wq, m.c, g) - E0) <= 1e-10 * E0
+    assert abs(energy.front_energy(F, lay.wq, m.c) - E0) > 1e-3 * E0     # the gradient term matters
