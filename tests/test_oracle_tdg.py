@@ -160,6 +160,15 @@ def test_energy_identity_2d_interior():
     assert worst < 1e-12
 
 
+def test_energy_identity_3d_interior():
+    """The per-tent energy identity on the interior tents of a 3D mesh
+    (jittered 3^3 hexes, six tetrahedra each, p = 2)."""
+    mesh = inputs.mesh_cube(3, 0.1, seed=4)
+    worst, checked, F, lay = _energy_identity_check(mesh, 2, 0.3, inputs.standing_wave_3d)
+    assert checked > 10
+    assert worst < 1e-12
+
+
 def test_energy_decreases_1d():
     """Section 6.5: with exact (constant-energy) data the numerical energy at
     the flat final front is below the initial one."""
