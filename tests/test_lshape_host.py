@@ -87,6 +87,11 @@ def test_stored_oracle_values_match_the_meshes_and_the_paper_trend(libtp):
             assert 0.7 * ref <= g["l2_error"] <= 1.3 * ref, (g["h_max"], g["l2_error"], ref)
     for (d0, e0), (d1, e1) in zip(uni[:-1], uni[1:]):
         assert 0.9 <= lshape.dof_rate(d0, e0, d1, e1) <= 1.5
+    # graded meshes: near the optimal rate p + 1 = 4 (Table 1 prints 5.13, 4.70, 4.21)
+    gra = sorted(((16 * g["n_tents"], g["l2_error"]) for g in stored if g["mu"] < 1.0))
+    assert len(gra) >= 3
+    for (d0, e0), (d1, e1) in zip(gra[:-1], gra[1:]):
+        assert 3.0 <= lshape.dof_rate(d0, e0, d1, e1) <= 5.5
 
 
 def test_stored_oracle_values_show_the_graded_mesh_advantage():
