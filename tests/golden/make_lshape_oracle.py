@@ -26,7 +26,8 @@ from oracle import pitching, tdg  # noqa: E402
 from paper_1907_02367_gb300 import inputs  # noqa: E402
 
 P, T = 3, 1.0
-MESHES = [(0.07, 1.0), (0.05, 1.0), (0.03, 1.0), (0.12, 1.0 / 3.0), (0.10, 1.0 / 3.0), (0.08, 1.0 / 3.0)]
+MESHES = [(0.07, 1.0), (0.05, 1.0), (0.03, 1.0), (0.12, 1.0 / 3.0), (0.10, 1.0 / 3.0), (0.08, 1.0 / 3.0),
+          (0.06, 1.0 / 3.0)]
 N_SAMPLE = 256
 
 

@@ -110,7 +110,7 @@ def _stored():
 @pytest.mark.parametrize("idx", range(len(_stored())))
 def test_lshape_table1_sizes_match_stored_oracle(cuda_device, idx, precision, tol, err_tol):
     """At the mesh sizes of the paper's Table 1 (uniform h_max = 0.07, 0.05,
-    0.03 and graded 0.12, 0.10, 0.08; 13 000 to 210 000 tents) the oracle takes minutes,
+    0.03 and graded 0.12, 0.10, 0.08, 0.06; 13 000 to 520 000 tents) the oracle takes minutes,
     so its results are stored (tests/golden/make_lshape_oracle.py): the
     binary64 and mixed sweeps match them at 256 seeded front entries within
     the parity bound (1e-11, 1e-8) times the front's norm, in the front's
