@@ -24,6 +24,7 @@ import oracle.adjoint  # noqa: E402
 import oracle.tdg  # noqa: E402
 import test_oracle_adjoint as Az  # noqa: E402
 import test_oracle_basis as Bz  # noqa: E402
+import test_oracle_dissipation as Dz  # noqa: E402
 import test_oracle_pitching as Pz  # noqa: E402
 import test_oracle_quadrature as Qz  # noqa: E402
 import test_oracle_tdg as Tz  # noqa: E402
@@ -73,6 +74,9 @@ PITCH_PINS = [
 ENERGY_PINS = [
     lambda: Tz.test_energy_through_a_curved_front_is_conserved_for_exact_solutions(2.0),
     lambda: Tz.test_energy_decreases_1d(),
+    lambda: Dz.test_energy_balance_closes("1d_dirichlet_data"),
+    lambda: Dz.test_energy_balance_closes("2d_interface"),
+    lambda: Dz.test_energy_balance_closes("2d_neumann_data"),
 ]
 ADJ_PINS = [
     lambda: Az.test_dot_product_identity(1),
@@ -82,6 +86,9 @@ ADJ_PINS = [
     lambda: Az.test_speed_gradient_two_materials_matches_swept_difference(),
     lambda: Az.test_global_space_time_solve_equals_sweep(*Az.GLOBAL_CASES[1]),
     lambda: Az.test_speed_gradient_transposed_system_equals_swept_difference(2),
+    lambda: Az.test_multi_material_adjoint_dot_product_and_whole_system("2d_two_materials"),
+    lambda: Az.test_multi_material_adjoint_dot_product_and_whole_system("2d_neumann_two_materials"),
+    lambda: Az.test_per_material_speed_gradient_two_routes("1d_per_element"),
 ]
 
 # (id, oracle module, original text, planted text)
@@ -119,11 +126,23 @@ MUTATIONS = [
      "mu = np.linalg.solve(A, Em.T @ lt)"),
     ("adjoint-bottom-sign", "adjoint", "(w[:, None] * (c2 * Vb - Sgb)).T", "(w[:, None] * (c2 * Vb + Sgb)).T"),
     ("adjoint-speed-step-not-relative", "adjoint", "(2.0 * rel_step * cm)", "(2.0 * rel_step)"),
-    ("adjoint-speed-moves-every-material", "adjoint", "cp[c == cm] = cm * (1.0 + sgn * rel_step)",
-     "cp[:] = c * (1.0 + sgn * rel_step)"),
+    ("adjoint-speed-moves-every-material", "adjoint",
+     "cp[c == cm] = cm * (1.0 + sgn * rel_step)\n            F, _ = _tdg.sweep",
+     "cp[:] = c * (1.0 + sgn * rel_step)\n            F, _ = _tdg.sweep"),
+    ("adjoint-transposed-moves-every-material", "adjoint",
+     "cp[c == cm] = cm * (1.0 + sgn * rel_step)\n            sys_.append",
+     "cp[:] = c * (1.0 + sgn * rel_step)\n            sys_.append"),
     ("adjoint-speed-one-sided", "adjoint", "(J[0] - J[1]) / (2.0", "(J[0] - J[1]) / (1.0"),
-    ("adjoint-global-coupling-sign", "adjoint", "M[rows, tp * nb:(tp + 1) * nb] -= Bm[:, cols] @ Ep",
-     "M[rows, tp * nb:(tp + 1) * nb] += Bm[:, cols] @ Ep"),
+    ("adjoint-global-coupling-sign", "adjoint", "M[rows, off[tp]:off[tp + 1]] -= Bm[:, cols] @ Ep",
+     "M[rows, off[tp]:off[tp + 1]] += Bm[:, cols] @ Ep"),
+    ("adjoint-interface-side-sign", "adjoint", "A[blk] += 0.5 * st * (", "A[blk] += 0.5 * ss * ("),
+    ("adjoint-neumann-coupling-sign", "adjoint", "wf, Sn, Vd + beta * Sn", "wf, Sn, -Vd + beta * Sn"),
+    ("adjoint-top-map-sigma-dropped", "adjoint", "Em[j, :, 2:, blk] = St", "Em[j, :, 2:, blk] = 0.0 * St"),
+    ("energy-diss-recovery-dropped", "energy", "(U - fb[:, 0]) * U", "0.0 * U"),
+    ("energy-diss-dirichlet-data-sign", "energy", "gd * (alpha * V - sn)", "gd * (alpha * V + sn)"),
+    ("energy-diss-neumann-data-sign", "energy", "gn * (beta * sn - V)", "gn * (beta * sn + V)"),
+    ("energy-diss-interface-beta-dropped", "energy", "+ beta * dsn * dsn", "+ 0.0 * dsn * dsn"),
+    ("energy-diss-bottom-gradient-sign", "energy", "- 2.0 * dv * (ds @ gb)", "+ 2.0 * dv * (ds @ gb)"),
     ("adjoint-global-stale-front", "adjoint", "            last[K] = (it, Em[j * blk:(j + 1) * blk, :])",
      "            last[K] = last[K] or (it, Em[j * blk:(j + 1) * blk, :])"),
     ("adjoint-transposed-gradient-sign", "adjoint", "y @ (dR @ f0 - dM @ x)", "y @ (dR @ f0 + dM @ x)"),
@@ -146,6 +165,7 @@ def _install(monkeypatch, name, mod):
         return PITCH_PINS
     if name == "energy":
         monkeypatch.setattr(Tz, "energy", mod)
+        monkeypatch.setattr(Dz, "energy", mod)
         return ENERGY_PINS
     if name == "adjoint":
         monkeypatch.setattr(Az, "adjoint", mod)
