@@ -20,7 +20,13 @@ Modules and the passages they follow:
   tdg         - the tent-by-tent sweep: local system eq. (4.1) plus the
                 recovery terms of Section 5, Dirichlet faces from eq. (2.5),
                 LU solve, outflow written at the top points (Section 4.1).
-  energy      - energy E (Section 6.5) and the error functional e (Section 6).
+  energy      - energy E (Section 6.5), the error functional e (Section 6)
+                and each tent's energy loss from eq. (2.5)/(4.1) tested with
+                its own solution.
+  adjoint     - the transposed tent maps, the whole space-time system and
+                the wave-speed gradient through it and by differences.
+  parallel    - the sweep over the independent tents of a level on several
+                processes (the paper's parallel loop over a layer, Section 6).
 
 Parity status: the pins in tests/test_oracle_*.py cover every function;
 "parity unpinned" items are listed in each module header.

@@ -56,9 +56,16 @@ def edge_length(xa, xb) -> float:
     return math.sqrt(s)
 
 
-def pitch(coords: np.ndarray, elems: np.ndarray, c: np.ndarray, kappa: float, T: float):
+def pitch(coords: np.ndarray, elems: np.ndarray, c: np.ndarray, kappa: float, T: float,
+          max_level: int | None = None):
     """Return dict of arrays sorted by (level, round, v):
-    vert, t_bot, t_top, level, round; and n_levels, n_rounds."""
+    vert, t_bot, t_top, level, round; and n_levels, n_rounds.
+
+    max_level: stop the rounds once every vertex's last level is at least
+    max_level and keep the tents of level <= max_level.  A later tent at v
+    has level >= 1 + lam_v, and lam never decreases, so no later round adds
+    a tent of level <= max_level: the result is the first tents of the full
+    pitch, in the same order (n_levels = max_level then)."""
     nv = coords.shape[0]
     ce = mesh_edges(elems, c)
     nbr = [[] for _ in range(nv)]
@@ -77,6 +84,8 @@ def pitch(coords: np.ndarray, elems: np.ndarray, c: np.ndarray, kappa: float, T:
     tents = []            # (level, round, v, t_bot, t_top)
     rnd = 0
     while any(t < T for t in tau):
+        if max_level is not None and min(lam) >= max_level:
+            break
         rnd += 1
         r0 = [v for v in range(nv)
               if tau[v] < T and all(tau[v] <= tau[w] for w in nbr[v])]
@@ -98,6 +107,8 @@ def pitch(coords: np.ndarray, elems: np.ndarray, c: np.ndarray, kappa: float, T:
             lam[v] = level
         tents.extend(new)
 
+    if max_level is not None:
+        tents = [e for e in tents if e[0] <= max_level]
     tents.sort(key=lambda e: (e[0], e[1], e[2]))
     arr = np.array(tents, dtype=object) if tents else np.zeros((0, 5), dtype=object)
     out = {

@@ -130,8 +130,9 @@ MUTATIONS = [
      "cp[c == cm] = cm * (1.0 + sgn * rel_step)\n            F, _ = _tdg.sweep",
      "cp[:] = c * (1.0 + sgn * rel_step)\n            F, _ = _tdg.sweep"),
     ("adjoint-transposed-moves-every-material", "adjoint",
-     "cp[c == cm] = cm * (1.0 + sgn * rel_step)\n            sys_.append",
-     "cp[:] = c * (1.0 + sgn * rel_step)\n            sys_.append"),
+     "cp[c == cm] = cm * (1.0 + j * rel_step)",
+     "cp[:] = c * (1.0 + j * rel_step)"),
+    ("adjoint-transposed-stencil-weight", "adjoint", "(-sys_[2][i] + 8.0 * sys_[1][i]", "(-sys_[2][i] + 7.0 * sys_[1][i]"),
     ("adjoint-speed-one-sided", "adjoint", "(J[0] - J[1]) / (2.0", "(J[0] - J[1]) / (1.0"),
     ("adjoint-global-coupling-sign", "adjoint", "M[rows, off[tp]:off[tp + 1]] -= Bm[:, cols] @ Ep",
      "M[rows, off[tp]:off[tp + 1]] += Bm[:, cols] @ Ep"),

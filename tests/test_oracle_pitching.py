@@ -125,3 +125,21 @@ def test_invariants_2d_heterogeneous():
     m.c[:] = np.where(np.linalg.norm(cen - 0.5, axis=1) < 0.3, 3.0, 1.0)
     r, worst = _replay_and_check(m, inputs.pitch_kappa(m), 0.3)
     assert worst <= 0.9 + 1e-12
+
+
+def test_truncated_pitch_is_a_prefix_of_the_full_pitch():
+    """pitch(..., max_level=L) stops early and returns exactly the tents of
+    level <= L of the full pitch, in the same order (graded inclusion mesh at
+    h_max = 0.05: tents of very different heights, many rounds)."""
+    m = inputs.mesh_inclusion_graded(h_max=0.05)
+    kappa = inputs.pitch_kappa(m)
+    full = pitching.pitch(m.coords, m.elems, m.c, kappa, 0.05)
+    for L in (1, 2, 5):
+        part = pitching.pitch(m.coords, m.elems, m.c, kappa, 0.05, max_level=L)
+        n = int(np.sum(full["level"] <= L))
+        assert len(part["vert"]) == n > 0
+        for key in ("vert", "t_bot", "t_top", "level", "round"):
+            assert np.array_equal(part[key], full[key][:n]), key
+        assert part["n_rounds"] <= full["n_rounds"]
+        if L == 1:
+            assert part["n_rounds"] < full["n_rounds"]
