@@ -1,15 +1,23 @@
 """Benchmark: Trefftz dofs advanced per second for the tent-pitched Trefftz-DG sweep.
 
-Workload (N = 1): the 2+1D FP64 batched case -- unit square, 22x22 jittered
-grid made Delaunay (968 triangles, h ~ 0.045), c = 1, p = 4 (dim U^4 = 25
-unknowns per tent), standing wave cos(sqrt2 pi t) sin(pi x) sin(pi y), T = 1,
-all tents of a level in one launch, the level sweep replayed as a CUDA graph.
-One step = reset the front to the initial data + the full sweep (20216 tents,
-320 levels) with the schedule the library's autotuner picks before timing.
-dofs advanced per step = sum over tents of dim U^p x nrhs.
+Workload (N = 1): the 3+1D many-right-hand-side configuration -- unit cube,
+20^3 jittered hexahedra split into 48 000 tetrahedra (seed 4), c = 1, p = 3
+(dim U^3 = 30 unknowns per tent), 64 seeded Gaussian pulses advanced
+together and sharing every tent's matrix, T = 1 (468 243 tents in 1099
+levels).  One step = reset the front to the 64 initial fields + the full
+sweep (one CUDA graph holding the persistent dataflow sweep kernel).
+dofs advanced per step = sum over tents of dim U^p x 64.
 
---impl reference times the CPU oracle (plain numpy, FP64) on a bounded
-sample of the same workload (the first tents of the sweep).
+`value` is the mixed path (float-float assembly on the binary32 pipes,
+binary32 inverse of the equilibrated tent matrix, refinement to float-float
+accuracy); the binary64 path runs the same workload beside it (`fp64`).
+Each has its roofline against the measured peak of the ALU pipe it runs on.
+The mixed error is given against the binary64 sweep (whole front, all 64
+columns) and against the CPU oracle after the first level (every touched
+front entry of one column).
+
+--impl reference times the CPU oracle (plain numpy, FP64) on the host cores,
+on the tents of the first level (independent tents, split over processes).
 Under torchrun each rank runs an independent replica (no data exchange).
 """
 from __future__ import annotations
@@ -17,12 +25,13 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
 import time
 
-# the CPU baseline reports the cores it uses: keep numpy's BLAS on one thread
+# the oracle's processes each run numpy on one core
 for _var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
     os.environ[_var] = "1"
 
@@ -33,18 +42,16 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Trefftz dofs advanced/s, mixed vs FP64 at rel err ≤1e-8; % of roofline"
 UNIT = "dofs/s"
-WORKLOAD = "standing2d"
-CONFIG = {"workload": "2+1D plain FP64 batched: unit square, 968-triangle seeded jittered-grid "
-                      "Delaunay mesh (h~0.045), c=1, p=4 (25 dofs/tent), standing wave, T=1, "
-                      "layer-parallel tents",
-          "n_elem": 968, "p": 4, "T": 1.0, "nrhs": 1, "precision": "fp64",
-          "l2": "flushed between timed steps (256 MiB write); working set ~1 MB < L2"}
-FP64_PEAK_TFLOPS = 1.25      # nominal GB300 FP64 rate (152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz)
-# DRAM read + write bytes of one binary64 sweep launch of this workload, from the
-# ncu capture summarised in profiles/k_layer_dataflow_standing2d.md, and the
-# kernel source it was taken on
-SWEEP_DRAM_BYTES = 5.153536e6 + 0.393984e6
-SWEEP_DRAM_SOURCE = "ncu capture of k_layer<2,0,0,1,0> at commit d48bde1"
+WORKLOAD = "many_rhs_3d"
+NRHS = 64
+CONFIG = {"workload": "3+1D many-RHS mixed precision: unit cube, 20^3 seeded jittered hexes x 6 tets "
+                      "= 48000 tets, c=1, p=3 (30 dofs/tent), 64 seeded Gaussian pulses sharing the tent "
+                      "matrices, T=1, dataflow sweep in one CUDA graph",
+          "n_elem": 48000, "p": 3, "T": 1.0, "nrhs": NRHS, "precision": "mixed",
+          "l2": "inputs larger than L2: the 64-column front is 7.9 GB against a 129 MB L2"}
+# instructions of one compensated float-float multiply-add of the mixed path
+# (product and its error by fmaf: 4, TwoSum of the running sum: 6, error sum: 2)
+FF_INSTR_PER_FMA = 12
 
 
 def max_over_ranks(x: float, world: int, device: str = "cuda") -> float:
@@ -71,14 +78,15 @@ def _dist():
 
 
 def algorithmic_flops(solver, tents_export, mesh) -> float:
-    """FP64 flops (2 per FMA) of one sweep, counted from the method's operations
-    per tent (patch of P elements, Q front points each, nb = dim U^p):
+    """Flops (2 per multiply-add) of one sweep, counted from the method's
+    operations per tent (patch of P elements, Q front points each,
+    nb = dim U^p, nrhs right-hand sides sharing the tent matrix):
       * basis at the P*Q bottom and P*Q top points, and again at the top points
         for the outflow: monomial chain (nmono - 1) + U-values (nnz of the U
         coefficient table); first derivatives from U-values ((n+1) nb products);
-      * symmetric Gram of (n+2) rows per point: (n+2) nb (nb+1)/2;
+      * symmetric Gram of (n+2) rows per point: (n+2) nb (nb+1)/2 (once per tent);
       * right-hand sides (n+2) nb nrhs per point; outflow (n+2) nb nrhs per point;
-      * LU nb^3/3 and the triangular solves nb^2 nrhs;
+      * LU nb^3/3 (once per tent) and the triangular solves nb^2 nrhs;
       * Dirichlet faces: basis + nb^2 + 3 nb per face point."""
     n, nb, Q, nrhs = solver.dim, solver.basis.nb, solver.Q, solver.nrhs
     C = n + 2
@@ -112,7 +120,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
@@ -144,80 +152,130 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def _cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.TimeoutExpired):
+        pass
+    return platform.processor() or platform.machine()
+
+
+def oracle_level1(nproc: int, single_tents: int):
+    """The oracle as it stands on the first level of the workload's sweep
+    (column 0): the level's tents are independent, so they run split over
+    nproc processes (oracle.parallel); and one process alone on the first
+    single_tents tents.  Returns (all-core record, single-thread record,
+    oracle front after level 1, the level-1 tent list)."""
+    from paper_1907_02367_gb300 import inputs
+    from oracle import parallel, pitching, tdg
+    w = inputs.workload(WORKLOAD)
+    m = w.mesh
+    r = pitching.pitch(m.coords, m.elems, m.c, w.kappa, w.T, max_level=1)
+    lay = tdg.front_layout(m.coords, m.elems, w.p)
+    pulse = inputs.gaussian_pulses_3d()[0]
+    f0 = np.asarray(pulse(lay.xq.reshape(-1, 3))).reshape(lay.wq.shape + (5,))
+    nt = len(r["vert"])
+    nb = 30
+    t0 = time.perf_counter()
+    F, tau, done = parallel.sweep_levels(m.coords, m.elems, m.c, w.p, r, f0, 1, nproc=nproc)
+    dt_all = time.perf_counter() - t0
+    n1 = min(single_tents, nt)
+    t0 = time.perf_counter()
+    tdg.sweep(m.coords, m.elems, m.c, w.p, r, None, front0=f0, tent_range=(0, n1))
+    dt_one = time.perf_counter() - t0
+    model = _cpu_model()
+    all_core = {"value": done * nb / dt_all, "unit": UNIT, "cores": nproc, "kind": "oracle",
+                "sample": f"the {done} independent tents of level 1 of column 0, split over {nproc} "
+                          f"processes ({dt_all:.1f} s wall, numpy FP64, one thread each; {model})"}
+    single = {"value": n1 * nb / dt_one, "unit": UNIT, "cores": 1, "kind": "oracle",
+              "sample": f"the first {n1} tents of level 1 of column 0 in one process ({dt_one:.1f} s, "
+                        f"numpy FP64, one thread; {model})"}
+    return all_core, single, F, r
+
+
 def run_ours(args, rank, world, local):
     import torch
     import torch.distributed as dist
     import paper_1907_02367_gb300 as pkg
     from paper_1907_02367_gb300 import inputs
 
+    # the CPU legs first: the oracle's process pool starts before any GPU use
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        nproc = os.cpu_count() or 1
+        cpu = oracle_level1(nproc, args.cpu_tents)
+
     torch.cuda.set_device(local)
     w = inputs.workload(WORKLOAD)
     m = w.mesh
-    solver = pkg.Solver(m.coords, m.elems, m.c, w.p, w.T, w.kappa)
-    xq, _ = solver.front_points()
-    front0_host = torch.tensor(w.init(xq), dtype=torch.float64).reshape(solver.front_shape())
-    front0_host = front0_host.contiguous().pin_memory()
-    front0 = front0_host.to("cuda")
-    out_host = torch.empty(solver.front_shape(), dtype=torch.float64).pin_memory()
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    pulses = inputs.gaussian_pulses_3d()
+    fp64_peak, fp32_peak = pkg.measure_alu_peaks()
+    ff_peak = fp32_peak / FF_INSTR_PER_FMA        # float-float multiply-adds at the binary32 pipe's rate
+    tents = pkg.Tents(m.coords, m.elems, m.c, w.kappa, w.T)
+    te = tents.export()
     stream = torch.cuda.current_stream()
+
+    def make(precision):
+        return pkg.Solver(m.coords, m.elems, m.c, w.p, w.T, w.kappa, nrhs=NRHS, precision=precision,
+                          tents=tents, rhs_split=args.rhs_split)
+
+    solver = make("mixed")
+    xq, _ = solver.front_points()
+    front0_host = torch.empty(solver.front_shape(), dtype=torch.float64).pin_memory()
+    for r in range(NRHS):
+        front0_host[r].copy_(torch.from_numpy(np.ascontiguousarray(pulses[r](xq))).reshape(front0_host.shape[1:]))
+    front0 = front0_host.to("cuda")
     dofs = solver.dofs_per_sweep()
-    te = solver.tents.export()
-    # schedule chosen by the library's autotuner (outside the timed region)
-    solver.set_state(front0)
-    chosen, tune_ms = (4, 0.0) if args.no_autotune else solver.autotune()
-    # kernels per step: dataflow = sweep set-up + one persistent sweep kernel;
-    # per-level schedule = one launch per level
-    n_launch = 2 if chosen > 0 else solver.n_levels
-
-    def step():
-        solver.set_state(front0)
-        solver.advance()
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    st, info = solver.sync_status()
-    if st != 0:
-        raise RuntimeError(f"device status {st} at tent {info}")
+    flops = algorithmic_flops(solver, te, m)
 
     def barrier():
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
 
+    def timed_sweeps(s, steps, warmup):
+        for _ in range(warmup):
+            s.set_state(front0)
+            s.advance()
+        torch.cuda.synchronize()
+        st = s.sync_status()
+        if st[0] != 0:
+            raise RuntimeError(f"device status {st[0]} at tent {st[1]}")
+        barrier()
+        total = sweep = 0.0
+        for _ in range(steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            em = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.set_state(front0)
+            em.record(stream)
+            s.advance()
+            e1.record(stream)
+            e1.synchronize()
+            total += e0.elapsed_time(e1)
+            sweep += em.elapsed_time(e1)
+        barrier()
+        return max_over_ranks(total, world) / steps, max_over_ranks(sweep, world) / steps
+
     clocks = ClockSampler(local)
     clocks.start()
-    barrier()
-    total_ms = 0.0
-    sweep_ms = 0.0                          # the sweep kernel(s) alone, for the roofline
-    for _ in range(args.steps):
-        flush.zero_()                       # L2 flush outside the events
-        e0 = torch.cuda.Event(enable_timing=True)
-        em = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        solver.set_state(front0)
-        em.record(stream)
-        solver.advance()
-        e1.record(stream)
-        e1.synchronize()
-        total_ms += e0.elapsed_time(e1)
-        sweep_ms += em.elapsed_time(e1)
-    barrier()
+    ms_step, ms_sweep = timed_sweeps(solver, args.steps, args.warmup)
     clk = clocks.stop()
-    total_ms = max_over_ranks(total_ms, world)
-    sweep_ms = max_over_ranks(sweep_ms, world)
-    ms_step = total_ms / args.steps
-    ms_sweep = sweep_ms / args.steps
+    mixed_front, _ = solver.get_state()
+    st_mixed = solver.sync_status()
 
-    # end to end through the public API with host buffers: H2D of the initial
-    # front from pinned memory, sweep, D2H of the final front, every step
+    # end to end through the public API with host buffers: H2D of the 64
+    # initial fields from pinned memory, the sweep, D2H of the final front
+    out_host = torch.empty(solver.front_shape(), dtype=torch.float64).pin_memory()
     front_dev = torch.empty_like(front0)
+    e2e_steps = min(args.steps, args.e2e_steps)
     barrier()
     e_ms = 0.0
-    for _ in range(args.steps):
-        flush.zero_()
+    for _ in range(e2e_steps):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -230,121 +288,116 @@ def run_ours(args, rank, world, local):
         e1.synchronize()
         e_ms += e0.elapsed_time(e1)
     barrier()
-    e_ms = max_over_ranks(e_ms, world)
-    e_step = e_ms / args.steps
+    e_step = max_over_ranks(e_ms, world) / e2e_steps
     nbytes = front0.numel() * 8
+    del out, front_dev
 
-    flops = algorithmic_flops(solver, te, m)
-    achieved = flops / (ms_sweep * 1e-3) / 1e12
-    # the mixed-precision path on the same workload (float-float assembly,
-    # binary32 factorisation + refinement): dofs/s and its error against this
-    # run's binary64 front (which the tests hold within 1e-11 of the oracle)
-    mixed = None
-    if not args.no_mixed:
-        ref_front, _ = solver.get_state()
-        ref_front = ref_front.clone()
-        ms_solver = pkg.Solver(m.coords, m.elems, m.c, w.p, w.T, w.kappa, precision="mixed")
-        ms_solver.set_state(front0)
-        if not args.no_autotune:
-            ms_solver.autotune()
-        for _ in range(args.warmup):
-            ms_solver.set_state(front0)
-            ms_solver.advance()
-        torch.cuda.synchronize()
-        mx_ms = 0.0
-        for _ in range(args.steps):
-            flush.zero_()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            ms_solver.set_state(front0)
-            ms_solver.advance()
-            e1.record(stream)
-            e1.synchronize()
-            mx_ms += e0.elapsed_time(e1)
-        mst = ms_solver.sync_status()
-        mfront, _ = ms_solver.get_state()
-        rel = float(torch.linalg.norm(mfront - ref_front) / torch.linalg.norm(ref_front))
-        mixed = {"value": whole_job_rate(dofs, world, mx_ms / args.steps), "unit": UNIT,
-                 "ms_per_step": mx_ms / args.steps, "rel_err_vs_fp64": rel, "status": mst[0]}
+    # the binary64 path on the same workload, and the mixed error against it
+    fp64 = None
+    if not args.no_fp64:
+        s64 = make("fp64")
+        ms64_step, ms64_sweep = timed_sweeps(s64, args.fp64_steps, 1)
+        f64_front, _ = s64.get_state()
+        rel_vs_fp64 = float(torch.linalg.norm(mixed_front - f64_front) / torch.linalg.norm(f64_front))
+        ach64 = flops / (ms64_sweep * 1e-3) / 1e12
+        fp64 = {"value": whole_job_rate(dofs, world, ms64_step), "unit": UNIT, "ms_per_step": ms64_step,
+                "steps": args.fp64_steps, "warmup": 1, "status": s64.sync_status()[0],
+                "roofline": {"bound": "alu", "achieved": ach64, "peak": fp64_peak, "unit": "TFLOP/s",
+                             "frac": ach64 / fp64_peak, "traffic": None,
+                             "kernel": "k_layer<3, binary64, dataflow> (tp_kernel.cuh)",
+                             "note": "algorithmic flops / mean sweep duration; peak = binary64 "
+                                     "multiply-add rate measured by tp_measure_alu_peaks on this GPU"}}
+        mixed_front_rel = rel_vs_fp64
+        del s64, f64_front
+    else:
+        mixed_front_rel = None
+
+    # mixed and binary64 against the CPU oracle after level 1 (column 0, every touched entry)
+    vs_oracle = None
+    if cpu is not None:
+        F_ref, r1 = cpu[2], cpu[3]
+        from oracle import tdg as otdg
+        star = otdg.vertex_star(m.elems, m.n_vert)
+        touched = np.array(sorted({k for v in r1["vert"] for k in star[int(v)]}))
+        vs_oracle = {"levels": 1, "column": 0, "touched_elements": int(len(touched))}
+        for precision in ("mixed", "fp64"):
+            s1 = make(precision)
+            s1.set_state(front0)
+            s1.advance(1, 2)
+            g, _ = s1.get_state()
+            g0 = g[0].cpu().numpy()[touched]
+            vs_oracle[precision] = float(np.linalg.norm(g0 - F_ref[touched]) / np.linalg.norm(F_ref[touched]))
+            del s1, g
+
+    ach = flops / (ms_sweep * 1e-3) / 1e12
     result = {
         "metric": METRIC, "value": whole_job_rate(dofs, world, ms_step), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic (seeded mesh, closed-form standing wave)",
-        "config": dict(CONFIG, parallelism=f"replicas{world}", n_tents=solver.tents.n_tents,
-                       n_levels=solver.n_levels, dofs_per_step=dofs,
-                       schedule=("dataflow, clusters of %d CTAs" % chosen) if chosen > 0 else "one launch per level"),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32x2 (float-float)",
+        "data": "synthetic (seeded mesh, 64 seeded Gaussian pulses)",
+        "config": dict(CONFIG, parallelism=f"replicas{world}", n_tents=tents.n_tents,
+                       n_levels=tents.n_levels, dofs_per_step=dofs,
+                       schedule=solver.schedule()),
         "e2e": {"value": whole_job_rate(dofs, world, e_step), "unit": UNIT,
-                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
-        "gpu_launches": n_launch * args.steps,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": SWEEP_DRAM_BYTES,
-                     "traffic_source": SWEEP_DRAM_SOURCE,
-                     "kernel": "k_layer<dim 2, binary64> (tp_kernel.cuh)",
+                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "steps": e2e_steps},
+        "gpu_launches": 2 * args.steps,
+        "roofline": {"bound": "alu", "achieved": ach, "peak": ff_peak, "unit": "TFLOP/s",
+                     "frac": ach / ff_peak, "traffic": None,
+                     "kernel": "k_layer<3, float-float, dataflow> (tp_kernel.cuh)",
                      "sweep_ms": ms_sweep,
-                     "note": "algorithmic FP64 flops of one sweep / mean duration of the sweep "
-                             "(events around tp_advance on its stream: the sweep kernel and its "
-                             "set-up kernel); peak = GB300 FP64, 152 SMs x 2 DFMA/clk x 2 flop "
-                             "x 2.07 GHz"},
+                     "note": "algorithmic flops of one sweep / mean duration of the sweep (events "
+                             "around tp_advance on its stream: the sweep kernel and its set-up "
+                             "kernel); peak = the float-float multiply-add rate, the binary32 "
+                             f"multiply-add peak measured by tp_measure_alu_peaks ({fp32_peak:.1f} "
+                             f"TFLOP/s) / {FF_INSTR_PER_FMA} binary32 instructions per compensated "
+                             "multiply-add"},
         "clocks": clk,
-        "mixed": mixed,
+        "mixed_status": st_mixed[0],
+        "mixed_rel_err_vs_fp64": mixed_front_rel,
+        "rel_err_vs_oracle": vs_oracle,
+        "fp64": fp64,
+        "measured_alu_peaks_tflops": {"fp64": fp64_peak, "fp32": fp32_peak},
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        result["cpu_baseline"] = cpu_baseline(args.cpu_tents)
+    if cpu is not None:
+        result["cpu_baseline"] = cpu[0]
+        result["cpu_baseline_single_thread"] = cpu[1]
     return result
-
-
-def cpu_baseline(n_tents: int):
-    """The oracle, as it stands, on the host cores: the first n_tents of the
-    same sweep (bounded sample)."""
-    from paper_1907_02367_gb300 import inputs
-    from oracle import pitching, tdg
-    w = inputs.workload(WORKLOAD)
-    m = w.mesh
-    r = pitching.pitch(m.coords, m.elems, m.c, w.kappa, w.T)
-    n = min(n_tents, len(r["vert"]))
-    t0 = time.perf_counter()
-    tdg.sweep(m.coords, m.elems, m.c, w.p, r, w.init, None, tent_range=(0, n))
-    dt = time.perf_counter() - t0
-    nb = (w.p + 1) ** 2
-    return {"value": n * nb / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"first {n} of {len(r['vert'])} tents of the same sweep ({dt:.1f} s, numpy FP64, 1 thread)"}
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return None
+    nproc = os.cpu_count() or 1
     vals = []
-    for _ in range(args.warmup):
-        cpu_baseline(max(50, args.cpu_tents // 20))
-    samples = []
-    for _ in range(args.steps):
-        cb = cpu_baseline(args.cpu_tents)
-        vals.append(cb["value"])
-        samples.append(cb)
-    v = statistics.median(vals)
-    cb = dict(samples[0], value=v)
+    cb = None
+    for i in range(args.warmup + args.steps):
+        all_core, single, _, _ = oracle_level1(nproc, max(8, args.cpu_tents // 4))
+        if i >= args.warmup:
+            vals.append(all_core["value"])
+            cb = all_core
+    v = statistics.median(vals) if vals else None
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": None,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic (seeded mesh, closed-form standing wave)",
+            "data": "synthetic (seeded mesh, 64 seeded Gaussian pulses)",
             "config": dict(CONFIG, parallelism="cpu-oracle"),
-            "cpu_baseline": cb,
+            "cpu_baseline": dict(cb, value=v) if cb else None,
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--cpu-tents", type=int, default=8000)
+    ap.add_argument("--cpu-tents", type=int, default=200,
+                    help="tents of the single-thread oracle sample")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--rhs-split", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-autotune", action="store_true",
-                    help="keep the default schedule (dataflow sweep) instead of tuning it")
-    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
     args = ap.parse_args()
     rank, world, local = _dist()
     if args.impl == "reference":

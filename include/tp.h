@@ -91,6 +91,25 @@ typedef struct tp_params {
   int32_t precision;
   int32_t nrhs;
   int32_t schedule;
+  /* rhs_split: how a tent's right-hand sides are shared out over the CTAs of
+   * its cluster.  0 = automatic (split when each CTA keeps 16 or more,
+   * i.e. nrhs >= 32 and divisible by 2, 4 or 8), 1 = never split
+   * (every CTA takes a slice of the points for all right-hand sides), 2, 4
+   * or 8 = that many CTAs, each owning nrhs / rhs_split of the right-hand
+   * sides at every point of the tent (data moments, solve and outflow),
+   * while the tent matrix is assembled once, its points split over the
+   * same CTAs.  A value that does not divide nrhs is TP_ERR_ARG. */
+  int32_t rhs_split;
+  /* dissipation: 1 = every forward tent adds the energy it loses,
+   *   D = 1/2 int_bot Q(u - u_b) + int_bot (U - U_b) U + the Dirichlet, Neumann
+   *   and interface terms of eq. (2.5)/(4.1) tested with its own solution,
+   * to a per-right-hand-side sum reported by tp_energy (an extra pass over
+   * the tent's bottom and vertical-face points); 0 = not tracked. */
+  int32_t dissipation;
+  /* ckpt_stride: levels between the forward checkpoints tp_adjoint keeps
+   * for the wave-speed gradient; 0 = the context does not compute it (> 0
+   * also keeps a copy of the initial front at every tp_set_state). */
+  int32_t ckpt_stride;
 } tp_params;
 
 typedef struct tp_tents tp_tents;
@@ -146,6 +165,14 @@ int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const tp_basis* b
  * quadrature points over all tents, n_levels. */
 int tp_ctx_info(const tp_ctx* ctx, int64_t* n_front, int32_t* n_comp, int64_t* n_bnd,
                 int32_t* n_levels);
+/* How tp_advance runs this context (chosen by tp_create or tp_autotune):
+ * *dataflow = 1 for the persistent dataflow sweep, 0 for one launch per
+ * level; *cluster = CTAs per tent (the largest, per level, with one launch
+ * per level); *rhs_split = CTAs a tent's right-hand sides are split over
+ * (1: not split); *rhs_groups = groups of right-hand sides swept one after
+ * the other.  Any pointer may be NULL. */
+int tp_ctx_schedule(const tp_ctx* ctx, int32_t* dataflow, int32_t* cluster, int32_t* rhs_split,
+                    int32_t* rhs_groups);
 /* Front points (Section 4.1: one spatial rule mapped onto the faces):
  * host arrays xq (n_front x dim) and wq (n_front) physical weights. */
 int tp_front_points(const tp_ctx* ctx, double* xq, double* wq);
@@ -162,6 +189,31 @@ int tp_boundary_kinds(const tp_ctx* ctx, double* nrm, int8_t* kind);
  * tp_boundary_points: g_D or g_N by the facet's kind; NULL for zero data).  Both are
  * copied; the front times are reset to 0.  Asynchronous on `stream`. */
 int tp_set_state(tp_ctx* ctx, const double* d_front, const double* d_gD, void* stream);
+/* Resumes a sweep: copies a front (device, front layout) and the vertex
+ * front times (device, n_vert doubles) into the context, e.g. the state
+ * tp_get_state returned after some levels, so that tp_advance can continue
+ * from the next level.  Boundary data, status and counters are kept. */
+int tp_set_front(tp_ctx* ctx, const double* d_front, const double* d_tau, void* stream);
+/* Bounds of the device-side loops (defaults for values <= 0, resp. < 0):
+ * max_polls, the polls of a dependency wait of the dataflow sweep before it
+ * reports TP_ERR_TIMEOUT (default 2^20, well under a second); max_refine,
+ * the refinement steps after which a tent's solve falls back to the direct
+ * binary64 LU (default 40; 0 sends every tent to the LU).  Drops the
+ * context's captured graphs. */
+int tp_set_limits(tp_ctx* ctx, int64_t max_polls, int32_t max_refine);
+/* Failure injection for testing the bounded waits (the paper has no
+ * counterpart): from now on tent `tent` of the sorted list waits for `extra`
+ * more completions of each vertex it depends on than will ever come, so the
+ * next dataflow sweep's wait runs out (TP_ERR_TIMEOUT through
+ * tp_sync_status, first failing tent = `tent`; the other waits stop once the
+ * error is flagged).  extra = 0 restores the true counts.  TP_ERR_ARG if the
+ * tent waits for no earlier tent. */
+int tp_inject_wait(tp_ctx* ctx, int64_t tent, int32_t extra);
+/* Solve statistics since tp_set_state (synchronises the context's last
+ * stream): *direct_lu = tents solved by the direct binary64 LU because their
+ * refinement did not settle (or max_refine is 0); hist[k] = tents whose
+ * refinement settled after k steps, k < nhist (steps beyond 40 are 0). */
+int tp_solve_stats(tp_ctx* ctx, int64_t* direct_lu, int64_t* hist, int32_t nhist);
 /* Solves every tent of one level (1-based) of the sorted tent list:
  * assembly of eq. (4.1) with the Section 5 recovery terms (and the
  * interface terms of eq. 2.5 on multi-material tents), LU solve in the
@@ -185,18 +237,44 @@ int tp_autotune(tp_ctx* ctx, void* stream, int32_t* chosen, double* best_ms);
 /* Energy flux through the current front (Section 6.5 energy generalised to
  * a front t = tau(x)):  E_r = 1/2 sum_K sum_q w_q (c_K^-2 v^2 + |sigma|^2
  * - 2 v sigma.grad tau_K) for every rhs r; equals the paper's E on a flat
- * front.  d_out: device array of nrhs doubles. */
+ * front.  And the energy the tents swept since tp_set_state have lost,
+ * D_r = sum over tents of 1/2 int_bot Q(u - u_b) + int_bot (U - U_b) U
+ * + int_D [alpha v^2 - g_D (alpha v - sigma.n)] + int_N [beta (sigma.n)^2
+ * - g_N (beta sigma.n - v)] + int_time [alpha [[v]]^2 + beta [[sigma]]_N^2]
+ * (eq. 2.5 and eq. 4.1 tested with each tent's own solution, Section 6.5),
+ * accumulated in binary64 when the context was created with
+ * tp_params.dissipation = 1, else 0.  The method conserves energy inside
+ * each Trefftz tent, so E_r(now) = E_r(t = 0) - D_r.
+ * d_out: device array of 2 nrhs doubles, (E_r, D_r) for r = 0 .. nrhs-1. */
 int tp_energy(tp_ctx* ctx, double* d_out, void* stream);
-/* Adjoint sweep.  With the tents fixed and g_D = 0 the sweep is a linear map
- * F: front(t = 0) -> front(T), a composition of the tent maps
- * b = B f_bot, A x = b, f_top = E x of eq. (4.1) with the Section 5 recovery
- * terms.  tp_adjoint applies F^* tent by tent in reverse level order
- * (mu = A^-T E^T lambda_top, lambda_bot = B^T mu), in binary64:
- * d_lambda_T (device, front layout, nrhs sets) is the gradient of a
- * functional with respect to the final front, d_lambda_0 (device, same
- * layout) receives its gradient with respect to the initial front.  The
- * forward state is not touched; the reverse sweep is one CUDA graph. */
-int tp_adjoint(tp_ctx* ctx, const double* d_lambda_T, double* d_lambda_0, void* stream);
+/* Adjoint sweep (the paper has none; it differentiates the method of
+ * Section 4).  With the tents fixed, the sweep maps the initial front to
+ * the final one through the tent maps b = B f_bot (+ boundary data),
+ * A x = b, f_top = E x of eq. (4.1) with the Section 5 recovery terms, so a
+ * functional J of the final front with gradient d_lambda_T (device, front
+ * layout, nrhs sets) has
+ *   d_lambda_0 (device, same layout): dJ/d(initial front), F^* applied tent
+ *     by tent in reverse level order (mu = A^-T E^T lambda_top,
+ *     lambda_bot = B^T mu), binary64;
+ *   d_dJ_dc (device, n_elem doubles, or NULL): dJ/dc, c the wave speed, with
+ *     the tents held fixed: every tent adds
+ *       lambda_top . (dE/dc) x + mu^T ((dB/dc) f_bot - (dA/dc) x),
+ *     evaluated at its points through dF/dc = ((t - t_c)/c) F(x') + (0, v/c, 0),
+ *     x' = (c/h) D_t^T x (Remark 3.1: the basis of a material moves with its
+ *     speed through t^ = c (t - t_c)/h); summed over the right-hand sides.
+ *     Entry K holds the terms of element K's points (and of its facets): for
+ *     a material of several elements (bitwise-equal c) their sum is dJ/dc of
+ *     that material; with one speed per element it is dJ/dc_K.  The forward
+ *     solutions come from sweeping again from the initial state of the last
+ *     tp_set_state (the boundary data set there count as fixed), keeping a
+ *     checkpoint every tp_params.ckpt_stride levels and recomputing one
+ *     segment at a time.  Needs a context created with ckpt_stride > 0
+ *     (TP_ERR_ARG otherwise) and every right-hand side in one group
+ *     (TP_ERR_UNSUPPORTED otherwise); allocates its checkpoints on first use
+ *     (TP_ERR_OOM).
+ * The forward state is not touched.  Without d_dJ_dc the reverse sweep is
+ * one CUDA graph. */
+int tp_adjoint(tp_ctx* ctx, const double* d_lambda_T, double* d_dJ_dc, double* d_lambda_0, void* stream);
 /* Copies the front (device, front layout) and/or the vertex front times
  * (device, n_vert doubles); either may be NULL. */
 int tp_get_state(const tp_ctx* ctx, double* d_front, double* d_tau, void* stream);
@@ -208,6 +286,14 @@ int tp_get_state(const tp_ctx* ctx, double* d_front, double* d_tau, void* stream
  * sorted list.  The first error wins; tp_set_state clears it. */
 int tp_sync_status(tp_ctx* ctx, int32_t* status, int64_t* info);
 void tp_destroy_ctx(tp_ctx* ctx);
+
+/* Measured arithmetic peaks of the current GPU's plain ALUs (the paper has
+ * no counterpart; the rooflines of the tent sweep use them): independent
+ * chains of binary64 and binary32 fused multiply-adds on every SM, timed
+ * with events (best of three after a warm-up launch), 2 flops per fused
+ * multiply-add.  *fp64_tflops, *fp32_tflops in TFLOP/s.  Allocates a small
+ * scratch array; synchronises `stream`. */
+int tp_measure_alu_peaks(double* fp64_tflops, double* fp32_tflops, void* stream);
 
 /* Allocation-free variant of tp_energy for callers that may not allocate
  * device memory at that point (a framework that has reserved the free device

@@ -4,8 +4,8 @@ wave equation (Perugia, Schoberl, Stocker, Wintersteiger).
 The numerics run in libtp (C ABI, include/tp.h): host C++ for pitching and
 tables, hand-written sm_103a CUDA kernels for the layer-by-layer tent solve.
 This package is the thin Python layer over it: `Tents`, `Basis` and `Solver`
-mirror tp_pitch_mesh / tp_build_basis / tp_create ... tp_energy; `TentSweep`
-and `speed_gradient` differentiate the sweep.  `inputs` builds the seeded
+mirror tp_pitch_mesh / tp_build_basis / tp_create ... tp_energy; `TentSweep` and
+`Solver.speed_gradient` differentiate the sweep (tp_adjoint).  `inputs` builds the seeded
 workloads; `lshape` and `energy_study` run the studies of Section 6.
 """
 from __future__ import annotations
@@ -16,12 +16,20 @@ import numpy as np
 
 from . import _binding as B
 
-__all__ = ["Tents", "Basis", "Solver", "TentSweep", "speed_gradient", "pitch_mesh", "build_basis",
-           "load_library"]
+__all__ = ["Tents", "Basis", "Solver", "TentSweep", "pitch_mesh", "build_basis", "load_library",
+           "measure_alu_peaks"]
 
 
 def load_library():
     return B.load()
+
+
+def measure_alu_peaks(stream=None):
+    """tp_measure_alu_peaks: measured (binary64, binary32) fused multiply-add
+    peaks of the current GPU in TFLOP/s."""
+    f64, f32 = ct.c_double(), ct.c_double()
+    B.check(B.load().tp_measure_alu_peaks(ct.byref(f64), ct.byref(f32), B.stream_ptr(stream)))
+    return float(f64.value), float(f32.value)
 
 
 class Tents:
@@ -102,7 +110,14 @@ class Solver:
     facet opposite local vertex o of element k as Neumann (sigma.n = g_N),
     else Dirichlet; boundary_kinds() tells which data each boundary point
     takes.  nrhs right-hand sides share the tents and their matrices (in
-    groups when one CTA cannot hold all of them).  tents: a Tents object to
+    groups when one CTA cannot hold all of them); rhs_split: 0 picks how a
+    tent's right-hand sides are shared out over the CTAs of its cluster, 1
+    keeps them together, 2/4/8 gives each CTA that fraction of them
+    (tp_params.rhs_split).  track_dissipation: every tent adds the energy it
+    loses (the jump terms of eq. 2.5) to a sum that energy_and_dissipation()
+    reports.  ckpt_stride: levels between the forward checkpoints of the
+    wave-speed gradient (adjoint(..., dJ_dc=...)); 0 = no gradient with
+    respect to c.  tents: a Tents object to
     sweep over instead of pitching the mesh with c (the wave speeds always
     come from c; see speed_gradient).  All device memory handed to libtp is
     torch CUDA float64 memory; the current torch stream is passed to every
@@ -110,7 +125,8 @@ class Solver:
 
     def __init__(self, coords, elems, c, p: int, T: float, kappa: float, alpha: float = 0.5,
                  nrhs: int = 1, tents: Tents | None = None, precision: str = "fp64",
-                 schedule: str = "dataflow", bnd_type=None, beta: float = 0.5):
+                 schedule: str = "dataflow", bnd_type=None, beta: float = 0.5, rhs_split: int = 0,
+                 track_dissipation: bool = False, ckpt_stride: int = 0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("libtp Solver needs a CUDA device")
@@ -126,7 +142,8 @@ class Solver:
         self.params = B.make_params(p, T, kappa, alpha=alpha, beta=beta, nrhs=nrhs,
                                     precision=B.TP_FP64 if precision == "fp64" else B.TP_MIXED,
                                     schedule=B.TP_SCHED_DATAFLOW if schedule == "dataflow"
-                                    else B.TP_SCHED_LEVELS)
+                                    else B.TP_SCHED_LEVELS, rhs_split=rhs_split,
+                                    dissipation=1 if track_dissipation else 0, ckpt_stride=ckpt_stride)
         h = ct.c_void_p()
         B.check(lib.tp_create(ct.byref(self._mesh.desc), self.tents.handle, self.basis.handle,
                               ct.byref(self.params), ct.byref(h)))
@@ -178,6 +195,31 @@ class Solver:
             gptr = B.tensor_ptr(gD)
         B.check(B.load().tp_set_state(self.handle, B.tensor_ptr(front), gptr, B.stream_ptr(stream)))
 
+    def set_front(self, front, tau, stream=None):
+        """tp_set_front: resume from a front and its vertex times (e.g. what
+        get_state returned after some levels)."""
+        import torch
+        assert front.is_cuda and front.dtype == torch.float64 and front.is_contiguous()
+        assert front.numel() == self.nrhs * self.n_front * self.n_comp
+        assert tau.is_cuda and tau.dtype == torch.float64 and tau.is_contiguous()
+        assert tau.numel() == self._mesh.coords.shape[0]
+        B.check(B.load().tp_set_front(self.handle, B.tensor_ptr(front), B.tensor_ptr(tau), B.stream_ptr(stream)))
+
+    def set_limits(self, max_polls: int = 0, max_refine: int = -1):
+        """tp_set_limits: dependency-wait polls and refinement steps (defaults for 0 / -1)."""
+        B.check(B.load().tp_set_limits(self.handle, int(max_polls), int(max_refine)))
+
+    def inject_wait(self, tent: int, extra: int):
+        """tp_inject_wait: make tent `tent` wait for completions that never come (testing)."""
+        B.check(B.load().tp_inject_wait(self.handle, int(tent), int(extra)))
+
+    def solve_stats(self, nhist: int = 41):
+        """tp_solve_stats: (tents solved by the direct LU, histogram of refinement steps)."""
+        lu = ct.c_int64()
+        hist = np.zeros(nhist, np.int64)
+        B.check(B.load().tp_solve_stats(self.handle, ct.byref(lu), hist.ctypes.data, int(nhist)))
+        return int(lu.value), hist
+
     def solve_layer(self, level: int, stream=None):
         B.check(B.load().tp_solve_layer(self.handle, int(level), B.stream_ptr(stream)))
 
@@ -186,16 +228,35 @@ class Solver:
             level_end = self.n_levels + 1
         B.check(B.load().tp_advance(self.handle, int(level_begin), int(level_end), B.stream_ptr(stream)))
 
-    def adjoint(self, lam_T, out=None, stream=None):
+    def adjoint(self, lam_T, out=None, dJ_dc=None, stream=None):
         """Gradient with respect to the initial front of a functional whose
-        gradient with respect to the final front is lam_T (tp_adjoint)."""
+        gradient with respect to the final front is lam_T (tp_adjoint).
+        dJ_dc: optional CUDA float64 tensor of n_elem entries that receives
+        the gradient with respect to the wave speed (per element; summed over
+        a material's elements it is dJ/dc of the material), computed in the
+        same reverse sweep from the initial state of the last set_state (the
+        solver must be created with ckpt_stride > 0)."""
         import torch
         assert lam_T.is_cuda and lam_T.dtype == torch.float64 and lam_T.is_contiguous()
         assert lam_T.numel() == self.nrhs * self.n_front * self.n_comp
         if out is None:
             out = torch.empty(self.front_shape(), dtype=torch.float64, device="cuda")
-        B.check(B.load().tp_adjoint(self.handle, B.tensor_ptr(lam_T), B.tensor_ptr(out), B.stream_ptr(stream)))
+        gptr = None
+        if dJ_dc is not None:
+            assert dJ_dc.is_cuda and dJ_dc.dtype == torch.float64 and dJ_dc.is_contiguous()
+            assert dJ_dc.numel() == self.n_elem
+            gptr = B.tensor_ptr(dJ_dc)
+        B.check(B.load().tp_adjoint(self.handle, B.tensor_ptr(lam_T), gptr, B.tensor_ptr(out),
+                                    B.stream_ptr(stream)))
         return out
+
+    def speed_gradient(self, lam_T, stream=None):
+        """dJ/dc per element (CUDA float64, n_elem) of J = <lam_T, front(T)>
+        from the initial state of the last set_state (tp_adjoint)."""
+        import torch
+        g = torch.empty(self.n_elem, dtype=torch.float64, device="cuda")
+        self.adjoint(lam_T, dJ_dc=g, stream=stream)
+        return g
 
     def autotune(self, stream=None):
         """tp_autotune: pick the sweep schedule (one launch per level, or the
@@ -206,10 +267,17 @@ class Solver:
         B.check(B.load().tp_autotune(self.handle, B.stream_ptr(stream), ct.byref(c), ct.byref(ms)))
         return int(c.value), float(ms.value)
 
-    def energy(self, out=None, stream=None):
+    def energy(self, stream=None):
+        """Energy flux through the current front per right-hand side (nrhs,)."""
+        return self.energy_and_dissipation(stream=stream)[:, 0]
+
+    def energy_and_dissipation(self, out=None, stream=None):
+        """tp_energy: (nrhs, 2) CUDA tensor, column 0 the energy flux through
+        the current front, column 1 the energy the swept tents lost since
+        set_state (zero unless the solver tracks it, track_dissipation=True)."""
         import torch
         if out is None:
-            out = torch.empty(self.nrhs, dtype=torch.float64, device="cuda")
+            out = torch.empty((self.nrhs, 2), dtype=torch.float64, device="cuda")
         B.check(B.load().tp_energy(self.handle, B.tensor_ptr(out), B.stream_ptr(stream)))
         return out
 
@@ -228,9 +296,24 @@ class Solver:
         B.check(B.load().tp_sync_status(self.handle, ct.byref(s), ct.byref(i)))
         return int(s.value), int(i.value)
 
+    def schedule(self) -> dict:
+        """tp_ctx_schedule: dataflow (bool), cluster (CTAs per tent),
+        rhs_split (CTAs the right-hand sides are split over), rhs_groups."""
+        v = [ct.c_int32() for _ in range(4)]
+        B.check(B.load().tp_ctx_schedule(self.handle, *[ct.byref(x) for x in v]))
+        return {"dataflow": bool(v[0].value), "cluster": int(v[1].value), "rhs_split": int(v[2].value),
+                "rhs_groups": int(v[3].value)}
+
     def dofs_per_sweep(self) -> int:
-        """Trefftz dofs advanced by one full sweep: sum over tents of dim U^p, times nrhs."""
-        return self.tents.n_tents * self.basis.nb * self.nrhs
+        """Trefftz dofs advanced by one full sweep: sum over tents of (materials
+        of the tent) x dim U^p, times nrhs (Section 4.2: one polynomial per
+        material of the tent's patch)."""
+        el = self._mesh.elems
+        pairs = np.stack([el.reshape(-1).astype(np.float64), np.repeat(self._mesh.c, el.shape[1])], axis=1)
+        uv = np.unique(pairs, axis=0)
+        ng = np.bincount(uv[:, 0].astype(np.int64), minlength=self._mesh.coords.shape[0])
+        vert = self.tents.export()["vert"]
+        return int(ng[vert].sum()) * self.basis.nb * self.nrhs
 
     def __del__(self):
         if getattr(self, "handle", None) and B._lib is not None:
@@ -242,21 +325,30 @@ def _make_tent_sweep():
     import torch
 
     class TentSweep(torch.autograd.Function):
-        """front(T) = F(front(0)) through libtp, differentiable: the backward
-        pass is the reverse tent sweep (tp_adjoint).  g_D must be zero (the
-        map is then linear)."""
+        """front(T) = F(front(0); c) through libtp, differentiable: the
+        backward pass is the reverse tent sweep (tp_adjoint), which returns
+        the gradient with respect to the initial front and, when a tensor c
+        of the element speeds is passed, with respect to c (the solver must
+        then be created with ckpt_stride > 0; c must hold the speeds the
+        solver was created with, the gradient is taken there with the tents
+        held fixed)."""
 
         @staticmethod
-        def forward(ctx, front0, solver):
+        def forward(ctx, front0, solver, c=None):
             solver.set_state(front0.contiguous())
             solver.advance()
             out, _ = solver.get_state()
             ctx.solver = solver
+            ctx.with_c = c is not None
             return out
 
         @staticmethod
         def backward(ctx, grad_out):
-            return ctx.solver.adjoint(grad_out.contiguous()), None
+            g = grad_out.contiguous()
+            if ctx.with_c:
+                dc = torch.empty(ctx.solver.n_elem, dtype=torch.float64, device="cuda")
+                return ctx.solver.adjoint(g, dJ_dc=dc), None, dc
+            return ctx.solver.adjoint(g), None, None
 
     return TentSweep
 
@@ -264,47 +356,10 @@ def _make_tent_sweep():
 class _LazyTentSweep:
     _cls = None
 
-    def apply(self, front0, solver):
+    def apply(self, front0, solver, c=None):
         if _LazyTentSweep._cls is None:
             _LazyTentSweep._cls = _make_tent_sweep()
-        return _LazyTentSweep._cls.apply(front0, solver)
+        return _LazyTentSweep._cls.apply(front0, solver, c)
 
 
 TentSweep = _LazyTentSweep()
-
-
-def speed_gradient(coords, elems, c, p: int, T: float, kappa: float, front0, lam_T, gD=None,
-                   rel_step: float = 1e-6, **solver_kw):
-    """Gradient of J(c) = <lam_T, front_T(c)> with respect to the wave speed of
-    each material (the distinct values of c, all elements of a material
-    moving together), the tents pitched once with c and held fixed.
-
-    Central differences of two GPU sweeps per material,
-    dJ/dc_m ~ (J(c_m (1 + s)) - J(c_m (1 - s))) / (2 s c_m), s = rel_step:
-    each sweep runs in a context created with the perturbed speeds over the
-    same Tents (tp_create reads the speeds from the mesh and the tent times
-    from the pitched tents).  front0, lam_T: CUDA float64 tensors of
-    front_shape(); gD: boundary data as for Solver.set_state (independent of
-    c: the boundary points depend only on the mesh and the tents).
-    solver_kw goes to Solver (precision, bnd_type, alpha, beta, schedule).
-    Returns (speeds (M,) float64, dJ/dc (M,) float64) as numpy arrays."""
-    import torch
-    c = np.ascontiguousarray(c, dtype=np.float64)
-    tents = Tents(coords, elems, c, kappa, T)
-    speeds = np.unique(c)
-    grad = np.zeros(len(speeds))
-    for m, cm in enumerate(speeds):
-        J = []
-        for sgn in (1.0, -1.0):
-            cp = c.copy()
-            cp[c == cm] = cm * (1.0 + sgn * rel_step)
-            s = Solver(coords, elems, cp, p, T, kappa, tents=tents, **solver_kw)
-            s.set_state(front0, gD)
-            s.advance()
-            F, _ = s.get_state()
-            st = s.sync_status()
-            if st[0] != 0:
-                raise RuntimeError(f"speed_gradient: device status {st[0]} at tent {st[1]}")
-            J.append(float(torch.sum(lam_T * F)))
-        grad[m] = (J[0] - J[1]) / (2.0 * rel_step * cm)
-    return speeds, grad

@@ -94,12 +94,16 @@ __global__ void k_energy_partial(const KArgs a, double* partial, int nblk_per_rh
   if (threadIdx.x == 0) partial[(int64_t)r * nblk_per_rhs + blockIdx.x] = red[0];
 }
 
-__global__ void k_energy_final(const double* partial, int nblk, int nrhs, double* out) {
+// E_r into out[r * stride]; with stride 2 the accumulated energy loss D_r
+// (zero when diss is null) into out[2 r + 1]
+__global__ void k_energy_final(const double* partial, int nblk, int nrhs, double* out, int stride = 1,
+                               const double* diss = nullptr) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= nrhs) return;
   double s = 0.0;
   for (int b = 0; b < nblk; ++b) s += partial[(int64_t)r * nblk + b];
-  out[r] = s;
+  out[(int64_t)r * stride] = s;
+  if (stride == 2) out[2 * (int64_t)r + 1] = diss != nullptr ? diss[r] : 0.0;
 }
 
 template <typename T>
@@ -144,11 +148,27 @@ struct tp_ctx {
   double* d_tau = nullptr;
   double* d_gD = nullptr;
   double* d_partial = nullptr;
+  double* d_diss = nullptr;   // per right-hand side: energy lost in the tents since tp_set_state (tracked contexts)
+  // wave-speed gradient (contexts created with ckpt_stride > 0): the initial
+  // front of the last tp_set_state, a work front and its times, forward
+  // checkpoints every ckpt_stride levels, the fronts before each level of one
+  // segment, and the forward solutions of one segment's tents
+  int ckpt_stride = 0;
+  double* d_front0 = nullptr;
+  double* d_work = nullptr;
+  double* d_tau_work = nullptr;
+  double* d_ckpt = nullptr;
+  double* d_ckpt_tau = nullptr;
+  double* d_snap = nullptr;
+  double* d_xsave = nullptr;
+  long long xs_stride = 0, xsave_tents = 0;
   int* d_status = nullptr;
   long long* d_info = nullptr;
   cudaStream_t cap_stream = nullptr;
   cudaStream_t last_stream = nullptr;
   int n_sm = 152, max_cs = 1;
+  // right-hand sides split over the CTAs of a tent's cluster (1: not split)
+  int rsplit_cs = 1;
   bool mixed = false;
   // persistent dataflow sweep
   bool persistent = true;
@@ -158,6 +178,10 @@ struct tp_ctx {
   int* d_queue = nullptr;
   int* d_done = nullptr;
   int* d_tent_vert = nullptr;
+  // dependency lists of the dataflow sweep kept on the host (tp_inject_wait)
+  std::vector<int32_t> dep_ptr_h, dep_need_h;
+  int* d_dep_need = nullptr;
+  unsigned long long* d_stats = nullptr;   // solve statistics (kMaxRefine + 2 counters)
   std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
   int device = 0;
 };
@@ -239,6 +263,7 @@ bool tuned_lookup(const int* key, int* cs, bool* dataflow) {
 // cluster size for a level of nt tents: a power of two <= max_cs with
 // nt * cs <= 2 CTAs per SM
 int level_cluster_size(const tp_ctx* ctx, int64_t nt) {
+  if (ctx->rsplit_cs > 1) return ctx->rsplit_cs;   // one CTA per slice of the right-hand sides
   int cs = 1;
   while (cs * 2 <= ctx->max_cs && nt * cs * 2 <= 2LL * ctx->n_sm) cs *= 2;
   return cs;
@@ -249,6 +274,7 @@ int level_cluster_size(const tp_ctx* ctx, int64_t nt) {
 KArgs group_args(const tp_ctx* ctx, KArgs a, int k) {
   a.front += (size_t)k * ctx->nrhs_g * ctx->ne * ctx->Q * ctx->C;
   if (a.gD) a.gD += (size_t)k * ctx->nrhs_g * ctx->n_bnd;
+  if (a.diss) a.diss += (size_t)k * ctx->nrhs_g;
   return a;
 }
 
@@ -271,6 +297,16 @@ int launch_level(tp_ctx* ctx, int32_t L, cudaStream_t st, bool adj = false, int 
     TP_CUDA_OK(e);
     TP_CUDA_OK(cudaGetLastError());
   }
+  return TP_OK;
+}
+
+// one level with explicit kernel arguments (one right-hand-side group)
+int launch_level_with(tp_ctx* ctx, int32_t L, cudaStream_t st, bool adj, const KArgs& a) {
+  const int64_t t0 = ctx->level_ptr[L - 1], t1 = ctx->level_ptr[L];
+  if (t1 <= t0) return TP_OK;
+  const int nt = (int)(t1 - t0);
+  TP_CUDA_OK(launch_layer(ctx, a, nt, level_cluster_size(ctx, nt), (int)t0, st, adj ? 2 : (ctx->mixed ? 1 : 0), false));
+  TP_CUDA_OK(cudaGetLastError());
   return TP_OK;
 }
 
@@ -568,9 +604,10 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
   // per vertex: one record with all of its star that does not depend on the
   // sweep, so that a tent reads it in one round of loads.
   //   ints:    per element (el, material, vertex ids[n+1]); per facet (Dirichlet
-  //            first, then interface, then Neumann): (vertex ids other than v in
-  //            slots 2..n, material of the + element, of the - element, position
-  //            among the vertex's boundary facets = block of its boundary data)
+  //            first, then interface, then Neumann): (elements of the + and -
+  //            sides in slots 0, 1, vertex ids other than v in slots 2..n,
+  //            material of the + element, of the - element, position among the
+  //            vertex's boundary facets = block of its boundary data)
   //   doubles: x_v[n], speeds[kMaxGroups], their 1/c^2 [kMaxGroups]; per element its vertex coordinates
   //            [(n+1) n]; per facet its normal [n] and vertex coordinates [(n+1) n]
   // per tent: (v, int offset, double offset, elements, Dirichlet facets,
@@ -626,7 +663,12 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
         int c2 = 2;
         for (int i = 0; i < n; ++i)
           if (fv[i] != v) w_[c2++] = fv[i];
-        for (int i = 0; i < NVn; ++i) rec_i.push_back(w_[i]);
+        // slots 0 and 1: the elements on the facet's + and - sides (a boundary
+        // facet's own element twice; read by the wave-speed gradient), then the
+        // facet's other vertices
+        rec_i.push_back(bnd ? T.facet_elem[fid] : T.ifac_kp[fid]);
+        rec_i.push_back(bnd ? T.facet_elem[fid] : T.ifac_km[fid]);
+        for (int i = 2; i < NVn; ++i) rec_i.push_back(w_[i]);
         rec_i.push_back(grp_of(v, T.c[bnd ? T.facet_elem[fid] : T.ifac_kp[fid]]));
         rec_i.push_back(grp_of(v, T.c[bnd ? T.facet_elem[fid] : T.ifac_km[fid]]));
         rec_i.push_back(fo[2]);
@@ -683,17 +725,28 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
     tp::set_error("tp_create: device allocation of the front state failed");
     return fail(TP_ERR_OOM);
   }
-  if (cudaMalloc(&ctx->d_adj, nfront * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&ctx->d_tau_adj, T.nv * sizeof(double)) != cudaSuccess) {
-    tp::set_error("tp_create: device allocation of the adjoint state failed");
-    return fail(TP_ERR_OOM);
-  }
+  // (the adjoint state is allocated by the first tp_adjoint)
   ctx->T_final = tents->T;
   if (cudaMalloc(&ctx->d_queue, sizeof(int)) != cudaSuccess ||
       cudaMalloc(&ctx->d_done, T.nv * sizeof(int)) != cudaSuccess) {
     tp::set_error("tp_create: device allocation failed");
     return fail(TP_ERR_OOM);
   }
+  if (prm->ckpt_stride < 0) {
+    tp::set_error("tp_create: ckpt_stride must be >= 0");
+    return fail(TP_ERR_ARG);
+  }
+  ctx->ckpt_stride = prm->ckpt_stride;
+  if (ctx->ckpt_stride > 0 &&
+      cudaMalloc(&ctx->d_front0, (size_t)ctx->nrhs * T.ne * Q * ctx->C * sizeof(double)) != cudaSuccess) {
+    tp::set_error("tp_create: device allocation of the initial-state copy failed");
+    return fail(TP_ERR_OOM);
+  }
+  if (prm->dissipation && cudaMalloc(&ctx->d_diss, (size_t)ctx->nrhs * sizeof(double)) != cudaSuccess) {
+    tp::set_error("tp_create: device allocation failed");
+    return fail(TP_ERR_OOM);
+  }
+  if (ctx->d_diss) cudaMemset(ctx->d_diss, 0, (size_t)ctx->nrhs * sizeof(double));
   ctx->energy_blocks = (int)std::min<int64_t>(1024, (T.ne + kThreads - 1) / kThreads);
   if (cudaMalloc(&ctx->d_partial, (size_t)ctx->nrhs * ctx->energy_blocks * sizeof(double)) != cudaSuccess) {
     tp::set_error("tp_create: device allocation failed");
@@ -756,6 +809,17 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
   a.dep_ptr = ddp;
   a.dep_vert = ddv;
   a.dep_need = ddn;
+  ctx->d_dep_need = ddn;
+  ctx->dep_ptr_h = dep_ptr;
+  ctx->dep_need_h = dep_need;
+  a.max_spin = tp::kMaxSpin;
+  a.max_refine = tp::kMaxRefine;
+  if (cudaMalloc(&ctx->d_stats, (tp::kMaxRefine + 2) * sizeof(unsigned long long)) != cudaSuccess) {
+    tp::set_error("tp_create: device allocation failed");
+    return fail(TP_ERR_OOM);
+  }
+  cudaMemset(ctx->d_stats, 0, (tp::kMaxRefine + 2) * sizeof(unsigned long long));
+  a.solve_stats = ctx->d_stats;
   a.queue_tent = dqt;
   a.X = dX;
   a.elems = del;
@@ -812,6 +876,7 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
   a.tent_end = (int)ctx->ntents;
   a.front = ctx->d_front;
   a.gD = nullptr;
+  a.diss = ctx->d_diss;
   a.status = ctx->d_status;
   a.status_info = ctx->d_info;
   // shared-memory plan: the largest chunk of points that fits
@@ -825,6 +890,8 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
   // shared-memory plan: the largest chunk of points that keeps two CTAs per SM,
   // else the largest that fits one
   int nrg = ctx->nrhs;   // right-hand sides per group
+  bool ifneu = false;   // some tent has interface or Neumann facets
+  for (const auto& m : facet_mix) ifneu = ifneu || m[2] > 0 || m[3] > 0;
   auto plan = [&](int CH, int keep) {
     size_t off = 0;
     auto take = [&](int* field, size_t count) {
@@ -862,9 +929,10 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
     take(&a.off_pm, (size_t)ngmax * nmom);        // moments: partials, summed in place, then the outflow vectors
     a.off_sm = a.off_y = a.off_pm;
     take(&a.off_pd, pd);
-    take(&a.off_f, npair);
-    take(&a.off_f2, npair);
-    take(&a.off_fpm, (size_t)nb * nb);
+    // facet Grams of interface and Neumann facets (none on meshes without them)
+    take(&a.off_f, ifneu ? npair : 0);
+    take(&a.off_f2, ifneu ? npair : 0);
+    take(&a.off_fpm, ifneu ? (size_t)nb * nb : 0);
     take(&a.off_del, (size_t)nrg * nb);
     take(&a.off_u, (size_t)2 * CH * nb);
     take(&a.off_pt, (size_t)2 * CH * (n + 2));
@@ -874,15 +942,33 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
     take(&a.off_eq, half_nb);
     take(&a.off_keep, (size_t)keep * nb);          // top U-values of the CTA's slice, kept for the outflow
     take(&a.off_keepw, (size_t)keep);
+    // wave-speed gradient (reverse sweep): y(x), y(x'), y(mu') per material and the forward solution
+    take(&a.off_yg, prm->ckpt_stride > 0 ? 3 * (size_t)ngmax * nmom + (size_t)nrg * NB : 0);
     return off * sizeof(double);
   };
   int CH = 0;
   size_t bytes = 0, cap_used = 0;
   size_t max_dyn = 0;
   if ((rc = max_dyn_smem(n, &max_dyn)) != TP_OK) return fail(rc);
-  // the most right-hand sides per group (a divisor of nrhs) whose plan fits
-  for (nrg = ctx->nrhs; nrg >= 1 && CH == 0; --nrg) {
-    if (ctx->nrhs % nrg) continue;
+  // right-hand sides split over the cluster: rs CTAs, each owning a slice of
+  // every group's right-hand sides (automatic: 16 or more per CTA; at 3D
+  // p = 3 with 64 right-hand sides, 4 CTAs of 16 sweep 1.6x faster than 8 of 8)
+  int rs = prm->rhs_split;
+  if (rs == 0) {
+    rs = 1;
+    for (int r : {8, 4, 2})
+      if (rs == 1 && ctx->nrhs % r == 0 && ctx->nrhs / r >= 16) rs = r;
+  }
+  if (!(rs == 1 || rs == 2 || rs == 4 || rs == 8) || ctx->nrhs % rs != 0) {
+    tp::set_error("tp_create: rhs_split must be 0, 1, 2, 4 or 8 and divide nrhs");
+    return fail(TP_ERR_ARG);
+  }
+  // the most right-hand sides per group (a divisor of nrhs, a multiple of rs)
+  // whose plan fits; the plan holds one CTA's nrg = group / rs of them
+  int grp = 0;
+  for (grp = ctx->nrhs; grp >= 1 && CH == 0; --grp) {
+    if (ctx->nrhs % grp || grp % rs) continue;
+    nrg = grp / rs;
     for (size_t cap : {kTwoPerSmSmem, max_dyn}) {
       for (int ch : {48, 32, 16, 8})
         if (CH == 0 && plan(ch, 0) <= cap) CH = ch;
@@ -899,15 +985,18 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
   }
   // the rest of the budget keeps the top U-values of up to `keep` points per
   // CTA (a slice that fits skips their second evaluation in the outflow)
-  int keep = (int)std::min<size_t>((cap_used - plan(CH, 0)) / ((size_t)(nb + 1) * sizeof(double)),
-                                   (size_t)pmax * Q);
+  // (split right-hand sides evaluate the top U-values of every point again: no keep buffer)
+  int keep = rs > 1 ? 0 : (int)std::min<size_t>((cap_used - plan(CH, 0)) / ((size_t)(nb + 1) * sizeof(double)),
+                                                (size_t)pmax * Q);
   while (keep > 0 && plan(CH, keep) > cap_used) --keep;
   bytes = plan(CH, keep);
   a.CH = CH;
   a.keep_pts = keep;
   a.nrhs = nrg;
-  ctx->nrhs_g = nrg;
-  ctx->rhs_groups = ctx->nrhs / nrg;
+  a.rsplit = rs > 1 ? 1 : 0;
+  ctx->rsplit_cs = rs;
+  ctx->nrhs_g = grp;
+  ctx->rhs_groups = ctx->nrhs / grp;
   if (ctx->rhs_groups > 1 && cudaMalloc(&ctx->d_tau_save, T.nv * sizeof(double)) != cudaSuccess) {
     tp::set_error("tp_create: out of device memory");
     return fail(TP_ERR_OOM);
@@ -916,6 +1005,7 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
   ctx->args_adj.front = ctx->d_adj;
   ctx->args_adj.tau = ctx->d_tau_adj;
   ctx->args_adj.gD = nullptr;
+  ctx->args_adj.diss = nullptr;
   ctx->smem_bytes = bytes;
   rc = set_smem_attr(n, max_dyn);
   if (rc) return fail(rc);
@@ -937,6 +1027,7 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
     int cs = ctx->max_cs;
     bool sched_dataflow = true;
     if (tuned_lookup(ctx->tune_key, &cs, &sched_dataflow)) ctx->persistent = sched_dataflow;
+    if (rs > 1) cs = rs;   // the cluster is the right-hand-side split
     if (ctx->persistent && set_persist_cs(ctx, cs) != TP_OK) ctx->persistent = false;   // one launch per level
   }
   if (cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
@@ -961,6 +1052,19 @@ extern "C" int tp_ctx_info(const tp_ctx* ctx, int64_t* n_front, int32_t* n_comp,
   if (n_comp) *n_comp = ctx->C;
   if (n_bnd) *n_bnd = ctx->n_bnd;
   if (n_levels) *n_levels = ctx->n_levels;
+  return TP_OK;
+}
+
+extern "C" int tp_ctx_schedule(const tp_ctx* ctx, int32_t* dataflow, int32_t* cluster, int32_t* rhs_split,
+                               int32_t* rhs_groups) {
+  if (!ctx) {
+    tp::set_error("tp_ctx_schedule: null context");
+    return TP_ERR_ARG;
+  }
+  if (dataflow) *dataflow = ctx->persistent ? 1 : 0;
+  if (cluster) *cluster = ctx->persistent ? ctx->persist_cs : ctx->max_cs;
+  if (rhs_split) *rhs_split = ctx->rsplit_cs;
+  if (rhs_groups) *rhs_groups = ctx->rhs_groups;
   return TP_OK;
 }
 
@@ -1021,9 +1125,13 @@ extern "C" int tp_set_state(tp_ctx* ctx, const double* d_front, const double* d_
   cudaStream_t st = (cudaStream_t)stream;
   const size_t nfront = (size_t)ctx->nrhs * ctx->ne * ctx->Q * ctx->C;
   TP_CUDA_OK(cudaMemcpyAsync(ctx->d_front, d_front, nfront * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  if (ctx->d_front0)   // the wave-speed gradient sweeps forward again from here
+    TP_CUDA_OK(cudaMemcpyAsync(ctx->d_front0, d_front, nfront * sizeof(double), cudaMemcpyDeviceToDevice, st));
   TP_CUDA_OK(cudaMemsetAsync(ctx->d_tau, 0, ctx->nv * sizeof(double), st));
   TP_CUDA_OK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), st));
   TP_CUDA_OK(cudaMemsetAsync(ctx->d_info, 0, sizeof(long long), st));
+  if (ctx->d_diss) TP_CUDA_OK(cudaMemsetAsync(ctx->d_diss, 0, (size_t)ctx->nrhs * sizeof(double), st));
+  TP_CUDA_OK(cudaMemsetAsync(ctx->d_stats, 0, (tp::kMaxRefine + 2) * sizeof(unsigned long long), st));
   if (ctx->n_bnd > 0) {
     if (d_gD) {
       TP_CUDA_OK(cudaMemcpyAsync(ctx->d_gD, d_gD, (size_t)ctx->nrhs * ctx->n_bnd * sizeof(double),
@@ -1035,6 +1143,73 @@ extern "C" int tp_set_state(tp_ctx* ctx, const double* d_front, const double* d_
     }
   }
   ctx->last_stream = st;
+  return TP_OK;
+}
+
+extern "C" int tp_set_front(tp_ctx* ctx, const double* d_front, const double* d_tau, void* stream) {
+  if (!ctx || !d_front || !d_tau) {
+    tp::set_error("tp_set_front: null argument");
+    return TP_ERR_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t nfront = (size_t)ctx->nrhs * ctx->ne * ctx->Q * ctx->C;
+  TP_CUDA_OK(cudaMemcpyAsync(ctx->d_front, d_front, nfront * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  TP_CUDA_OK(cudaMemcpyAsync(ctx->d_tau, d_tau, ctx->nv * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  ctx->last_stream = st;
+  return TP_OK;
+}
+
+namespace {
+void drop_graphs(tp_ctx* ctx) {   // captured graphs hold the kernel arguments by value
+  for (auto& kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
+  ctx->graphs.clear();
+  if (ctx->adj_graph) cudaGraphExecDestroy(ctx->adj_graph);
+  ctx->adj_graph = nullptr;
+}
+}  // namespace
+
+extern "C" int tp_set_limits(tp_ctx* ctx, int64_t max_polls, int32_t max_refine) {
+  if (!ctx) {
+    tp::set_error("tp_set_limits: null context");
+    return TP_ERR_ARG;
+  }
+  const long long spin = max_polls > 0 ? (long long)max_polls : tp::kMaxSpin;
+  const int ref = max_refine >= 0 ? std::min<int>(max_refine, tp::kMaxRefine) : tp::kMaxRefine;
+  for (KArgs* a : {&ctx->args, &ctx->args_adj}) {
+    a->max_spin = spin;
+    a->max_refine = ref;
+  }
+  drop_graphs(ctx);
+  return TP_OK;
+}
+
+extern "C" int tp_inject_wait(tp_ctx* ctx, int64_t tent, int32_t extra) {
+  if (!ctx || tent < 0 || tent >= ctx->ntents || extra < 0) {
+    tp::set_error("tp_inject_wait: invalid argument");
+    return TP_ERR_ARG;
+  }
+  const int d0 = ctx->dep_ptr_h[tent], d1 = ctx->dep_ptr_h[tent + 1];
+  if (d1 <= d0) {
+    tp::set_error("tp_inject_wait: tent " + std::to_string(tent) + " waits for no earlier tent");
+    return TP_ERR_ARG;
+  }
+  std::vector<int32_t> need(ctx->dep_need_h.begin() + d0, ctx->dep_need_h.begin() + d1);
+  for (auto& x : need) x += extra;
+  TP_CUDA_OK(cudaMemcpy(ctx->d_dep_need + d0, need.data(), need.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  return TP_OK;
+}
+
+extern "C" int tp_solve_stats(tp_ctx* ctx, int64_t* direct_lu, int64_t* hist, int32_t nhist) {
+  if (!ctx || (hist && nhist < 0)) {
+    tp::set_error("tp_solve_stats: invalid argument");
+    return TP_ERR_ARG;
+  }
+  unsigned long long h[tp::kMaxRefine + 2];
+  TP_CUDA_OK(cudaStreamSynchronize(ctx->last_stream));
+  TP_CUDA_OK(cudaMemcpy(h, ctx->d_stats, sizeof(h), cudaMemcpyDeviceToHost));
+  if (direct_lu) *direct_lu = (int64_t)h[0];
+  if (hist)
+    for (int k = 0; k < nhist; ++k) hist[k] = k <= tp::kMaxRefine ? (int64_t)h[1 + k] : 0;
   return TP_OK;
 }
 
@@ -1128,18 +1303,128 @@ __global__ void k_fill(double* p, int64_t n, double v) {
 }
 }  // namespace
 
-extern "C" int tp_adjoint(tp_ctx* ctx, const double* d_lambda_T, double* d_lambda_0, void* stream) {
+namespace {
+
+// the buffers of the wave-speed gradient, allocated on its first use
+int grad_buffers(tp_ctx* ctx) {
+  if (ctx->d_work) return TP_OK;
+  const size_t nfront = (size_t)ctx->nrhs * ctx->ne * ctx->Q * ctx->C;
+  const int S = ctx->ckpt_stride, nseg = (ctx->n_levels + S - 1) / S;
+  int64_t most = 0;   // tents of the largest segment
+  for (int sg = 0; sg < nseg; ++sg) {
+    const int L0 = 1 + sg * S, L1 = std::min(L0 + S, ctx->n_levels + 1);
+    most = std::max<int64_t>(most, ctx->level_ptr[L1 - 1] - ctx->level_ptr[L0 - 1]);
+  }
+  ctx->xs_stride = (long long)ctx->nrhs * ctx->args.ngmax * ctx->nb;
+  ctx->xsave_tents = most;
+  if (cudaMalloc(&ctx->d_work, nfront * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&ctx->d_tau_work, ctx->nv * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&ctx->d_ckpt, (size_t)nseg * nfront * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&ctx->d_ckpt_tau, (size_t)nseg * ctx->nv * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&ctx->d_snap, (size_t)S * nfront * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&ctx->d_xsave, (size_t)std::max<int64_t>(1, most) * ctx->xs_stride * sizeof(double)) != cudaSuccess) {
+    for (double** g : {&ctx->d_work, &ctx->d_tau_work, &ctx->d_ckpt, &ctx->d_ckpt_tau, &ctx->d_snap, &ctx->d_xsave}) {
+      cudaFree(*g);
+      *g = nullptr;
+    }
+    cudaGetLastError();
+    tp::set_error("tp_adjoint: device allocation of the checkpoints failed");
+    return TP_ERR_OOM;
+  }
+  return TP_OK;
+}
+
+// reverse sweep with the wave-speed gradient: forward from the initial state
+// of the last tp_set_state keeping a checkpoint (front and times) at the start
+// of every segment of ckpt_stride levels; then segment by segment from the
+// last: forward again from its checkpoint keeping the front before each level
+// and every tent's solution, and the reverse levels of the segment, each
+// adding its tents' dJ/dc
+int adjoint_with_gradient(tp_ctx* ctx, double* d_dJ_dc, cudaStream_t st) {
+  const size_t nfront = (size_t)ctx->nrhs * ctx->ne * ctx->Q * ctx->C;
+  const size_t fb = nfront * sizeof(double), tb = ctx->nv * sizeof(double);
+  const int S = ctx->ckpt_stride, nseg = (ctx->n_levels + S - 1) / S;
+  int rc = grad_buffers(ctx);
+  if (rc != TP_OK) return rc;
+  TP_CUDA_OK(cudaMemsetAsync(d_dJ_dc, 0, ctx->ne * sizeof(double), st));
+  KArgs af = ctx->args;   // forward on the work front
+  af.front = ctx->d_work;
+  af.tau = ctx->d_tau_work;
+  af.diss = nullptr;
+  af.xsave = nullptr;
+  TP_CUDA_OK(cudaMemcpyAsync(ctx->d_work, ctx->d_front0, fb, cudaMemcpyDeviceToDevice, st));
+  TP_CUDA_OK(cudaMemsetAsync(ctx->d_tau_work, 0, tb, st));
+  for (int sg = 0; sg < nseg; ++sg) {
+    const int L0 = 1 + sg * S, L1 = std::min(L0 + S, ctx->n_levels + 1);
+    TP_CUDA_OK(cudaMemcpyAsync(ctx->d_ckpt + (size_t)sg * nfront, ctx->d_work, fb, cudaMemcpyDeviceToDevice, st));
+    TP_CUDA_OK(cudaMemcpyAsync(ctx->d_ckpt_tau + (size_t)sg * ctx->nv, ctx->d_tau_work, tb, cudaMemcpyDeviceToDevice, st));
+    for (int L = L0; L < L1; ++L)
+      if ((rc = launch_level_with(ctx, L, st, false, af)) != TP_OK) return rc;
+  }
+  KArgs aa = ctx->args_adj;   // reverse, with the forward boundary data and the gradient
+  aa.gD = ctx->args.gD;
+  aa.dJdc = d_dJ_dc;
+  aa.xsave = ctx->d_xsave;
+  aa.xs_stride = ctx->xs_stride;
+  af.xsave = ctx->d_xsave;
+  af.xs_stride = ctx->xs_stride;
+  for (int sg = nseg - 1; sg >= 0; --sg) {
+    const int L0 = 1 + sg * S, L1 = std::min(L0 + S, ctx->n_levels + 1);
+    af.xbase = aa.xbase = ctx->level_ptr[L0 - 1];
+    TP_CUDA_OK(cudaMemcpyAsync(ctx->d_work, ctx->d_ckpt + (size_t)sg * nfront, fb, cudaMemcpyDeviceToDevice, st));
+    TP_CUDA_OK(cudaMemcpyAsync(ctx->d_tau_work, ctx->d_ckpt_tau + (size_t)sg * ctx->nv, tb, cudaMemcpyDeviceToDevice, st));
+    for (int L = L0; L < L1; ++L) {
+      TP_CUDA_OK(cudaMemcpyAsync(ctx->d_snap + (size_t)(L - L0) * nfront, ctx->d_work, fb, cudaMemcpyDeviceToDevice, st));
+      if ((rc = launch_level_with(ctx, L, st, false, af)) != TP_OK) return rc;
+    }
+    for (int L = L1 - 1; L >= L0; --L) {
+      aa.front_fwd = ctx->d_snap + (size_t)(L - L0) * nfront;
+      if ((rc = launch_level_with(ctx, L, st, true, aa)) != TP_OK) return rc;
+    }
+  }
+  return TP_OK;
+}
+
+}  // namespace
+
+extern "C" int tp_adjoint(tp_ctx* ctx, const double* d_lambda_T, double* d_dJ_dc, double* d_lambda_0,
+                          void* stream) {
   if (!ctx || !d_lambda_T || !d_lambda_0) {
     tp::set_error("tp_adjoint: null argument");
     return TP_ERR_ARG;
   }
+  if (d_dJ_dc && ctx->ckpt_stride <= 0) {
+    tp::set_error("tp_adjoint: the wave-speed gradient needs a context created with ckpt_stride > 0");
+    return TP_ERR_ARG;
+  }
+  if (d_dJ_dc && ctx->rhs_groups > 1) {
+    tp::set_error("tp_adjoint: the wave-speed gradient needs every right-hand side in one group");
+    return TP_ERR_UNSUPPORTED;
+  }
   cudaStream_t st = (cudaStream_t)stream;
   const size_t nfront = (size_t)ctx->nrhs * ctx->ne * ctx->Q * ctx->C;
+  if (!ctx->d_adj) {   // the adjoint state, on first use
+    if (cudaMalloc(&ctx->d_adj, nfront * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&ctx->d_tau_adj, ctx->nv * sizeof(double)) != cudaSuccess) {
+      cudaFree(ctx->d_adj);
+      ctx->d_adj = nullptr;
+      cudaGetLastError();
+      tp::set_error("tp_adjoint: device allocation of the adjoint state failed");
+      return TP_ERR_OOM;
+    }
+    ctx->args_adj.front = ctx->d_adj;
+    ctx->args_adj.tau = ctx->d_tau_adj;
+  }
   TP_CUDA_OK(cudaMemcpyAsync(ctx->d_adj, d_lambda_T, nfront * sizeof(double), cudaMemcpyDeviceToDevice, st));
   k_fill<<<(unsigned)std::min<int64_t>(1024, (ctx->nv + 255) / 256), 256, 0, st>>>(ctx->d_tau_adj, ctx->nv,
                                                                                  ctx->T_final);
   TP_CUDA_OK(cudaGetLastError());
-  if (ctx->n_levels > 0) {
+  if (d_dJ_dc && ctx->n_levels > 0) {
+    const int rc = adjoint_with_gradient(ctx, d_dJ_dc, st);
+    if (rc != TP_OK) return rc;
+  } else if (d_dJ_dc) {
+    TP_CUDA_OK(cudaMemsetAsync(d_dJ_dc, 0, ctx->ne * sizeof(double), st));
+  } else if (ctx->n_levels > 0) {
     if (!ctx->adj_graph) {
       cudaGraph_t g = nullptr;
       TP_CUDA_OK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
@@ -1199,7 +1484,8 @@ extern "C" int tp_autotune(tp_ctx* ctx, void* stream, int32_t* chosen, double* b
     if (c == 0) {
       ctx->persistent = false;
     } else {
-      if (c > ctx->max_cs * 2 || set_persist_cs(ctx, c) != TP_OK) continue;
+      if ((ctx->rsplit_cs > 1 ? c != ctx->rsplit_cs : c > ctx->max_cs * 2) || set_persist_cs(ctx, c) != TP_OK)
+        continue;
       ctx->persistent = true;
     }
     for (auto& kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
@@ -1253,7 +1539,8 @@ extern "C" int tp_energy(tp_ctx* ctx, double* d_out, void* stream) {
     default: k_energy_partial<3><<<grid, kThreads, 0, st>>>(ctx->args, ctx->d_partial, ctx->energy_blocks); break;
   }
   TP_CUDA_OK(cudaGetLastError());
-  k_energy_final<<<(ctx->nrhs + 127) / 128, 128, 0, st>>>(ctx->d_partial, ctx->energy_blocks, ctx->nrhs, d_out);
+  k_energy_final<<<(ctx->nrhs + 127) / 128, 128, 0, st>>>(ctx->d_partial, ctx->energy_blocks, ctx->nrhs, d_out, 2,
+                                                         ctx->d_diss);
   TP_CUDA_OK(cudaGetLastError());
   ctx->last_stream = st;
   return TP_OK;
@@ -1296,6 +1583,10 @@ extern "C" void tp_destroy_ctx(tp_ctx* ctx) {
   cudaFree(ctx->d_tau);
   cudaFree(ctx->d_gD);
   cudaFree(ctx->d_partial);
+  cudaFree(ctx->d_diss);
+  cudaFree(ctx->d_stats);
+  for (double* g : {ctx->d_front0, ctx->d_work, ctx->d_tau_work, ctx->d_ckpt, ctx->d_ckpt_tau, ctx->d_snap, ctx->d_xsave})
+    cudaFree(g);
   cudaFree(ctx->d_adj);
   cudaFree(ctx->d_queue);
   cudaFree(ctx->d_done);
@@ -1402,4 +1693,73 @@ extern "C" int tp_front_energy_noalloc(int32_t dim, int64_t n_elem, int32_t Q, i
   k_energy_final<<<(nrhs + 127) / 128, 128, 0, st>>>(partial, nblk, nrhs, d_out);
   TP_CUDA_OK(cudaGetLastError());
   return TP_OK;
+}
+
+// ===========================================================================
+// Arithmetic peaks of the plain ALUs (tp_measure_alu_peaks): the rooflines of
+// the tent sweep are set by the binary64 pipe (binary64 path) and the
+// binary32 pipe (float-float mixed path), for which no library figure exists.
+// Eight independent fused multiply-add chains per thread, enough warps per SM
+// to hide the pipe latency; 2 flops per fused multiply-add.
+// ===========================================================================
+namespace {
+
+template <typename F>
+__global__ void k_fma_chains(F* sink, int iters, F m, F c) {
+  F a[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) a[j] = (F)(threadIdx.x + j) * (F)1e-3;
+  for (int i = 0; i < iters; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a[j] = fma(a[j], m, c);
+  F s = 0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) s += a[j];
+  if (s == (F)-1.25) sink[blockIdx.x] = s;   // never true; keeps the chains live
+}
+
+template <typename F>
+int fma_peak(int n_sm, cudaStream_t st, double* tflops) {
+  F* sink = nullptr;
+  TP_CUDA_OK(cudaMalloc(&sink, 8 * n_sm * sizeof(F)));
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int blocks = 8 * n_sm, threads = 256, iters = 1 << 14;
+  float best = 3.4e38f;
+  int rc = TP_OK;
+  for (int rep = 0; rep < 4 && rc == TP_OK; ++rep) {
+    cudaEventRecord(e0, st);
+    k_fma_chains<F><<<blocks, threads, 0, st>>>(sink, iters, (F)0.999999, (F)1e-7);
+    cudaEventRecord(e1, st);
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+      tp::set_error("tp_measure_alu_peaks: kernel failed");
+      rc = TP_ERR_CUDA;
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0) best = std::min(best, ms);   // the first launch warms up
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(sink);
+  if (rc == TP_OK) *tflops = 2.0 * 8.0 * iters * (double)blocks * threads / (best * 1e-3) / 1e12;
+  return rc;
+}
+
+}  // namespace
+
+extern "C" int tp_measure_alu_peaks(double* fp64_tflops, double* fp32_tflops, void* stream) {
+  if (!fp64_tflops || !fp32_tflops) {
+    tp::set_error("tp_measure_alu_peaks: null argument");
+    return TP_ERR_ARG;
+  }
+  int dev = 0, nsm = 0;
+  TP_CUDA_OK(cudaGetDevice(&dev));
+  TP_CUDA_OK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = fma_peak<double>(nsm, st, fp64_tflops);
+  if (rc == TP_OK) rc = fma_peak<float>(nsm, st, fp32_tflops);
+  return rc;
 }

@@ -32,6 +32,11 @@ __device__ __forceinline__ void red_release_add(int* p, int v) {
 
 struct KArgs {
   int nb, nmono, Q, nrhs, CH, mono_stride, ngmax;
+  // right-hand sides split over the cluster: CTA r of a tent's cluster owns
+  // right-hand sides [r nrhs, (r + 1) nrhs) of the group (nrhs = per CTA) for
+  // the data moments, the solve and the outflow, over all points of the
+  // patch; the Grams stay split by points.  0: every CTA sees all nrhs.
+  int rsplit;
   int p;                          // degree of U^p
   int mono_lv[kMaxP + 2];         // monomials of total degree d: [mono_lv[d], mono_lv[d+1])
   // U-value sums: basis functions in classes of equal term count (class with
@@ -76,6 +81,25 @@ struct KArgs {
   double* tau;
   double* front;
   const double* gD;
+  double* diss;               // per right-hand side: accumulated energy lost in the tents (nullptr: not tracked)
+  // wave-speed gradient: the forward sweep stores each tent's solution
+  // (xsave[(tent - xbase) * xs_stride + r * ngmax * nb + row], r over the
+  // group's right-hand sides) when xsave is set; the reverse sweep reads it
+  // back with the forward front before the level (front_fwd) and adds
+  // dJ/dc per element into dJdc when dJdc is set
+  double* xsave;
+  long long xbase, xs_stride;
+  const double* front_fwd;
+  double* dJdc;
+  int off_yg;                 // shared memory of the gradient: y(x), y(x'), y(mu') and x
+  // bounded waits and the solve's refinement: the dependency wait gives up
+  // after max_spin polls (TP_ERR_TIMEOUT); a refinement that has not settled
+  // after max_refine steps hands the tent to the direct binary64 LU;
+  // solve_stats (kMaxRefine + 2 counters, or nullptr): [0] tents solved by
+  // the direct LU, [1 + k] tents whose refinement settled after k steps
+  long long max_spin;
+  int max_refine;
+  unsigned long long* solve_stats;
   int* status;
   long long* status_info;
   // persistent sweep: tent queue, completed tents per vertex, dependencies
@@ -366,6 +390,12 @@ struct Fac<dd> {
   }
 };
 
+// butterfly exchange of a value of the path's arithmetic within a warp
+__device__ __forceinline__ double shfl_xor_t(double v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ dd shfl_xor_t(dd v, int o) {
+  return {__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+}
+
 // packed upper-triangle index of (i, j), i, j < nb
 __device__ __forceinline__ int pair_index(int i, int j, int nb) {
   const int lo = min(i, j), hi = max(i, j);
@@ -553,6 +583,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
   __shared__ double s_fsq[tp::kMaxFacets], s_fn[tp::kMaxFacets][DIM];   // sqrt(n! volume), normal
   __shared__ int s_fg[tp::kMaxFacets], s_fg2[tp::kMaxFacets];   // groups (Dirichlet: one; interface: +, -)
   __shared__ int s_pgrp[2 * 64];
+  __shared__ double s_gel[tp::kMaxPatch];   // wave-speed gradient of the tent per patch element
   __shared__ int s_piv;
   __shared__ float s_pb[2][4][32];   // register sweeps: the pivot rows of a block of four steps
   __shared__ float s_red[2][kThreads / 32];
@@ -581,6 +612,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
     tent = tent0 + blockIdx.x / CS;
   }
   const int nb = a.nb, Q = a.Q, nrhs = a.nrhs, CH = a.CH, NG = a.ngmax;
+  // this CTA's right-hand sides (all of the group unless they are split over the cluster)
+  const bool rsplit = a.rsplit != 0;
+  double* const front = a.front + (rsplit ? (size_t)rank * nrhs * a.ne * Q * C : 0);
+  const double* const gD = a.gD != nullptr ? a.gD + (rsplit ? (size_t)rank * nrhs * a.n_bnd : 0) : nullptr;
   const int npair = nb * (nb + 1) / 2;
   const int nmom = nrhs * C * nb;
   T* sA = reinterpret_cast<T*>(sm);                  // N*N        assembled A, then LU factors
@@ -669,7 +704,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
         const int w = a.dep_vert[e], need = a.dep_need[e] * CS;
         long long spins = 0;
         while (ld_acquire(a.done + w) < need) {
-          if (++spins > kMaxSpin) {
+          if (++spins > a.max_spin) {
             flag_error(a, TP_ERR_TIMEOUT, tent);
             break;
           }
@@ -768,7 +803,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
   int curg = (q1 > q0) ? s_grp[curk] : 0;
   // forward sweep: the top U-values of a slice that fits the keep buffer are
   // kept for the outflow instead of being evaluated a second time
-  const bool keep = !ADJ && (q1 - q0) <= a.keep_pts;
+  const bool keep = !ADJ && !rsplit && (q1 - q0) <= a.keep_pts;
   T* sKeep = reinterpret_cast<T*>(sm + a.off_keep);   // keep_pts*nb  sqrt(w)-scaled top U-values
   double* sKeepW = sm + a.off_keepw;                   // keep_pts     1 / sqrt(w)
   // element flush: G += G_K, H_m += g_{K,m} G_K;  group flush: publish G, H, Gbot of the group
@@ -800,6 +835,87 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
       for (int d = 0; d < DIM; ++d) aH[s][d] = R::zero();
     }
   };
+  // a patch point q of element k mapped to the tent's reference coordinates
+  // (Remark 3.1) on the top (TOP) or bottom face, with sqrt(w) as the scale of
+  // its U-values; returns sqrt(w)
+  auto map_point = [&](T* pp, int k, int q, bool top) {
+    const double cg = s_gc[s_grp[k]];
+    double x[DIM], tt = 0.0;
+    for (int d = 0; d < DIM; ++d) x[d] = 0.0;
+    for (int i = 0; i < NV; ++i) {
+      const double l = __ldg(a.bary + q * NV + i);
+      for (int d = 0; d < DIM; ++d) x[d] = fma(l, s_X[k][i][d], x[d]);
+      tt = fma(l, top ? s_tt[k][i] : s_tb[k][i], tt);
+    }
+    pp[0] = R::from(cg * (tt - tc) * ih);
+    for (int d = 0; d < DIM; ++d) pp[1 + d] = R::from((x[d] - s_xv[d]) * ih);
+    const double sw = __ldg(a.sqw + q) * s_sdet[k];
+    pp[DIM + 1] = R::from(sw);
+    return sw;
+  };
+  // data coefficients of the points base .. base + nq - 1 (patch point
+  // numbering) for every right-hand side, one (point, right-hand side) per
+  // thread so that the front loads of a chunk are all in flight at once:
+  // forward, the bottom values in the form of the moments (gamma, alpha,
+  // beta_m); adjoint, lambda at the top point
+  auto data_coefs = [&](int base, int nq) {
+    for (int id = tid; id < nq * nrhs; id += blockDim.x) {   // (consecutive threads: consecutive points)
+      const int r = id / nq, ql = id % nq, qg = base + ql, k = qg / Q, q = qg % Q;
+      const double* f = front + (((int64_t)r * a.ne + s_el[k]) * Q + q) * C;
+      double fv[C];
+#pragma unroll
+      for (int cc = 0; cc < C; ++cc) fv[cc] = __ldcg(f + cc);
+      T* cb = sCB + ((size_t)ql * nrhs + r) * C;
+      if constexpr (ADJ) {
+        // adjoint: zeta = sum_q lambda_q u_q over the top points
+        const double isw = __ldg(a.isqw + q) * s_isdet[k];
+#pragma unroll
+        for (int cc = 0; cc < C; ++cc) cb[cc] = R::from(fv[cc] * isw);
+      } else {
+        const double sw = __ldg(a.sqw + q) * s_sdet[k], ic2 = s_gic2[s_grp[k]];
+        const double Ub = fv[0], vb = fv[1];
+        double sg = 0.0;
+        for (int d = 0; d < DIM; ++d) sg = fma(fv[2 + d], s_gb[k][d], sg);
+        cb[0] = R::from(sw * Ub);                       // gamma
+        cb[1] = R::from(sw * (ic2 * vb - sg));          // alpha
+        for (int d = 0; d < DIM; ++d) cb[2 + d] = R::from(sw * (fv[2 + d] - vb * s_gb[k][d]));   // beta_m
+      }
+    }
+  };
+  // moments of the data of nq points whose U-values are rows prow.. of sU, per
+  // material: one (material, right-hand side, basis function) per group of
+  // ps lanes with its C components as independent sums; the lanes of a group
+  // take every ps-th point and are added by butterfly shuffles (a fixed order)
+  auto data_moments = [&](int nq, int prow) {
+    const int nitem = ng * nrhs * nb;
+    int ps = 1;
+    while (ps < 8 && nitem * ps * 2 <= (int)blockDim.x) ps *= 2;
+    for (int id0 = 0; id0 < nitem * ps; id0 += blockDim.x) {
+      const int id = id0 + tid, item = id / ps, part = id % ps;
+      const int g = item / (nrhs * nb), rest = item % (nrhs * nb), r = rest / nb, i = rest % nb;
+      T t[C];
+#pragma unroll
+      for (int cc = 0; cc < C; ++cc) t[cc] = R::zero();
+      if (item < nitem)
+        for (int ql = part; ql < nq; ql += ps)
+          if (s_pgrp[ql] == g) {
+            const T u = sU[(size_t)(prow + ql) * nb + i];
+            const T* cb = sCB + ((size_t)ql * nrhs + r) * C;
+#pragma unroll
+            for (int cc = 0; cc < C; ++cc) t[cc] = R::acc(t[cc], cb[cc], u);
+          }
+#pragma unroll
+      for (int cc = 0; cc < C; ++cc) t[cc] = R::norm(t[cc]);
+      for (int o = 1; o < ps; o <<= 1)
+#pragma unroll
+        for (int cc = 0; cc < C; ++cc) t[cc] = R::add(t[cc], shfl_xor_t(t[cc], o));
+      if (part == 0 && item < nitem) {
+        T* M = sPM + (size_t)g * nmom + (size_t)r * C * nb + i;
+#pragma unroll
+        for (int cc = 0; cc < C; ++cc) M[cc * nb] = R::add(M[cc * nb], t[cc]);
+      }
+    }
+  };
   for (int base = q0; base < q1; base += CH) {
     const int nq = min(CH, q1 - base);
     // (a) one thread per (side, point): mapped coordinates, sqrt(w), data
@@ -808,47 +924,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
     const int npt = 2 * nq;
     for (int id = tid; id < npt; id += blockDim.x) {
       const int side = id / nq, ql = id % nq, qg = base + ql;
-      const int k = qg / Q, q = qg % Q, g = s_grp[k];
-      const double cg = s_gc[g], ic2 = s_gic2[g];
-      if (side == 0) s_pgrp[ql] = g;
-      double x[DIM], tt = 0.0;
-      for (int d = 0; d < DIM; ++d) x[d] = 0.0;
-      for (int i = 0; i < NV; ++i) {
-        const double l = __ldg(a.bary + q * NV + i);
-        for (int d = 0; d < DIM; ++d) x[d] = fma(l, s_X[k][i][d], x[d]);
-        tt = fma(l, side == 0 ? s_tt[k][i] : s_tb[k][i], tt);
-      }
-      T* pp = sPt + id * (DIM + 2);
-      pp[0] = R::from(cg * (tt - tc) * ih);
-      for (int d = 0; d < DIM; ++d) pp[1 + d] = R::from((x[d] - s_xv[d]) * ih);
-      const double sw = __ldg(a.sqw + q) * s_sdet[k];
-      pp[DIM + 1] = R::from(sw);
+      const int k = qg / Q, q = qg % Q;
+      if (side == 0) s_pgrp[ql] = s_grp[k];
+      map_point(sPt + id * (DIM + 2), k, q, side == 0);
       if (keep && side == 0) sKeepW[base - q0 + ql] = __ldg(a.isqw + q) * s_isdet[k];
-      const int el = s_el[k];
-      if (ADJ && side == 0) {
-        // adjoint: zeta = sum_q lambda_q u_q over the top points
-        const double isw = __ldg(a.isqw + q) * s_isdet[k];
-        for (int r = 0; r < nrhs; ++r) {
-          const double* f = a.front + (((int64_t)r * a.ne + el) * Q + q) * C;
-          T* cb = sCB + ((size_t)ql * nrhs + r) * C;
-          for (int cc = 0; cc < C; ++cc) cb[cc] = R::from(__ldcg(f + cc) * isw);
-        }
-      }
-      if (!ADJ && side == 1) {
-        for (int r = 0; r < nrhs; ++r) {
-          const double* f = a.front + (((int64_t)r * a.ne + el) * Q + q) * C;
-          double fv[C];
-          for (int cc = 0; cc < C; ++cc) fv[cc] = __ldcg(f + cc);
-          const double Ub = fv[0], vb = fv[1];
-          double sg = 0.0;
-          for (int d = 0; d < DIM; ++d) sg = fma(fv[2 + d], s_gb[k][d], sg);
-          T* cb = sCB + ((size_t)ql * nrhs + r) * C;
-          cb[0] = R::from(sw * Ub);                       // gamma
-          cb[1] = R::from(sw * (ic2 * vb - sg));          // alpha
-          for (int d = 0; d < DIM; ++d) cb[2 + d] = R::from(sw * (fv[2 + d] - vb * s_gb[k][d]));   // beta_m
-        }
-      }
     }
+    // (with the right-hand sides split over the cluster the moments take a pass of their own)
+    if (!rsplit) data_coefs(base, nq);
     eval_uvalues_block<DIM, T>(a, npt, sPt, sM, sU);
     if (keep)
       for (int id = tid; id < nq * nb; id += blockDim.x) sKeep[(size_t)(base - q0) * nb + id] = sU[id];
@@ -875,20 +957,29 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
       }
     }
     // (c) moments of the data (forward: bottom points; adjoint: top points), per material
-    const int prow = ADJ ? 0 : nq;
-    for (int id = tid; id < ng * nmom; id += blockDim.x) {
-      const int g = id / nmom, rest = id % nmom;
-      const int r = rest / (C * nb), rem = rest % (C * nb), cc = rem / nb, i = rem % nb;
-      T t = R::zero();
-      for (int ql = 0; ql < nq; ++ql)
-        if (s_pgrp[ql] == g) t = R::acc(t, sCB[((size_t)ql * nrhs + r) * C + cc], sU[(size_t)(prow + ql) * nb + i]);
-      sPM[id] = R::add(sPM[id], R::norm(t));
-    }
+    if (!rsplit) data_moments(nq, ADJ ? 0 : nq);
     __syncthreads();
   }
   if (q1 > q0) {
     flush_element(curk);
     flush_group(curg);
+  }
+  if (rsplit) {
+    // this CTA's right-hand sides at every point of the patch (forward: the
+    // bottom points; adjoint: the top points): the moments are complete in
+    // this CTA and take no cluster reduction
+    for (int base = 0; base < NP; base += CH) {
+      const int nq = min(CH, NP - base);
+      for (int id = tid; id < nq; id += blockDim.x) {
+        const int qg = base + id, k = qg / Q, q = qg % Q;
+        s_pgrp[id] = s_grp[k];
+        map_point(sPt + id * (DIM + 2), k, q, ADJ);
+      }
+      data_coefs(base, nq);
+      eval_uvalues_block<DIM, T>(a, nq, sPt, sM, sU);
+      data_moments(nq, 0);
+      __syncthreads();
+    }
   }
 
   // ---------------- phase 2: vertical faces ----------------
@@ -914,7 +1005,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
     if (nneu > 0)
       for (int id = tid; id < nrhs * N; id += blockDim.x) sPBN[id] = R::zero();
     for (int id = tid; id < nrhs * nb; id += blockDim.x) sDel[id] = R::zero();
-    for (int id = tid; id < nb * nb; id += blockDim.x) sFpm[id] = R::zero();
+    if (nif > 0)
+      for (int id = tid; id < nb * nb; id += blockDim.x) sFpm[id] = R::zero();
     __syncthreads();
     // (a) Dirichlet facets: the points of all of them (facet after facet) in
     // one pass, split over the cluster; a facet's Gram and moments are folded
@@ -922,6 +1014,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
     if (nfac > 0) {
       const int NPD = nfac * Q, dsl = (NPD + CS - 1) / CS;
       const int d0 = min(NPD, rank * dsl), d1 = min(NPD, d0 + dsl);
+      // the Grams take this CTA's slice [d0, d1); the data moments of split
+      // right-hand sides take every point
+      const int l0 = rsplit ? 0 : d0, l1 = rsplit ? NPD : d1;
       T aF[kMaxPair];
 #pragma unroll
       for (int s = 0; s < kMaxPair; ++s) aF[s] = R::zero();
@@ -945,9 +1040,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
         for (int d = 0; d < DIM; ++d)
           Dg[(1 + d) * nrhs * nb + id] = R::fma(R::from(s_fn[f][d]), t, Dg[(1 + d) * nrhs * nb + id]);
       };
-      int fc = d0 / Q;   // facet of the points being accumulated (uniform over the CTA)
-      for (int base = d0; base < d1; base += CH) {
-        const int nq = min(CH, d1 - base);
+      int fc = l0 / Q;   // facet of the points being accumulated (uniform over the CTA)
+      for (int base = l0; base < l1; base += CH) {
+        const int nq = min(CH, l1 - base);
         for (int id = tid; id < nq; id += blockDim.x) {
           const int q = base + id, f = q / Q, qf = q - f * Q;
           double xt[DIM + 1];
@@ -964,12 +1059,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
           // the facet's block of boundary data (without Neumann facets: the facet's own index)
           const long long goff = a.tent_gdoff[tent] + (NEU ? (long long)s_fw[f][0] * Q + qf : (long long)q);
           for (int r = 0; r < nrhs; ++r)
-            sGd[id * nrhs + r] = R::from((!ADJ && a.gD != nullptr) ? sw * a.gD[(long long)r * a.n_bnd + goff] : 0.0);
+            sGd[id * nrhs + r] = R::from((!ADJ && gD != nullptr) ? sw * gD[(long long)r * a.n_bnd + goff] : 0.0);
         }
         eval_uvalues_block<DIM, T>(a, nq, sPt, sM, sU);
         const int fc0 = fc;
         for (int ql = 0; ql < nq; ++ql) {
           if (base + ql >= (fc + 1) * Q) fold_gram(fc++);
+          if (base + ql < d0 || base + ql >= d1) continue;   // another CTA's Gram points
           const T* u = sU + (size_t)ql * nb;
 #pragma unroll
           for (int s = 0; s < kMaxPair; ++s)
@@ -1013,8 +1109,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
       T aF[kMaxPair], aF2[kMaxPair];
 #pragma unroll
       for (int s = 0; s < kMaxPair; ++s) aF[s] = aF2[s] = R::zero();
-      for (int base = f0; base < f1; base += CH) {
-        const int nq = min(CH, f1 - base);
+      // (a Neumann facet's data moments of split right-hand sides take every point)
+      const int l0 = (rsplit && neu) ? 0 : f0, l1 = (rsplit && neu) ? Q : f1;
+      for (int base = l0; base < l1; base += CH) {
+        const int nq = min(CH, l1 - base);
         const int npt = neu ? nq : 2 * nq;   // interface: + side points, then - side
         for (int id = tid; id < nq; id += blockDim.x) {
           const int q = base + id;
@@ -1032,7 +1130,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
           if (neu) {
             const long long goff = a.tent_gdoff[tent] + (long long)s_fw[f][0] * Q + q;
             for (int r = 0; r < nrhs; ++r)
-              sGd[id * nrhs + r] = R::from((!ADJ && a.gD != nullptr) ? sw * a.gD[(long long)r * a.n_bnd + goff] : 0.0);
+              sGd[id * nrhs + r] = R::from((!ADJ && gD != nullptr) ? sw * gD[(long long)r * a.n_bnd + goff] : 0.0);
           } else {
             T* p2 = sPt + (nq + id) * (DIM + 2);
             p2[0] = R::from(cm * (xt[DIM] - tc) * ih);
@@ -1042,6 +1140,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
         }
         eval_uvalues_block<DIM, T>(a, npt, sPt, sM, sU);
         for (int ql = 0; ql < nq; ++ql) {
+          if (base + ql < f0 || base + ql >= f1) continue;   // another CTA's Gram points
           const T* u = sU + (size_t)ql * nb;
           const T* u2 = sU + (size_t)(nq + ql) * nb;
 #pragma unroll
@@ -1159,15 +1258,22 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
   cluster.sync();
   // layout [G (NG*npair) | H_m (NG*DIM*npair) | Gbot (NG*npair)]; unused groups hold zeros
   cluster_reduce(sPG, sSG, NG * (DIM + 2) * npair);
-  cluster_reduce(sPM, sSM, ng * nmom);   // in place (sSM == sPM): each entry has one owner
+  // (split right-hand sides: each CTA's moments, Dirichlet data sums and
+  // Neumann partial b already cover every point for its own right-hand sides)
+  if (!rsplit) cluster_reduce(sPM, sSM, ng * nmom);   // in place (sSM == sPM): each entry has one owner
   if (pblk) cluster_reduce(sPD, sA, N * N);   // interface and Neumann blocks
   else
     for (int id = tid; id < N * N; id += blockDim.x) sA[id] = R::zero();
-  if (NEU && s_nneu > 0) cluster_reduce(sFD + nfd, sb, nrhs * N);   // Neumann data (after the Dirichlet sums)
-  else
+  if (NEU && s_nneu > 0) {   // Neumann data (after the Dirichlet sums)
+    if (rsplit)
+      for (int id = tid; id < nrhs * N; id += blockDim.x) sb[id] = sFD[nfd + id];
+    else
+      cluster_reduce(sFD + nfd, sb, nrhs * N);
+  } else {
     for (int id = tid; id < nrhs * N; id += blockDim.x) sb[id] = R::zero();
+  }
   // in place: each entry is read and rewritten by the one thread that owns it
-  if (nfac > 0) cluster_reduce(sFD, sFD, nfd);
+  if (nfac > 0) cluster_reduce(sFD, sFD, rsplit ? ng * (DIM + 1) * npair : nfd);
   cluster.sync();   // no CTA leaves or reuses its partials while another still reads them
   // congruence: rank r forms rows [N r / CS, N (r + 1) / CS) of A and b and
   // stores them into rank 0's A and b; rank 0 alone solves.  Every CTA holds
@@ -1253,8 +1359,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
         A0[o2] = R::add(sA[o2], val);
       }
     }
-    for (int id = tid; id < nrhs * nrow; id += blockDim.x) {
-      const int r = id / nrow, Rw = row0 + id % nrow;
+    // (split right-hand sides: every row of this CTA's own b, kept in this CTA)
+    const int brow0 = rsplit ? 0 : row0, bnrow = rsplit ? N : nrow;
+    T* const bdst = rsplit ? sb : b0;
+    for (int id = tid; id < nrhs * bnrow; id += blockDim.x) {
+      const int r = id / bnrow, Rw = brow0 + id % bnrow;
       const int g = Rw / nb, i = Rw % nb;
       const T* M = sSM + (size_t)g * nmom + (size_t)r * C * nb;   // gamma, alpha, beta_1..beta_n
       T t = R::fma(R::from(s_gc[g] * ih), rel_apply<DIM, T>(a, i, 0, M + nb), M[i]);
@@ -1269,11 +1378,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
         t = R::add(t, R::fma(R::from(ih), dn, R::mul(ac, rel_apply<DIM, T>(a, i, 0, Dg))));
       }
       const size_t o = (size_t)r * N + Rw;
-      b0[o] = R::add(sb[o], t);
+      bdst[o] = R::add(sb[o], t);
     }
   }
   cluster.sync();   // rank 0 holds the assembled A and b
-  if (rank == 0) {
+  if (rsplit) {
+    // every CTA solves for its own right-hand sides with its own copy of A
+    if (rank != 0)
+      for (int id = tid; id < N * N; id += blockDim.x) sA[id] = A0[id];
+    cluster.sync();   // rank 0's A is read before any CTA's solve overwrites its own
+  }
+  if (rank == 0 || rsplit) {
   if constexpr (ADJ) {   // solve with A^T
     for (int id = tid; id < N * N; id += blockDim.x) {
       const int i = id / N, j = id % N;
@@ -1423,7 +1538,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
     __syncthreads();
     // refinement
     float prev = 3.4e38f;
-    const int maxit = kMaxRefine;
+    const int maxit = min(a.max_refine, kMaxRefine);
     for (int it = 0; it < maxit; ++it) {
       // residual b - A x, each row split over 8 lanes of one warp; stored
       // scaled by D in binary32 (the first iterate is x = 0: the residual is b)
@@ -1537,6 +1652,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
       prev = dm;
       if (done) {
         refined = true;
+        if (a.solve_stats != nullptr && tid == 0) atomicAdd(a.solve_stats + 1 + min(it + 1, kMaxRefine), 1ull);
         break;
       }
       // (the next iteration writes s_red only after its first barrier)
@@ -1548,6 +1664,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
     }
   }
   if (!refined) {   // direct binary64 LU (the mixed path converts A and b to binary64 first)
+    if (a.solve_stats != nullptr && tid == 0) atomicAdd(a.solve_stats, 1ull);
     __syncthreads();
     double* dA = reinterpret_cast<double*>(sA);   // in place: a float-float pair and a double share 8 bytes
     double* db = reinterpret_cast<double*>(sb);
@@ -1674,10 +1791,18 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
       }
     }
   }
-  }   // rank 0
-  cluster.sync();   // the solution is in rank 0's b
-  if (rank != 0)
+  }   // rank 0 (every rank with split right-hand sides)
+  cluster.sync();   // the solution is in rank 0's b (split right-hand sides: in each CTA's own)
+  if (rank != 0 && !rsplit)
     for (int id = tid; id < nrhs * N; id += blockDim.x) sb[id] = b0[id];
+  if constexpr (!ADJ) {
+    // the forward solution kept for the reverse sweep of the wave-speed gradient
+    if (a.xsave != nullptr && (rank == 0 || rsplit)) {
+      const int NBg = NG * nb;
+      double* xs = a.xsave + (size_t)(tent - a.xbase) * a.xs_stride + (size_t)(rsplit ? rank * nrhs : 0) * NBg;
+      for (int id = tid; id < nrhs * N; id += blockDim.x) xs[(size_t)(id / N) * NBg + id % N] = R::to(sb[id]);
+    }
+  }
   __syncthreads();
 
   // ---------------- phase 4: outflow at this CTA's top points (adjoint: bottom points) ----------------
@@ -1692,8 +1817,329 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
     sY[id] = t;
   }
   __syncthreads();
-  for (int base = q0; base < q1; base += 2 * CH) {
-    const int nq = min(2 * CH, q1 - base);
+  // the points whose front values this CTA overwrites (split right-hand
+  // sides: this CTA's own right-hand sides at every point)
+  const int o0 = rsplit ? 0 : q0, o1 = rsplit ? NP : q1;
+  // ---------------- energy lost in the tent (forward sweep, when tracked) ----------------
+  // Testing the tent system with V = U_h and using d/dt e + div(v sigma) = 0
+  // inside the Trefftz tent: 1/2 int_top Q_{g_t}(u) = 1/2 int_bot Q_{g_b}(u_b) - D,
+  //   D = 1/2 int_bot Q_{g_b}(u - u_b) + int_bot (U - U_b) U
+  //     + int_D [alpha v^2 - g_D (alpha v - sigma.n)] + int_N [beta (sigma.n)^2 - g_N (beta sigma.n - v)]
+  //     + int_time [alpha (v+ - v-)^2 + beta ((sigma+ - sigma-).n)^2]
+  // (eq. 2.5, eq. 4.1, Section 6.5; Q_g(w) = c^-2 w_v^2 + |w_s|^2 - 2 w_v w_s.g).
+  // Point values of the solution come from the outflow vectors and U-values
+  // scaled by sqrt(w); the stored bottom values are read before this CTA
+  // overwrites them below.  Summed over the sweep: E(T) = E(0) - sum D.
+  if constexpr (!ADJ) {
+    if (a.diss != nullptr) {
+      double* sDis = reinterpret_cast<double*>(sDel);   // nrhs partial sums (sDel is dead after phase 2)
+      double* sFb = reinterpret_cast<double*>(sCB);     // CH*nrhs*C stored values (sCB is dead after phase 1)
+      double* sGdd = reinterpret_cast<double*>(sGd);    // CH*nrhs boundary data (dead after phase 2)
+      for (int id = tid; id < nrhs; id += blockDim.x) sDis[id] = 0.0;
+      __syncthreads();
+      auto fieldv = [&](int g, int r, int cc, const T* u) {   // sqrt(w) times component cc of the solution
+        const T* y = sY + (size_t)g * nmom + ((size_t)r * C + cc) * nb;
+        T t = R::zero();
+        for (int j = 0; j < nb; ++j) t = R::acc(t, y[j], u[j]);
+        return R::to(R::norm(t));
+      };
+      // (a) bottom face: the jump to the stored front and the recovery term
+      for (int base = o0; base < o1; base += CH) {
+        const int nq = min(CH, o1 - base);
+        for (int id = tid; id < nq; id += blockDim.x) {
+          const int qg = base + id;
+          map_point(sPt + id * (DIM + 2), qg / Q, qg % Q, false);
+        }
+        for (int id = tid; id < nq * nrhs; id += blockDim.x) {
+          const int ql = id / nrhs, r = id % nrhs, qg = base + ql, k = qg / Q, q = qg % Q;
+          const double sw = __ldg(a.sqw + q) * s_sdet[k];
+          const double* f = front + (((int64_t)r * a.ne + s_el[k]) * Q + q) * C;
+#pragma unroll
+          for (int cc = 0; cc < C; ++cc) sFb[(size_t)id * C + cc] = sw * __ldcg(f + cc);
+        }
+        eval_uvalues_block<DIM, T>(a, nq, sPt, sM, sU);
+        for (int id = tid; id < nq * nrhs; id += blockDim.x) {
+          const int ql = id / nrhs, r = id % nrhs, k = (base + ql) / Q, g = s_grp[k];
+          const T* u = sU + (size_t)ql * nb;
+          const double* fb = sFb + (size_t)id * C;
+          const double Uh = fieldv(g, r, 0, u), dv = fieldv(g, r, 1, u) - fb[1];
+          double ds2 = 0.0, dsg = 0.0;
+          for (int d = 0; d < DIM; ++d) {
+            const double ds = fieldv(g, r, 2 + d, u) - fb[2 + d];
+            ds2 = fma(ds, ds, ds2);
+            dsg = fma(ds, s_gb[k][d], dsg);
+          }
+          atomicAdd(sDis + r, 0.5 * (s_gic2[g] * dv * dv + ds2 - 2.0 * dv * dsg) + (Uh - fb[0]) * Uh);
+        }
+        __syncthreads();
+      }
+      // (b) vertical faces: Dirichlet, then interface, then Neumann facets,
+      // each facet's points split over the cluster (split right-hand sides: every point)
+      const int fsl = (Q + CS - 1) / CS;
+      const int p0 = rsplit ? 0 : min(Q, rank * fsl), p1 = rsplit ? Q : min(Q, p0 + fsl);
+      for (int f = 0; f < nfac + nif + nneu; ++f) {
+        const bool ifc = f >= nfac && f < nfac + nif, neu = NEU && f >= nfac + nif;
+        const int gp = s_fg[f], gm = s_fg2[f];
+        for (int base = p0; base < p1; base += CH) {
+          const int nq = min(CH, p1 - base);
+          for (int id = tid; id < nq; id += blockDim.x) {
+            const int q = base + id;
+            double xt[DIM + 1];
+            for (int d = 0; d <= DIM; ++d) xt[d] = 0.0;
+            for (int i = 0; i < NV; ++i) {
+              const double l = __ldg(a.bary + q * NV + i);
+              for (int d = 0; d <= DIM; ++d) xt[d] = fma(l, s_fP[f][i][d], xt[d]);
+            }
+            const double sw = __ldg(a.sqw + q) * s_fsq[f];
+            T* pp = sPt + id * (DIM + 2);
+            pp[0] = R::from(s_gc[gp] * (xt[DIM] - tc) * ih);
+            for (int d = 0; d < DIM; ++d) pp[1 + d] = R::from((xt[d] - s_xv[d]) * ih);
+            pp[DIM + 1] = R::from(sw);
+            if (ifc) {
+              T* p2 = sPt + (nq + id) * (DIM + 2);
+              p2[0] = R::from(s_gc[gm] * (xt[DIM] - tc) * ih);
+              for (int d = 0; d < DIM; ++d) p2[1 + d] = pp[1 + d];
+              p2[DIM + 1] = pp[DIM + 1];
+            } else {
+              // the facet's block of boundary data (without Neumann facets: the facet's own index)
+              const long long goff = a.tent_gdoff[tent] + (NEU ? (long long)s_fw[f][0] * Q : (long long)f * Q) + q;
+              for (int r = 0; r < nrhs; ++r)
+                sGdd[id * nrhs + r] = gD != nullptr ? sw * gD[(long long)r * a.n_bnd + goff] : 0.0;
+            }
+          }
+          eval_uvalues_block<DIM, T>(a, ifc ? 2 * nq : nq, sPt, sM, sU);
+          for (int id = tid; id < nq * nrhs; id += blockDim.x) {
+            const int ql = id / nrhs, r = id % nrhs;
+            const T* u = sU + (size_t)ql * nb;
+            const double vh = fieldv(gp, r, 1, u);
+            double sn = 0.0;
+            for (int d = 0; d < DIM; ++d) sn = fma(s_fn[f][d], fieldv(gp, r, 2 + d, u), sn);
+            double val;
+            if (ifc) {
+              const T* u2 = sU + (size_t)(nq + ql) * nb;
+              double sn2 = 0.0;
+              for (int d = 0; d < DIM; ++d) sn2 = fma(s_fn[f][d], fieldv(gm, r, 2 + d, u2), sn2);
+              const double jv = vh - fieldv(gm, r, 1, u2), js = sn - sn2;
+              val = a.alpha * jv * jv + a.beta * js * js;
+            } else {
+              const double gv = sGdd[id];
+              val = neu ? a.beta * sn * sn - gv * (a.beta * sn - vh) : a.alpha * vh * vh - gv * (a.alpha * vh - sn);
+            }
+            atomicAdd(sDis + r, val);
+          }
+          __syncthreads();
+        }
+      }
+      double* diss = a.diss + (rsplit ? (size_t)rank * nrhs : 0);
+      for (int r = tid; r < nrhs; r += blockDim.x) atomicAdd(diss + r, sDis[r]);
+      __syncthreads();
+    }
+  }
+  // ---------------- wave-speed gradient (reverse sweep, when requested) ----------------
+  // With the tents held fixed, J depends on the speed c_g of material g
+  // through every tent's maps b = B f_bot, A x = b, f_top = E x (eq. 4.1), so
+  //   dJ/dc_g += lambda_top . (dE/dc_g) x + mu^T ((dB/dc_g) f_bot - (dA/dc_g) x),
+  // x the tent's forward solution, f_bot the forward front below it,
+  // lambda_top the adjoint front at its top points, mu = A^-T E^T lambda_top.
+  // With t^ = c (t - t_c)/h (Remark 3.1) the fields F = (U, v, sigma) of a
+  // coefficient vector x move with c as
+  //   dF/dc = ((t - t_c)/c) F(x') + (0, v/c, 0),   x' = (c/h) D_t^T x
+  // (the time derivative of U_h is again in U^p), so every derivative is a
+  // point value of the forms of eq. (4.1) and eq. (2.5) on F and dF; the
+  // only explicit c of the forms is c^-2 of the top and bottom faces.  Each
+  // point's contribution is booked on its element (a facet's on the element
+  // of its side): summed over the elements of a material it is dJ/dc of
+  // that material.
+  if constexpr (ADJ) {
+    if (a.dJdc != nullptr) {
+      const int NBg = NG * nb;
+      T* sYx = reinterpret_cast<T*>(sm + a.off_yg);   // NG*nmom  y(x)
+      T* sYxp = sYx + (size_t)NG * nmom;               // NG*nmom  y(x')
+      T* sYmp = sYxp + (size_t)NG * nmom;              // NG*nmom  y(mu')
+      T* sXf = sYmp + (size_t)NG * nmom;               // nrhs*N   forward solution
+      const int rg0 = rsplit ? rank * nrhs : 0;
+      {
+        const double* xs = a.xsave + (size_t)(tent - a.xbase) * a.xs_stride;
+        for (int id = tid; id < nrhs * N; id += blockDim.x) sXf[id] = R::from(xs[(size_t)(rg0 + id / N) * NBg + id % N]);
+      }
+      for (int k = tid; k < P; k += blockDim.x) s_gel[k] = 0.0;
+      __syncthreads();
+      // y = (z_g, (c/h) D_t^T z_g, -(1/h) D_m^T z_g) of a coefficient vector z per material and right-hand side
+      auto coefs = [&](T* dst, const T* src, int rstride, int gstride) {
+        for (int id = tid; id < ng * nmom; id += blockDim.x) {
+          const int g = id / nmom, rest = id % nmom;
+          const int r = rest / (C * nb), rem = rest % (C * nb), cc = rem / nb, kk = rem % nb;
+          const T* zg = src + (size_t)r * rstride + (size_t)g * gstride;
+          dst[id] = cc == 0 ? zg[kk]
+                            : R::mul(R::from(cc == 1 ? s_gc[g] * ih : -ih), relT_apply<DIM, T>(a, kk, cc - 1, zg));
+        }
+      };
+      coefs(sYx, sXf, N, nb);
+      coefs(sYmp, sY + nb, C * nb, nmom);              // mu' = y_v(mu)
+      __syncthreads();
+      coefs(sYxp, sYx + nb, C * nb, nmom);             // x' = y_v(x)
+      __syncthreads();
+      // sqrt(w) times the C components of the field of vectors Y at U-values u
+      auto fld = [&](const T* Y, int g, int r, const T* u, double* F) {
+        for (int cc = 0; cc < C; ++cc) {
+          const T* y = Y + (size_t)g * nmom + ((size_t)r * C + cc) * nb;
+          T t = R::zero();
+          for (int j = 0; j < nb; ++j) t = R::acc(t, y[j], u[j]);
+          F[cc] = R::to(R::norm(t));
+        }
+      };
+      // fields of x and mu and their c-derivatives at a point of material g
+      auto fields4 = [&](int g, int r, const T* u, double tq, double* Fx, double* dFx, double* Fm, double* dFm) {
+        const double cg = s_gc[g];
+        fld(sYx, g, r, u, Fx);
+        fld(sYxp, g, r, u, dFx);
+        fld(sY, g, r, u, Fm);
+        fld(sYmp, g, r, u, dFm);
+        for (int cc = 0; cc < C; ++cc) {
+          dFx[cc] *= tq / cg;
+          dFm[cc] *= tq / cg;
+        }
+        dFx[1] += Fx[1] / cg;
+        dFm[1] += Fm[1] / cg;
+      };
+      // (a) top points (the map E and the top form) and bottom points (the
+      // bottom form of b and the recovery terms), this CTA's points
+      for (int side = 0; side < 2; ++side) {
+        for (int base = o0; base < o1; base += CH) {
+          const int nq = min(CH, o1 - base);
+          for (int id = tid; id < nq; id += blockDim.x) {
+            const int qg = base + id;
+            map_point(sPt + id * (DIM + 2), qg / Q, qg % Q, side == 0);
+          }
+          eval_uvalues_block<DIM, T>(a, nq, sPt, sM, sU);
+          for (int id = tid; id < nq * nrhs; id += blockDim.x) {
+            const int ql = id / nrhs, r = id % nrhs, qg = base + ql, k = qg / Q, q = qg % Q, g = s_grp[k];
+            double tt = 0.0;
+            for (int i = 0; i < NV; ++i) tt = fma(__ldg(a.bary + q * NV + i), side == 0 ? s_tt[k][i] : s_tb[k][i], tt);
+            double Fx[C], dFx[C], Fm[C], dFm[C];
+            fields4(g, r, sU + (size_t)ql * nb, tt - tc, Fx, dFx, Fm, dFm);
+            const double ic2 = s_gic2[g], dic2 = -2.0 * ic2 / s_gc[g];   // c^-2 and its derivative
+            const double* gk = side == 0 ? s_gt[k] : s_gb[k];
+            // c^-2 a_v b_v + a_s.b_s - a_v (b_s.g) - (a_s.g) b_v: the face form of eq. (4.1)
+            auto Qf = [&](const double* A_, const double* B_) {
+              double s2 = ic2 * A_[1] * B_[1], ag = 0.0, bg = 0.0;
+              for (int d = 0; d < DIM; ++d) {
+                s2 = fma(A_[2 + d], B_[2 + d], s2);
+                ag = fma(A_[2 + d], gk[d], ag);
+                bg = fma(B_[2 + d], gk[d], bg);
+              }
+              return s2 - A_[1] * bg - ag * B_[1];
+            };
+            double val;
+            if (side == 0) {
+              const double* lam = front + (((int64_t)r * a.ne + s_el[k]) * Q + q) * C;
+              const double isw = __ldg(a.isqw + q) * s_isdet[k];
+              double e = 0.0;
+              for (int cc = 0; cc < C; ++cc) e = fma(__ldcg(lam + cc) * isw, dFx[cc], e);
+              val = e - (Qf(dFx, Fm) + Qf(Fx, dFm) + dic2 * Fx[1] * Fm[1]);
+            } else {
+              const double sw = __ldg(a.sqw + q) * s_sdet[k];
+              const double* f0 = a.front_fwd + (((int64_t)(rg0 + r) * a.ne + s_el[k]) * Q + q) * C;
+              double fb[C];
+              for (int cc = 0; cc < C; ++cc) fb[cc] = sw * __ldcg(f0 + cc);
+              val = Qf(fb, dFm) + dic2 * fb[1] * Fm[1] + fb[0] * dFm[0] - (dFx[0] * Fm[0] + Fx[0] * dFm[0]);
+            }
+            atomicAdd(s_gel + k, val);
+          }
+          __syncthreads();
+        }
+      }
+      // (b) vertical faces: Dirichlet, interface and Neumann facets (each
+      // facet's points split over the cluster; split right-hand sides: every point)
+      const int fsl = (Q + CS - 1) / CS;
+      const int p0 = rsplit ? 0 : min(Q, rank * fsl), p1 = rsplit ? Q : min(Q, p0 + fsl);
+      const int* rfi = a.vrec_i + h0.y + P * (2 + NV);
+      double* sGdd = reinterpret_cast<double*>(sGd);
+      for (int f = 0; f < nfac + nif + nneu; ++f) {
+        const bool ifc = f >= nfac && f < nfac + nif, neu = NEU && f >= nfac + nif;
+        const int gp = s_fg[f], gm = s_fg2[f];
+        // patch slots of the elements on the facet's + and - sides (boundary facets: one element)
+        int kp = 0, km = 0;
+        {
+          const int ep = __ldg(rfi + f * (NV + 3)), em = __ldg(rfi + f * (NV + 3) + 1);
+          for (int k = 0; k < P; ++k) {
+            if (s_el[k] == ep) kp = k;
+            if (s_el[k] == em) km = k;
+          }
+        }
+        for (int base = p0; base < p1; base += CH) {
+          const int nq = min(CH, p1 - base);
+          for (int id = tid; id < nq; id += blockDim.x) {
+            const int q = base + id;
+            double xt[DIM + 1];
+            for (int d = 0; d <= DIM; ++d) xt[d] = 0.0;
+            for (int i = 0; i < NV; ++i) {
+              const double l = __ldg(a.bary + q * NV + i);
+              for (int d = 0; d <= DIM; ++d) xt[d] = fma(l, s_fP[f][i][d], xt[d]);
+            }
+            const double sw = __ldg(a.sqw + q) * s_fsq[f];
+            T* pp = sPt + id * (DIM + 2);
+            pp[0] = R::from(s_gc[gp] * (xt[DIM] - tc) * ih);
+            for (int d = 0; d < DIM; ++d) pp[1 + d] = R::from((xt[d] - s_xv[d]) * ih);
+            pp[DIM + 1] = R::from(sw);
+            if (ifc) {
+              T* p2 = sPt + (nq + id) * (DIM + 2);
+              p2[0] = R::from(s_gc[gm] * (xt[DIM] - tc) * ih);
+              for (int d = 0; d < DIM; ++d) p2[1 + d] = pp[1 + d];
+              p2[DIM + 1] = pp[DIM + 1];
+            } else {
+              // the forward boundary data of the facet (g_D or g_N)
+              const long long goff = a.tent_gdoff[tent] + (NEU ? (long long)s_fw[f][0] * Q : (long long)f * Q) + q;
+              for (int r = 0; r < nrhs; ++r)
+                sGdd[id * nrhs + r] = gD != nullptr ? sw * gD[(long long)r * a.n_bnd + goff] : 0.0;
+            }
+          }
+          eval_uvalues_block<DIM, T>(a, ifc ? 2 * nq : nq, sPt, sM, sU);
+          for (int id = tid; id < nq * nrhs; id += blockDim.x) {
+            const int ql = id / nrhs, r = id % nrhs, q = base + ql;
+            double tt = 0.0;
+            for (int i = 0; i < NV; ++i) tt = fma(__ldg(a.bary + q * NV + i), s_fP[f][i][DIM], tt);
+            double Fx[C], dFx[C], Fm[C], dFm[C];
+            fields4(gp, r, sU + (size_t)ql * nb, tt - tc, Fx, dFx, Fm, dFm);
+            auto sn = [&](const double* F_) {
+              double t_ = 0.0;
+              for (int d = 0; d < DIM; ++d) t_ = fma(s_fn[f][d], F_[2 + d], t_);
+              return t_;
+            };
+            if (ifc) {
+              double Gx[C], dGx[C], Gm[C], dGm[C], Z[C];
+              fields4(gm, r, sU + (size_t)(nq + ql) * nb, tt - tc, Gx, dGx, Gm, dGm);
+              for (int cc = 0; cc < C; ++cc) Z[cc] = 0.0;
+              // the interface form of eq. (2.5) with trial fields X+-, test fields M+-
+              auto I = [&](const double* Xp, const double* Xm, const double* Mp, const double* Mm) {
+                const double jm = sn(Mp) - sn(Mm), dv = Mp[1] - Mm[1];
+                return 0.5 * (jm * (Xp[1] + Xm[1]) + dv * (sn(Xp) + sn(Xm))) + a.alpha * dv * (Xp[1] - Xm[1]) +
+                       a.beta * jm * (sn(Xp) - sn(Xm));
+              };
+              atomicAdd(s_gel + kp, -(I(dFx, Z, Fm, Gm) + I(Fx, Gx, dFm, Z)));
+              atomicAdd(s_gel + km, -(I(Z, dGx, Fm, Gm) + I(Fx, Gx, Z, dGm)));
+            } else {
+              const double gv = sGdd[id];
+              double val;
+              if (neu) {   // A: v (tau.n) + beta (sigma.n)(tau.n); b: g_N (beta tau.n - w)
+                val = gv * (a.beta * sn(dFm) - dFm[1]) -
+                      (dFx[1] * sn(Fm) + Fx[1] * sn(dFm) + a.beta * (sn(dFx) * sn(Fm) + sn(Fx) * sn(dFm)));
+              } else {     // A: (sigma.n + alpha v) w; b: g_D (alpha w - tau.n)
+                val = gv * (a.alpha * dFm[1] - sn(dFm)) -
+                      ((sn(dFx) + a.alpha * dFx[1]) * Fm[1] + (sn(Fx) + a.alpha * Fx[1]) * dFm[1]);
+              }
+              atomicAdd(s_gel + kp, val);
+            }
+          }
+          __syncthreads();
+        }
+      }
+      for (int k = tid; k < P; k += blockDim.x) atomicAdd(a.dJdc + s_el[k], s_gel[k]);
+      __syncthreads();
+    }
+  }
+  for (int base = o0; base < o1; base += 2 * CH) {
+    const int nq = min(2 * CH, o1 - base);
     if (!keep) {
     for (int id = tid; id < nq; id += blockDim.x) {
       const int qg = base + id, k = qg / Q, q = qg % Q;
@@ -1713,16 +2159,25 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
     eval_uvalues_block<DIM, T, false>(a, nq, sPt, sM, sU);
     }
     if constexpr (!ADJ) {
-      for (int id = tid; id < nq * nrhs * C; id += blockDim.x) {
-        const int ql = id / (nrhs * C), rc = id % (nrhs * C), r = rc / C, cc = rc % C;
+      // one (point, right-hand side) per thread, its C components as
+      // independent sums (consecutive threads: consecutive points)
+      for (int id = tid; id < nq * nrhs; id += blockDim.x) {
+        const int r = id / nq, ql = id % nq;
         const int qg = base + ql, k = qg / Q, q = qg % Q;
         const T* u = keep ? sKeep + (size_t)(base - q0 + ql) * nb : sU + (size_t)ql * nb;
-        const T* y = sY + (size_t)s_grp[k] * nmom + ((size_t)r * C + cc) * nb;
-        T t = R::zero();
-        for (int j = 0; j < nb; ++j) t = R::acc(t, y[j], u[j]);
-        t = R::norm(t);
-        const double val = keep ? R::to(t) * sKeepW[base - q0 + ql] : R::to(t);
-        a.front[(((int64_t)r * a.ne + s_el[k]) * Q + q) * C + cc] = val;
+        const T* y = sY + (size_t)s_grp[k] * nmom + (size_t)r * C * nb;
+        T t[C];
+#pragma unroll
+        for (int cc = 0; cc < C; ++cc) t[cc] = R::zero();
+        for (int j = 0; j < nb; ++j) {
+          const T uj = u[j];
+#pragma unroll
+          for (int cc = 0; cc < C; ++cc) t[cc] = R::acc(t[cc], y[cc * nb + j], uj);
+        }
+        const double sc = keep ? sKeepW[base - q0 + ql] : 1.0;
+        double* f = front + (((int64_t)r * a.ne + s_el[k]) * Q + q) * C;
+#pragma unroll
+        for (int cc = 0; cc < C; ++cc) f[cc] = R::to(R::norm(t[cc])) * sc;
       }
     } else {
       // lambda_bot = w (s0, c^-2 s_t - g_b.s, s_m - g_b,m s_t)
@@ -1743,7 +2198,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
         const double w = sq * sq;
         double gs = 0.0;
         for (int d = 0; d < DIM; ++d) gs = fma(s_gb[k][d], sv[2 + d], gs);
-        double* f = a.front + (((int64_t)r * a.ne + s_el[k]) * Q + q) * C;
+        double* f = front + (((int64_t)r * a.ne + s_el[k]) * Q + q) * C;
         f[0] = w * sv[0];
         f[1] = w * (sv[1] / (cg * cg) - gs);
         for (int d = 0; d < DIM; ++d) f[2 + d] = w * (sv[2 + d] - s_gb[k][d] * sv[1]);

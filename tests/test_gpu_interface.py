@@ -55,20 +55,22 @@ def test_inclusion_matches_oracle(cuda_device, precision, tol):
     assert rel <= tol, rel
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-8)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("mixed", 1e-8)])
 def test_inclusion_degree5_matches_oracle(cuda_device, precision, tol):
     """The inclusion workload at the degree of the heterogeneous target
-    configuration (p = 5: 36 unknowns per material, 72 on interface tents),
-    which takes the shared-memory Gauss-Jordan path and row interchanges.
-    Two binary64 solvers of the same tent system agree to about kappa(A) u;
-    at p = 5 kappa(A) is ~200x its p = 4 value (up to 7e8), so the binary64
-    path is held to 1e-10 here (1e-11 at p <= 4)."""
+    configuration (p = 5: 36 unknowns per material, 72 on interface tents,
+    more than the 32 the register Gauss-Jordan holds: the shared-memory
+    Gauss-Jordan path, without row interchanges).  At p = 5 the tent systems
+    reach kappa(A) ~ 1e8 and one binary64 LU moves the oracle's own sweep by
+    6e-12 on this mesh, so the reference solves every tent system with
+    extended-precision refinement (oracle.tdg.solve_refined, pinned against
+    an exact rational solve); against it the binary64 path keeps 1e-11."""
     w = inputs.workload("inclusion_small")
     m = w.mesh
     s, got, tau, st = _run(m, 5, w.T, w.kappa, w.init, None, precision)
     assert st == (0, 0)
     r = pitching.pitch(m.coords, m.elems, m.c, w.kappa, w.T)
-    ref, rtau = tdg.sweep(m.coords, m.elems, m.c, 5, r, w.init, None)
+    ref, rtau = tdg.sweep(m.coords, m.elems, m.c, 5, r, w.init, None, refine=True)
     assert np.array_equal(tau, rtau)
     rel = float(np.linalg.norm(got.reshape(ref.shape) - ref) / np.linalg.norm(ref))
     assert rel <= tol, rel

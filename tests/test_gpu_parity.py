@@ -24,12 +24,12 @@ def _rel(a, b):
 
 
 def _gpu_run(mesh, p, T, kappa, init, dirichlet, nrhs_inits=None, alpha=0.5, levels=None,
-             layerwise=False, precision="fp64", schedule="dataflow"):
+             layerwise=False, precision="fp64", schedule="dataflow", rhs_split=0):
     import torch
     import paper_1907_02367_gb300 as pkg
     inits = nrhs_inits or [init]
     s = pkg.Solver(mesh.coords, mesh.elems, mesh.c, p, T, kappa, alpha=alpha, nrhs=len(inits),
-                   precision=precision, schedule=schedule)
+                   precision=precision, schedule=schedule, rhs_split=rhs_split)
     xq, wq = s.front_points()
     f0 = np.stack([np.asarray(f(xq)) for f in inits])
     front0 = torch.tensor(f0, dtype=torch.float64, device="cuda").contiguous()
@@ -309,13 +309,15 @@ def test_mixed_many_rhs(cuda_device):
 def test_many_rhs_3d(cuda_device, precision, tol):
     """Thirty-two Gaussian pulses (seeded centres and widths) advanced together
     in 3D at p = 3, sharing every tent's factorisation (the shape of the
-    many-right-hand-side target configuration; 32 is the most one CTA's
-    shared memory holds at p = 3 in 3D); columns against the oracle."""
+    many-right-hand-side target configuration), all in one CTA per slice of
+    points (rhs_split = 1; 32 is the most one CTA's shared memory holds at
+    p = 3 in 3D); columns against the oracle."""
     m = inputs.mesh_cube(2, 0.1, seed=4)
     kappa = inputs.pitch_kappa(m)
     rng = np.random.default_rng(44)
     inits = [inputs.gaussian_pulse(rng.uniform(0.25, 0.75, 3), rng.uniform(0.15, 0.3)) for _ in range(32)]
-    s, got, tau, st = _gpu_run(m, 3, 0.1, kappa, None, None, nrhs_inits=inits, precision=precision)
+    s, got, tau, st = _gpu_run(m, 3, 0.1, kappa, None, None, nrhs_inits=inits, precision=precision,
+                               rhs_split=1)
     assert st == (0, 0)
     got = got.reshape(len(inits), m.n_elem, -1, 5)
     for r in (0, 17, 31):
@@ -326,22 +328,25 @@ def test_many_rhs_3d(cuda_device, precision, tol):
 @pytest.mark.parametrize("precision,tol,schedule", [("fp64", TOL, "dataflow"), ("mixed", MIXED_TOL, "dataflow"),
                                                      ("fp64", TOL, "levels")])
 def test_many_rhs_3d_in_groups(cuda_device, precision, tol, schedule):
-    """Sixty-four Gaussian pulses in 3D at p = 3: more right-hand sides than
-    one CTA's shared memory holds, so the library sweeps them in two groups
-    of 32 from the same front times; columns of both groups against the
-    oracle, and the front times after the sweep are the pitched ones."""
+    """Sixty-four Gaussian pulses in 3D at p = 3 kept together in each CTA
+    (rhs_split = 1): more right-hand sides than one CTA's shared memory
+    holds, so the library sweeps them in two groups of 32 from the same
+    front times; columns of both groups against the oracle, and the front
+    times after the sweep are the pitched ones.  The default (the 64 split
+    over clusters of 4 CTAs of 16, one group) is checked the same way."""
     m = inputs.mesh_cube(2, 0.1, seed=4)
     kappa = inputs.pitch_kappa(m)
     rng = np.random.default_rng(44)
     inits = [inputs.gaussian_pulse(rng.uniform(0.25, 0.75, 3), rng.uniform(0.15, 0.3)) for _ in range(64)]
-    s, got, tau, st = _gpu_run(m, 3, 0.1, kappa, None, None, nrhs_inits=inits, precision=precision,
-                               schedule=schedule)
-    assert st == (0, 0)
-    got = got.reshape(len(inits), m.n_elem, -1, 5)
-    for r in (0, 31, 32, 63):
-        ref, tau_ref, _ = _oracle(m, 3, 0.1, kappa, inits[r], None)
-        assert _rel(got[r], ref) <= tol, r
-    assert np.array_equal(tau, tau_ref)
+    for split in (1, 0):
+        s, got, tau, st = _gpu_run(m, 3, 0.1, kappa, None, None, nrhs_inits=inits, precision=precision,
+                                   schedule=schedule, rhs_split=split)
+        assert st == (0, 0)
+        got = got.reshape(len(inits), m.n_elem, -1, 5)
+        for r in (0, 31, 32, 63):
+            ref, tau_ref, _ = _oracle(m, 3, 0.1, kappa, inits[r], None)
+            assert _rel(got[r], ref) <= tol, (split, r)
+        assert np.array_equal(tau, tau_ref)
 
 
 def test_autotune_keeps_results(cuda_device):

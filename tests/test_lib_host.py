@@ -136,39 +136,23 @@ def test_no_cpu_fallback(libtp, tmp_path):
         B._lib = saved
 
 
-def test_many_rhs_3d_stored_oracle_matches_the_pitching(libtp):
-    """The stored oracle values of the full-size 3+1D workload
-    (tests/golden/many_rhs_3d_oracle.json) cover the tents of levels 1-2 of
-    the library's pitching of that mesh."""
-    import json
-    import os
+@pytest.mark.parametrize("name,levels", [("many_rhs_3d", 2), ("inclusion_graded", 4)])
+def test_full_size_pitching_prefix_matches_oracle(libtp, name, levels):
+    """The two large workloads' pitching: the library's tents of the first
+    levels equal, bit for bit and in order, the oracle's (the oracle pitches
+    up to that level only: its full pitch of the graded mesh takes tens of
+    minutes); the full-size GPU parity tests compare these tents."""
+    from oracle import pitching
     import paper_1907_02367_gb300 as pkg
-    with open(os.path.join(os.path.dirname(__file__), "golden", "many_rhs_3d_oracle.json")) as f:
-        g = json.load(f)
-    w = inputs.workload("many_rhs_3d")
-    assert w.mesh.n_elem == 48000
-    lev = pkg.Tents(w.mesh.coords, w.mesh.elems, w.mesh.c, w.kappa, w.T).export()["level"]
-    assert int(np.sum(lev <= g["levels"])) == g["n_tents"]
-    assert [c["column"] for c in g["columns"]] == [0, 63] and len(inputs.gaussian_pulses_3d()) == 64
-
-
-def test_inclusion_graded_stored_oracle_matches_the_pitching(libtp):
-    """The stored oracle values of the full-size graded inclusion workload
-    (tests/golden/inclusion_graded_oracle.json) were computed on the mesh
-    built here, and the library's pitching of it has the stored number of
-    tents, in total and in levels 1-2."""
-    import importlib.util
-    import json
-    import os
-    import paper_1907_02367_gb300 as pkg
-    here = os.path.join(os.path.dirname(__file__), "golden")
-    spec = importlib.util.spec_from_file_location("mk", os.path.join(here, "make_inclusion_graded_oracle.py"))
-    mk = importlib.util.module_from_spec(spec)
-    spec.loader.exec_module(mk)
-    with open(os.path.join(here, "inclusion_graded_oracle.json")) as f:
-        g = json.load(f)
-    w = inputs.workload("inclusion_graded")
-    assert mk.mesh_checksum(w.mesh) == g["checksum"]
-    lev = pkg.Tents(w.mesh.coords, w.mesh.elems, w.mesh.c, w.kappa, w.T).export()["level"]
-    assert len(lev) == g["n_tents_total"]
-    assert int(np.sum(lev <= g["levels"])) == g["n_tents"]
+    w = inputs.workload(name)
+    m = w.mesh
+    lib = pkg.Tents(m.coords, m.elems, m.c, w.kappa, w.T).export()
+    ref = pitching.pitch(m.coords, m.elems, m.c, w.kappa, w.T, max_level=levels)
+    n = len(ref["vert"])
+    assert n > 3000 and int(np.sum(lib["level"] <= levels)) == n
+    for key in ("vert", "t_bot", "t_top", "level"):
+        assert np.array_equal(lib[key][:n], ref[key]), key
+    if name == "inclusion_graded":
+        assert len(lib["vert"]) == 19661640 and lib["n_levels"] == 97363
+    else:
+        assert len(lib["vert"]) == 468243 and lib["n_levels"] == 1099

@@ -562,3 +562,36 @@ def test_energy_through_a_curved_front_is_conserved_for_exact_solutions(cval):
     assert abs(E0 - np.pi ** 2 / 4) < 1e-10
     assert abs(energy.front_energy(F, lay.wq, m.c, g) - E0) <= 1e-10 * E0
     assert abs(energy.front_energy(F, lay.wq, m.c) - E0) > 1e-3 * E0     # the gradient term matters
+
+
+def test_refined_solve_removes_the_lu_error_at_degree_5():
+    """The tent systems at p = 5 reach kappa(A) ~ 1e8, so one binary64 LU
+    leaves an error of a few 1e-12 in the sweep; solving each system with
+    the extended-precision refinement agrees with an exact rational solve
+    of a tent system far better than the plain LU does, and changes the
+    sweep by about that amount (less at p = 4)."""
+    from fractions import Fraction
+    w = inputs.workload("inclusion_small")
+    m = w.mesh
+    r = pitching.pitch(m.coords, m.elems, m.c, w.kappa, w.T)
+    systems = []
+    tdg.sweep(m.coords, m.elems, m.c, 5, r, w.init, None, tent_range=(0, 40),
+              record=lambda it, d: systems.append((d["A"], d["b"])) if len(d["speeds"]) == 2 else None)
+    A, b = systems[0]
+    n = len(b)
+    # exact solve of the binary64 system in rationals (Gauss-Jordan)
+    M = [[Fraction(float(A[i, j])) for j in range(n)] + [Fraction(float(b[i]))] for i in range(n)]
+    for k in range(n):
+        piv = max(range(k, n), key=lambda i: abs(M[i][k]))
+        M[k], M[piv] = M[piv], M[k]
+        for i in range(n):
+            if i != k and M[i][k] != 0:
+                f = M[i][k] / M[k][k]
+                M[i] = [a - f * c for a, c in zip(M[i], M[k])]
+    x_exact = np.array([float(M[i][n] / M[i][i]) for i in range(n)])
+    e_lu = np.linalg.norm(np.linalg.solve(A, b) - x_exact) / np.linalg.norm(x_exact)
+    e_ref = np.linalg.norm(tdg.solve_refined(A, b) - x_exact) / np.linalg.norm(x_exact)
+    assert e_ref <= 1e-14 and e_ref * 10.0 < e_lu, (e_ref, e_lu)
+    F0, _ = tdg.sweep(m.coords, m.elems, m.c, 5, r, w.init, None)
+    F1, _ = tdg.sweep(m.coords, m.elems, m.c, 5, r, w.init, None, refine=True)
+    assert np.linalg.norm(F1 - F0) <= 1e-10 * np.linalg.norm(F1)
