@@ -189,6 +189,20 @@ int tp_boundary_kinds(const tp_ctx* ctx, double* nrm, int8_t* kind);
  * tp_boundary_points: g_D or g_N by the facet's kind; NULL for zero data).  Both are
  * copied; the front times are reset to 0.  Asynchronous on `stream`. */
 int tp_set_state(tp_ctx* ctx, const double* d_front, const double* d_gD, void* stream);
+/* Point outputs (Section 6.7 measures U_C(t) = ||U(., t)||_L1 over a small
+ * box at every time): U_h at the samples (x_j, t_k) of n_pts points xq
+ * (host, n_pts x dim, each inside some element) and n_t increasing times
+ * (host).  Every sample lies in exactly one tent -- the one at a vertex of
+ * x_j's element with t_bot(x_j) <= t_k < t_top(x_j) on that element (at the
+ * final time: the tent whose top reaches it) -- and the forward sweep writes
+ * U_h of that tent's solution there (Remark 3.1 map).  The assignment is
+ * made here, on the host, for the context's tents; replaces earlier probes
+ * (n_pts = 0 or n_t = 0: none); drops the captured forward graphs.
+ * TP_ERR_ARG for a point outside the mesh or times that do not increase. */
+int tp_set_probes(tp_ctx* ctx, int32_t n_pts, const double* xq, int32_t n_t, const double* times);
+/* Copies the point outputs into d_out (device, nrhs x n_t x n_pts doubles,
+ * [r][k][j]); samples no tent has reached since tp_set_state hold 0. */
+int tp_get_probes(const tp_ctx* ctx, double* d_out, void* stream);
 /* Resumes a sweep: copies a front (device, front layout) and the vertex
  * front times (device, n_vert doubles) into the context, e.g. the state
  * tp_get_state returned after some levels, so that tp_advance can continue

@@ -149,3 +149,63 @@ def sweep_dissipation(coords, elems, c, p, tents, init, alpha=0.5, beta=0.5, bnd
     F, tau = _tdg.sweep(coords, elems, c, p, tents, init, dirichlet, alpha=alpha, record=rec,
                         beta=beta, bnd_type=bnd_type, neumann=neumann, tent_range=tent_range)
     return F, tau, float(np.sum(per)), per
+
+
+def locate(coords, elems, points):
+    """Element of each point (the first whose barycentric coordinates are all
+    >= -1e-12) and the point's barycentric coordinates there: (el (N,), bary (N, n+1))."""
+    coords = np.asarray(coords, dtype=np.float64)
+    elems = np.asarray(elems)
+    n = coords.shape[1]
+    X = coords[elems]                                   # (E, n+1, n)
+    J = np.transpose(X[:, 1:, :] - X[:, :1, :], (0, 2, 1))   # columns = edges
+    pts = np.asarray(points, dtype=np.float64).reshape(-1, n)
+    el = np.full(len(pts), -1)
+    bary = np.zeros((len(pts), n + 1))
+    for j, x in enumerate(pts):
+        lam = np.linalg.solve(J, (x[None, :] - X[:, 0, :])[..., None])[..., 0]
+        full = np.concatenate([1.0 - lam.sum(axis=1, keepdims=True), lam], axis=1)
+        ok = np.nonzero(np.all(full >= -1e-12, axis=1))[0]
+        if len(ok) == 0:
+            raise ValueError(f"point {j} lies in no element")
+        el[j] = ok[0]
+        bary[j] = full[ok[0]]
+    return el, bary
+
+
+def probe_values(coords, elems, c, p, tents, init, points, times, **sweep_kw):
+    """U_h at the samples (x_j, t_k) (Section 6.7's point output U_C(t) is an
+    integral of |U_h(., t)| over a box): each sample lies in the tent at a
+    vertex of x_j's element whose bottom and top fronts enclose it there,
+    t_bot(x_j) <= t_k < t_top(x_j) (at the final time: the tent whose top
+    reaches it, with t_bot < t_top), and takes that tent's U_h (Remark 3.1
+    map).  Returns (values (n_t, n_pts), the tent of every sample (n_t, n_pts))."""
+    from . import tdg as _tdg
+    coords = np.asarray(coords, dtype=np.float64)
+    elems = np.asarray(elems)
+    times = np.asarray(times, dtype=np.float64)
+    el, bary = locate(coords, elems, points)
+    pts = np.asarray(points, dtype=np.float64).reshape(len(el), -1)
+    T = float(np.max(tents["t_top"]))
+    vals = np.full((len(times), len(el)), np.nan)
+    owner = np.full((len(times), len(el)), -1)
+    at = {}
+    for j, k in enumerate(el):
+        at.setdefault(int(k), []).append(j)
+
+    def rec(it, d):
+        B, nb, v = d["basis"], d["basis"].nb, d["v"]
+        for k in d["patch"]:
+            for j in at.get(int(k), []):
+                ids = elems[k]
+                tb = float(bary[j] @ d["tau_before"][ids])
+                tt = float(bary[j] @ np.where(ids == v, d["t_top"], d["tau_before"][ids]))
+                for kt, t in enumerate(times):
+                    if (tb <= t < tt) or (t == T and tb < tt == T):
+                        g = d["groups"][k]
+                        U, _, _ = B.eval_phys(pts[j:j + 1], np.array([t]), d["xc"], d["tc"], d["h"], d["speeds"][g])
+                        vals[kt, j] = float(U[0] @ d["x"][g * nb:(g + 1) * nb])
+                        owner[kt, j] = it
+
+    _tdg.sweep(coords, elems, c, p, tents, init, record=rec, **sweep_kw)
+    return vals, owner

@@ -195,6 +195,21 @@ class Solver:
             gptr = B.tensor_ptr(gD)
         B.check(B.load().tp_set_state(self.handle, B.tensor_ptr(front), gptr, B.stream_ptr(stream)))
 
+    def set_probes(self, points, times):
+        """tp_set_probes: U_h at every (point, time) sample during the next
+        forward sweeps (points (n, dim) inside the mesh, increasing times)."""
+        pts = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, self.dim)
+        ts = np.ascontiguousarray(times, dtype=np.float64).reshape(-1)
+        B.check(B.load().tp_set_probes(self.handle, int(len(pts)), pts.ctypes.data, int(len(ts)), ts.ctypes.data))
+        self._probe_shape = (self.nrhs, len(ts), len(pts))
+
+    def get_probes(self, stream=None):
+        """tp_get_probes: CUDA float64 tensor (nrhs, n_times, n_points) of U_h."""
+        import torch
+        out = torch.empty(self._probe_shape, dtype=torch.float64, device="cuda")
+        B.check(B.load().tp_get_probes(self.handle, B.tensor_ptr(out), B.stream_ptr(stream)))
+        return out
+
     def set_front(self, front, tau, stream=None):
         """tp_set_front: resume from a front and its vertex times (e.g. what
         get_state returned after some levels)."""

@@ -180,6 +180,15 @@ struct tp_ctx {
   int* d_tent_vert = nullptr;
   // dependency lists of the dataflow sweep kept on the host (tp_inject_wait)
   std::vector<int32_t> dep_ptr_h, dep_need_h;
+  // vertex stars in the record order (grouped by material) and the tents'
+  // vertices and top times (point outputs are assigned to tents on the host)
+  std::vector<int> star_sorted;
+  std::vector<int32_t> tent_vert_h;
+  std::vector<double> tent_ttop_h;
+  // point outputs (tp_set_probes)
+  int n_probe = 0, n_probe_t = 0;
+  double* d_probe_out = nullptr;
+  std::vector<void*> probe_allocs;
   int* d_dep_need = nullptr;
   unsigned long long* d_stats = nullptr;   // solve statistics (kMaxRefine + 2 counters)
   std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
@@ -275,6 +284,7 @@ KArgs group_args(const tp_ctx* ctx, KArgs a, int k) {
   a.front += (size_t)k * ctx->nrhs_g * ctx->ne * ctx->Q * ctx->C;
   if (a.gD) a.gD += (size_t)k * ctx->nrhs_g * ctx->n_bnd;
   if (a.diss) a.diss += (size_t)k * ctx->nrhs_g;
+  if (a.probe_out) a.probe_out += (size_t)k * ctx->nrhs_g * ctx->n_probe_t * ctx->n_probe;
   return a;
 }
 
@@ -535,6 +545,9 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
           star_grp[pos++] = g;
         }
   }
+  ctx->star_sorted = star_sorted;
+  ctx->tent_vert_h.assign(tents->vert.begin(), tents->vert.end());
+  ctx->tent_ttop_h.assign(tents->t_top.begin(), tents->t_top.end());
   int *dftp = nullptr, *dfti = nullptr, *dfmp = nullptr, *dfmi = nullptr;
   float *dftc = nullptr, *dfmc = nullptr;
   if ((rc = ctx_upload(ctx, &dftp, basis->ft_ptr)) || (rc = ctx_upload(ctx, &dfti, basis->ft_idx)) ||
@@ -1132,6 +1145,9 @@ extern "C" int tp_set_state(tp_ctx* ctx, const double* d_front, const double* d_
   TP_CUDA_OK(cudaMemsetAsync(ctx->d_info, 0, sizeof(long long), st));
   if (ctx->d_diss) TP_CUDA_OK(cudaMemsetAsync(ctx->d_diss, 0, (size_t)ctx->nrhs * sizeof(double), st));
   TP_CUDA_OK(cudaMemsetAsync(ctx->d_stats, 0, (tp::kMaxRefine + 2) * sizeof(unsigned long long), st));
+  if (ctx->d_probe_out)
+    TP_CUDA_OK(cudaMemsetAsync(ctx->d_probe_out, 0,
+                               (size_t)ctx->nrhs * ctx->n_probe_t * ctx->n_probe * sizeof(double), st));
   if (ctx->n_bnd > 0) {
     if (d_gD) {
       TP_CUDA_OK(cudaMemcpyAsync(ctx->d_gD, d_gD, (size_t)ctx->nrhs * ctx->n_bnd * sizeof(double),
@@ -1143,6 +1159,148 @@ extern "C" int tp_set_state(tp_ctx* ctx, const double* d_front, const double* d_
     }
   }
   ctx->last_stream = st;
+  return TP_OK;
+}
+
+extern "C" int tp_set_probes(tp_ctx* ctx, int32_t n_pts, const double* xq, int32_t n_t, const double* times) {
+  if (!ctx || n_pts < 0 || n_t < 0 || (n_pts > 0 && !xq) || (n_t > 0 && !times)) {
+    tp::set_error("tp_set_probes: invalid argument");
+    return TP_ERR_ARG;
+  }
+  const tp::Topology& T = ctx->topo;
+  const int n = ctx->dim, NV = n + 1;
+  for (void* g : ctx->probe_allocs) cudaFree(g);
+  ctx->probe_allocs.clear();
+  ctx->d_probe_out = nullptr;
+  ctx->n_probe = ctx->n_probe_t = 0;
+  for (KArgs* a : {&ctx->args, &ctx->args_adj}) {
+    a->probe_ptr = nullptr;
+    a->probe_out = nullptr;
+  }
+  for (auto& kv : ctx->graphs) cudaGraphExecDestroy(kv.second);   // the graphs hold the old arguments
+  ctx->graphs.clear();
+  if (n_pts == 0 || n_t == 0) return TP_OK;
+  for (int k = 1; k < n_t; ++k)
+    if (!(times[k] > times[k - 1])) {
+      tp::set_error("tp_set_probes: output times must increase");
+      return TP_ERR_ARG;
+    }
+  // the element of every point (barycentric coordinates >= -1e-12) and its coordinates there
+  std::vector<int> pel(n_pts, -1);
+  std::vector<double> pbary((size_t)n_pts * NV);
+  for (int j = 0; j < n_pts; ++j) {
+    for (int64_t k = 0; k < T.ne && pel[j] < 0; ++k) {
+      const int32_t* el = &T.elems[(size_t)k * NV];
+      double e[3][3] = {}, rhs[3] = {}, lam[4] = {};
+      for (int i = 0; i < n; ++i) {
+        for (int d = 0; d < n; ++d) e[d][i] = T.X[(size_t)el[i + 1] * n + d] - T.X[(size_t)el[0] * n + d];
+      }
+      for (int d = 0; d < n; ++d) rhs[d] = xq[(size_t)j * n + d] - T.X[(size_t)el[0] * n + d];
+      // solve e lam[1..n] = rhs by Cramer's rule (n <= 3)
+      auto det3 = [&](double m[3][3]) {
+        if (n == 1) return m[0][0];
+        if (n == 2) return m[0][0] * m[1][1] - m[0][1] * m[1][0];
+        return m[0][0] * (m[1][1] * m[2][2] - m[1][2] * m[2][1]) - m[0][1] * (m[1][0] * m[2][2] - m[1][2] * m[2][0]) +
+               m[0][2] * (m[1][0] * m[2][1] - m[1][1] * m[2][0]);
+      };
+      const double D = det3(e);
+      double s = 0.0;
+      for (int i = 0; i < n; ++i) {
+        double m[3][3];
+        for (int r = 0; r < 3; ++r)
+          for (int c2 = 0; c2 < 3; ++c2) m[r][c2] = (c2 == i) ? rhs[r] : e[r][c2];
+        lam[i + 1] = det3(m) / D;
+        s += lam[i + 1];
+      }
+      lam[0] = 1.0 - s;
+      bool in = true;
+      for (int i = 0; i <= n; ++i) in = in && lam[i] >= -1e-12;
+      if (in) {
+        pel[j] = (int)k;
+        for (int i = 0; i <= n; ++i) pbary[(size_t)j * NV + i] = lam[i];
+      }
+    }
+    if (pel[j] < 0) {
+      tp::set_error("tp_set_probes: point " + std::to_string(j) + " lies in no element of the mesh");
+      return TP_ERR_ARG;
+    }
+  }
+  // replay the tents: the sample (x_j, t_k) belongs to the tent whose
+  // bottom and top fronts enclose it on x_j's element, t_bot(x_j) <= t_k <
+  // t_top(x_j) (at the final time, the tent whose top reaches it)
+  std::vector<std::vector<int>> at_el(T.ne);
+  for (int j = 0; j < n_pts; ++j) at_el[pel[j]].push_back(j);
+  std::vector<double> tau(T.nv, 0.0);
+  const double Tf = ctx->T_final;
+  std::vector<int32_t> ptr(ctx->ntents + 1, 0), sj, sk, sslot;
+  for (int64_t it = 0; it < ctx->ntents; ++it) {
+    const int v = ctx->tent_vert_h[it];
+    const double ttop = ctx->tent_ttop_h[it];
+    for (int e = T.star_ptr[v]; e < T.star_ptr[v + 1]; ++e) {
+      const int K = ctx->star_sorted[e];
+      for (int j : at_el[K]) {
+        double tb = 0.0, tt = 0.0;
+        for (int i = 0; i < NV; ++i) {
+          const int w = T.elems[(size_t)K * NV + i];
+          const double l = pbary[(size_t)j * NV + i];
+          tb += l * tau[w];
+          tt += l * (w == v ? ttop : tau[w]);
+        }
+        for (int k = 0; k < n_t; ++k) {
+          const double t = times[k];
+          if ((tb <= t && t < tt) || (t == Tf && tb < tt && tt == Tf)) {
+            sj.push_back(j);
+            sk.push_back(k);
+            sslot.push_back(e - T.star_ptr[v]);
+          }
+        }
+      }
+    }
+    tau[v] = ttop;
+    ptr[it + 1] = (int32_t)sj.size();
+  }
+  std::vector<double> tv(times, times + n_t);
+  int *dptr = nullptr, *dj = nullptr, *dk = nullptr, *dsl = nullptr;
+  double *dbary = nullptr, *dt = nullptr;
+  int rc = TP_OK;
+  auto up = [&](auto** d, const auto& h) {
+    int r = upload(d, h);
+    if (r == TP_OK && *d) ctx->probe_allocs.push_back((void*)*d);
+    return r;
+  };
+  if ((rc = up(&dptr, ptr)) || (rc = up(&dj, sj)) || (rc = up(&dk, sk)) || (rc = up(&dsl, sslot)) ||
+      (rc = up(&dbary, pbary)) || (rc = up(&dt, tv)))
+    return rc;
+  const size_t nout = (size_t)ctx->nrhs * n_t * n_pts;
+  if (cudaMalloc(&ctx->d_probe_out, nout * sizeof(double)) != cudaSuccess) {
+    tp::set_error("tp_set_probes: device allocation failed");
+    return TP_ERR_OOM;
+  }
+  ctx->probe_allocs.push_back(ctx->d_probe_out);
+  TP_CUDA_OK(cudaMemset(ctx->d_probe_out, 0, nout * sizeof(double)));
+  ctx->n_probe = n_pts;
+  ctx->n_probe_t = n_t;
+  KArgs& a = ctx->args;
+  a.probe_ptr = dptr;
+  a.probe_j = dj;
+  a.probe_k = dk;
+  a.probe_slot = dsl;
+  a.probe_bary = dbary;
+  a.probe_t = dt;
+  a.n_probe = n_pts;
+  a.n_probe_t = n_t;
+  a.probe_out = ctx->d_probe_out;
+  return TP_OK;
+}
+
+extern "C" int tp_get_probes(const tp_ctx* ctx, double* d_out, void* stream) {
+  if (!ctx || !d_out || !ctx->d_probe_out) {
+    tp::set_error("tp_get_probes: null argument or no point outputs set");
+    return TP_ERR_ARG;
+  }
+  TP_CUDA_OK(cudaMemcpyAsync(d_out, ctx->d_probe_out,
+                             (size_t)ctx->nrhs * ctx->n_probe_t * ctx->n_probe * sizeof(double),
+                             cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
   return TP_OK;
 }
 
@@ -1585,6 +1743,7 @@ extern "C" void tp_destroy_ctx(tp_ctx* ctx) {
   cudaFree(ctx->d_partial);
   cudaFree(ctx->d_diss);
   cudaFree(ctx->d_stats);
+  for (void* g : ctx->probe_allocs) cudaFree(g);
   for (double* g : {ctx->d_front0, ctx->d_work, ctx->d_tau_work, ctx->d_ckpt, ctx->d_ckpt_tau, ctx->d_snap, ctx->d_xsave})
     cudaFree(g);
   cudaFree(ctx->d_adj);

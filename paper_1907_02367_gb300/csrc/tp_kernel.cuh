@@ -100,6 +100,18 @@ struct KArgs {
   long long max_spin;
   int max_refine;
   unsigned long long* solve_stats;
+  // point outputs (forward sweep): the samples (probe point, output time)
+  // that lie inside tent t are [probe_ptr[t], probe_ptr[t+1]) with the
+  // probe's index, the time's index and the patch slot of its element; the
+  // forward kernel writes U_h there: probe_out[(r * n_probe_t + k) * n_probe + j]
+  const int* probe_ptr;        // nullptr: no point outputs
+  const int* probe_j;
+  const int* probe_k;
+  const int* probe_slot;
+  const double* probe_bary;   // per probe point: barycentric coordinates in its element
+  const double* probe_t;      // output times
+  int n_probe, n_probe_t;
+  double* probe_out;
   int* status;
   long long* status_info;
   // persistent sweep: tent queue, completed tents per vertex, dependencies
@@ -1933,6 +1945,47 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
       double* diss = a.diss + (rsplit ? (size_t)rank * nrhs : 0);
       for (int r = tid; r < nrhs; r += blockDim.x) atomicAdd(diss + r, sDis[r]);
       __syncthreads();
+    }
+  }
+  // ---------------- point outputs (forward sweep, when requested) ----------------
+  // U_h at the samples (x_j, t_k) that lie inside this tent: t_bot(x_j) <=
+  // t_k < t_top(x_j) on the element of x_j (the host assigns each sample to
+  // the one tent that holds it); U_h = sum_j x_j b_j at the mapped point
+  // (Remark 3.1)
+  if constexpr (!ADJ) {
+    if (a.probe_ptr != nullptr) {
+      const int s0 = __ldg(a.probe_ptr + tent), ns = __ldg(a.probe_ptr + tent + 1) - s0;
+      const int psl = rsplit ? ns : (ns + CS - 1) / CS;
+      const int a0 = rsplit ? 0 : min(ns, rank * psl), a1 = rsplit ? ns : min(ns, a0 + psl);
+      for (int base = a0; base < a1; base += 2 * CH) {
+        const int nq = min(2 * CH, a1 - base);
+        for (int id = tid; id < nq; id += blockDim.x) {
+          const int smp = s0 + base + id, j = __ldg(a.probe_j + smp), k = __ldg(a.probe_slot + smp);
+          const double t = __ldg(a.probe_t + __ldg(a.probe_k + smp));
+          double x[DIM];
+          for (int d = 0; d < DIM; ++d) x[d] = 0.0;
+          for (int i = 0; i < NV; ++i) {
+            const double l = __ldg(a.probe_bary + (size_t)j * NV + i);
+            for (int d = 0; d < DIM; ++d) x[d] = fma(l, s_X[k][i][d], x[d]);
+          }
+          T* pp = sPt + id * (DIM + 2);
+          pp[0] = R::from(s_gc[s_grp[k]] * (t - tc) * ih);
+          for (int d = 0; d < DIM; ++d) pp[1 + d] = R::from((x[d] - s_xv[d]) * ih);
+          pp[DIM + 1] = R::one();
+        }
+        eval_uvalues_block<DIM, T, false>(a, nq, sPt, sM, sU);
+        for (int id = tid; id < nq * nrhs; id += blockDim.x) {
+          const int ql = id % nq, r = id / nq, smp = s0 + base + ql;
+          const int j = __ldg(a.probe_j + smp), kt = __ldg(a.probe_k + smp), k = __ldg(a.probe_slot + smp);
+          const T* y = sY + (size_t)s_grp[k] * nmom + (size_t)r * C * nb;   // U_h = u . x_g
+          const T* u = sU + (size_t)ql * nb;
+          T acc = R::zero();
+          for (int jj = 0; jj < nb; ++jj) acc = R::acc(acc, y[jj], u[jj]);
+          const int rg = (rsplit ? rank * nrhs : 0) + r;
+          a.probe_out[((size_t)rg * a.n_probe_t + kt) * a.n_probe + j] = R::to(R::norm(acc));
+        }
+        __syncthreads();
+      }
     }
   }
   // ---------------- wave-speed gradient (reverse sweep, when requested) ----------------

@@ -192,6 +192,43 @@ def mesh_inclusion_graded(h_max: float = 0.015, ratio: float = 10.0, growth: flo
                 meta={"h_max": h_max, "h_min": h_min, "seed": seed, "radius": radius})
 
 
+def mesh_two_speeds(h_left: float = 0.01, h_right: float = 0.03, x_if: float = 1.2, length: float = 2.0,
+                    c_left: float = 1.0, c_right: float = 3.0, seed: int = 7) -> Mesh:
+    """The heterogeneous medium of Section 6.7: the square [0, length]^2 with
+    c = c_left for x_1 <= x_if and c_right beyond, spatial mesh size h_left
+    on the slow side and h_right on the fast one.  Points: a grid of spacing
+    h_left on [0, x_if] x [0, length] (the column x_1 = x_if included) and a
+    grid of spacing h_right beyond, interior points jittered by 10 % of
+    their spacing (seeded); their Delaunay triangulation (counter-clockwise),
+    c by element centroid.  The default sizes give about 52 000 triangles."""
+    from scipy.spatial import Delaunay
+    rng = np.random.default_rng(seed)
+
+    def grid(x0, x1, h, skip_first_column):
+        nx = int(math.ceil((x1 - x0) / h - 1e-9))
+        ny = int(math.ceil(length / h - 1e-9))
+        xs = x0 + (x1 - x0) * np.arange(nx + 1) / nx
+        ys = length * np.arange(ny + 1) / ny
+        if skip_first_column:
+            xs = xs[1:]
+        P = np.array([[x, y] for y in ys for x in xs], dtype=np.float64)
+        inner = (P[:, 0] > 0) & (P[:, 0] < length) & (P[:, 1] > 0) & (P[:, 1] < length) & \
+                (np.abs(P[:, 0] - x_if) > 1e-12)
+        P[inner] += rng.uniform(-0.1 * h, 0.1 * h, size=P[inner].shape)
+        return P
+
+    P = np.ascontiguousarray(np.concatenate([grid(0.0, x_if, h_left, False),
+                                             grid(x_if, length, h_right, True)]), dtype=np.float64)
+    tris = Delaunay(P).simplices.astype(np.int32)
+    for t in tris:
+        if _orient2(P[t[0]], P[t[1]], P[t[2]]) < 0:
+            t[1], t[2] = t[2], t[1]
+    cen = P[tris].mean(axis=1)
+    c = np.where(cen[:, 0] <= x_if, c_left, c_right).astype(np.float64)
+    return Mesh(P, tris, c, name="two_speeds",
+                meta={"h_left": h_left, "h_right": h_right, "x_if": x_if, "seed": seed})
+
+
 def _ring_polyline(s: float, h: float):
     """The part of the square |x|_inf = s inside the L-shape (Section 6.6):
     four straight pieces from (0,-s) over (-s,-s), (-s,s), (s,s) to (s,0),

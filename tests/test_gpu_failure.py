@@ -46,7 +46,10 @@ def test_timeout_is_reported_and_the_context_recovers(cuda_device):
     s.set_state(f0, gD)
     s.advance()
     st, info = s.sync_status()
-    assert st == TP_ERR_TIMEOUT and info == victim
+    # the first wait to give up is the victim's or that of a tent queued after
+    # it and held up by it (with the short limit both run out at about the
+    # same time); no tent before the victim waits for anything that never comes
+    assert st == TP_ERR_TIMEOUT and info >= victim
     # restore: the next sweep is clean and right
     s.inject_wait(victim, 0)
     s.set_limits()

@@ -55,16 +55,20 @@ def test_inclusion_matches_oracle(cuda_device, precision, tol):
     assert rel <= tol, rel
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("mixed", 1e-8)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-8)])
 def test_inclusion_degree5_matches_oracle(cuda_device, precision, tol):
     """The inclusion workload at the degree of the heterogeneous target
     configuration (p = 5: 36 unknowns per material, 72 on interface tents,
     more than the 32 the register Gauss-Jordan holds: the shared-memory
     Gauss-Jordan path, without row interchanges).  At p = 5 the tent systems
-    reach kappa(A) ~ 1e8 and one binary64 LU moves the oracle's own sweep by
+    reach kappa(A) ~ 1e8: one binary64 LU moves the oracle's own sweep by
     6e-12 on this mesh, so the reference solves every tent system with
     extended-precision refinement (oracle.tdg.solve_refined, pinned against
-    an exact rational solve); against it the binary64 path keeps 1e-11."""
+    an exact rational solve); and perturbing every entry of each tent's A and
+    b by one unit roundoff moves the sweep by 3.4e-12 (4e-14 at p = 4).  The
+    library assembles A through Grams of U-values and congruences, other
+    roundings of the same integrals by several units, so at p = 5 the
+    binary64 path is held to 1e-10 (measured 2.2e-11); 1e-11 at p <= 4."""
     w = inputs.workload("inclusion_small")
     m = w.mesh
     s, got, tau, st = _run(m, 5, w.T, w.kappa, w.init, None, precision)
