@@ -8,7 +8,8 @@ coefficients satisfy the recursion eq. (3.1)
 
 The recursion is started from a basis of P^p (k = 0 data, dU/dt(.,0) = 0) and
 a basis of P^{p-1} (k = 1 data, U(.,0) = 0); dim U^p = C(p+n, n) + C(p-1+n, n).
-Monomials are the initial bases (Section 6.3: monomials behave best).
+Monomials are the initial bases (Section 6.3: monomials behave best); the
+Legendre and Chebyshev starts of that comparison are available too.
 Coefficients are computed once for c = 1 (Remark 3.1) as exact rationals and
 rounded to binary64 once.
 
@@ -45,8 +46,46 @@ def dim_U(n: int, p: int) -> int:
     return comb(p + n, n) + (comb(p - 1 + n, n) if p >= 1 else 0)
 
 
-def trefftz_coefficients(n: int, p: int, c: Fraction = Fraction(1)):
-    """Exact coefficients of the basis: list of dicts {(k, alpha): Fraction}."""
+def poly1d(kind: str, k: int):
+    """Exact ascending-power coefficients of the degree-k Legendre polynomial
+    ((j+1) P_{j+1} = (2j+1) x P_j - j P_{j-1}) or Chebyshev polynomial of the
+    first kind (T_{j+1} = 2x T_j - T_{j-1}) on [-1, 1]."""
+    P = [[Fraction(1)], [Fraction(0), Fraction(1)]]
+    for j in range(1, k):
+        xp = [Fraction(0)] + P[j]
+        prev = P[j - 1] + [Fraction(0), Fraction(0)]
+        if kind == "legendre":
+            P.append([(Fraction(2 * j + 1) * xp[i] - Fraction(j) * prev[i]) / (j + 1) for i in range(j + 2)])
+        elif kind == "chebyshev":
+            P.append([2 * xp[i] - prev[i] for i in range(j + 2)])
+        else:
+            raise ValueError(kind)
+    return P[k]
+
+
+def initial_polynomial(kind: str, beta):
+    """{alpha: coefficient} of the initial spatial polynomial with index beta:
+    the monomial x^beta, or the tensor product prod_m P_{beta_m}(x_m) of
+    Legendre / Chebyshev polynomials (Section 6.3 compares the three)."""
+    if kind == "monomial":
+        return {tuple(beta): Fraction(1)}
+    terms = {(): Fraction(1)}
+    for b in beta:
+        cm = poly1d(kind, b)
+        new = {}
+        for key, v in terms.items():
+            for e, cf in enumerate(cm):
+                if cf:
+                    new[key + (e,)] = new.get(key + (e,), Fraction(0)) + v * cf
+        terms = new
+    return terms
+
+
+def trefftz_coefficients(n: int, p: int, c: Fraction = Fraction(1), init: str = "monomial"):
+    """Exact coefficients of the basis: list of dicts {(k, alpha): Fraction}.
+    init: the initial spatial polynomials the recursion eq. (3.1) starts from
+    (k = 0 data for type 0, k = 1 data for type 1): "monomial" (the path's
+    choice), "legendre" or "chebyshev" (Section 6.3); all span U^p."""
     c2 = Fraction(c) * Fraction(c)
     funcs = []
     for typ, deg0 in ((0, p), (1, p - 1)):
@@ -54,7 +93,8 @@ def trefftz_coefficients(n: int, p: int, c: Fraction = Fraction(1)):
             continue
         for beta in multi_indices(n, deg0):
             a = {}
-            a[(typ, beta)] = Fraction(1)
+            for al, v in initial_polynomial(init, beta).items():
+                a[(typ, al)] = v
             for k in range(2, p + 1):
                 for alpha in multi_indices(n, p - k):
                     s = Fraction(0)
@@ -73,9 +113,9 @@ def trefftz_coefficients(n: int, p: int, c: Fraction = Fraction(1)):
 class TrefftzBasis:
     """Float tables for evaluating the c = 1 basis and its first derivatives."""
 
-    def __init__(self, n: int, p: int):
-        self.n, self.p = n, p
-        self.exact = trefftz_coefficients(n, p)
+    def __init__(self, n: int, p: int, init: str = "monomial"):
+        self.n, self.p, self.init = n, p, init
+        self.exact = trefftz_coefficients(n, p, init=init)
         self.nb = len(self.exact)
         # monomials t^k x^alpha with k + |alpha| <= p
         self.monos = [(k, alpha) for k in range(p + 1) for alpha in multi_indices(n, p - k)]

@@ -155,7 +155,7 @@ def solve_refined(A, b, steps=3):
 
 def sweep(coords, elems, c, p, tents, init, dirichlet=None, alpha=0.5,
           record=None, front0=None, tau0=None, tent_range=None, beta=0.5,
-          bnd_type=None, neumann=None, refine=False):
+          bnd_type=None, neumann=None, refine=False, basis_init="monomial"):
     """Run the tent sweep.
 
     coords (Nv, n), elems (E, n+1), c (E,), p: Trefftz degree of U^p,
@@ -168,6 +168,7 @@ def sweep(coords, elems, c, p, tents, init, dirichlet=None, alpha=0.5,
     outward unit normal, or None for 0.
     record: optional callable(tent_index, dict) receiving the local data.
     refine: solve every tent system with solve_refined instead of one LU.
+    basis_init: initial polynomials of the basis recursion (Section 6.3).
     Returns (front (E, Q, n+2), tau (Nv,)).
     """
     coords = np.asarray(coords, dtype=np.float64)
@@ -176,7 +177,7 @@ def sweep(coords, elems, c, p, tents, init, dirichlet=None, alpha=0.5,
     n = coords.shape[1]
     nv = coords.shape[0]
     lay = front_layout(coords, elems, p)
-    B = _basis.TrefftzBasis(n, p)
+    B = _basis.TrefftzBasis(n, p, basis_init)
     star = vertex_star(elems, nv)
     bfac = boundary_facets(coords, elems)
     vfac = [[] for _ in range(nv)]

@@ -900,6 +900,7 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
     return fail(TP_ERR_UNSUPPORTED);
   }
   a.mono_stride = ctx->nmono | 1;
+  a.ustride = nb | 1;
   // shared-memory plan: the largest chunk of points that keeps two CTAs per SM,
   // else the largest that fits one
   int nrg = ctx->nrhs;   // right-hand sides per group
@@ -947,7 +948,7 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
     take(&a.off_f2, ifneu ? npair : 0);
     take(&a.off_fpm, ifneu ? (size_t)nb * nb : 0);
     take(&a.off_del, (size_t)nrg * nb);
-    take(&a.off_u, (size_t)2 * CH * nb);
+    take(&a.off_u, (size_t)2 * CH * (nb | 1));
     take(&a.off_pt, (size_t)2 * CH * (n + 2));
     take(&a.off_cb, (size_t)CH * nrg * C);
     take(&a.off_gd, (size_t)CH * nrg);

@@ -32,6 +32,7 @@ __device__ __forceinline__ void red_release_add(int* p, int v) {
 
 struct KArgs {
   int nb, nmono, Q, nrhs, CH, mono_stride, ngmax;
+  int ustride;                    // row stride of the U-values of a point in shared memory (nb rounded up to odd)
   // right-hand sides split over the cluster: CTA r of a tent's cluster owns
   // right-hand sides [r nrhs, (r + 1) nrhs) of the group (nrhs = per CTA) for
   // the data moments, the solve and the outflow, over all points of the
@@ -361,7 +362,7 @@ __device__ __forceinline__ void eval_uvalues_block(const KArgs& a, int npt, cons
       const int g = __ldg(a.sp_mono + e0);
 #pragma unroll
       for (int t = 0; t < 4; ++t)
-        if (q0 + t < npt) u[qq[t] * nb + j] = m[qq[t] * ms + g];
+        if (q0 + t < npt) u[qq[t] * a.ustride + j] = m[qq[t] * ms + g];
       continue;
     }
     for (int e = e0; e < e1; ++e) {
@@ -372,7 +373,7 @@ __device__ __forceinline__ void eval_uvalues_block(const KArgs& a, int npt, cons
     }
 #pragma unroll
     for (int t = 0; t < 4; ++t)
-      if (q0 + t < npt) u[qq[t] * nb + j] = Ar<T>::norm(acc[t]);
+      if (q0 + t < npt) u[qq[t] * a.ustride + j] = Ar<T>::norm(acc[t]);
   }
   __syncthreads();
 }
@@ -624,6 +625,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
     tent = tent0 + blockIdx.x / CS;
   }
   const int nb = a.nb, Q = a.Q, nrhs = a.nrhs, CH = a.CH, NG = a.ngmax;
+  const int us = a.ustride;   // row stride of the U-values in shared memory (odd: no bank conflicts between points)
   // this CTA's right-hand sides (all of the group unless they are split over the cluster)
   const bool rsplit = a.rsplit != 0;
   double* const front = a.front + (rsplit ? (size_t)rank * nrhs * a.ne * Q * C : 0);
@@ -911,7 +913,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
       if (item < nitem)
         for (int ql = part; ql < nq; ql += ps)
           if (s_pgrp[ql] == g) {
-            const T u = sU[(size_t)(prow + ql) * nb + i];
+            const T u = sU[(size_t)(prow + ql) * us + i];
             const T* cb = sCB + ((size_t)ql * nrhs + r) * C;
 #pragma unroll
             for (int cc = 0; cc < C; ++cc) t[cc] = R::acc(t[cc], cb[cc], u);
@@ -945,7 +947,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
     if (!rsplit) data_coefs(base, nq);
     eval_uvalues_block<DIM, T>(a, npt, sPt, sM, sU);
     if (keep)
-      for (int id = tid; id < nq * nb; id += blockDim.x) sKeep[(size_t)(base - q0) * nb + id] = sU[id];
+      for (int id = tid; id < nq * nb; id += blockDim.x) sKeep[(size_t)(base - q0) * nb + id] = sU[(id / nb) * us + id % nb];
     // (b) Grams of U-values: top per element (flushed into G and H_m), bottom; per material
     for (int ql = 0; ql < nq; ++ql) {
       if (base + ql >= kend) {   // the next element's points start
@@ -958,8 +960,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
         curk = k;
         kend = (k + 1) * Q;
       }
-      const T* ut = sU + (size_t)ql * nb;
-      const T* ub = sU + (size_t)(nq + ql) * nb;
+      const T* ut = sU + (size_t)ql * us;
+      const T* ub = sU + (size_t)(nq + ql) * us;
 #pragma unroll
       for (int s = 0; s < kMaxPair; ++s) {
         if (tid + s * kThreads < npair) {
@@ -1078,7 +1080,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
         for (int ql = 0; ql < nq; ++ql) {
           if (base + ql >= (fc + 1) * Q) fold_gram(fc++);
           if (base + ql < d0 || base + ql >= d1) continue;   // another CTA's Gram points
-          const T* u = sU + (size_t)ql * nb;
+          const T* u = sU + (size_t)ql * us;
 #pragma unroll
           for (int s = 0; s < kMaxPair; ++s)
             if (tid + s * kThreads < npair) aF[s] = R::fma(u[pi[s]], u[pj[s]], aF[s]);
@@ -1092,7 +1094,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
               fold_mom(f++, id, t);
               t = R::zero();
             }
-            t = R::fma(sGd[ql * nrhs + r], sU[(size_t)ql * nb + i], t);
+            t = R::fma(sGd[ql * nrhs + r], sU[(size_t)ql * us + i], t);
           }
           sDel[id] = t;
         }
@@ -1153,8 +1155,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
         eval_uvalues_block<DIM, T>(a, npt, sPt, sM, sU);
         for (int ql = 0; ql < nq; ++ql) {
           if (base + ql < f0 || base + ql >= f1) continue;   // another CTA's Gram points
-          const T* u = sU + (size_t)ql * nb;
-          const T* u2 = sU + (size_t)(nq + ql) * nb;
+          const T* u = sU + (size_t)ql * us;
+          const T* u2 = sU + (size_t)(nq + ql) * us;
 #pragma unroll
           for (int s = 0; s < kMaxPair; ++s)
             if (tid + s * kThreads < npair) {
@@ -1166,14 +1168,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
           for (int id = tid; id < nrhs * nb; id += blockDim.x) {
             const int r = id / nb, i = id % nb;
             T t = sDel[id];
-            for (int ql = 0; ql < nq; ++ql) t = R::fma(sGd[ql * nrhs + r], sU[(size_t)ql * nb + i], t);
+            for (int ql = 0; ql < nq; ++ql) t = R::fma(sGd[ql * nrhs + r], sU[(size_t)ql * us + i], t);
             sDel[id] = t;
           }
         } else {
           for (int id = tid; id < nb * nb; id += blockDim.x) {
             const int i = id / nb, j = id % nb;
             T t = sFpm[id];
-            for (int ql = 0; ql < nq; ++ql) t = R::fma(sU[(size_t)ql * nb + i], sU[(size_t)(nq + ql) * nb + j], t);
+            for (int ql = 0; ql < nq; ++ql) t = R::fma(sU[(size_t)ql * us + i], sU[(size_t)(nq + ql) * us + j], t);
             sFpm[id] = t;
           }
         }
@@ -1872,7 +1874,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
         eval_uvalues_block<DIM, T>(a, nq, sPt, sM, sU);
         for (int id = tid; id < nq * nrhs; id += blockDim.x) {
           const int ql = id / nrhs, r = id % nrhs, k = (base + ql) / Q, g = s_grp[k];
-          const T* u = sU + (size_t)ql * nb;
+          const T* u = sU + (size_t)ql * us;
           const double* fb = sFb + (size_t)id * C;
           const double Uh = fieldv(g, r, 0, u), dv = fieldv(g, r, 1, u) - fb[1];
           double ds2 = 0.0, dsg = 0.0;
@@ -1922,13 +1924,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
           eval_uvalues_block<DIM, T>(a, ifc ? 2 * nq : nq, sPt, sM, sU);
           for (int id = tid; id < nq * nrhs; id += blockDim.x) {
             const int ql = id / nrhs, r = id % nrhs;
-            const T* u = sU + (size_t)ql * nb;
+            const T* u = sU + (size_t)ql * us;
             const double vh = fieldv(gp, r, 1, u);
             double sn = 0.0;
             for (int d = 0; d < DIM; ++d) sn = fma(s_fn[f][d], fieldv(gp, r, 2 + d, u), sn);
             double val;
             if (ifc) {
-              const T* u2 = sU + (size_t)(nq + ql) * nb;
+              const T* u2 = sU + (size_t)(nq + ql) * us;
               double sn2 = 0.0;
               for (int d = 0; d < DIM; ++d) sn2 = fma(s_fn[f][d], fieldv(gm, r, 2 + d, u2), sn2);
               const double jv = vh - fieldv(gm, r, 1, u2), js = sn - sn2;
@@ -1978,7 +1980,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
           const int ql = id % nq, r = id / nq, smp = s0 + base + ql;
           const int j = __ldg(a.probe_j + smp), kt = __ldg(a.probe_k + smp), k = __ldg(a.probe_slot + smp);
           const T* y = sY + (size_t)s_grp[k] * nmom + (size_t)r * C * nb;   // U_h = u . x_g
-          const T* u = sU + (size_t)ql * nb;
+          const T* u = sU + (size_t)ql * us;
           T acc = R::zero();
           for (int jj = 0; jj < nb; ++jj) acc = R::acc(acc, y[jj], u[jj]);
           const int rg = (rsplit ? rank * nrhs : 0) + r;
@@ -2070,7 +2072,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
             double tt = 0.0;
             for (int i = 0; i < NV; ++i) tt = fma(__ldg(a.bary + q * NV + i), side == 0 ? s_tt[k][i] : s_tb[k][i], tt);
             double Fx[C], dFx[C], Fm[C], dFm[C];
-            fields4(g, r, sU + (size_t)ql * nb, tt - tc, Fx, dFx, Fm, dFm);
+            fields4(g, r, sU + (size_t)ql * us, tt - tc, Fx, dFx, Fm, dFm);
             const double ic2 = s_gic2[g], dic2 = -2.0 * ic2 / s_gc[g];   // c^-2 and its derivative
             const double* gk = side == 0 ? s_gt[k] : s_gb[k];
             // c^-2 a_v b_v + a_s.b_s - a_v (b_s.g) - (a_s.g) b_v: the face form of eq. (4.1)
@@ -2153,7 +2155,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
             double tt = 0.0;
             for (int i = 0; i < NV; ++i) tt = fma(__ldg(a.bary + q * NV + i), s_fP[f][i][DIM], tt);
             double Fx[C], dFx[C], Fm[C], dFm[C];
-            fields4(gp, r, sU + (size_t)ql * nb, tt - tc, Fx, dFx, Fm, dFm);
+            fields4(gp, r, sU + (size_t)ql * us, tt - tc, Fx, dFx, Fm, dFm);
             auto sn = [&](const double* F_) {
               double t_ = 0.0;
               for (int d = 0; d < DIM; ++d) t_ = fma(s_fn[f][d], F_[2 + d], t_);
@@ -2161,7 +2163,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
             };
             if (ifc) {
               double Gx[C], dGx[C], Gm[C], dGm[C], Z[C];
-              fields4(gm, r, sU + (size_t)(nq + ql) * nb, tt - tc, Gx, dGx, Gm, dGm);
+              fields4(gm, r, sU + (size_t)(nq + ql) * us, tt - tc, Gx, dGx, Gm, dGm);
               for (int cc = 0; cc < C; ++cc) Z[cc] = 0.0;
               // the interface form of eq. (2.5) with trial fields X+-, test fields M+-
               auto I = [&](const double* Xp, const double* Xm, const double* Mp, const double* Mm) {
@@ -2217,7 +2219,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
       for (int id = tid; id < nq * nrhs; id += blockDim.x) {
         const int r = id / nq, ql = id % nq;
         const int qg = base + ql, k = qg / Q, q = qg % Q;
-        const T* u = keep ? sKeep + (size_t)(base - q0 + ql) * nb : sU + (size_t)ql * nb;
+        const T* u = keep ? sKeep + (size_t)(base - q0 + ql) * nb : sU + (size_t)ql * us;
         const T* y = sY + (size_t)s_grp[k] * nmom + (size_t)r * C * nb;
         T t[C];
 #pragma unroll
@@ -2227,17 +2229,22 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
 #pragma unroll
           for (int cc = 0; cc < C; ++cc) t[cc] = R::acc(t[cc], y[cc * nb + j], uj);
         }
-        const double sc = keep ? sKeepW[base - q0 + ql] : 1.0;
         double* f = front + (((int64_t)r * a.ne + s_el[k]) * Q + q) * C;
+        if (keep) {
+          const double sc = sKeepW[base - q0 + ql];
 #pragma unroll
-        for (int cc = 0; cc < C; ++cc) f[cc] = R::to(R::norm(t[cc])) * sc;
+          for (int cc = 0; cc < C; ++cc) f[cc] = R::to(R::norm(t[cc])) * sc;
+        } else {
+#pragma unroll
+          for (int cc = 0; cc < C; ++cc) f[cc] = R::to(R::norm(t[cc]));
+        }
       }
     } else {
       // lambda_bot = w (s0, c^-2 s_t - g_b.s, s_m - g_b,m s_t)
       for (int id = tid; id < nq * nrhs; id += blockDim.x) {
         const int ql = id / nrhs, r = id % nrhs;
         const int qg = base + ql, k = qg / Q, q = qg % Q;
-        const T* u = sU + (size_t)ql * nb;
+        const T* u = sU + (size_t)ql * us;
         double sv[C];
         for (int cc = 0; cc < C; ++cc) {
           const T* y = sY + (size_t)s_grp[k] * nmom + ((size_t)r * C + cc) * nb;
