@@ -2214,6 +2214,21 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
     eval_uvalues_block<DIM, T, false>(a, nq, sPt, sM, sU);
     }
     if constexpr (!ADJ) {
+      // few right-hand sides: one (point, right-hand side, component) per
+      // thread, so that every warp (and every sub-partition's binary64 unit)
+      // has work
+      if (nq * nrhs < (int)blockDim.x) {
+        for (int id = tid; id < nq * nrhs * C; id += blockDim.x) {
+          const int cc = id % C, rq = id / C, r = rq / nq, ql = rq % nq;
+          const int qg = base + ql, k = qg / Q, q = qg % Q;
+          const T* u = keep ? sKeep + (size_t)(base - q0 + ql) * nb : sU + (size_t)ql * us;
+          const T* y = sY + (size_t)s_grp[k] * nmom + ((size_t)r * C + cc) * nb;
+          T t = R::zero();
+          for (int j = 0; j < nb; ++j) t = R::acc(t, y[j], u[j]);
+          const double val = R::to(R::norm(t));
+          front[(((int64_t)r * a.ne + s_el[k]) * Q + q) * C + cc] = keep ? val * sKeepW[base - q0 + ql] : val;
+        }
+      } else
       // one (point, right-hand side) per thread, its C components as
       // independent sums (consecutive threads: consecutive points)
       for (int id = tid; id < nq * nrhs; id += blockDim.x) {
