@@ -110,6 +110,19 @@ typedef struct tp_params {
    * for the wave-speed gradient; 0 = the context does not compute it (> 0
    * also keeps a copy of the initial front at every tp_set_state). */
   int32_t ckpt_stride;
+  /* tensor_cores: 0 = automatic: the mixed forward sweep with split
+   *   right-hand sides (rhs_split > 1) runs the data moments and the outflow
+   *   of single-material tents as exact digit products on the tensor cores
+   *   (tcgen05): each float-float operand split into five signed 9-bit
+   *   digits with a power-of-two scale per row (per column), the digit
+   *   products summed exactly in binary32 tensor memory, i.e. contractions
+   *   exact to ~2^-42 of the scales, as close as the compensated float-float
+   *   sums they replace; used when the context's shared-memory plan allows
+   *   it (nrhs / rhs_split * (dim + 2) <= 128, dim U^p <= 32, point chunks
+   *   of 16 or 48, or 16 when two CTAs share an SM;
+   *   tp_ctx_tensor_cores reports the choice).  -1 = never (float-float sums
+   *   on the CUDA cores). */
+  int32_t tensor_cores;
 } tp_params;
 
 typedef struct tp_tents tp_tents;
@@ -173,6 +186,11 @@ int tp_ctx_info(const tp_ctx* ctx, int64_t* n_front, int32_t* n_comp, int64_t* n
  * the other.  Any pointer may be NULL. */
 int tp_ctx_schedule(const tp_ctx* ctx, int32_t* dataflow, int32_t* cluster, int32_t* rhs_split,
                     int32_t* rhs_groups);
+/* *used = 1 when the context's forward sweep runs the data moments and the
+ * outflow of single-material tents on the tensor cores (tp_params.tensor_cores),
+ * 0 when it sums them on the CUDA cores.  Errors: TP_ERR_ARG for a null
+ * context or pointer. */
+int tp_ctx_tensor_cores(const tp_ctx* ctx, int32_t* used);
 /* Front points (Section 4.1: one spatial rule mapped onto the faces):
  * host arrays xq (n_front x dim) and wq (n_front) physical weights. */
 int tp_front_points(const tp_ctx* ctx, double* xq, double* wq);

@@ -117,7 +117,11 @@ class Solver:
     loses (the jump terms of eq. 2.5) to a sum that energy_and_dissipation()
     reports.  ckpt_stride: levels between the forward checkpoints of the
     wave-speed gradient (adjoint(..., dJ_dc=...)); 0 = no gradient with
-    respect to c.  tents: a Tents object to
+    respect to c.  tensor_cores: True lets the mixed forward sweep with split
+    right-hand sides run its data moments and outflow as exact digit
+    products on the tensor cores where the plan allows it
+    (tp_params.tensor_cores; tensor_cores_used() tells); False keeps the
+    float-float sums.  tents: a Tents object to
     sweep over instead of pitching the mesh with c (the wave speeds always
     come from c; see speed_gradient).  All device memory handed to libtp is
     torch CUDA float64 memory; the current torch stream is passed to every
@@ -126,7 +130,7 @@ class Solver:
     def __init__(self, coords, elems, c, p: int, T: float, kappa: float, alpha: float = 0.5,
                  nrhs: int = 1, tents: Tents | None = None, precision: str = "fp64",
                  schedule: str = "dataflow", bnd_type=None, beta: float = 0.5, rhs_split: int = 0,
-                 track_dissipation: bool = False, ckpt_stride: int = 0):
+                 track_dissipation: bool = False, ckpt_stride: int = 0, tensor_cores: bool = True):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("libtp Solver needs a CUDA device")
@@ -143,7 +147,8 @@ class Solver:
                                     precision=B.TP_FP64 if precision == "fp64" else B.TP_MIXED,
                                     schedule=B.TP_SCHED_DATAFLOW if schedule == "dataflow"
                                     else B.TP_SCHED_LEVELS, rhs_split=rhs_split,
-                                    dissipation=1 if track_dissipation else 0, ckpt_stride=ckpt_stride)
+                                    dissipation=1 if track_dissipation else 0, ckpt_stride=ckpt_stride,
+                                    tensor_cores=0 if tensor_cores else -1)
         h = ct.c_void_p()
         B.check(lib.tp_create(ct.byref(self._mesh.desc), self.tents.handle, self.basis.handle,
                               ct.byref(self.params), ct.byref(h)))
@@ -318,6 +323,13 @@ class Solver:
         B.check(B.load().tp_ctx_schedule(self.handle, *[ct.byref(x) for x in v]))
         return {"dataflow": bool(v[0].value), "cluster": int(v[1].value), "rhs_split": int(v[2].value),
                 "rhs_groups": int(v[3].value)}
+
+    def tensor_cores_used(self) -> bool:
+        """tp_ctx_tensor_cores: whether the forward sweep runs the data moments
+        and the outflow of single-material tents on the tensor cores."""
+        v = ct.c_int32()
+        B.check(B.load().tp_ctx_tensor_cores(self.handle, ct.byref(v)))
+        return bool(v.value)
 
     def dofs_per_sweep(self) -> int:
         """Trefftz dofs advanced by one full sweep: sum over tents of (materials

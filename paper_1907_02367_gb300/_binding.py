@@ -22,7 +22,7 @@ TP_SCHED_DATAFLOW, TP_SCHED_LEVELS = 0, 1
 EXPORTED = [
     "tp_last_error", "tp_pitch_mesh", "tp_tents_info", "tp_tents_export", "tp_destroy_tents",
     "tp_build_basis", "tp_basis_info", "tp_basis_export", "tp_destroy_basis", "tp_create",
-    "tp_ctx_info", "tp_ctx_schedule", "tp_set_probes", "tp_get_probes", "tp_set_front", "tp_set_limits", "tp_inject_wait", "tp_solve_stats",
+    "tp_ctx_info", "tp_ctx_schedule", "tp_ctx_tensor_cores", "tp_set_probes", "tp_get_probes", "tp_set_front", "tp_set_limits", "tp_inject_wait", "tp_solve_stats",
     "tp_front_points", "tp_boundary_points", "tp_boundary_kinds", "tp_set_state", "tp_solve_layer",
     "tp_advance", "tp_adjoint", "tp_autotune", "tp_energy", "tp_get_state", "tp_sync_status", "tp_destroy_ctx",
     "tp_front_energy_noalloc", "tp_measure_alu_peaks",
@@ -45,7 +45,7 @@ class Params(ct.Structure):
     _fields_ = [("p", ct.c_int32), ("alpha", ct.c_double), ("beta", ct.c_double),
                 ("kappa", ct.c_double), ("T", ct.c_double), ("precision", ct.c_int32),
                 ("nrhs", ct.c_int32), ("schedule", ct.c_int32), ("rhs_split", ct.c_int32),
-                ("dissipation", ct.c_int32), ("ckpt_stride", ct.c_int32)]
+                ("dissipation", ct.c_int32), ("ckpt_stride", ct.c_int32), ("tensor_cores", ct.c_int32)]
 
 
 _lib = None
@@ -74,6 +74,7 @@ def load(path: str = LIB_PATH):
         "tp_create": (ct.c_int, [P(MeshDesc), vp, vp, P(Params), P(vp)]),
         "tp_ctx_info": (ct.c_int, [vp, P(i64), P(i32), P(i64), P(i32)]),
         "tp_ctx_schedule": (ct.c_int, [vp, P(i32), P(i32), P(i32), P(i32)]),
+        "tp_ctx_tensor_cores": (ct.c_int, [vp, P(i32)]),
         "tp_set_probes": (ct.c_int, [vp, i32, vp, i32, vp]),
         "tp_get_probes": (ct.c_int, [vp, vp, vp]),
         "tp_set_front": (ct.c_int, [vp, vp, vp, vp]),
@@ -133,9 +134,9 @@ class _MeshArrays:
 
 
 def make_params(p, T, kappa, alpha=0.5, beta=0.5, precision=TP_FP64, nrhs=1,
-                schedule=TP_SCHED_DATAFLOW, rhs_split=0, dissipation=0, ckpt_stride=0) -> Params:
+                schedule=TP_SCHED_DATAFLOW, rhs_split=0, dissipation=0, ckpt_stride=0, tensor_cores=0) -> Params:
     return Params(int(p), float(alpha), float(beta), float(kappa), float(T), int(precision), int(nrhs),
-                  int(schedule), int(rhs_split), int(dissipation), int(ckpt_stride))
+                  int(schedule), int(rhs_split), int(dissipation), int(ckpt_stride), int(tensor_cores))
 
 
 def stream_ptr(stream=None) -> int:

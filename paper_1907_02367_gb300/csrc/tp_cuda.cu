@@ -169,6 +169,7 @@ struct tp_ctx {
   int n_sm = 152, max_cs = 1;
   // right-hand sides split over the CTAs of a tent's cluster (1: not split)
   int rsplit_cs = 1;
+  bool tc_used = false;   // tensor-core moments and outflow in the forward sweep
   bool mixed = false;
   // persistent dataflow sweep
   bool persistent = true;
@@ -508,6 +509,7 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
   int *ddp, *ddv, *ddn, *dqt;
   double *drf, *dtf;
   float2* dcdd;
+  float2* dsqwff = nullptr;
   float *drff, *dtff;
   std::vector<float2> coef_dd(basis->sp_coef.size());
   for (size_t i = 0; i < coef_dd.size(); ++i) {
@@ -519,6 +521,12 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
   long long* dgo;
   std::vector<double> sqw(Q);
   for (int q = 0; q < Q; ++q) sqw[q] = std::sqrt(ctx->rule.w[q]);
+  // sqrt(w) as a float-float pair (hi = nearest binary32, lo = the rest rounded)
+  std::vector<float2> sqw_ff(Q);
+  for (int q = 0; q < Q; ++q) {
+    const float h = (float)sqw[q];
+    sqw_ff[q] = make_float2(h, (float)(sqw[q] - (double)h));
+  }
   std::vector<double> ttop(tents->t_top.begin(), tents->t_top.end());
   std::vector<double> tbot(tents->t_bot.begin(), tents->t_bot.end());
   double* dtbot = nullptr;
@@ -725,7 +733,7 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
       (rc = ctx_upload(ctx, &dvar, basis->var)) || (rc = ctx_upload(ctx, &drp, basis->rel_ptr)) ||
       (rc = ctx_upload(ctx, &drs, basis->rel_src)) || (rc = ctx_upload(ctx, &drf, basis->rel_fac)) ||
       (rc = ctx_upload(ctx, &dtp, basis->relT_ptr)) || (rc = ctx_upload(ctx, &dtd, basis->relT_dst)) ||
-      (rc = ctx_upload(ctx, &dtf, basis->relT_fac)) || (rc = ctx_upload(ctx, &dcdd, coef_dd)) ||
+      (rc = ctx_upload(ctx, &dtf, basis->relT_fac)) || (rc = ctx_upload(ctx, &dcdd, coef_dd)) || (rc = ctx_upload(ctx, &dsqwff, sqw_ff)) ||
       (rc = ctx_upload(ctx, &drff, rel_ff)) || (rc = ctx_upload(ctx, &dtff, relT_ff)))
     return fail(rc == TP_ERR_CUDA ? TP_ERR_OOM : rc);
   const size_t nfront = (size_t)ctx->nrhs * T.ne * Q * ctx->C;
@@ -881,6 +889,7 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
   a.relT_dst = dtd;
   a.relT_fac = dtf;
   a.sp_coef_dd = dcdd;
+  a.sqw_dd = dsqwff;
   a.rel_facf = drff;
   a.relT_facf = dtff;
   a.tau = ctx->d_tau;
@@ -906,6 +915,7 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
   int nrg = ctx->nrhs;   // right-hand sides per group
   bool ifneu = false;   // some tent has interface or Neumann facets
   for (const auto& m : facet_mix) ifneu = ifneu || m[2] > 0 || m[3] > 0;
+  bool tc_try = false;   // the plan with the tensor-core staging
   auto plan = [&](int CH, int keep) {
     size_t off = 0;
     auto take = [&](int* field, size_t count) {
@@ -942,7 +952,23 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
     take(&a.off_pgb, (size_t)ngmax * npair);
     take(&a.off_pm, (size_t)ngmax * nmom);        // moments: partials, summed in place, then the outflow vectors
     a.off_sm = a.off_y = a.off_pm;
-    take(&a.off_pd, pd);
+    // tensor-core staging (bf16 digit planes), in the region of the facet
+    // sums (dead during the point passes before phase 2 and during the
+    // outflow): the moments' A (rows of data coefficients x CH points) and B
+    // (32 basis functions x CH points), or the outflow's A (rows x 32) and B
+    // (2 CH points x 32), plus room for the row groups that A's M = 128 tile
+    // reads past its stored rows
+    size_t tcd = 0;
+    if (tc_try) {
+      const size_t RG = ((size_t)nrg * C + 7) / 8, NP2 = ((size_t)2 * CH + 15) / 16 * 16;
+      const size_t NY = ((size_t)nrg * C + 15) / 16 * 16;
+      const size_t mom = (size_t)tp::kTcSlices * CH * (RG * 8 + 32);
+      const size_t out = (size_t)tp::kTcSlices * 32 * (NP2 + NY);
+      tcd = ((std::max(mom, out) + 512 + 3) / 4 + 1) & ~(size_t)1;
+    }
+    off += off & 1;                                // 16-byte alignment of the staging
+    a.off_tc = (int)off;
+    take(&a.off_pd, std::max(pd, tcd));
     // facet Grams of interface and Neumann facets (none on meshes without them)
     take(&a.off_f, ifneu ? npair : 0);
     take(&a.off_f2, ifneu ? npair : 0);
@@ -980,18 +1006,42 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
   // the most right-hand sides per group (a divisor of nrhs, a multiple of rs)
   // whose plan fits; the plan holds one CTA's nrg = group / rs of them
   int grp = 0;
-  for (grp = ctx->nrhs; grp >= 1 && CH == 0; --grp) {
-    if (ctx->nrhs % grp || grp % rs) continue;
-    nrg = grp / rs;
-    for (size_t cap : {kTwoPerSmSmem, max_dyn}) {
-      for (int ch : {48, 32, 16, 8})
-        if (CH == 0 && plan(ch, 0) <= cap) CH = ch;
-      if (CH) {
-        cap_used = cap;
-        break;
+  // tensor-core contractions (mixed precision, split right-hand sides): a
+  // first search with their staging, over chunks that are multiples of the
+  // MMA's K step of 16 points and at most 48 points (the level sums of
+  // 48 x 5 digit products of at most 2^16 stay below 2^24), with at most 96
+  // rows (right-hand sides x components: the outflow's five level sums of
+  // that many columns fill the 512 tensor-memory columns) and 32 basis
+  // functions.  The CTA holds all 512 columns: its shared-memory request is
+  // raised above half the SM's, so that no second CTA shares the SM.
+  int smem_sm = 0, dev_ = 0;
+  size_t stat_smem = 0;
+  TP_CUDA_OK(cudaGetDevice(&dev_));
+  TP_CUDA_OK(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev_));
+  TP_CUDA_OK(n == 1 ? tp::layer_static_smem_d1(&stat_smem) : n == 2 ? tp::layer_static_smem_d2(&stat_smem)
+                                                                     : tp::layer_static_smem_d3(&stat_smem));
+  const bool tc_want = prm->tensor_cores >= 0 && ctx->mixed && rs > 1 && nb <= 32 &&
+                       (ctx->nrhs / rs) * C <= 96;
+  for (int pass = 0; pass < 2 && CH == 0; ++pass) {
+    tc_try = tc_want && pass == 0;
+    if (!tc_want && pass == 0) continue;
+    for (grp = ctx->nrhs; grp >= 1 && CH == 0; --grp) {
+      if (ctx->nrhs % grp || grp % rs) continue;
+      nrg = grp / rs;
+      if (tc_try && nrg * C > 96) continue;
+      for (size_t cap : {kTwoPerSmSmem, max_dyn}) {
+        for (int ch : {48, 32, 16, 8}) {
+          if (CH != 0 || plan(ch, 0) > cap) continue;
+          if (tc_try && (ch % 16 != 0 || ch * tp::kTcSlices * 65536 >= (1 << 24))) continue;
+          CH = ch;
+        }
+        if (CH) {
+          cap_used = cap;
+          break;
+        }
       }
+      if (CH) break;
     }
-    if (CH) break;
   }
   if (CH == 0) {
     tp::set_error("tp_create: shared-memory plan does not fit (nb/nrhs too large)");
@@ -1004,10 +1054,15 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
                                                 (size_t)pmax * Q);
   while (keep > 0 && plan(CH, keep) > cap_used) --keep;
   bytes = plan(CH, keep);
+  // one CTA per SM with the tensor-core contractions (it holds all 512 columns)
+  if (tc_try) bytes = std::max(bytes, std::min(max_dyn, (size_t)smem_sm / 2 + 1024 - stat_smem));
   a.CH = CH;
   a.keep_pts = keep;
   a.nrhs = nrg;
   a.rsplit = rs > 1 ? 1 : 0;
+  a.tc = tc_try ? 1 : 0;
+  a.tc_cols = tc_try ? tp::tc_cols_max : 0;
+  ctx->tc_used = tc_try;
   ctx->rsplit_cs = rs;
   ctx->nrhs_g = grp;
   ctx->rhs_groups = ctx->nrhs / grp;
@@ -1079,6 +1134,15 @@ extern "C" int tp_ctx_schedule(const tp_ctx* ctx, int32_t* dataflow, int32_t* cl
   if (cluster) *cluster = ctx->persistent ? ctx->persist_cs : ctx->max_cs;
   if (rhs_split) *rhs_split = ctx->rsplit_cs;
   if (rhs_groups) *rhs_groups = ctx->rhs_groups;
+  return TP_OK;
+}
+
+extern "C" int tp_ctx_tensor_cores(const tp_ctx* ctx, int32_t* used) {
+  if (!ctx || !used) {
+    tp::set_error("tp_ctx_tensor_cores: null argument");
+    return TP_ERR_ARG;
+  }
+  *used = ctx->tc_used ? 1 : 0;
   return TP_OK;
 }
 

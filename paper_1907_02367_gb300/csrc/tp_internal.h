@@ -18,6 +18,8 @@ constexpr int kMaxEvCls = 16;   // classes of basis functions by term count
 constexpr int kMaxPatch = 64;     // elements in one vertex star handled by one CTA
 constexpr int kMaxFacets = 16;    // Dirichlet + interface facets through one vertex
 constexpr int kMaxGroups = 4;     // materials (distinct wave speeds) in one tent
+constexpr int kTcSlices = 5;      // digits per operand of the tensor-core contractions
+constexpr int tc_cols_max = 512;  // tensor-memory columns of an SM, all held by a CTA of the tensor-core path
 
 // ---------------------------------------------------------------------------
 // mesh topology built on the host

@@ -11,6 +11,7 @@
 #include <type_traits>
 
 #include "tp_internal.h"
+#include "tp_tc.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -57,6 +58,7 @@ struct KArgs {
   const double* bary;     // Q * (dim+1)
   const double* wref;     // Q
   const double* sqw;      // Q, sqrt(wref)
+  const float2* sqw_dd;   // Q, sqrt(wref) as a float-float pair
   const double* isqw;     // Q, 1 / sqrt(wref)
   const int* tent_v;
   const double* tent_ttop;
@@ -139,6 +141,13 @@ struct KArgs {
   int keep_pts, off_keep, off_keepw;            // kept top U-values (scaled) and 1/sqrt(w) of a CTA's slice
   int off_b, off_pg, off_ph, off_pgb, off_pm, off_pd, off_sg, off_sm, off_f, off_f2, off_fpm, off_del,
       off_u, off_mono, off_cb, off_gd, off_y, off_rd;
+  // tensor-core contractions (mixed forward sweep with split right-hand
+  // sides, single-material tents): the data moments and the outflow run as
+  // exact digit products on tcgen05 (tp_tc.cuh); off_tc: their staging
+  // (bf16 digit planes, in the region of the facet sums, which is dead in
+  // the point passes before phase 2 and in the outflow), tc_cols
+  // tensor-memory columns held per CTA
+  int tc, off_tc, tc_cols;
 };
 
 __device__ __forceinline__ void flag_error(const KArgs& a, int code, long long info) {
@@ -233,6 +242,33 @@ __device__ __forceinline__ dd dd_mulf(dd a, float f) {   // f exact in binary32
   float e = fmaf(a.hi, f, -p);
   e = fmaf(a.lo, f, e);
   return fast_two_sum(p, e);
+}
+
+// float-float split of a binary64 value, hi = x rounded to binary32 and
+// lo = x - hi rounded, by integer operations on its bits (the binary64 unit,
+// ~2 operations per clock per SM on this GPU, stays free); values outside
+// [2^-74, 2^126) in magnitude (where lo would leave binary32's normal range)
+// take the conversion instructions.  Equal in value to the conversions (a
+// zero lo may carry the sign of x).
+__device__ __forceinline__ dd dd_split(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const int E = (int)((u >> 52) & 0x7FF) - 1023;
+  if (E < -74 || E > 125) {
+    const float h = __double2float_rn(x);
+    return {h, __double2float_rn(x - (double)h)};
+  }
+  const unsigned long long frac = u & ((1ull << 52) - 1);
+  const unsigned int low = (unsigned int)(frac & ((1u << 29) - 1));   // the 29 bits below binary32's fraction
+  unsigned int hb = ((unsigned int)(u >> 63) << 31) | ((unsigned int)(E + 127) << 23) | (unsigned int)(frac >> 29);
+  const bool up = low > (1u << 28) || (low == (1u << 28) && (hb & 1u));
+  hb += up ? 1u : 0u;   // a carry out of the fraction raises the exponent
+  // lo = x - hi = +-(low - up 2^29) 2^(E - 52), |.| <= 2^28 units
+  const int r = (int)low - (up ? (1 << 29) : 0);
+  const int k = E - 52, k1 = k / 2;
+  float lo = __fmul_rn(__fmul_rn(__int2float_rn(r), __uint_as_float((unsigned int)(127 + k1) << 23)),
+                       __uint_as_float((unsigned int)(127 + k - k1) << 23));
+  if (u >> 63) lo = -lo;
+  return {__uint_as_float(hb), lo};
 }
 
 template <typename T>
@@ -592,6 +628,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
   __shared__ double s_tb[tp::kMaxPatch][NV], s_tt[tp::kMaxPatch][NV];
   __shared__ double s_gb[tp::kMaxPatch][DIM], s_gt[tp::kMaxPatch][DIM];
   __shared__ double s_sdet[tp::kMaxPatch], s_isdet[tp::kMaxPatch];
+  // mixed path: g_bot (DIM) and sqrt|det| (slot DIM) of each element and c^-2 of each material as float-float pairs
+  __shared__ float2 s_gbf[MIXED ? tp::kMaxPatch : 1][DIM + 1];
+  __shared__ float2 s_gic2f[tp::kMaxGroups];
   __shared__ double s_fP[tp::kMaxFacets][NV][DIM + 1];   // vertical face simplices (x, t)
   __shared__ double s_fsq[tp::kMaxFacets], s_fn[tp::kMaxFacets][DIM];   // sqrt(n! volume), normal
   __shared__ int s_fg[tp::kMaxFacets], s_fg2[tp::kMaxFacets];   // groups (Dirichlet: one; interface: +, -)
@@ -602,11 +641,25 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
   __shared__ float s_red[2][kThreads / 32];
 
   __shared__ int s_tent;
+  // tensor-core contractions: tensor-memory base, completion barrier of the
+  // MMAs, binary exponents of the rows of A (0) and the columns of B (1)
+  __shared__ uint32_t s_tmem;
+  __shared__ __align__(8) uint64_t s_tcbar;
+  __shared__ int s_tce[2][tc::kMaxM];
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
   const int CS = (int)cluster.num_blocks();
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
+  constexpr bool kTC = MIXED && !ADJ;   // the tensor-core path exists for the mixed forward sweep
+  uint32_t tc_phase = 0;                // parity of the next completion of s_tcbar
+  if (kTC && a.tc) {
+    if (warp == 0) tc::tmem_alloc(&s_tmem, a.tc_cols);
+    if (tid == 0) tc::mbar_init(&s_tcbar, 1);
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+  }
   for (;;) {
   int tent;
   if constexpr (PERSIST) {
@@ -682,6 +735,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
     if (tid < ng) {
       s_gc[tid] = __ldg(rd + DIM + tid);
       s_gic2[tid] = __ldg(rd + DIM + tp::kMaxGroups + tid);
+      if constexpr (MIXED) {
+        const T g2 = R::from(s_gic2[tid]);
+        s_gic2f[tid] = make_float2(g2.hi, g2.lo);
+      }
     }
     const double* rX = rd + DIM + 2 * tp::kMaxGroups;
     for (int k = tid; k < P; k += blockDim.x) {
@@ -767,6 +824,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
     }
     s_sdet[k] = __ldg(a.elem_sdet + el);
     s_isdet[k] = __ldg(a.elem_isdet + el);
+    if constexpr (MIXED) {
+      for (int d = 0; d < DIM; ++d) {
+        const dd gf = dd_split(s_gb[k][d]);
+        s_gbf[k][d] = make_float2(gf.hi, gf.lo);
+      }
+      const dd sf = dd_split(s_sdet[k]);
+      s_gbf[k][DIM] = make_float2(sf.hi, sf.lo);
+    }
     const double ck = s_gc[s_grp[k]];
     if (!(ck * ck * g2 < 1.0)) flag_error(a, TP_ERR_CAUSALITY, tent);   // space-like top face: c |g| < 1
   }
@@ -808,6 +873,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
   }
   __syncthreads();
 
+  // tensor-core contractions for this tent (single material, split right-hand sides)
+  const bool tc_on = kTC && a.tc && ng == 1;
   // ---------------- phase 1: this CTA's slice of the patch points ----------------
   const int NP = P * Q;
   const int slice = (NP + CS - 1) / CS;
@@ -885,6 +952,24 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
         const double isw = __ldg(a.isqw + q) * s_isdet[k];
 #pragma unroll
         for (int cc = 0; cc < C; ++cc) cb[cc] = R::from(fv[cc] * isw);
+      } else if constexpr (MIXED) {
+        // the same coefficients in float-float, the stored values split by
+        // integer operations (no binary64 arithmetic per point and column)
+        const float2 w2 = __ldg(a.sqw_dd + q), d2 = s_gbf[k][DIM], c2 = s_gic2f[s_grp[k]];
+        const dd sw = dd_mul({w2.x, w2.y}, {d2.x, d2.y});
+        dd f[C];
+#pragma unroll
+        for (int cc = 0; cc < C; ++cc) f[cc] = dd_split(fv[cc]);
+        dd gb[DIM];
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) gb[d] = {s_gbf[k][d].x, s_gbf[k][d].y};
+        dd sg = dd_mul(f[2], gb[0]);
+#pragma unroll
+        for (int d = 1; d < DIM; ++d) sg = dd_add(sg, dd_mul(f[2 + d], gb[d]));
+        cb[0] = dd_mul(sw, f[0]);                                                     // gamma
+        cb[1] = dd_mul(sw, R::sub(dd_mul({c2.x, c2.y}, f[1]), sg));                   // alpha
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) cb[2 + d] = dd_mul(sw, R::sub(f[2 + d], dd_mul(f[1], gb[d])));   // beta_m
       } else {
         const double sw = __ldg(a.sqw + q) * s_sdet[k], ic2 = s_gic2[s_grp[k]];
         const double Ub = fv[0], vb = fv[1];
@@ -928,6 +1013,142 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
 #pragma unroll
         for (int cc = 0; cc < C; ++cc) M[cc * nb] = R::add(M[cc * nb], t[cc]);
       }
+    }
+  };
+  // ---- tensor-core contractions (tp_tc.cuh) ----
+  // the digit-plane products of one contraction: level L = i + j sums planes
+  // i of A and j of B over ksteps K steps of 16 into tensor-memory columns
+  // (L - 2) cstride; one thread issues them (tc_issue), every thread waits
+  // (bounded) for their completion (tc_wait, which returns whether they
+  // completed, the same in every thread)
+  auto tc_issue = [&](uint32_t aA, uint32_t planeA, uint32_t lboA, uint32_t aB, uint32_t planeB, uint32_t lboB,
+                      int ksteps, int N, int cstride) {
+    tc::fence_async_smem();
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    if (tid == 0) {
+      const uint32_t id_ = tc::idesc_bf16(tc::kMaxM, N);
+      for (int L = 2; L <= tc::kSlices + 1; ++L) {
+        bool acc = false;
+        for (int i = 1; i <= tc::kSlices; ++i) {
+          const int j = L - i;
+          if (j < 1 || j > tc::kSlices) continue;
+          for (int ks = 0; ks < ksteps; ++ks) {
+            tc::mma_bf16(s_tmem + (uint32_t)((L - 2) * cstride),
+                         tc::sdesc(aA + (uint32_t)(i - 1) * planeA + (uint32_t)ks * 2 * lboA, lboA, 128),
+                         tc::sdesc(aB + (uint32_t)(j - 1) * planeB + (uint32_t)ks * 2 * lboB, lboB, 128), id_, acc);
+            acc = true;
+          }
+        }
+      }
+      tc::commit(&s_tcbar);
+    }
+  };
+  auto tc_wait = [&]() {
+    bool ok = tc::mbar_wait(&s_tcbar, tc_phase, tc::kMaxPolls);
+    if (!ok) {
+      flag_error(a, TP_ERR_TIMEOUT, tent);
+      tc::mbar_wait(&s_tcbar, tc_phase, 16 * tc::kMaxPolls);   // the products still in flight
+    }
+    tc_phase ^= 1u;
+    ok = __syncthreads_and(ok) != 0;
+    tc::fence_after();
+    return ok;
+  };
+  auto tc_product = [&](uint32_t aA, uint32_t planeA, uint32_t lboA, uint32_t aB, uint32_t planeB, uint32_t lboB,
+                        int ksteps, int N, int cstride) {
+    tc_issue(aA, planeA, lboA, aB, planeB, lboB, ksteps, N, cstride);
+    return tc_wait();
+  };
+  // data moments of nq bottom points (U-values in rows 0.. of sU) of a
+  // single-material tent on the tensor cores:
+  //   M[r, c, i] += sum_q cb[q, r, c] U_i(q)
+  // A: the data coefficients, rows (r, c), scaled per row; B: the U-values,
+  // rows i (padded to 32), scaled per basis function; K: the points (padded
+  // to 16 with zeros, at most CH, so that the level sums stay below 2^24)
+  // (tc_mom_start digit-splits the chunk and issues its products; the
+  // caller evaluates the next chunk while they run; tc_mom_finish waits and
+  // adds the level sums into the moments)
+  auto tc_mom_start = [&](int nq) {
+    if constexpr (kTC) {
+      const int M = nrhs * C, RG = (M + 7) >> 3, KC = ((nq + 15) >> 4) << 1;
+      uint16_t* sTA = reinterpret_cast<uint16_t*>(sm + a.off_tc);
+      const int planeA = CH * RG * 8;
+      uint16_t* sTB = sTA + tc::kSlices * planeA + 512;
+      const int planeB = CH * 32;
+      int* eA = s_tce[0];
+      int* eB = s_tce[1];
+      for (int m = tid; m < M + nb; m += blockDim.x) {
+        float mx = 0.f;
+        if (m < M) {
+          const int r = m / C, cc = m % C;
+          for (int ql = 0; ql < nq; ++ql) mx = fmaxf(mx, fabsf(sCB[((size_t)ql * nrhs + r) * C + cc].hi));
+          eA[m] = tc::scale_exp(mx);
+        } else {
+          for (int ql = 0; ql < nq; ++ql) mx = fmaxf(mx, fabsf(sU[(size_t)ql * us + (m - M)].hi));
+          eB[m - M] = tc::scale_exp(mx);
+        }
+      }
+      __syncthreads();
+      // digit planes, one item = 8 consecutive points of one row of A or B
+      for (int id = tid; id < (M + 32) * KC; id += blockDim.x) {
+        const bool isA = id < M * KC;
+        const int id2 = isA ? id : id - M * KC, rows = isA ? M : 32;
+        const int kc = id2 / rows, m = id2 % rows;
+        const bool live = isA || m < nb;
+        const int ex = isA ? eA[m] : (live ? eB[m] : 0);
+        float d[8][tc::kSlices];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int ql = kc * 8 + j;
+          T x = R::zero();
+          if (ql < nq && live) x = isA ? sCB[((size_t)ql * nrhs + m / C) * C + m % C] : sU[(size_t)ql * us + m];
+          tc::digits(x.hi, x.lo, ex, d[j]);
+        }
+        if (isA) tc::store_row8(sTA + ((size_t)(kc * RG + (m >> 3)) * 64 + (m & 7) * 8), planeA, d);
+        else tc::store_row8(sTB + ((size_t)(kc * 4 + (m >> 3)) * 64 + (m & 7) * 8), planeB, d);
+      }
+      tc_issue(tc::smem_addr(sTA), (uint32_t)planeA * 2, (uint32_t)RG * 128, tc::smem_addr(sTB),
+               (uint32_t)planeB * 2, 4 * 128, KC >> 1, 32, 32);
+    }
+  };
+  auto tc_mom_finish = [&]() {
+    if constexpr (kTC) {
+      const int M = nrhs * C;
+      const int* eA = s_tce[0];
+      const int* eB = s_tce[1];
+      const bool ok = tc_wait();
+      // levels -> float-float moments: warp w reads rows 32 (w % 4) .. + 31,
+      // basis functions 16 (w / 4) .. + 15
+      const int q4 = warp & 3, h = warp >> 2;
+      if (ok && 32 * q4 < M) {
+        const int m = 32 * q4 + lane;
+        for (int c8 = 0; c8 < 2; ++c8) {
+          float lv[tc::kSlices][8];
+#pragma unroll
+          for (int l = 0; l < tc::kSlices; ++l)
+            tc::ld8(s_tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)(l * 32 + 16 * h + 8 * c8), lv[l]);
+          tc::wait_ld();
+          if (m < M) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              const int i = 16 * h + 8 * c8 + j;
+              if (i >= nb) continue;
+              float acc[tc::kSlices];
+#pragma unroll
+              for (int l = 0; l < tc::kSlices; ++l) acc[l] = lv[l][j];
+              T v;
+              tc::combine_ff(acc, v.hi, v.lo);
+              tc::ff_scale(v.hi, v.lo, eA[m] + eB[i] - 16);
+              T* Mp = sPM + (size_t)m * nb + i;
+              *Mp = R::add(*Mp, v);
+            }
+          }
+        }
+      }
+      tc::fence_before();
+      __syncthreads();
     }
   };
   for (int base = q0; base < q1; base += CH) {
@@ -991,9 +1212,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
       }
       data_coefs(base, nq);
       eval_uvalues_block<DIM, T>(a, nq, sPt, sM, sU);
-      data_moments(nq, 0);
+      if (tc_on) {
+        if (base > 0) tc_mom_finish();   // the previous chunk's products ran meanwhile
+        tc_mom_start(nq);
+      } else {
+        data_moments(nq, 0);
+      }
       __syncthreads();
     }
+    if (tc_on && NP > 0) tc_mom_finish();
   }
 
   // ---------------- phase 2: vertical faces ----------------
@@ -2193,6 +2420,110 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
       __syncthreads();
     }
   }
+  // tensor-core outflow: f(q)[r, c] = sum_j U_j(q) y[r, c, j] for a chunk
+  // of up to 2 CH top points, one M = 128 tile of points: A = the digit
+  // planes of the points' U-values (rows = points, K = basis functions
+  // padded to 32, scaled per point), B = those of y (rows (r, c) padded to
+  // 16, scaled per row; formed once per tent); the level sums take
+  // tc_cols / kSlices columns each
+  const int M_tc = nrhs * C, NY = (M_tc + 15) & ~15, planeY = 32 * NY;
+  const int planeU = 32 * ((2 * CH + 15) & ~15);
+  if constexpr (kTC) {
+    if (tc_on) {
+      uint16_t* sTB = reinterpret_cast<uint16_t*>(sm + a.off_tc) + tc::kSlices * planeU + 512;
+      for (int m = tid; m < NY; m += blockDim.x) {
+        float mx = 0.f;
+        if (m < M_tc)
+          for (int j = 0; j < nb; ++j) mx = fmaxf(mx, fabsf(sY[(size_t)m * nb + j].hi));
+        s_tce[0][m] = tc::scale_exp(mx);
+      }
+      __syncthreads();
+      for (int id = tid; id < NY * 4; id += blockDim.x) {
+        const int kc = id / NY, m = id % NY;
+        float d[8][tc::kSlices];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int jj = kc * 8 + j;
+          const T x = (m < M_tc && jj < nb) ? sY[(size_t)m * nb + jj] : R::zero();
+          tc::digits(x.hi, x.lo, s_tce[0][m], d[j]);
+        }
+        tc::store_row8(sTB + ((size_t)(kc * (NY >> 3) + (m >> 3)) * 64 + (m & 7) * 8), planeY, d);
+      }
+      // (the first chunk's barriers order these writes before the products)
+    }
+  }
+  auto tc_outflow = [&](int base, int nq) {
+    if constexpr (kTC) {
+      const int NP = (nq + 15) & ~15, RGU = NP >> 3;
+      uint16_t* sTA = reinterpret_cast<uint16_t*>(sm + a.off_tc);
+      uint16_t* sTB = sTA + tc::kSlices * planeU + 512;
+      int* eY = s_tce[0];
+      int* eU = s_tce[1];
+      for (int ql = tid; ql < NP; ql += blockDim.x) {
+        float mx = 0.f;
+        if (ql < nq)
+          for (int j = 0; j < nb; ++j) mx = fmaxf(mx, fabsf(sU[(size_t)ql * us + j].hi));
+        eU[ql] = tc::scale_exp(mx);
+      }
+      __syncthreads();
+      for (int id = tid; id < NP * 4; id += blockDim.x) {
+        const int kc = id / NP, n = id % NP;
+        float d[8][tc::kSlices];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int jj = kc * 8 + j;
+          const T x = (n < nq && jj < nb) ? sU[(size_t)n * us + jj] : R::zero();
+          tc::digits(x.hi, x.lo, eU[n], d[j]);
+        }
+        tc::store_row8(sTA + ((size_t)(kc * RGU + (n >> 3)) * 64 + (n & 7) * 8), planeU, d);
+      }
+      const int cstride = (a.tc_cols / tc::kSlices) & ~31;   // columns per level sum (>= NY)
+      const bool ok = tc_product(tc::smem_addr(sTA), (uint32_t)planeU * 2, (uint32_t)RGU * 128,
+                                 tc::smem_addr(sTB), (uint32_t)planeY * 2, (uint32_t)(NY >> 3) * 128, 2, NY, cstride);
+      // levels -> binary64 front values: the thread of lane l of warp w holds
+      // point 32 (w % 4) + l and the rows (r, c) of half w / 4
+      const int q4 = warp & 3, h = warp >> 2, half = NY >> 1;
+      if (ok && 32 * q4 < nq) {
+        const int ql = 32 * q4 + lane;
+        const bool live = ql < nq;
+        double* fq = front;
+        int ep = 0;
+        if (live) {
+          const int qg = base + ql, k = qg / Q, q = qg % Q;
+          fq = front + ((int64_t)s_el[k] * Q + q) * C;
+          ep = eU[ql] - 16;
+        }
+        const int64_t rstride = (int64_t)a.ne * Q * C;
+        for (int c0 = h * half; c0 < (h + 1) * half; c0 += 8) {
+          float lv[tc::kSlices][8];
+#pragma unroll
+          for (int l = 0; l < tc::kSlices; ++l)
+            tc::ld8(s_tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)(l * cstride + c0), lv[l]);
+          tc::wait_ld();
+          if (live) {
+            int r = c0 / C, cc = c0 - r * C;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              if (c0 + j < M_tc) {
+                float acc[tc::kSlices];
+#pragma unroll
+                for (int l = 0; l < tc::kSlices; ++l) acc[l] = lv[l][j];
+                float sh, se;
+                tc::combine_ff(acc, sh, se);
+                fq[r * rstride + cc] = tc::ff_to_double(sh, se, ep + eY[c0 + j]);
+              }
+              if (++cc == C) {
+                cc = 0;
+                ++r;
+              }
+            }
+          }
+        }
+      }
+      tc::fence_before();
+      __syncthreads();
+    }
+  };
   for (int base = o0; base < o1; base += 2 * CH) {
     const int nq = min(2 * CH, o1 - base);
     if (!keep) {
@@ -2217,7 +2548,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
       // few right-hand sides: one (point, right-hand side, component) per
       // thread, so that every warp (and every sub-partition's binary64 unit)
       // has work
-      if (nq * nrhs < (int)blockDim.x) {
+      if (tc_on) {
+        tc_outflow(base, nq);
+      } else if (nq * nrhs < (int)blockDim.x) {
         for (int id = tid; id < nq * nrhs * C; id += blockDim.x) {
           const int cc = id % C, rq = id / C, r = rq / nq, ql = rq % nq;
           const int qg = base + ql, k = qg / Q, q = qg % Q;
@@ -2294,6 +2627,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
     break;
   }
   }   // tent loop
+  if (kTC && a.tc) {
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0) tc::tmem_free(s_tmem, a.tc_cols);
+  }
 }
 
 
