@@ -1029,19 +1029,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
     tc::fence_after();
     if (tid == 0) {
       const uint32_t id_ = tc::idesc_bf16(tc::kMaxM, N);
-      for (int L = 2; L <= tc::kSlices + 1; ++L) {
-        bool acc = false;
-        for (int i = 1; i <= tc::kSlices; ++i) {
-          const int j = L - i;
-          if (j < 1 || j > tc::kSlices) continue;
-          for (int ks = 0; ks < ksteps; ++ks) {
+      // K steps outermost, so that consecutive products go to different
+      // level sums; the first product of each level overwrites its columns
+      for (int ks = 0; ks < ksteps; ++ks)
+        for (int L = 2; L <= tc::kSlices + 1; ++L)
+          for (int i = max(1, L - tc::kSlices); i <= min(tc::kSlices, L - 1); ++i) {
+            const int j = L - i;
             tc::mma_bf16(s_tmem + (uint32_t)((L - 2) * cstride),
                          tc::sdesc(aA + (uint32_t)(i - 1) * planeA + (uint32_t)ks * 2 * lboA, lboA, 128),
-                         tc::sdesc(aB + (uint32_t)(j - 1) * planeB + (uint32_t)ks * 2 * lboB, lboB, 128), id_, acc);
-            acc = true;
+                         tc::sdesc(aB + (uint32_t)(j - 1) * planeB + (uint32_t)ks * 2 * lboB, lboB, 128), id_,
+                         ks > 0 || i > max(1, L - tc::kSlices));
           }
-        }
-      }
       tc::commit(&s_tcbar);
     }
   };
