@@ -1029,6 +1029,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
     tc::fence_after();
     if (tid == 0) {
       const uint32_t id_ = tc::idesc_bf16(tc::kMaxM, N);
+      if (planeB == 0) {
+        // B's digit planes stacked along N at cstride-row offsets (plane j at
+        // rows (j - 1) cstride): one product per plane i of A and K step puts
+        // A_i B_j into the columns of level i + j for every j at once (the
+        // columns past level S + 1 take unused pairs and are never read)
+        for (int ks = 0; ks < ksteps; ++ks)
+          for (int i = 1; i <= tc::kSlices; ++i)
+            tc::mma_bf16(s_tmem + (uint32_t)((i - 1) * cstride),
+                         tc::sdesc(aA + (uint32_t)(i - 1) * planeA + (uint32_t)ks * 2 * lboA, lboA, 128),
+                         tc::sdesc(aB + (uint32_t)ks * 2 * lboB, lboB, 128), id_, ks > 0 || i > 1);
+      } else
       // K steps outermost, so that consecutive products go to different
       // level sums; the first product of each level overwrites its columns
       for (int ks = 0; ks < ksteps; ++ks)
@@ -1074,7 +1085,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
       uint16_t* sTA = reinterpret_cast<uint16_t*>(sm + a.off_tc);
       const int planeA = CH * RG * 8;
       uint16_t* sTB = sTA + tc::kSlices * planeA + 512;
-      const int planeB = CH * 32;
       int* eA = s_tce[0];
       int* eB = s_tce[1];
       for (int m = tid; m < M + nb; m += blockDim.x) {
@@ -1105,10 +1115,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
           tc::digits(x.hi, x.lo, ex, d[j]);
         }
         if (isA) tc::store_row8(sTA + ((size_t)(kc * RG + (m >> 3)) * 64 + (m & 7) * 8), planeA, d);
-        else tc::store_row8(sTB + ((size_t)(kc * 4 + (m >> 3)) * 64 + (m & 7) * 8), planeB, d);
+        else tc::store_row8(sTB + ((size_t)(kc * 4 * tc::kSlices + (m >> 3)) * 64 + (m & 7) * 8), 4 * 64, d);
       }
-      tc_issue(tc::smem_addr(sTA), (uint32_t)planeA * 2, (uint32_t)RG * 128, tc::smem_addr(sTB),
-               (uint32_t)planeB * 2, 4 * 128, KC >> 1, 32, 32);
+      // B: the planes stacked along N, 32 rows each (planeB = 0 selects the stacked products)
+      tc_issue(tc::smem_addr(sTA), (uint32_t)planeA * 2, (uint32_t)RG * 128, tc::smem_addr(sTB), 0u,
+               (uint32_t)(4 * tc::kSlices) * 128, KC >> 1, 32 * tc::kSlices, 32);
     }
   };
   auto tc_mom_finish = [&]() {
