@@ -337,20 +337,24 @@ def run_ours(args, rank, world, local):
         "data": "synthetic (seeded mesh, 64 seeded Gaussian pulses)",
         "config": dict(CONFIG, parallelism=f"replicas{world}", n_tents=tents.n_tents,
                        n_levels=tents.n_levels, dofs_per_step=dofs,
-                       schedule=solver.schedule()),
+                       schedule=solver.schedule(), tensor_cores=solver.tensor_cores_used()),
         "e2e": {"value": whole_job_rate(dofs, world, e_step), "unit": UNIT,
                 "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "steps": e2e_steps},
         "gpu_launches": 2 * args.steps,
         "roofline": {"bound": "alu", "achieved": ach, "peak": ff_peak, "unit": "TFLOP/s",
                      "frac": ach / ff_peak, "traffic": None,
-                     "kernel": "k_layer<3, float-float, dataflow> (tp_kernel.cuh)",
+                     "kernel": "k_layer<3, float-float, dataflow> (tp_kernel.cuh); data moments and "
+                               "outflow as exact bf16 digit products on tcgen05 (tp_tc.cuh)",
                      "sweep_ms": ms_sweep,
                      "note": "algorithmic flops of one sweep / mean duration of the sweep (events "
                              "around tp_advance on its stream: the sweep kernel and its set-up "
                              "kernel); peak = the float-float multiply-add rate, the binary32 "
                              f"multiply-add peak measured by tp_measure_alu_peaks ({fp32_peak:.1f} "
                              f"TFLOP/s) / {FF_INSTR_PER_FMA} binary32 instructions per compensated "
-                             "multiply-add"},
+                             "multiply-add (the rate of the float-float path this kernel replaces; "
+                             "the two contractions that carry most of the flops run on the tensor "
+                             "cores, whose bf16 rate is not the bound: their products take ~2% of "
+                             "the sweep)"},
         "clocks": clk,
         "mixed_status": st_mixed[0],
         "mixed_rel_err_vs_fp64": mixed_front_rel,
