@@ -976,7 +976,7 @@ extern "C" int tp_create(const tp_mesh_desc* mesh, const tp_tents* tents, const 
     take(&a.off_del, (size_t)nrg * nb);
     take(&a.off_u, (size_t)2 * CH * (nb | 1));
     take(&a.off_pt, (size_t)2 * CH * (n + 2));
-    take(&a.off_cb, (size_t)CH * nrg * C);
+    take(&a.off_cb, (size_t)(CH + 1) * nrg * C);   // data coefficients, rows of CH + 1
     take(&a.off_gd, (size_t)CH * nrg);
     take(&a.off_rd, NB);
     take(&a.off_eq, half_nb);

@@ -701,7 +701,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
   T* sU = reinterpret_cast<T*>(sm + a.off_u);        // 2*CH*nb    U-values (scaled) per (side, point)
   T* sPt = reinterpret_cast<T*>(sm + a.off_pt);      // 2*CH*(DIM+2)  (that, xhat, scale) per point
   T* sM = reinterpret_cast<T*>(sm + a.off_mono);     // 2*CH*mono_stride
-  T* sCB = reinterpret_cast<T*>(sm + a.off_cb);      // CH*nrhs*C  data coefficients
+  T* sCB = reinterpret_cast<T*>(sm + a.off_cb);      // nrhs*C*(CH+1) data coefficients, point fastest
+  const int cbs = CH + 1;                            // their row stride (odd: no bank conflicts along a row)
   T* sGd = reinterpret_cast<T*>(sm + a.off_gd);      // CH*nrhs    Dirichlet data coefficients
   T* sY = reinterpret_cast<T*>(sm + a.off_y);        // NG*nmom    outflow coefficient vectors (sPM, dead after the congruence)
   double* sRD = sm + a.off_rd;                       // N          reciprocal pivots (binary64 path)
@@ -946,12 +947,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
       double fv[C];
 #pragma unroll
       for (int cc = 0; cc < C; ++cc) fv[cc] = __ldcg(f + cc);
-      T* cb = sCB + ((size_t)ql * nrhs + r) * C;
+      T* cb = sCB + (size_t)r * C * cbs + ql;   // component cc at cb[cc * cbs]
       if constexpr (ADJ) {
         // adjoint: zeta = sum_q lambda_q u_q over the top points
         const double isw = __ldg(a.isqw + q) * s_isdet[k];
 #pragma unroll
-        for (int cc = 0; cc < C; ++cc) cb[cc] = R::from(fv[cc] * isw);
+        for (int cc = 0; cc < C; ++cc) cb[cc * cbs] = R::from(fv[cc] * isw);
       } else if constexpr (MIXED) {
         // the same coefficients in float-float, the stored values split by
         // integer operations (no binary64 arithmetic per point and column)
@@ -967,17 +968,17 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
 #pragma unroll
         for (int d = 1; d < DIM; ++d) sg = dd_add(sg, dd_mul(f[2 + d], gb[d]));
         cb[0] = dd_mul(sw, f[0]);                                                     // gamma
-        cb[1] = dd_mul(sw, R::sub(dd_mul({c2.x, c2.y}, f[1]), sg));                   // alpha
+        cb[cbs] = dd_mul(sw, R::sub(dd_mul({c2.x, c2.y}, f[1]), sg));                   // alpha
 #pragma unroll
-        for (int d = 0; d < DIM; ++d) cb[2 + d] = dd_mul(sw, R::sub(f[2 + d], dd_mul(f[1], gb[d])));   // beta_m
+        for (int d = 0; d < DIM; ++d) cb[(2 + d) * cbs] = dd_mul(sw, R::sub(f[2 + d], dd_mul(f[1], gb[d])));   // beta_m
       } else {
         const double sw = __ldg(a.sqw + q) * s_sdet[k], ic2 = s_gic2[s_grp[k]];
         const double Ub = fv[0], vb = fv[1];
         double sg = 0.0;
         for (int d = 0; d < DIM; ++d) sg = fma(fv[2 + d], s_gb[k][d], sg);
         cb[0] = R::from(sw * Ub);                       // gamma
-        cb[1] = R::from(sw * (ic2 * vb - sg));          // alpha
-        for (int d = 0; d < DIM; ++d) cb[2 + d] = R::from(sw * (fv[2 + d] - vb * s_gb[k][d]));   // beta_m
+        cb[cbs] = R::from(sw * (ic2 * vb - sg));          // alpha
+        for (int d = 0; d < DIM; ++d) cb[(2 + d) * cbs] = R::from(sw * (fv[2 + d] - vb * s_gb[k][d]));   // beta_m
       }
     }
   };
@@ -999,9 +1000,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
         for (int ql = part; ql < nq; ql += ps)
           if (s_pgrp[ql] == g) {
             const T u = sU[(size_t)(prow + ql) * us + i];
-            const T* cb = sCB + ((size_t)ql * nrhs + r) * C;
+            const T* cb = sCB + (size_t)r * C * cbs + ql;
 #pragma unroll
-            for (int cc = 0; cc < C; ++cc) t[cc] = R::acc(t[cc], cb[cc], u);
+            for (int cc = 0; cc < C; ++cc) t[cc] = R::acc(t[cc], cb[cc * cbs], u);
           }
 #pragma unroll
       for (int cc = 0; cc < C; ++cc) t[cc] = R::norm(t[cc]);
@@ -1090,8 +1091,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
       for (int m = tid; m < M + nb; m += blockDim.x) {
         float mx = 0.f;
         if (m < M) {
-          const int r = m / C, cc = m % C;
-          for (int ql = 0; ql < nq; ++ql) mx = fmaxf(mx, fabsf(sCB[((size_t)ql * nrhs + r) * C + cc].hi));
+          for (int ql = 0; ql < nq; ++ql) mx = fmaxf(mx, fabsf(sCB[(size_t)m * cbs + ql].hi));
           eA[m] = tc::scale_exp(mx);
         } else {
           for (int ql = 0; ql < nq; ++ql) mx = fmaxf(mx, fabsf(sU[(size_t)ql * us + (m - M)].hi));
@@ -1111,7 +1111,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
         for (int j = 0; j < 8; ++j) {
           const int ql = kc * 8 + j;
           T x = R::zero();
-          if (ql < nq && live) x = isA ? sCB[((size_t)ql * nrhs + m / C) * C + m % C] : sU[(size_t)ql * us + m];
+          if (ql < nq && live) x = isA ? sCB[(size_t)m * cbs + ql] : sU[(size_t)ql * us + m];
           tc::digits(x.hi, x.lo, ex, d[j]);
         }
         if (isA) tc::store_row8(sTA + ((size_t)(kc * RG + (m >> 3)) * 64 + (m & 7) * 8), planeA, d);
