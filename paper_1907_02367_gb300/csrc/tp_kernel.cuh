@@ -982,6 +982,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
       }
     }
   };
+  // the front records (C values each) that data_coefs(base, nq) will read,
+  // prefetched into L2 (their latency then overlaps the work on the chunk before)
+  auto prefetch_front = [&](int base, int nq) {
+    for (int id = tid; id < nq * nrhs; id += blockDim.x) {
+      const int r = id / nq, ql = id % nq, qg = base + ql, k = qg / Q, q = qg % Q;
+      const double* f = front + (((int64_t)r * a.ne + s_el[k]) * Q + q) * C;
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(f));
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(f + C - 1));
+    }
+  };
   // moments of the data of nq points whose U-values are rows prow.. of sU, per
   // material: one (material, right-hand side, basis function) per group of
   // ps lanes with its C components as independent sums; the lanes of a group
@@ -1212,6 +1222,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
     // this CTA's right-hand sides at every point of the patch (forward: the
     // bottom points; adjoint: the top points): the moments are complete in
     // this CTA and take no cluster reduction
+    prefetch_front(0, min(CH, NP));
     for (int base = 0; base < NP; base += CH) {
       const int nq = min(CH, NP - base);
       for (int id = tid; id < nq; id += blockDim.x) {
@@ -1220,6 +1231,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
         map_point(sPt + id * (DIM + 2), k, q, ADJ);
       }
       data_coefs(base, nq);
+      if (base + CH < NP) prefetch_front(base + CH, min(CH, NP - base - CH));
       eval_uvalues_block<DIM, T>(a, nq, sPt, sM, sU);
       if (tc_on) {
         if (base > 0) tc_mom_finish();   // the previous chunk's products ran meanwhile
