@@ -1098,15 +1098,19 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
       uint16_t* sTB = sTA + tc::kSlices * planeA + 512;
       int* eA = s_tce[0];
       int* eB = s_tce[1];
-      for (int m = tid; m < M + nb; m += blockDim.x) {
+      // two threads per row (M + nb <= 128 rows, so every thread takes part
+      // once and the pair's maxima meet by one shuffle)
+      {
+        const int m = tid >> 1, part = tid & 1;
         float mx = 0.f;
         if (m < M) {
-          for (int ql = 0; ql < nq; ++ql) mx = fmaxf(mx, fabsf(sCB[(size_t)m * cbs + ql].hi));
-          eA[m] = tc::scale_exp(mx);
-        } else {
-          for (int ql = 0; ql < nq; ++ql) mx = fmaxf(mx, fabsf(sU[(size_t)ql * us + (m - M)].hi));
-          eB[m - M] = tc::scale_exp(mx);
+          for (int ql = part; ql < nq; ql += 2) mx = fmaxf(mx, fabsf(sCB[(size_t)m * cbs + ql].hi));
+        } else if (m < M + nb) {
+          for (int ql = part; ql < nq; ql += 2) mx = fmaxf(mx, fabsf(sU[(size_t)ql * us + (m - M)].hi));
         }
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+        if (part == 0 && m < M) eA[m] = tc::scale_exp(mx);
+        if (part == 0 && m >= M && m < M + nb) eB[m - M] = tc::scale_exp(mx);
       }
       __syncthreads();
       // digit planes, one item = 8 consecutive points of one row of A or B
@@ -1167,7 +1171,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
         }
       }
       tc::fence_before();
-      __syncthreads();
+      __syncthreads();   // the exponents and columns read above are rewritten by the next chunk
     }
   };
   for (int base = q0; base < q1; base += CH) {
@@ -1235,11 +1239,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
       eval_uvalues_block<DIM, T>(a, nq, sPt, sM, sU);
       if (tc_on) {
         if (base > 0) tc_mom_finish();   // the previous chunk's products ran meanwhile
-        tc_mom_start(nq);
+        tc_mom_start(nq);                // (its issue barrier orders this chunk's reads before the next writes)
       } else {
         data_moments(nq, 0);
+        __syncthreads();
       }
-      __syncthreads();
     }
     if (tc_on && NP > 0) tc_mom_finish();
   }
