@@ -118,8 +118,9 @@ typedef struct tp_params {
    *   products summed exactly in binary32 tensor memory, i.e. contractions
    *   exact to ~2^-42 of the scales, as close as the compensated float-float
    *   sums they replace; used when the context's shared-memory plan allows
-   *   it (nrhs / rhs_split * (dim + 2) <= 128, dim U^p <= 32, point chunks
-   *   of 16 or 48, or 16 when two CTAs share an SM;
+   *   it (nrhs / rhs_split * (dim + 2) <= 96, dim U^p <= 32, point chunks a
+   *   multiple of 16 and at most 48; the CTA then takes one SM and all 512
+   *   tensor-memory columns; multi-material tents keep the float-float sums;
    *   tp_ctx_tensor_cores reports the choice).  -1 = never (float-float sums
    *   on the CUDA cores). */
   int32_t tensor_cores;

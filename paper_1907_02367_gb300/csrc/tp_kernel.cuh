@@ -2449,8 +2449,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_layer(const KArgs a, const int 
   // of up to 2 CH top points, one M = 128 tile of points: A = the digit
   // planes of the points' U-values (rows = points, K = basis functions
   // padded to 32, scaled per point), B = those of y (rows (r, c) padded to
-  // 16, scaled per row; formed once per tent); the level sums take
-  // tc_cols / kSlices columns each
+  // 16, scaled per row; formed once per tent); each level sum takes
+  // (tc_cols / kSlices) rounded down to 32, i.e. 96 columns (>= NY)
   const int M_tc = nrhs * C, NY = (M_tc + 15) & ~15, planeY = 32 * NY;
   const int planeU = 32 * ((2 * CH + 15) & ~15);
   if constexpr (kTC) {
