@@ -19,6 +19,9 @@ from paper_1907_02367_gb300 import inputs
 def test_legendre_and_chebyshev_polynomials_exact():
     assert ob.poly1d("legendre", 3) == [0, Fraction(-3, 2), 0, Fraction(5, 2)]
     assert ob.poly1d("chebyshev", 4) == [1, 0, -8, 0, 8]
+    # a 2D index is the tensor product: P_2(x) P_1(y) = (3x^2 - 1)/2 * y
+    assert ob.initial_polynomial("legendre", (2, 1)) == {(0, 1): Fraction(-1, 2), (2, 1): Fraction(3, 2)}
+    assert ob.initial_polynomial("chebyshev", (1, 2)) == {(1, 0): Fraction(-1), (1, 2): Fraction(2)}
 
 
 @pytest.mark.parametrize("init", ["legendre", "chebyshev"])

@@ -24,6 +24,7 @@ import oracle.adjoint  # noqa: E402
 import oracle.tdg  # noqa: E402
 import test_oracle_adjoint as Az  # noqa: E402
 import test_oracle_basis as Bz  # noqa: E402
+import test_oracle_basis_variants as Vz  # noqa: E402
 import test_oracle_dissipation as Dz  # noqa: E402
 import test_oracle_pitching as Pz  # noqa: E402
 import test_oracle_quadrature as Qz  # noqa: E402
@@ -31,7 +32,8 @@ import test_oracle_tdg as Tz  # noqa: E402
 
 
 def _mutant(name: str, old: str, new: str):
-    path = os.path.join(ROOT, "oracle", name + ".py")
+    # (the basis-variant pins take mutants of oracle/basis.py)
+    path = os.path.join(ROOT, "oracle", {"basis_variants": "basis"}.get(name, name) + ".py")
     with open(path) as f:
         src = f.read()
     assert src.count(old) == 1, f"mutation site not unique in oracle/{name}.py: {old!r}"
@@ -61,6 +63,11 @@ BASIS_PINS = [
     lambda: Bz.test_trefftz_property_exact(3, 3),
     lambda: Bz.test_derivative_tables_fd(2, 4),
 ] + TDG_PINS
+VARIANT_PINS = [
+    lambda: Vz.test_legendre_and_chebyshev_polynomials_exact(),
+    lambda: Vz.test_every_start_gives_trefftz_functions_of_the_same_space("legendre", 2, 4),
+    lambda: Vz.test_every_start_gives_trefftz_functions_of_the_same_space("chebyshev", 3, 3),
+]
 QUAD_PINS = [
     lambda: Qz.test_simplex_moments_exact(2, 3),
     lambda: Qz.test_simplex_moments_exact(3, 3),
@@ -147,6 +154,13 @@ MUTATIONS = [
     ("adjoint-global-stale-front", "adjoint", "            last[K] = (it, Em[j * blk:(j + 1) * blk, :])",
      "            last[K] = last[K] or (it, Em[j * blk:(j + 1) * blk, :])"),
     ("adjoint-transposed-gradient-sign", "adjoint", "y @ (dR @ f0 - dM @ x)", "y @ (dR @ f0 + dM @ x)"),
+    ("basis-legendre-recursion-sign", "basis_variants",
+     "(Fraction(2 * j + 1) * xp[i] - Fraction(j) * prev[i]) / (j + 1)",
+     "(Fraction(2 * j + 1) * xp[i] + Fraction(j) * prev[i]) / (j + 1)"),
+    ("basis-chebyshev-recursion-factor", "basis_variants",
+     "P.append([2 * xp[i] - prev[i] for i in range(j + 2)])", "P.append([xp[i] - prev[i] for i in range(j + 2)])"),
+    ("basis-tensor-product-factor-dropped", "basis_variants",
+     "new.get(key + (e,), Fraction(0)) + v * cf", "new.get(key + (e,), Fraction(0)) + cf"),
 ]
 
 
@@ -158,6 +172,10 @@ def _install(monkeypatch, name, mod):
         monkeypatch.setattr(Bz, "bz", mod)
         monkeypatch.setattr(oracle.tdg, "_basis", mod)
         return BASIS_PINS
+    if name == "basis_variants":
+        monkeypatch.setattr(Vz, "ob", mod)
+        monkeypatch.setattr(oracle.tdg, "_basis", mod)
+        return VARIANT_PINS
     if name == "quadrature":
         monkeypatch.setattr(Qz, "q", mod)
         return QUAD_PINS
@@ -188,7 +206,7 @@ def test_planted_mistake_fails_a_pin(monkeypatch, mid, name, old, new):
     assert caught, f"no pin fails for the planted mistake {mid}"
 
 
-@pytest.mark.parametrize("name", ["tdg", "basis", "quadrature", "pitching", "energy", "adjoint"])
+@pytest.mark.parametrize("name", ["tdg", "basis", "basis_variants", "quadrature", "pitching", "energy", "adjoint"])
 def test_unplanted_copy_passes_every_pin(monkeypatch, name):
     """The loader itself changes nothing: an unmodified copy passes the pins."""
     pins = _install(monkeypatch, name, _mutant(name, "from __future__ import annotations",
