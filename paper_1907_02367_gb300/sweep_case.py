@@ -29,6 +29,8 @@ def main(argv=None):
     ap.add_argument("--rhs-split", type=int, default=0)
     ap.add_argument("--T", type=float, default=1.0)
     ap.add_argument("--levels", type=int, nargs=2, default=None, metavar=("BEGIN", "END"))
+    ap.add_argument("--no-tensor-cores", action="store_true",
+                    help="keep the float-float sums on the CUDA cores (tp_params.tensor_cores = -1)")
     args = ap.parse_args(argv)
     import torch
     from . import Solver
@@ -43,7 +45,8 @@ def main(argv=None):
         m, p = inputs.mesh_inclusion_graded(h_max=1.0 / args.n), 5
         inits = [inputs.gaussian_pulse((0.45, 0.58), 0.08)] * args.nrhs
     s = Solver(m.coords, m.elems, m.c, p, args.T, inputs.pitch_kappa(m), nrhs=args.nrhs,
-               precision=args.precision, schedule=args.schedule, rhs_split=args.rhs_split)
+               precision=args.precision, schedule=args.schedule, rhs_split=args.rhs_split,
+               tensor_cores=not args.no_tensor_cores)
     xq, _ = s.front_points()
     f0 = torch.empty(s.front_shape(), dtype=torch.float64, device="cuda")
     for r, f in enumerate(inits):
@@ -58,7 +61,8 @@ def main(argv=None):
     e1.synchronize()
     print(json.dumps({"case": args.case, "n": args.n, "n_elem": m.n_elem, "n_tents": s.tents.n_tents,
                       "levels": [L0, L1], "nrhs": args.nrhs, "precision": args.precision,
-                      "schedule": s.schedule(), "ms": e0.elapsed_time(e1), "status": list(s.sync_status())}))
+                      "schedule": s.schedule(), "tensor_cores": s.tensor_cores_used(),
+                      "ms": e0.elapsed_time(e1), "status": list(s.sync_status())}))
 
 
 if __name__ == "__main__":
